@@ -1,0 +1,185 @@
+/*
+ * cbspmv -- cache-friendly blocked sparse matrix-vector product for NVIDIA GB300 (sm_103a).
+ *
+ * The method is CB-SpMV (Cong, Sun, Chen, Xie, Liu, Qian, ICS '25): the matrix is cut
+ * into independent 16x16 sub-blocks (Sec. 3.1); the coordinate bytes and values of each
+ * sub-block are packed behind one virtual pointer (Sec. 3.2); sparse block rows get
+ * block-aware column aggregation and every sub-block a COO / CSR / Dense format
+ * (Sec. 3.3); the sub-blocks are spread over the GPU's workers by a priority-queue load
+ * balance (Sec. 3.4, Algorithm 2); a kernel then forms y = alpha*A*x + beta*y
+ * (Sec. 3.5, Algorithms 3 and 4).
+ *
+ * Conventions that hold for every call:
+ *   - Every call returns a cbspmv_status_t. No call aborts, traps or prints; on failure
+ *     cbspmv_last_error() holds a one-line message for the calling thread.
+ *   - A handle owns all device memory it allocated until cbspmv_destroy(). Handles are
+ *     not thread-safe: one host thread (or external locking) per handle.
+ *   - Device pointers passed to run calls belong to the caller and must stay valid until
+ *     the enqueued work has finished on the given stream. Run calls are asynchronous on
+ *     that stream and do not synchronise the host (cbspmv_run_host is the exception).
+ *   - cudaStream_t is passed as void* (NULL = the legacy default stream), so this header
+ *     needs no CUDA include.
+ *   - BLAS scaling: beta == 0 means y is not read (NaN/Inf in y are overwritten).
+ *   - Matrices are canonical CSR: row_ptr non-decreasing from 0 to nnz, column indices
+ *     strictly increasing inside each row and inside [0, n). Explicitly stored zeros are
+ *     kept as entries. m, n < 2^31; nnz < 2^31.
+ */
+#ifndef CBSPMV_H_
+#define CBSPMV_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cbspmv_handle_s* cbspmv_handle_t;
+
+typedef enum {
+  CBSPMV_OK = 0,
+  CBSPMV_ERR_INVALID = 1,        /* bad argument, size or handle */
+  CBSPMV_ERR_NOT_CANONICAL = 2,  /* CSR not sorted / duplicate columns / index out of range */
+  CBSPMV_ERR_OOM = 3,            /* host or device allocation failed */
+  CBSPMV_ERR_CUDA = 4,           /* a CUDA runtime call failed (message has the CUDA error) */
+  CBSPMV_ERR_TIMEOUT = 5,        /* a bounded device wait gave up (see cbspmv_check_device) */
+  CBSPMV_ERR_UNSUPPORTED = 6,    /* option combination not implemented */
+  CBSPMV_ERR_BUSY = 7            /* resource temporarily unavailable */
+} cbspmv_status_t;
+
+/* Storage type of the matrix values on the device. F64 is the reference path: values,
+ * x, y and accumulation in IEEE double. */
+typedef enum { CBSPMV_F64 = 0, CBSPMV_F32 = 1, CBSPMV_BF16 = 2, CBSPMV_F16 = 3 } cbspmv_dtype_t;
+
+/* Sub-block storage formats (Sec. 3.3.2). */
+enum { CBSPMV_FMT_COO = 0, CBSPMV_FMT_CSR = 1, CBSPMV_FMT_DENSE = 2 };
+
+/* A CSR matrix given by the caller. Values are always FP64 here; cbspmv_analyze copies
+ * everything it needs, so the caller may free the arrays when the call returns.
+ * on_device = 0: the three arrays are host pointers. (Device-resident input is not
+ * supported in this version: CBSPMV_ERR_UNSUPPORTED.) */
+typedef struct {
+  int64_t m, n, nnz;
+  const int64_t* row_ptr;   /* m + 1 entries */
+  const int32_t* col_idx;   /* nnz entries */
+  const double* val;        /* nnz entries */
+  int on_device;
+} cbspmv_csr_t;
+
+/* Analysis options. Fill with cbspmv_default_opts() and override fields.
+ *   th0: column aggregation is applied when the share of "super-sparse" 16x16
+ *        sub-blocks (fewer than th1 nonzeros) exceeds th0 (Sec. 3.3.1; paper: 0.15).
+ *   th1, th2: sub-block format thresholds, COO if nnz < th1, Dense if nnz > th2, CSR
+ *        otherwise (Sec. 3.3.2; paper: 32 and 128). 0 <= th1 <= th2 <= 256.
+ *   col_agg: -1 decide by th0, 0 never aggregate, 1 always aggregate.
+ *   value_dtype: storage type of the values (CBSPMV_F64 for the FP64 path).
+ *   unit_work: target number of multiply-adds per scheduling unit (0 = default).
+ *   load_balance: 1 (default) spread units over workers by the longest-first
+ *        priority-queue rule; 0 deal them out round-robin in matrix order (ablation).
+ *   device: CUDA device ordinal for the handle's memory; -1 builds a host-only handle
+ *        (analysis, export and statistics work; run calls return CBSPMV_ERR_INVALID). */
+typedef struct {
+  double th0;
+  int th1, th2;
+  int col_agg;
+  cbspmv_dtype_t value_dtype;
+  int unit_work;
+  int load_balance;
+  int device;
+  int reserved[8];
+} cbspmv_opts_t;
+
+/* Statistics of an analysed matrix. Byte counts follow the storage model of Sec. 4.4.1
+ * where noted. */
+typedef struct {
+  int64_t m, n, nnz;
+  int64_t n_block_rows;
+  int64_t n_tiles;                 /* non-empty 16x16 sub-blocks after aggregation */
+  int64_t n_tiles_plain;           /* non-empty 16x16 sub-blocks without aggregation */
+  double super_sparse_fraction;    /* share of plain sub-blocks with nnz < th1 */
+  int aggregated;                  /* column aggregation applied (Sec. 3.3.1) */
+  int value_dtype;
+  int64_t n_fmt[3];                /* sub-blocks per format: COO, CSR, Dense */
+  int64_t nnz_fmt[3];              /* stored entries per format */
+  int64_t hist_coarse[8];          /* sub-block nnz histogram 1-32, 33-64, ..., 225-256 */
+  int64_t hist_fine[4];            /* 1-8, 9-16, 17-24, 25-32 */
+  int64_t restore_cols_len;        /* entries of restore_cols (without padding) */
+  int64_t stream_bytes;            /* packed sub-block stream incl. alignment padding */
+  int64_t metadata_bytes;          /* per-sub-block records as stored on the device */
+  int64_t model_bytes_cb;          /* Sec. 4.4.1: nnzb*21 + nnz*9 (all-COO CB model) */
+  int64_t model_bytes_csr;         /* Sec. 4.4.1: (m+1)*4 + nnz*12 */
+  int64_t model_bytes_bsr16;       /* Sec. 4.4.1: 2048*nnzb + (blk_m+1)*4 + 4*nnzb */
+  int64_t algo_bytes_per_run;      /* bytes model of one y = A x (beta = 0) */
+  int64_t flops_per_run;           /* 2 * nnz */
+  int64_t mults_per_run;           /* multiply-adds issued incl. Dense zero fill */
+  int64_t n_units, n_split_units, n_split_rows, n_workers;
+  double worker_load_max, worker_load_mean, worker_load_std;  /* multiply-adds per worker */
+  double tb8_load_std;             /* per-thread-block (8 sub-blocks) nnz std, Algorithm 2 order */
+  double analyze_ms;               /* host time of cbspmv_analyze */
+} cbspmv_stats_t;
+
+/* Fills *opts with the paper's settings: th0 0.15, th1 32, th2 128, col_agg -1,
+ * FP64 values, default unit size, load balance on, device 0. */
+cbspmv_status_t cbspmv_default_opts(cbspmv_opts_t* opts);
+
+/* Analyses a CSR matrix (Sec. 3 overview; Sec. 3.1-3.4): validation, 16x16 tiling, the
+ * column-aggregation decision and aggregation, per-sub-block format selection, packing
+ * into one byte stream with 16-byte aligned virtual pointers, units of work and their
+ * load-balanced assignment to the kernel's workers; then one upload per device array.
+ * stream: upload stream (void* cudaStream_t); the call synchronises it before returning.
+ * On success *out is a new handle. Errors: CBSPMV_ERR_INVALID (NULL pointers, sizes),
+ * CBSPMV_ERR_NOT_CANONICAL, CBSPMV_ERR_OOM, CBSPMV_ERR_CUDA, CBSPMV_ERR_UNSUPPORTED. */
+cbspmv_status_t cbspmv_analyze(const cbspmv_csr_t* A, const cbspmv_opts_t* opts, void* stream,
+                               cbspmv_handle_t* out);
+
+/* y = alpha * A * x + beta * y on the device (Sec. 3.5, Algorithms 3 and 4).
+ * x: device array of n values, y: device array of m values, both of the handle's
+ * vector type (double for CBSPMV_F64 and for all value types in this version), 8-byte
+ * aligned; y must not overlap x. Enqueued on `stream`, no host synchronisation. One
+ * kernel launch. Concurrent runs on one handle must be serialised on one stream (they
+ * share the handle's partial-sum buffer). Errors: CBSPMV_ERR_INVALID, CBSPMV_ERR_CUDA. */
+cbspmv_status_t cbspmv_run(cbspmv_handle_t h, const void* x, void* y, double alpha, double beta,
+                           void* stream);
+
+/* The same product end to end from host memory: copies x (n doubles) to the device,
+ * runs, copies y back (m doubles; read first when beta != 0), then synchronises the
+ * stream. x_host / y_host may be pageable or pinned. Uses staging buffers owned by the
+ * handle (allocated on first use). */
+cbspmv_status_t cbspmv_run_host(cbspmv_handle_t h, const double* x_host, double* y_host,
+                                double alpha, double beta, void* stream);
+
+/* Reads the handle's device error word (set by bounded device-side waits that gave up)
+ * and clears it: CBSPMV_OK or CBSPMV_ERR_TIMEOUT. Synchronises `stream`. */
+cbspmv_status_t cbspmv_check_device(cbspmv_handle_t h, void* stream);
+
+/* Reconstructs the CSR matrix from the handle's device-resident blocked format
+ * (bit-exact round trip of row_ptr, col_idx and the value bits for FP64 values).
+ * Host output arrays of m+1, nnz, nnz entries. Synchronous. */
+cbspmv_status_t cbspmv_export_csr(cbspmv_handle_t h, int64_t* row_ptr, int32_t* col_idx,
+                                  double* val);
+
+/* The high-level metadata of Sec. 3.1 in matrix (row-major) order, before the load
+ * balance: per sub-block its block row, block column (the aggregated block column when
+ * aggregation is on), nnz and format; and the aggregation arrays of Sec. 3.3.1
+ * (cols_offset: n_block_rows + 1 entries; restore_cols: stats.restore_cols_len entries).
+ * Any output pointer may be NULL. Host arrays sized from cbspmv_get_stats(). */
+cbspmv_status_t cbspmv_export_blocked(cbspmv_handle_t h, int32_t* blk_row, int32_t* blk_col,
+                                      int32_t* nnz_per_blk, uint8_t* type_per_blk,
+                                      int64_t* cols_offset, int32_t* restore_cols);
+
+cbspmv_status_t cbspmv_get_stats(cbspmv_handle_t h, cbspmv_stats_t* stats);
+
+/* Frees the handle and all its device memory (synchronises the device first).
+ * NULL is accepted. */
+cbspmv_status_t cbspmv_destroy(cbspmv_handle_t h);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char* cbspmv_last_error(void);
+
+/* Library version string. */
+const char* cbspmv_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CBSPMV_H_ */

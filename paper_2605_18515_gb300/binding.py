@@ -1,0 +1,226 @@
+"""ctypes binding of the cbspmv C ABI (include/cbspmv.h).
+
+Argument marshalling only: every step of the analysis and of the product runs inside
+libcbspmv.so. PyTorch provides device memory and streams. If the library is missing the
+import of this module raises; there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+CBSPMV_OK = 0
+STATUS = {0: "OK", 1: "ERR_INVALID", 2: "ERR_NOT_CANONICAL", 3: "ERR_OOM", 4: "ERR_CUDA",
+          5: "ERR_TIMEOUT", 6: "ERR_UNSUPPORTED", 7: "ERR_BUSY"}
+DTYPES = {"f64": 0, "f32": 1, "bf16": 2, "f16": 3}
+FMT_NAMES = ("COO", "CSR", "DENSE")
+
+
+class CbspmvError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Csr(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p), ("val", ctypes.c_void_p),
+                ("on_device", ctypes.c_int)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("th0", ctypes.c_double), ("th1", ctypes.c_int), ("th2", ctypes.c_int),
+                ("col_agg", ctypes.c_int), ("value_dtype", ctypes.c_int), ("unit_work", ctypes.c_int),
+                ("load_balance", ctypes.c_int), ("device", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("n_block_rows", ctypes.c_int64), ("n_tiles", ctypes.c_int64),
+                ("n_tiles_plain", ctypes.c_int64), ("super_sparse_fraction", ctypes.c_double),
+                ("aggregated", ctypes.c_int), ("value_dtype", ctypes.c_int),
+                ("n_fmt", ctypes.c_int64 * 3), ("nnz_fmt", ctypes.c_int64 * 3),
+                ("hist_coarse", ctypes.c_int64 * 8), ("hist_fine", ctypes.c_int64 * 4),
+                ("restore_cols_len", ctypes.c_int64), ("stream_bytes", ctypes.c_int64),
+                ("metadata_bytes", ctypes.c_int64), ("model_bytes_cb", ctypes.c_int64),
+                ("model_bytes_csr", ctypes.c_int64), ("model_bytes_bsr16", ctypes.c_int64),
+                ("algo_bytes_per_run", ctypes.c_int64), ("flops_per_run", ctypes.c_int64),
+                ("mults_per_run", ctypes.c_int64), ("n_units", ctypes.c_int64),
+                ("n_split_units", ctypes.c_int64), ("n_split_rows", ctypes.c_int64),
+                ("n_workers", ctypes.c_int64), ("worker_load_max", ctypes.c_double),
+                ("worker_load_mean", ctypes.c_double), ("worker_load_std", ctypes.c_double),
+                ("tb8_load_std", ctypes.c_double), ("analyze_ms", ctypes.c_double)]
+
+
+# Every entry point the header declares, with its ctypes signature.
+_P, _D, _I, _I64 = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int64
+SIGNATURES = {
+    "cbspmv_default_opts": [ctypes.POINTER(Opts)],
+    "cbspmv_analyze": [ctypes.POINTER(Csr), ctypes.POINTER(Opts), _P, ctypes.POINTER(_P)],
+    "cbspmv_run": [_P, _P, _P, _D, _D, _P],
+    "cbspmv_run_host": [_P, _P, _P, _D, _D, _P],
+    "cbspmv_check_device": [_P, _P],
+    "cbspmv_export_csr": [_P, _P, _P, _P],
+    "cbspmv_export_blocked": [_P, _P, _P, _P, _P, _P, _P],
+    "cbspmv_get_stats": [_P, ctypes.POINTER(Stats)],
+    "cbspmv_destroy": [_P],
+    "cbspmv_last_error": [],
+    "cbspmv_version": [],
+}
+
+
+def load_library(path: str | None = None) -> ctypes.CDLL:
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libcbspmv.so not built ({path}); run paper_2605_18515_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, args in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_char_p if name in ("cbspmv_last_error", "cbspmv_version") else ctypes.c_int
+    return lib
+
+
+_lib: ctypes.CDLL | None = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        _lib = load_library()
+    return _lib
+
+
+def _check(status: int):
+    if status != CBSPMV_OK:
+        raise CbspmvError(status, lib().cbspmv_last_error().decode())
+
+
+def default_opts() -> Opts:
+    o = Opts()
+    _check(lib().cbspmv_default_opts(ctypes.byref(o)))
+    return o
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream or None
+    if isinstance(stream, int):
+        return stream or None
+    return stream.cuda_stream or None
+
+
+def _dev_ptr(t, n: int, name: str) -> int | None:
+    """Device pointer of a torch tensor holding >= n float64 values (contiguous)."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor on the GPU")
+    if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+    if t.numel() < n:
+        raise ValueError(f"{name} has {t.numel()} elements, needs {n}")
+    return t.data_ptr() or None
+
+
+class BlockedMatrix:
+    """An analysed matrix (cbspmv handle). `A` is any object with m, n, row_ptr, col, val
+    (e.g. inputs.CSR). device=-1 gives a host-only handle (analysis and export only)."""
+
+    def __init__(self, A, *, th0=0.15, th1=32, th2=128, col_agg=-1, value_dtype="f64",
+                 unit_work=0, load_balance=True, device=0, stream=None):
+        self._h = ctypes.c_void_p(None)
+        self.m, self.n = int(A.m), int(A.n)
+        rp = np.ascontiguousarray(A.row_ptr, dtype=np.int64)
+        col = np.ascontiguousarray(A.col, dtype=np.int32)
+        val = np.ascontiguousarray(A.val, dtype=np.float64)
+        self.nnz = int(rp[-1]) if rp.size else 0
+        csr = Csr(self.m, self.n, self.nnz, rp.ctypes.data, col.ctypes.data, val.ctypes.data, 0)
+        o = default_opts()
+        o.th0, o.th1, o.th2, o.col_agg = th0, th1, th2, col_agg
+        o.value_dtype = DTYPES[value_dtype]
+        o.unit_work = unit_work
+        o.load_balance = 1 if load_balance else 0
+        o.device = device
+        self.device = device
+        s = _stream_ptr(stream) if device >= 0 else None
+        _check(lib().cbspmv_analyze(ctypes.byref(csr), ctypes.byref(o), s, ctypes.byref(self._h)))
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    def run(self, x, y, alpha: float = 1.0, beta: float = 0.0, stream=None):
+        """y <- alpha*A*x + beta*y on the device (asynchronous on the stream)."""
+        _check(lib().cbspmv_run(self._h, _dev_ptr(x, self.n, "x"), _dev_ptr(y, self.m, "y"),
+                                float(alpha), float(beta), _stream_ptr(stream)))
+        return y
+
+    def run_host(self, x: np.ndarray, y: np.ndarray | None = None, alpha: float = 1.0,
+                 beta: float = 0.0, stream=None) -> np.ndarray:
+        """The product from host arrays (copies in and out, synchronous)."""
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        if y is None:
+            y = np.zeros(self.m, dtype=np.float64)
+        if y.dtype != np.float64 or not y.flags.c_contiguous:
+            raise TypeError("y must be a contiguous float64 array")
+        _check(lib().cbspmv_run_host(self._h, x.ctypes.data, y.ctypes.data, float(alpha), float(beta),
+                                     _stream_ptr(stream)))
+        return y
+
+    def check_device(self, stream=None):
+        _check(lib().cbspmv_check_device(self._h, _stream_ptr(stream)))
+
+    def export_csr(self):
+        rp = np.empty(self.m + 1, dtype=np.int64)
+        col = np.empty(max(self.nnz, 1), dtype=np.int32)
+        val = np.empty(max(self.nnz, 1), dtype=np.float64)
+        _check(lib().cbspmv_export_csr(self._h, rp.ctypes.data, col.ctypes.data, val.ctypes.data))
+        return rp, col[:self.nnz], val[:self.nnz]
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib().cbspmv_get_stats(self._h, ctypes.byref(s)))
+        out = {}
+        for name, _ in Stats._fields_:
+            v = getattr(s, name)
+            out[name] = list(v) if hasattr(v, "__len__") else v
+        return out
+
+    def export_blocked(self) -> dict:
+        st = self.stats()
+        nt, nbr, rl = st["n_tiles"], st["n_block_rows"], st["restore_cols_len"]
+        br = np.empty(nt, np.int32); bc = np.empty(nt, np.int32)
+        nz = np.empty(nt, np.int32); ty = np.empty(nt, np.uint8)
+        co = np.zeros(nbr + 1 if st["aggregated"] else 0, np.int64)
+        rc = np.zeros(rl, np.int32)
+        _check(lib().cbspmv_export_blocked(self._h, br.ctypes.data, bc.ctypes.data, nz.ctypes.data,
+                                           ty.ctypes.data, co.ctypes.data if co.size else None,
+                                           rc.ctypes.data if rc.size else None))
+        return {"blk_row": br, "blk_col": bc, "nnz": nz, "type": ty, "cols_offset": co,
+                "restore_cols": rc, "aggregated": bool(st["aggregated"])}
+
+    def close(self):
+        if self._h and self._h.value:
+            _check(lib().cbspmv_destroy(self._h))
+            self._h = ctypes.c_void_p(None)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def version() -> str:
+    return lib().cbspmv_version().decode()

@@ -1,0 +1,547 @@
+// Host analysis of a CSR matrix into the blocked layout (Sec. 3 of the paper):
+//   1. validation of the canonical CSR input;
+//   2. 16x16 tiling of each block row and the super-sparse share that decides column
+//      aggregation (Sec. 3.3.1, threshold th0);
+//   3. per block row: column aggregation (restore_cols / cols_offset), re-tiling, per-tile
+//      format selection (Sec. 3.3.2, th1 / th2) and packing of every tile into one
+//      16-byte aligned record behind its virtual pointer (Sec. 3.2);
+//   4. cutting the tile sequence into units of work for the kernel's warps and the
+//      load balance of units over the persistent thread blocks (Sec. 3.4): units sorted
+//      by cost, each handed to the least-loaded thread block taken from a min-heap.
+// Block rows are independent, so steps 2-3 run on all host cores.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <queue>
+#include <thread>
+
+#include "cb_plan.h"
+
+namespace cb {
+namespace {
+
+int host_threads() {
+  unsigned h = std::thread::hardware_concurrency();
+  if (h == 0) h = 1;
+  return (int)std::min(h, 64u);
+}
+
+// Runs f(lo, hi) over [0, n) in chunks on all host cores.
+void parallel_for(int64_t n, int64_t grain, const std::function<void(int64_t, int64_t)>& f) {
+  int T = host_threads();
+  if (n <= grain || T == 1) {
+    f(0, n);
+    return;
+  }
+  std::atomic<int64_t> next(0);
+  auto work = [&]() {
+    for (;;) {
+      int64_t lo = next.fetch_add(grain);
+      if (lo >= n) break;
+      f(lo, std::min(n, lo + grain));
+    }
+  };
+  std::vector<std::thread> th;
+  int nt = (int)std::min<int64_t>(T, (n + grain - 1) / grain);
+  for (int i = 1; i < nt; ++i) th.emplace_back(work);
+  work();
+  for (auto& t : th) t.join();
+}
+
+inline int select_format(int nnz, int th1, int th2) {
+  if (nnz < th1) return CB_FMT_COO;
+  if (nnz > th2) return CB_FMT_DENSE;
+  return CB_FMT_CSR;
+}
+
+inline uint32_t align16(uint32_t v) { return (v + 15u) & ~15u; }
+
+// Bytes of one packed tile record.
+inline uint32_t record_bytes(int fmt, int nnz, int vsize) {
+  switch (fmt) {
+    case CB_FMT_COO: return align16(align16((uint32_t)nnz) + (uint32_t)nnz * vsize);
+    case CB_FMT_CSR: return align16(align16(17u + (uint32_t)nnz) + (uint32_t)nnz * vsize);
+    default: return align16(32u + 256u * vsize);
+  }
+}
+
+struct BlockRowOut {
+  std::vector<uint8_t> bytes;      // packed records of this block row
+  std::vector<uint32_t> off;       // record offsets inside `bytes`
+  std::vector<int32_t> bcol;       // block column per tile
+  std::vector<uint16_t> nnz;
+  std::vector<uint8_t> fmt;
+  std::vector<int32_t> distinct;   // distinct columns in order (aggregated only)
+};
+
+// Entries of one block row as (key = col << 4 | local row, CSR position), sorted by key.
+void gather_block_row(const cbspmv_csr_t& A, int64_t b, std::vector<std::pair<uint64_t, int64_t>>& e) {
+  e.clear();
+  int64_t r0 = b * CB_BLK, r1 = std::min<int64_t>(A.m, r0 + CB_BLK);
+  for (int64_t r = r0; r < r1; ++r)
+    for (int64_t k = A.row_ptr[r]; k < A.row_ptr[r + 1]; ++k)
+      e.emplace_back(((uint64_t)(uint32_t)A.col_idx[k] << 4) | (uint64_t)(r - r0), k);
+  std::sort(e.begin(), e.end());
+}
+
+void write_value(uint8_t* dst, double v, int vsize) {
+  // Only the FP64 storage type is produced by this analyser version.
+  (void)vsize;
+  std::memcpy(dst, &v, 8);
+}
+
+void build_block_row(const cbspmv_csr_t& A, int64_t b, bool agg, int th1, int th2, int vsize,
+                     std::vector<std::pair<uint64_t, int64_t>>& e, BlockRowOut& out) {
+  gather_block_row(A, b, e);
+  out = BlockRowOut();
+  const size_t ne = e.size();
+  if (ne == 0) return;
+  // aggregated column of every entry (Sec. 3.3.1): rank of its column among the block
+  // row's distinct columns; plain: the column itself.
+  std::vector<uint32_t> acol(ne);
+  if (agg) {
+    int64_t prev = -1;
+    uint32_t rank = 0;
+    for (size_t i = 0; i < ne; ++i) {
+      int64_t c = (int64_t)(e[i].first >> 4);
+      if (c != prev) {
+        if (prev >= 0) ++rank;
+        out.distinct.push_back((int32_t)c);
+        prev = c;
+      }
+      acol[i] = rank;
+    }
+  } else {
+    for (size_t i = 0; i < ne; ++i) acol[i] = (uint32_t)(e[i].first >> 4);
+  }
+  std::vector<std::pair<uint32_t, int64_t>> tile;  // (row * 16 + col in tile, CSR position)
+  size_t a = 0;
+  while (a < ne) {
+    uint32_t bj = acol[a] >> 4;
+    size_t z = a;
+    tile.clear();
+    while (z < ne && (acol[z] >> 4) == bj) {
+      uint32_t lr = (uint32_t)(e[z].first & 15u), lc = acol[z] & 15u;
+      tile.emplace_back(lr * 16u + lc, e[z].second);
+      ++z;
+    }
+    std::sort(tile.begin(), tile.end());
+    int nnz = (int)tile.size();
+    int fmt = select_format(nnz, th1, th2);
+    uint32_t rb = record_bytes(fmt, nnz, vsize);
+    uint32_t base = (uint32_t)out.bytes.size();
+    out.bytes.resize(base + rb, 0);
+    uint8_t* rec = out.bytes.data() + base;
+    if (fmt == CB_FMT_DENSE) {
+      for (auto& t : tile) {
+        uint32_t pos = t.first;  // row * 16 + col
+        rec[pos >> 3] |= (uint8_t)(1u << (pos & 7));
+        write_value(rec + 32 + pos * vsize, A.val[t.second], vsize);
+      }
+    } else {
+      uint8_t* idx = rec;
+      if (fmt == CB_FMT_CSR) {
+        // 17 row-pointer bytes
+        int cnt[16] = {0};
+        for (auto& t : tile) cnt[t.first >> 4]++;
+        rec[0] = 0;
+        for (int r = 0; r < 16; ++r) rec[r + 1] = (uint8_t)(rec[r] + cnt[r]);
+        idx = rec + 17;
+      }
+      uint32_t voff = align16((uint32_t)(idx - rec) + (uint32_t)nnz);
+      for (int i = 0; i < nnz; ++i) {
+        uint32_t lr = tile[i].first >> 4, lc = tile[i].first & 15u;
+        idx[i] = (uint8_t)(lr | (lc << 4));          // row low nibble, col high nibble
+        write_value(rec + voff + (uint32_t)i * vsize, A.val[tile[i].second], vsize);
+      }
+    }
+    out.off.push_back(base);
+    out.bcol.push_back((int32_t)bj);
+    out.nnz.push_back((uint16_t)nnz);
+    out.fmt.push_back((uint8_t)fmt);
+    a = z;
+  }
+}
+
+cbspmv_status_t validate(const cbspmv_csr_t& A, std::string* msg) {
+  if (A.m < 0 || A.n < 0 || A.nnz < 0 || A.m >= (1LL << 31) || A.n >= (1LL << 31) ||
+      A.nnz >= (1LL << 31)) {
+    *msg = "matrix dimensions out of range";
+    return CBSPMV_ERR_INVALID;
+  }
+  if (!A.row_ptr || (A.nnz > 0 && (!A.col_idx || !A.val))) {
+    *msg = "NULL CSR array";
+    return CBSPMV_ERR_INVALID;
+  }
+  if (A.row_ptr[0] != 0 || A.row_ptr[A.m] != A.nnz) {
+    *msg = "row_ptr must start at 0 and end at nnz";
+    return CBSPMV_ERR_NOT_CANONICAL;
+  }
+  std::atomic<int> bad(0);
+  parallel_for(A.m, 1 << 14, [&](int64_t lo, int64_t hi) {
+    for (int64_t r = lo; r < hi && !bad.load(std::memory_order_relaxed); ++r) {
+      int64_t a = A.row_ptr[r], z = A.row_ptr[r + 1];
+      if (z < a || a < 0 || z > A.nnz) { bad = 1; return; }
+      int64_t prev = -1;
+      for (int64_t k = a; k < z; ++k) {
+        int64_t c = A.col_idx[k];
+        if (c <= prev || c >= A.n) { bad = 2; return; }
+        prev = c;
+      }
+    }
+  });
+  if (bad.load() == 1) { *msg = "row_ptr is not non-decreasing"; return CBSPMV_ERR_NOT_CANONICAL; }
+  if (bad.load() == 2) {
+    *msg = "column indices must be strictly increasing within a row and lie in [0, n)";
+    return CBSPMV_ERR_NOT_CANONICAL;
+  }
+  return CBSPMV_OK;
+}
+
+}  // namespace
+
+cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, int n_workers,
+                             Plan* P, std::string* msg) {
+  auto t_start = std::chrono::steady_clock::now();
+  if (opts.th1 < 0 || opts.th2 < opts.th1 || opts.th2 > 256 || !(opts.th0 >= 0.0)) {
+    *msg = "thresholds must satisfy th0 >= 0 and 0 <= th1 <= th2 <= 256";
+    return CBSPMV_ERR_INVALID;
+  }
+  if (opts.value_dtype != CBSPMV_F64) {
+    *msg = "this analyser stores FP64 values only";
+    return CBSPMV_ERR_UNSUPPORTED;
+  }
+  if (opts.col_agg < -1 || opts.col_agg > 1) { *msg = "col_agg must be -1, 0 or 1"; return CBSPMV_ERR_INVALID; }
+  if (n_workers <= 0) { *msg = "no workers"; return CBSPMV_ERR_INVALID; }
+  cbspmv_status_t st = validate(A, msg);
+  if (st != CBSPMV_OK) return st;
+
+  Plan& p = *P;
+  p = Plan();
+  p.m = A.m; p.n = A.n; p.nnz = A.nnz;
+  p.nbr = (A.m + CB_BLK - 1) / CB_BLK;
+  p.value_dtype = opts.value_dtype;
+  p.vsize = 8;
+  p.th0 = opts.th0; p.th1 = opts.th1; p.th2 = opts.th2;
+  const int64_t nbr = p.nbr;
+
+  // --- step 2: plain 16x16 tiles and the super-sparse share (Sec. 3.3.1)
+  std::atomic<int64_t> plain_tiles(0), plain_sparse(0);
+  parallel_for(nbr, 256, [&](int64_t lo, int64_t hi) {
+    std::vector<uint32_t> bj;
+    int64_t pt = 0, ps = 0;
+    for (int64_t b = lo; b < hi; ++b) {
+      bj.clear();
+      int64_t r0 = b * CB_BLK, r1 = std::min<int64_t>(A.m, r0 + CB_BLK);
+      for (int64_t r = r0; r < r1; ++r)
+        for (int64_t k = A.row_ptr[r]; k < A.row_ptr[r + 1]; ++k) bj.push_back((uint32_t)A.col_idx[k] >> 4);
+      std::sort(bj.begin(), bj.end());
+      size_t i = 0;
+      while (i < bj.size()) {
+        size_t j = i;
+        while (j < bj.size() && bj[j] == bj[i]) ++j;
+        ++pt;
+        if ((int64_t)(j - i) < opts.th1) ++ps;
+        i = j;
+      }
+    }
+    plain_tiles += pt;
+    plain_sparse += ps;
+  });
+  double frac = plain_tiles.load() ? (double)plain_sparse.load() / (double)plain_tiles.load() : 0.0;
+  p.aggregated = opts.col_agg < 0 ? (frac > opts.th0) : (opts.col_agg == 1);
+
+  // --- step 3: per block row aggregation, tiling, format selection and packing
+  std::vector<BlockRowOut> rows(nbr);
+  parallel_for(nbr, 64, [&](int64_t lo, int64_t hi) {
+    std::vector<std::pair<uint64_t, int64_t>> e;
+    for (int64_t b = lo; b < hi; ++b)
+      build_block_row(A, b, p.aggregated, opts.th1, opts.th2, p.vsize, e, rows[b]);
+  });
+  // prefix sums over block rows: tiles, stream bytes, distinct columns
+  std::vector<int64_t> tile_off(nbr + 1, 0), byte_off(nbr + 1, 0);
+  p.cols_offset.assign(p.aggregated ? nbr + 1 : 0, 0);
+  for (int64_t b = 0; b < nbr; ++b) {
+    tile_off[b + 1] = tile_off[b] + (int64_t)rows[b].off.size();
+    byte_off[b + 1] = byte_off[b] + (int64_t)rows[b].bytes.size();
+    if (p.aggregated) p.cols_offset[b + 1] = p.cols_offset[b] + (int64_t)rows[b].distinct.size();
+  }
+  const int64_t ntiles = tile_off[nbr];
+  if (byte_off[nbr] / 16 >= (1LL << 32)) { *msg = "packed stream exceeds 64 GiB"; return CBSPMV_ERR_UNSUPPORTED; }
+  p.restore_cols_len = p.aggregated ? p.cols_offset[nbr] : 0;
+  try {
+    p.tiles.resize(ntiles);
+    p.tile_bcol.resize(ntiles);
+    p.stream.resize(byte_off[nbr]);
+    p.restore_cols.assign(p.restore_cols_len + CB_RC_PAD, 0);
+  } catch (...) {
+    *msg = "host allocation failed";
+    return CBSPMV_ERR_OOM;
+  }
+  parallel_for(nbr, 256, [&](int64_t lo, int64_t hi) {
+    for (int64_t b = lo; b < hi; ++b) {
+      BlockRowOut& o = rows[b];
+      if (!o.bytes.empty()) std::memcpy(p.stream.data() + byte_off[b], o.bytes.data(), o.bytes.size());
+      for (size_t i = 0; i < o.off.size(); ++i) {
+        CbTile t{};
+        t.vp16 = (uint32_t)((byte_off[b] + o.off[i]) / 16);
+        t.xbase = p.aggregated ? (uint32_t)(p.cols_offset[b] + 16 * (int64_t)o.bcol[i]) : (uint32_t)(16 * o.bcol[i]);
+        t.brow = (uint32_t)b;
+        t.nnz = o.nnz[i];
+        t.fmt = o.fmt[i];
+        p.tiles[tile_off[b] + i] = t;
+        p.tile_bcol[tile_off[b] + i] = o.bcol[i];
+      }
+      if (p.aggregated && !o.distinct.empty())
+        std::memcpy(p.restore_cols.data() + p.cols_offset[b], o.distinct.data(), o.distinct.size() * 4);
+      BlockRowOut().bytes.swap(o.bytes);
+    }
+  });
+
+  // --- step 4a: units of work
+  const uint32_t U = opts.unit_work > 0 ? (uint32_t)opts.unit_work : CB_UNIT_WORK_DEFAULT;
+  auto tile_work = [&](int64_t t) -> uint32_t { return p.tiles[t].fmt == CB_FMT_DENSE ? 256u : p.tiles[t].nnz; };
+  auto tile_bytes = [&](int64_t t) -> uint32_t {
+    return record_bytes(p.tiles[t].fmt, p.tiles[t].nnz, p.vsize);
+  };
+  auto finish_unit = [&](CbUnit& u) {
+    if (p.aggregated && u.ntiles > 0) {
+      uint32_t first = p.tiles[u.tile_lo].xbase;
+      uint32_t last = p.tiles[u.tile_lo + u.ntiles - 1].xbase + 16;
+      u.rc_lo = first & ~3u;
+      u.rc_n = (last - u.rc_lo + 3u) & ~3u;
+    } else {
+      u.rc_lo = 0;
+      u.rc_n = 0;
+    }
+    if (u.ntiles > 0) u.byte_lo16 = p.tiles[u.tile_lo].vp16;
+    p.units.push_back(u);
+  };
+  CbUnit open{};
+  bool have_open = false;
+  int32_t split_id = 0;
+  uint32_t slot = 0;
+  for (int64_t b = 0; b < nbr; ++b) {
+    int64_t t0 = tile_off[b], t1 = tile_off[b + 1];
+    uint64_t W = 0, B = 0;
+    for (int64_t t = t0; t < t1; ++t) { W += tile_work(t); B += tile_bytes(t); }
+    int64_t T = t1 - t0;
+    bool big = W > U || B > CB_B_MAX || T > CB_T_MAX;
+    if (!big) {
+      if (have_open && open.work + W <= U && open.nbytes + B <= CB_B_MAX &&
+          open.ntiles + T <= CB_T_MAX && open.nbr < CB_NBR_MAX) {
+        open.ntiles = (uint16_t)(open.ntiles + T);
+        open.nbr = (uint16_t)(open.nbr + 1);
+        open.nbytes += (uint32_t)B;
+        open.work += (uint32_t)W;
+        if (open.ntiles == T) open.tile_lo = (uint32_t)t0;
+        continue;
+      }
+      if (have_open) finish_unit(open);
+      open = CbUnit{};
+      open.tile_lo = (uint32_t)t0;
+      open.ntiles = (uint16_t)T;
+      open.nbr = 1;
+      open.brow_lo = (uint32_t)b;
+      open.nbytes = (uint32_t)B;
+      open.work = (uint32_t)W;
+      open.split = -1;
+      open.nparts = 1;
+      have_open = true;
+      continue;
+    }
+    if (have_open) { finish_unit(open); have_open = false; }
+    // cut the block row into parts of about equal work within the unit limits
+    uint64_t nparts_est = std::max<uint64_t>({(W + U - 1) / U, (B + CB_B_MAX - 1) / CB_B_MAX,
+                                              (uint64_t)((T + CB_T_MAX - 1) / CB_T_MAX), 2});
+    uint64_t target = (W + nparts_est - 1) / nparts_est;
+    size_t first_unit = p.units.size();
+    CbUnit u{};
+    u.tile_lo = (uint32_t)t0; u.nbr = 1; u.brow_lo = (uint32_t)b; u.split = split_id;
+    for (int64_t t = t0; t < t1; ++t) {
+      uint32_t wt = tile_work(t), bt = tile_bytes(t);
+      if (u.ntiles > 0 && (u.work + wt > U || u.nbytes + bt > CB_B_MAX || u.ntiles + 1 > CB_T_MAX ||
+                           u.work >= target)) {
+        finish_unit(u);
+        CbUnit v{};
+        v.tile_lo = (uint32_t)t; v.nbr = 1; v.brow_lo = (uint32_t)b; v.split = split_id;
+        u = v;
+      }
+      u.ntiles++;
+      u.work += wt;
+      u.nbytes += bt;
+    }
+    finish_unit(u);
+    uint16_t np = (uint16_t)(p.units.size() - first_unit);
+    for (size_t i = first_unit; i < p.units.size(); ++i) {
+      p.units[i].part = (uint16_t)(i - first_unit);
+      p.units[i].nparts = np;
+      p.units[i].slot = slot++;
+    }
+    ++split_id;
+  }
+  if (have_open) finish_unit(open);
+  p.n_split_rows = split_id;
+  p.n_slots = (int)slot;
+
+  // --- step 4b: load balance of units over the persistent thread blocks (Sec. 3.4):
+  // longest-processing-time order, min-heap of (load, worker id).
+  const int64_t nu = (int64_t)p.units.size();
+  p.n_workers = n_workers;
+  std::vector<double> cost(nu);
+  for (int64_t i = 0; i < nu; ++i) {
+    const CbUnit& u = p.units[i];
+    cost[i] = (double)u.work + 8.0 * u.ntiles + 2.0 * CB_BLK * u.nbr + 64.0;
+  }
+  std::vector<std::vector<uint32_t>> lists(n_workers);
+  std::vector<double> load(n_workers, 0.0);
+  if (opts.load_balance) {
+    std::vector<uint32_t> order(nu);
+    for (int64_t i = 0; i < nu; ++i) order[i] = (uint32_t)i;
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return cost[a] > cost[b]; });
+    typedef std::pair<double, int> Item;
+    std::priority_queue<Item, std::vector<Item>, std::greater<Item>> pq;
+    for (int w = 0; w < n_workers; ++w) pq.push(Item(0.0, w));
+    for (uint32_t u : order) {
+      Item top = pq.top();
+      pq.pop();
+      lists[top.second].push_back(u);
+      top.first += cost[u];
+      load[top.second] = top.first;
+      pq.push(top);
+    }
+    for (auto& l : lists) std::sort(l.begin(), l.end());   // matrix order inside a worker
+  } else {
+    for (int64_t i = 0; i < nu; ++i) {
+      lists[i % n_workers].push_back((uint32_t)i);
+      load[i % n_workers] += cost[i];
+    }
+  }
+  p.worker_off.assign(n_workers + 1, 0);
+  p.worker_units.reserve(nu);
+  for (int w = 0; w < n_workers; ++w) {
+    p.worker_off[w + 1] = p.worker_off[w] + (uint32_t)lists[w].size();
+    p.worker_units.insert(p.worker_units.end(), lists[w].begin(), lists[w].end());
+  }
+
+  // --- statistics
+  cbspmv_stats_t& s = p.stats;
+  s = cbspmv_stats_t{};
+  s.m = A.m; s.n = A.n; s.nnz = A.nnz;
+  s.n_block_rows = nbr;
+  s.n_tiles = ntiles;
+  s.n_tiles_plain = plain_tiles.load();
+  s.super_sparse_fraction = frac;
+  s.aggregated = p.aggregated ? 1 : 0;
+  s.value_dtype = p.value_dtype;
+  int64_t mults = 0;
+  for (int64_t t = 0; t < ntiles; ++t) {
+    const CbTile& x = p.tiles[t];
+    s.n_fmt[x.fmt]++;
+    s.nnz_fmt[x.fmt] += x.nnz;
+    s.hist_coarse[std::min(7, (x.nnz - 1) / 32)]++;
+    if (x.nnz <= 32) s.hist_fine[(x.nnz - 1) / 8]++;
+    mults += x.fmt == CB_FMT_DENSE ? 256 : x.nnz;
+  }
+  s.restore_cols_len = p.restore_cols_len;
+  s.stream_bytes = (int64_t)p.stream.size();
+  s.metadata_bytes = ntiles * (int64_t)sizeof(CbTile);
+  s.model_bytes_cb = ntiles * 21 + A.nnz * 9;
+  s.model_bytes_csr = (A.m + 1) * 4 + A.nnz * 12;
+  s.model_bytes_bsr16 = 2048 * ntiles + (nbr + 1) * 4 + 4 * ntiles;
+  s.algo_bytes_per_run = A.nnz * (int64_t)(p.vsize + 1) + ntiles * 21 + A.n * 8 + A.m * 8 +
+                         (p.aggregated ? 4 * p.restore_cols_len : 0);
+  s.flops_per_run = 2 * A.nnz;
+  s.mults_per_run = mults;
+  s.n_units = nu;
+  int64_t nsplit_units = 0;
+  for (auto& u : p.units) nsplit_units += u.split >= 0;
+  s.n_split_units = nsplit_units;
+  s.n_split_rows = p.n_split_rows;
+  s.n_workers = n_workers;
+  double lmax = 0, lsum = 0, lsq = 0;
+  for (double l : load) { lmax = std::max(lmax, l); lsum += l; lsq += l * l; }
+  s.worker_load_max = lmax;
+  s.worker_load_mean = lsum / n_workers;
+  s.worker_load_std = std::sqrt(std::max(0.0, lsq / n_workers - s.worker_load_mean * s.worker_load_mean));
+  {
+    int64_t ng = (ntiles + 7) / 8;
+    double gs = 0, gq = 0;
+    for (int64_t g = 0; g < ng; ++g) {
+      double v = 0;
+      for (int64_t t = 8 * g; t < std::min(ntiles, 8 * g + 8); ++t) v += p.tiles[t].nnz;
+      gs += v; gq += v * v;
+    }
+    double mean = ng ? gs / ng : 0;
+    s.tb8_load_std = ng ? std::sqrt(std::max(0.0, gq / ng - mean * mean)) : 0.0;
+  }
+  s.analyze_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  return CBSPMV_OK;
+}
+
+cbspmv_status_t decode_to_csr(int64_t m, int64_t n, int vsize, bool aggregated,
+                              const std::vector<CbTile>& tiles, const uint8_t* stream,
+                              size_t stream_size, const int32_t* restore_cols, size_t restore_len,
+                              int64_t* row_ptr, int32_t* col, double* val, int64_t nnz_expected,
+                              std::string* msg) {
+  if (vsize != 8) { *msg = "export supports FP64 storage only"; return CBSPMV_ERR_UNSUPPORTED; }
+  std::vector<int64_t> cnt(m + 1, 0);
+  auto for_entries = [&](const CbTile& t, const std::function<void(int64_t, int64_t, const uint8_t*)>& f) -> bool {
+    size_t off = (size_t)t.vp16 * 16;
+    uint32_t rb = record_bytes(t.fmt, t.nnz, vsize);
+    if (off + rb > stream_size) return false;
+    const uint8_t* rec = stream + off;
+    auto colof = [&](uint32_t lc, int64_t* c) -> bool {
+      if (aggregated) {
+        size_t i = (size_t)t.xbase + lc;
+        if (i >= restore_len) return false;
+        *c = restore_cols[i];
+      } else {
+        *c = (int64_t)t.xbase + lc;
+      }
+      return *c >= 0 && *c < n;
+    };
+    if (t.fmt == CB_FMT_DENSE) {
+      for (uint32_t pos = 0; pos < 256; ++pos) {
+        if (!(rec[pos >> 3] & (1u << (pos & 7)))) continue;
+        int64_t r = (int64_t)t.brow * 16 + (pos >> 4), c;
+        if (r >= m || !colof(pos & 15u, &c)) return false;
+        f(r, c, rec + 32 + pos * vsize);
+      }
+    } else {
+      const uint8_t* idx = rec + (t.fmt == CB_FMT_CSR ? 17 : 0);
+      uint32_t voff = align16((uint32_t)(idx - rec) + t.nnz);
+      for (uint32_t i = 0; i < t.nnz; ++i) {
+        int64_t r = (int64_t)t.brow * 16 + (idx[i] & 15u), c;
+        if (r >= m || !colof(idx[i] >> 4, &c)) return false;
+        f(r, c, rec + voff + i * vsize);
+      }
+    }
+    return true;
+  };
+  for (const CbTile& t : tiles)
+    if (!for_entries(t, [&](int64_t r, int64_t, const uint8_t*) { cnt[r + 1]++; })) {
+      *msg = "corrupt blocked layout";
+      return CBSPMV_ERR_INVALID;
+    }
+  for (int64_t r = 0; r < m; ++r) cnt[r + 1] += cnt[r];
+  if (cnt[m] != nnz_expected) { *msg = "entry count mismatch in blocked layout"; return CBSPMV_ERR_INVALID; }
+  std::vector<int64_t> cur(cnt.begin(), cnt.end() - 1);
+  for (const CbTile& t : tiles)
+    for_entries(t, [&](int64_t r, int64_t c, const uint8_t* v) {
+      int64_t k = cur[r]++;
+      col[k] = (int32_t)c;
+      std::memcpy(&val[k], v, 8);
+    });
+  std::memcpy(row_ptr, cnt.data(), (m + 1) * sizeof(int64_t));
+  // tiles of a block row are in increasing column order, so rows come out sorted; check
+  for (int64_t r = 0; r < m; ++r)
+    for (int64_t k = row_ptr[r] + 1; k < row_ptr[r + 1]; ++k)
+      if (col[k] <= col[k - 1]) { *msg = "blocked layout decodes to unsorted rows"; return CBSPMV_ERR_INVALID; }
+  return CBSPMV_OK;
+}
+
+}  // namespace cb

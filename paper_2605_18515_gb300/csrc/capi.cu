@@ -1,0 +1,341 @@
+// The C ABI of include/cbspmv.h: argument checking, handle ownership, device uploads and
+// kernel launches. All errors become status codes plus a thread-local message.
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/cbspmv.h"
+#include "cb_kernels.h"
+#include "cb_plan.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+cbspmv_status_t fail(cbspmv_status_t s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+cbspmv_status_t ok() {
+  g_err.clear();
+  return CBSPMV_OK;
+}
+
+// Makes `dev` current for the lifetime of the object and restores the caller's device.
+struct DeviceGuard {
+  int prev = -1;
+  bool changed = false;
+  cudaError_t err = cudaSuccess;
+  explicit DeviceGuard(int dev) {
+    err = cudaGetDevice(&prev);
+    if (err == cudaSuccess && prev != dev) {
+      err = cudaSetDevice(dev);
+      changed = err == cudaSuccess;
+    }
+  }
+  ~DeviceGuard() {
+    if (changed) cudaSetDevice(prev);
+  }
+};
+
+#define CB_CUDA(call)                                                                      \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail(e_ == cudaErrorMemoryAllocation ? CBSPMV_ERR_OOM : CBSPMV_ERR_CUDA,      \
+                  "%s: %s", #call, cudaGetErrorString(e_));                                \
+  } while (0)
+
+}  // namespace
+
+struct cbspmv_handle_s {
+  uint32_t magic = 0xCB5B0001u;
+  cb::Plan plan;
+  int device = -1;
+  int grid = 0;
+  size_t stream_bytes = 0;
+  uint8_t* d_stream = nullptr;
+  CbTile* d_tiles = nullptr;
+  int32_t* d_rcols = nullptr;
+  CbUnit* d_units = nullptr;
+  uint32_t* d_wunits = nullptr;
+  uint32_t* d_woff = nullptr;
+  double* d_partial = nullptr;
+  uint32_t* d_split_count = nullptr;
+  uint32_t* d_err = nullptr;
+  double* d_xstage = nullptr;
+  double* d_ystage = nullptr;
+
+  void free_device() {
+    if (device < 0) return;
+    DeviceGuard g(device);
+    cudaDeviceSynchronize();
+    void* ptrs[] = {d_stream, d_tiles, d_rcols, d_units, d_wunits, d_woff, d_partial, d_split_count,
+                    d_err, d_xstage, d_ystage};
+    for (void* p : ptrs)
+      if (p) cudaFree(p);
+    d_stream = nullptr;
+    d_tiles = nullptr;
+    d_rcols = nullptr;
+    d_units = nullptr;
+    d_wunits = nullptr;
+    d_woff = nullptr;
+    d_partial = nullptr;
+    d_split_count = nullptr;
+    d_err = nullptr;
+    d_xstage = nullptr;
+    d_ystage = nullptr;
+  }
+};
+
+static bool valid_handle(cbspmv_handle_t h) { return h && h->magic == 0xCB5B0001u; }
+
+template <class T>
+static cudaError_t upload(T** dst, const T* src, size_t count, cudaStream_t s) {
+  size_t bytes = count * sizeof(T);
+  cudaError_t e = cudaMalloc((void**)dst, bytes ? bytes : 16);
+  if (e != cudaSuccess) return e;
+  if (bytes) e = cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, s);
+  return e;
+}
+
+extern "C" {
+
+cbspmv_status_t cbspmv_default_opts(cbspmv_opts_t* o) {
+  if (!o) return fail(CBSPMV_ERR_INVALID, "opts is NULL");
+  std::memset(o, 0, sizeof(*o));
+  o->th0 = 0.15;
+  o->th1 = 32;
+  o->th2 = 128;
+  o->col_agg = -1;
+  o->value_dtype = CBSPMV_F64;
+  o->unit_work = 0;
+  o->load_balance = 1;
+  o->device = 0;
+  return ok();
+}
+
+cbspmv_status_t cbspmv_analyze(const cbspmv_csr_t* A, const cbspmv_opts_t* opts_in, void* stream,
+                               cbspmv_handle_t* out) {
+  if (!A || !out) return fail(CBSPMV_ERR_INVALID, "NULL argument");
+  *out = nullptr;
+  if (A->on_device) return fail(CBSPMV_ERR_UNSUPPORTED, "device-resident CSR input is not supported");
+  cbspmv_opts_t opts;
+  if (opts_in) opts = *opts_in; else cbspmv_default_opts(&opts);
+  if (opts.unit_work < 0 || opts.unit_work > 16384)
+    return fail(CBSPMV_ERR_INVALID, "unit_work must be in [0, 16384]");
+  int grid = 1;
+  if (opts.device >= 0) {
+    int ndev = 0;
+    CB_CUDA(cudaGetDeviceCount(&ndev));
+    if (opts.device >= ndev) return fail(CBSPMV_ERR_INVALID, "device %d not present", opts.device);
+    DeviceGuard g(opts.device);
+    CB_CUDA(g.err);
+    int sms = 0, smem_optin = 0;
+    CB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, opts.device));
+    CB_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, opts.device));
+    if ((size_t)smem_optin < cb::spmv_f64_smem_bytes())
+      return fail(CBSPMV_ERR_UNSUPPORTED, "device has %d B of shared memory per block, kernel needs %zu",
+                  smem_optin, cb::spmv_f64_smem_bytes());
+    grid = sms;
+  } else if (opts.device != -1) {
+    return fail(CBSPMV_ERR_INVALID, "device must be >= 0 or -1 (host only)");
+  }
+  cbspmv_handle_t h = new (std::nothrow) cbspmv_handle_s();
+  if (!h) return fail(CBSPMV_ERR_OOM, "host allocation failed");
+  std::string msg;
+  cbspmv_status_t st;
+  try {
+    st = cb::analyze_host(*A, opts, grid, &h->plan, &msg);
+  } catch (const std::bad_alloc&) {
+    st = CBSPMV_ERR_OOM;
+    msg = "host allocation failed during analysis";
+  }
+  if (st != CBSPMV_OK) {
+    delete h;
+    return fail(st, "%s", msg.c_str());
+  }
+  h->device = opts.device;
+  h->grid = grid;
+  if (opts.device < 0) {
+    *out = h;
+    return ok();
+  }
+  DeviceGuard g(opts.device);
+  cudaStream_t s = (cudaStream_t)stream;
+  cb::Plan& p = h->plan;
+  h->stream_bytes = p.stream.size();
+  cudaError_t e = cudaSuccess;
+  auto step = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+  step(upload(&h->d_stream, p.stream.data(), p.stream.size(), s));
+  step(upload(&h->d_tiles, p.tiles.data(), p.tiles.size(), s));
+  step(upload(&h->d_rcols, p.restore_cols.data(), p.restore_cols.size(), s));
+  step(upload(&h->d_units, p.units.data(), p.units.size(), s));
+  step(upload(&h->d_wunits, p.worker_units.data(), p.worker_units.size(), s));
+  step(upload(&h->d_woff, p.worker_off.data(), p.worker_off.size(), s));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_partial, (size_t)(p.n_slots ? p.n_slots : 1) * 16 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_split_count, (size_t)(p.n_split_rows ? p.n_split_rows : 1) * 4);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_split_count, 0, (size_t)(p.n_split_rows ? p.n_split_rows : 1) * 4, s);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_err, 4);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, 4, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    h->free_device();
+    delete h;
+    return fail(e == cudaErrorMemoryAllocation ? CBSPMV_ERR_OOM : CBSPMV_ERR_CUDA, "upload failed: %s",
+                cudaGetErrorString(e));
+  }
+  // the packed stream now lives on the device; export reads it back from there
+  std::vector<uint8_t>().swap(p.stream);
+  *out = h;
+  return ok();
+}
+
+static cbspmv_status_t run_device(cbspmv_handle_t h, const double* x, double* y, double alpha, double beta,
+                                  cudaStream_t s) {
+  const cb::Plan& p = h->plan;
+  if (p.m == 0) return ok();
+  cb::RunArgs a{};
+  a.stream = h->d_stream;
+  a.tiles = h->d_tiles;
+  a.rcols = h->d_rcols;
+  a.units = h->d_units;
+  a.worker_units = h->d_wunits;
+  a.worker_off = h->d_woff;
+  a.x = x;
+  a.y = y;
+  a.partial = h->d_partial;
+  a.split_count = h->d_split_count;
+  a.err = h->d_err;
+  a.m = p.m;
+  a.n = p.n;
+  a.alpha = alpha;
+  a.beta = beta;
+  a.aggregated = p.aggregated ? 1 : 0;
+  a.alpha_one = alpha == 1.0;
+  a.beta_nonzero = beta != 0.0;
+  CB_CUDA(cb::launch_spmv_f64(a, h->grid, s));
+  return ok();
+}
+
+cbspmv_status_t cbspmv_run(cbspmv_handle_t h, const void* x, void* y, double alpha, double beta, void* stream) {
+  if (!valid_handle(h)) return fail(CBSPMV_ERR_INVALID, "invalid handle");
+  if (h->device < 0) return fail(CBSPMV_ERR_INVALID, "host-only handle cannot run");
+  if ((!x && h->plan.n > 0) || (!y && h->plan.m > 0)) return fail(CBSPMV_ERR_INVALID, "NULL x or y");
+  if (((uintptr_t)x & 7) || ((uintptr_t)y & 7)) return fail(CBSPMV_ERR_INVALID, "x and y must be 8-byte aligned");
+  const char* xb = (const char*)x;
+  const char* yb = (const char*)y;
+  if (x && y && xb < yb + 8 * h->plan.m && yb < xb + 8 * h->plan.n)
+    return fail(CBSPMV_ERR_INVALID, "x and y overlap");
+  DeviceGuard g(h->device);
+  CB_CUDA(g.err);
+  return run_device(h, (const double*)x, (double*)y, alpha, beta, (cudaStream_t)stream);
+}
+
+cbspmv_status_t cbspmv_run_host(cbspmv_handle_t h, const double* x_host, double* y_host, double alpha, double beta,
+                                void* stream) {
+  if (!valid_handle(h)) return fail(CBSPMV_ERR_INVALID, "invalid handle");
+  if (h->device < 0) return fail(CBSPMV_ERR_INVALID, "host-only handle cannot run");
+  const cb::Plan& p = h->plan;
+  if ((!x_host && p.n > 0) || (!y_host && p.m > 0)) return fail(CBSPMV_ERR_INVALID, "NULL x or y");
+  DeviceGuard g(h->device);
+  CB_CUDA(g.err);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!h->d_xstage) CB_CUDA(cudaMalloc((void**)&h->d_xstage, (size_t)(p.n ? p.n : 1) * 8));
+  if (!h->d_ystage) CB_CUDA(cudaMalloc((void**)&h->d_ystage, (size_t)(p.m ? p.m : 1) * 8));
+  if (p.n) CB_CUDA(cudaMemcpyAsync(h->d_xstage, x_host, (size_t)p.n * 8, cudaMemcpyHostToDevice, s));
+  if (beta != 0.0 && p.m) CB_CUDA(cudaMemcpyAsync(h->d_ystage, y_host, (size_t)p.m * 8, cudaMemcpyHostToDevice, s));
+  cbspmv_status_t st = run_device(h, h->d_xstage, h->d_ystage, alpha, beta, s);
+  if (st != CBSPMV_OK) return st;
+  if (p.m) CB_CUDA(cudaMemcpyAsync(y_host, h->d_ystage, (size_t)p.m * 8, cudaMemcpyDeviceToHost, s));
+  CB_CUDA(cudaStreamSynchronize(s));
+  return ok();
+}
+
+cbspmv_status_t cbspmv_check_device(cbspmv_handle_t h, void* stream) {
+  if (!valid_handle(h)) return fail(CBSPMV_ERR_INVALID, "invalid handle");
+  if (h->device < 0) return ok();
+  DeviceGuard g(h->device);
+  CB_CUDA(g.err);
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t err = 0;
+  CB_CUDA(cudaStreamSynchronize(s));
+  CB_CUDA(cudaMemcpy(&err, h->d_err, 4, cudaMemcpyDeviceToHost));
+  if (err) {
+    CB_CUDA(cudaMemset(h->d_err, 0, 4));
+    return fail(CBSPMV_ERR_TIMEOUT, "a bounded device wait gave up (code 0x%x)", err);
+  }
+  return ok();
+}
+
+cbspmv_status_t cbspmv_export_csr(cbspmv_handle_t h, int64_t* row_ptr, int32_t* col_idx, double* val) {
+  if (!valid_handle(h)) return fail(CBSPMV_ERR_INVALID, "invalid handle");
+  const cb::Plan& p = h->plan;
+  if (!row_ptr || (p.nnz && (!col_idx || !val))) return fail(CBSPMV_ERR_INVALID, "NULL output array");
+  std::string msg;
+  cbspmv_status_t st;
+  if (h->device < 0) {
+    st = cb::decode_to_csr(p.m, p.n, p.vsize, p.aggregated, p.tiles, p.stream.data(), p.stream.size(),
+                           p.restore_cols.data(), p.restore_cols.size(), row_ptr, col_idx, val, p.nnz, &msg);
+  } else {
+    DeviceGuard g(h->device);
+    CB_CUDA(g.err);
+    std::vector<uint8_t> stream(h->stream_bytes);
+    std::vector<CbTile> tiles(p.tiles.size());
+    std::vector<int32_t> rcols(p.restore_cols.size());
+    CB_CUDA(cudaDeviceSynchronize());
+    if (!stream.empty()) CB_CUDA(cudaMemcpy(stream.data(), h->d_stream, stream.size(), cudaMemcpyDeviceToHost));
+    if (!tiles.empty()) CB_CUDA(cudaMemcpy(tiles.data(), h->d_tiles, tiles.size() * sizeof(CbTile), cudaMemcpyDeviceToHost));
+    if (!rcols.empty()) CB_CUDA(cudaMemcpy(rcols.data(), h->d_rcols, rcols.size() * 4, cudaMemcpyDeviceToHost));
+    st = cb::decode_to_csr(p.m, p.n, p.vsize, p.aggregated, tiles, stream.data(), stream.size(), rcols.data(),
+                           rcols.size(), row_ptr, col_idx, val, p.nnz, &msg);
+  }
+  if (st != CBSPMV_OK) return fail(st, "%s", msg.c_str());
+  return ok();
+}
+
+cbspmv_status_t cbspmv_export_blocked(cbspmv_handle_t h, int32_t* blk_row, int32_t* blk_col, int32_t* nnz_per_blk,
+                                      uint8_t* type_per_blk, int64_t* cols_offset, int32_t* restore_cols) {
+  if (!valid_handle(h)) return fail(CBSPMV_ERR_INVALID, "invalid handle");
+  const cb::Plan& p = h->plan;
+  for (size_t t = 0; t < p.tiles.size(); ++t) {
+    if (blk_row) blk_row[t] = (int32_t)p.tiles[t].brow;
+    if (blk_col) blk_col[t] = p.tile_bcol[t];
+    if (nnz_per_blk) nnz_per_blk[t] = p.tiles[t].nnz;
+    if (type_per_blk) type_per_blk[t] = p.tiles[t].fmt;
+  }
+  if (cols_offset && p.aggregated) std::memcpy(cols_offset, p.cols_offset.data(), p.cols_offset.size() * 8);
+  if (restore_cols && p.aggregated) std::memcpy(restore_cols, p.restore_cols.data(), (size_t)p.restore_cols_len * 4);
+  return ok();
+}
+
+cbspmv_status_t cbspmv_get_stats(cbspmv_handle_t h, cbspmv_stats_t* s) {
+  if (!valid_handle(h) || !s) return fail(CBSPMV_ERR_INVALID, "invalid handle or NULL stats");
+  *s = h->plan.stats;
+  return ok();
+}
+
+cbspmv_status_t cbspmv_destroy(cbspmv_handle_t h) {
+  if (!h) return ok();
+  if (!valid_handle(h)) return fail(CBSPMV_ERR_INVALID, "invalid handle");
+  h->free_device();
+  h->magic = 0;
+  delete h;
+  return ok();
+}
+
+const char* cbspmv_last_error(void) { return g_err.c_str(); }
+
+const char* cbspmv_version(void) { return "cbspmv 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,35 @@
+// Launch interface of the run kernels (kernels.cu), used by the C ABI (capi.cu).
+#ifndef CB_KERNELS_H_
+#define CB_KERNELS_H_
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cb_layout.h"
+
+namespace cb {
+
+struct RunArgs {
+  const uint8_t* stream;        // packed tile records
+  const CbTile* tiles;          // per-tile records, matrix order
+  const int32_t* rcols;         // restore_cols (+ padding); unused when plain
+  const CbUnit* units;
+  const uint32_t* worker_units; // unit ids per persistent CTA
+  const uint32_t* worker_off;   // grid + 1 offsets into worker_units
+  const double* x;
+  double* y;
+  double* partial;              // partial sums of split block rows (16 per slot)
+  uint32_t* split_count;        // arrival counters of split block rows (zero between launches)
+  uint32_t* err;                // device error word
+  int64_t m, n;
+  double alpha, beta;
+  int aggregated;
+  int alpha_one;                // alpha == 1: skip the scaling multiply
+  int beta_nonzero;             // beta != 0: read y
+};
+
+size_t spmv_f64_smem_bytes();
+int spmv_f64_threads();
+cudaError_t launch_spmv_f64(const RunArgs& a, int grid, cudaStream_t stream);
+
+}  // namespace cb
+#endif

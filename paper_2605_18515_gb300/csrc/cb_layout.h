@@ -1,0 +1,72 @@
+// Device-resident layout of an analysed matrix, shared by the host analyser (analyze.cpp)
+// and the kernels (kernels.cu). Plain structs, no CUDA or C++ library types.
+//
+// Packed sub-block stream (Sec. 3.2, "intra-block data aggregation"): every non-empty
+// 16x16 sub-block ("tile") occupies one 16-byte aligned record of the byte stream; its
+// virtual pointer is the record's offset in 16-byte units. Inside a record:
+//   COO   (nnz < th1):  nnz coordinate bytes (row = b & 15, col = b >> 4; Sec. 3.2 and the
+//                       decode of Algorithm 3), entries sorted by (row, col);
+//                       zero padding to 16 B; nnz values.
+//   CSR   (otherwise):  17 row-pointer bytes (0..nnz), then the same coordinate bytes,
+//                       padding to 16 B, nnz values.
+//   DENSE (nnz > th2):  a 32-byte presence bitmap (bit r*16+c), then 256 values
+//                       row-major (Algorithm 4 reads dense_val[row*16 + col]); absent
+//                       entries hold +0.0. The bitmap keeps explicitly stored zeros
+//                       distinguishable so the CSR round trip is exact; the kernel
+//                       ignores it.
+// Values are stored in the handle's value type; the record size is rounded up to 16 B.
+//
+// Column aggregation (Sec. 3.3.1): when on, tile column c of a tile with x-base xb reads
+// x[restore_cols[xb + c]]; when off, x[xb + c] (xb = 16 * block column).
+#ifndef CB_LAYOUT_H_
+#define CB_LAYOUT_H_
+#include <stdint.h>
+
+#define CB_BLK 16
+#define CB_FMT_COO 0
+#define CB_FMT_CSR 1
+#define CB_FMT_DENSE 2
+
+// One high-level metadata record per tile (the five arrays of Sec. 3.1, minus the
+// block column which the kernel does not need, plus the x base it does need).
+struct CbTile {
+  uint32_t vp16;    // virtual pointer: byte offset of the record / 16
+  uint32_t xbase;   // restore_cols index (aggregated) or first column (plain) of column 0
+  uint32_t brow;    // block row
+  uint16_t nnz;     // stored entries (1..256)
+  uint8_t fmt;      // CB_FMT_*
+  uint8_t pad;
+};
+
+// A unit of work: a run of consecutive tiles processed by one warp. Either a group of
+// whole block rows [brow_lo, brow_lo + nbr) (split < 0), or one part of a single block
+// row that was cut into nparts units (split >= 0); the parts combine through the
+// partial-sum buffer in a fixed order.
+struct CbUnit {
+  uint32_t tile_lo;   // first tile
+  uint16_t ntiles;
+  uint16_t nbr;       // block rows covered (1 for split parts)
+  uint32_t brow_lo;
+  uint32_t byte_lo16; // stream offset of the first tile / 16
+  uint32_t nbytes;    // stream bytes of the unit's tiles (multiple of 16)
+  uint32_t work;      // multiply-adds: sum of nnz (COO/CSR) and 256 per Dense tile
+  uint32_t rc_lo;     // first restore_cols entry copied (multiple of 4)
+  uint32_t rc_n;      // restore_cols entries copied (multiple of 4; 0 when plain)
+  int32_t split;      // split-row id or -1
+  uint16_t part, nparts;
+  uint32_t slot;      // partial-sum slot of this part (16 values per slot)
+};
+
+// Kernel geometry for the FP64 path (bytes of shared memory per stage and limits the
+// analyser must respect when it cuts units).
+#define CB_STAGES 8
+#define CB_CONSUMERS 4
+#define CB_B_MAX 14336          // stream bytes per unit
+#define CB_T_MAX 36             // tiles per unit
+#define CB_NBR_MAX 8            // block rows per group unit
+#define CB_R_MAX (CB_NBR_MAX * CB_BLK)
+#define CB_RC_MAX (CB_T_MAX * 16 + 16)   // restore_cols entries per unit (incl. alignment)
+#define CB_RC_PAD 32            // zero entries appended to restore_cols
+#define CB_UNIT_WORK_DEFAULT 1536
+
+#endif

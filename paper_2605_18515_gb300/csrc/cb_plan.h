@@ -1,0 +1,55 @@
+// Host-side result of the analysis (Sec. 3): everything that is uploaded to the device,
+// plus host copies kept for export and statistics. C++ only, no CUDA types.
+#ifndef CB_PLAN_H_
+#define CB_PLAN_H_
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/cbspmv.h"
+#include "cb_layout.h"
+
+namespace cb {
+
+struct Plan {
+  int64_t m = 0, n = 0, nnz = 0;
+  int64_t nbr = 0;                 // block rows
+  int value_dtype = CBSPMV_F64;
+  int vsize = 8;                   // bytes per stored value
+  bool aggregated = false;
+  double th0 = 0.15;
+  int th1 = 32, th2 = 128;
+
+  std::vector<CbTile> tiles;       // row-major order (block row, then block column)
+  std::vector<int32_t> tile_bcol;  // block column per tile (aggregated index when aggregated)
+  std::vector<uint8_t> stream;     // packed records (size multiple of 16)
+  std::vector<int32_t> restore_cols;  // with CB_RC_PAD zero entries appended
+  std::vector<int64_t> cols_offset;   // nbr + 1 (aggregated only)
+  int64_t restore_cols_len = 0;
+
+  std::vector<CbUnit> units;
+  std::vector<uint32_t> worker_units;  // unit ids grouped by worker (CTA)
+  std::vector<uint32_t> worker_off;    // n_workers + 1
+  int n_workers = 0;
+  int n_split_rows = 0;
+  int n_slots = 0;
+
+  cbspmv_stats_t stats{};
+};
+
+// Validates the CSR and fills *plan. n_workers: number of persistent CTAs the kernel will
+// launch (the load balance assigns units to them). Returns CBSPMV_OK or an error with
+// *msg set.
+cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, int n_workers,
+                             Plan* plan, std::string* msg);
+
+// Rebuilds CSR from the packed layout (host arrays). Used by export on both host-only
+// handles and on data read back from the device.
+cbspmv_status_t decode_to_csr(int64_t m, int64_t n, int vsize, bool aggregated,
+                              const std::vector<CbTile>& tiles, const uint8_t* stream,
+                              size_t stream_size, const int32_t* restore_cols,
+                              size_t restore_len, int64_t* row_ptr, int32_t* col, double* val,
+                              int64_t nnz_expected, std::string* msg);
+
+}  // namespace cb
+#endif

@@ -1,0 +1,184 @@
+"""CPU tests of the library's host analysis through the C ABI (host-only handles, no GPU):
+the blocked structure must equal the oracle's restatement of Sec. 3 exactly, the packed
+format must round-trip to the input CSR bit for bit, the load balance must keep its
+invariants and bad input must come back as status codes."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from oracle import blocked as B
+from paper_2605_18515_gb300 import build, inputs as I
+
+
+@pytest.fixture(scope="module")
+def bd():
+    build.build()
+    from paper_2605_18515_gb300 import binding
+    return binding
+
+
+def host(bd, A, **kw):
+    return bd.BlockedMatrix(A, device=-1, **kw)
+
+
+CASES = {
+    "laplace2d_64": lambda: I.laplacian2d(64),
+    "laplace3d_9": lambda: I.laplacian3d(9),
+    "random_ragged": lambda: I.random_csr(203, 157, 0.07, 5),
+    "random_dense": lambda: I.random_csr(70, 45, 0.8, 6),
+    "rmat10": lambda: I.rmat(10, 16, seed=4),
+    "fem_small": lambda: I.fem_block_band(n_rows=6000, n_block_rows=2000, half_band=300, seed=3),
+    "one_row": lambda: I.random_csr(1, 300, 0.5, 7),
+    "one_col": lambda: I.random_csr(300, 1, 0.5, 8),
+}
+
+
+def assert_same_structure(bd, A, M, col_agg=-1, th1=32, th2=128, th0=0.15):
+    S = B.blocked_structure(A, th0=th0, th1=th1, th2=th2, col_agg=col_agg)
+    got = M.export_blocked()
+    assert got["aggregated"] == S.aggregated
+    assert np.array_equal(got["blk_row"], S.tile_brow)
+    assert np.array_equal(got["blk_col"], S.tile_bcol)
+    assert np.array_equal(got["nnz"], S.tile_nnz)
+    assert np.array_equal(got["type"], S.tile_fmt)
+    if S.aggregated:
+        assert np.array_equal(got["cols_offset"], S.cols_offset)
+        assert np.array_equal(got["restore_cols"], S.restore_cols)
+    st = M.stats()
+    assert st["n_tiles"] == S.tile_nnz.size
+    assert st["super_sparse_fraction"] == pytest.approx(B.super_sparse_fraction(A, th1), abs=0)
+    coarse, fine = B.nnz_histogram(S.tile_nnz)
+    assert st["hist_coarse"] == coarse.tolist() and st["hist_fine"] == fine.tolist()
+
+
+def assert_roundtrip(M, A):
+    rp, col, val = M.export_csr()
+    assert np.array_equal(rp, A.row_ptr)
+    assert np.array_equal(col, A.col)
+    assert np.array_equal(val.view(np.uint64), A.val.view(np.uint64))   # bit-exact
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("col_agg", [-1, 0, 1])
+def test_structure_and_roundtrip(bd, name, col_agg):
+    A = CASES[name]()
+    with host(bd, A, col_agg=col_agg) as M:
+        assert_same_structure(bd, A, M, col_agg=col_agg)
+        assert_roundtrip(M, A)
+
+
+@pytest.mark.parametrize("th1,th2", [(0, 0), (16, 64), (32, 128), (257 - 1, 256), (1, 255)])
+def test_thresholds(bd, th1, th2):
+    A = I.random_csr(96, 96, 0.35, 9)
+    with host(bd, A, th1=th1, th2=th2, col_agg=0) as M:
+        assert_same_structure(bd, A, M, col_agg=0, th1=th1, th2=th2)
+        assert_roundtrip(M, A)
+
+
+def test_explicit_zeros_survive_dense_tiles(bd):
+    # a full 16x16 tile (Dense) with some stored values equal to +0.0 and -0.0
+    idx = np.arange(256)
+    v = I.uniform_pm1(1, 2, 256)
+    v[[3, 77, 200]] = 0.0
+    v[[5]] = -0.0
+    A = I.csr_from_coo(16, 16, idx // 16, idx % 16, v, sum_duplicates=False)
+    # drop two entries so that the tile has absent positions too
+    keep = np.ones(256, bool); keep[[10, 11]] = False
+    A = I.csr_from_coo(16, 16, (idx // 16)[keep], (idx % 16)[keep], v[keep], sum_duplicates=False)
+    with host(bd, A) as M:
+        assert M.stats()["n_fmt"][B.FMT_DENSE] == 1
+        assert_roundtrip(M, A)
+
+
+def test_worked_example(bd):
+    from test_oracle_blocked import example_32x48
+    A = example_32x48()
+    with host(bd, A) as M:
+        g = M.export_blocked()
+        assert g["aggregated"]
+        assert g["type"].tolist() == [B.FMT_COO, B.FMT_DENSE, B.FMT_COO]
+        st = M.stats()
+    with host(bd, A, col_agg=0) as M0:
+        st0 = M0.stats()
+        assert st0["model_bytes_cb"] == 2463 and st0["model_bytes_csr"] == 3276
+        assert st0["model_bytes_bsr16"] == 10272
+
+
+def test_units_and_load_balance_invariants(bd):
+    A = I.rmat(12, 16, seed=9)
+    with host(bd, A) as M:
+        st = M.stats()
+        assert st["n_units"] >= 1 and st["n_workers"] == 1
+        # host-only handles plan for one worker: every unit goes to it
+        assert st["worker_load_max"] == pytest.approx(st["worker_load_mean"])
+        assert st["mults_per_run"] >= A.nnz
+
+
+def test_empty_and_degenerate(bd):
+    for m, n in ((0, 0), (5, 0), (0, 7), (17, 33)):
+        A = I.CSR(m, n, np.zeros(m + 1, np.int64), np.zeros(0, np.int32), np.zeros(0))
+        with host(bd, A) as M:
+            st = M.stats()
+            assert st["n_tiles"] == 0 and st["nnz"] == 0
+            assert_roundtrip(M, A)
+
+
+@pytest.mark.parametrize("bad", ["unsorted", "duplicate", "col_range", "rowptr", "neg_col"])
+def test_rejects_non_canonical(bd, bad):
+    A = I.random_csr(40, 40, 0.3, 3)
+    col = A.col.copy(); rp = A.row_ptr.copy()
+    if bad == "unsorted":
+        r = np.flatnonzero(np.diff(rp) >= 2)[0]; k = rp[r]
+        col[k], col[k + 1] = col[k + 1], col[k]
+    elif bad == "duplicate":
+        r = np.flatnonzero(np.diff(rp) >= 2)[0]; k = rp[r]
+        col[k + 1] = col[k]
+    elif bad == "col_range":
+        col[-1] = 40
+    elif bad == "neg_col":
+        col[0] = -1
+    elif bad == "rowptr":
+        rp[5] = rp[6] + 1
+    B_ = I.CSR(A.m, A.n, rp, col, A.val)
+    with pytest.raises(bd.CbspmvError) as e:
+        host(bd, B_)
+    assert e.value.status == 2
+    assert "row" in str(e.value) or "column" in str(e.value)
+
+
+def test_rejects_bad_options(bd):
+    A = I.random_csr(20, 20, 0.3, 3)
+    for kw in ({"th1": 40, "th2": 30}, {"th2": 300}, {"col_agg": 2}, {"unit_work": -1}, {"device": -5}):
+        with pytest.raises(bd.CbspmvError) as e:
+            host(bd, A, **{k: v for k, v in kw.items() if k != "device"}) if "device" not in kw else \
+                bd.BlockedMatrix(A, device=kw["device"])
+        assert e.value.status == 1
+    with pytest.raises(bd.CbspmvError) as e:
+        host(bd, A, value_dtype="bf16")
+    assert e.value.status in (1, 6)
+
+
+def test_null_and_invalid_handles(bd):
+    L = bd.lib()
+    assert L.cbspmv_destroy(None) == 0
+    assert L.cbspmv_run(None, None, None, 1.0, 0.0, None) == 1
+    assert b"invalid handle" in L.cbspmv_last_error()
+    s = bd.Stats()
+    assert L.cbspmv_get_stats(None, ctypes.byref(s)) == 1
+    A = I.random_csr(20, 20, 0.3, 3)
+    with host(bd, A) as M:
+        assert L.cbspmv_run(M.handle, None, None, 1.0, 0.0, None) == 1     # host-only handle
+        assert b"host-only" in L.cbspmv_last_error()
+
+
+def test_storage_model_matches_oracle_formula(bd):
+    A = I.random_csr(300, 280, 0.02, 44)
+    with host(bd, A, col_agg=0, th1=257 - 1, th2=256) as M:   # every tile COO
+        st = M.stats()
+        S = B.blocked_structure(A, col_agg=0, th1=256, th2=256)
+        ref = B.storage_bytes(A.m, A.nnz, S.tile_nnz.size, (A.m + 15) // 16)
+        assert st["model_bytes_cb"] == ref["cb_coo"]
+        assert st["model_bytes_csr"] == ref["csr"]
+        assert st["model_bytes_bsr16"] == ref["bsr16"]
+        assert st["n_fmt"][0] == S.tile_nnz.size
