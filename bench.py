@@ -34,6 +34,7 @@ WORKLOADS = {
     "fem3x3_band_1m": "FP64 block-structured FEM-like matrix: 1,048,576 rows of dense 3x3 blocks, "
                       "~27 blocks per block row within a 2,000 block-column band, N(0,1) values, "
                       "x U[-1,1], seed 1",
+    "fem3x3_band_256k": "FP64 FEM-like 3x3 block band, quarter size (262,144 rows), for profiling",
     "rmat_s21": "FP64 R-MAT scale 21, edge factor 16, (a,b,c,d) = (.57,.19,.19,.05), duplicates summed, "
                 "U[-1,1] values, seed 2",
     "laplace2d_64": "FP64 2D 5-point Laplacian on a 64x64 grid, x U[-1,1], seed 0",

@@ -261,6 +261,10 @@ def config_matrix(name: str) -> tuple[CSR, np.ndarray]:
     if name == "fem3x3_band_1m":
         A = fem_block_band(seed=1)
         return A, vector_x(A.n, 1)
+    if name == "fem3x3_band_256k":
+        # quarter-size profiling case of the FEM family (packed stream still > L2)
+        A = fem_block_band(n_rows=262_144, n_block_rows=87_382, seed=1)
+        return A, vector_x(A.n, 1)
     if name == "rmat_s21":
         A = rmat(21, 16, seed=2)
         return A, vector_x(A.n, 2)
