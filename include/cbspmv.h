@@ -148,6 +148,25 @@ cbspmv_status_t cbspmv_run(cbspmv_handle_t h, const void* x, void* y, double alp
 cbspmv_status_t cbspmv_run_host(cbspmv_handle_t h, const double* x_host, double* y_host,
                                 double alpha, double beta, void* stream);
 
+/* The product of cbspmv_run with no allocation of any kind. The paper has no counterpart:
+ * this entry point exists for callers that may not call cudaMalloc, cudaFree or any
+ * allocating routine when they run the product, for example code whose device memory
+ * is owned by another allocator (a framework's memory pool) or code on a latency-critical
+ * path where an allocation, which can synchronise the device, is not acceptable.
+ * Arguments, layouts and the result are those of cbspmv_run; h must be a device handle.
+ * Scratch: the partial sums and arrival counters of block rows cut into several units come
+ * from one fixed array in the library's device image (7.75 MiB, held by every GPU that
+ * loads the library until the process exits): at most 61,440 partial-sum slots and 65,536
+ * cut block rows (cbspmv_get_stats: n_split_units, n_split_rows); larger matrices are
+ * rejected with CBSPMV_ERR_INVALID. The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture. Every call clears the array's counters on `stream` and then reuses the
+ * whole array, so calls whose work overlaps on the GPU (other streams, other handles, other
+ * host threads) race and give wrong results: serialise them. Device-side wait errors go to
+ * the handle's error word (cbspmv_check_device). */
+cbspmv_status_t cbspmv_run_noalloc(cbspmv_handle_t h, const void* x, void* y, double alpha,
+                                   double beta, void* stream);
+
 /* Reads the handle's device error word (set by bounded device-side waits that gave up)
  * and clears it: CBSPMV_OK or CBSPMV_ERR_TIMEOUT. Synchronises `stream`. */
 cbspmv_status_t cbspmv_check_device(cbspmv_handle_t h, void* stream);

@@ -63,6 +63,7 @@ SIGNATURES = {
     "cbspmv_analyze": [ctypes.POINTER(Csr), ctypes.POINTER(Opts), _P, ctypes.POINTER(_P)],
     "cbspmv_run": [_P, _P, _P, _D, _D, _P],
     "cbspmv_run_host": [_P, _P, _P, _D, _D, _P],
+    "cbspmv_run_noalloc": [_P, _P, _P, _D, _D, _P],
     "cbspmv_check_device": [_P, _P],
     "cbspmv_export_csr": [_P, _P, _P, _P],
     "cbspmv_export_blocked": [_P, _P, _P, _P, _P, _P, _P],

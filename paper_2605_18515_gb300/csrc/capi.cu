@@ -10,6 +10,7 @@
 
 #include "../../include/cbspmv.h"
 #include "cb_kernels.h"
+#include "cb_noalloc.h"
 #include "cb_plan.h"
 
 namespace {
@@ -339,3 +340,29 @@ const char* cbspmv_last_error(void) { return g_err.c_str(); }
 const char* cbspmv_version(void) { return "cbspmv 0.1 (sm_103a)"; }
 
 }  // extern "C"
+
+namespace cb {
+
+bool noalloc_view(cbspmv_handle_t h, NoallocView* v) {
+  if (!valid_handle(h)) return false;
+  v->device = h->device;
+  v->grid = h->grid;
+  v->plan = &h->plan;
+  RunArgs a{};
+  a.stream = h->d_stream;
+  a.tiles = h->d_tiles;
+  a.rcols = h->d_rcols;
+  a.units = h->d_units;
+  a.worker_units = h->d_wunits;
+  a.worker_off = h->d_woff;
+  a.err = h->d_err;
+  a.m = h->plan.m;
+  a.n = h->plan.n;
+  a.aggregated = h->plan.aggregated ? 1 : 0;
+  v->args = a;
+  return true;
+}
+
+void set_last_error(const std::string& msg) { g_err = msg; }
+
+}  // namespace cb
