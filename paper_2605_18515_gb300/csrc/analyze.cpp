@@ -74,6 +74,7 @@ struct BlockRowOut {
   std::vector<int32_t> bcol;       // block column per tile
   std::vector<uint16_t> nnz;
   std::vector<uint8_t> fmt;
+  std::vector<uint8_t> rowcnt;     // 16 per tile: multiply-adds of each tile row
   std::vector<int32_t> distinct;   // distinct columns in order (aggregated only)
 };
 
@@ -131,6 +132,13 @@ void build_block_row(const cbspmv_csr_t& A, int64_t b, bool agg, int th1, int th
     std::sort(tile.begin(), tile.end());
     int nnz = (int)tile.size();
     int fmt = select_format(nnz, th1, th2);
+    {
+      size_t rc0 = out.rowcnt.size();
+      out.rowcnt.resize(rc0 + 16, 0);
+      for (auto& t : tile) out.rowcnt[rc0 + (t.first >> 4)]++;
+      if (fmt == CB_FMT_DENSE)
+        for (int r = 0; r < 16; ++r) out.rowcnt[rc0 + r] = 16;   // zero fill is multiplied too
+    }
     uint32_t rb = record_bytes(fmt, nnz, vsize);
     uint32_t base = (uint32_t)out.bytes.size();
     out.bytes.resize(base + rb, 0);
@@ -272,7 +280,9 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
   const int64_t ntiles = tile_off[nbr];
   if (byte_off[nbr] / 16 >= (1LL << 32)) { *msg = "packed stream exceeds 64 GiB"; return CBSPMV_ERR_UNSUPPORTED; }
   p.restore_cols_len = p.aggregated ? p.cols_offset[nbr] : 0;
+  std::vector<uint8_t> rowcnt;
   try {
+    rowcnt.resize((size_t)ntiles * 16);
     p.tiles.resize(ntiles);
     p.tile_bcol.resize(ntiles);
     p.stream.resize(byte_off[nbr]);
@@ -297,12 +307,15 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
       }
       if (p.aggregated && !o.distinct.empty())
         std::memcpy(p.restore_cols.data() + p.cols_offset[b], o.distinct.data(), o.distinct.size() * 4);
+      if (!o.rowcnt.empty()) std::memcpy(rowcnt.data() + (size_t)tile_off[b] * 16, o.rowcnt.data(), o.rowcnt.size());
       BlockRowOut().bytes.swap(o.bytes);
+      std::vector<uint8_t>().swap(o.rowcnt);
     }
   });
 
   // --- step 4a: units of work
-  const uint32_t U = opts.unit_work > 0 ? (uint32_t)opts.unit_work : CB_UNIT_WORK_DEFAULT;
+  const uint32_t U = opts.unit_work > 0 ? std::min<uint32_t>((uint32_t)opts.unit_work, CB_UNIT_WORK_MAX)
+                                        : CB_UNIT_WORK_DEFAULT;
   auto tile_work = [&](int64_t t) -> uint32_t { return p.tiles[t].fmt == CB_FMT_DENSE ? 256u : p.tiles[t].nnz; };
   auto tile_bytes = [&](int64_t t) -> uint32_t {
     return record_bytes(p.tiles[t].fmt, p.tiles[t].nnz, p.vsize);
@@ -387,6 +400,106 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
   p.n_split_rows = split_id;
   p.n_slots = (int)slot;
 
+  // --- step 4a': lane schedule of every unit (chunks of <= CB_CHUNK entries, see cb_layout.h)
+  {
+    const size_t nun = p.units.size();
+    // bytes of each unit's schedule: header + steps * 64
+    std::vector<uint64_t> sbytes(nun), chunks_of(nun);
+    parallel_for((int64_t)nun, 256, [&](int64_t lo, int64_t hi) {
+      for (int64_t i = lo; i < hi; ++i) {
+        const CbUnit& u = p.units[i];
+        const int64_t R = std::min<int64_t>((int64_t)CB_BLK * u.nbr, A.m - (int64_t)u.brow_lo * CB_BLK);
+        uint64_t nch = 0;
+        for (uint32_t t = 0; t < u.ntiles; ++t) {
+          const int64_t brl = (int64_t)p.tiles[u.tile_lo + t].brow - u.brow_lo;
+          for (int rr = 0; rr < 16; ++rr)
+            if (brl * 16 + rr < R) nch += (rowcnt[(size_t)(u.tile_lo + t) * 16 + rr] + CB_CHUNK - 1) / CB_CHUNK;
+        }
+        chunks_of[i] = nch;
+        sbytes[i] = CB_SCHED_HDR(R) + 64 * ((nch + CB_VLANES - 1) / CB_VLANES);
+      }
+    });
+    std::vector<uint64_t> off(nun + 1, 0);
+    for (size_t i = 0; i < nun; ++i) off[i + 1] = off[i] + sbytes[i];
+    if (off[nun] / 16 >= (1ULL << 32)) { *msg = "schedule array too large"; return CBSPMV_ERR_UNSUPPORTED; }
+    p.sched.assign(off[nun] / 4, 0);
+    parallel_for((int64_t)nun, 128, [&](int64_t lo, int64_t hi) {
+      std::vector<uint16_t> chunk;      // descriptors in row-major order
+      std::vector<uint8_t> chunk_row;   // row of each chunk
+      std::vector<uint8_t> chunk_first; // chunk starts its row
+      for (int64_t i = lo; i < hi; ++i) {
+        CbUnit& u = p.units[i];
+        const int64_t R = std::min<int64_t>((int64_t)CB_BLK * u.nbr, A.m - (int64_t)u.brow_lo * CB_BLK);
+        uint8_t* base = reinterpret_cast<uint8_t*>(p.sched.data()) + off[i];
+        uint16_t* hdr = reinterpret_cast<uint16_t*>(base);
+        uint8_t* nxt = base + 64;
+        uint16_t* desc = reinterpret_cast<uint16_t*>(base + CB_SCHED_HDR(R));
+        chunk.clear(); chunk_row.clear(); chunk_first.clear();
+        // tiles of each block row of the unit are consecutive; walk rows in order
+        uint32_t t_begin = 0;
+        for (int64_t brl = 0; brl < u.nbr; ++brl) {
+          uint32_t t_end = t_begin;
+          while (t_end < u.ntiles && (int64_t)p.tiles[u.tile_lo + t_end].brow - u.brow_lo == brl) ++t_end;
+          for (int rr = 0; rr < 16; ++rr) {
+            const int64_t row = brl * 16 + rr;
+            if (row >= R) break;
+            bool first = true;
+            for (uint32_t t = t_begin; t < t_end; ++t) {
+              const size_t tg = (size_t)(u.tile_lo + t);
+              const uint32_t c = rowcnt[tg * 16 + rr];
+              if (!c) continue;
+              uint32_t s0;
+              if (p.tiles[tg].fmt == CB_FMT_DENSE) {
+                s0 = 16u * rr;
+              } else {
+                s0 = 0;
+                for (int q = 0; q < rr; ++q) s0 += rowcnt[tg * 16 + q];
+              }
+              for (uint32_t o = 0; o < c; o += CB_CHUNK) {
+                const uint32_t len = std::min<uint32_t>(CB_CHUNK, c - o);
+                chunk.push_back((uint16_t)(t | ((s0 + o) << 5) | (len << 13)));
+                chunk_row.push_back((uint8_t)row);
+                chunk_first.push_back(first ? 1 : 0);
+                first = false;
+              }
+            }
+            if (!first) chunk.back() |= (uint16_t)0x8000u;    // last chunk of the row
+          }
+          t_begin = t_end;
+        }
+        // next row holding entries, for every row
+        {
+          std::vector<uint8_t> has(R, 0);
+          for (uint8_t r : chunk_row) has[r] = 1;
+          int next = 0xff;
+          for (int64_t r = R - 1; r >= 0; --r) {
+            nxt[r] = (uint8_t)next;
+            if (has[r]) next = (int)r;
+          }
+        }
+        const uint64_t nch = chunk.size();
+        for (uint32_t l = 0; l < CB_VLANES; ++l) {
+          const uint64_t c0 = (l * nch) / CB_VLANES, c1 = ((l + 1) * nch) / CB_VLANES;
+          if (c1 == c0) { hdr[l] = 0; continue; }
+          const uint32_t hs = chunk_first[c0] ? 0u : 1u;
+          hdr[l] = (uint16_t)(chunk_row[c0] | (hs << 8) | ((uint32_t)(c1 - c0) << 9));
+          for (uint64_t k = c0; k < c1; ++k) desc[(k - c0) * CB_VLANES + l] = chunk[k];
+        }
+        u.sched16 = (uint32_t)(off[i] / 16);
+        u.sched_bytes = (uint32_t)sbytes[i];
+      }
+    });
+  }
+
+  // every unit must fit one shared-memory stage of the kernel
+  for (const CbUnit& u : p.units) {
+    if (u.nbytes > CB_B_MAX || u.ntiles > CB_T_MAX || u.rc_n > CB_RC_MAX || u.sched_bytes > CB_SCHED_MAX ||
+        u.nbr > CB_NBR_MAX || u.nbr == 0) {
+      *msg = "internal error: a unit exceeds the kernel's stage limits";
+      return CBSPMV_ERR_INVALID;
+    }
+  }
+
   // --- step 4b: load balance of units over the persistent thread blocks (Sec. 3.4):
   // longest-processing-time order, min-heap of (load, worker id).
   const int64_t nu = (int64_t)p.units.size();
@@ -448,7 +561,8 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
   }
   s.restore_cols_len = p.restore_cols_len;
   s.stream_bytes = (int64_t)p.stream.size();
-  s.metadata_bytes = ntiles * (int64_t)sizeof(CbTile);
+  s.metadata_bytes = ntiles * (int64_t)sizeof(CbTile) + (int64_t)p.sched.size() * 4 +
+                     (int64_t)p.units.size() * (int64_t)sizeof(CbUnit);
   s.model_bytes_cb = ntiles * 21 + A.nnz * 9;
   s.model_bytes_csr = (A.m + 1) * 4 + A.nnz * 12;
   s.model_bytes_bsr16 = 2048 * ntiles + (nbr + 1) * 4 + 4 * ntiles;

@@ -69,6 +69,7 @@ struct cbspmv_handle_s {
   CbTile* d_tiles = nullptr;
   int32_t* d_rcols = nullptr;
   CbUnit* d_units = nullptr;
+  uint32_t* d_sched = nullptr;
   uint32_t* d_wunits = nullptr;
   uint32_t* d_woff = nullptr;
   double* d_partial = nullptr;
@@ -81,7 +82,7 @@ struct cbspmv_handle_s {
     if (device < 0) return;
     DeviceGuard g(device);
     cudaDeviceSynchronize();
-    void* ptrs[] = {d_stream, d_tiles, d_rcols, d_units, d_wunits, d_woff, d_partial, d_split_count,
+    void* ptrs[] = {d_stream, d_tiles, d_rcols, d_units, d_sched, d_wunits, d_woff, d_partial, d_split_count,
                     d_err, d_xstage, d_ystage};
     for (void* p : ptrs)
       if (p) cudaFree(p);
@@ -89,6 +90,7 @@ struct cbspmv_handle_s {
     d_tiles = nullptr;
     d_rcols = nullptr;
     d_units = nullptr;
+    d_sched = nullptr;
     d_wunits = nullptr;
     d_woff = nullptr;
     d_partial = nullptr;
@@ -182,6 +184,7 @@ cbspmv_status_t cbspmv_analyze(const cbspmv_csr_t* A, const cbspmv_opts_t* opts_
   step(upload(&h->d_tiles, p.tiles.data(), p.tiles.size(), s));
   step(upload(&h->d_rcols, p.restore_cols.data(), p.restore_cols.size(), s));
   step(upload(&h->d_units, p.units.data(), p.units.size(), s));
+  step(upload(&h->d_sched, p.sched.data(), p.sched.size(), s));
   step(upload(&h->d_wunits, p.worker_units.data(), p.worker_units.size(), s));
   step(upload(&h->d_woff, p.worker_off.data(), p.worker_off.size(), s));
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_partial, (size_t)(p.n_slots ? p.n_slots : 1) * 16 * sizeof(double));
@@ -211,6 +214,7 @@ static cbspmv_status_t run_device(cbspmv_handle_t h, const double* x, double* y,
   a.tiles = h->d_tiles;
   a.rcols = h->d_rcols;
   a.units = h->d_units;
+  a.sched = h->d_sched;
   a.worker_units = h->d_wunits;
   a.worker_off = h->d_woff;
   a.x = x;
@@ -353,6 +357,7 @@ bool noalloc_view(cbspmv_handle_t h, NoallocView* v) {
   a.tiles = h->d_tiles;
   a.rcols = h->d_rcols;
   a.units = h->d_units;
+  a.sched = h->d_sched;
   a.worker_units = h->d_wunits;
   a.worker_off = h->d_woff;
   a.err = h->d_err;

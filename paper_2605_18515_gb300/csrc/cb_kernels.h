@@ -13,6 +13,7 @@ struct RunArgs {
   const CbTile* tiles;          // per-tile records, matrix order
   const int32_t* rcols;         // restore_cols (+ padding); unused when plain
   const CbUnit* units;
+  const uint32_t* sched;        // lane schedules of the units
   const uint32_t* worker_units; // unit ids per persistent CTA
   const uint32_t* worker_off;   // grid + 1 offsets into worker_units
   const double* x;

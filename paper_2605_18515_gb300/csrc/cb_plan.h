@@ -28,6 +28,7 @@ struct Plan {
   int64_t restore_cols_len = 0;
 
   std::vector<CbUnit> units;
+  std::vector<uint32_t> sched;         // lane schedules of all units (see cb_layout.h)
   std::vector<uint32_t> worker_units;  // unit ids grouped by worker (CTA)
   std::vector<uint32_t> worker_off;    // n_workers + 1
   int n_workers = 0;
