@@ -135,9 +135,10 @@ cbspmv_status_t cbspmv_analyze(const cbspmv_csr_t* A, const cbspmv_opts_t* opts,
 /* y = alpha * A * x + beta * y on the device (Sec. 3.5, Algorithms 3 and 4).
  * x: device array of n values, y: device array of m values, both of the handle's
  * vector type (double for CBSPMV_F64 and for all value types in this version), 8-byte
- * aligned; y must not overlap x. Enqueued on `stream`, no host synchronisation. One
- * kernel launch. Concurrent runs on one handle must be serialised on one stream (they
- * share the handle's partial-sum buffer). Errors: CBSPMV_ERR_INVALID, CBSPMV_ERR_CUDA. */
+ * aligned; y must not overlap x. Enqueued on `stream`, no host synchronisation. One kernel
+ * launch, plus a second small one that adds the parts of block rows the analysis cut into
+ * several units (when there are any). Concurrent runs on one handle must be serialised on
+ * one stream (they share the handle's partial-sum buffer). Errors: CBSPMV_ERR_INVALID, CBSPMV_ERR_CUDA. */
 cbspmv_status_t cbspmv_run(cbspmv_handle_t h, const void* x, void* y, double alpha, double beta,
                            void* stream);
 
@@ -154,15 +155,15 @@ cbspmv_status_t cbspmv_run_host(cbspmv_handle_t h, const double* x_host, double*
  * is owned by another allocator (a framework's memory pool) or code on a latency-critical
  * path where an allocation, which can synchronise the device, is not acceptable.
  * Arguments, layouts and the result are those of cbspmv_run; h must be a device handle.
- * Scratch: the partial sums and arrival counters of block rows cut into several units come
- * from one fixed array in the library's device image (7.75 MiB, held by every GPU that
- * loads the library until the process exits): at most 61,440 partial-sum slots and 65,536
- * cut block rows (cbspmv_get_stats: n_split_units, n_split_rows); larger matrices are
- * rejected with CBSPMV_ERR_INVALID. The first call on each device looks up the array's
- * device address (cudaGetSymbolAddress) and caches it; make that first call before any
- * stream capture. Every call clears the array's counters on `stream` and then reuses the
- * whole array, so calls whose work overlaps on the GPU (other streams, other handles, other
- * host threads) race and give wrong results: serialise them. Device-side wait errors go to
+ * Scratch: the partial sums of block rows cut into several units come from one fixed array
+ * in the library's device image (7.75 MiB, held by every GPU that loads the library until
+ * the process exits): at most 63,488 partial-sum slots (cbspmv_get_stats: n_split_units);
+ * larger matrices are rejected with CBSPMV_ERR_INVALID. The first call on each device looks
+ * up the array's device address (cudaGetSymbolAddress) and caches it; make that first call
+ * before any stream capture. Every call writes each slot it reads before reading it, so no
+ * clearing is needed, but all calls share the array: calls whose work overlaps on the GPU
+ * (other streams, other handles, other host threads) race and give wrong results, so
+ * serialise them. Device-side wait errors go to
  * the handle's error word (cbspmv_check_device). */
 cbspmv_status_t cbspmv_run_noalloc(cbspmv_handle_t h, const void* x, void* y, double alpha,
                                    double beta, void* stream);

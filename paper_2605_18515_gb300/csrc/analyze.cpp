@@ -389,6 +389,12 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
     }
     finish_unit(u);
     uint16_t np = (uint16_t)(p.units.size() - first_unit);
+    CbSplitRow sr{};
+    sr.slot0 = slot;
+    sr.brow = (uint32_t)b;
+    sr.nparts = np;
+    sr.rows = (uint16_t)std::min<int64_t>(CB_BLK, A.m - b * CB_BLK);
+    p.split_rows.push_back(sr);
     for (size_t i = first_unit; i < p.units.size(); ++i) {
       p.units[i].part = (uint16_t)(i - first_unit);
       p.units[i].nparts = np;
@@ -416,7 +422,10 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
             if (brl * 16 + rr < R) nch += (rowcnt[(size_t)(u.tile_lo + t) * 16 + rr] + CB_CHUNK - 1) / CB_CHUNK;
         }
         chunks_of[i] = nch;
-        sbytes[i] = CB_SCHED_HDR(R) + 64 * ((nch + CB_VLANES - 1) / CB_VLANES);
+        // descriptor rows: chunks of the longest run, rounded up to an even count because
+        // the kernel reads the chunks of a run in pairs
+        const uint64_t rows = ((nch + CB_VLANES - 1) / CB_VLANES + 1) & ~1ULL;
+        sbytes[i] = CB_SCHED_HDR(R) + 2 * CB_VLANES * rows;
       }
     });
     std::vector<uint64_t> off(nun + 1, 0);
@@ -432,7 +441,7 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
         const int64_t R = std::min<int64_t>((int64_t)CB_BLK * u.nbr, A.m - (int64_t)u.brow_lo * CB_BLK);
         uint8_t* base = reinterpret_cast<uint8_t*>(p.sched.data()) + off[i];
         uint16_t* hdr = reinterpret_cast<uint16_t*>(base);
-        uint8_t* nxt = base + 64;
+        uint8_t* nxt = base + 2 * CB_VLANES;
         uint16_t* desc = reinterpret_cast<uint16_t*>(base + CB_SCHED_HDR(R));
         chunk.clear(); chunk_row.clear(); chunk_first.clear();
         // tiles of each block row of the unit are consecutive; walk rows in order
@@ -491,9 +500,35 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
     });
   }
 
+  // --- unit blobs: tile records, restore_cols slice and schedule of each unit, back to back
+  {
+    const size_t nun = p.units.size();
+    std::vector<uint64_t> boff(nun + 1, 0);
+    for (size_t i = 0; i < nun; ++i) {
+      CbUnit& u = p.units[i];
+      u.blob_bytes = 16u * u.ntiles + 4u * u.rc_n + u.sched_bytes;
+      boff[i + 1] = boff[i] + u.blob_bytes;
+    }
+    if (boff[nun] / 16 >= (1ULL << 32)) { *msg = "unit blob array too large"; return CBSPMV_ERR_UNSUPPORTED; }
+    p.blob.assign(boff[nun], 0);
+    parallel_for((int64_t)nun, 256, [&](int64_t lo, int64_t hi) {
+      for (int64_t i = lo; i < hi; ++i) {
+        CbUnit& u = p.units[i];
+        uint8_t* d = p.blob.data() + boff[i];
+        if (u.ntiles) std::memcpy(d, p.tiles.data() + u.tile_lo, 16u * u.ntiles);
+        if (u.rc_n) std::memcpy(d + 16u * u.ntiles, p.restore_cols.data() + u.rc_lo, 4u * u.rc_n);
+        if (u.sched_bytes)
+          std::memcpy(d + 16u * u.ntiles + 4u * u.rc_n, reinterpret_cast<const uint8_t*>(p.sched.data()) + (size_t)u.sched16 * 16,
+                      u.sched_bytes);
+        u.blob16 = (uint32_t)(boff[i] / 16);
+      }
+    });
+  }
+
   // every unit must fit one shared-memory stage of the kernel
   for (const CbUnit& u : p.units) {
     if (u.nbytes > CB_B_MAX || u.ntiles > CB_T_MAX || u.rc_n > CB_RC_MAX || u.sched_bytes > CB_SCHED_MAX ||
+        u.blob_bytes > 16u * CB_T_MAX + 4u * CB_RC_MAX + CB_SCHED_MAX ||
         u.nbr > CB_NBR_MAX || u.nbr == 0) {
       *msg = "internal error: a unit exceeds the kernel's stage limits";
       return CBSPMV_ERR_INVALID;
@@ -533,11 +568,18 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
       load[i % n_workers] += cost[i];
     }
   }
+  // store the units in worker order: each CTA's units are one contiguous range
   p.worker_off.assign(n_workers + 1, 0);
   p.worker_units.reserve(nu);
   for (int w = 0; w < n_workers; ++w) {
     p.worker_off[w + 1] = p.worker_off[w] + (uint32_t)lists[w].size();
     p.worker_units.insert(p.worker_units.end(), lists[w].begin(), lists[w].end());
+  }
+  {
+    std::vector<CbUnit> ordered(nu);
+    static_assert(sizeof(CbUnit) == 64, "unit descriptor is 64 bytes");
+    for (int64_t i = 0; i < nu; ++i) ordered[i] = p.units[p.worker_units[i]];
+    p.units.swap(ordered);
   }
 
   // --- statistics

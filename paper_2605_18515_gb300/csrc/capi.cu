@@ -69,11 +69,11 @@ struct cbspmv_handle_s {
   CbTile* d_tiles = nullptr;
   int32_t* d_rcols = nullptr;
   CbUnit* d_units = nullptr;
-  uint32_t* d_sched = nullptr;
+  uint8_t* d_blob = nullptr;
   uint32_t* d_wunits = nullptr;
   uint32_t* d_woff = nullptr;
   double* d_partial = nullptr;
-  uint32_t* d_split_count = nullptr;
+  CbSplitRow* d_split_rows = nullptr;
   uint32_t* d_err = nullptr;
   double* d_xstage = nullptr;
   double* d_ystage = nullptr;
@@ -82,7 +82,7 @@ struct cbspmv_handle_s {
     if (device < 0) return;
     DeviceGuard g(device);
     cudaDeviceSynchronize();
-    void* ptrs[] = {d_stream, d_tiles, d_rcols, d_units, d_sched, d_wunits, d_woff, d_partial, d_split_count,
+    void* ptrs[] = {d_stream, d_tiles, d_rcols, d_units, d_blob, d_wunits, d_woff, d_partial, d_split_rows,
                     d_err, d_xstage, d_ystage};
     for (void* p : ptrs)
       if (p) cudaFree(p);
@@ -90,11 +90,11 @@ struct cbspmv_handle_s {
     d_tiles = nullptr;
     d_rcols = nullptr;
     d_units = nullptr;
-    d_sched = nullptr;
+    d_blob = nullptr;
     d_wunits = nullptr;
     d_woff = nullptr;
     d_partial = nullptr;
-    d_split_count = nullptr;
+    d_split_rows = nullptr;
     d_err = nullptr;
     d_xstage = nullptr;
     d_ystage = nullptr;
@@ -184,12 +184,11 @@ cbspmv_status_t cbspmv_analyze(const cbspmv_csr_t* A, const cbspmv_opts_t* opts_
   step(upload(&h->d_tiles, p.tiles.data(), p.tiles.size(), s));
   step(upload(&h->d_rcols, p.restore_cols.data(), p.restore_cols.size(), s));
   step(upload(&h->d_units, p.units.data(), p.units.size(), s));
-  step(upload(&h->d_sched, p.sched.data(), p.sched.size(), s));
+  step(upload(&h->d_blob, p.blob.data(), p.blob.size(), s));
   step(upload(&h->d_wunits, p.worker_units.data(), p.worker_units.size(), s));
   step(upload(&h->d_woff, p.worker_off.data(), p.worker_off.size(), s));
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_partial, (size_t)(p.n_slots ? p.n_slots : 1) * 16 * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_split_count, (size_t)(p.n_split_rows ? p.n_split_rows : 1) * 4);
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_split_count, 0, (size_t)(p.n_split_rows ? p.n_split_rows : 1) * 4, s);
+  step(upload(&h->d_split_rows, p.split_rows.data(), p.split_rows.size(), s));
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_err, 4);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, 4, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -214,13 +213,14 @@ static cbspmv_status_t run_device(cbspmv_handle_t h, const double* x, double* y,
   a.tiles = h->d_tiles;
   a.rcols = h->d_rcols;
   a.units = h->d_units;
-  a.sched = h->d_sched;
+  a.blob = h->d_blob;
   a.worker_units = h->d_wunits;
   a.worker_off = h->d_woff;
   a.x = x;
   a.y = y;
   a.partial = h->d_partial;
-  a.split_count = h->d_split_count;
+  a.split_rows = h->d_split_rows;
+  a.n_split_rows = (uint32_t)p.split_rows.size();
   a.err = h->d_err;
   a.m = p.m;
   a.n = p.n;
@@ -357,10 +357,12 @@ bool noalloc_view(cbspmv_handle_t h, NoallocView* v) {
   a.tiles = h->d_tiles;
   a.rcols = h->d_rcols;
   a.units = h->d_units;
-  a.sched = h->d_sched;
+  a.blob = h->d_blob;
   a.worker_units = h->d_wunits;
   a.worker_off = h->d_woff;
   a.err = h->d_err;
+  a.split_rows = h->d_split_rows;
+  a.n_split_rows = (uint32_t)h->plan.split_rows.size();
   a.m = h->plan.m;
   a.n = h->plan.n;
   a.aggregated = h->plan.aggregated ? 1 : 0;

@@ -13,13 +13,14 @@ struct RunArgs {
   const CbTile* tiles;          // per-tile records, matrix order
   const int32_t* rcols;         // restore_cols (+ padding); unused when plain
   const CbUnit* units;
-  const uint32_t* sched;        // lane schedules of the units
+  const uint8_t* blob;          // unit blobs: tile records, restore_cols slice, lane schedule
   const uint32_t* worker_units; // unit ids per persistent CTA
   const uint32_t* worker_off;   // grid + 1 offsets into worker_units
   const double* x;
   double* y;
   double* partial;              // partial sums of split block rows (16 per slot)
-  uint32_t* split_count;        // arrival counters of split block rows (zero between launches)
+  const CbSplitRow* split_rows; // block rows cut into several units
+  uint32_t n_split_rows;
   uint32_t* err;                // device error word
   int64_t m, n;
   double alpha, beta;
@@ -30,6 +31,8 @@ struct RunArgs {
 
 size_t spmv_f64_smem_bytes();
 int spmv_f64_threads();
+// Launches the run kernel and, when the matrix has block rows cut into several units, the
+// kernel that adds their parts (two launches on `stream`).
 cudaError_t launch_spmv_f64(const RunArgs& a, int grid, cudaStream_t stream);
 
 }  // namespace cb

@@ -57,37 +57,59 @@ struct CbUnit {
   uint32_t slot;      // partial-sum slot of this part (16 values per slot)
   uint32_t sched16;   // offset of the unit's lane schedule in the schedule array / 16
   uint32_t sched_bytes;  // bytes of the schedule (multiple of 16)
+  uint32_t blob16;    // offset of the unit blob in the blob array / 16
+  uint32_t blob_bytes;   // 16 * ntiles + 4 * rc_n + sched_bytes
+  uint32_t pad;
+};
+
+// Unit blob: the unit's tile records, its restore_cols slice and its lane schedule, stored
+// back to back (each part a multiple of 16 bytes) so that the kernel stages all of the
+// unit's metadata with one bulk copy:
+//   [0, 16 * ntiles) tile records | [.., + 4 * rc_n) restore_cols | [.., + sched_bytes) schedule
+
+// A block row cut into several units: its parts store 16 partial row sums each in
+// consecutive slots slot0 .. slot0 + nparts - 1; a second kernel adds them in part order.
+struct CbSplitRow {
+  uint32_t slot0;
+  uint32_t brow;
+  uint16_t nparts;
+  uint16_t rows;      // rows of the block row inside the matrix (<= 16)
+  uint32_t pad;
 };
 
 // Lane schedule of a unit (built by the analyser, staged with the unit). The unit's
 // multiply-adds are taken in row-major order (row, then tile, then entry) and cut into
 // chunks of at most CB_CHUNK consecutive entries of one (tile, row) piece; the chunk list
-// is dealt to the 32 lanes in contiguous runs of (nearly) equal length. Layout:
-//   32 x uint16 lane header: bits [0,8) row of the lane's first chunk, bit 8 set when
-//     that row began in an earlier lane's run, bits [9,16) number of chunks of the lane;
+// is dealt to CB_VLANES runs of (nearly) equal length, one per lane. A lane sends the
+// even chunks of its run to one accumulator and the odd ones to another, so it keeps two
+// independent FP64 accumulation chains.
+// Layout:
+//   CB_VLANES x uint16 run header: bits [0,8) row of the run's first chunk, bit 8 set when
+//     that row began in an earlier run, bits [9,16) number of chunks of the run;
 //   R x uint8 next row: for each row of the unit, the next row holding entries;
 //   padding to a multiple of 16 bytes from the start;
-//   CB_SCHED_ROWS(u) x 32 x uint16 chunk descriptors, row-major by (step, lane):
+//   rows x CB_VLANES x uint16 chunk descriptors, row-major by (chunk index, run), rows =
+//   the longest run's chunk count rounded up to an even number:
 //     bits [0,5) tile in the unit, [5,13) first entry inside the tile record (entry order
 //     of the record: row-major; Dense: row * 16 + col), [13,15) length 1..CB_CHUNK (0 = no
 //     chunk), bit 15 set when the chunk ends its row.
 #define CB_CHUNK 3
 #define CB_VLANES 32
-#define CB_SCHED_HDR(R) ((64u + (uint32_t)(R) + 15u) & ~15u)
-#define CB_STEPS_MAX (CB_UNIT_WORK_MAX / CB_VLANES)
-#define CB_SCHED_MAX (CB_SCHED_HDR(CB_R_MAX) + 64 * CB_STEPS_MAX)
+#define CB_SCHED_HDR(R) ((2u * CB_VLANES + (uint32_t)(R) + 15u) & ~15u)
+#define CB_STEPS_MAX ((((CB_UNIT_WORK_MAX + CB_VLANES - 1) / CB_VLANES) + 1) & ~1)
+#define CB_SCHED_MAX (CB_SCHED_HDR(CB_R_MAX) + 2 * CB_VLANES * CB_STEPS_MAX)
 
 // Kernel geometry for the FP64 path (bytes of shared memory per stage and limits the
 // analyser must respect when it cuts units).
-#define CB_STAGES 8
-#define CB_CONSUMERS 6
-#define CB_B_MAX 14336          // stream bytes per unit
-#define CB_T_MAX 32             // tiles per unit (one bit each in a 32-bit mask)
+#define CB_STAGES 13
+#define CB_CONSUMERS 8
+#define CB_B_MAX 8192           // stream bytes per unit
+#define CB_T_MAX 20             // tiles per unit
 #define CB_NBR_MAX 8            // block rows per group unit
 #define CB_R_MAX (CB_NBR_MAX * CB_BLK)
 #define CB_RC_MAX (CB_T_MAX * 16 + 16)   // restore_cols entries per unit (incl. alignment)
 #define CB_RC_PAD 32            // zero entries appended to restore_cols
-#define CB_UNIT_WORK_DEFAULT 1536
-#define CB_UNIT_WORK_MAX 1536   // multiply-adds per unit (bounds the chunks per unit)
+#define CB_UNIT_WORK_DEFAULT 1024
+#define CB_UNIT_WORK_MAX 1024   // multiply-adds per unit (bounds the chunks per unit)
 
 #endif

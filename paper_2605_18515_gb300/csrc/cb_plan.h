@@ -29,6 +29,8 @@ struct Plan {
 
   std::vector<CbUnit> units;
   std::vector<uint32_t> sched;         // lane schedules of all units (see cb_layout.h)
+  std::vector<uint8_t> blob;           // unit blobs (see cb_layout.h)
+  std::vector<CbSplitRow> split_rows;  // block rows cut into several units
   std::vector<uint32_t> worker_units;  // unit ids grouped by worker (CTA)
   std::vector<uint32_t> worker_off;    // n_workers + 1
   int n_workers = 0;

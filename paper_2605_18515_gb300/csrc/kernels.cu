@@ -7,27 +7,26 @@
 // and lanes that are masked off cost the same), so this kernel keeps the data structure
 // and the per-tile decoding of the paper but reorganises the work:
 //
-//   * Persistent grid, one CTA per SM: warp 0 is the producer, warps 1..CB_CONSUMERS are
-//     consumers. One producer lane stages each unit of work (a run of consecutive tiles)
-//     into a ring of CB_STAGES shared-memory stages with bulk TMA copies (cp.async.bulk)
-//     of the unit's packed records, tile records and restore_cols slice; mbarriers hand
-//     stages between the producer and the consumers.
-//   * A consumer first gathers the unit's x values into the stage with cp.async (the x
-//     preload of Algorithms 3/4, through restore_cols for aggregated tiles) and computes
-//     each tile's base addresses from its record (CSR row pointer, COO coordinate bytes
-//     of Algorithm 3, the fixed rows of Algorithm 4).
+//   * Persistent grid, one CTA per SM: kLoaders loader warps and CB_CONSUMERS consumer
+//     warps. Loaders stage each unit of work (a run of consecutive tiles) into a ring of
+//     CB_STAGES shared-memory stages with two bulk TMA copies (cp.async.bulk): the unit's
+//     packed records and its blob (tile records, restore_cols slice, lane schedule). They
+//     then gather the unit's x values into the stage with cp.async (the x preload of
+//     Algorithms 3/4, through restore_cols for aggregated tiles); mbarriers hand stages to
+//     the consumers and back. A consumer computes each tile's base addresses from its
+//     record (CSR row pointer, COO coordinate bytes of Algorithm 3, the fixed rows of
+//     Algorithm 4).
 //   * The analyser's lane schedule cuts the unit's entries, in row-major order, into
 //     chunks of at most CB_CHUNK entries of one (tile, row) piece and deals them to the
 //     32 lanes in equal runs. Every lane then runs the same number of steps; a step reads
 //     one 16-bit chunk descriptor, decodes up to three coordinate bytes and issues up to
 //     three DFMAs into the lane's row accumulator. No FP64 work is spent on reductions:
 //     a row sum is stored when its last chunk is done.
-//   * Rows that cross lane boundaries are completed by the lane holding the row's end
-//     (adding its neighbours' carries in a fixed order); units that cover whole block rows
-//     write y directly (no atomics, y read once when beta != 0). Block rows cut into
-//     several units combine their parts through a partial-sum buffer: the last part to
-//     arrive (atomic counter) adds the parts in part order and writes y, so results do
-//     not depend on scheduling.
+//   * Rows that cross run boundaries are completed by the run holding the row's end
+//     (adding the earlier runs' carries in a fixed order); units that cover whole block
+//     rows write y directly (no atomics, y read once when beta != 0). Block rows cut into
+//     several units store 16 partial sums per part; a second small kernel adds the parts
+//     in part order and writes y, so results do not depend on scheduling.
 //   * Every wait is bounded (clock64 budget); on expiry the kernel records an error code,
 //     drains its own copies in flight and returns.
 #include <cuda_runtime.h>
@@ -41,31 +40,35 @@ namespace {
 
 constexpr int kStages = CB_STAGES;
 constexpr int kConsumers = CB_CONSUMERS;
-constexpr int kThreads = 32 * (1 + kConsumers);
+constexpr int kLoaders = 4;                       // warps 0..3: bulk copies and x gather
+constexpr int kProducers = kLoaders;
+constexpr int kThreads = 32 * (kProducers + kConsumers);
 constexpr long long kWaitBudget = 4000000000LL;   // clock64 cycles (~2 s) per wait
 
-// Stage layout (byte offsets): the unit's packed records, its tile records, its
-// restore_cols slice, the gathered x values (16 per tile) and its lane schedule.
-constexpr uint32_t kOffStream = 0;
-constexpr uint32_t kOffTiles = CB_B_MAX;
-constexpr uint32_t kOffRcols = kOffTiles + CB_T_MAX * 16;
-constexpr uint32_t kOffXs = kOffRcols + CB_RC_MAX * 4;
-constexpr uint32_t kOffSched = kOffXs + CB_T_MAX * 16 * 8;
-constexpr uint32_t kStageBytes = (kOffSched + CB_SCHED_MAX + 127) & ~127u;
-static_assert(kOffStream % 16 == 0 && kOffTiles % 16 == 0 && kOffRcols % 16 == 0 && kOffXs % 16 == 0 &&
-              kOffSched % 16 == 0, "bulk copy destinations must be 16-byte aligned");
+// Stage layout (byte offsets): the unit descriptor, the unit's packed records, its blob
+// (tile records, restore_cols slice, lane schedule) and the gathered x values (16 per tile).
+constexpr uint32_t kOffUnit = 0;
+constexpr uint32_t kOffStream = 64;
+constexpr uint32_t kOffBlob = kOffStream + CB_B_MAX;
+constexpr uint32_t kBlobMax = 16 * CB_T_MAX + 4 * CB_RC_MAX + CB_SCHED_MAX;
+constexpr uint32_t kOffXs = kOffBlob + kBlobMax;
+constexpr uint32_t kStageBytes = (kOffXs + CB_T_MAX * 16 * 8 + 127) & ~127u;
+static_assert(sizeof(CbUnit) == 64, "unit descriptor slot");
+static_assert(kOffStream % 16 == 0 && kOffBlob % 16 == 0 && kOffXs % 16 == 0 && kBlobMax % 16 == 0,
+              "bulk copy destinations must be 16-byte aligned");
 
 struct Scratch {
   uint4 tinfo[CB_T_MAX];        // per tile: value base, coordinate base, x-row base (smem offsets)
   double srow[CB_R_MAX];        // row sums
-  double cval[32];              // per-lane carry value
-  int32_t crow[32];             // per-lane carry row (-1 none, -2 no chunks)
+  double cval[CB_VLANES];       // per-run carry value
+  int32_t crow[CB_VLANES];      // per-run carry row (-1 none, -2 no chunks)
 };
 
 struct Shared {
   __align__(128) uint8_t stage[kStages][kStageBytes];
-  uint64_t bar_tma[kStages];
-  uint64_t bar_empty[kStages];
+  uint64_t bar_tma[kStages];    // bulk copies of the unit landed
+  uint64_t bar_full[kStages];   // x gathered (the 32 lanes of a gatherer)
+  uint64_t bar_empty[kStages];  // the consumer is done with the stage
   Scratch scratch[kConsumers];
   uint8_t ident[256];           // byte k = (k & 15) << 4: coordinate bytes of a Dense record
   uint32_t ticket;
@@ -116,65 +119,123 @@ __device__ __forceinline__ void cp_async_8(uint32_t dst_smem, const void* src, u
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst_smem), "l"(src), "r"(src_bytes)
                : "memory");
 }
+__device__ __forceinline__ void cp_async_arrive_noinc(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t align16u(uint32_t v) { return (v + 15u) & ~15u; }
 
 __device__ void set_error(const RunArgs& a, uint32_t code) { atomicOr(a.err, code); }
 
-// ---- producer: one lane issues the bulk copies of every unit, in ticket order ------------
-__device__ void producer(const RunArgs& a, Shared& sh, const uint32_t* list, uint32_t nu) {
-  uint32_t issued = 0;
-  bool ok = true;
-  for (uint32_t j = 0; j < nu; ++j) {
-    const uint32_t s = j % kStages, q = j / kStages;
-    if (q > 0 && !mbar_wait(&sh.bar_empty[s], (q - 1) & 1)) { ok = false; break; }
-    const CbUnit u = a.units[list[j]];
-    uint8_t* S = sh.stage[s];
-    mbar_arrive_expect_tx(&sh.bar_tma[s], u.nbytes + 16u * u.ntiles + 4u * u.rc_n + u.sched_bytes);
+// ---- loader warps ------------------------------------------------------------------------
+// Loader l (l = 0 .. kLoaders-1) owns tickets l, l + kLoaders, ...: for each it stores the
+// unit descriptor in the stage and issues two bulk copies (packed records, unit blob) one
+// ticket ahead, then gathers the current ticket's x values with cp.async (all 16 per tile;
+// columns through restore_cols when aggregated) and signals the consumer through the
+// stage's full barrier. Bulk copies issued by one thread complete one after another, so
+// the copies are spread over several loader warps.
+__device__ __forceinline__ uint32_t load_desc_word(const CbUnit* units, uint32_t k, uint32_t nu, int lane) {
+  return (k < nu && lane < 16) ? __ldg(reinterpret_cast<const uint32_t*>(units + k) + lane) : 0u;
+}
+
+__device__ bool loader_issue(const RunArgs& a, Shared& sh, uint32_t k, uint32_t dw, int lane) {
+  const uint32_t s = k % kStages, q = k / kStages;
+  if (q > 0 && !mbar_wait(&sh.bar_empty[s], (q - 1) & 1)) return false;
+  uint8_t* S = sh.stage[s];
+  if (lane < 16) reinterpret_cast<uint32_t*>(S + kOffUnit)[lane] = dw;
+  __syncwarp();
+  if (lane == 0) {
+    const CbUnit& u = *reinterpret_cast<const CbUnit*>(S + kOffUnit);
+    mbar_arrive_expect_tx(&sh.bar_tma[s], u.nbytes + u.blob_bytes);
     if (u.nbytes) bulk_g2s(S + kOffStream, a.stream + (size_t)u.byte_lo16 * 16, u.nbytes, &sh.bar_tma[s]);
-    if (u.ntiles) bulk_g2s(S + kOffTiles, a.tiles + u.tile_lo, 16u * u.ntiles, &sh.bar_tma[s]);
-    if (u.rc_n) bulk_g2s(S + kOffRcols, a.rcols + u.rc_lo, 4u * u.rc_n, &sh.bar_tma[s]);
-    if (u.sched_bytes) bulk_g2s(S + kOffSched, a.sched + (size_t)u.sched16 * 4, u.sched_bytes, &sh.bar_tma[s]);
-    issued = j + 1;
+    if (u.blob_bytes) bulk_g2s(S + kOffBlob, a.blob + (size_t)u.blob16 * 16, u.blob_bytes, &sh.bar_tma[s]);
+  }
+  __syncwarp();
+  return true;
+}
+
+__device__ void loader(const RunArgs& a, Shared& sh, const CbUnit* units, uint32_t nu, uint32_t l, int lane) {
+  constexpr int kPerLane = CB_T_MAX * 16 / 32;
+  bool ok = true;
+  uint32_t next = l;                                      // next own ticket to issue
+  uint32_t dw = load_desc_word(units, next, nu, lane);    // its descriptor (16 lanes, one word each)
+  if (next < nu) {
+    ok = loader_issue(a, sh, next, dw, lane);
+    next += kLoaders;
+    dw = load_desc_word(units, next, nu, lane);
+  }
+  for (uint32_t j = l; j < nu && ok; j += kLoaders) {
+    const uint32_t s = j % kStages, q = j / kStages;
+    if (!mbar_wait(&sh.bar_tma[s], q & 1) || *(volatile uint32_t*)&sh.abort_flag) { ok = false; break; }
+    const uint8_t* S = sh.stage[s];
+    const CbUnit& u = *reinterpret_cast<const CbUnit*>(S + kOffUnit);
+    const CbTile* tiles = reinterpret_cast<const CbTile*>(S + kOffBlob);
+    const int32_t* rcols = reinterpret_cast<const int32_t*>(S + kOffBlob + 16u * u.ntiles);
+    const uint32_t xs_smem = smem_u32(S + kOffXs);
+    const uint32_t nx = 16u * u.ntiles, rc_lo = u.rc_lo;
+    int64_t col[kPerLane];
+#pragma unroll
+    for (int k = 0; k < kPerLane; ++k) {
+      const uint32_t idx = (uint32_t)lane + 32u * k;
+      col[k] = -1;
+      if (idx < nx) {
+        const uint32_t xb = tiles[idx >> 4].xbase;
+        col[k] = a.aggregated ? (int64_t)rcols[xb - rc_lo + (idx & 15u)] : (int64_t)xb + (idx & 15u);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kPerLane; ++k) {
+      const uint32_t idx = (uint32_t)lane + 32u * k;
+      if (idx < nx) {
+        const bool valid = col[k] >= 0 && col[k] < a.n;
+        cp_async_8(xs_smem + 8u * idx, a.x + (valid ? col[k] : 0), valid ? 8u : 0u);
+      }
+    }
+    cp_async_arrive_noinc(&sh.bar_full[s]);
+    if (next < nu) {            // then keep one own ticket in flight ahead of the consumers
+      ok = loader_issue(a, sh, next, dw, lane);
+      next += kLoaders;
+      dw = load_desc_word(units, next, nu, lane);
+    }
   }
   if (!ok) {
-    set_error(a, 1u);
+    if (lane == 0) set_error(a, 1u);
     *(volatile uint32_t*)&sh.abort_flag = 1;
-    // drain: the copies of the last kStages tickets may still be in flight
-    for (uint32_t j = issued > (uint32_t)kStages ? issued - kStages : 0; j < issued; ++j)
-      mbar_wait(&sh.bar_tma[j % kStages], (j / kStages) & 1);
+    // drain: copies of this loader's tickets issued but not waited for
+    for (uint32_t k = l; k < next && k < nu; k += kLoaders)
+      if (k + kStages >= next) mbar_wait(&sh.bar_tma[k % kStages], (k / kStages) & 1);
   }
+  cp_async_wait_all();
 }
 
 // ---- consumer -----------------------------------------------------------------------------
+// acc + v * x when p holds, acc otherwise (a predicated FP64 FMA, no branch).
+__device__ __forceinline__ double pfma(bool p, double v, double x, double acc) {
+  asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\t@q fma.rn.f64 %0, %1, %2, %0;\n\t}"
+      : "+d"(acc)
+      : "d"(v), "d"(x), "r"((uint32_t)p));
+  return acc;
+}
+#define CB_LDD(off) (*reinterpret_cast<const double*>(sm + (off)))
+
 // sm: base of the CTA's shared memory; so: offset of the unit's stage in it.
-__device__ void consume_unit(const RunArgs& a, const CbUnit& u, uint8_t* sm, uint32_t so, uint32_t ident_off,
-                             Scratch& sc, int lane) {
+__device__ void consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_t ident_off, Scratch& sc,
+                             int lane) {
   uint8_t* S = sm + so;
+  const CbUnit& u = *reinterpret_cast<const CbUnit*>(S + kOffUnit);
   const uint32_t T = u.ntiles;
   const uint32_t byte_lo = u.byte_lo16 * 16u;
   const int64_t row0 = (int64_t)u.brow_lo * CB_BLK;
   const int64_t rows_left = a.m - row0;
   const int64_t rows_unit = (int64_t)CB_BLK * u.nbr;
   const uint32_t R = (uint32_t)(rows_unit < rows_left ? rows_unit : rows_left);
-  const CbTile* tiles = reinterpret_cast<const CbTile*>(S + kOffTiles);
-  const int32_t* rcols = reinterpret_cast<const int32_t*>(S + kOffRcols);
-  const uint32_t xs_smem = smem_u32(S + kOffXs);
+  const CbTile* tiles = reinterpret_cast<const CbTile*>(S + kOffBlob);
 
-  // 0. gather the unit's x values into the stage (asynchronous; waited for before the walk)
-  const uint32_t nx = 16u * T;
-  for (uint32_t idx = lane; idx < nx; idx += 32) {
-    const uint32_t t = idx >> 4, c = idx & 15u;
-    const uint32_t xb = tiles[t].xbase;
-    const int64_t col = a.aggregated ? (int64_t)rcols[xb - u.rc_lo + c] : (int64_t)xb + c;
-    const bool valid = col >= 0 && col < a.n;
-    cp_async_8(xs_smem + 8u * idx, a.x + (valid ? col : 0), valid ? 8u : 0u);
-  }
   // 1. per-tile bases (lane = tile) and zeroed row sums
   if ((uint32_t)lane < T) {
     const CbTile rec = tiles[lane];
-    const uint32_t soff = so + rec.vp16 * 16u - byte_lo;
+    const uint32_t soff = so + kOffStream + rec.vp16 * 16u - byte_lo;
     uint32_t vb, cb;
     if (rec.fmt == CB_FMT_CSR) {
       vb = soff + align16u(17u + rec.nnz);
@@ -189,50 +250,96 @@ __device__ void consume_unit(const RunArgs& a, const CbUnit& u, uint8_t* sm, uin
     sc.tinfo[lane] = make_uint4(vb, cb, so + kOffXs + 128u * lane, 0u);
   }
   for (uint32_t r = lane; r < R; r += 32) sc.srow[r] = 0.0;
-  cp_async_wait_all();
-  __syncwarp();   // x values and tile bases are visible to every lane
+  __syncwarp();
 
-  // 2. the lane's chunks: up to CB_CHUNK entries of one (tile, row) piece per step
-  const uint8_t* sched = S + kOffSched;
+  // 2. one run per lane: a sequence of chunks of up to three entries; even chunks go to
+  //    accumulator a0, odd chunks to a1 (two independent FP64 chains)
+  const uint8_t* sched = S + kOffBlob + 16u * T + 4u * u.rc_n;
+  const uint16_t* hdr = reinterpret_cast<const uint16_t*>(sched);
+  const uint8_t* nxt = sched + 2 * CB_VLANES;
   const uint16_t* desc = reinterpret_cast<const uint16_t*>(sched + CB_SCHED_HDR(R));
-  const uint32_t h = reinterpret_cast<const uint16_t*>(sched)[lane];
+  const uint32_t h = hdr[lane];
+  const uint32_t nch = h >> 9;
+  const uint32_t nmax = __reduce_max_sync(0xffffffffu, nch);
+  const uint32_t steps = (nmax + 1) / 2;
   uint32_t row = h & 0xffu;
   const bool hs = (h >> 8) & 1u;
-  const uint32_t nch = h >> 9;
-  const uint32_t steps = __reduce_max_sync(0xffffffffu, nch);
-  double acc = 0.0;
   bool first = true, open = false;
   int32_t own_row = -1;
   double own_val = 0.0;
-  for (uint32_t i = 0; i < steps; ++i) {
-    const uint32_t d = desc[i * 32u + lane];
-    if (d) {
-      const uint32_t t = d & 31u, o = (d >> 5) & 255u, len = (d >> 13) & 3u;
-      const uint4 ti = sc.tinfo[t];
-      const uint32_t va = ti.x + 8u * o, ca = ti.y + o, xr = ti.z;
-      const uint32_t b0 = sm[ca];
-      const double v0 = *reinterpret_cast<const double*>(sm + va);
-      uint32_t b1 = 0, b2 = 0;
-      double v1 = 0.0, v2 = 0.0;
-      if (len > 1) { b1 = sm[ca + 1]; v1 = *reinterpret_cast<const double*>(sm + va + 8u); }
-      if (len > 2) { b2 = sm[ca + 2]; v2 = *reinterpret_cast<const double*>(sm + va + 16u); }
-      const double x0 = *reinterpret_cast<const double*>(sm + xr + ((b0 >> 4) << 3));
-      acc = fma(v0, x0, acc);
-      if (len > 1) acc = fma(v1, *reinterpret_cast<const double*>(sm + xr + ((b1 >> 4) << 3)), acc);
-      if (len > 2) acc = fma(v2, *reinterpret_cast<const double*>(sm + xr + ((b2 >> 4) << 3)), acc);
-      open = true;
-      if (d & 0x8000u) {   // the chunk ends its row
-        if (first && hs) { own_row = (int32_t)row; own_val = acc; }
-        else sc.srow[row] = acc;
-        acc = 0.0;
-        first = false;
-        open = false;
-        row = sched[64u + row];
-      }
-    }
+  double a0 = 0.0, a1 = 0.0;
+  // Software pipeline: the operands of step i + 1 are loaded before the DFMAs of step i.
+  // Loads are unconditional (a chunk shorter than three entries reads at most two entries
+  // past its piece and column nibbles stay inside the tile's x row, so every address stays
+  // in shared memory); the DFMA slots beyond the chunk's length are predicated off.
+  uint32_t dA = 0, dB = 0;
+  double vA0 = 0, vA1 = 0, vA2 = 0, xA0 = 0, xA1 = 0, xA2 = 0;
+  double vB0 = 0, vB1 = 0, vB2 = 0, xB0 = 0, xB1 = 0, xB2 = 0;
+#define CB_LOAD_CHUNK(d, v0, v1, v2, x0, x1, x2)                                   \
+  {                                                                                \
+    const uint4 ti_ = sc.tinfo[(d) & 31u];                                         \
+    const uint32_t o_ = ((d) >> 5) & 255u;                                         \
+    const uint32_t va_ = ti_.x + 8u * o_, ca_ = ti_.y + o_, xr_ = ti_.z;           \
+    const uint32_t b0_ = sm[ca_], b1_ = sm[ca_ + 1], b2_ = sm[ca_ + 2];            \
+    v0 = CB_LDD(va_);                                                              \
+    v1 = CB_LDD(va_ + 8u);                                                         \
+    v2 = CB_LDD(va_ + 16u);                                                        \
+    x0 = CB_LDD(xr_ + ((b0_ >> 1) & 0x78u));                                       \
+    x1 = CB_LDD(xr_ + ((b1_ >> 1) & 0x78u));                                       \
+    x2 = CB_LDD(xr_ + ((b2_ >> 1) & 0x78u));                                       \
   }
+  if (steps) {
+    dA = desc[lane];
+    dB = desc[CB_VLANES + lane];
+    CB_LOAD_CHUNK(dA, vA0, vA1, vA2, xA0, xA1, xA2);
+    CB_LOAD_CHUNK(dB, vB0, vB1, vB2, xB0, xB1, xB2);
+  }
+  for (uint32_t i = 0; i < steps; ++i) {
+    const uint32_t nb = (i + 1 < steps ? 2u * (i + 1) : 2u * i) * CB_VLANES;
+    const uint32_t dA_n = desc[nb + lane], dB_n = desc[nb + CB_VLANES + lane];
+    double nvA0, nvA1, nvA2, nxA0, nxA1, nxA2, nvB0, nvB1, nvB2, nxB0, nxB1, nxB2;
+    CB_LOAD_CHUNK(dA_n, nvA0, nvA1, nvA2, nxA0, nxA1, nxA2);
+    CB_LOAD_CHUNK(dB_n, nvB0, nvB1, nvB2, nxB0, nxB1, nxB2);
+    const uint32_t lA = (dA >> 13) & 3u, lB = (dB >> 13) & 3u;
+    const bool eA = (dA & 0x8000u) != 0, eB = (dB & 0x8000u) != 0;
+    // chunk B starts a new row when chunk A ends one: its chain then starts from zero
+    const double a1_old = a1;
+    double b = eA ? 0.0 : a1;
+    a0 = pfma(lA > 0, vA0, xA0, a0);
+    b = pfma(lB > 0, vB0, xB0, b);
+    a0 = pfma(lA > 1, vA1, xA1, a0);
+    b = pfma(lB > 1, vB1, xB1, b);
+    a0 = pfma(lA > 2, vA2, xA2, a0);
+    b = pfma(lB > 2, vB2, xB2, b);
+    a1 = b;
+    if (lA | lB) open = true;
+    if (eA) {                              // chunk A ends its row: a0 + (a1 before chunk B)
+      const double sum = a0 + a1_old;
+      if (first && hs) { own_row = (int32_t)row; own_val = sum; }
+      else sc.srow[row] = sum;
+      first = false;
+      a0 = 0.0;
+      open = lB != 0;
+      row = nxt[row];
+    }
+    if (eB) {                              // chunk B ends its row
+      const double sum = a0 + a1;
+      if (first && hs) { own_row = (int32_t)row; own_val = sum; }
+      else sc.srow[row] = sum;
+      first = false;
+      a0 = 0.0;
+      a1 = 0.0;
+      open = false;
+      row = nxt[row];
+    }
+    dA = dA_n;
+    dB = dB_n;
+    vA0 = nvA0; vA1 = nvA1; vA2 = nvA2; xA0 = nxA0; xA1 = nxA1; xA2 = nxA2;
+    vB0 = nvB0; vB1 = nvB1; vB2 = nvB2; xB0 = nxB0; xB1 = nxB1; xB2 = nxB2;
+  }
+#undef CB_LOAD_CHUNK
   sc.crow[lane] = nch == 0 ? -2 : (open ? (int32_t)row : -1);
-  sc.cval[lane] = acc;
+  sc.cval[lane] = open ? a0 + a1 : 0.0;
   __syncwarp();
   if (own_row >= 0) {
     double sum = own_val;
@@ -257,26 +364,8 @@ __device__ void consume_unit(const RunArgs& a, const CbUnit& u, uint8_t* sm, uin
       a.y[gr] = v;
     }
   } else {
-    double* part = a.partial + (size_t)u.slot * 16;
-    if (lane < 16) part[lane] = (uint32_t)lane < R ? sc.srow[lane] : 0.0;
-    __threadfence();
-    __syncwarp();
-    uint32_t last = 0;
-    if (lane == 0) last = atomicAdd(&a.split_count[u.split], 1u) == (uint32_t)u.nparts - 1u;
-    last = __shfl_sync(0xffffffffu, last, 0);
-    if (last) {
-      __threadfence();
-      if ((uint32_t)lane < R && lane < 16) {
-        const double* base = a.partial + (size_t)(u.slot - u.part) * 16;
-        double sum = 0.0;
-        for (uint32_t p = 0; p < u.nparts; ++p) sum += __ldcg(base + p * 16 + lane);
-        const int64_t gr = row0 + lane;
-        double v = a.alpha_one ? sum : alpha * sum;
-        if (a.beta_nonzero) v = fma(beta, a.y[gr], v);
-        a.y[gr] = v;
-      }
-      if (lane == 0) a.split_count[u.split] = 0;   // ready for the next launch
-    }
+    // part of a block row cut into several units: 16 partial sums, added by combine_kernel
+    if (lane < 16) a.partial[(size_t)u.slot * 16 + lane] = (uint32_t)lane < R ? sc.srow[lane] : 0.0;
   }
 }
 
@@ -285,11 +374,12 @@ __global__ void __launch_bounds__(kThreads, 1) spmv_f64_kernel(const RunArgs a) 
   Shared& sh = *reinterpret_cast<Shared*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t w0 = a.worker_off[blockIdx.x], w1 = a.worker_off[blockIdx.x + 1];
-  const uint32_t* list = a.worker_units + w0;
+  const CbUnit* units = a.units + w0;   // this CTA's units, stored contiguously
   const uint32_t nu = w1 - w0;
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&sh.bar_tma[s], 1);
+      mbar_init(&sh.bar_full[s], 32);
       mbar_init(&sh.bar_empty[s], 1);
     }
     sh.ticket = 0;
@@ -298,27 +388,44 @@ __global__ void __launch_bounds__(kThreads, 1) spmv_f64_kernel(const RunArgs a) 
   }
   for (uint32_t i = threadIdx.x; i < 256u; i += blockDim.x) sh.ident[i] = (uint8_t)((i & 15u) << 4);
   __syncthreads();
-  if (warp == 0) {
-    if (lane == 0) producer(a, sh, list, nu);
+  if (warp < kLoaders) {
+    loader(a, sh, units, nu, (uint32_t)warp, lane);
     return;
   }
-  Scratch& sc = sh.scratch[warp - 1];
+  Scratch& sc = sh.scratch[warp - kProducers];
+  const uint32_t ident_off = (uint32_t)(sh.ident - smem_raw);
   for (;;) {
     uint32_t j = 0;
     if (lane == 0) j = atomicAdd(&sh.ticket, 1u);
     j = __shfl_sync(0xffffffffu, j, 0);
     if (j >= nu) break;
     const uint32_t s = j % kStages, q = j / kStages;
-    const bool ok = mbar_wait(&sh.bar_tma[s], q & 1);
+    bool ok = mbar_wait(&sh.bar_full[s], q & 1);
+    ok = ok && mbar_wait(&sh.bar_tma[s], q & 1);
     if (!__all_sync(0xffffffffu, ok) || *(volatile uint32_t*)&sh.abort_flag) {
       if (lane == 0) set_error(a, 2u);
       break;
     }
-    const CbUnit u = a.units[list[j]];
-    consume_unit(a, u, smem_raw, (uint32_t)(sh.stage[s] - smem_raw), (uint32_t)(sh.ident - smem_raw), sc, lane);
+    consume_unit(a, smem_raw, (uint32_t)(sh.stage[s] - smem_raw), ident_off, sc, lane);
     __syncwarp();
     if (lane == 0) mbar_arrive(&sh.bar_empty[s]);
   }
+}
+
+// Adds the parts of every block row cut into several units, in part order, and writes y.
+__global__ void __launch_bounds__(256) combine_kernel(const RunArgs a) {
+  const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t sr = g >> 4, r = g & 15u;
+  if (sr >= a.n_split_rows) return;
+  const CbSplitRow s = a.split_rows[sr];
+  if (r >= s.rows) return;
+  const double* p = a.partial + (size_t)s.slot0 * 16 + r;
+  double sum = 0.0;
+  for (uint32_t k = 0; k < s.nparts; ++k) sum += p[(size_t)k * 16];
+  const int64_t gr = (int64_t)s.brow * CB_BLK + r;
+  double v = a.alpha_one ? sum : a.alpha * sum;
+  if (a.beta_nonzero) v = fma(a.beta, a.y[gr], v);
+  a.y[gr] = v;
 }
 
 }  // namespace
@@ -338,6 +445,10 @@ cudaError_t launch_spmv_f64(const RunArgs& a, int grid, cudaStream_t stream) {
     if (dev >= 0 && dev < 64) configured[dev] = true;
   }
   spmv_f64_kernel<<<grid, kThreads, smem, stream>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || a.n_split_rows == 0) return e;
+  const uint32_t threads = 16u * a.n_split_rows;
+  combine_kernel<<<(threads + 255) / 256, 256, 0, stream>>>(a);
   return cudaGetLastError();
 }
 

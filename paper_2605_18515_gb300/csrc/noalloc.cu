@@ -1,8 +1,8 @@
 // cbspmv_run_noalloc: the product of cbspmv_run with no allocation of any kind.
 //
-// The run kernel needs scratch memory for block rows that the analysis cut into several
-// units: 16 partial sums per unit part and one arrival counter per cut block row.
-// cbspmv_run takes that scratch from buffers the handle allocated. This entry point takes
+// The run needs scratch memory for block rows that the analysis cut into several units:
+// 16 partial sums per unit part, which a second kernel adds in part order.
+// cbspmv_run takes that scratch from a buffer the handle allocated. This entry point takes
 // it from one fixed array that lives in the library's device image instead, so the call
 // itself never allocates: it is for callers that may not call cudaMalloc, cudaFree or
 // any allocating routine when they run the product (code whose device memory is owned
@@ -24,10 +24,8 @@
 
 namespace {
 
-constexpr size_t kNoallocMaxSplitRows = 65536;   // arrival counters (4 B each)
-constexpr size_t kNoallocMaxSlots = 61440;       // partial-sum slots (16 doubles each)
-constexpr size_t kCountersBytes = kNoallocMaxSplitRows * sizeof(uint32_t);       // 256 KiB
-constexpr size_t kNoallocBytes = kCountersBytes + kNoallocMaxSlots * 16 * sizeof(double);  // 7.75 MiB
+constexpr size_t kNoallocMaxSlots = 63488;       // partial-sum slots (16 doubles each)
+constexpr size_t kNoallocBytes = kNoallocMaxSlots * 16 * sizeof(double);   // 7.75 MiB
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
@@ -49,12 +47,11 @@ extern "C" cbspmv_status_t cbspmv_run_noalloc(cbspmv_handle_t h, const void* x, 
     return CBSPMV_ERR_INVALID;
   }
   const cb::Plan& p = *v.plan;
-  if ((size_t)p.n_slots > kNoallocMaxSlots || (size_t)p.n_split_rows > kNoallocMaxSplitRows) {
+  if ((size_t)p.n_slots > kNoallocMaxSlots) {
     char buf[256];
     snprintf(buf, sizeof(buf),
-             "cbspmv_run_noalloc: matrix needs %d partial-sum slots and %d split-row counters; the static "
-             "scratch holds at most %zu and %zu",
-             p.n_slots, p.n_split_rows, kNoallocMaxSlots, kNoallocMaxSplitRows);
+             "cbspmv_run_noalloc: matrix needs %d partial-sum slots; the static scratch holds at most %zu",
+             p.n_slots, kNoallocMaxSlots);
     cb::set_last_error(buf);
     return CBSPMV_ERR_INVALID;
   }
@@ -88,23 +85,17 @@ extern "C" cbspmv_status_t cbspmv_run_noalloc(cbspmv_handle_t h, const void* x, 
     cb::set_last_error(std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
     st = CBSPMV_ERR_CUDA;
   } else if (p.m > 0) {
-    cudaStream_t s = (cudaStream_t)stream;
-    uint32_t* counters = (uint32_t*)base;
-    double* partial = (double*)((unsigned char*)base + kCountersBytes);
-    // the array keeps the previous call's contents: counters must start at zero
-    e = cudaMemsetAsync(counters, 0, (size_t)(p.n_split_rows ? p.n_split_rows : 1) * sizeof(uint32_t), s);
-    if (e == cudaSuccess) {
-      cb::RunArgs a = v.args;
-      a.x = (const double*)x;
-      a.y = (double*)y;
-      a.partial = partial;
-      a.split_count = counters;
-      a.alpha = alpha;
-      a.beta = beta;
-      a.alpha_one = alpha == 1.0;
-      a.beta_nonzero = beta != 0.0;
-      e = cb::launch_spmv_f64(a, v.grid, s);
-    }
+    // Every slot a run reads was written earlier in the same run, so the array's previous
+    // contents never matter and nothing needs clearing.
+    cb::RunArgs a = v.args;
+    a.x = (const double*)x;
+    a.y = (double*)y;
+    a.partial = (double*)base;
+    a.alpha = alpha;
+    a.beta = beta;
+    a.alpha_one = alpha == 1.0;
+    a.beta_nonzero = beta != 0.0;
+    e = cb::launch_spmv_f64(a, v.grid, (cudaStream_t)stream);
     if (e != cudaSuccess) {
       cb::set_last_error(std::string("cbspmv_run_noalloc: ") + cudaGetErrorString(e));
       st = CBSPMV_ERR_CUDA;
