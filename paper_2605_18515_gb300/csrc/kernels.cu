@@ -67,8 +67,13 @@ struct Scratch {
 struct Shared {
   __align__(128) uint8_t stage[kStages][kStageBytes];
   uint64_t bar_tma[kStages];    // bulk copies of the unit landed
-  uint64_t bar_full[kStages];   // x gathered (the 32 lanes of a gatherer)
-  uint64_t bar_empty[kStages];  // the consumer is done with the stage
+  uint64_t bar_full[kStages];   // x gathered (the 32 lanes of a loader)
+  // Exact hand-off words: the ticket whose copies were issued into the stage and the last
+  // ticket released from it. Loaders issue their tickets out of order, so a stage's
+  // barriers can be more than one phase behind a waiter; a waiter therefore first waits
+  // for the exact ticket here, after which the parity waits are unambiguous.
+  uint32_t issued[kStages];
+  uint32_t released[kStages];
   Scratch scratch[kConsumers];
   uint8_t ident[256];           // byte k = (k & 15) << 4: coordinate bytes of a Dense record
   uint32_t ticket;
@@ -99,6 +104,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "r"(smem_u32(bar)), "r"(parity)
       : "memory");
   return ok != 0;
+}
+// Bounded wait until *p == v: false when the budget ran out.
+__device__ __forceinline__ bool wait_value(const uint32_t* p, uint32_t v) {
+  const volatile uint32_t* vp = p;
+  if (*vp == v) return true;
+  long long t0 = clock64();
+  while (*vp != v) {
+    __nanosleep(32);
+    if (clock64() - t0 > kWaitBudget) return false;
+  }
+  return true;
 }
 // Bounded wait: false when the budget ran out.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
@@ -140,12 +156,15 @@ __device__ __forceinline__ uint32_t load_desc_word(const CbUnit* units, uint32_t
 }
 
 __device__ bool loader_issue(const RunArgs& a, Shared& sh, uint32_t k, uint32_t dw, int lane) {
-  const uint32_t s = k % kStages, q = k / kStages;
-  if (q > 0 && !mbar_wait(&sh.bar_empty[s], (q - 1) & 1)) return false;
+  const uint32_t s = k % kStages;
+  // the stage's previous ticket (k - kStages) must have been released by its consumer
+  if (k >= (uint32_t)kStages && !wait_value(&sh.released[s], k - kStages)) return false;
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   uint8_t* S = sh.stage[s];
   if (lane < 16) reinterpret_cast<uint32_t*>(S + kOffUnit)[lane] = dw;
   __syncwarp();
   if (lane == 0) {
+    *(volatile uint32_t*)&sh.issued[s] = k;
     const CbUnit& u = *reinterpret_cast<const CbUnit*>(S + kOffUnit);
     mbar_arrive_expect_tx(&sh.bar_tma[s], u.nbytes + u.blob_bytes);
     if (u.nbytes) bulk_g2s(S + kOffStream, a.stream + (size_t)u.byte_lo16 * 16, u.nbytes, &sh.bar_tma[s]);
@@ -380,7 +399,8 @@ __global__ void __launch_bounds__(kThreads, 1) spmv_f64_kernel(const RunArgs a) 
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&sh.bar_tma[s], 1);
       mbar_init(&sh.bar_full[s], 32);
-      mbar_init(&sh.bar_empty[s], 1);
+      sh.issued[s] = 0xffffffffu;
+      sh.released[s] = 0xffffffffu;
     }
     sh.ticket = 0;
     sh.abort_flag = 0;
@@ -400,7 +420,8 @@ __global__ void __launch_bounds__(kThreads, 1) spmv_f64_kernel(const RunArgs a) 
     j = __shfl_sync(0xffffffffu, j, 0);
     if (j >= nu) break;
     const uint32_t s = j % kStages, q = j / kStages;
-    bool ok = mbar_wait(&sh.bar_full[s], q & 1);
+    bool ok = wait_value(&sh.issued[s], j);    // the stage now holds ticket j's copies
+    ok = ok && mbar_wait(&sh.bar_full[s], q & 1);
     ok = ok && mbar_wait(&sh.bar_tma[s], q & 1);
     if (!__all_sync(0xffffffffu, ok) || *(volatile uint32_t*)&sh.abort_flag) {
       if (lane == 0) set_error(a, 2u);
@@ -408,7 +429,10 @@ __global__ void __launch_bounds__(kThreads, 1) spmv_f64_kernel(const RunArgs a) 
     }
     consume_unit(a, smem_raw, (uint32_t)(sh.stage[s] - smem_raw), ident_off, sc, lane);
     __syncwarp();
-    if (lane == 0) mbar_arrive(&sh.bar_empty[s]);
+    if (lane == 0) {
+      __threadfence_block();
+      *(volatile uint32_t*)&sh.released[s] = j;
+    }
   }
 }
 
