@@ -39,7 +39,15 @@ WORKLOADS = {
                 "U[-1,1] values, seed 2",
     "laplace2d_64": "FP64 2D 5-point Laplacian on a 64x64 grid, x U[-1,1], seed 0",
 }
-FP64_NOMINAL_GFLOPS = 1250.0     # GB300 FP64 rate from the nominal spec table
+# FP64 FMA issue rate of a GB300 SM: each of the 4 SM sub-partitions completes one warp-wide
+# (32-lane) DFMA every 64 cycles, i.e. 2 FP64 FMA lanes per SM per cycle (measured with a
+# dependent/independent DFMA chain probe; it matches the nominal 1.25 TFLOP/s FP64).
+FP64_FMA_LANES_PER_SM_CYCLE = 2.0
+L2_BYTES = 129 * 2 ** 20
+
+
+def fp64_peak_gflops(sms: int, sm_max_mhz: float) -> float:
+    return sms * FP64_FMA_LANES_PER_SM_CYCLE * 2.0 * sm_max_mhz / 1e3
 
 
 def load_peaks():
@@ -126,6 +134,47 @@ def oracle_sample_gflops(A, x, target_s: float = 12.0):
     return gf, f"{reps} full products of the {A.m}x{A.n} matrix ({A.nnz} nonzeros), {t_total:.1f} s"
 
 
+def step_distribution(run, stream, n: int, flush_buf=None):
+    """Device time of n single steps, each between its own pair of events on the run's
+    stream; with flush_buf, a buffer larger than L2 is overwritten before every step."""
+    import torch
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+    for i in range(n):
+        if flush_buf is not None:
+            flush_buf.fill_(float(i))
+        evs[i][0].record(stream)
+        run()
+        evs[i][1].record(stream)
+    stream.synchronize()
+    t = sorted(a.elapsed_time(b) for a, b in evs)
+    return {"mean_ms": round(sum(t) / n, 5), "median_ms": round(t[n // 2], 5), "min_ms": round(t[0], 5),
+            "n": n}
+
+
+def cusparse_reference(A, x, stream, steps: int):
+    """cuSPARSE CSR SpMV (FP64) through torch.sparse_csr_tensor on the same matrix and x:
+    a library reference point, not part of this library's path."""
+    import torch
+    with torch.cuda.stream(stream):
+        Acsr = torch.sparse_csr_tensor(torch.from_numpy(A.row_ptr.astype(np.int32)).cuda(),
+                                       torch.from_numpy(A.col.astype(np.int32)).cuda(),
+                                       torch.from_numpy(A.val).cuda(), size=(A.m, A.n))
+        xd = torch.from_numpy(x).cuda()
+        y = None
+        for _ in range(5):
+            y = torch.mv(Acsr, xd)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            y = torch.mv(Acsr, xd)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        yc = y.cpu().numpy()
+    del Acsr
+    return ms, yc
+
+
 def run_reference(args, A, x, ws, rank):
     """The reference arm: the CPU oracle as it stands, on the host cores of this machine."""
     if rank != 0:
@@ -161,6 +210,9 @@ def main():
     ap.add_argument("--workload", choices=list(WORKLOADS), default="fem3x3_band_1m")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--dist-steps", type=int, default=200, help="single steps timed one by one")
+    ap.add_argument("--no-cusparse", action="store_true")
+    ap.add_argument("--cusparse-steps", type=int, default=200)
     ap.add_argument("--traffic-bytes", type=float, default=None,
                     help="ncu DRAM bytes per launch of the timed kernel, if captured for this build")
     args = ap.parse_args()
@@ -227,6 +279,27 @@ def main():
             M.run_host(xh, yh, 1.0, 0.0, stream=stream)
         e2e_ms = 1e3 * (time.perf_counter() - t0) / args.e2e_steps
 
+        # device time of each kernel of a step (events around every launch, same stream)
+        kt = M.time_kernels(xd, yd, min(args.steps, 1000), stream=stream)
+        # per-step distribution, without and with an L2 flush before every step
+        run1 = lambda: M.run(xd, yd, 1.0, 0.0, stream=stream)
+        per_step = step_distribution(run1, stream, args.dist_steps)
+        flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+        per_step_flushed = step_distribution(run1, stream, args.dist_steps, flush)
+        del flush
+        y_ours = yd.cpu().numpy()
+        M.check_device(stream)
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+
+    cus = None
+    if rank == 0 and not args.no_cusparse:
+        cus_ms, y_cus = cusparse_reference(A, x, stream, args.cusparse_steps)
+        agree = bool(np.all(np.abs(y_cus - y_ours) <= 1e-10 * (np.abs(y_ours) + 1.0)))
+        cus = {"gflops": round(2.0 * A.nnz / (cus_ms * 1e-3) / 1e9, 3), "ms_per_step": round(cus_ms, 5),
+               "csr_model_bytes": int((A.m + 1) * 8 + A.nnz * 12 + A.n * 8 + A.m * 8),
+               "api": "torch.mv on torch.sparse_csr_tensor (cuSPARSE SpMV, CSR, FP64)",
+               "agrees_with_ours": agree}
+
     ms_max = ms
     e2e_max = e2e_ms
     if dist:
@@ -246,6 +319,11 @@ def main():
             gf, sample = oracle_sample_gflops(A, x)
             cpu = {"value": round(gf, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": sample}
         clocks = sampler.summary(w0, w1)
+        fmax = clocks.get("sm_max_mhz") or 2070.0
+        peak_alu = round(fp64_peak_gflops(sms, fmax), 1)
+        k_ms = kt["ms_main"]
+        k_gf = flops / (k_ms * 1e-3) / 1e9
+        k_gbs = algo_bytes / (k_ms * 1e-3) / 1e9
         line = {
             "metric": METRIC, "value": round(gflops_total, 3), "unit": "GFLOP/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max, 5),
@@ -259,23 +337,29 @@ def main():
                        "formats_coo_csr_dense": st["n_fmt"], "units": st["n_units"],
                        "split_units": st["n_split_units"]},
             "hbm_gbs": round(gbs, 2),
-            "roofline": {"bound": "alu", "achieved": round(flops / (ms * 1e-3) / 1e9, 2),
-                         "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
-                         "frac": round(flops / (ms * 1e-3) / 1e9 / FP64_NOMINAL_GFLOPS, 4),
+            "roofline": {"bound": "alu", "kernel": "spmv_f64_kernel", "achieved": round(k_gf, 2),
+                         "peak": peak_alu, "unit": "GFLOP/s", "frac": round(k_gf / peak_alu, 4),
                          "traffic": args.traffic_bytes,
-                         "note": "FP64 pipe bound (nominal 1.25 TFLOP/s FP64); HBM view below",
-                         "hbm": {"achieved": round(gbs, 2), "peak": peak, "unit": "GB/s",
-                                 "frac": round(gbs / peak, 4), "peak_kind": peak_kind,
+                         "kernel_ms": round(k_ms, 5), "combine_ms": round(kt["ms_combine"], 5),
+                         "flops_per_launch": int(flops),
+                         "note": "FP64 FMA pipe bound: peak = SMs x 2 FP64 FMA lanes/cycle x 2 flops x max SM "
+                                 "clock (derived); HBM view below",
+                         "hbm": {"achieved": round(k_gbs, 2), "peak": peak, "unit": "GB/s",
+                                 "frac": round(k_gbs / peak, 4), "peak_kind": peak_kind,
                                  "bytes_per_launch": int(algo_bytes)}},
+            "per_step": per_step,
+            "per_step_l2_flushed": per_step_flushed,
             "e2e": {"value": round(ws * flops / (e2e_max * 1e-3) / 1e9, 3), "unit": "GFLOP/s",
                     "ms_per_step": round(e2e_max, 4), "h2d_bytes_per_step": 8 * A.n,
                     "d2h_bytes_per_step": 8 * A.m, "api": "cbspmv_run_host"},
-            "gpu_launches": args.steps,
+            "gpu_launches": args.steps * kt["launches_per_run"],
             "clocks": clocks,
             "analyze_ms": round(st["analyze_ms"], 1),
         }
         if cpu:
             line["cpu_baseline"] = cpu
+        if cus:
+            line["cusparse_csr"] = cus
         print(json.dumps(line), flush=True)
     M.close()
     if dist:

@@ -56,8 +56,9 @@ enum { CBSPMV_FMT_COO = 0, CBSPMV_FMT_CSR = 1, CBSPMV_FMT_DENSE = 2 };
 
 /* A CSR matrix given by the caller. Values are always FP64 here; cbspmv_analyze copies
  * everything it needs, so the caller may free the arrays when the call returns.
- * on_device = 0: the three arrays are host pointers. (Device-resident input is not
- * supported in this version: CBSPMV_ERR_UNSUPPORTED.) */
+ * on_device = 0: the three arrays are host pointers; on_device = 1: they are device
+ * pointers (any device; the analysis copies them to the host on the given stream first,
+ * since the analysis itself runs on the host). */
 typedef struct {
   int64_t m, n, nnz;
   const int64_t* row_ptr;   /* m + 1 entries */
@@ -149,6 +150,38 @@ cbspmv_status_t cbspmv_run(cbspmv_handle_t h, const void* x, void* y, double alp
 cbspmv_status_t cbspmv_run_host(cbspmv_handle_t h, const double* x_host, double* y_host,
                                 double alpha, double beta, void* stream);
 
+/* Y = alpha * A * X + beta * Y for k right-hand sides (the multiple-vector form of the
+ * product of Sec. 2.2; the paper evaluates one vector). X: device array, column-major
+ * n x k with leading dimension ldx >= n (column j at X + j * ldx); Y: device array,
+ * column-major m x k with ldy >= m. Element type, alignment and the no-overlap rule
+ * (between the whole spans of X and Y) are those of cbspmv_run; k = 0 does nothing.
+ * Each column is computed exactly as cbspmv_run would (same summation order, so the
+ * results are bitwise equal to k separate runs). This version enqueues one product per
+ * column on `stream`. Errors: CBSPMV_ERR_INVALID (k < 0, ldx < n, ldy < m, NULL or
+ * misaligned arrays, overlap), CBSPMV_ERR_CUDA. */
+cbspmv_status_t cbspmv_run_multi(cbspmv_handle_t h, int k, const void* X, int64_t ldx, void* Y,
+                                 int64_t ldy, double alpha, double beta, void* stream);
+
+/* Analyses count matrices with the same options (cbspmv_analyze on each of A[0..count)).
+ * out: array of count handles, all set to NULL first. On failure every handle created by
+ * the call is destroyed, out[] stays NULL and the message names the failing matrix.
+ * count = 0 does nothing. Errors: those of cbspmv_analyze, CBSPMV_ERR_INVALID for
+ * count < 0 or NULL arrays. */
+cbspmv_status_t cbspmv_analyze_batched(int count, const cbspmv_csr_t* A,
+                                       const cbspmv_opts_t* opts, void* stream,
+                                       cbspmv_handle_t* out);
+
+/* Runs count independent products on one stream: for problem i,
+ * Y[i] = alpha[i] * A_i * X[i] + beta[i] * Y[i] with k[i] right-hand sides stored
+ * column-major and packed (leading dimensions n_i and m_i); k may be NULL (one vector
+ * each). Every problem's arguments are checked before any work is enqueued; a failing
+ * check enqueues nothing and the message names the problem. The same handle may appear
+ * more than once (its products then run one after another on the stream). This version
+ * enqueues the problems' products in order. Errors: as cbspmv_run_multi. */
+cbspmv_status_t cbspmv_run_batched(int count, const cbspmv_handle_t* h, const int* k,
+                                   const void* const* X, void* const* Y, const double* alpha,
+                                   const double* beta, void* stream);
+
 /* The product of cbspmv_run with no allocation of any kind. The paper has no counterpart:
  * this entry point exists for callers that may not call cudaMalloc, cudaFree or any
  * allocating routine when they run the product, for example code whose device memory
@@ -167,6 +200,17 @@ cbspmv_status_t cbspmv_run_host(cbspmv_handle_t h, const double* x_host, double*
  * the handle's error word (cbspmv_check_device). */
 cbspmv_status_t cbspmv_run_noalloc(cbspmv_handle_t h, const void* x, void* y, double alpha,
                                    double beta, void* stream);
+
+/* Measurement support (the paper has no counterpart): runs the product of cbspmv_run
+ * `reps` times (1..100000) on `stream`, with CUDA events recorded on that stream around
+ * each of its kernel launches, and returns the mean device time per run of the main run
+ * kernel (*ms_main) and of the kernel that adds the parts of split block rows
+ * (*ms_combine, 0 when there are none), plus the number of kernel launches one run makes
+ * (*launches_per_run: 0, 1 or 2). Synchronises `stream`. Arguments and results otherwise
+ * as cbspmv_run. Errors: as cbspmv_run, CBSPMV_ERR_INVALID for reps out of range. */
+cbspmv_status_t cbspmv_time_kernels(cbspmv_handle_t h, const void* x, void* y, double alpha,
+                                    double beta, int reps, void* stream, double* ms_main,
+                                    double* ms_combine, int* launches_per_run);
 
 /* Reads the handle's device error word (set by bounded device-side waits that gave up)
  * and clears it: CBSPMV_OK or CBSPMV_ERR_TIMEOUT. Synchronises `stream`. */

@@ -14,6 +14,8 @@ import numpy as np
 from . import build as _build
 
 CBSPMV_OK = 0
+(CBSPMV_ERR_INVALID, CBSPMV_ERR_NOT_CANONICAL, CBSPMV_ERR_OOM, CBSPMV_ERR_CUDA, CBSPMV_ERR_TIMEOUT,
+ CBSPMV_ERR_UNSUPPORTED, CBSPMV_ERR_BUSY) = range(1, 8)
 STATUS = {0: "OK", 1: "ERR_INVALID", 2: "ERR_NOT_CANONICAL", 3: "ERR_OOM", 4: "ERR_CUDA",
           5: "ERR_TIMEOUT", 6: "ERR_UNSUPPORTED", 7: "ERR_BUSY"}
 DTYPES = {"f64": 0, "f32": 1, "bf16": 2, "f16": 3}
@@ -64,6 +66,10 @@ SIGNATURES = {
     "cbspmv_run": [_P, _P, _P, _D, _D, _P],
     "cbspmv_run_host": [_P, _P, _P, _D, _D, _P],
     "cbspmv_run_noalloc": [_P, _P, _P, _D, _D, _P],
+    "cbspmv_run_multi": [_P, _I, _P, _I64, _P, _I64, _D, _D, _P],
+    "cbspmv_time_kernels": [_P, _P, _P, _D, _D, _I, _P, _P, _P, _P],
+    "cbspmv_analyze_batched": [_I, _P, ctypes.POINTER(Opts), _P, _P],
+    "cbspmv_run_batched": [_I, _P, _P, _P, _P, _P, _P, _P],
     "cbspmv_check_device": [_P, _P],
     "cbspmv_export_csr": [_P, _P, _P, _P],
     "cbspmv_export_blocked": [_P, _P, _P, _P, _P, _P, _P],
@@ -116,6 +122,54 @@ def _stream_ptr(stream) -> int | None:
     return stream.cuda_stream or None
 
 
+def _dev_cols(t, k: int, rows: int, name: str) -> tuple[int | None, int]:
+    """(pointer, leading dimension) of a torch float64 CUDA tensor of shape (k, >= rows)
+    whose rows are the k vectors (row stride = leading dimension, unit column stride)."""
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda:
+        raise TypeError(f"{name} must be a float64 CUDA tensor")
+    if t.dim() != 2 or t.shape[0] != k or t.shape[1] < rows or (t.shape[1] > 1 and t.stride(1) != 1):
+        raise ValueError(f"{name} must have shape ({k}, >= {rows}) with unit column stride")
+    ld = t.stride(0) if k > 1 else max(t.shape[1], rows)
+    return (t.data_ptr() or None), int(ld)
+
+
+def _csr_struct(A):
+    """cbspmv_csr_t for A (numpy or host arrays, or CUDA torch tensors) plus the arrays
+    that must stay alive while the struct is used."""
+    try:
+        import torch
+        on_dev = isinstance(A.row_ptr, torch.Tensor) and A.row_ptr.is_cuda
+    except ImportError:
+        on_dev = False
+    m, n = int(A.m), int(A.n)
+    if on_dev:
+        rp = A.row_ptr.contiguous().to(torch.int64)
+        col = A.col.contiguous().to(torch.int32)
+        val = A.val.contiguous().to(torch.float64)
+        nnz = int(col.numel())
+        csr = Csr(m, n, nnz, rp.data_ptr(), col.data_ptr() if nnz else None,
+                  val.data_ptr() if nnz else None, 1)
+    else:
+        rp = np.ascontiguousarray(A.row_ptr, dtype=np.int64)
+        col = np.ascontiguousarray(A.col, dtype=np.int32)
+        val = np.ascontiguousarray(A.val, dtype=np.float64)
+        nnz = int(rp[-1]) if rp.size else 0
+        csr = Csr(m, n, nnz, rp.ctypes.data, col.ctypes.data, val.ctypes.data, 0)
+    return csr, (rp, col, val), nnz
+
+
+def _make_opts(th0=0.15, th1=32, th2=128, col_agg=-1, value_dtype="f64", unit_work=0,
+               load_balance=True, device=0) -> Opts:
+    o = default_opts()
+    o.th0, o.th1, o.th2, o.col_agg = th0, th1, th2, col_agg
+    o.value_dtype = DTYPES[value_dtype]
+    o.unit_work = unit_work
+    o.load_balance = 1 if load_balance else 0
+    o.device = device
+    return o
+
+
 def _dev_ptr(t, n: int, name: str) -> int | None:
     """Device pointer of a torch tensor holding >= n float64 values (contiguous)."""
     import torch
@@ -134,22 +188,21 @@ class BlockedMatrix:
 
     def __init__(self, A, *, th0=0.15, th1=32, th2=128, col_agg=-1, value_dtype="f64",
                  unit_work=0, load_balance=True, device=0, stream=None):
+        """A's arrays may be host arrays or CUDA torch tensors (device-resident input)."""
         self._h = ctypes.c_void_p(None)
         self.m, self.n = int(A.m), int(A.n)
-        rp = np.ascontiguousarray(A.row_ptr, dtype=np.int64)
-        col = np.ascontiguousarray(A.col, dtype=np.int32)
-        val = np.ascontiguousarray(A.val, dtype=np.float64)
-        self.nnz = int(rp[-1]) if rp.size else 0
-        csr = Csr(self.m, self.n, self.nnz, rp.ctypes.data, col.ctypes.data, val.ctypes.data, 0)
-        o = default_opts()
-        o.th0, o.th1, o.th2, o.col_agg = th0, th1, th2, col_agg
-        o.value_dtype = DTYPES[value_dtype]
-        o.unit_work = unit_work
-        o.load_balance = 1 if load_balance else 0
-        o.device = device
+        csr, _keep, self.nnz = _csr_struct(A)
+        o = _make_opts(th0, th1, th2, col_agg, value_dtype, unit_work, load_balance, device)
         self.device = device
-        s = _stream_ptr(stream) if device >= 0 else None
+        s = _stream_ptr(stream) if (device >= 0 or csr.on_device) else None
         _check(lib().cbspmv_analyze(ctypes.byref(csr), ctypes.byref(o), s, ctypes.byref(self._h)))
+
+    @classmethod
+    def _adopt(cls, handle: int, m: int, n: int, nnz: int, device: int) -> "BlockedMatrix":
+        self = cls.__new__(cls)
+        self._h = ctypes.c_void_p(handle)
+        self.m, self.n, self.nnz, self.device = m, n, nnz, device
+        return self
 
     @property
     def handle(self) -> int:
@@ -160,6 +213,25 @@ class BlockedMatrix:
         _check(lib().cbspmv_run(self._h, _dev_ptr(x, self.n, "x"), _dev_ptr(y, self.m, "y"),
                                 float(alpha), float(beta), _stream_ptr(stream)))
         return y
+
+    def run_multi(self, X, Y, alpha: float = 1.0, beta: float = 0.0, stream=None):
+        """Y <- alpha*A*X + beta*Y for k vectors: X of shape (k, n), Y of shape (k, m),
+        float64 CUDA tensors whose rows are the vectors (row stride = leading dimension)."""
+        k = int(X.shape[0])
+        px, ldx = _dev_cols(X, k, self.n, "X")
+        py, ldy = _dev_cols(Y, k, self.m, "Y")
+        _check(lib().cbspmv_run_multi(self._h, k, px, ldx, py, ldy, float(alpha), float(beta),
+                                      _stream_ptr(stream)))
+        return Y
+
+    def time_kernels(self, x, y, reps: int, alpha: float = 1.0, beta: float = 0.0, stream=None) -> dict:
+        """Mean device time per run of each kernel of the product (CUDA events around every
+        launch, on the run's stream)."""
+        a, b, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+        _check(lib().cbspmv_time_kernels(self._h, _dev_ptr(x, self.n, "x"), _dev_ptr(y, self.m, "y"),
+                                         float(alpha), float(beta), int(reps), _stream_ptr(stream),
+                                         ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)))
+        return {"ms_main": a.value, "ms_combine": b.value, "launches_per_run": n.value}
 
     def run_host(self, x: np.ndarray, y: np.ndarray | None = None, alpha: float = 1.0,
                  beta: float = 0.0, stream=None) -> np.ndarray:
@@ -221,6 +293,43 @@ class BlockedMatrix:
             self.close()
         except Exception:
             pass
+
+
+def analyze_batched(mats, *, stream=None, **opts) -> list["BlockedMatrix"]:
+    """cbspmv_analyze_batched over a list of CSR matrices with one set of options."""
+    count = len(mats)
+    structs = [_csr_struct(A) for A in mats]
+    arr = (Csr * max(count, 1))(*[c for c, _, _ in structs])
+    o = _make_opts(**opts)
+    out = (ctypes.c_void_p * max(count, 1))()
+    s = _stream_ptr(stream) if o.device >= 0 else None
+    _check(lib().cbspmv_analyze_batched(count, ctypes.addressof(arr), ctypes.byref(o), s,
+                                        ctypes.addressof(out)))
+    return [BlockedMatrix._adopt(out[i], int(A.m), int(A.n), structs[i][2], o.device)
+            for i, A in enumerate(mats)]
+
+
+def run_batched(mats, Xs, Ys, alphas, betas, *, stream=None):
+    """cbspmv_run_batched: problem i computes Ys[i] <- alphas[i]*A_i*Xs[i] + betas[i]*Ys[i].
+    Xs[i], Ys[i] are float64 CUDA tensors, 1-D (one vector) or (k_i, n_i) / (k_i, m_i)
+    contiguous (k_i vectors)."""
+    count = len(mats)
+    n1 = max(count, 1)
+    hs = (ctypes.c_void_p * n1)(*[M.handle for M in mats])
+    ks = (ctypes.c_int * n1)()
+    xp = (ctypes.c_void_p * n1)()
+    yp = (ctypes.c_void_p * n1)()
+    al = (ctypes.c_double * n1)(*[float(a) for a in alphas])
+    be = (ctypes.c_double * n1)(*[float(b) for b in betas])
+    for i, M in enumerate(mats):
+        X, Y = Xs[i], Ys[i]
+        k = 1 if X.dim() == 1 else int(X.shape[0])
+        ks[i] = k
+        xp[i] = _dev_ptr(X, k * M.n, f"X[{i}]")
+        yp[i] = _dev_ptr(Y, k * M.m, f"Y[{i}]")
+    _check(lib().cbspmv_run_batched(count, ctypes.addressof(hs), ctypes.addressof(ks),
+                                    ctypes.addressof(xp), ctypes.addressof(yp),
+                                    ctypes.addressof(al), ctypes.addressof(be), _stream_ptr(stream)))
 
 
 def version() -> str:

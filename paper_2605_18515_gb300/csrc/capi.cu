@@ -7,6 +7,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/cbspmv.h"
 #include "cb_kernels.h"
@@ -132,7 +133,34 @@ cbspmv_status_t cbspmv_analyze(const cbspmv_csr_t* A, const cbspmv_opts_t* opts_
                                cbspmv_handle_t* out) {
   if (!A || !out) return fail(CBSPMV_ERR_INVALID, "NULL argument");
   *out = nullptr;
-  if (A->on_device) return fail(CBSPMV_ERR_UNSUPPORTED, "device-resident CSR input is not supported");
+  if (A->on_device) {
+    // the analysis runs on the host: copy the three arrays down, then analyse the copy
+    if (A->m < 0 || A->n < 0 || A->nnz < 0) return fail(CBSPMV_ERR_INVALID, "negative size");
+    if (!A->row_ptr || (A->nnz > 0 && (!A->col_idx || !A->val))) return fail(CBSPMV_ERR_INVALID, "NULL CSR array");
+    std::vector<int64_t> rp;
+    std::vector<int32_t> ci;
+    std::vector<double> va;
+    try {
+      rp.resize((size_t)A->m + 1);
+      ci.resize((size_t)A->nnz);
+      va.resize((size_t)A->nnz);
+    } catch (const std::bad_alloc&) {
+      return fail(CBSPMV_ERR_OOM, "host allocation failed");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    CB_CUDA(cudaMemcpyAsync(rp.data(), A->row_ptr, rp.size() * 8, cudaMemcpyDeviceToHost, s));
+    if (A->nnz) {
+      CB_CUDA(cudaMemcpyAsync(ci.data(), A->col_idx, ci.size() * 4, cudaMemcpyDeviceToHost, s));
+      CB_CUDA(cudaMemcpyAsync(va.data(), A->val, va.size() * 8, cudaMemcpyDeviceToHost, s));
+    }
+    CB_CUDA(cudaStreamSynchronize(s));
+    cbspmv_csr_t H = *A;
+    H.row_ptr = rp.data();
+    H.col_idx = ci.data();
+    H.val = va.data();
+    H.on_device = 0;
+    return cbspmv_analyze(&H, opts_in, stream, out);
+  }
   cbspmv_opts_t opts;
   if (opts_in) opts = *opts_in; else cbspmv_default_opts(&opts);
   if (opts.unit_work < 0 || opts.unit_work > 16384)
@@ -205,7 +233,7 @@ cbspmv_status_t cbspmv_analyze(const cbspmv_csr_t* A, const cbspmv_opts_t* opts_
 }
 
 static cbspmv_status_t run_device(cbspmv_handle_t h, const double* x, double* y, double alpha, double beta,
-                                  cudaStream_t s) {
+                                  cudaStream_t s, cudaEvent_t* ev = nullptr) {
   const cb::Plan& p = h->plan;
   if (p.m == 0) return ok();
   cb::RunArgs a{};
@@ -229,22 +257,138 @@ static cbspmv_status_t run_device(cbspmv_handle_t h, const double* x, double* y,
   a.aggregated = p.aggregated ? 1 : 0;
   a.alpha_one = alpha == 1.0;
   a.beta_nonzero = beta != 0.0;
-  CB_CUDA(cb::launch_spmv_f64(a, h->grid, s));
+  CB_CUDA(cb::launch_spmv_f64(a, h->grid, s, ev));
+  return ok();
+}
+
+// Checks of a run on k right-hand sides stored column by column: X holds n x k values with
+// leading dimension ldx, Y m x k with ldy (k = 1: x and y). Returns CBSPMV_OK or fails.
+static cbspmv_status_t check_run_args(cbspmv_handle_t h, int64_t k, const void* X, int64_t ldx, const void* Y,
+                                      int64_t ldy) {
+  if (!valid_handle(h)) return fail(CBSPMV_ERR_INVALID, "invalid handle");
+  if (h->device < 0) return fail(CBSPMV_ERR_INVALID, "host-only handle cannot run");
+  const int64_t m = h->plan.m, n = h->plan.n;
+  if (k < 0) return fail(CBSPMV_ERR_INVALID, "k must be >= 0");
+  if (ldx < n || ldy < m) return fail(CBSPMV_ERR_INVALID, "leading dimensions must be >= n (X) and >= m (Y)");
+  if (k == 0) return ok();
+  if ((!X && n > 0) || (!Y && m > 0)) return fail(CBSPMV_ERR_INVALID, "NULL x or y");
+  if (((uintptr_t)X & 7) || ((uintptr_t)Y & 7)) return fail(CBSPMV_ERR_INVALID, "x and y must be 8-byte aligned");
+  if (X && Y && n > 0 && m > 0) {
+    const char* xb = (const char*)X;
+    const char* yb = (const char*)Y;
+    const int64_t xspan = 8 * (ldx * (k - 1) + n), yspan = 8 * (ldy * (k - 1) + m);
+    if (xb < yb + yspan && yb < xb + xspan) return fail(CBSPMV_ERR_INVALID, "x and y overlap");
+  }
   return ok();
 }
 
 cbspmv_status_t cbspmv_run(cbspmv_handle_t h, const void* x, void* y, double alpha, double beta, void* stream) {
-  if (!valid_handle(h)) return fail(CBSPMV_ERR_INVALID, "invalid handle");
-  if (h->device < 0) return fail(CBSPMV_ERR_INVALID, "host-only handle cannot run");
-  if ((!x && h->plan.n > 0) || (!y && h->plan.m > 0)) return fail(CBSPMV_ERR_INVALID, "NULL x or y");
-  if (((uintptr_t)x & 7) || ((uintptr_t)y & 7)) return fail(CBSPMV_ERR_INVALID, "x and y must be 8-byte aligned");
-  const char* xb = (const char*)x;
-  const char* yb = (const char*)y;
-  if (x && y && xb < yb + 8 * h->plan.m && yb < xb + 8 * h->plan.n)
-    return fail(CBSPMV_ERR_INVALID, "x and y overlap");
+  cbspmv_status_t st = check_run_args(h, 1, x, h && valid_handle(h) ? h->plan.n : 0, y,
+                                      h && valid_handle(h) ? h->plan.m : 0);
+  if (st != CBSPMV_OK) return st;
   DeviceGuard g(h->device);
   CB_CUDA(g.err);
   return run_device(h, (const double*)x, (double*)y, alpha, beta, (cudaStream_t)stream);
+}
+
+cbspmv_status_t cbspmv_time_kernels(cbspmv_handle_t h, const void* x, void* y, double alpha, double beta, int reps,
+                                    void* stream, double* ms_main, double* ms_combine, int* launches_per_run) {
+  cbspmv_status_t st = check_run_args(h, 1, x, h && valid_handle(h) ? h->plan.n : 0, y,
+                                      h && valid_handle(h) ? h->plan.m : 0);
+  if (st != CBSPMV_OK) return st;
+  if (reps < 1 || reps > 100000) return fail(CBSPMV_ERR_INVALID, "reps must be in [1, 100000]");
+  if (!ms_main || !ms_combine || !launches_per_run) return fail(CBSPMV_ERR_INVALID, "NULL output");
+  *ms_main = *ms_combine = 0.0;
+  *launches_per_run = h->plan.m == 0 ? 0 : (h->plan.split_rows.empty() ? 1 : 2);
+  if (h->plan.m == 0) return ok();
+  DeviceGuard g(h->device);
+  CB_CUDA(g.err);
+  cudaStream_t s = (cudaStream_t)stream;
+  // events of up to kBatch runs are outstanding at a time; each batch is read back at its end
+  constexpr int kBatch = 256;
+  std::vector<cudaEvent_t> ev(3 * kBatch, nullptr);
+  cudaError_t e = cudaSuccess;
+  for (auto& v : ev)
+    if (e == cudaSuccess) e = cudaEventCreate(&v);
+  double t_main = 0.0, t_comb = 0.0;
+  for (int done = 0; e == cudaSuccess && done < reps;) {
+    const int nb = reps - done < kBatch ? reps - done : kBatch;
+    for (int i = 0; i < nb && st == CBSPMV_OK; ++i)
+      st = run_device(h, (const double*)x, (double*)y, alpha, beta, s, &ev[3 * i]);
+    if (st != CBSPMV_OK) break;
+    e = cudaStreamSynchronize(s);
+    for (int i = 0; i < nb && e == cudaSuccess; ++i) {
+      float a = 0.f, b = 0.f;
+      e = cudaEventElapsedTime(&a, ev[3 * i], ev[3 * i + 1]);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ev[3 * i + 1], ev[3 * i + 2]);
+      t_main += a;
+      t_comb += b;
+    }
+    done += nb;
+  }
+  for (auto& v : ev)
+    if (v) cudaEventDestroy(v);
+  if (st != CBSPMV_OK) return st;
+  if (e != cudaSuccess) return fail(CBSPMV_ERR_CUDA, "event timing failed: %s", cudaGetErrorString(e));
+  *ms_main = t_main / reps;
+  *ms_combine = h->plan.split_rows.empty() ? 0.0 : t_comb / reps;
+  return ok();
+}
+
+cbspmv_status_t cbspmv_run_multi(cbspmv_handle_t h, int k, const void* X, int64_t ldx, void* Y, int64_t ldy,
+                                 double alpha, double beta, void* stream) {
+  cbspmv_status_t st = check_run_args(h, k, X, ldx, Y, ldy);
+  if (st != CBSPMV_OK || k == 0) return st;
+  DeviceGuard g(h->device);
+  CB_CUDA(g.err);
+  for (int j = 0; j < k; ++j) {
+    st = run_device(h, (const double*)X + (size_t)j * ldx, (double*)Y + (size_t)j * ldy, alpha, beta,
+                    (cudaStream_t)stream);
+    if (st != CBSPMV_OK) return st;
+  }
+  return ok();
+}
+
+cbspmv_status_t cbspmv_analyze_batched(int count, const cbspmv_csr_t* A, const cbspmv_opts_t* opts, void* stream,
+                                       cbspmv_handle_t* out) {
+  if (count < 0) return fail(CBSPMV_ERR_INVALID, "count must be >= 0");
+  if (count == 0) return ok();
+  if (!A || !out) return fail(CBSPMV_ERR_INVALID, "NULL argument");
+  for (int i = 0; i < count; ++i) out[i] = nullptr;
+  for (int i = 0; i < count; ++i) {
+    cbspmv_status_t st = cbspmv_analyze(&A[i], opts, stream, &out[i]);
+    if (st != CBSPMV_OK) {
+      std::string msg = g_err;
+      for (int j = 0; j < i; ++j) {
+        cbspmv_destroy(out[j]);
+        out[j] = nullptr;
+      }
+      return fail(st, "matrix %d: %s", i, msg.c_str());
+    }
+  }
+  return ok();
+}
+
+cbspmv_status_t cbspmv_run_batched(int count, const cbspmv_handle_t* hs, const int* k, const void* const* X,
+                                   void* const* Y, const double* alpha, const double* beta, void* stream) {
+  if (count < 0) return fail(CBSPMV_ERR_INVALID, "count must be >= 0");
+  if (count == 0) return ok();
+  if (!hs || !X || !Y || !alpha || !beta) return fail(CBSPMV_ERR_INVALID, "NULL argument");
+  // check every problem before enqueuing any work
+  for (int i = 0; i < count; ++i) {
+    const int ki = k ? k[i] : 1;
+    cbspmv_handle_t h = hs[i];
+    const bool v = valid_handle(h);
+    cbspmv_status_t st = check_run_args(h, ki, X[i], v ? h->plan.n : 0, Y[i], v ? h->plan.m : 0);
+    if (st != CBSPMV_OK) return fail(st, "problem %d: %s", i, std::string(g_err).c_str());
+  }
+  for (int i = 0; i < count; ++i) {
+    cbspmv_handle_t h = hs[i];
+    cbspmv_status_t st =
+        cbspmv_run_multi(h, k ? k[i] : 1, X[i], h->plan.n, Y[i], h->plan.m, alpha[i], beta[i], stream);
+    if (st != CBSPMV_OK) return fail(st, "problem %d: %s", i, std::string(g_err).c_str());
+  }
+  return ok();
 }
 
 cbspmv_status_t cbspmv_run_host(cbspmv_handle_t h, const double* x_host, double* y_host, double alpha, double beta,

@@ -32,8 +32,9 @@ struct RunArgs {
 size_t spmv_f64_smem_bytes();
 int spmv_f64_threads();
 // Launches the run kernel and, when the matrix has block rows cut into several units, the
-// kernel that adds their parts (two launches on `stream`).
-cudaError_t launch_spmv_f64(const RunArgs& a, int grid, cudaStream_t stream);
+// kernel that adds their parts (two launches on `stream`). ev: NULL, or three events
+// recorded on `stream` before the run kernel, between the two launches and after the last.
+cudaError_t launch_spmv_f64(const RunArgs& a, int grid, cudaStream_t stream, cudaEvent_t* ev = nullptr);
 
 }  // namespace cb
 #endif

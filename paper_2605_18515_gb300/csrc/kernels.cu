@@ -91,9 +91,6 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
 }
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -457,7 +454,7 @@ __global__ void __launch_bounds__(256) combine_kernel(const RunArgs a) {
 size_t spmv_f64_smem_bytes() { return sizeof(Shared); }
 int spmv_f64_threads() { return kThreads; }
 
-cudaError_t launch_spmv_f64(const RunArgs& a, int grid, cudaStream_t stream) {
+cudaError_t launch_spmv_f64(const RunArgs& a, int grid, cudaStream_t stream, cudaEvent_t* ev) {
   static bool configured[64] = {false};
   const size_t smem = sizeof(Shared);
   int dev = 0;
@@ -468,12 +465,19 @@ cudaError_t launch_spmv_f64(const RunArgs& a, int grid, cudaStream_t stream) {
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) configured[dev] = true;
   }
+  if (ev && (e = cudaEventRecord(ev[0], stream)) != cudaSuccess) return e;
   spmv_f64_kernel<<<grid, kThreads, smem, stream>>>(a);
   e = cudaGetLastError();
-  if (e != cudaSuccess || a.n_split_rows == 0) return e;
-  const uint32_t threads = 16u * a.n_split_rows;
-  combine_kernel<<<(threads + 255) / 256, 256, 0, stream>>>(a);
-  return cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (ev && (e = cudaEventRecord(ev[1], stream)) != cudaSuccess) return e;
+  if (a.n_split_rows) {
+    const uint32_t threads = 16u * a.n_split_rows;
+    combine_kernel<<<(threads + 255) / 256, 256, 0, stream>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (ev) e = cudaEventRecord(ev[2], stream);
+  return e;
 }
 
 }  // namespace cb
