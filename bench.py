@@ -151,15 +151,16 @@ def step_distribution(run, stream, n: int, flush_buf=None):
             "n": n}
 
 
-def cusparse_reference(A, x, stream, steps: int):
-    """cuSPARSE CSR SpMV (FP64) through torch.sparse_csr_tensor on the same matrix and x:
-    a library reference point, not part of this library's path."""
+def cusparse_reference(A, x, stream, steps: int, vec=np.float64):
+    """cuSPARSE CSR SpMV (FP64, or FP32 for the reduced value types) through
+    torch.sparse_csr_tensor on the same matrix and x: a library reference point, not part of
+    this library's path."""
     import torch
     with torch.cuda.stream(stream):
         Acsr = torch.sparse_csr_tensor(torch.from_numpy(A.row_ptr.astype(np.int32)).cuda(),
                                        torch.from_numpy(A.col.astype(np.int32)).cuda(),
-                                       torch.from_numpy(A.val).cuda(), size=(A.m, A.n))
-        xd = torch.from_numpy(x).cuda()
+                                       torch.from_numpy(A.val.astype(vec)).cuda(), size=(A.m, A.n))
+        xd = torch.from_numpy(x.astype(vec)).cuda()
         y = None
         for _ in range(5):
             y = torch.mv(Acsr, xd)
@@ -173,6 +174,19 @@ def cusparse_reference(A, x, stream, steps: int):
         yc = y.cpu().numpy()
     del Acsr
     return ms, yc
+
+
+def error_vs_fp64_oracle(A, x, y, n_rows: int = 20000):
+    """Normalised error |y_i - y_oracle_i| / sum_k |a_ik x_k| of the bench's result on a
+    seeded sample of rows against the FP64 CPU oracle (original values and x)."""
+    import oracle
+    from paper_2605_18515_gb300 import inputs as I
+    rows = np.unique((I.uniform01(11, 9, n_rows) * A.m).astype(np.int64))
+    yref, s = oracle.spmv_rows(A, x, rows)
+    err = np.abs(y[rows] - yref)
+    norm = np.where(s > 0, err / np.where(s > 0, s, 1.0), np.where(err > 0, np.inf, 0.0))
+    return {"max": float(norm.max()), "median": float(np.median(norm)), "rows": int(rows.size),
+            "sample": f"{rows.size} seeded rows, error / sum_k |a_ik x_k|"}
 
 
 def run_reference(args, A, x, ws, rank):
@@ -210,6 +224,8 @@ def main():
     ap.add_argument("--workload", choices=list(WORKLOADS), default="fem3x3_band_1m")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--dtype", choices=["f64", "f32", "bf16", "f16"], default="f64",
+                    help="storage type of the matrix values (reduced types: FP32 x, y and accumulation)")
     ap.add_argument("--dist-steps", type=int, default=200, help="single steps timed one by one")
     ap.add_argument("--no-cusparse", action="store_true")
     ap.add_argument("--cusparse-steps", type=int, default=200)
@@ -236,12 +252,16 @@ def main():
     build.build()
     from paper_2605_18515_gb300 import binding as bd
 
+    lp = args.dtype != "f64"
+    vec = np.float32 if lp else np.float64
+    tvec = torch.float32 if lp else torch.float64
+    esz = 4 if lp else 8
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        M = bd.BlockedMatrix(A, device=local, stream=stream)
+        M = bd.BlockedMatrix(A, device=local, stream=stream, value_dtype=args.dtype)
         st = M.stats()
-        xd = torch.from_numpy(x).cuda()
-        yd = torch.empty(A.m, dtype=torch.float64, device="cuda")
+        xd = torch.from_numpy(x.astype(vec)).cuda()
+        yd = torch.empty(A.m, dtype=tvec, device="cuda")
         for _ in range(args.warmup):
             M.run(xd, yd, 1.0, 0.0, stream=stream)
         stream.synchronize()
@@ -270,8 +290,8 @@ def main():
         M.check_device(stream)
 
         # end to end through the C ABI from pinned host memory
-        xh = torch.from_numpy(x).pin_memory().numpy()
-        yh = torch.empty(A.m, dtype=torch.float64).pin_memory().numpy()
+        xh = torch.from_numpy(x.astype(vec)).pin_memory().numpy()
+        yh = torch.empty(A.m, dtype=tvec).pin_memory().numpy()
         for _ in range(3):
             M.run_host(xh, yh, 1.0, 0.0, stream=stream)
         t0 = time.perf_counter()
@@ -287,17 +307,18 @@ def main():
         flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
         per_step_flushed = step_distribution(run1, stream, args.dist_steps, flush)
         del flush
-        y_ours = yd.cpu().numpy()
+        y_ours = yd.cpu().numpy().astype(np.float64)
         M.check_device(stream)
         sms = torch.cuda.get_device_properties(local).multi_processor_count
 
     cus = None
     if rank == 0 and not args.no_cusparse:
-        cus_ms, y_cus = cusparse_reference(A, x, stream, args.cusparse_steps)
-        agree = bool(np.all(np.abs(y_cus - y_ours) <= 1e-10 * (np.abs(y_ours) + 1.0)))
+        cus_ms, y_cus = cusparse_reference(A, x, stream, args.cusparse_steps, vec)
+        tol = 1e-3 if lp else 1e-10
+        agree = bool(np.all(np.abs(y_cus.astype(np.float64) - y_ours) <= tol * (np.abs(y_ours) + 1.0)))
         cus = {"gflops": round(2.0 * A.nnz / (cus_ms * 1e-3) / 1e9, 3), "ms_per_step": round(cus_ms, 5),
-               "csr_model_bytes": int((A.m + 1) * 8 + A.nnz * 12 + A.n * 8 + A.m * 8),
-               "api": "torch.mv on torch.sparse_csr_tensor (cuSPARSE SpMV, CSR, FP64)",
+               "csr_model_bytes": int((A.m + 1) * 8 + A.nnz * (4 + esz) + A.n * esz + A.m * esz),
+               "api": "torch.mv on torch.sparse_csr_tensor (cuSPARSE SpMV, CSR, %s)" % ("FP32" if lp else "FP64"),
                "agrees_with_ours": agree}
 
     ms_max = ms
@@ -315,19 +336,41 @@ def main():
 
     if rank == 0:
         cpu = None
+        err = None
         if not args.no_cpu_baseline and ws == 1:
             gf, sample = oracle_sample_gflops(A, x)
             cpu = {"value": round(gf, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": sample}
+            err = error_vs_fp64_oracle(A, x, y_ours)
         clocks = sampler.summary(w0, w1)
         fmax = clocks.get("sm_max_mhz") or 2070.0
         peak_alu = round(fp64_peak_gflops(sms, fmax), 1)
         k_ms = kt["ms_main"]
         k_gf = flops / (k_ms * 1e-3) / 1e9
         k_gbs = algo_bytes / (k_ms * 1e-3) / 1e9
+        if lp:
+            roof = {"bound": "hbm", "kernel": "spmv_kernel<%s>" % args.dtype, "achieved": round(k_gbs, 2),
+                    "peak": peak, "unit": "GB/s", "frac": round(k_gbs / peak, 4), "peak_kind": peak_kind,
+                    "traffic": args.traffic_bytes, "kernel_ms": round(k_ms, 5),
+                    "combine_ms": round(kt["ms_combine"], 5), "bytes_per_launch": int(algo_bytes),
+                    "gflops": round(k_gf, 2),
+                    "note": "FP32 FMA is far from binding; the bytes model (values + coordinates + "
+                            "metadata + x + y + restore_cols) over the kernel's time vs measured copy bandwidth"}
+        else:
+            roof = {"bound": "alu", "kernel": "spmv_kernel<f64>", "achieved": round(k_gf, 2),
+                    "peak": peak_alu, "unit": "GFLOP/s", "frac": round(k_gf / peak_alu, 4),
+                    "traffic": args.traffic_bytes,
+                    "kernel_ms": round(k_ms, 5), "combine_ms": round(kt["ms_combine"], 5),
+                    "flops_per_launch": int(flops),
+                    "note": "FP64 FMA pipe bound: peak = SMs x 2 FP64 FMA lanes/cycle x 2 flops x max SM "
+                            "clock (derived); HBM view below",
+                    "hbm": {"achieved": round(k_gbs, 2), "peak": peak, "unit": "GB/s",
+                            "frac": round(k_gbs / peak, 4), "peak_kind": peak_kind,
+                            "bytes_per_launch": int(algo_bytes)}}
         line = {
             "metric": METRIC, "value": round(gflops_total, 3), "unit": "GFLOP/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max, 5),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": args.dtype if not lp else f"{args.dtype} values, f32 x/y/accumulate",
             "data": "synthetic",
             "config": {"workload": args.workload, "description": WORKLOADS[args.workload],
                        "m": A.m, "n": A.n, "nnz": A.nnz, "parallelism": f"replicas x{ws}",
@@ -337,21 +380,12 @@ def main():
                        "formats_coo_csr_dense": st["n_fmt"], "units": st["n_units"],
                        "split_units": st["n_split_units"]},
             "hbm_gbs": round(gbs, 2),
-            "roofline": {"bound": "alu", "kernel": "spmv_f64_kernel", "achieved": round(k_gf, 2),
-                         "peak": peak_alu, "unit": "GFLOP/s", "frac": round(k_gf / peak_alu, 4),
-                         "traffic": args.traffic_bytes,
-                         "kernel_ms": round(k_ms, 5), "combine_ms": round(kt["ms_combine"], 5),
-                         "flops_per_launch": int(flops),
-                         "note": "FP64 FMA pipe bound: peak = SMs x 2 FP64 FMA lanes/cycle x 2 flops x max SM "
-                                 "clock (derived); HBM view below",
-                         "hbm": {"achieved": round(k_gbs, 2), "peak": peak, "unit": "GB/s",
-                                 "frac": round(k_gbs / peak, 4), "peak_kind": peak_kind,
-                                 "bytes_per_launch": int(algo_bytes)}},
+            "roofline": roof,
             "per_step": per_step,
             "per_step_l2_flushed": per_step_flushed,
             "e2e": {"value": round(ws * flops / (e2e_max * 1e-3) / 1e9, 3), "unit": "GFLOP/s",
-                    "ms_per_step": round(e2e_max, 4), "h2d_bytes_per_step": 8 * A.n,
-                    "d2h_bytes_per_step": 8 * A.m, "api": "cbspmv_run_host"},
+                    "ms_per_step": round(e2e_max, 4), "h2d_bytes_per_step": esz * A.n,
+                    "d2h_bytes_per_step": esz * A.m, "api": "cbspmv_run_host"},
             "gpu_launches": args.steps * kt["launches_per_run"],
             "clocks": clocks,
             "analyze_ms": round(st["analyze_ms"], 1),
@@ -360,6 +394,8 @@ def main():
             line["cpu_baseline"] = cpu
         if cus:
             line["cusparse_csr"] = cus
+        if err:
+            line["error_vs_fp64_oracle"] = err
         print(json.dumps(line), flush=True)
     M.close()
     if dist:

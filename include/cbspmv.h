@@ -48,7 +48,11 @@ typedef enum {
 } cbspmv_status_t;
 
 /* Storage type of the matrix values on the device. F64 is the reference path: values,
- * x, y and accumulation in IEEE double. */
+ * x, y and accumulation in IEEE double. F32, BF16 and F16 store the values in that type
+ * (each FP64 input value rounded to nearest, ties to even, directly from FP64; overflow
+ * gives an infinity) and use FP32 for x, y, alpha, beta and the accumulation: the
+ * mixed-precision form the paper mentions (Sec. 2.2) without fixing its details. The
+ * "vector type" of a handle is double for F64 and float for the other three. */
 typedef enum { CBSPMV_F64 = 0, CBSPMV_F32 = 1, CBSPMV_BF16 = 2, CBSPMV_F16 = 3 } cbspmv_dtype_t;
 
 /* Sub-block storage formats (Sec. 3.3.2). */
@@ -73,7 +77,8 @@ typedef struct {
  *   th1, th2: sub-block format thresholds, COO if nnz < th1, Dense if nnz > th2, CSR
  *        otherwise (Sec. 3.3.2; paper: 32 and 128). 0 <= th1 <= th2 <= 256.
  *   col_agg: -1 decide by th0, 0 never aggregate, 1 always aggregate.
- *   value_dtype: storage type of the values (CBSPMV_F64 for the FP64 path).
+ *   value_dtype: storage type of the values (CBSPMV_F64 for the FP64 path; see
+ *        cbspmv_dtype_t for the reduced types).
  *   unit_work: target number of multiply-adds per scheduling unit (0 = default).
  *   load_balance: 1 (default) spread units over workers by the longest-first
  *        priority-queue rule; 0 deal them out round-robin in matrix order (ablation).
@@ -135,19 +140,19 @@ cbspmv_status_t cbspmv_analyze(const cbspmv_csr_t* A, const cbspmv_opts_t* opts,
 
 /* y = alpha * A * x + beta * y on the device (Sec. 3.5, Algorithms 3 and 4).
  * x: device array of n values, y: device array of m values, both of the handle's
- * vector type (double for CBSPMV_F64 and for all value types in this version), 8-byte
- * aligned; y must not overlap x. Enqueued on `stream`, no host synchronisation. One kernel
+ * vector type (double for CBSPMV_F64, float for F32, BF16 and F16), aligned to the
+ * element size; y must not overlap x. Enqueued on `stream`, no host synchronisation. One kernel
  * launch, plus a second small one that adds the parts of block rows the analysis cut into
  * several units (when there are any). Concurrent runs on one handle must be serialised on
  * one stream (they share the handle's partial-sum buffer). Errors: CBSPMV_ERR_INVALID, CBSPMV_ERR_CUDA. */
 cbspmv_status_t cbspmv_run(cbspmv_handle_t h, const void* x, void* y, double alpha, double beta,
                            void* stream);
 
-/* The same product end to end from host memory: copies x (n doubles) to the device,
- * runs, copies y back (m doubles; read first when beta != 0), then synchronises the
- * stream. x_host / y_host may be pageable or pinned. Uses staging buffers owned by the
- * handle (allocated on first use). */
-cbspmv_status_t cbspmv_run_host(cbspmv_handle_t h, const double* x_host, double* y_host,
+/* The same product end to end from host memory: copies x (n values of the handle's
+ * vector type) to the device, runs, copies y back (m values; read first when beta != 0),
+ * then synchronises the stream. x_host / y_host may be pageable or pinned. Uses staging
+ * buffers owned by the handle (allocated on first use). */
+cbspmv_status_t cbspmv_run_host(cbspmv_handle_t h, const void* x_host, void* y_host,
                                 double alpha, double beta, void* stream);
 
 /* Y = alpha * A * X + beta * Y for k right-hand sides (the multiple-vector form of the
@@ -217,7 +222,8 @@ cbspmv_status_t cbspmv_time_kernels(cbspmv_handle_t h, const void* x, void* y, d
 cbspmv_status_t cbspmv_check_device(cbspmv_handle_t h, void* stream);
 
 /* Reconstructs the CSR matrix from the handle's device-resident blocked format
- * (bit-exact round trip of row_ptr, col_idx and the value bits for FP64 values).
+ * (bit-exact round trip of row_ptr, col_idx and the value bits for FP64 values; for the
+ * reduced types, the stored values widened exactly to double).
  * Host output arrays of m+1, nnz, nnz entries. Synchronous. */
 cbspmv_status_t cbspmv_export_csr(cbspmv_handle_t h, int64_t* row_ptr, int32_t* col_idx,
                                   double* val);

@@ -122,12 +122,18 @@ def _stream_ptr(stream) -> int | None:
     return stream.cuda_stream or None
 
 
-def _dev_cols(t, k: int, rows: int, name: str) -> tuple[int | None, int]:
-    """(pointer, leading dimension) of a torch float64 CUDA tensor of shape (k, >= rows)
-    whose rows are the k vectors (row stride = leading dimension, unit column stride)."""
+def _torch_dtype(vec: str):
     import torch
-    if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda:
-        raise TypeError(f"{name} must be a float64 CUDA tensor")
+    return torch.float64 if vec == "f64" else torch.float32
+
+
+def _dev_cols(t, k: int, rows: int, name: str, vec: str = "f64") -> tuple[int | None, int]:
+    """(pointer, leading dimension) of a torch CUDA tensor of the vector type, shape
+    (k, >= rows), whose rows are the k vectors (row stride = leading dimension, unit column
+    stride)."""
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dtype != _torch_dtype(vec) or not t.is_cuda:
+        raise TypeError(f"{name} must be a {_torch_dtype(vec)} CUDA tensor")
     if t.dim() != 2 or t.shape[0] != k or t.shape[1] < rows or (t.shape[1] > 1 and t.stride(1) != 1):
         raise ValueError(f"{name} must have shape ({k}, >= {rows}) with unit column stride")
     ld = t.stride(0) if k > 1 else max(t.shape[1], rows)
@@ -170,13 +176,14 @@ def _make_opts(th0=0.15, th1=32, th2=128, col_agg=-1, value_dtype="f64", unit_wo
     return o
 
 
-def _dev_ptr(t, n: int, name: str) -> int | None:
-    """Device pointer of a torch tensor holding >= n float64 values (contiguous)."""
+def _dev_ptr(t, n: int, name: str, vec: str = "f64") -> int | None:
+    """Device pointer of a contiguous torch CUDA tensor holding >= n values of the vector
+    type (float64 for FP64 handles, float32 for the reduced value types)."""
     import torch
     if not isinstance(t, torch.Tensor):
         raise TypeError(f"{name} must be a torch.Tensor on the GPU")
-    if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
-        raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+    if t.dtype != _torch_dtype(vec) or not t.is_cuda or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous {_torch_dtype(vec)} CUDA tensor")
     if t.numel() < n:
         raise ValueError(f"{name} has {t.numel()} elements, needs {n}")
     return t.data_ptr() or None
@@ -194,15 +201,25 @@ class BlockedMatrix:
         csr, _keep, self.nnz = _csr_struct(A)
         o = _make_opts(th0, th1, th2, col_agg, value_dtype, unit_work, load_balance, device)
         self.device = device
+        self.value_dtype = value_dtype
+        self.vec = "f64" if value_dtype == "f64" else "f32"
         s = _stream_ptr(stream) if (device >= 0 or csr.on_device) else None
         _check(lib().cbspmv_analyze(ctypes.byref(csr), ctypes.byref(o), s, ctypes.byref(self._h)))
 
     @classmethod
-    def _adopt(cls, handle: int, m: int, n: int, nnz: int, device: int) -> "BlockedMatrix":
+    def _adopt(cls, handle: int, m: int, n: int, nnz: int, device: int,
+               value_dtype: str = "f64") -> "BlockedMatrix":
         self = cls.__new__(cls)
         self._h = ctypes.c_void_p(handle)
         self.m, self.n, self.nnz, self.device = m, n, nnz, device
+        self.value_dtype = value_dtype
+        self.vec = "f64" if value_dtype == "f64" else "f32"
         return self
+
+    @property
+    def vector_dtype(self):
+        """numpy dtype of x and y: float64 for FP64 values, float32 for the reduced types."""
+        return np.float64 if self.vec == "f64" else np.float32
 
     @property
     def handle(self) -> int:
@@ -210,7 +227,7 @@ class BlockedMatrix:
 
     def run(self, x, y, alpha: float = 1.0, beta: float = 0.0, stream=None):
         """y <- alpha*A*x + beta*y on the device (asynchronous on the stream)."""
-        _check(lib().cbspmv_run(self._h, _dev_ptr(x, self.n, "x"), _dev_ptr(y, self.m, "y"),
+        _check(lib().cbspmv_run(self._h, _dev_ptr(x, self.n, "x", self.vec), _dev_ptr(y, self.m, "y", self.vec),
                                 float(alpha), float(beta), _stream_ptr(stream)))
         return y
 
@@ -218,8 +235,8 @@ class BlockedMatrix:
         """Y <- alpha*A*X + beta*Y for k vectors: X of shape (k, n), Y of shape (k, m),
         float64 CUDA tensors whose rows are the vectors (row stride = leading dimension)."""
         k = int(X.shape[0])
-        px, ldx = _dev_cols(X, k, self.n, "X")
-        py, ldy = _dev_cols(Y, k, self.m, "Y")
+        px, ldx = _dev_cols(X, k, self.n, "X", self.vec)
+        py, ldy = _dev_cols(Y, k, self.m, "Y", self.vec)
         _check(lib().cbspmv_run_multi(self._h, k, px, ldx, py, ldy, float(alpha), float(beta),
                                       _stream_ptr(stream)))
         return Y
@@ -228,19 +245,21 @@ class BlockedMatrix:
         """Mean device time per run of each kernel of the product (CUDA events around every
         launch, on the run's stream)."""
         a, b, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
-        _check(lib().cbspmv_time_kernels(self._h, _dev_ptr(x, self.n, "x"), _dev_ptr(y, self.m, "y"),
+        _check(lib().cbspmv_time_kernels(self._h, _dev_ptr(x, self.n, "x", self.vec),
+                                         _dev_ptr(y, self.m, "y", self.vec),
                                          float(alpha), float(beta), int(reps), _stream_ptr(stream),
                                          ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)))
         return {"ms_main": a.value, "ms_combine": b.value, "launches_per_run": n.value}
 
     def run_host(self, x: np.ndarray, y: np.ndarray | None = None, alpha: float = 1.0,
                  beta: float = 0.0, stream=None) -> np.ndarray:
-        """The product from host arrays (copies in and out, synchronous)."""
-        x = np.ascontiguousarray(x, dtype=np.float64)
+        """The product from host arrays of the vector type (copies in and out, synchronous)."""
+        vt = self.vector_dtype
+        x = np.ascontiguousarray(x, dtype=vt)
         if y is None:
-            y = np.zeros(self.m, dtype=np.float64)
-        if y.dtype != np.float64 or not y.flags.c_contiguous:
-            raise TypeError("y must be a contiguous float64 array")
+            y = np.zeros(self.m, dtype=vt)
+        if y.dtype != vt or not y.flags.c_contiguous:
+            raise TypeError(f"y must be a contiguous {np.dtype(vt).name} array")
         _check(lib().cbspmv_run_host(self._h, x.ctypes.data, y.ctypes.data, float(alpha), float(beta),
                                      _stream_ptr(stream)))
         return y
@@ -305,7 +324,8 @@ def analyze_batched(mats, *, stream=None, **opts) -> list["BlockedMatrix"]:
     s = _stream_ptr(stream) if o.device >= 0 else None
     _check(lib().cbspmv_analyze_batched(count, ctypes.addressof(arr), ctypes.byref(o), s,
                                         ctypes.addressof(out)))
-    return [BlockedMatrix._adopt(out[i], int(A.m), int(A.n), structs[i][2], o.device)
+    vd = opts.get("value_dtype", "f64")
+    return [BlockedMatrix._adopt(out[i], int(A.m), int(A.n), structs[i][2], o.device, vd)
             for i, A in enumerate(mats)]
 
 
@@ -325,8 +345,8 @@ def run_batched(mats, Xs, Ys, alphas, betas, *, stream=None):
         X, Y = Xs[i], Ys[i]
         k = 1 if X.dim() == 1 else int(X.shape[0])
         ks[i] = k
-        xp[i] = _dev_ptr(X, k * M.n, f"X[{i}]")
-        yp[i] = _dev_ptr(Y, k * M.m, f"Y[{i}]")
+        xp[i] = _dev_ptr(X, k * M.n, f"X[{i}]", M.vec)
+        yp[i] = _dev_ptr(Y, k * M.m, f"Y[{i}]", M.vec)
     _check(lib().cbspmv_run_batched(count, ctypes.addressof(hs), ctypes.addressof(ks),
                                     ctypes.addressof(xp), ctypes.addressof(yp),
                                     ctypes.addressof(al), ctypes.addressof(be), _stream_ptr(stream)))

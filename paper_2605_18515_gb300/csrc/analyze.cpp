@@ -88,14 +88,94 @@ void gather_block_row(const cbspmv_csr_t& A, int64_t b, std::vector<std::pair<ui
   std::sort(e.begin(), e.end());
 }
 
-void write_value(uint8_t* dst, double v, int vsize) {
-  // Only the FP64 storage type is produced by this analyser version.
-  (void)vsize;
-  std::memcpy(dst, &v, 8);
+}  // namespace
+
+// v rounded to the nearest number of a binary floating-point format with p significand
+// bits (implicit bit included), smallest normal exponent emin and largest exponent emax;
+// ties go to the even significand, magnitudes beyond the largest finite number become
+// infinities, below the smallest normal the quantum stays 2^(emin - p + 1) (gradual
+// underflow); NaN and signed zeros pass through (IEEE 754 roundTiesToEven). The result
+// is exact in double.
+double round_to_format(double v, int p, int emin, int emax) {
+  if (!std::isfinite(v) || v == 0.0) return v;
+  int e = std::ilogb(v);                         // floor(log2 |v|)
+  if (e > emax) return std::copysign(INFINITY, v);
+  if (e < emin) e = emin;
+  const int q = e - (p - 1);                     // exponent of the quantum
+  const double r = std::nearbyint(std::ldexp(v, -q)) ;   // the default mode rounds ties to even
+  const double out = std::ldexp(r, q);
+  if (std::ilogb(out) > emax) return std::copysign(INFINITY, v);
+  return out;
 }
 
-void build_block_row(const cbspmv_csr_t& A, int64_t b, bool agg, int th1, int th2, int vsize,
+namespace {
+
+// IEEE binary16 bits of a double that is exactly representable in binary16 (or +-inf).
+uint16_t half_bits(double h) {
+  const uint16_t sign = std::signbit(h) ? 0x8000u : 0u;
+  if (std::isnan(h)) return 0x7e00u;
+  if (std::isinf(h)) return sign | 0x7c00u;
+  const double a = std::fabs(h);
+  if (a == 0.0) return sign;
+  const int e = std::ilogb(a);
+  if (e < -14) return sign | (uint16_t)std::ldexp(a, 24);          // subnormal: a / 2^-24
+  const uint32_t mant = (uint32_t)std::ldexp(a, 10 - e) - 1024u;   // 10 fraction bits
+  return sign | (uint16_t)((uint32_t)(e + 15) << 10) | (uint16_t)mant;
+}
+
+// Stores v in the handle's value type, rounded to nearest (ties to even) directly from
+// the FP64 input; the rounded value is exact in the stored type.
+void write_value(uint8_t* dst, double v, int dtype) {
+  switch (dtype) {
+    case CBSPMV_F64: std::memcpy(dst, &v, 8); break;
+    case CBSPMV_F32: {
+      const float f = (float)round_to_format(v, 24, -126, 127);
+      std::memcpy(dst, &f, 4);
+      break;
+    }
+    case CBSPMV_BF16: {
+      const float f = (float)round_to_format(v, 8, -126, 127);     // exact in binary32
+      uint32_t b;
+      std::memcpy(&b, &f, 4);
+      const uint16_t h = std::isnan(f) ? (uint16_t)0x7fc0u : (uint16_t)(b >> 16);
+      std::memcpy(dst, &h, 2);
+      break;
+    }
+    default: {
+      const uint16_t h = half_bits(round_to_format(v, 11, -14, 15));
+      std::memcpy(dst, &h, 2);
+      break;
+    }
+  }
+}
+
+// The stored value at src widened exactly to double.
+double read_value(const uint8_t* src, int dtype) {
+  switch (dtype) {
+    case CBSPMV_F64: { double d; std::memcpy(&d, src, 8); return d; }
+    case CBSPMV_F32: { float f; std::memcpy(&f, src, 4); return f; }
+    case CBSPMV_BF16: {
+      uint16_t h; std::memcpy(&h, src, 2);
+      const uint32_t b = (uint32_t)h << 16;
+      float f; std::memcpy(&f, &b, 4);
+      return f;
+    }
+    default: {
+      uint16_t h; std::memcpy(&h, src, 2);
+      const double sign = (h & 0x8000u) ? -1.0 : 1.0;
+      const int ex = (h >> 10) & 31, fr = h & 1023;
+      if (ex == 31) return fr ? NAN : sign * INFINITY;
+      if (ex == 0) return sign * std::ldexp((double)fr, -24);
+      return sign * std::ldexp((double)(1024 + fr), ex - 25);
+    }
+  }
+}
+
+int value_size(int dtype) { return dtype == CBSPMV_F64 ? 8 : dtype == CBSPMV_F32 ? 4 : 2; }
+
+void build_block_row(const cbspmv_csr_t& A, int64_t b, bool agg, int th1, int th2, int dtype,
                      std::vector<std::pair<uint64_t, int64_t>>& e, BlockRowOut& out) {
+  const int vsize = value_size(dtype);
   gather_block_row(A, b, e);
   out = BlockRowOut();
   const size_t ne = e.size();
@@ -147,7 +227,7 @@ void build_block_row(const cbspmv_csr_t& A, int64_t b, bool agg, int th1, int th
       for (auto& t : tile) {
         uint32_t pos = t.first;  // row * 16 + col
         rec[pos >> 3] |= (uint8_t)(1u << (pos & 7));
-        write_value(rec + 32 + pos * vsize, A.val[t.second], vsize);
+        write_value(rec + 32 + pos * vsize, A.val[t.second], dtype);
       }
     } else {
       uint8_t* idx = rec;
@@ -163,7 +243,7 @@ void build_block_row(const cbspmv_csr_t& A, int64_t b, bool agg, int th1, int th
       for (int i = 0; i < nnz; ++i) {
         uint32_t lr = tile[i].first >> 4, lc = tile[i].first & 15u;
         idx[i] = (uint8_t)(lr | (lc << 4));          // row low nibble, col high nibble
-        write_value(rec + voff + (uint32_t)i * vsize, A.val[tile[i].second], vsize);
+        write_value(rec + voff + (uint32_t)i * vsize, A.val[tile[i].second], dtype);
       }
     }
     out.off.push_back(base);
@@ -218,9 +298,9 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
     *msg = "thresholds must satisfy th0 >= 0 and 0 <= th1 <= th2 <= 256";
     return CBSPMV_ERR_INVALID;
   }
-  if (opts.value_dtype != CBSPMV_F64) {
-    *msg = "this analyser stores FP64 values only";
-    return CBSPMV_ERR_UNSUPPORTED;
+  if (opts.value_dtype < CBSPMV_F64 || opts.value_dtype > CBSPMV_F16) {
+    *msg = "unknown value_dtype";
+    return CBSPMV_ERR_INVALID;
   }
   if (opts.col_agg < -1 || opts.col_agg > 1) { *msg = "col_agg must be -1, 0 or 1"; return CBSPMV_ERR_INVALID; }
   if (n_workers <= 0) { *msg = "no workers"; return CBSPMV_ERR_INVALID; }
@@ -232,7 +312,7 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
   p.m = A.m; p.n = A.n; p.nnz = A.nnz;
   p.nbr = (A.m + CB_BLK - 1) / CB_BLK;
   p.value_dtype = opts.value_dtype;
-  p.vsize = 8;
+  p.vsize = value_size(opts.value_dtype);
   p.th0 = opts.th0; p.th1 = opts.th1; p.th2 = opts.th2;
   const int64_t nbr = p.nbr;
 
@@ -267,7 +347,7 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
   parallel_for(nbr, 64, [&](int64_t lo, int64_t hi) {
     std::vector<std::pair<uint64_t, int64_t>> e;
     for (int64_t b = lo; b < hi; ++b)
-      build_block_row(A, b, p.aggregated, opts.th1, opts.th2, p.vsize, e, rows[b]);
+      build_block_row(A, b, p.aggregated, opts.th1, opts.th2, p.value_dtype, e, rows[b]);
   });
   // prefix sums over block rows: tiles, stream bytes, distinct columns
   std::vector<int64_t> tile_off(nbr + 1, 0), byte_off(nbr + 1, 0);
@@ -608,7 +688,8 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
   s.model_bytes_cb = ntiles * 21 + A.nnz * 9;
   s.model_bytes_csr = (A.m + 1) * 4 + A.nnz * 12;
   s.model_bytes_bsr16 = 2048 * ntiles + (nbr + 1) * 4 + 4 * ntiles;
-  s.algo_bytes_per_run = A.nnz * (int64_t)(p.vsize + 1) + ntiles * 21 + A.n * 8 + A.m * 8 +
+  const int64_t es = p.value_dtype == CBSPMV_F64 ? 8 : 4;   // x, y element size
+  s.algo_bytes_per_run = A.nnz * (int64_t)(p.vsize + 1) + ntiles * 21 + A.n * es + A.m * es +
                          (p.aggregated ? 4 * p.restore_cols_len : 0);
   s.flops_per_run = 2 * A.nnz;
   s.mults_per_run = mults;
@@ -638,12 +719,13 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
   return CBSPMV_OK;
 }
 
-cbspmv_status_t decode_to_csr(int64_t m, int64_t n, int vsize, bool aggregated,
+cbspmv_status_t decode_to_csr(int64_t m, int64_t n, int dtype, bool aggregated,
                               const std::vector<CbTile>& tiles, const uint8_t* stream,
                               size_t stream_size, const int32_t* restore_cols, size_t restore_len,
                               int64_t* row_ptr, int32_t* col, double* val, int64_t nnz_expected,
                               std::string* msg) {
-  if (vsize != 8) { *msg = "export supports FP64 storage only"; return CBSPMV_ERR_UNSUPPORTED; }
+  if (dtype < CBSPMV_F64 || dtype > CBSPMV_F16) { *msg = "unknown value type"; return CBSPMV_ERR_INVALID; }
+  const int vsize = value_size(dtype);
   std::vector<int64_t> cnt(m + 1, 0);
   auto for_entries = [&](const CbTile& t, const std::function<void(int64_t, int64_t, const uint8_t*)>& f) -> bool {
     size_t off = (size_t)t.vp16 * 16;
@@ -690,7 +772,7 @@ cbspmv_status_t decode_to_csr(int64_t m, int64_t n, int vsize, bool aggregated,
     for_entries(t, [&](int64_t r, int64_t c, const uint8_t* v) {
       int64_t k = cur[r]++;
       col[k] = (int32_t)c;
-      std::memcpy(&val[k], v, 8);
+      val[k] = read_value(v, dtype);
     });
   std::memcpy(row_ptr, cnt.data(), (m + 1) * sizeof(int64_t));
   // tiles of a block row are in increasing column order, so rows come out sorted; check

@@ -73,11 +73,13 @@ struct cbspmv_handle_s {
   uint8_t* d_blob = nullptr;
   uint32_t* d_wunits = nullptr;
   uint32_t* d_woff = nullptr;
-  double* d_partial = nullptr;
+  void* d_partial = nullptr;
   CbSplitRow* d_split_rows = nullptr;
   uint32_t* d_err = nullptr;
-  double* d_xstage = nullptr;
-  double* d_ystage = nullptr;
+  void* d_xstage = nullptr;
+  void* d_ystage = nullptr;
+  // bytes of one x or y element: double for FP64 values, float for the reduced types
+  size_t esize() const { return plan.value_dtype == CBSPMV_F64 ? 8 : 4; }
 
   void free_device() {
     if (device < 0) return;
@@ -175,9 +177,9 @@ cbspmv_status_t cbspmv_analyze(const cbspmv_csr_t* A, const cbspmv_opts_t* opts_
     int sms = 0, smem_optin = 0;
     CB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, opts.device));
     CB_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, opts.device));
-    if ((size_t)smem_optin < cb::spmv_f64_smem_bytes())
+    if ((size_t)smem_optin < cb::spmv_smem_bytes())
       return fail(CBSPMV_ERR_UNSUPPORTED, "device has %d B of shared memory per block, kernel needs %zu",
-                  smem_optin, cb::spmv_f64_smem_bytes());
+                  smem_optin, cb::spmv_smem_bytes());
     grid = sms;
   } else if (opts.device != -1) {
     return fail(CBSPMV_ERR_INVALID, "device must be >= 0 or -1 (host only)");
@@ -215,7 +217,7 @@ cbspmv_status_t cbspmv_analyze(const cbspmv_csr_t* A, const cbspmv_opts_t* opts_
   step(upload(&h->d_blob, p.blob.data(), p.blob.size(), s));
   step(upload(&h->d_wunits, p.worker_units.data(), p.worker_units.size(), s));
   step(upload(&h->d_woff, p.worker_off.data(), p.worker_off.size(), s));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_partial, (size_t)(p.n_slots ? p.n_slots : 1) * 16 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_partial, (size_t)(p.n_slots ? p.n_slots : 1) * 16 * h->esize());
   step(upload(&h->d_split_rows, p.split_rows.data(), p.split_rows.size(), s));
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_err, 4);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, 4, s);
@@ -232,7 +234,7 @@ cbspmv_status_t cbspmv_analyze(const cbspmv_csr_t* A, const cbspmv_opts_t* opts_
   return ok();
 }
 
-static cbspmv_status_t run_device(cbspmv_handle_t h, const double* x, double* y, double alpha, double beta,
+static cbspmv_status_t run_device(cbspmv_handle_t h, const void* x, void* y, double alpha, double beta,
                                   cudaStream_t s, cudaEvent_t* ev = nullptr) {
   const cb::Plan& p = h->plan;
   if (p.m == 0) return ok();
@@ -257,7 +259,8 @@ static cbspmv_status_t run_device(cbspmv_handle_t h, const double* x, double* y,
   a.aggregated = p.aggregated ? 1 : 0;
   a.alpha_one = alpha == 1.0;
   a.beta_nonzero = beta != 0.0;
-  CB_CUDA(cb::launch_spmv_f64(a, h->grid, s, ev));
+  a.value_dtype = p.value_dtype;
+  CB_CUDA(cb::launch_spmv(a, h->grid, s, ev));
   return ok();
 }
 
@@ -272,11 +275,13 @@ static cbspmv_status_t check_run_args(cbspmv_handle_t h, int64_t k, const void* 
   if (ldx < n || ldy < m) return fail(CBSPMV_ERR_INVALID, "leading dimensions must be >= n (X) and >= m (Y)");
   if (k == 0) return ok();
   if ((!X && n > 0) || (!Y && m > 0)) return fail(CBSPMV_ERR_INVALID, "NULL x or y");
-  if (((uintptr_t)X & 7) || ((uintptr_t)Y & 7)) return fail(CBSPMV_ERR_INVALID, "x and y must be 8-byte aligned");
+  const int64_t es = (int64_t)h->esize();
+  if (((uintptr_t)X & (es - 1)) || ((uintptr_t)Y & (es - 1)))
+    return fail(CBSPMV_ERR_INVALID, "x and y must be aligned to their element size (%d bytes)", (int)es);
   if (X && Y && n > 0 && m > 0) {
     const char* xb = (const char*)X;
     const char* yb = (const char*)Y;
-    const int64_t xspan = 8 * (ldx * (k - 1) + n), yspan = 8 * (ldy * (k - 1) + m);
+    const int64_t xspan = es * (ldx * (k - 1) + n), yspan = es * (ldy * (k - 1) + m);
     if (xb < yb + yspan && yb < xb + xspan) return fail(CBSPMV_ERR_INVALID, "x and y overlap");
   }
   return ok();
@@ -288,7 +293,7 @@ cbspmv_status_t cbspmv_run(cbspmv_handle_t h, const void* x, void* y, double alp
   if (st != CBSPMV_OK) return st;
   DeviceGuard g(h->device);
   CB_CUDA(g.err);
-  return run_device(h, (const double*)x, (double*)y, alpha, beta, (cudaStream_t)stream);
+  return run_device(h, x, y, alpha, beta, (cudaStream_t)stream);
 }
 
 cbspmv_status_t cbspmv_time_kernels(cbspmv_handle_t h, const void* x, void* y, double alpha, double beta, int reps,
@@ -314,7 +319,7 @@ cbspmv_status_t cbspmv_time_kernels(cbspmv_handle_t h, const void* x, void* y, d
   for (int done = 0; e == cudaSuccess && done < reps;) {
     const int nb = reps - done < kBatch ? reps - done : kBatch;
     for (int i = 0; i < nb && st == CBSPMV_OK; ++i)
-      st = run_device(h, (const double*)x, (double*)y, alpha, beta, s, &ev[3 * i]);
+      st = run_device(h, x, y, alpha, beta, s, &ev[3 * i]);
     if (st != CBSPMV_OK) break;
     e = cudaStreamSynchronize(s);
     for (int i = 0; i < nb && e == cudaSuccess; ++i) {
@@ -342,7 +347,8 @@ cbspmv_status_t cbspmv_run_multi(cbspmv_handle_t h, int k, const void* X, int64_
   DeviceGuard g(h->device);
   CB_CUDA(g.err);
   for (int j = 0; j < k; ++j) {
-    st = run_device(h, (const double*)X + (size_t)j * ldx, (double*)Y + (size_t)j * ldy, alpha, beta,
+    const size_t es = h->esize();
+    st = run_device(h, (const char*)X + es * j * ldx, (char*)Y + es * j * ldy, alpha, beta,
                     (cudaStream_t)stream);
     if (st != CBSPMV_OK) return st;
   }
@@ -391,7 +397,7 @@ cbspmv_status_t cbspmv_run_batched(int count, const cbspmv_handle_t* hs, const i
   return ok();
 }
 
-cbspmv_status_t cbspmv_run_host(cbspmv_handle_t h, const double* x_host, double* y_host, double alpha, double beta,
+cbspmv_status_t cbspmv_run_host(cbspmv_handle_t h, const void* x_host, void* y_host, double alpha, double beta,
                                 void* stream) {
   if (!valid_handle(h)) return fail(CBSPMV_ERR_INVALID, "invalid handle");
   if (h->device < 0) return fail(CBSPMV_ERR_INVALID, "host-only handle cannot run");
@@ -400,13 +406,14 @@ cbspmv_status_t cbspmv_run_host(cbspmv_handle_t h, const double* x_host, double*
   DeviceGuard g(h->device);
   CB_CUDA(g.err);
   cudaStream_t s = (cudaStream_t)stream;
-  if (!h->d_xstage) CB_CUDA(cudaMalloc((void**)&h->d_xstage, (size_t)(p.n ? p.n : 1) * 8));
-  if (!h->d_ystage) CB_CUDA(cudaMalloc((void**)&h->d_ystage, (size_t)(p.m ? p.m : 1) * 8));
-  if (p.n) CB_CUDA(cudaMemcpyAsync(h->d_xstage, x_host, (size_t)p.n * 8, cudaMemcpyHostToDevice, s));
-  if (beta != 0.0 && p.m) CB_CUDA(cudaMemcpyAsync(h->d_ystage, y_host, (size_t)p.m * 8, cudaMemcpyHostToDevice, s));
+  const size_t es = h->esize();
+  if (!h->d_xstage) CB_CUDA(cudaMalloc(&h->d_xstage, (size_t)(p.n ? p.n : 1) * es));
+  if (!h->d_ystage) CB_CUDA(cudaMalloc(&h->d_ystage, (size_t)(p.m ? p.m : 1) * es));
+  if (p.n) CB_CUDA(cudaMemcpyAsync(h->d_xstage, x_host, (size_t)p.n * es, cudaMemcpyHostToDevice, s));
+  if (beta != 0.0 && p.m) CB_CUDA(cudaMemcpyAsync(h->d_ystage, y_host, (size_t)p.m * es, cudaMemcpyHostToDevice, s));
   cbspmv_status_t st = run_device(h, h->d_xstage, h->d_ystage, alpha, beta, s);
   if (st != CBSPMV_OK) return st;
-  if (p.m) CB_CUDA(cudaMemcpyAsync(y_host, h->d_ystage, (size_t)p.m * 8, cudaMemcpyDeviceToHost, s));
+  if (p.m) CB_CUDA(cudaMemcpyAsync(y_host, h->d_ystage, (size_t)p.m * es, cudaMemcpyDeviceToHost, s));
   CB_CUDA(cudaStreamSynchronize(s));
   return ok();
 }
@@ -434,7 +441,7 @@ cbspmv_status_t cbspmv_export_csr(cbspmv_handle_t h, int64_t* row_ptr, int32_t* 
   std::string msg;
   cbspmv_status_t st;
   if (h->device < 0) {
-    st = cb::decode_to_csr(p.m, p.n, p.vsize, p.aggregated, p.tiles, p.stream.data(), p.stream.size(),
+    st = cb::decode_to_csr(p.m, p.n, p.value_dtype, p.aggregated, p.tiles, p.stream.data(), p.stream.size(),
                            p.restore_cols.data(), p.restore_cols.size(), row_ptr, col_idx, val, p.nnz, &msg);
   } else {
     DeviceGuard g(h->device);
@@ -446,7 +453,7 @@ cbspmv_status_t cbspmv_export_csr(cbspmv_handle_t h, int64_t* row_ptr, int32_t* 
     if (!stream.empty()) CB_CUDA(cudaMemcpy(stream.data(), h->d_stream, stream.size(), cudaMemcpyDeviceToHost));
     if (!tiles.empty()) CB_CUDA(cudaMemcpy(tiles.data(), h->d_tiles, tiles.size() * sizeof(CbTile), cudaMemcpyDeviceToHost));
     if (!rcols.empty()) CB_CUDA(cudaMemcpy(rcols.data(), h->d_rcols, rcols.size() * 4, cudaMemcpyDeviceToHost));
-    st = cb::decode_to_csr(p.m, p.n, p.vsize, p.aggregated, tiles, stream.data(), stream.size(), rcols.data(),
+    st = cb::decode_to_csr(p.m, p.n, p.value_dtype, p.aggregated, tiles, stream.data(), stream.size(), rcols.data(),
                            rcols.size(), row_ptr, col_idx, val, p.nnz, &msg);
   }
   if (st != CBSPMV_OK) return fail(st, "%s", msg.c_str());
@@ -510,6 +517,7 @@ bool noalloc_view(cbspmv_handle_t h, NoallocView* v) {
   a.m = h->plan.m;
   a.n = h->plan.n;
   a.aggregated = h->plan.aggregated ? 1 : 0;
+  a.value_dtype = h->plan.value_dtype;
   v->args = a;
   return true;
 }

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/cbspmv.h"
 #include "cb_layout.h"
 
 namespace cb {
@@ -16,9 +17,9 @@ struct RunArgs {
   const uint8_t* blob;          // unit blobs: tile records, restore_cols slice, lane schedule
   const uint32_t* worker_units; // unit ids per persistent CTA
   const uint32_t* worker_off;   // grid + 1 offsets into worker_units
-  const double* x;
-  double* y;
-  double* partial;              // partial sums of split block rows (16 per slot)
+  const void* x;                // n values of the vector type (double for F64, else float)
+  void* y;                      // m values of the vector type
+  void* partial;                // partial sums of split block rows (16 per slot, vector type)
   const CbSplitRow* split_rows; // block rows cut into several units
   uint32_t n_split_rows;
   uint32_t* err;                // device error word
@@ -27,14 +28,16 @@ struct RunArgs {
   int aggregated;
   int alpha_one;                // alpha == 1: skip the scaling multiply
   int beta_nonzero;             // beta != 0: read y
+  int value_dtype;              // cbspmv_dtype_t of the stored values
 };
 
-size_t spmv_f64_smem_bytes();
-int spmv_f64_threads();
-// Launches the run kernel and, when the matrix has block rows cut into several units, the
-// kernel that adds their parts (two launches on `stream`). ev: NULL, or three events
-// recorded on `stream` before the run kernel, between the two launches and after the last.
-cudaError_t launch_spmv_f64(const RunArgs& a, int grid, cudaStream_t stream, cudaEvent_t* ev = nullptr);
+size_t spmv_smem_bytes();      // dynamic shared memory of the largest instantiation
+int spmv_threads();
+// Launches the run kernel for a.value_dtype and, when the matrix has block rows cut into
+// several units, the kernel that adds their parts (two launches on `stream`). ev: NULL, or
+// three events recorded on `stream` before the run kernel, between the two launches and
+// after the last.
+cudaError_t launch_spmv(const RunArgs& a, int grid, cudaStream_t stream, cudaEvent_t* ev = nullptr);
 
 }  // namespace cb
 #endif

@@ -47,12 +47,16 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
                              Plan* plan, std::string* msg);
 
 // Rebuilds CSR from the packed layout (host arrays). Used by export on both host-only
-// handles and on data read back from the device.
-cbspmv_status_t decode_to_csr(int64_t m, int64_t n, int vsize, bool aggregated,
+// handles and on data read back from the device. Stored values are widened exactly to FP64.
+cbspmv_status_t decode_to_csr(int64_t m, int64_t n, int value_dtype, bool aggregated,
                               const std::vector<CbTile>& tiles, const uint8_t* stream,
                               size_t stream_size, const int32_t* restore_cols,
                               size_t restore_len, int64_t* row_ptr, int32_t* col, double* val,
                               int64_t nnz_expected, std::string* msg);
+
+// v rounded to nearest, ties to even, in a binary format with p significand bits and
+// exponent range [emin, emax] (the conversion of FP64 input values to the storage type).
+double round_to_format(double v, int p, int emin, int emax);
 
 }  // namespace cb
 #endif

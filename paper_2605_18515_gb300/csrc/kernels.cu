@@ -1,4 +1,9 @@
-// Run kernel of the blocked SpMV, y = alpha * A * x + beta * y, FP64, for sm_103a.
+// Run kernel of the blocked SpMV, y = alpha * A * x + beta * y, for sm_103a.
+//
+// One kernel template serves every value storage type: FP64 values with FP64 x, y and
+// accumulation (the paper's setting), and FP32 / BF16 / FP16 values with FP32 x, y and
+// accumulation (the mixed-precision storage the paper mentions but does not specify;
+// values are widened exactly to FP32 before each FMA).
 //
 // The paper's kernel (Sec. 3.5, Algorithms 3 and 4) maps one sub-block to one warp,
 // preloads x into shared memory (plain tiles) or reads it through restore_cols
@@ -29,6 +34,8 @@
 //     in part order and writes y, so results do not depend on scheduling.
 //   * Every wait is bounded (clock64 budget); on expiry the kernel records an error code,
 //     drains its own copies in flight and returns.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -57,13 +64,38 @@ static_assert(sizeof(CbUnit) == 64, "unit descriptor slot");
 static_assert(kOffStream % 16 == 0 && kOffBlob % 16 == 0 && kOffXs % 16 == 0 && kBlobMax % 16 == 0,
               "bulk copy destinations must be 16-byte aligned");
 
+// Stored value types: V is the storage type, Acc the type of x, y and the accumulators.
+template <class V> struct ValT;
+template <> struct ValT<double> {
+  using Acc = double;
+  __device__ static __forceinline__ double load(const uint8_t* p) { return *reinterpret_cast<const double*>(p); }
+};
+template <> struct ValT<float> {
+  using Acc = float;
+  __device__ static __forceinline__ float load(const uint8_t* p) { return *reinterpret_cast<const float*>(p); }
+};
+template <> struct ValT<__nv_bfloat16> {
+  using Acc = float;
+  __device__ static __forceinline__ float load(const uint8_t* p) {   // exact: bf16 is the top half of fp32
+    return __uint_as_float((uint32_t)*reinterpret_cast<const uint16_t*>(p) << 16);
+  }
+};
+template <> struct ValT<__half> {
+  using Acc = float;
+  __device__ static __forceinline__ float load(const uint8_t* p) {   // exact widening
+    return __half2float(*reinterpret_cast<const __half*>(p));
+  }
+};
+
+template <class Acc>
 struct Scratch {
   uint4 tinfo[CB_T_MAX];        // per tile: value base, coordinate base, x-row base (smem offsets)
-  double srow[CB_R_MAX];        // row sums
-  double cval[CB_VLANES];       // per-run carry value
+  Acc srow[CB_R_MAX];           // row sums
+  Acc cval[CB_VLANES];          // per-run carry value
   int32_t crow[CB_VLANES];      // per-run carry row (-1 none, -2 no chunks)
 };
 
+template <class Acc>
 struct Shared {
   __align__(128) uint8_t stage[kStages][kStageBytes];
   uint64_t bar_tma[kStages];    // bulk copies of the unit landed
@@ -74,7 +106,7 @@ struct Shared {
   // for the exact ticket here, after which the parity waits are unambiguous.
   uint32_t issued[kStages];
   uint32_t released[kStages];
-  Scratch scratch[kConsumers];
+  Scratch<Acc> scratch[kConsumers];
   uint8_t ident[256];           // byte k = (k & 15) << 4: coordinate bytes of a Dense record
   uint32_t ticket;
   uint32_t abort_flag;
@@ -128,9 +160,16 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
-__device__ __forceinline__ void cp_async_8(uint32_t dst_smem, const void* src, uint32_t src_bytes) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst_smem), "l"(src), "r"(src_bytes)
-               : "memory");
+// cp.async of one x element (8 or 4 bytes); src_bytes = 0 writes zeros
+template <int kBytes>
+__device__ __forceinline__ void cp_async_elem(uint32_t dst_smem, const void* src, uint32_t src_bytes) {
+  static_assert(kBytes == 8 || kBytes == 4, "x element size");
+  if constexpr (kBytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst_smem), "l"(src), "r"(src_bytes)
+                 : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst_smem), "l"(src), "r"(src_bytes)
+                 : "memory");
 }
 __device__ __forceinline__ void cp_async_arrive_noinc(uint64_t* bar) {
   asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -152,7 +191,8 @@ __device__ __forceinline__ uint32_t load_desc_word(const CbUnit* units, uint32_t
   return (k < nu && lane < 16) ? __ldg(reinterpret_cast<const uint32_t*>(units + k) + lane) : 0u;
 }
 
-__device__ bool loader_issue(const RunArgs& a, Shared& sh, uint32_t k, uint32_t dw, int lane) {
+template <class Acc>
+__device__ bool loader_issue(const RunArgs& a, Shared<Acc>& sh, uint32_t k, uint32_t dw, int lane) {
   const uint32_t s = k % kStages;
   // the stage's previous ticket (k - kStages) must have been released by its consumer
   if (k >= (uint32_t)kStages && !wait_value(&sh.released[s], k - kStages)) return false;
@@ -171,8 +211,11 @@ __device__ bool loader_issue(const RunArgs& a, Shared& sh, uint32_t k, uint32_t 
   return true;
 }
 
-__device__ void loader(const RunArgs& a, Shared& sh, const CbUnit* units, uint32_t nu, uint32_t l, int lane) {
+template <class Acc>
+__device__ void loader(const RunArgs& a, Shared<Acc>& sh, const CbUnit* units, uint32_t nu, uint32_t l, int lane) {
   constexpr int kPerLane = CB_T_MAX * 16 / 32;
+  constexpr uint32_t kXs = sizeof(Acc);
+  const Acc* x = static_cast<const Acc*>(a.x);
   bool ok = true;
   uint32_t next = l;                                      // next own ticket to issue
   uint32_t dw = load_desc_word(units, next, nu, lane);    // its descriptor (16 lanes, one word each)
@@ -205,7 +248,7 @@ __device__ void loader(const RunArgs& a, Shared& sh, const CbUnit* units, uint32
       const uint32_t idx = (uint32_t)lane + 32u * k;
       if (idx < nx) {
         const bool valid = col[k] >= 0 && col[k] < a.n;
-        cp_async_8(xs_smem + 8u * idx, a.x + (valid ? col[k] : 0), valid ? 8u : 0u);
+        cp_async_elem<kXs>(xs_smem + kXs * idx, x + (valid ? col[k] : 0), valid ? kXs : 0u);
       }
     }
     cp_async_arrive_noinc(&sh.bar_full[s]);
@@ -233,11 +276,23 @@ __device__ __forceinline__ double pfma(bool p, double v, double x, double acc) {
       : "d"(v), "d"(x), "r"((uint32_t)p));
   return acc;
 }
-#define CB_LDD(off) (*reinterpret_cast<const double*>(sm + (off)))
+__device__ __forceinline__ float pfma(bool p, float v, float x, float acc) {
+  asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\t@q fma.rn.f32 %0, %1, %2, %0;\n\t}"
+      : "+f"(acc)
+      : "f"(v), "f"(x), "r"((uint32_t)p));
+  return acc;
+}
+#define CB_LDV(off) (ValT<V>::load(sm + (off)))
+#define CB_LDX(off) (*reinterpret_cast<const Acc*>(sm + (off)))
 
 // sm: base of the CTA's shared memory; so: offset of the unit's stage in it.
-__device__ void consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_t ident_off, Scratch& sc,
-                             int lane) {
+template <class V>
+__device__ void consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_t ident_off,
+                             Scratch<typename ValT<V>::Acc>& sc, int lane) {
+  using Acc = typename ValT<V>::Acc;
+  constexpr uint32_t kVs = sizeof(V), kXs = sizeof(Acc);
+  // byte offset of x[col] in the tile's x row for a coordinate byte b (col = b >> 4)
+  constexpr uint32_t kXShift = kXs == 8 ? 1 : 2, kXMask = 15u * kXs;
   uint8_t* S = sm + so;
   const CbUnit& u = *reinterpret_cast<const CbUnit*>(S + kOffUnit);
   const uint32_t T = u.ntiles;
@@ -263,9 +318,9 @@ __device__ void consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_
       vb = soff + align16u(rec.nnz);
       cb = soff;
     }
-    sc.tinfo[lane] = make_uint4(vb, cb, so + kOffXs + 128u * lane, 0u);
+    sc.tinfo[lane] = make_uint4(vb, cb, so + kOffXs + 16u * kXs * lane, 0u);
   }
-  for (uint32_t r = lane; r < R; r += 32) sc.srow[r] = 0.0;
+  for (uint32_t r = lane; r < R; r += 32) sc.srow[r] = Acc(0);
   __syncwarp();
 
   // 2. one run per lane: a sequence of chunks of up to three entries; even chunks go to
@@ -282,27 +337,27 @@ __device__ void consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_
   const bool hs = (h >> 8) & 1u;
   bool first = true, open = false;
   int32_t own_row = -1;
-  double own_val = 0.0;
-  double a0 = 0.0, a1 = 0.0;
+  Acc own_val = Acc(0);
+  Acc a0 = Acc(0), a1 = Acc(0);
   // Software pipeline: the operands of step i + 1 are loaded before the DFMAs of step i.
   // Loads are unconditional (a chunk shorter than three entries reads at most two entries
   // past its piece and column nibbles stay inside the tile's x row, so every address stays
   // in shared memory); the DFMA slots beyond the chunk's length are predicated off.
   uint32_t dA = 0, dB = 0;
-  double vA0 = 0, vA1 = 0, vA2 = 0, xA0 = 0, xA1 = 0, xA2 = 0;
-  double vB0 = 0, vB1 = 0, vB2 = 0, xB0 = 0, xB1 = 0, xB2 = 0;
+  Acc vA0 = 0, vA1 = 0, vA2 = 0, xA0 = 0, xA1 = 0, xA2 = 0;
+  Acc vB0 = 0, vB1 = 0, vB2 = 0, xB0 = 0, xB1 = 0, xB2 = 0;
 #define CB_LOAD_CHUNK(d, v0, v1, v2, x0, x1, x2)                                   \
   {                                                                                \
     const uint4 ti_ = sc.tinfo[(d) & 31u];                                         \
     const uint32_t o_ = ((d) >> 5) & 255u;                                         \
-    const uint32_t va_ = ti_.x + 8u * o_, ca_ = ti_.y + o_, xr_ = ti_.z;           \
+    const uint32_t va_ = ti_.x + kVs * o_, ca_ = ti_.y + o_, xr_ = ti_.z;          \
     const uint32_t b0_ = sm[ca_], b1_ = sm[ca_ + 1], b2_ = sm[ca_ + 2];            \
-    v0 = CB_LDD(va_);                                                              \
-    v1 = CB_LDD(va_ + 8u);                                                         \
-    v2 = CB_LDD(va_ + 16u);                                                        \
-    x0 = CB_LDD(xr_ + ((b0_ >> 1) & 0x78u));                                       \
-    x1 = CB_LDD(xr_ + ((b1_ >> 1) & 0x78u));                                       \
-    x2 = CB_LDD(xr_ + ((b2_ >> 1) & 0x78u));                                       \
+    v0 = CB_LDV(va_);                                                              \
+    v1 = CB_LDV(va_ + kVs);                                                        \
+    v2 = CB_LDV(va_ + 2u * kVs);                                                   \
+    x0 = CB_LDX(xr_ + ((b0_ >> kXShift) & kXMask));                                \
+    x1 = CB_LDX(xr_ + ((b1_ >> kXShift) & kXMask));                                \
+    x2 = CB_LDX(xr_ + ((b2_ >> kXShift) & kXMask));                                \
   }
   if (steps) {
     dA = desc[lane];
@@ -313,14 +368,14 @@ __device__ void consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_
   for (uint32_t i = 0; i < steps; ++i) {
     const uint32_t nb = (i + 1 < steps ? 2u * (i + 1) : 2u * i) * CB_VLANES;
     const uint32_t dA_n = desc[nb + lane], dB_n = desc[nb + CB_VLANES + lane];
-    double nvA0, nvA1, nvA2, nxA0, nxA1, nxA2, nvB0, nvB1, nvB2, nxB0, nxB1, nxB2;
+    Acc nvA0, nvA1, nvA2, nxA0, nxA1, nxA2, nvB0, nvB1, nvB2, nxB0, nxB1, nxB2;
     CB_LOAD_CHUNK(dA_n, nvA0, nvA1, nvA2, nxA0, nxA1, nxA2);
     CB_LOAD_CHUNK(dB_n, nvB0, nvB1, nvB2, nxB0, nxB1, nxB2);
     const uint32_t lA = (dA >> 13) & 3u, lB = (dB >> 13) & 3u;
     const bool eA = (dA & 0x8000u) != 0, eB = (dB & 0x8000u) != 0;
     // chunk B starts a new row when chunk A ends one: its chain then starts from zero
-    const double a1_old = a1;
-    double b = eA ? 0.0 : a1;
+    const Acc a1_old = a1;
+    Acc b = eA ? Acc(0) : a1;
     a0 = pfma(lA > 0, vA0, xA0, a0);
     b = pfma(lB > 0, vB0, xB0, b);
     a0 = pfma(lA > 1, vA1, xA1, a0);
@@ -330,21 +385,21 @@ __device__ void consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_
     a1 = b;
     if (lA | lB) open = true;
     if (eA) {                              // chunk A ends its row: a0 + (a1 before chunk B)
-      const double sum = a0 + a1_old;
+      const Acc sum = a0 + a1_old;
       if (first && hs) { own_row = (int32_t)row; own_val = sum; }
       else sc.srow[row] = sum;
       first = false;
-      a0 = 0.0;
+      a0 = Acc(0);
       open = lB != 0;
       row = nxt[row];
     }
     if (eB) {                              // chunk B ends its row
-      const double sum = a0 + a1;
+      const Acc sum = a0 + a1;
       if (first && hs) { own_row = (int32_t)row; own_val = sum; }
       else sc.srow[row] = sum;
       first = false;
-      a0 = 0.0;
-      a1 = 0.0;
+      a0 = Acc(0);
+      a1 = Acc(0);
       open = false;
       row = nxt[row];
     }
@@ -355,10 +410,10 @@ __device__ void consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_
   }
 #undef CB_LOAD_CHUNK
   sc.crow[lane] = nch == 0 ? -2 : (open ? (int32_t)row : -1);
-  sc.cval[lane] = open ? a0 + a1 : 0.0;
+  sc.cval[lane] = open ? a0 + a1 : Acc(0);
   __syncwarp();
   if (own_row >= 0) {
-    double sum = own_val;
+    Acc sum = own_val;
     for (int j = (int)lane - 1; j >= 0; --j) {
       const int32_t cr = sc.crow[j];
       if (cr == -2) continue;
@@ -369,25 +424,31 @@ __device__ void consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_
   }
   __syncwarp();
 
-  // 3. outputs
-  const double alpha = a.alpha, beta = a.beta;
+  // 3. outputs (alpha and beta in the accumulation type)
+  const Acc alpha = (Acc)a.alpha, beta = (Acc)a.beta;
+  Acc* y = static_cast<Acc*>(a.y);
   if (u.split < 0) {
     for (uint32_t r = lane; r < R; r += 32) {
       const int64_t gr = row0 + r;
-      double v = sc.srow[r];
+      Acc v = sc.srow[r];
       if (!a.alpha_one) v = alpha * v;
-      if (a.beta_nonzero) v = fma(beta, a.y[gr], v);
-      a.y[gr] = v;
+      if (a.beta_nonzero) v = fma(beta, y[gr], v);
+      y[gr] = v;
     }
   } else {
     // part of a block row cut into several units: 16 partial sums, added by combine_kernel
-    if (lane < 16) a.partial[(size_t)u.slot * 16 + lane] = (uint32_t)lane < R ? sc.srow[lane] : 0.0;
+    Acc* partial = static_cast<Acc*>(a.partial);
+    if (lane < 16) partial[(size_t)u.slot * 16 + lane] = (uint32_t)lane < R ? sc.srow[lane] : Acc(0);
   }
 }
+#undef CB_LDV
+#undef CB_LDX
 
-__global__ void __launch_bounds__(kThreads, 1) spmv_f64_kernel(const RunArgs a) {
+template <class V>
+__global__ void __launch_bounds__(kThreads, 1) spmv_kernel(const RunArgs a) {
+  using Acc = typename ValT<V>::Acc;
   extern __shared__ __align__(128) uint8_t smem_raw[];
-  Shared& sh = *reinterpret_cast<Shared*>(smem_raw);
+  Shared<Acc>& sh = *reinterpret_cast<Shared<Acc>*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t w0 = a.worker_off[blockIdx.x], w1 = a.worker_off[blockIdx.x + 1];
   const CbUnit* units = a.units + w0;   // this CTA's units, stored contiguously
@@ -409,7 +470,7 @@ __global__ void __launch_bounds__(kThreads, 1) spmv_f64_kernel(const RunArgs a) 
     loader(a, sh, units, nu, (uint32_t)warp, lane);
     return;
   }
-  Scratch& sc = sh.scratch[warp - kProducers];
+  Scratch<Acc>& sc = sh.scratch[warp - kProducers];
   const uint32_t ident_off = (uint32_t)(sh.ident - smem_raw);
   for (;;) {
     uint32_t j = 0;
@@ -424,7 +485,7 @@ __global__ void __launch_bounds__(kThreads, 1) spmv_f64_kernel(const RunArgs a) 
       if (lane == 0) set_error(a, 2u);
       break;
     }
-    consume_unit(a, smem_raw, (uint32_t)(sh.stage[s] - smem_raw), ident_off, sc, lane);
+    consume_unit<V>(a, smem_raw, (uint32_t)(sh.stage[s] - smem_raw), ident_off, sc, lane);
     __syncwarp();
     if (lane == 0) {
       __threadfence_block();
@@ -434,50 +495,64 @@ __global__ void __launch_bounds__(kThreads, 1) spmv_f64_kernel(const RunArgs a) 
 }
 
 // Adds the parts of every block row cut into several units, in part order, and writes y.
+template <class Acc>
 __global__ void __launch_bounds__(256) combine_kernel(const RunArgs a) {
   const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t sr = g >> 4, r = g & 15u;
   if (sr >= a.n_split_rows) return;
   const CbSplitRow s = a.split_rows[sr];
   if (r >= s.rows) return;
-  const double* p = a.partial + (size_t)s.slot0 * 16 + r;
-  double sum = 0.0;
+  const Acc* p = static_cast<const Acc*>(a.partial) + (size_t)s.slot0 * 16 + r;
+  Acc sum = Acc(0);
   for (uint32_t k = 0; k < s.nparts; ++k) sum += p[(size_t)k * 16];
   const int64_t gr = (int64_t)s.brow * CB_BLK + r;
-  double v = a.alpha_one ? sum : a.alpha * sum;
-  if (a.beta_nonzero) v = fma(a.beta, a.y[gr], v);
-  a.y[gr] = v;
+  Acc* y = static_cast<Acc*>(a.y);
+  Acc v = a.alpha_one ? sum : (Acc)a.alpha * sum;
+  if (a.beta_nonzero) v = fma((Acc)a.beta, y[gr], v);
+  y[gr] = v;
 }
 
-}  // namespace
-
-size_t spmv_f64_smem_bytes() { return sizeof(Shared); }
-int spmv_f64_threads() { return kThreads; }
-
-cudaError_t launch_spmv_f64(const RunArgs& a, int grid, cudaStream_t stream, cudaEvent_t* ev) {
+template <class V>
+cudaError_t launch_typed(const RunArgs& a, int grid, cudaStream_t stream, cudaEvent_t* ev) {
+  using Acc = typename ValT<V>::Acc;
   static bool configured[64] = {false};
-  const size_t smem = sizeof(Shared);
+  const size_t smem = sizeof(Shared<Acc>);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64 || !configured[dev]) {
-    e = cudaFuncSetAttribute(spmv_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(spmv_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) configured[dev] = true;
   }
   if (ev && (e = cudaEventRecord(ev[0], stream)) != cudaSuccess) return e;
-  spmv_f64_kernel<<<grid, kThreads, smem, stream>>>(a);
+  spmv_kernel<V><<<grid, kThreads, smem, stream>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[1], stream)) != cudaSuccess) return e;
   if (a.n_split_rows) {
     const uint32_t threads = 16u * a.n_split_rows;
-    combine_kernel<<<(threads + 255) / 256, 256, 0, stream>>>(a);
+    combine_kernel<Acc><<<(threads + 255) / 256, 256, 0, stream>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   if (ev) e = cudaEventRecord(ev[2], stream);
   return e;
+}
+
+}  // namespace
+
+size_t spmv_smem_bytes() { return sizeof(Shared<double>) > sizeof(Shared<float>) ? sizeof(Shared<double>) : sizeof(Shared<float>); }
+int spmv_threads() { return kThreads; }
+
+cudaError_t launch_spmv(const RunArgs& a, int grid, cudaStream_t stream, cudaEvent_t* ev) {
+  switch (a.value_dtype) {
+    case CBSPMV_F64: return launch_typed<double>(a, grid, stream, ev);
+    case CBSPMV_F32: return launch_typed<float>(a, grid, stream, ev);
+    case CBSPMV_BF16: return launch_typed<__nv_bfloat16>(a, grid, stream, ev);
+    case CBSPMV_F16: return launch_typed<__half>(a, grid, stream, ev);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace cb

@@ -59,8 +59,9 @@ extern "C" cbspmv_status_t cbspmv_run_noalloc(cbspmv_handle_t h, const void* x, 
     cb::set_last_error("NULL x or y");
     return CBSPMV_ERR_INVALID;
   }
-  if (((uintptr_t)x & 7) || ((uintptr_t)y & 7)) {
-    cb::set_last_error("x and y must be 8-byte aligned");
+  const uintptr_t es = p.value_dtype == CBSPMV_F64 ? 8 : 4;   // x, y element size
+  if (((uintptr_t)x & (es - 1)) || ((uintptr_t)y & (es - 1))) {
+    cb::set_last_error("x and y must be aligned to their element size");
     return CBSPMV_ERR_INVALID;
   }
   int prev = -1;
@@ -88,14 +89,14 @@ extern "C" cbspmv_status_t cbspmv_run_noalloc(cbspmv_handle_t h, const void* x, 
     // Every slot a run reads was written earlier in the same run, so the array's previous
     // contents never matter and nothing needs clearing.
     cb::RunArgs a = v.args;
-    a.x = (const double*)x;
-    a.y = (double*)y;
-    a.partial = (double*)base;
+    a.x = x;
+    a.y = y;
+    a.partial = base;
     a.alpha = alpha;
     a.beta = beta;
     a.alpha_one = alpha == 1.0;
     a.beta_nonzero = beta != 0.0;
-    e = cb::launch_spmv_f64(a, v.grid, (cudaStream_t)stream);
+    e = cb::launch_spmv(a, v.grid, (cudaStream_t)stream);
     if (e != cudaSuccess) {
       cb::set_last_error(std::string("cbspmv_run_noalloc: ") + cudaGetErrorString(e));
       st = CBSPMV_ERR_CUDA;
