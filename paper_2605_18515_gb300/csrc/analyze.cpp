@@ -394,6 +394,7 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
   });
 
   // --- step 4a: units of work
+  const uint32_t BMAX = CB_B_MAX_FOR(p.vsize);   // stream bytes per unit for this value size
   const uint32_t U = opts.unit_work > 0 ? std::min<uint32_t>((uint32_t)opts.unit_work, CB_UNIT_WORK_MAX)
                                         : CB_UNIT_WORK_DEFAULT;
   auto tile_work = [&](int64_t t) -> uint32_t { return p.tiles[t].fmt == CB_FMT_DENSE ? 256u : p.tiles[t].nnz; };
@@ -422,9 +423,9 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
     uint64_t W = 0, B = 0;
     for (int64_t t = t0; t < t1; ++t) { W += tile_work(t); B += tile_bytes(t); }
     int64_t T = t1 - t0;
-    bool big = W > U || B > CB_B_MAX || T > CB_T_MAX;
+    bool big = W > U || B > BMAX || T > CB_T_MAX;
     if (!big) {
-      if (have_open && open.work + W <= U && open.nbytes + B <= CB_B_MAX &&
+      if (have_open && open.work + W <= U && open.nbytes + B <= BMAX &&
           open.ntiles + T <= CB_T_MAX && open.nbr < CB_NBR_MAX) {
         open.ntiles = (uint16_t)(open.ntiles + T);
         open.nbr = (uint16_t)(open.nbr + 1);
@@ -448,7 +449,7 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
     }
     if (have_open) { finish_unit(open); have_open = false; }
     // cut the block row into parts of about equal work within the unit limits
-    uint64_t nparts_est = std::max<uint64_t>({(W + U - 1) / U, (B + CB_B_MAX - 1) / CB_B_MAX,
+    uint64_t nparts_est = std::max<uint64_t>({(W + U - 1) / U, (B + BMAX - 1) / BMAX,
                                               (uint64_t)((T + CB_T_MAX - 1) / CB_T_MAX), 2});
     uint64_t target = (W + nparts_est - 1) / nparts_est;
     size_t first_unit = p.units.size();
@@ -456,7 +457,7 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
     u.tile_lo = (uint32_t)t0; u.nbr = 1; u.brow_lo = (uint32_t)b; u.split = split_id;
     for (int64_t t = t0; t < t1; ++t) {
       uint32_t wt = tile_work(t), bt = tile_bytes(t);
-      if (u.ntiles > 0 && (u.work + wt > U || u.nbytes + bt > CB_B_MAX || u.ntiles + 1 > CB_T_MAX ||
+      if (u.ntiles > 0 && (u.work + wt > U || u.nbytes + bt > BMAX || u.ntiles + 1 > CB_T_MAX ||
                            u.work >= target)) {
         finish_unit(u);
         CbUnit v{};
@@ -607,10 +608,10 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
 
   // every unit must fit one shared-memory stage of the kernel
   for (const CbUnit& u : p.units) {
-    if (u.nbytes > CB_B_MAX || u.ntiles > CB_T_MAX || u.rc_n > CB_RC_MAX || u.sched_bytes > CB_SCHED_MAX ||
+    if (u.nbytes > BMAX || u.ntiles > CB_T_MAX || u.rc_n > CB_RC_MAX || u.sched_bytes > CB_SCHED_MAX ||
         u.blob_bytes > 16u * CB_T_MAX + 4u * CB_RC_MAX + CB_SCHED_MAX ||
         u.nbr > CB_NBR_MAX || u.nbr == 0) {
-      *msg = "internal error: a unit exceeds the kernel's stage limits";
+      *msg = "internal error: a unit exceeds the run kernel buffer limits";
       return CBSPMV_ERR_INVALID;
     }
   }

@@ -32,7 +32,7 @@ struct RunArgs {
 };
 
 size_t spmv_smem_bytes();      // dynamic shared memory of the largest instantiation
-int spmv_threads();
+int spmv_warps(int value_dtype);   // worker warps per CTA of the run kernel for a value type
 // Launches the run kernel for a.value_dtype and, when the matrix has block rows cut into
 // several units, the kernel that adds their parts (two launches on `stream`). ev: NULL, or
 // three events recorded on `stream` before the run kernel, between the two launches and

@@ -99,12 +99,21 @@ struct CbSplitRow {
 #define CB_STEPS_MAX ((((CB_UNIT_WORK_MAX + CB_VLANES - 1) / CB_VLANES) + 1) & ~1)
 #define CB_SCHED_MAX (CB_SCHED_HDR(CB_R_MAX) + 2 * CB_VLANES * CB_STEPS_MAX)
 
-// Kernel geometry for the FP64 path (bytes of shared memory per stage and limits the
-// analyser must respect when it cuts units).
-#define CB_STAGES 13
-#define CB_CONSUMERS 8
-#define CB_B_MAX 8192           // stream bytes per unit
-#define CB_T_MAX 20             // tiles per unit
+// Limits the analyser must respect when it cuts units: every unit must fit one warp buffer
+// of the run kernel. (Each can be overridden at compile time for geometry sweeps.)
+#ifndef CB_B_MAX
+#define CB_B_MAX 8192           // stream bytes per unit, 8-byte values
+#endif
+#ifndef CB_B_MAX_4
+#define CB_B_MAX_4 6144         // stream bytes per unit, 4-byte values
+#endif
+#ifndef CB_B_MAX_2
+#define CB_B_MAX_2 4096         // stream bytes per unit, 2-byte values
+#endif
+#define CB_B_MAX_FOR(vsize) ((vsize) == 8 ? CB_B_MAX : (vsize) == 4 ? CB_B_MAX_4 : CB_B_MAX_2)
+#ifndef CB_T_MAX
+#define CB_T_MAX 20             // tiles per unit (at most 32: 5-bit tile field of a descriptor)
+#endif
 #define CB_NBR_MAX 8            // block rows per group unit
 #define CB_R_MAX (CB_NBR_MAX * CB_BLK)
 #define CB_RC_MAX (CB_T_MAX * 16 + 16)   // restore_cols entries per unit (incl. alignment)

@@ -8,32 +8,36 @@
 // The paper's kernel (Sec. 3.5, Algorithms 3 and 4) maps one sub-block to one warp,
 // preloads x into shared memory (plain tiles) or reads it through restore_cols
 // (aggregated tiles), reduces with warp shuffles and adds into y with atomics. On GB300
-// the FP64 pipe is the scarce unit (a warp-wide DFMA occupies it for ~19 cycles per SM
-// and lanes that are masked off cost the same), so this kernel keeps the data structure
-// and the per-tile decoding of the paper but reorganises the work:
+// the FP64 pipe is the scarce unit (a warp-wide DFMA issues once per 64 cycles on each SM
+// sub-partition, and lanes that are masked off cost the same), so this kernel keeps the
+// data structure and the per-tile decoding of the paper but reorganises the work:
 //
-//   * Persistent grid, one CTA per SM: kLoaders loader warps and CB_CONSUMERS consumer
-//     warps. Loaders stage each unit of work (a run of consecutive tiles) into a ring of
-//     CB_STAGES shared-memory stages with two bulk TMA copies (cp.async.bulk): the unit's
-//     packed records and its blob (tile records, restore_cols slice, lane schedule). They
-//     then gather the unit's x values into the stage with cp.async (the x preload of
-//     Algorithms 3/4, through restore_cols for aggregated tiles); mbarriers hand stages to
-//     the consumers and back. A consumer computes each tile's base addresses from its
-//     record (CSR row pointer, COO coordinate bytes of Algorithm 3, the fixed rows of
-//     Algorithm 4).
-//   * The analyser's lane schedule cuts the unit's entries, in row-major order, into
-//     chunks of at most CB_CHUNK entries of one (tile, row) piece and deals them to the
-//     32 lanes in equal runs. Every lane then runs the same number of steps; a step reads
-//     one 16-bit chunk descriptor, decodes up to three coordinate bytes and issues up to
-//     three DFMAs into the lane's row accumulator. No FP64 work is spent on reductions:
-//     a row sum is stored when its last chunk is done.
+//   * Persistent grid, one CTA per SM; every warp of the CTA is an independent worker
+//     with its own shared-memory buffer (as many warps as buffers fit in shared memory).
+//     A warp takes the next unit of work of its CTA (a run of consecutive tiles; the
+//     CTA's unit list comes from the load balance of Algorithm 2), stages it with two
+//     bulk TMA copies (cp.async.bulk: the unit's packed records and its blob of tile
+//     records, restore_cols slice and lane schedule) completing on the warp's mbarrier,
+//     gathers the unit's x values into its buffer with cp.async (the x preload of
+//     Algorithms 3/4, through restore_cols for aggregated tiles) and computes. Warps never
+//     wait for one another: the latency of one warp's copies is hidden by the other
+//     warps' arithmetic, and the descriptor of a warp's next unit is fetched while it
+//     computes the current one.
+//   * A warp computes each tile's base addresses from its record (CSR row pointer, COO
+//     coordinate bytes of Algorithm 3, the fixed rows of Algorithm 4). The analyser's lane
+//     schedule cuts the unit's entries, in row-major order, into chunks of at most CB_CHUNK
+//     entries of one (tile, row) piece and deals them to the 32 lanes in equal runs. Every
+//     lane then runs the same number of steps; a step reads one 16-bit chunk descriptor,
+//     decodes up to three coordinate bytes and issues up to three FMAs into the lane's row
+//     accumulator. No FMA slot is spent on reductions: a row sum is stored when its last
+//     chunk is done.
 //   * Rows that cross run boundaries are completed by the run holding the row's end
 //     (adding the earlier runs' carries in a fixed order); units that cover whole block
 //     rows write y directly (no atomics, y read once when beta != 0). Block rows cut into
 //     several units store 16 partial sums per part; a second small kernel adds the parts
 //     in part order and writes y, so results do not depend on scheduling.
-//   * Every wait is bounded (clock64 budget); on expiry the kernel records an error code,
-//     drains its own copies in flight and returns.
+//   * The only wait is a warp's wait for its own bulk copies; it is bounded (clock64
+//     budget), and on expiry the kernel records an error code and returns.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -45,45 +49,73 @@
 namespace cb {
 namespace {
 
-constexpr int kStages = CB_STAGES;
-constexpr int kConsumers = CB_CONSUMERS;
-constexpr int kLoaders = 4;                       // warps 0..3: bulk copies and x gather
-constexpr int kProducers = kLoaders;
-constexpr int kThreads = 32 * (kProducers + kConsumers);
 constexpr long long kWaitBudget = 4000000000LL;   // clock64 cycles (~2 s) per wait
-
-// Stage layout (byte offsets): the unit descriptor, the unit's packed records, its blob
-// (tile records, restore_cols slice, lane schedule) and the gathered x values (16 per tile).
-constexpr uint32_t kOffUnit = 0;
-constexpr uint32_t kOffStream = 64;
-constexpr uint32_t kOffBlob = kOffStream + CB_B_MAX;
-constexpr uint32_t kBlobMax = 16 * CB_T_MAX + 4 * CB_RC_MAX + CB_SCHED_MAX;
-constexpr uint32_t kOffXs = kOffBlob + kBlobMax;
-constexpr uint32_t kStageBytes = (kOffXs + CB_T_MAX * 16 * 8 + 127) & ~127u;
-static_assert(sizeof(CbUnit) == 64, "unit descriptor slot");
-static_assert(kOffStream % 16 == 0 && kOffBlob % 16 == 0 && kOffXs % 16 == 0 && kBlobMax % 16 == 0,
-              "bulk copy destinations must be 16-byte aligned");
+constexpr uint32_t kSmemMax = 232448;             // dynamic shared memory per CTA (227 KB)
 
 // Stored value types: V is the storage type, Acc the type of x, y and the accumulators.
 template <class V> struct ValT;
+// load3: the three consecutive values starting at byte offset va of sm with two aligned
+// shared-memory loads (instead of three); it may read up to 4 bytes past the third value.
 template <> struct ValT<double> {
   using Acc = double;
   __device__ static __forceinline__ double load(const uint8_t* p) { return *reinterpret_cast<const double*>(p); }
+  __device__ static __forceinline__ void load3(const uint8_t* sm, uint32_t va, double& v0, double& v1, double& v2) {
+    const bool odd = (va & 8u) != 0;               // va is 8-byte aligned
+    const double2 p = *reinterpret_cast<const double2*>(sm + (odd ? va + 8u : va));
+    const double q = *reinterpret_cast<const double*>(sm + (odd ? va : va + 16u));
+    v0 = odd ? q : p.x;
+    v1 = odd ? p.x : p.y;
+    v2 = odd ? p.y : q;
+  }
 };
 template <> struct ValT<float> {
   using Acc = float;
   __device__ static __forceinline__ float load(const uint8_t* p) { return *reinterpret_cast<const float*>(p); }
+  __device__ static __forceinline__ void load3(const uint8_t* sm, uint32_t va, float& v0, float& v1, float& v2) {
+    const uint32_t b = va & ~7u;                   // va is 4-byte aligned
+    const float2 p = *reinterpret_cast<const float2*>(sm + b);
+    const float2 q = *reinterpret_cast<const float2*>(sm + b + 8u);
+    const bool odd = (va & 4u) != 0;
+    v0 = odd ? p.y : p.x;
+    v1 = odd ? q.x : p.y;
+    v2 = odd ? q.y : q.x;
+  }
 };
+// the three 16-bit values starting at byte offset va (2-byte aligned), from two aligned
+// 32-bit loads
+__device__ __forceinline__ void load3_u16(const uint8_t* sm, uint32_t va, uint32_t& h0, uint32_t& h1, uint32_t& h2) {
+  const uint32_t b = va & ~3u;
+  const uint32_t w0 = *reinterpret_cast<const uint32_t*>(sm + b);
+  const uint32_t w1 = *reinterpret_cast<const uint32_t*>(sm + b + 4u);
+  const bool odd = (va & 2u) != 0;
+  h0 = odd ? w0 >> 16 : w0 & 0xffffu;
+  h1 = odd ? w1 & 0xffffu : w0 >> 16;
+  h2 = odd ? w1 >> 16 : w1 & 0xffffu;
+}
 template <> struct ValT<__nv_bfloat16> {
   using Acc = float;
   __device__ static __forceinline__ float load(const uint8_t* p) {   // exact: bf16 is the top half of fp32
     return __uint_as_float((uint32_t)*reinterpret_cast<const uint16_t*>(p) << 16);
+  }
+  __device__ static __forceinline__ void load3(const uint8_t* sm, uint32_t va, float& v0, float& v1, float& v2) {
+    uint32_t h0, h1, h2;
+    load3_u16(sm, va, h0, h1, h2);
+    v0 = __uint_as_float(h0 << 16);
+    v1 = __uint_as_float(h1 << 16);
+    v2 = __uint_as_float(h2 << 16);
   }
 };
 template <> struct ValT<__half> {
   using Acc = float;
   __device__ static __forceinline__ float load(const uint8_t* p) {   // exact widening
     return __half2float(*reinterpret_cast<const __half*>(p));
+  }
+  __device__ static __forceinline__ void load3(const uint8_t* sm, uint32_t va, float& v0, float& v1, float& v2) {
+    uint32_t h0, h1, h2;
+    load3_u16(sm, va, h0, h1, h2);
+    v0 = __half2float(__ushort_as_half((unsigned short)h0));
+    v1 = __half2float(__ushort_as_half((unsigned short)h1));
+    v2 = __half2float(__ushort_as_half((unsigned short)h2));
   }
 };
 
@@ -95,22 +127,39 @@ struct Scratch {
   int32_t crow[CB_VLANES];      // per-run carry row (-1 none, -2 no chunks)
 };
 
-template <class Acc>
-struct Shared {
-  __align__(128) uint8_t stage[kStages][kStageBytes];
-  uint64_t bar_tma[kStages];    // bulk copies of the unit landed
-  uint64_t bar_full[kStages];   // x gathered (the 32 lanes of a loader)
-  // Exact hand-off words: the ticket whose copies were issued into the stage and the last
-  // ticket released from it. Loaders issue their tickets out of order, so a stage's
-  // barriers can be more than one phase behind a waiter; a waiter therefore first waits
-  // for the exact ticket here, after which the parity waits are unambiguous.
-  uint32_t issued[kStages];
-  uint32_t released[kStages];
-  Scratch<Acc> scratch[kConsumers];
+__host__ __device__ constexpr uint32_t align128(uint32_t v) { return (v + 127u) & ~127u; }
+
+// Per-CTA header: the Dense coordinate bytes and the CTA's unit ticket counter.
+struct CtaHeader {
   uint8_t ident[256];           // byte k = (k & 15) << 4: coordinate bytes of a Dense record
   uint32_t ticket;
-  uint32_t abort_flag;
 };
+constexpr uint32_t kHeaderBytes = align128(sizeof(CtaHeader));
+
+// Layout of one warp's buffer (byte offsets): the unit descriptor, the unit's packed
+// records, its blob (tile records, restore_cols slice, lane schedule), the gathered x
+// values (16 per tile), the warp's scratch and its mbarrier.
+template <class V>
+struct Geom {
+  using Acc = typename ValT<V>::Acc;
+  static constexpr uint32_t kBMax = CB_B_MAX_FOR(sizeof(V));
+  static constexpr uint32_t kOffUnit = 0;
+  static constexpr uint32_t kOffStream = 64;
+  static constexpr uint32_t kOffBlob = kOffStream + kBMax;
+  static constexpr uint32_t kBlobMax = 16 * CB_T_MAX + 4 * CB_RC_MAX + CB_SCHED_MAX;
+  static constexpr uint32_t kOffXs = kOffBlob + kBlobMax;
+  static constexpr uint32_t kOffScratch = align128(kOffXs + CB_T_MAX * 16 * (uint32_t)sizeof(Acc));
+  static constexpr uint32_t kOffBar = kOffScratch + (((uint32_t)sizeof(Scratch<Acc>) + 15u) & ~15u);
+  static constexpr uint32_t kWarpBytes = align128(kOffBar + 16);
+  static constexpr uint32_t kFit = (kSmemMax - kHeaderBytes) / kWarpBytes;
+  static constexpr int kWarps = kFit > 32 ? 32 : (int)kFit;
+  static constexpr uint32_t kSmem = kHeaderBytes + kWarps * kWarpBytes;
+  static_assert(kWarps >= 4, "warp buffers too large");
+  static_assert(kOffStream % 16 == 0 && kOffBlob % 16 == 0 && kOffXs % 16 == 0 && kBlobMax % 16 == 0,
+                "bulk copy destinations must be 16-byte aligned");
+};
+static_assert(sizeof(CbUnit) == 64, "unit descriptor slot");
+static_assert(CB_T_MAX <= 32 && (CB_T_MAX * 16) % 32 == 0, "tile count per unit");
 
 // ---- PTX helpers (mbarrier, bulk copy, cp.async) --------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -133,17 +182,6 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "r"(smem_u32(bar)), "r"(parity)
       : "memory");
   return ok != 0;
-}
-// Bounded wait until *p == v: false when the budget ran out.
-__device__ __forceinline__ bool wait_value(const uint32_t* p, uint32_t v) {
-  const volatile uint32_t* vp = p;
-  if (*vp == v) return true;
-  long long t0 = clock64();
-  while (*vp != v) {
-    __nanosleep(32);
-    if (clock64() - t0 > kWaitBudget) return false;
-  }
-  return true;
 }
 // Bounded wait: false when the budget ran out.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
@@ -171,99 +209,48 @@ __device__ __forceinline__ void cp_async_elem(uint32_t dst_smem, const void* src
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst_smem), "l"(src), "r"(src_bytes)
                  : "memory");
 }
-__device__ __forceinline__ void cp_async_arrive_noinc(uint64_t* bar) {
-  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t align16u(uint32_t v) { return (v + 15u) & ~15u; }
 
 __device__ void set_error(const RunArgs& a, uint32_t code) { atomicOr(a.err, code); }
 
-// ---- loader warps ------------------------------------------------------------------------
-// Loader l (l = 0 .. kLoaders-1) owns tickets l, l + kLoaders, ...: for each it stores the
-// unit descriptor in the stage and issues two bulk copies (packed records, unit blob) one
-// ticket ahead, then gathers the current ticket's x values with cp.async (all 16 per tile;
-// columns through restore_cols when aggregated) and signals the consumer through the
-// stage's full barrier. Bulk copies issued by one thread complete one after another, so
-// the copies are spread over several loader warps.
+// ---- staging of one unit by its warp ---------------------------------------------------
 __device__ __forceinline__ uint32_t load_desc_word(const CbUnit* units, uint32_t k, uint32_t nu, int lane) {
   return (k < nu && lane < 16) ? __ldg(reinterpret_cast<const uint32_t*>(units + k) + lane) : 0u;
 }
 
-template <class Acc>
-__device__ bool loader_issue(const RunArgs& a, Shared<Acc>& sh, uint32_t k, uint32_t dw, int lane) {
-  const uint32_t s = k % kStages;
-  // the stage's previous ticket (k - kStages) must have been released by its consumer
-  if (k >= (uint32_t)kStages && !wait_value(&sh.released[s], k - kStages)) return false;
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  uint8_t* S = sh.stage[s];
-  if (lane < 16) reinterpret_cast<uint32_t*>(S + kOffUnit)[lane] = dw;
-  __syncwarp();
-  if (lane == 0) {
-    *(volatile uint32_t*)&sh.issued[s] = k;
-    const CbUnit& u = *reinterpret_cast<const CbUnit*>(S + kOffUnit);
-    mbar_arrive_expect_tx(&sh.bar_tma[s], u.nbytes + u.blob_bytes);
-    if (u.nbytes) bulk_g2s(S + kOffStream, a.stream + (size_t)u.byte_lo16 * 16, u.nbytes, &sh.bar_tma[s]);
-    if (u.blob_bytes) bulk_g2s(S + kOffBlob, a.blob + (size_t)u.blob16 * 16, u.blob_bytes, &sh.bar_tma[s]);
-  }
-  __syncwarp();
-  return true;
-}
-
-template <class Acc>
-__device__ void loader(const RunArgs& a, Shared<Acc>& sh, const CbUnit* units, uint32_t nu, uint32_t l, int lane) {
+// Gathers the unit's x values into the warp's buffer: 16 per tile (column c of tile t at
+// index 16 t + c), x[restore_cols[xbase + c]] when aggregated, x[xbase + c] otherwise;
+// columns outside [0, n) (padding of the last block column) read as zero.
+template <class V>
+__device__ __forceinline__ void gather_x(const RunArgs& a, const uint8_t* W, uint32_t w_smem, int lane) {
+  using G = Geom<V>;
+  using Acc = typename G::Acc;
   constexpr int kPerLane = CB_T_MAX * 16 / 32;
   constexpr uint32_t kXs = sizeof(Acc);
   const Acc* x = static_cast<const Acc*>(a.x);
-  bool ok = true;
-  uint32_t next = l;                                      // next own ticket to issue
-  uint32_t dw = load_desc_word(units, next, nu, lane);    // its descriptor (16 lanes, one word each)
-  if (next < nu) {
-    ok = loader_issue(a, sh, next, dw, lane);
-    next += kLoaders;
-    dw = load_desc_word(units, next, nu, lane);
-  }
-  for (uint32_t j = l; j < nu && ok; j += kLoaders) {
-    const uint32_t s = j % kStages, q = j / kStages;
-    if (!mbar_wait(&sh.bar_tma[s], q & 1) || *(volatile uint32_t*)&sh.abort_flag) { ok = false; break; }
-    const uint8_t* S = sh.stage[s];
-    const CbUnit& u = *reinterpret_cast<const CbUnit*>(S + kOffUnit);
-    const CbTile* tiles = reinterpret_cast<const CbTile*>(S + kOffBlob);
-    const int32_t* rcols = reinterpret_cast<const int32_t*>(S + kOffBlob + 16u * u.ntiles);
-    const uint32_t xs_smem = smem_u32(S + kOffXs);
-    const uint32_t nx = 16u * u.ntiles, rc_lo = u.rc_lo;
-    int64_t col[kPerLane];
+  const CbUnit& u = *reinterpret_cast<const CbUnit*>(W + G::kOffUnit);
+  const CbTile* tiles = reinterpret_cast<const CbTile*>(W + G::kOffBlob);
+  const int32_t* rcols = reinterpret_cast<const int32_t*>(W + G::kOffBlob + 16u * u.ntiles);
+  const uint32_t nx = 16u * u.ntiles, rc_lo = u.rc_lo;
+  int64_t col[kPerLane];
 #pragma unroll
-    for (int k = 0; k < kPerLane; ++k) {
-      const uint32_t idx = (uint32_t)lane + 32u * k;
-      col[k] = -1;
-      if (idx < nx) {
-        const uint32_t xb = tiles[idx >> 4].xbase;
-        col[k] = a.aggregated ? (int64_t)rcols[xb - rc_lo + (idx & 15u)] : (int64_t)xb + (idx & 15u);
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < kPerLane; ++k) {
-      const uint32_t idx = (uint32_t)lane + 32u * k;
-      if (idx < nx) {
-        const bool valid = col[k] >= 0 && col[k] < a.n;
-        cp_async_elem<kXs>(xs_smem + kXs * idx, x + (valid ? col[k] : 0), valid ? kXs : 0u);
-      }
-    }
-    cp_async_arrive_noinc(&sh.bar_full[s]);
-    if (next < nu) {            // then keep one own ticket in flight ahead of the consumers
-      ok = loader_issue(a, sh, next, dw, lane);
-      next += kLoaders;
-      dw = load_desc_word(units, next, nu, lane);
+  for (int k = 0; k < kPerLane; ++k) {
+    const uint32_t idx = (uint32_t)lane + 32u * k;
+    col[k] = -1;
+    if (idx < nx) {
+      const uint32_t xb = tiles[idx >> 4].xbase;
+      col[k] = a.aggregated ? (int64_t)rcols[xb - rc_lo + (idx & 15u)] : (int64_t)xb + (idx & 15u);
     }
   }
-  if (!ok) {
-    if (lane == 0) set_error(a, 1u);
-    *(volatile uint32_t*)&sh.abort_flag = 1;
-    // drain: copies of this loader's tickets issued but not waited for
-    for (uint32_t k = l; k < next && k < nu; k += kLoaders)
-      if (k + kStages >= next) mbar_wait(&sh.bar_tma[k % kStages], (k / kStages) & 1);
+#pragma unroll
+  for (int k = 0; k < kPerLane; ++k) {
+    const uint32_t idx = (uint32_t)lane + 32u * k;
+    if (idx < nx) {
+      const bool valid = col[k] >= 0 && col[k] < a.n;
+      cp_async_elem<kXs>(w_smem + G::kOffXs + kXs * idx, x + (valid ? col[k] : 0), valid ? kXs : 0u);
+    }
   }
   cp_async_wait_all();
 }
@@ -282,7 +269,6 @@ __device__ __forceinline__ float pfma(bool p, float v, float x, float acc) {
       : "f"(v), "f"(x), "r"((uint32_t)p));
   return acc;
 }
-#define CB_LDV(off) (ValT<V>::load(sm + (off)))
 #define CB_LDX(off) (*reinterpret_cast<const Acc*>(sm + (off)))
 
 // sm: base of the CTA's shared memory; so: offset of the unit's stage in it.
@@ -290,6 +276,9 @@ template <class V>
 __device__ void consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_t ident_off,
                              Scratch<typename ValT<V>::Acc>& sc, int lane) {
   using Acc = typename ValT<V>::Acc;
+  using G = Geom<V>;
+  constexpr uint32_t kOffUnit = G::kOffUnit, kOffStream = G::kOffStream, kOffBlob = G::kOffBlob,
+                     kOffXs = G::kOffXs;
   constexpr uint32_t kVs = sizeof(V), kXs = sizeof(Acc);
   // byte offset of x[col] in the tile's x row for a coordinate byte b (col = b >> 4)
   constexpr uint32_t kXShift = kXs == 8 ? 1 : 2, kXMask = 15u * kXs;
@@ -340,9 +329,10 @@ __device__ void consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_
   Acc own_val = Acc(0);
   Acc a0 = Acc(0), a1 = Acc(0);
   // Software pipeline: the operands of step i + 1 are loaded before the DFMAs of step i.
-  // Loads are unconditional (a chunk shorter than three entries reads at most two entries
-  // past its piece and column nibbles stay inside the tile's x row, so every address stays
-  // in shared memory); the DFMA slots beyond the chunk's length are predicated off.
+  // Loads are unconditional (a chunk shorter than three entries reads at most two entries,
+  // plus up to 4 value bytes and 5 coordinate bytes of alignment slack, past its piece;
+  // column nibbles stay inside the tile's x row, so every address stays in the warp's
+  // buffer or the CTA header); the DFMA slots beyond the chunk's length are predicated off.
   uint32_t dA = 0, dB = 0;
   Acc vA0 = 0, vA1 = 0, vA2 = 0, xA0 = 0, xA1 = 0, xA2 = 0;
   Acc vB0 = 0, vB1 = 0, vB2 = 0, xB0 = 0, xB1 = 0, xB2 = 0;
@@ -351,10 +341,12 @@ __device__ void consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_
     const uint4 ti_ = sc.tinfo[(d) & 31u];                                         \
     const uint32_t o_ = ((d) >> 5) & 255u;                                         \
     const uint32_t va_ = ti_.x + kVs * o_, ca_ = ti_.y + o_, xr_ = ti_.z;          \
-    const uint32_t b0_ = sm[ca_], b1_ = sm[ca_ + 1], b2_ = sm[ca_ + 2];            \
-    v0 = CB_LDV(va_);                                                              \
-    v1 = CB_LDV(va_ + kVs);                                                        \
-    v2 = CB_LDV(va_ + 2u * kVs);                                                   \
+    const uint32_t cw_ = ca_ & ~3u;                                                \
+    const uint32_t cb_ = __funnelshift_r(*reinterpret_cast<const uint32_t*>(sm + cw_), \
+                                         *reinterpret_cast<const uint32_t*>(sm + cw_ + 4u), \
+                                         8u * (ca_ & 3u));                         \
+    const uint32_t b0_ = cb_ & 0xffu, b1_ = (cb_ >> 8) & 0xffu, b2_ = (cb_ >> 16) & 0xffu; \
+    ValT<V>::load3(sm, va_, v0, v1, v2);                                           \
     x0 = CB_LDX(xr_ + ((b0_ >> kXShift) & kXMask));                                \
     x1 = CB_LDX(xr_ + ((b1_ >> kXShift) & kXMask));                                \
     x2 = CB_LDX(xr_ + ((b2_ >> kXShift) & kXMask));                                \
@@ -441,56 +433,67 @@ __device__ void consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_
     if (lane < 16) partial[(size_t)u.slot * 16 + lane] = (uint32_t)lane < R ? sc.srow[lane] : Acc(0);
   }
 }
-#undef CB_LDV
 #undef CB_LDX
 
 template <class V>
-__global__ void __launch_bounds__(kThreads, 1) spmv_kernel(const RunArgs a) {
-  using Acc = typename ValT<V>::Acc;
+__global__ void __launch_bounds__(32 * Geom<V>::kWarps, 1) spmv_kernel(const RunArgs a) {
+  using G = Geom<V>;
+  using Acc = typename G::Acc;
   extern __shared__ __align__(128) uint8_t smem_raw[];
-  Shared<Acc>& sh = *reinterpret_cast<Shared<Acc>*>(smem_raw);
+  CtaHeader& hd = *reinterpret_cast<CtaHeader*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t w0 = a.worker_off[blockIdx.x], w1 = a.worker_off[blockIdx.x + 1];
   const CbUnit* units = a.units + w0;   // this CTA's units, stored contiguously
   const uint32_t nu = w1 - w0;
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
-      mbar_init(&sh.bar_tma[s], 1);
-      mbar_init(&sh.bar_full[s], 32);
-      sh.issued[s] = 0xffffffffu;
-      sh.released[s] = 0xffffffffu;
-    }
-    sh.ticket = 0;
-    sh.abort_flag = 0;
+  const uint32_t wo = kHeaderBytes + (uint32_t)warp * G::kWarpBytes;   // this warp's buffer
+  uint8_t* W = smem_raw + wo;
+  const uint32_t w_smem = smem_u32(W);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(W + G::kOffBar);
+  Scratch<Acc>& sc = *reinterpret_cast<Scratch<Acc>*>(W + G::kOffScratch);
+  if (threadIdx.x == 0) hd.ticket = 0;
+  for (uint32_t i = threadIdx.x; i < 256u; i += blockDim.x) hd.ident[i] = (uint8_t)((i & 15u) << 4);
+  if (lane == 0) {
+    mbar_init(bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (uint32_t i = threadIdx.x; i < 256u; i += blockDim.x) sh.ident[i] = (uint8_t)((i & 15u) << 4);
   __syncthreads();
-  if (warp < kLoaders) {
-    loader(a, sh, units, nu, (uint32_t)warp, lane);
-    return;
-  }
-  Scratch<Acc>& sc = sh.scratch[warp - kProducers];
-  const uint32_t ident_off = (uint32_t)(sh.ident - smem_raw);
-  for (;;) {
-    uint32_t j = 0;
-    if (lane == 0) j = atomicAdd(&sh.ticket, 1u);
-    j = __shfl_sync(0xffffffffu, j, 0);
-    if (j >= nu) break;
-    const uint32_t s = j % kStages, q = j / kStages;
-    bool ok = wait_value(&sh.issued[s], j);    // the stage now holds ticket j's copies
-    ok = ok && mbar_wait(&sh.bar_full[s], q & 1);
-    ok = ok && mbar_wait(&sh.bar_tma[s], q & 1);
-    if (!__all_sync(0xffffffffu, ok) || *(volatile uint32_t*)&sh.abort_flag) {
+  const uint32_t ident_off = (uint32_t)(hd.ident - smem_raw);
+  auto grab = [&]() -> uint32_t {
+    uint32_t t = 0;
+    if (lane == 0) t = atomicAdd(&hd.ticket, 1u);
+    return __shfl_sync(0xffffffffu, t, 0);
+  };
+  uint32_t phase = 0;
+  uint32_t j = grab();
+  uint32_t dw = load_desc_word(units, j, nu, lane);
+  while (j < nu) {
+    if (lane < 16) reinterpret_cast<uint32_t*>(W + G::kOffUnit)[lane] = dw;
+    __syncwarp();
+    // the next unit's descriptor is fetched while this one is staged and computed
+    const uint32_t jn = grab();
+    const uint32_t dwn = load_desc_word(units, jn, nu, lane);
+    if (lane == 0) {
+      // the buffer was last read and written through the generic proxy
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      const CbUnit& u = *reinterpret_cast<const CbUnit*>(W + G::kOffUnit);
+      mbar_arrive_expect_tx(bar, u.nbytes + u.blob_bytes);
+      if (u.nbytes) bulk_g2s(W + G::kOffStream, a.stream + (size_t)u.byte_lo16 * 16, u.nbytes, bar);
+      if (u.blob_bytes) bulk_g2s(W + G::kOffBlob, a.blob + (size_t)u.blob16 * 16, u.blob_bytes, bar);
+    }
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(bar, phase));
+    phase ^= 1u;
+    if (!ok) {
       if (lane == 0) set_error(a, 2u);
+      // the copies may still land in the buffer: give them a second bounded wait
+      mbar_wait(bar, phase ^ 1u);
       break;
     }
-    consume_unit<V>(a, smem_raw, (uint32_t)(sh.stage[s] - smem_raw), ident_off, sc, lane);
+    gather_x<V>(a, W, w_smem, lane);
     __syncwarp();
-    if (lane == 0) {
-      __threadfence_block();
-      *(volatile uint32_t*)&sh.released[s] = j;
-    }
+    consume_unit<V>(a, smem_raw, wo, ident_off, sc, lane);
+    __syncwarp();
+    j = jn;
+    dw = dwn;
   }
 }
 
@@ -516,7 +519,7 @@ template <class V>
 cudaError_t launch_typed(const RunArgs& a, int grid, cudaStream_t stream, cudaEvent_t* ev) {
   using Acc = typename ValT<V>::Acc;
   static bool configured[64] = {false};
-  const size_t smem = sizeof(Shared<Acc>);
+  const size_t smem = Geom<V>::kSmem;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -526,7 +529,7 @@ cudaError_t launch_typed(const RunArgs& a, int grid, cudaStream_t stream, cudaEv
     if (dev >= 0 && dev < 64) configured[dev] = true;
   }
   if (ev && (e = cudaEventRecord(ev[0], stream)) != cudaSuccess) return e;
-  spmv_kernel<V><<<grid, kThreads, smem, stream>>>(a);
+  spmv_kernel<V><<<grid, 32 * Geom<V>::kWarps, smem, stream>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[1], stream)) != cudaSuccess) return e;
@@ -542,8 +545,17 @@ cudaError_t launch_typed(const RunArgs& a, int grid, cudaStream_t stream, cudaEv
 
 }  // namespace
 
-size_t spmv_smem_bytes() { return sizeof(Shared<double>) > sizeof(Shared<float>) ? sizeof(Shared<double>) : sizeof(Shared<float>); }
-int spmv_threads() { return kThreads; }
+size_t spmv_smem_bytes() {
+  const uint32_t a = Geom<double>::kSmem, b = Geom<float>::kSmem, c = Geom<__half>::kSmem;
+  return a > b ? (a > c ? a : c) : (b > c ? b : c);
+}
+int spmv_warps(int value_dtype) {
+  switch (value_dtype) {
+    case CBSPMV_F64: return Geom<double>::kWarps;
+    case CBSPMV_F32: return Geom<float>::kWarps;
+    default: return Geom<__half>::kWarps;
+  }
+}
 
 cudaError_t launch_spmv(const RunArgs& a, int grid, cudaStream_t stream, cudaEvent_t* ev) {
   switch (a.value_dtype) {
