@@ -180,9 +180,14 @@ cbspmv_status_t cbspmv_analyze_batched(int count, const cbspmv_csr_t* A,
  * Y[i] = alpha[i] * A_i * X[i] + beta[i] * Y[i] with k[i] right-hand sides stored
  * column-major and packed (leading dimensions n_i and m_i); k may be NULL (one vector
  * each). Every problem's arguments are checked before any work is enqueued; a failing
- * check enqueues nothing and the message names the problem. The same handle may appear
- * more than once (its products then run one after another on the stream). This version
- * enqueues the problems' products in order. Errors: as cbspmv_run_multi. */
+ * check enqueues nothing and the message names the problem. All handles must belong to
+ * one device. The products of all problems run in one persistent launch of the run
+ * kernel per value type and per 64 products (each CTA works through its share of every
+ * problem, as given by each problem's load balance), plus one small launch that adds the
+ * parts of split block rows; a handle that appears more than once, or with k > 1, has its
+ * further products in further launches (they share its partial-sum buffer). Every
+ * product is computed exactly as cbspmv_run computes it, so results are bitwise equal to
+ * separate runs. Errors: as cbspmv_run_multi. */
 cbspmv_status_t cbspmv_run_batched(int count, const cbspmv_handle_t* h, const int* k,
                                    const void* const* X, void* const* Y, const double* alpha,
                                    const double* beta, void* stream);
@@ -216,6 +221,89 @@ cbspmv_status_t cbspmv_run_noalloc(cbspmv_handle_t h, const void* x, void* y, do
 cbspmv_status_t cbspmv_time_kernels(cbspmv_handle_t h, const void* x, void* y, double alpha,
                                     double beta, int reps, void* stream, double* ms_main,
                                     double* ms_combine, int* launches_per_run);
+
+/* ---- Serving (the paper has no serving system; it motivates its preprocessing cost by
+ * repeated products as in iterative solvers, Sec. 4.5) ---------------------------------
+ * A server keeps analysed matrices resident on one device and runs requests submitted
+ * from any host thread: y = alpha*A*x + beta*y products and CG solves of A x = b for
+ * symmetric positive definite A. A background engine thread admits queued requests in
+ * arrival order while a slot (max_inflight) and device memory (memory_budget, a pool the
+ * server allocates once) are free, and advances every in-flight request by one step per
+ * tick: the products of all in-flight requests run as one batched launch of the run kernel
+ * per value type (see cbspmv_run_batched), the CG vector steps as batched kernels. Each
+ * result is the same whether the request runs alone or among others.
+ * CG (mixed precision with FP64 refinement): r = b - A x and x += d in FP64 with the
+ * FP64-value product; each correction A d = r is solved by CG on cg_inner_dtype values
+ * (FP32 vectors and accumulation for the reduced types; FP64 for CBSPMV_F64) to
+ * inner_tol relative to its start; the solve ends when ||b - A x|| <= tol ||b|| (FP64). */
+typedef struct cbspmv_server_s* cbspmv_server_t;
+
+typedef struct {
+  int device;               /* CUDA device of the server and its matrices */
+  int64_t memory_budget;    /* bytes of request workspace (allocated at creation) */
+  int max_inflight;         /* requests in flight, 1..64 (1 = one request at a time) */
+  cbspmv_dtype_t cg_inner_dtype;  /* values of the inner CG product (default BF16) */
+  double inner_tol;         /* inner CG: stop at ||r|| <= inner_tol ||r0|| (default 1e-4) */
+  int inner_max_iter;       /* inner CG iterations per correction (default 2000) */
+  int max_outer;            /* refinement steps before a solve fails (default 30) */
+  int reserved[8];
+} cbspmv_server_opts_t;
+
+enum { CBSPMV_REQ_SPMV = 0, CBSPMV_REQ_CG = 1 };
+
+/* A request. SPMV: in = x (n doubles, host), out = y (m doubles, host; read first when
+ * beta != 0). CG: in = b (n doubles), out = x (n doubles), tol = relative residual
+ * target (e.g. 1e-8). Host buffers must stay valid until the request is done. */
+typedef struct {
+  int kind;
+  int matrix;               /* id from cbspmv_server_register */
+  const double* in;
+  double* out;
+  double alpha, beta;       /* SPMV only */
+  double tol;               /* CG only */
+  int reserved[4];
+} cbspmv_request_t;
+
+typedef struct {
+  int done;                 /* 1 when finished (out written) */
+  cbspmv_status_t status;   /* CBSPMV_OK, CBSPMV_ERR_TIMEOUT (CG did not converge within
+                               max_outer refinements) or CBSPMV_ERR_CUDA */
+  int iterations;           /* CG: inner iterations in total */
+  int refinements;          /* CG: FP64 refinement steps after the first residual */
+  double rel_residual;      /* CG: ||b - A x|| / ||b|| measured in FP64 at the end */
+  double t_submit, t_admit, t_done;   /* host steady-clock seconds */
+} cbspmv_result_t;
+
+typedef struct {
+  int64_t submitted, admitted, completed, ticks, launches;
+  int64_t max_inflight_seen, arena_used_max, arena_capacity, queued, inflight;
+} cbspmv_server_stats_t;
+
+/* Defaults: device 0, 4 GiB budget, 64 in flight, BF16 inner values, inner_tol 1e-4,
+ * 2000 inner iterations, 30 refinements. */
+cbspmv_status_t cbspmv_server_default_opts(cbspmv_server_opts_t* opts);
+/* Creates a server (allocates the memory budget, a stream and the engine thread).
+ * Errors: CBSPMV_ERR_INVALID (options), CBSPMV_ERR_OOM, CBSPMV_ERR_CUDA. */
+cbspmv_status_t cbspmv_server_create(const cbspmv_server_opts_t* opts, cbspmv_server_t* out);
+/* Analyses A (opts as cbspmv_analyze; device and value type are the server's) with FP64
+ * values and, for a square A, also with cg_inner_dtype values; the matrices stay
+ * resident until cbspmv_server_destroy. *matrix_id names it in requests (at most 1024). */
+cbspmv_status_t cbspmv_server_register(cbspmv_server_t s, const cbspmv_csr_t* A,
+                                       const cbspmv_opts_t* opts, int* matrix_id);
+/* Queues a request; *ticket identifies it. Errors: CBSPMV_ERR_INVALID (unknown matrix,
+ * NULL buffers, CG on a non-square matrix, tol <= 0), CBSPMV_ERR_CUDA (engine stopped). */
+cbspmv_status_t cbspmv_server_submit(cbspmv_server_t s, const cbspmv_request_t* req,
+                                     uint64_t* ticket);
+/* Non-blocking: *res = the request's state (res->done = 0 while it runs). A finished
+ * request's ticket is released by the call that reports it done. */
+cbspmv_status_t cbspmv_server_poll(cbspmv_server_t s, uint64_t ticket, cbspmv_result_t* res);
+/* Waits up to timeout_ms for the request; CBSPMV_ERR_TIMEOUT if it is still running (the
+ * ticket stays valid). */
+cbspmv_status_t cbspmv_server_wait(cbspmv_server_t s, uint64_t ticket, int timeout_ms,
+                                   cbspmv_result_t* res);
+cbspmv_status_t cbspmv_server_get_stats(cbspmv_server_t s, cbspmv_server_stats_t* stats);
+/* Stops the engine (requests still queued or in flight are abandoned), frees everything. */
+cbspmv_status_t cbspmv_server_destroy(cbspmv_server_t s);
 
 /* Reads the handle's device error word (set by bounded device-side waits that gave up)
  * and clears it: CBSPMV_OK or CBSPMV_ERR_TIMEOUT. Synchronises `stream`. */

@@ -58,6 +58,33 @@ class Stats(ctypes.Structure):
                 ("tb8_load_std", ctypes.c_double), ("analyze_ms", ctypes.c_double)]
 
 
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("memory_budget", ctypes.c_int64), ("max_inflight", ctypes.c_int),
+                ("cg_inner_dtype", ctypes.c_int), ("inner_tol", ctypes.c_double),
+                ("inner_max_iter", ctypes.c_int), ("max_outer", ctypes.c_int),
+                ("reserved", ctypes.c_int * 8)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("matrix", ctypes.c_int), ("inp", ctypes.c_void_p),
+                ("out", ctypes.c_void_p), ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
+                ("tol", ctypes.c_double), ("reserved", ctypes.c_int * 4)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("done", ctypes.c_int), ("status", ctypes.c_int), ("iterations", ctypes.c_int),
+                ("refinements", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "admitted", "completed", "ticks", "launches",
+                                              "max_inflight_seen", "arena_used_max", "arena_capacity",
+                                              "queued", "inflight")]
+
+
+REQ_SPMV, REQ_CG = 0, 1
+
 # Every entry point the header declares, with its ctypes signature.
 _P, _D, _I, _I64 = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int64
 SIGNATURES = {
@@ -75,6 +102,14 @@ SIGNATURES = {
     "cbspmv_export_blocked": [_P, _P, _P, _P, _P, _P, _P],
     "cbspmv_get_stats": [_P, ctypes.POINTER(Stats)],
     "cbspmv_destroy": [_P],
+    "cbspmv_server_default_opts": [ctypes.POINTER(ServerOpts)],
+    "cbspmv_server_create": [ctypes.POINTER(ServerOpts), ctypes.POINTER(_P)],
+    "cbspmv_server_register": [_P, ctypes.POINTER(Csr), ctypes.POINTER(Opts), ctypes.POINTER(_I)],
+    "cbspmv_server_submit": [_P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)],
+    "cbspmv_server_poll": [_P, ctypes.c_uint64, ctypes.POINTER(Result)],
+    "cbspmv_server_wait": [_P, ctypes.c_uint64, _I, ctypes.POINTER(Result)],
+    "cbspmv_server_get_stats": [_P, ctypes.POINTER(ServerStats)],
+    "cbspmv_server_destroy": [_P],
     "cbspmv_last_error": [],
     "cbspmv_version": [],
 }
@@ -350,6 +385,89 @@ def run_batched(mats, Xs, Ys, alphas, betas, *, stream=None):
     _check(lib().cbspmv_run_batched(count, ctypes.addressof(hs), ctypes.addressof(ks),
                                     ctypes.addressof(xp), ctypes.addressof(yp),
                                     ctypes.addressof(al), ctypes.addressof(be), _stream_ptr(stream)))
+
+
+class Server:
+    """A serving engine (cbspmv_server_*): resident matrices, requests from host arrays,
+    continuous batching of in-flight requests on the device."""
+
+    def __init__(self, device=0, memory_budget=4 << 30, max_inflight=64, cg_inner_dtype="bf16",
+                 inner_tol=1e-4, inner_max_iter=2000, max_outer=30):
+        o = ServerOpts()
+        _check(lib().cbspmv_server_default_opts(ctypes.byref(o)))
+        o.device, o.memory_budget, o.max_inflight = device, int(memory_budget), max_inflight
+        o.cg_inner_dtype = DTYPES[cg_inner_dtype]
+        o.inner_tol, o.inner_max_iter, o.max_outer = inner_tol, inner_max_iter, max_outer
+        self._s = ctypes.c_void_p(None)
+        _check(lib().cbspmv_server_create(ctypes.byref(o), ctypes.byref(self._s)))
+        self._keep: dict[int, tuple] = {}
+        self.shapes: list[tuple[int, int]] = []
+
+    def register(self, A, **opts) -> int:
+        csr, _keep, _ = _csr_struct(A)
+        o = _make_opts(**opts)
+        mid = ctypes.c_int()
+        _check(lib().cbspmv_server_register(self._s, ctypes.byref(csr), ctypes.byref(o), ctypes.byref(mid)))
+        self.shapes.append((int(A.m), int(A.n)))
+        return mid.value
+
+    def _shape(self, mid: int) -> tuple[int, int]:
+        # an unknown id is passed on for the library to reject
+        return self.shapes[mid] if 0 <= mid < len(self.shapes) else (1, 1)
+
+    def _submit(self, kind, mid, inp, out, alpha=1.0, beta=0.0, tol=0.0) -> int:
+        q = Request(kind, mid, inp.ctypes.data, out.ctypes.data, float(alpha), float(beta), float(tol))
+        t = ctypes.c_uint64()
+        _check(lib().cbspmv_server_submit(self._s, ctypes.byref(q), ctypes.byref(t)))
+        self._keep[t.value] = (inp, out)
+        return t.value
+
+    def submit_spmv(self, mid: int, x: np.ndarray, y: np.ndarray | None = None, alpha=1.0, beta=0.0):
+        """y <- alpha A x + beta y; returns (ticket, y)."""
+        m, n = self._shape(mid)
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        if y is None:
+            y = np.zeros(m, np.float64)
+        return self._submit(REQ_SPMV, mid, x, y, alpha, beta), y
+
+    def submit_cg(self, mid: int, b: np.ndarray, tol=1e-8):
+        """Solves A x = b to ||b - A x|| <= tol ||b||; returns (ticket, x)."""
+        m, n = self._shape(mid)
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.zeros(n, np.float64)
+        return self._submit(REQ_CG, mid, b, x, tol=tol), x
+
+    def wait(self, ticket: int, timeout_ms: int = 60000) -> dict:
+        r = Result()
+        st = lib().cbspmv_server_wait(self._s, ticket, int(timeout_ms), ctypes.byref(r))
+        if st == CBSPMV_OK:
+            self._keep.pop(ticket, None)
+        elif st != CBSPMV_ERR_TIMEOUT:
+            _check(st)
+        return {f: getattr(r, f) for f, _ in Result._fields_} | {"wait_status": st}
+
+    def poll(self, ticket: int) -> dict:
+        r = Result()
+        _check(lib().cbspmv_server_poll(self._s, ticket, ctypes.byref(r)))
+        if r.done:
+            self._keep.pop(ticket, None)
+        return {f: getattr(r, f) for f, _ in Result._fields_}
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().cbspmv_server_get_stats(self._s, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if self._s and self._s.value:
+            _check(lib().cbspmv_server_destroy(self._s))
+            self._s = ctypes.c_void_p(None)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def version() -> str:

@@ -234,10 +234,8 @@ cbspmv_status_t cbspmv_analyze(const cbspmv_csr_t* A, const cbspmv_opts_t* opts_
   return ok();
 }
 
-static cbspmv_status_t run_device(cbspmv_handle_t h, const void* x, void* y, double alpha, double beta,
-                                  cudaStream_t s, cudaEvent_t* ev = nullptr) {
+static cb::RunArgs run_args(cbspmv_handle_t h, const void* x, void* y, double alpha, double beta) {
   const cb::Plan& p = h->plan;
-  if (p.m == 0) return ok();
   cb::RunArgs a{};
   a.stream = h->d_stream;
   a.tiles = h->d_tiles;
@@ -260,7 +258,13 @@ static cbspmv_status_t run_device(cbspmv_handle_t h, const void* x, void* y, dou
   a.alpha_one = alpha == 1.0;
   a.beta_nonzero = beta != 0.0;
   a.value_dtype = p.value_dtype;
-  CB_CUDA(cb::launch_spmv(a, h->grid, s, ev));
+  return a;
+}
+
+static cbspmv_status_t run_device(cbspmv_handle_t h, const void* x, void* y, double alpha, double beta,
+                                  cudaStream_t s, cudaEvent_t* ev = nullptr) {
+  if (h->plan.m == 0) return ok();
+  CB_CUDA(cb::launch_spmv(run_args(h, x, y, alpha, beta), h->grid, s, ev));
   return ok();
 }
 
@@ -388,11 +392,41 @@ cbspmv_status_t cbspmv_run_batched(int count, const cbspmv_handle_t* hs, const i
     cbspmv_status_t st = check_run_args(h, ki, X[i], v ? h->plan.n : 0, Y[i], v ? h->plan.m : 0);
     if (st != CBSPMV_OK) return fail(st, "problem %d: %s", i, std::string(g_err).c_str());
   }
+  // One launch per (value type, round): round r holds the r-th product of every handle, so
+  // no handle's partial-sum buffer is used twice within a launch.
+  for (int i = 1; i < count; ++i)
+    if (hs[i]->device != hs[0]->device) return fail(CBSPMV_ERR_INVALID, "problems on different devices");
+  std::vector<std::vector<cb::RunArgs>> rounds;   // per round, all value types mixed
+  std::vector<std::pair<cbspmv_handle_t, int>> seen;
   for (int i = 0; i < count; ++i) {
     cbspmv_handle_t h = hs[i];
-    cbspmv_status_t st =
-        cbspmv_run_multi(h, k ? k[i] : 1, X[i], h->plan.n, Y[i], h->plan.m, alpha[i], beta[i], stream);
-    if (st != CBSPMV_OK) return fail(st, "problem %d: %s", i, std::string(g_err).c_str());
+    if (h->plan.m == 0) continue;
+    int occ = 0;
+    for (auto& sh : seen)
+      if (sh.first == h) occ = sh.second;
+    const int ki = k ? k[i] : 1;
+    const size_t es = h->esize();
+    for (int j = 0; j < ki; ++j) {
+      const int r = occ + j;
+      if ((int)rounds.size() <= r) rounds.resize(r + 1);
+      rounds[r].push_back(run_args(h, (const char*)X[i] + es * j * h->plan.n, (char*)Y[i] + es * j * h->plan.m,
+                                   alpha[i], beta[i]));
+    }
+    bool found = false;
+    for (auto& sh : seen)
+      if (sh.first == h) { sh.second += ki; found = true; }
+    if (!found) seen.push_back({h, ki});
+  }
+  if (rounds.empty()) return ok();
+  DeviceGuard g(hs[0]->device);
+  CB_CUDA(g.err);
+  for (auto& rd : rounds) {
+    for (int dt = CBSPMV_F64; dt <= CBSPMV_F16; ++dt) {
+      std::vector<cb::RunArgs> sel;
+      for (auto& a : rd)
+        if (a.value_dtype == dt) sel.push_back(a);
+      if (!sel.empty()) CB_CUDA(cb::launch_spmv_batch(sel.data(), (int)sel.size(), hs[0]->grid, (cudaStream_t)stream));
+    }
   }
   return ok();
 }
@@ -497,6 +531,17 @@ const char* cbspmv_version(void) { return "cbspmv 0.1 (sm_103a)"; }
 }  // extern "C"
 
 namespace cb {
+
+bool server_run_args(cbspmv_handle_t h, const void* x, void* y, double alpha, double beta, void* partial,
+                     RunArgs* out, int* grid, int* n_slots, int* value_dtype) {
+  if (!valid_handle(h)) return false;
+  *out = run_args(h, x, y, alpha, beta);
+  out->partial = partial;
+  *grid = h->grid;
+  *n_slots = h->plan.n_slots;
+  *value_dtype = h->plan.value_dtype;
+  return true;
+}
 
 bool noalloc_view(cbspmv_handle_t h, NoallocView* v) {
   if (!valid_handle(h)) return false;

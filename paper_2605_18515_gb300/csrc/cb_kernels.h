@@ -38,6 +38,10 @@ int spmv_warps(int value_dtype);   // worker warps per CTA of the run kernel for
 // three events recorded on `stream` before the run kernel, between the two launches and
 // after the last.
 cudaError_t launch_spmv(const RunArgs& a, int grid, cudaStream_t stream, cudaEvent_t* ev = nullptr);
+// Launches the products of `count` problems of one value type with one run-kernel launch
+// per 64 problems (plus one combine launch each when any has split block rows). The
+// problems must not share a partial-sum buffer (that is, come from distinct handles).
+cudaError_t launch_spmv_batch(const RunArgs* a, int count, int grid, cudaStream_t stream);
 
 }  // namespace cb
 #endif

@@ -129,10 +129,24 @@ struct Scratch {
 
 __host__ __device__ constexpr uint32_t align128(uint32_t v) { return (v + 127u) & ~127u; }
 
-// Per-CTA header: the Dense coordinate bytes and the CTA's unit ticket counter.
+// Products of one launch: up to kMaxP problems (matrix handle arrays, vectors, scalars)
+// passed by value as the kernel parameter. split_base: prefix sums of the problems' split
+// block rows (for the combine kernel).
+template <int kMaxP>
+struct BatchArgs {
+  int count;
+  uint32_t split_base[kMaxP + 1];
+  RunArgs p[kMaxP];
+};
+constexpr int kMaxBatch = 64;
+
+// Per-CTA header: the Dense coordinate bytes, the CTA's unit ticket counter and, for a
+// batch, the first unit and the ticket prefix of every problem in this CTA's lists.
 struct CtaHeader {
   uint8_t ident[256];           // byte k = (k & 15) << 4: coordinate bytes of a Dense record
   uint32_t ticket;
+  uint32_t first[kMaxBatch];    // this CTA's first unit of problem p
+  uint32_t pref[kMaxBatch + 1]; // tickets of problems 0..p-1
 };
 constexpr uint32_t kHeaderBytes = align128(sizeof(CtaHeader));
 
@@ -435,21 +449,27 @@ __device__ void consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_
 }
 #undef CB_LDX
 
-template <class V>
-__global__ void __launch_bounds__(32 * Geom<V>::kWarps, 1) spmv_kernel(const RunArgs a) {
+template <class V, int kMaxP>
+__global__ void __launch_bounds__(32 * Geom<V>::kWarps, 1) spmv_kernel(const __grid_constant__ BatchArgs<kMaxP> b) {
   using G = Geom<V>;
   using Acc = typename G::Acc;
   extern __shared__ __align__(128) uint8_t smem_raw[];
   CtaHeader& hd = *reinterpret_cast<CtaHeader*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t w0 = a.worker_off[blockIdx.x], w1 = a.worker_off[blockIdx.x + 1];
-  const CbUnit* units = a.units + w0;   // this CTA's units, stored contiguously
-  const uint32_t nu = w1 - w0;
   const uint32_t wo = kHeaderBytes + (uint32_t)warp * G::kWarpBytes;   // this warp's buffer
   uint8_t* W = smem_raw + wo;
   const uint32_t w_smem = smem_u32(W);
   uint64_t* bar = reinterpret_cast<uint64_t*>(W + G::kOffBar);
   Scratch<Acc>& sc = *reinterpret_cast<Scratch<Acc>*>(W + G::kOffScratch);
+  // this CTA's unit lists of the batch's problems (stored contiguously per CTA), one after
+  // another in ticket order
+  const int P = b.count;
+  if ((int)threadIdx.x < P) {
+    const RunArgs& a = b.p[threadIdx.x];
+    const uint32_t w0 = a.worker_off[blockIdx.x];
+    hd.first[threadIdx.x] = w0;
+    hd.pref[threadIdx.x + 1] = a.worker_off[blockIdx.x + 1] - w0;
+  }
   if (threadIdx.x == 0) hd.ticket = 0;
   for (uint32_t i = threadIdx.x; i < 256u; i += blockDim.x) hd.ident[i] = (uint8_t)((i & 15u) << 4);
   if (lane == 0) {
@@ -457,21 +477,43 @@ __global__ void __launch_bounds__(32 * Geom<V>::kWarps, 1) spmv_kernel(const Run
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
+  if (threadIdx.x == 0) {
+    hd.pref[0] = 0;
+    for (int q = 0; q < P; ++q) hd.pref[q + 1] += hd.pref[q];
+  }
+  __syncthreads();
+  const uint32_t total = hd.pref[P];
   const uint32_t ident_off = (uint32_t)(hd.ident - smem_raw);
   auto grab = [&]() -> uint32_t {
     uint32_t t = 0;
     if (lane == 0) t = atomicAdd(&hd.ticket, 1u);
     return __shfl_sync(0xffffffffu, t, 0);
   };
+  // problem of ticket t (t < total): the last q with pref[q] <= t
+  auto problem_of = [&](uint32_t t) -> int {
+    if (kMaxP == 1) return 0;
+    int lo = 0, hi = P - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (hd.pref[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+  };
+  auto desc_word = [&](uint32_t t) -> uint32_t {
+    if (t >= total) return 0u;
+    const int q = problem_of(t);
+    return load_desc_word(b.p[q].units + hd.first[q], t - hd.pref[q], 0xffffffffu, lane);
+  };
   uint32_t phase = 0;
   uint32_t j = grab();
-  uint32_t dw = load_desc_word(units, j, nu, lane);
-  while (j < nu) {
+  uint32_t dw = desc_word(j);
+  while (j < total) {
+    const RunArgs& a = b.p[problem_of(j)];
     if (lane < 16) reinterpret_cast<uint32_t*>(W + G::kOffUnit)[lane] = dw;
     __syncwarp();
     // the next unit's descriptor is fetched while this one is staged and computed
     const uint32_t jn = grab();
-    const uint32_t dwn = load_desc_word(units, jn, nu, lane);
+    const uint32_t dwn = desc_word(jn);
     if (lane == 0) {
       // the buffer was last read and written through the generic proxy
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -498,12 +540,22 @@ __global__ void __launch_bounds__(32 * Geom<V>::kWarps, 1) spmv_kernel(const Run
 }
 
 // Adds the parts of every block row cut into several units, in part order, and writes y.
-template <class Acc>
-__global__ void __launch_bounds__(256) combine_kernel(const RunArgs a) {
+template <class Acc, int kMaxP>
+__global__ void __launch_bounds__(256) combine_kernel(const __grid_constant__ BatchArgs<kMaxP> b) {
   const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-  const uint32_t sr = g >> 4, r = g & 15u;
-  if (sr >= a.n_split_rows) return;
-  const CbSplitRow s = a.split_rows[sr];
+  const uint32_t srg = g >> 4, r = g & 15u;
+  if (srg >= b.split_base[b.count]) return;
+  int q = 0;
+  if (kMaxP > 1) {
+    int lo = 0, hi = b.count - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (b.split_base[mid] <= srg) lo = mid; else hi = mid - 1;
+    }
+    q = lo;
+  }
+  const RunArgs& a = b.p[q];
+  const CbSplitRow s = a.split_rows[srg - b.split_base[q]];
   if (r >= s.rows) return;
   const Acc* p = static_cast<const Acc*>(a.partial) + (size_t)s.slot0 * 16 + r;
   Acc sum = Acc(0);
@@ -515,8 +567,8 @@ __global__ void __launch_bounds__(256) combine_kernel(const RunArgs a) {
   y[gr] = v;
 }
 
-template <class V>
-cudaError_t launch_typed(const RunArgs& a, int grid, cudaStream_t stream, cudaEvent_t* ev) {
+template <class V, int kMaxP>
+cudaError_t launch_typed(const BatchArgs<kMaxP>& b, int grid, cudaStream_t stream, cudaEvent_t* ev) {
   using Acc = typename ValT<V>::Acc;
   static bool configured[64] = {false};
   const size_t smem = Geom<V>::kSmem;
@@ -524,23 +576,35 @@ cudaError_t launch_typed(const RunArgs& a, int grid, cudaStream_t stream, cudaEv
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64 || !configured[dev]) {
-    e = cudaFuncSetAttribute(spmv_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(spmv_kernel<V, kMaxP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) configured[dev] = true;
   }
   if (ev && (e = cudaEventRecord(ev[0], stream)) != cudaSuccess) return e;
-  spmv_kernel<V><<<grid, 32 * Geom<V>::kWarps, smem, stream>>>(a);
+  spmv_kernel<V, kMaxP><<<grid, 32 * Geom<V>::kWarps, smem, stream>>>(b);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[1], stream)) != cudaSuccess) return e;
-  if (a.n_split_rows) {
-    const uint32_t threads = 16u * a.n_split_rows;
-    combine_kernel<Acc><<<(threads + 255) / 256, 256, 0, stream>>>(a);
+  const uint32_t nsplit = b.split_base[b.count];
+  if (nsplit) {
+    const uint32_t threads = 16u * nsplit;
+    combine_kernel<Acc, kMaxP><<<(threads + 255) / 256, 256, 0, stream>>>(b);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   if (ev) e = cudaEventRecord(ev[2], stream);
   return e;
+}
+
+template <int kMaxP>
+cudaError_t launch_dispatch(const BatchArgs<kMaxP>& b, int grid, cudaStream_t stream, cudaEvent_t* ev) {
+  switch (b.p[0].value_dtype) {
+    case CBSPMV_F64: return launch_typed<double, kMaxP>(b, grid, stream, ev);
+    case CBSPMV_F32: return launch_typed<float, kMaxP>(b, grid, stream, ev);
+    case CBSPMV_BF16: return launch_typed<__nv_bfloat16, kMaxP>(b, grid, stream, ev);
+    case CBSPMV_F16: return launch_typed<__half, kMaxP>(b, grid, stream, ev);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace
@@ -558,13 +622,30 @@ int spmv_warps(int value_dtype) {
 }
 
 cudaError_t launch_spmv(const RunArgs& a, int grid, cudaStream_t stream, cudaEvent_t* ev) {
-  switch (a.value_dtype) {
-    case CBSPMV_F64: return launch_typed<double>(a, grid, stream, ev);
-    case CBSPMV_F32: return launch_typed<float>(a, grid, stream, ev);
-    case CBSPMV_BF16: return launch_typed<__nv_bfloat16>(a, grid, stream, ev);
-    case CBSPMV_F16: return launch_typed<__half>(a, grid, stream, ev);
-    default: return cudaErrorInvalidValue;
+  BatchArgs<1> b;
+  b.count = 1;
+  b.split_base[0] = 0;
+  b.split_base[1] = a.n_split_rows;
+  b.p[0] = a;
+  return launch_dispatch<1>(b, grid, stream, ev);
+}
+
+cudaError_t launch_spmv_batch(const RunArgs* a, int count, int grid, cudaStream_t stream) {
+  for (int i = 0; i < count; ++i)
+    if (a[i].value_dtype != a[0].value_dtype) return cudaErrorInvalidValue;
+  for (int base = 0; base < count; base += kMaxBatch) {
+    const int c = count - base < kMaxBatch ? count - base : kMaxBatch;
+    static thread_local BatchArgs<kMaxBatch> b;
+    b.count = c;
+    b.split_base[0] = 0;
+    for (int i = 0; i < c; ++i) {
+      b.p[i] = a[base + i];
+      b.split_base[i + 1] = b.split_base[i] + a[base + i].n_split_rows;
+    }
+    const cudaError_t e = launch_dispatch<kMaxBatch>(b, grid, stream, nullptr);
+    if (e != cudaSuccess) return e;
   }
+  return cudaSuccess;
 }
 
 }  // namespace cb

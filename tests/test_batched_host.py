@@ -69,3 +69,23 @@ def test_run_calls_reject_host_only_handles(bd):
         assert st == bd.CBSPMV_ERR_INVALID
         assert "problem 0" in lib.cbspmv_last_error().decode()
         assert lib.cbspmv_run_batched(0, None, None, None, None, None, None, None) == bd.CBSPMV_OK
+
+
+def test_server_options_are_checked_without_a_device(bd):
+    import ctypes
+    o = bd.ServerOpts()
+    assert bd.lib().cbspmv_server_default_opts(ctypes.byref(o)) == bd.CBSPMV_OK
+    assert o.max_inflight == 64 and o.cg_inner_dtype == 2 and o.max_outer == 30
+    s = ctypes.c_void_p(None)
+    for field, bad in (("max_inflight", 0), ("max_inflight", 65), ("inner_tol", 0.0), ("max_outer", 0),
+                       ("memory_budget", 1024)):
+        o2 = bd.ServerOpts()
+        bd.lib().cbspmv_server_default_opts(ctypes.byref(o2))
+        setattr(o2, field, bad)
+        assert bd.lib().cbspmv_server_create(ctypes.byref(o2), ctypes.byref(s)) == bd.CBSPMV_ERR_INVALID
+        assert s.value is None
+    o.device = 9999                      # no such device: an error status, never a crash
+    assert bd.lib().cbspmv_server_create(ctypes.byref(o), ctypes.byref(s)) in (bd.CBSPMV_ERR_INVALID,
+                                                                               bd.CBSPMV_ERR_CUDA)
+    assert s.value is None
+    assert bd.lib().cbspmv_server_destroy(None) == bd.CBSPMV_OK
