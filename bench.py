@@ -189,6 +189,98 @@ def error_vs_fp64_oracle(A, x, y, n_rows: int = 20000):
             "sample": f"{rows.size} seeded rows, error / sum_k |a_ik x_k|"}
 
 
+# ---- serving: Poisson mix of y = Ax and CG solves over a resident pool ------------------------
+SERVE_POOLS = {
+    # SPD 3D 7-point Laplacians (CG and y = Ax) and R-MAT matrices (y = Ax only)
+    "small": {"lap": [32, 38, 44, 50, 56, 62], "rmat": [(14, 3), (15, 4), (16, 5)], "requests": 2000,
+              "baseline_requests": 300},
+    "full": {"lap": list(range(32, 129, 6)), "rmat": [(s, 3 + k) for s in range(16, 21) for k in range(3)],
+             "requests": 10000, "baseline_requests": 600},
+}
+
+
+def serve_pool(name):
+    from paper_2605_18515_gb300 import inputs as I
+    spec = SERVE_POOLS[name]
+    mats = [("lap%d" % g, I.laplacian3d(g), True) for g in spec["lap"]]
+    mats += [("rmat%d_%d" % (sc, sd), I.rmat(sc, 16, seed=sd), False) for sc, sd in spec["rmat"]]
+    return mats, spec
+
+
+def serve_run(bd, mats, n_req, rate, seed, **server_opts):
+    """Submits n_req requests (70% y = Ax on any pool matrix, 30% CG to 1e-8 on the SPD
+    ones) at Poisson arrival times of the given rate (req/s; inf = all at once) and returns
+    latency percentiles and throughput."""
+    import threading
+    rng = np.random.default_rng(seed)
+    spd = [i for i, m in enumerate(mats) if m[2]]
+    kinds = rng.random(n_req) < 0.3
+    picks = [int(rng.choice(spd)) if k else int(rng.integers(len(mats))) for k in kinds]
+    gaps = rng.exponential(1.0 / rate, n_req) if np.isfinite(rate) else np.zeros(n_req)
+    arrivals = np.cumsum(gaps)
+    inputs = {}
+    with bd.Server(**server_opts) as S:
+        ids = [S.register(A) for _, A, _ in mats]
+        for i, (_, A, _) in enumerate(mats):
+            inputs[i] = [np.random.default_rng(100 + 7 * i + j).uniform(-1, 1, A.n) for j in range(2)]
+        tickets = [None] * n_req
+        t0 = time.perf_counter()
+
+        def client():
+            for r in range(n_req):
+                dt = t0 + arrivals[r] - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                i = picks[r]
+                v = inputs[i][r & 1]
+                if kinds[r]:
+                    tickets[r] = (time.perf_counter(), S.submit_cg(ids[i], v, 1e-8)[0], True)
+                else:
+                    tickets[r] = (time.perf_counter(), S.submit_spmv(ids[i], v)[0], False)
+
+        th = threading.Thread(target=client)
+        th.start()
+        lat, worst_res, fails = [], 0.0, 0
+        t_last = t0
+        for r in range(n_req):
+            while tickets[r] is None:
+                time.sleep(0.0005)
+            t_sub, tk, is_cg = tickets[r]
+            res = S.wait(tk, 600000)
+            if res["status"] != 0:
+                fails += 1
+            lat.append(res["t_done"] - res["t_submit"])
+            if is_cg:
+                worst_res = max(worst_res, res["rel_residual"])
+        th.join()
+        t_end = time.perf_counter()
+        st = S.stats()
+    lat = np.sort(np.array(lat)) * 1e3
+    return {"requests": n_req, "req_per_s": round(n_req / (t_end - t0), 1),
+            "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
+            "mean_ms": round(float(lat.mean()), 3), "failed": fails, "cg_max_rel_residual": worst_res,
+            "max_inflight_seen": st["max_inflight_seen"], "ticks": st["ticks"], "launches": st["launches"]}
+
+
+def serve_bench(pool_name, seed=5):
+    from paper_2605_18515_gb300 import binding as bd
+    mats, spec = serve_pool(pool_name)
+    served_opts = dict(max_inflight=64, cg_inner_dtype="bf16", inner_tol=1e-4, memory_budget=8 << 30)
+    base_opts = dict(max_inflight=1, cg_inner_dtype="f64", inner_tol=1e-9, memory_budget=8 << 30)
+    cap = serve_run(bd, mats, spec["requests"], float("inf"), seed, **served_opts)
+    load = serve_run(bd, mats, spec["requests"], 0.7 * cap["req_per_s"], seed + 1, **served_opts)
+    bcap = serve_run(bd, mats, spec["baseline_requests"], float("inf"), seed, **base_opts)
+    bload = serve_run(bd, mats, spec["baseline_requests"], 0.7 * bcap["req_per_s"], seed + 1, **base_opts)
+    return {"pool": f"{len(spec['lap'])} SPD 3D Laplacians {spec['lap'][0]}^3..{spec['lap'][-1]}^3 + "
+                    f"{len(spec['rmat'])} R-MAT (scales {spec['rmat'][0][0]}-{spec['rmat'][-1][0]})",
+            "mix": "70% y=Ax (FP64), 30% CG to 1e-8 relative residual",
+            "served": {"mode": "continuous batching, 64 in flight, BF16-value CG with FP64 refinement",
+                       "capacity": cap, "poisson_at_70pct": load},
+            "one_at_a_time_fp64": {"mode": "one request at a time, FP64 products and FP64 CG",
+                                   "capacity": bcap, "poisson_at_70pct": bload},
+            "capacity_ratio": round(cap["req_per_s"] / max(bcap["req_per_s"], 1e-9), 2)}
+
+
 def run_reference(args, A, x, ws, rank):
     """The reference arm: the CPU oracle as it stands, on the host cores of this machine."""
     if rank != 0:
@@ -229,6 +321,9 @@ def main():
     ap.add_argument("--dist-steps", type=int, default=200, help="single steps timed one by one")
     ap.add_argument("--no-cusparse", action="store_true")
     ap.add_argument("--cusparse-steps", type=int, default=200)
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-full", action="store_true",
+                    help="serving measurement on the full pool (17 Laplacians, 15 R-MAT, 10,000 requests)")
     ap.add_argument("--traffic-bytes", type=float, default=None,
                     help="ncu DRAM bytes per launch of the timed kernel, if captured for this build")
     args = ap.parse_args()
@@ -394,6 +489,8 @@ def main():
             line["cpu_baseline"] = cpu
         if cus:
             line["cusparse_csr"] = cus
+        if not args.no_serve and ws == 1:
+            line["serving"] = serve_bench("full" if args.serve_full else "small")
         if err:
             line["error_vs_fp64_oracle"] = err
         print(json.dumps(line), flush=True)
