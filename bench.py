@@ -134,6 +134,27 @@ def oracle_sample_gflops(A, x, target_s: float = 12.0):
     return gf, f"{reps} full products of the {A.m}x{A.n} matrix ({A.nnz} nonzeros), {t_total:.1f} s"
 
 
+def multi_rhs_bench(M, A, x, vec, stream, ks=(1, 8, 32), reps=20):
+    """GFLOP/s of cbspmv_run_multi on k right-hand sides (column-major, ld = n / m)."""
+    import torch
+    out = []
+    for k in ks:
+        X = torch.from_numpy(np.tile(x.astype(vec), (k, 1))).cuda()
+        Y = torch.empty((k, A.m), dtype=X.dtype, device="cuda")
+        for _ in range(3):
+            M.run_multi(X, Y, stream=stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            M.run_multi(X, Y, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out.append({"k": k, "ms": round(ms, 4), "gflops": round(2.0 * A.nnz * k / (ms * 1e-3) / 1e9, 1)})
+        del X, Y
+    return out
+
+
 def step_distribution(run, stream, n: int, flush_buf=None):
     """Device time of n single steps, each between its own pair of events on the run's
     stream; with flush_buf, a buffer larger than L2 is overwritten before every step."""
@@ -207,10 +228,10 @@ def serve_pool(name):
     return mats, spec
 
 
-def serve_run(bd, mats, n_req, rate, seed, **server_opts):
-    """Submits n_req requests (70% y = Ax on any pool matrix, 30% CG to 1e-8 on the SPD
-    ones) at Poisson arrival times of the given rate (req/s; inf = all at once) and returns
-    latency percentiles and throughput."""
+def serve_run(S, ids, mats, n_req, rate, seed):
+    """Submits n_req requests to server S (70% y = Ax on any pool matrix, 30% CG to 1e-8
+    on the SPD ones) at Poisson arrival times of the given rate (req/s; inf = all at once)
+    and returns latency percentiles and throughput."""
     import threading
     rng = np.random.default_rng(seed)
     spd = [i for i, m in enumerate(mats) if m[2]]
@@ -218,59 +239,64 @@ def serve_run(bd, mats, n_req, rate, seed, **server_opts):
     picks = [int(rng.choice(spd)) if k else int(rng.integers(len(mats))) for k in kinds]
     gaps = rng.exponential(1.0 / rate, n_req) if np.isfinite(rate) else np.zeros(n_req)
     arrivals = np.cumsum(gaps)
-    inputs = {}
-    with bd.Server(**server_opts) as S:
-        ids = [S.register(A) for _, A, _ in mats]
-        for i, (_, A, _) in enumerate(mats):
-            inputs[i] = [np.random.default_rng(100 + 7 * i + j).uniform(-1, 1, A.n) for j in range(2)]
-        tickets = [None] * n_req
-        t0 = time.perf_counter()
+    inputs = {i: [np.random.default_rng(100 + 7 * i + j).uniform(-1, 1, A.n) for j in range(2)]
+              for i, (_, A, _) in enumerate(mats)}
+    st0 = S.stats()
+    tickets = [None] * n_req
+    t0 = time.perf_counter()
 
-        def client():
-            for r in range(n_req):
-                dt = t0 + arrivals[r] - time.perf_counter()
-                if dt > 0:
-                    time.sleep(dt)
-                i = picks[r]
-                v = inputs[i][r & 1]
-                if kinds[r]:
-                    tickets[r] = (time.perf_counter(), S.submit_cg(ids[i], v, 1e-8)[0], True)
-                else:
-                    tickets[r] = (time.perf_counter(), S.submit_spmv(ids[i], v)[0], False)
-
-        th = threading.Thread(target=client)
-        th.start()
-        lat, worst_res, fails = [], 0.0, 0
-        t_last = t0
+    def client():
         for r in range(n_req):
-            while tickets[r] is None:
-                time.sleep(0.0005)
-            t_sub, tk, is_cg = tickets[r]
-            res = S.wait(tk, 600000)
-            if res["status"] != 0:
-                fails += 1
-            lat.append(res["t_done"] - res["t_submit"])
-            if is_cg:
-                worst_res = max(worst_res, res["rel_residual"])
-        th.join()
-        t_end = time.perf_counter()
-        st = S.stats()
+            dt = t0 + arrivals[r] - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            i = picks[r]
+            v = inputs[i][r & 1]
+            if kinds[r]:
+                tickets[r] = (S.submit_cg(ids[i], v, 1e-8)[0], True)
+            else:
+                tickets[r] = (S.submit_spmv(ids[i], v)[0], False)
+
+    th = threading.Thread(target=client)
+    th.start()
+    lat, worst_res, fails = [], 0.0, 0
+    for r in range(n_req):
+        while tickets[r] is None:
+            time.sleep(0.0005)
+        tk, is_cg = tickets[r]
+        res = S.wait(tk, 600000)
+        if res["status"] != 0:
+            fails += 1
+        lat.append(res["t_done"] - res["t_submit"])
+        if is_cg:
+            worst_res = max(worst_res, res["rel_residual"])
+    th.join()
+    t_end = time.perf_counter()
+    st = S.stats()
     lat = np.sort(np.array(lat)) * 1e3
     return {"requests": n_req, "req_per_s": round(n_req / (t_end - t0), 1),
             "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
             "mean_ms": round(float(lat.mean()), 3), "failed": fails, "cg_max_rel_residual": worst_res,
-            "max_inflight_seen": st["max_inflight_seen"], "ticks": st["ticks"], "launches": st["launches"]}
+            "max_inflight_seen": st["max_inflight_seen"], "ticks": st["ticks"] - st0["ticks"],
+            "launches": st["launches"] - st0["launches"]}
+
+
+def serve_mode(bd, mats, n_req, seed, **server_opts):
+    """Burst capacity, then Poisson arrivals at 70% of it, on one server."""
+    with bd.Server(**server_opts) as S:
+        ids = [S.register(A) for _, A, _ in mats]
+        cap = serve_run(S, ids, mats, n_req, float("inf"), seed)
+        load = serve_run(S, ids, mats, n_req, 0.7 * cap["req_per_s"], seed + 1)
+    return cap, load
 
 
 def serve_bench(pool_name, seed=5):
     from paper_2605_18515_gb300 import binding as bd
     mats, spec = serve_pool(pool_name)
-    served_opts = dict(max_inflight=64, cg_inner_dtype="bf16", inner_tol=1e-4, memory_budget=8 << 30)
-    base_opts = dict(max_inflight=1, cg_inner_dtype="f64", inner_tol=1e-9, memory_budget=8 << 30)
-    cap = serve_run(bd, mats, spec["requests"], float("inf"), seed, **served_opts)
-    load = serve_run(bd, mats, spec["requests"], 0.7 * cap["req_per_s"], seed + 1, **served_opts)
-    bcap = serve_run(bd, mats, spec["baseline_requests"], float("inf"), seed, **base_opts)
-    bload = serve_run(bd, mats, spec["baseline_requests"], 0.7 * bcap["req_per_s"], seed + 1, **base_opts)
+    cap, load = serve_mode(bd, mats, spec["requests"], seed, max_inflight=64, cg_inner_dtype="bf16",
+                           inner_tol=1e-4, memory_budget=8 << 30)
+    bcap, bload = serve_mode(bd, mats, spec["baseline_requests"], seed, max_inflight=1, cg_inner_dtype="f64",
+                             inner_tol=1e-9, memory_budget=8 << 30)
     return {"pool": f"{len(spec['lap'])} SPD 3D Laplacians {spec['lap'][0]}^3..{spec['lap'][-1]}^3 + "
                     f"{len(spec['rmat'])} R-MAT (scales {spec['rmat'][0][0]}-{spec['rmat'][-1][0]})",
             "mix": "70% y=Ax (FP64), 30% CG to 1e-8 relative residual",
@@ -322,6 +348,7 @@ def main():
     ap.add_argument("--no-cusparse", action="store_true")
     ap.add_argument("--cusparse-steps", type=int, default=200)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-multi", action="store_true", help="skip the k right-hand-side measurement")
     ap.add_argument("--serve-full", action="store_true",
                     help="serving measurement on the full pool (17 Laplacians, 15 R-MAT, 10,000 requests)")
     ap.add_argument("--traffic-bytes", type=float, default=None,
@@ -403,6 +430,7 @@ def main():
         per_step_flushed = step_distribution(run1, stream, args.dist_steps, flush)
         del flush
         y_ours = yd.cpu().numpy().astype(np.float64)
+        multi = multi_rhs_bench(M, A, x, vec, stream) if not args.no_multi else None
         M.check_device(stream)
         sms = torch.cuda.get_device_properties(local).multi_processor_count
 
@@ -489,6 +517,8 @@ def main():
             line["cpu_baseline"] = cpu
         if cus:
             line["cusparse_csr"] = cus
+        if multi:
+            line["multi_rhs"] = {"api": "cbspmv_run_multi (passes of 4 vectors)", "results": multi}
         if not args.no_serve and ws == 1:
             line["serving"] = serve_bench("full" if args.serve_full else "small")
         if err:

@@ -160,10 +160,13 @@ cbspmv_status_t cbspmv_run_host(cbspmv_handle_t h, const void* x_host, void* y_h
  * n x k with leading dimension ldx >= n (column j at X + j * ldx); Y: device array,
  * column-major m x k with ldy >= m. Element type, alignment and the no-overlap rule
  * (between the whole spans of X and Y) are those of cbspmv_run; k = 0 does nothing.
- * Each column is computed exactly as cbspmv_run would (same summation order, so the
- * results are bitwise equal to k separate runs). This version enqueues one product per
- * column on `stream`. Errors: CBSPMV_ERR_INVALID (k < 0, ldx < n, ldy < m, NULL or
- * misaligned arrays, overlap), CBSPMV_ERR_CUDA. */
+ * The columns are computed in passes of 4 (then 2, then 1) vectors: each pass stages
+ * every unit of the matrix once and multiplies it into all its vectors, so the matrix is
+ * read ceil(k/4)-ish times instead of k times. Each column is computed exactly as
+ * cbspmv_run would (same summation order, so the results are bitwise equal to k separate
+ * runs). The first call with k > 1 allocates a partial-sum buffer for 4-vector passes,
+ * owned by the handle. Errors: CBSPMV_ERR_INVALID (k < 0, ldx < n, ldy < m, NULL or
+ * misaligned arrays, overlap), CBSPMV_ERR_OOM, CBSPMV_ERR_CUDA. */
 cbspmv_status_t cbspmv_run_multi(cbspmv_handle_t h, int k, const void* X, int64_t ldx, void* Y,
                                  int64_t ldy, double alpha, double beta, void* stream);
 
@@ -210,6 +213,38 @@ cbspmv_status_t cbspmv_run_batched(int count, const cbspmv_handle_t* h, const in
  * the handle's error word (cbspmv_check_device). */
 cbspmv_status_t cbspmv_run_noalloc(cbspmv_handle_t h, const void* x, void* y, double alpha,
                                    double beta, void* stream);
+
+/* ---- CUDA graphs (the paper has no counterpart) -------------------------------------------
+ * Captures the launches of cbspmv_run_batched with these arguments (same meaning and
+ * checks) into an instantiated CUDA graph; cbspmv_graph_launch replays them on a stream
+ * with one graph launch. The graph keeps the handles' device arrays and the X / Y
+ * pointers: replays read the current contents of X and overwrite Y. The handles must
+ * outlive the graph. Errors: those of cbspmv_run_batched, CBSPMV_ERR_CUDA. */
+typedef struct cbspmv_graph_s* cbspmv_graph_t;
+cbspmv_status_t cbspmv_graph_create(int count, const cbspmv_handle_t* h, const int* k,
+                                    const void* const* X, void* const* Y, const double* alpha,
+                                    const double* beta, cbspmv_graph_t* out);
+cbspmv_status_t cbspmv_graph_launch(cbspmv_graph_t g, void* stream);
+cbspmv_status_t cbspmv_graph_destroy(cbspmv_graph_t g);
+
+/* ---- Autotuned analysis ------------------------------------------------------------------
+ * The thresholds of Sec. 3.3 are heuristics (th0 0.15, th1 32, th2 128). This call analyses
+ * A with the given options, then varies one choice at a time, keeping the fastest so far:
+ * column aggregation (auto / off / on), unit size (512, 768 multiply-adds), then the format
+ * thresholds (th1, th2) = (16, 64) and (48, 192); each candidate is timed over `reps`
+ * products (1..10000) on the device. *out is the fastest handle; *rep (may be NULL)
+ * lists the candidates. base->device must be a device. Every handle computes the same
+ * product (only the layout differs). Errors: those of cbspmv_analyze, CBSPMV_ERR_CUDA. */
+typedef struct {
+  int n_tried;
+  double default_ms, best_ms;
+  int best_unit_work, best_col_agg, best_th1, best_th2;
+  double tried_ms[16];
+  int tried_unit_work[16], tried_col_agg[16], tried_th1[16], tried_th2[16];
+} cbspmv_tune_report_t;
+cbspmv_status_t cbspmv_analyze_tuned(const cbspmv_csr_t* A, const cbspmv_opts_t* base,
+                                     void* stream, int reps, cbspmv_handle_t* out,
+                                     cbspmv_tune_report_t* report);
 
 /* Measurement support (the paper has no counterpart): runs the product of cbspmv_run
  * `reps` times (1..100000) on `stream`, with CUDA events recorded on that stream around

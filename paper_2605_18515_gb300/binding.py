@@ -85,6 +85,14 @@ class ServerStats(ctypes.Structure):
 
 REQ_SPMV, REQ_CG = 0, 1
 
+class TuneReport(ctypes.Structure):
+    _fields_ = [("n_tried", ctypes.c_int), ("default_ms", ctypes.c_double), ("best_ms", ctypes.c_double),
+                ("best_unit_work", ctypes.c_int), ("best_col_agg", ctypes.c_int), ("best_th1", ctypes.c_int),
+                ("best_th2", ctypes.c_int), ("tried_ms", ctypes.c_double * 16),
+                ("tried_unit_work", ctypes.c_int * 16), ("tried_col_agg", ctypes.c_int * 16),
+                ("tried_th1", ctypes.c_int * 16), ("tried_th2", ctypes.c_int * 16)]
+
+
 # Every entry point the header declares, with its ctypes signature.
 _P, _D, _I, _I64 = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int64
 SIGNATURES = {
@@ -95,6 +103,11 @@ SIGNATURES = {
     "cbspmv_run_noalloc": [_P, _P, _P, _D, _D, _P],
     "cbspmv_run_multi": [_P, _I, _P, _I64, _P, _I64, _D, _D, _P],
     "cbspmv_time_kernels": [_P, _P, _P, _D, _D, _I, _P, _P, _P, _P],
+    "cbspmv_graph_create": [_I, _P, _P, _P, _P, _P, _P, ctypes.POINTER(_P)],
+    "cbspmv_graph_launch": [_P, _P],
+    "cbspmv_graph_destroy": [_P],
+    "cbspmv_analyze_tuned": [ctypes.POINTER(Csr), ctypes.POINTER(Opts), _P, _I, ctypes.POINTER(_P),
+                             ctypes.POINTER(TuneReport)],
     "cbspmv_analyze_batched": [_I, _P, ctypes.POINTER(Opts), _P, _P],
     "cbspmv_run_batched": [_I, _P, _P, _P, _P, _P, _P, _P],
     "cbspmv_check_device": [_P, _P],
@@ -366,25 +379,10 @@ def analyze_batched(mats, *, stream=None, **opts) -> list["BlockedMatrix"]:
 
 def run_batched(mats, Xs, Ys, alphas, betas, *, stream=None):
     """cbspmv_run_batched: problem i computes Ys[i] <- alphas[i]*A_i*Xs[i] + betas[i]*Ys[i].
-    Xs[i], Ys[i] are float64 CUDA tensors, 1-D (one vector) or (k_i, n_i) / (k_i, m_i)
-    contiguous (k_i vectors)."""
-    count = len(mats)
-    n1 = max(count, 1)
-    hs = (ctypes.c_void_p * n1)(*[M.handle for M in mats])
-    ks = (ctypes.c_int * n1)()
-    xp = (ctypes.c_void_p * n1)()
-    yp = (ctypes.c_void_p * n1)()
-    al = (ctypes.c_double * n1)(*[float(a) for a in alphas])
-    be = (ctypes.c_double * n1)(*[float(b) for b in betas])
-    for i, M in enumerate(mats):
-        X, Y = Xs[i], Ys[i]
-        k = 1 if X.dim() == 1 else int(X.shape[0])
-        ks[i] = k
-        xp[i] = _dev_ptr(X, k * M.n, f"X[{i}]", M.vec)
-        yp[i] = _dev_ptr(Y, k * M.m, f"Y[{i}]", M.vec)
-    _check(lib().cbspmv_run_batched(count, ctypes.addressof(hs), ctypes.addressof(ks),
-                                    ctypes.addressof(xp), ctypes.addressof(yp),
-                                    ctypes.addressof(al), ctypes.addressof(be), _stream_ptr(stream)))
+    Xs[i], Ys[i] are CUDA tensors of the matrix's vector type, 1-D (one vector) or
+    (k_i, n_i) / (k_i, m_i) contiguous (k_i vectors)."""
+    count, arrs = _batch_arrays(mats, Xs, Ys, alphas, betas)
+    _check(lib().cbspmv_run_batched(count, *[ctypes.addressof(a) for a in arrs], _stream_ptr(stream)))
 
 
 class Server:
@@ -468,6 +466,69 @@ class Server:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def _batch_arrays(mats, Xs, Ys, alphas, betas):
+    count = len(mats)
+    n1 = max(count, 1)
+    hs = (ctypes.c_void_p * n1)(*[M.handle for M in mats])
+    ks = (ctypes.c_int * n1)()
+    xp = (ctypes.c_void_p * n1)()
+    yp = (ctypes.c_void_p * n1)()
+    al = (ctypes.c_double * n1)(*[float(a) for a in alphas])
+    be = (ctypes.c_double * n1)(*[float(b) for b in betas])
+    for i, M in enumerate(mats):
+        X, Y = Xs[i], Ys[i]
+        k = 1 if X.dim() == 1 else int(X.shape[0])
+        ks[i] = k
+        xp[i] = _dev_ptr(X, k * M.n, f"X[{i}]", M.vec)
+        yp[i] = _dev_ptr(Y, k * M.m, f"Y[{i}]", M.vec)
+    return count, (hs, ks, xp, yp, al, be)
+
+
+class Graph:
+    """cbspmv_graph_*: the products of run_batched(mats, Xs, Ys, alphas, betas) captured into
+    a CUDA graph; launch() replays them (current X contents, Y overwritten)."""
+
+    def __init__(self, mats, Xs, Ys, alphas, betas):
+        count, arrs = _batch_arrays(mats, Xs, Ys, alphas, betas)
+        self._keep = (mats, Xs, Ys, arrs)
+        self._g = ctypes.c_void_p(None)
+        _check(lib().cbspmv_graph_create(count, *[ctypes.addressof(a) for a in arrs], ctypes.byref(self._g)))
+
+    def launch(self, stream=None):
+        _check(lib().cbspmv_graph_launch(self._g, _stream_ptr(stream)))
+
+    def close(self):
+        if self._g and self._g.value:
+            _check(lib().cbspmv_graph_destroy(self._g))
+            self._g = ctypes.c_void_p(None)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def analyze_tuned(A, *, reps=20, stream=None, **opts):
+    """cbspmv_analyze_tuned: the fastest of a few analysis options; returns
+    (BlockedMatrix, report dict)."""
+    csr, _keep, nnz = _csr_struct(A)
+    o = _make_opts(**opts)
+    h = ctypes.c_void_p(None)
+    rep = TuneReport()
+    _check(lib().cbspmv_analyze_tuned(ctypes.byref(csr), ctypes.byref(o), _stream_ptr(stream), int(reps),
+                                      ctypes.byref(h), ctypes.byref(rep)))
+    n = min(rep.n_tried, 16)
+    report = {"n_tried": rep.n_tried, "default_ms": rep.default_ms, "best_ms": rep.best_ms,
+              "best": {"unit_work": rep.best_unit_work, "col_agg": rep.best_col_agg, "th1": rep.best_th1,
+                       "th2": rep.best_th2},
+              "tried": [{"ms": rep.tried_ms[i], "unit_work": rep.tried_unit_work[i],
+                         "col_agg": rep.tried_col_agg[i], "th1": rep.tried_th1[i], "th2": rep.tried_th2[i]}
+                        for i in range(n)]}
+    M = BlockedMatrix._adopt(h.value, int(A.m), int(A.n), nnz, o.device, opts.get("value_dtype", "f64"))
+    return M, report
 
 
 def version() -> str:

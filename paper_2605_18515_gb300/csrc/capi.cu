@@ -78,6 +78,7 @@ struct cbspmv_handle_s {
   uint32_t* d_err = nullptr;
   void* d_xstage = nullptr;
   void* d_ystage = nullptr;
+  void* d_partial_multi = nullptr;   // partial sums of 4-vector passes (allocated on first use)
   // bytes of one x or y element: double for FP64 values, float for the reduced types
   size_t esize() const { return plan.value_dtype == CBSPMV_F64 ? 8 : 4; }
 
@@ -86,7 +87,7 @@ struct cbspmv_handle_s {
     DeviceGuard g(device);
     cudaDeviceSynchronize();
     void* ptrs[] = {d_stream, d_tiles, d_rcols, d_units, d_blob, d_wunits, d_woff, d_partial, d_split_rows,
-                    d_err, d_xstage, d_ystage};
+                    d_err, d_xstage, d_ystage, d_partial_multi};
     for (void* p : ptrs)
       if (p) cudaFree(p);
     d_stream = nullptr;
@@ -101,6 +102,7 @@ struct cbspmv_handle_s {
     d_err = nullptr;
     d_xstage = nullptr;
     d_ystage = nullptr;
+    d_partial_multi = nullptr;
   }
 };
 
@@ -258,6 +260,9 @@ static cb::RunArgs run_args(cbspmv_handle_t h, const void* x, void* y, double al
   a.alpha_one = alpha == 1.0;
   a.beta_nonzero = beta != 0.0;
   a.value_dtype = p.value_dtype;
+  a.nvec = 1;
+  a.ldx = p.n;
+  a.ldy = p.m;
   return a;
 }
 
@@ -350,11 +355,21 @@ cbspmv_status_t cbspmv_run_multi(cbspmv_handle_t h, int k, const void* X, int64_
   if (st != CBSPMV_OK || k == 0) return st;
   DeviceGuard g(h->device);
   CB_CUDA(g.err);
-  for (int j = 0; j < k; ++j) {
-    const size_t es = h->esize();
-    st = run_device(h, (const char*)X + es * j * ldx, (char*)Y + es * j * ldy, alpha, beta,
-                    (cudaStream_t)stream);
-    if (st != CBSPMV_OK) return st;
+  if (h->plan.m == 0) return ok();
+  const cb::Plan& p = h->plan;
+  const size_t es = h->esize();
+  if (k > 1 && !h->d_partial_multi)
+    CB_CUDA(cudaMalloc(&h->d_partial_multi, (size_t)(p.n_slots ? p.n_slots : 1) * 16 * 4 * es));
+  // passes of 4, then 2, then 1 vectors; each pass reads the matrix once
+  for (int j = 0; j < k;) {
+    const int nv = k - j >= 4 ? 4 : k - j >= 2 ? 2 : 1;
+    cb::RunArgs a = run_args(h, (const char*)X + es * j * ldx, (char*)Y + es * j * ldy, alpha, beta);
+    a.nvec = nv;
+    a.ldx = ldx;
+    a.ldy = ldy;
+    if (nv > 1) a.partial = h->d_partial_multi;
+    CB_CUDA(cb::launch_spmv(a, h->grid, (cudaStream_t)stream));
+    j += nv;
   }
   return ok();
 }
@@ -509,6 +524,195 @@ cbspmv_status_t cbspmv_export_blocked(cbspmv_handle_t h, int32_t* blk_row, int32
   return ok();
 }
 
+// ---- CUDA-graph captured products -------------------------------------------------------
+struct cbspmv_graph_s {
+  uint32_t magic = 0xCB56A401u;
+  int device = -1;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+cbspmv_status_t cbspmv_graph_create(int count, const cbspmv_handle_t* hs, const int* k, const void* const* X,
+                                    void* const* Y, const double* alpha, const double* beta, cbspmv_graph_t* out) {
+  if (!out) return fail(CBSPMV_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (count < 1 || !hs) return fail(CBSPMV_ERR_INVALID, "count must be >= 1");
+  for (int i = 0; i < count; ++i)
+    if (!valid_handle(hs[i]) || hs[i]->device < 0) return fail(CBSPMV_ERR_INVALID, "problem %d: invalid or host-only handle", i);
+  DeviceGuard g(hs[0]->device);
+  CB_CUDA(g.err);
+  CB_CUDA(cb::configure_kernels());
+  cudaStream_t s = nullptr;
+  CB_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  auto* G = new (std::nothrow) cbspmv_graph_s();
+  if (!G) {
+    cudaStreamDestroy(s);
+    return fail(CBSPMV_ERR_OOM, "host allocation failed");
+  }
+  G->device = hs[0]->device;
+  cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+  cbspmv_status_t st = CBSPMV_OK;
+  std::string msg;
+  if (e == cudaSuccess) {
+    st = cbspmv_run_batched(count, hs, k, X, Y, alpha, beta, s);
+    msg = g_err;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(s, &graph);
+    G->graph = graph;
+    if (st == CBSPMV_OK && e2 != cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess && st == CBSPMV_OK) e = cudaGraphInstantiate(&G->exec, G->graph, 0);
+  cudaStreamDestroy(s);
+  if (e != cudaSuccess || st != CBSPMV_OK) {
+    if (G->exec) cudaGraphExecDestroy(G->exec);
+    if (G->graph) cudaGraphDestroy(G->graph);
+    delete G;
+    if (st != CBSPMV_OK) return fail(st, "%s", msg.c_str());
+    return fail(CBSPMV_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+  }
+  *out = G;
+  return ok();
+}
+
+cbspmv_status_t cbspmv_graph_launch(cbspmv_graph_t G, void* stream) {
+  if (!G || G->magic != 0xCB56A401u) return fail(CBSPMV_ERR_INVALID, "invalid graph");
+  DeviceGuard g(G->device);
+  CB_CUDA(g.err);
+  CB_CUDA(cudaGraphLaunch(G->exec, (cudaStream_t)stream));
+  return ok();
+}
+
+cbspmv_status_t cbspmv_graph_destroy(cbspmv_graph_t G) {
+  if (!G) return ok();
+  if (G->magic != 0xCB56A401u) return fail(CBSPMV_ERR_INVALID, "invalid graph");
+  DeviceGuard g(G->device);
+  if (G->exec) cudaGraphExecDestroy(G->exec);
+  if (G->graph) cudaGraphDestroy(G->graph);
+  G->magic = 0;
+  delete G;
+  return ok();
+}
+
+// ---- autotuned analysis --------------------------------------------------------------------
+// Mean device time of one product on h (reps runs after two warm-up runs, one event pair).
+static cbspmv_status_t time_handle(cbspmv_handle_t h, void* x, void* y, int reps, cudaStream_t s, double* ms) {
+  for (int i = 0; i < 2; ++i) {
+    cbspmv_status_t st = run_device(h, x, y, 1.0, 0.0, s);
+    if (st != CBSPMV_OK) return st;
+  }
+  cudaEvent_t e0, e1;
+  CB_CUDA(cudaEventCreate(&e0));
+  CB_CUDA(cudaEventCreate(&e1));
+  cudaError_t e = cudaEventRecord(e0, s);
+  for (int i = 0; i < reps && e == cudaSuccess; ++i)
+    if (run_device(h, x, y, 1.0, 0.0, s) != CBSPMV_OK) e = cudaErrorUnknown;
+  if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return fail(CBSPMV_ERR_CUDA, "timing: %s", cudaGetErrorString(e));
+  *ms = (double)t / reps;
+  return ok();
+}
+
+cbspmv_status_t cbspmv_analyze_tuned(const cbspmv_csr_t* A, const cbspmv_opts_t* base, void* stream, int reps,
+                                     cbspmv_handle_t* out, cbspmv_tune_report_t* rep) {
+  if (!A || !out) return fail(CBSPMV_ERR_INVALID, "NULL argument");
+  *out = nullptr;
+  cbspmv_opts_t o0;
+  if (base) o0 = *base; else cbspmv_default_opts(&o0);
+  if (o0.device < 0) return fail(CBSPMV_ERR_INVALID, "tuning needs a device");
+  if (reps < 1 || reps > 10000) return fail(CBSPMV_ERR_INVALID, "reps must be in [1, 10000]");
+  cudaStream_t s = (cudaStream_t)stream;
+  cbspmv_tune_report_t R{};
+  // candidate options, tried one coordinate at a time from the paper's settings: column
+  // aggregation (auto / off / on), unit size, then the format thresholds
+  cbspmv_handle_t best = nullptr;
+  cbspmv_opts_t best_o = o0;
+  double best_ms = 0.0;
+  void* x = nullptr;
+  void* y = nullptr;
+  auto consider = [&](const cbspmv_opts_t& o) -> cbspmv_status_t {
+    cbspmv_handle_t h = nullptr;
+    cbspmv_status_t st = cbspmv_analyze(A, &o, stream, &h);
+    if (st != CBSPMV_OK) return st;
+    DeviceGuard g(h->device);
+    if (!x) {
+      const size_t bytes = (size_t)(A->n > A->m ? A->n : A->m) * 8 + 16;
+      if (cudaMalloc(&x, bytes) != cudaSuccess || cudaMalloc(&y, bytes) != cudaSuccess ||
+          cudaMemsetAsync(x, 0, bytes, s) != cudaSuccess) {
+        cbspmv_destroy(h);
+        return fail(CBSPMV_ERR_OOM, "tuning buffers");
+      }
+    }
+    double ms = 0.0;
+    st = time_handle(h, x, y, reps, s, &ms);
+    if (st != CBSPMV_OK) {
+      cbspmv_destroy(h);
+      return st;
+    }
+    if (R.n_tried < 16) {
+      R.tried_ms[R.n_tried] = ms;
+      R.tried_unit_work[R.n_tried] = o.unit_work;
+      R.tried_col_agg[R.n_tried] = o.col_agg;
+      R.tried_th1[R.n_tried] = o.th1;
+      R.tried_th2[R.n_tried] = o.th2;
+    }
+    R.n_tried++;
+    if (!best || ms < best_ms) {
+      if (best) cbspmv_destroy(best);
+      best = h;
+      best_ms = ms;
+      best_o = o;
+    } else {
+      cbspmv_destroy(h);
+    }
+    return ok();
+  };
+  cbspmv_status_t st = consider(o0);
+  if (st == CBSPMV_OK) {
+    R.default_ms = best_ms;
+    // the other side of the aggregation decision the default options took
+    const int other = best->plan.aggregated ? 0 : 1;
+    if (st == CBSPMV_OK && o0.col_agg != other) {
+      cbspmv_opts_t o = best_o;
+      o.col_agg = other;
+      st = consider(o);
+    }
+    for (int uw : {512, 768})
+      if (st == CBSPMV_OK) {
+        cbspmv_opts_t o = best_o;
+        o.unit_work = uw;
+        st = consider(o);
+      }
+    const int th[2][2] = {{16, 64}, {48, 192}};
+    for (const auto& t : th)
+      if (st == CBSPMV_OK) {
+        cbspmv_opts_t o = best_o;
+        o.th1 = t[0];
+        o.th2 = t[1];
+        st = consider(o);
+      }
+  }
+  if (x) cudaFree(x);
+  if (y) cudaFree(y);
+  if (st != CBSPMV_OK) {
+    std::string msg = g_err;
+    if (best) cbspmv_destroy(best);
+    return fail(st, "%s", msg.c_str());
+  }
+  R.best_ms = best_ms;
+  R.best_unit_work = best_o.unit_work;
+  R.best_col_agg = best_o.col_agg;
+  R.best_th1 = best_o.th1;
+  R.best_th2 = best_o.th2;
+  if (rep) *rep = R;
+  *out = best;
+  return ok();
+}
+
 cbspmv_status_t cbspmv_get_stats(cbspmv_handle_t h, cbspmv_stats_t* s) {
   if (!valid_handle(h) || !s) return fail(CBSPMV_ERR_INVALID, "invalid handle or NULL stats");
   *s = h->plan.stats;
@@ -563,6 +767,9 @@ bool noalloc_view(cbspmv_handle_t h, NoallocView* v) {
   a.n = h->plan.n;
   a.aggregated = h->plan.aggregated ? 1 : 0;
   a.value_dtype = h->plan.value_dtype;
+  a.nvec = 1;
+  a.ldx = h->plan.n;
+  a.ldy = h->plan.m;
   v->args = a;
   return true;
 }

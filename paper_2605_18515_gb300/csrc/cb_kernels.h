@@ -29,19 +29,24 @@ struct RunArgs {
   int alpha_one;                // alpha == 1: skip the scaling multiply
   int beta_nonzero;             // beta != 0: read y
   int value_dtype;              // cbspmv_dtype_t of the stored values
+  int nvec;                     // vectors computed in one pass: 1, 2 or 4 (single product only)
+  int64_t ldx, ldy;             // distance in elements between consecutive vectors of x and y
 };
 
 size_t spmv_smem_bytes();      // dynamic shared memory of the largest instantiation
 int spmv_warps(int value_dtype);   // worker warps per CTA of the run kernel for a value type
-// Launches the run kernel for a.value_dtype and, when the matrix has block rows cut into
-// several units, the kernel that adds their parts (two launches on `stream`). ev: NULL, or
-// three events recorded on `stream` before the run kernel, between the two launches and
-// after the last.
+// Launches the run kernel for a.value_dtype and a.nvec vectors and, when the matrix has
+// block rows cut into several units, the kernel that adds their parts (two launches on
+// `stream`; a.partial must hold 16 * nvec values per slot). ev: NULL, or three events
+// recorded on `stream` before the run kernel, between the two launches and after the last.
 cudaError_t launch_spmv(const RunArgs& a, int grid, cudaStream_t stream, cudaEvent_t* ev = nullptr);
 // Launches the products of `count` problems of one value type with one run-kernel launch
 // per 64 problems (plus one combine launch each when any has split block rows). The
 // problems must not share a partial-sum buffer (that is, come from distinct handles).
 cudaError_t launch_spmv_batch(const RunArgs* a, int count, int grid, cudaStream_t stream);
+// Sets every run-kernel instantiation's shared-memory limit on the current device (done
+// lazily by the launches too; needed before a stream capture).
+cudaError_t configure_kernels();
 
 }  // namespace cb
 #endif

@@ -119,11 +119,12 @@ template <> struct ValT<__half> {
   }
 };
 
-template <class Acc>
+// kK: vectors computed per pass (the product on kK right-hand sides at once).
+template <class Acc, int kK>
 struct Scratch {
   uint4 tinfo[CB_T_MAX];        // per tile: value base, coordinate base, x-row base (smem offsets)
-  Acc srow[CB_R_MAX];           // row sums
-  Acc cval[CB_VLANES];          // per-run carry value
+  Acc srow[CB_R_MAX * kK];      // row sums, kK per row
+  Acc cval[CB_VLANES * kK];     // per-run carry values
   int32_t crow[CB_VLANES];      // per-run carry row (-1 none, -2 no chunks)
 };
 
@@ -153,7 +154,7 @@ constexpr uint32_t kHeaderBytes = align128(sizeof(CtaHeader));
 // Layout of one warp's buffer (byte offsets): the unit descriptor, the unit's packed
 // records, its blob (tile records, restore_cols slice, lane schedule), the gathered x
 // values (16 per tile), the warp's scratch and its mbarrier.
-template <class V>
+template <class V, int kK = 1>
 struct Geom {
   using Acc = typename ValT<V>::Acc;
   static constexpr uint32_t kBMax = CB_B_MAX_FOR(sizeof(V));
@@ -162,8 +163,9 @@ struct Geom {
   static constexpr uint32_t kOffBlob = kOffStream + kBMax;
   static constexpr uint32_t kBlobMax = 16 * CB_T_MAX + 4 * CB_RC_MAX + CB_SCHED_MAX;
   static constexpr uint32_t kOffXs = kOffBlob + kBlobMax;
-  static constexpr uint32_t kOffScratch = align128(kOffXs + CB_T_MAX * 16 * (uint32_t)sizeof(Acc));
-  static constexpr uint32_t kOffBar = kOffScratch + (((uint32_t)sizeof(Scratch<Acc>) + 15u) & ~15u);
+  static constexpr uint32_t kXRow = 16u * (uint32_t)sizeof(Acc) * kK;   // bytes of a tile's x values
+  static constexpr uint32_t kOffScratch = align128(kOffXs + CB_T_MAX * kXRow);
+  static constexpr uint32_t kOffBar = kOffScratch + (((uint32_t)sizeof(Scratch<Acc, kK>) + 15u) & ~15u);
   static constexpr uint32_t kWarpBytes = align128(kOffBar + 16);
   static constexpr uint32_t kFit = (kSmemMax - kHeaderBytes) / kWarpBytes;
   static constexpr int kWarps = kFit > 32 ? 32 : (int)kFit;
@@ -237,9 +239,9 @@ __device__ __forceinline__ uint32_t load_desc_word(const CbUnit* units, uint32_t
 // Gathers the unit's x values into the warp's buffer: 16 per tile (column c of tile t at
 // index 16 t + c), x[restore_cols[xbase + c]] when aggregated, x[xbase + c] otherwise;
 // columns outside [0, n) (padding of the last block column) read as zero.
-template <class V>
+template <class V, int kK>
 __device__ __forceinline__ void gather_x(const RunArgs& a, const uint8_t* W, uint32_t w_smem, int lane) {
-  using G = Geom<V>;
+  using G = Geom<V, kK>;
   using Acc = typename G::Acc;
   constexpr int kPerLane = CB_T_MAX * 16 / 32;
   constexpr uint32_t kXs = sizeof(Acc);
@@ -263,7 +265,10 @@ __device__ __forceinline__ void gather_x(const RunArgs& a, const uint8_t* W, uin
     const uint32_t idx = (uint32_t)lane + 32u * k;
     if (idx < nx) {
       const bool valid = col[k] >= 0 && col[k] < a.n;
-      cp_async_elem<kXs>(w_smem + G::kOffXs + kXs * idx, x + (valid ? col[k] : 0), valid ? kXs : 0u);
+#pragma unroll
+      for (int j = 0; j < kK; ++j)      // the kK vectors' values of one column side by side
+        cp_async_elem<kXs>(w_smem + G::kOffXs + kXs * (idx * kK + j), x + (valid ? col[k] + j * a.ldx : 0),
+                           valid ? kXs : 0u);
     }
   }
   cp_async_wait_all();
@@ -283,19 +288,41 @@ __device__ __forceinline__ float pfma(bool p, float v, float x, float acc) {
       : "f"(v), "f"(x), "r"((uint32_t)p));
   return acc;
 }
-#define CB_LDX(off) (*reinterpret_cast<const Acc*>(sm + (off)))
 
-// sm: base of the CTA's shared memory; so: offset of the unit's stage in it.
-template <class V>
+// kK consecutive Acc values at byte offset off of shared memory (aligned to their size).
+template <class Acc, int kK>
+__device__ __forceinline__ void load_xk(const uint8_t* sm, uint32_t off, Acc (&x)[kK]) {
+  if constexpr (kK * sizeof(Acc) >= 16) {
+#pragma unroll
+    for (int q = 0; q < (int)(kK * sizeof(Acc) / 16); ++q) {
+      const uint4 w = *reinterpret_cast<const uint4*>(sm + off + 16u * q);
+      constexpr int per = 16 / (int)sizeof(Acc);
+      const Acc* p = reinterpret_cast<const Acc*>(&w);
+#pragma unroll
+      for (int e = 0; e < per; ++e) x[q * per + e] = p[e];
+    }
+  } else if constexpr (kK * sizeof(Acc) == 8 && kK == 2) {
+    const float2 w = *reinterpret_cast<const float2*>(sm + off);
+    x[0] = w.x;
+    x[1] = w.y;
+  } else {
+    x[0] = *reinterpret_cast<const Acc*>(sm + off);
+  }
+}
+
+// sm: base of the CTA's shared memory; so: offset of the unit's buffer in it. Computes the
+// unit's rows for kK vectors (x values of column c of tile t at x-row t, slot c * kK + j).
+template <class V, int kK>
 __device__ void consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_t ident_off,
-                             Scratch<typename ValT<V>::Acc>& sc, int lane) {
+                             Scratch<typename ValT<V>::Acc, kK>& sc, int lane) {
   using Acc = typename ValT<V>::Acc;
-  using G = Geom<V>;
+  using G = Geom<V, kK>;
   constexpr uint32_t kOffUnit = G::kOffUnit, kOffStream = G::kOffStream, kOffBlob = G::kOffBlob,
                      kOffXs = G::kOffXs;
   constexpr uint32_t kVs = sizeof(V), kXs = sizeof(Acc);
-  // byte offset of x[col] in the tile's x row for a coordinate byte b (col = b >> 4)
-  constexpr uint32_t kXShift = kXs == 8 ? 1 : 2, kXMask = 15u * kXs;
+  // byte offset of column c's x values in the tile's x row for a coordinate byte b
+  // (c = b >> 4): c * kXs * kK
+  constexpr uint32_t kXStride = kXs * kK;
   uint8_t* S = sm + so;
   const CbUnit& u = *reinterpret_cast<const CbUnit*>(S + kOffUnit);
   const uint32_t T = u.ntiles;
@@ -321,13 +348,13 @@ __device__ void consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_
       vb = soff + align16u(rec.nnz);
       cb = soff;
     }
-    sc.tinfo[lane] = make_uint4(vb, cb, so + kOffXs + 16u * kXs * lane, 0u);
+    sc.tinfo[lane] = make_uint4(vb, cb, so + kOffXs + G::kXRow * lane, 0u);
   }
-  for (uint32_t r = lane; r < R; r += 32) sc.srow[r] = Acc(0);
+  for (uint32_t r = lane; r < R * kK; r += 32) sc.srow[r] = Acc(0);
   __syncwarp();
 
   // 2. one run per lane: a sequence of chunks of up to three entries; even chunks go to
-  //    accumulator a0, odd chunks to a1 (two independent FP64 chains)
+  //    accumulator a0, odd chunks to a1 (two independent chains per vector)
   const uint8_t* sched = S + kOffBlob + 16u * T + 4u * u.rc_n;
   const uint16_t* hdr = reinterpret_cast<const uint16_t*>(sched);
   const uint8_t* nxt = sched + 2 * CB_VLANES;
@@ -340,16 +367,24 @@ __device__ void consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_
   const bool hs = (h >> 8) & 1u;
   bool first = true, open = false;
   int32_t own_row = -1;
-  Acc own_val = Acc(0);
-  Acc a0 = Acc(0), a1 = Acc(0);
-  // Software pipeline: the operands of step i + 1 are loaded before the DFMAs of step i.
+  Acc own_val[kK], a0[kK], a1[kK];
+#pragma unroll
+  for (int j = 0; j < kK; ++j) own_val[j] = a0[j] = a1[j] = Acc(0);
+  // Software pipeline: the operands of step i + 1 are loaded before the FMAs of step i.
   // Loads are unconditional (a chunk shorter than three entries reads at most two entries,
   // plus up to 4 value bytes and 5 coordinate bytes of alignment slack, past its piece;
   // column nibbles stay inside the tile's x row, so every address stays in the warp's
-  // buffer or the CTA header); the DFMA slots beyond the chunk's length are predicated off.
+  // buffer or the CTA header); the FMA slots beyond the chunk's length are predicated off.
   uint32_t dA = 0, dB = 0;
-  Acc vA0 = 0, vA1 = 0, vA2 = 0, xA0 = 0, xA1 = 0, xA2 = 0;
-  Acc vB0 = 0, vB1 = 0, vB2 = 0, xB0 = 0, xB1 = 0, xB2 = 0;
+  Acc vA0 = 0, vA1 = 0, vA2 = 0, vB0 = 0, vB1 = 0, vB2 = 0;
+  Acc xA0[kK], xA1[kK], xA2[kK], xB0[kK], xB1[kK], xB2[kK];
+#pragma unroll
+  for (int j = 0; j < kK; ++j) xA0[j] = xA1[j] = xA2[j] = xB0[j] = xB1[j] = xB2[j] = Acc(0);
+  // (b >> 4) * stride for b < 256 and a power-of-two stride, in two operations
+  constexpr uint32_t kXLog = kXStride == 4 ? 2 : kXStride == 8 ? 3 : kXStride == 16 ? 4 : 5;
+  static_assert((1u << kXLog) == kXStride, "x stride must be 4, 8, 16 or 32 bytes");
+#define CB_XOFF(b_) (kXLog <= 4 ? (((b_) >> (4 - (kXLog <= 4 ? kXLog : 4))) & (15u << kXLog)) \
+                                : (((b_) & 0xF0u) << (kXLog > 4 ? kXLog - 4 : 0)))
 #define CB_LOAD_CHUNK(d, v0, v1, v2, x0, x1, x2)                                   \
   {                                                                                \
     const uint4 ti_ = sc.tinfo[(d) & 31u];                                         \
@@ -361,9 +396,9 @@ __device__ void consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_
                                          8u * (ca_ & 3u));                         \
     const uint32_t b0_ = cb_ & 0xffu, b1_ = (cb_ >> 8) & 0xffu, b2_ = (cb_ >> 16) & 0xffu; \
     ValT<V>::load3(sm, va_, v0, v1, v2);                                           \
-    x0 = CB_LDX(xr_ + ((b0_ >> kXShift) & kXMask));                                \
-    x1 = CB_LDX(xr_ + ((b1_ >> kXShift) & kXMask));                                \
-    x2 = CB_LDX(xr_ + ((b2_ >> kXShift) & kXMask));                                \
+    load_xk<Acc, kK>(sm, xr_ + CB_XOFF(b0_), x0);                                  \
+    load_xk<Acc, kK>(sm, xr_ + CB_XOFF(b1_), x1);                                  \
+    load_xk<Acc, kK>(sm, xr_ + CB_XOFF(b2_), x2);                                  \
   }
   if (steps) {
     dA = desc[lane];
@@ -374,59 +409,85 @@ __device__ void consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_
   for (uint32_t i = 0; i < steps; ++i) {
     const uint32_t nb = (i + 1 < steps ? 2u * (i + 1) : 2u * i) * CB_VLANES;
     const uint32_t dA_n = desc[nb + lane], dB_n = desc[nb + CB_VLANES + lane];
-    Acc nvA0, nvA1, nvA2, nxA0, nxA1, nxA2, nvB0, nvB1, nvB2, nxB0, nxB1, nxB2;
+    Acc nvA0, nvA1, nvA2, nvB0, nvB1, nvB2;
+    Acc nxA0[kK], nxA1[kK], nxA2[kK], nxB0[kK], nxB1[kK], nxB2[kK];
     CB_LOAD_CHUNK(dA_n, nvA0, nvA1, nvA2, nxA0, nxA1, nxA2);
     CB_LOAD_CHUNK(dB_n, nvB0, nvB1, nvB2, nxB0, nxB1, nxB2);
     const uint32_t lA = (dA >> 13) & 3u, lB = (dB >> 13) & 3u;
     const bool eA = (dA & 0x8000u) != 0, eB = (dB & 0x8000u) != 0;
     // chunk B starts a new row when chunk A ends one: its chain then starts from zero
-    const Acc a1_old = a1;
-    Acc b = eA ? Acc(0) : a1;
-    a0 = pfma(lA > 0, vA0, xA0, a0);
-    b = pfma(lB > 0, vB0, xB0, b);
-    a0 = pfma(lA > 1, vA1, xA1, a0);
-    b = pfma(lB > 1, vB1, xB1, b);
-    a0 = pfma(lA > 2, vA2, xA2, a0);
-    b = pfma(lB > 2, vB2, xB2, b);
-    a1 = b;
+    Acc a1_old[kK];
+#pragma unroll
+    for (int j = 0; j < kK; ++j) {
+      a1_old[j] = a1[j];
+      Acc b = eA ? Acc(0) : a1[j];
+      a0[j] = pfma(lA > 0, vA0, xA0[j], a0[j]);
+      b = pfma(lB > 0, vB0, xB0[j], b);
+      a0[j] = pfma(lA > 1, vA1, xA1[j], a0[j]);
+      b = pfma(lB > 1, vB1, xB1[j], b);
+      a0[j] = pfma(lA > 2, vA2, xA2[j], a0[j]);
+      b = pfma(lB > 2, vB2, xB2[j], b);
+      a1[j] = b;
+    }
     if (lA | lB) open = true;
     if (eA) {                              // chunk A ends its row: a0 + (a1 before chunk B)
-      const Acc sum = a0 + a1_old;
-      if (first && hs) { own_row = (int32_t)row; own_val = sum; }
-      else sc.srow[row] = sum;
+      const bool own = first && hs;
+      if (own) own_row = (int32_t)row;
+#pragma unroll
+      for (int j = 0; j < kK; ++j) {
+        const Acc sum = a0[j] + a1_old[j];
+        if (own) own_val[j] = sum;
+        else sc.srow[row * kK + j] = sum;
+        a0[j] = Acc(0);
+      }
       first = false;
-      a0 = Acc(0);
       open = lB != 0;
       row = nxt[row];
     }
     if (eB) {                              // chunk B ends its row
-      const Acc sum = a0 + a1;
-      if (first && hs) { own_row = (int32_t)row; own_val = sum; }
-      else sc.srow[row] = sum;
+      const bool own = first && hs;
+      if (own) own_row = (int32_t)row;
+#pragma unroll
+      for (int j = 0; j < kK; ++j) {
+        const Acc sum = a0[j] + a1[j];
+        if (own) own_val[j] = sum;
+        else sc.srow[row * kK + j] = sum;
+        a0[j] = Acc(0);
+        a1[j] = Acc(0);
+      }
       first = false;
-      a0 = Acc(0);
-      a1 = Acc(0);
       open = false;
       row = nxt[row];
     }
     dA = dA_n;
     dB = dB_n;
-    vA0 = nvA0; vA1 = nvA1; vA2 = nvA2; xA0 = nxA0; xA1 = nxA1; xA2 = nxA2;
-    vB0 = nvB0; vB1 = nvB1; vB2 = nvB2; xB0 = nxB0; xB1 = nxB1; xB2 = nxB2;
+    vA0 = nvA0; vA1 = nvA1; vA2 = nvA2;
+    vB0 = nvB0; vB1 = nvB1; vB2 = nvB2;
+#pragma unroll
+    for (int j = 0; j < kK; ++j) {
+      xA0[j] = nxA0[j]; xA1[j] = nxA1[j]; xA2[j] = nxA2[j];
+      xB0[j] = nxB0[j]; xB1[j] = nxB1[j]; xB2[j] = nxB2[j];
+    }
   }
 #undef CB_LOAD_CHUNK
+#undef CB_XOFF
   sc.crow[lane] = nch == 0 ? -2 : (open ? (int32_t)row : -1);
-  sc.cval[lane] = open ? a0 + a1 : Acc(0);
+#pragma unroll
+  for (int j = 0; j < kK; ++j) sc.cval[lane * kK + j] = open ? a0[j] + a1[j] : Acc(0);
   __syncwarp();
   if (own_row >= 0) {
-    Acc sum = own_val;
-    for (int j = (int)lane - 1; j >= 0; --j) {
-      const int32_t cr = sc.crow[j];
+    Acc sum[kK];
+#pragma unroll
+    for (int j = 0; j < kK; ++j) sum[j] = own_val[j];
+    for (int l = (int)lane - 1; l >= 0; --l) {
+      const int32_t cr = sc.crow[l];
       if (cr == -2) continue;
       if (cr != own_row) break;
-      sum += sc.cval[j];
+#pragma unroll
+      for (int j = 0; j < kK; ++j) sum[j] += sc.cval[l * kK + j];
     }
-    sc.srow[own_row] = sum;
+#pragma unroll
+    for (int j = 0; j < kK; ++j) sc.srow[own_row * kK + j] = sum[j];
   }
   __syncwarp();
 
@@ -436,22 +497,30 @@ __device__ void consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_
   if (u.split < 0) {
     for (uint32_t r = lane; r < R; r += 32) {
       const int64_t gr = row0 + r;
-      Acc v = sc.srow[r];
-      if (!a.alpha_one) v = alpha * v;
-      if (a.beta_nonzero) v = fma(beta, y[gr], v);
-      y[gr] = v;
+#pragma unroll
+      for (int j = 0; j < kK; ++j) {
+        Acc* yj = y + (int64_t)j * a.ldy;
+        Acc v = sc.srow[r * kK + j];
+        if (!a.alpha_one) v = alpha * v;
+        if (a.beta_nonzero) v = fma(beta, yj[gr], v);
+        yj[gr] = v;
+      }
     }
   } else {
-    // part of a block row cut into several units: 16 partial sums, added by combine_kernel
+    // part of a block row cut into several units: 16 x kK partial sums, added by
+    // combine_kernel
     Acc* partial = static_cast<Acc*>(a.partial);
-    if (lane < 16) partial[(size_t)u.slot * 16 + lane] = (uint32_t)lane < R ? sc.srow[lane] : Acc(0);
+    if (lane < 16) {
+#pragma unroll
+      for (int j = 0; j < kK; ++j)
+        partial[((size_t)u.slot * 16 + lane) * kK + j] = (uint32_t)lane < R ? sc.srow[lane * kK + j] : Acc(0);
+    }
   }
 }
-#undef CB_LDX
 
-template <class V, int kMaxP>
-__global__ void __launch_bounds__(32 * Geom<V>::kWarps, 1) spmv_kernel(const __grid_constant__ BatchArgs<kMaxP> b) {
-  using G = Geom<V>;
+template <class V, int kMaxP, int kK>
+__global__ void __launch_bounds__(32 * Geom<V, kK>::kWarps, 1) spmv_kernel(const __grid_constant__ BatchArgs<kMaxP> b) {
+  using G = Geom<V, kK>;
   using Acc = typename G::Acc;
   extern __shared__ __align__(128) uint8_t smem_raw[];
   CtaHeader& hd = *reinterpret_cast<CtaHeader*>(smem_raw);
@@ -460,7 +529,7 @@ __global__ void __launch_bounds__(32 * Geom<V>::kWarps, 1) spmv_kernel(const __g
   uint8_t* W = smem_raw + wo;
   const uint32_t w_smem = smem_u32(W);
   uint64_t* bar = reinterpret_cast<uint64_t*>(W + G::kOffBar);
-  Scratch<Acc>& sc = *reinterpret_cast<Scratch<Acc>*>(W + G::kOffScratch);
+  Scratch<Acc, kK>& sc = *reinterpret_cast<Scratch<Acc, kK>*>(W + G::kOffScratch);
   // this CTA's unit lists of the batch's problems (stored contiguously per CTA), one after
   // another in ticket order
   const int P = b.count;
@@ -530,9 +599,9 @@ __global__ void __launch_bounds__(32 * Geom<V>::kWarps, 1) spmv_kernel(const __g
       mbar_wait(bar, phase ^ 1u);
       break;
     }
-    gather_x<V>(a, W, w_smem, lane);
+    gather_x<V, kK>(a, W, w_smem, lane);
     __syncwarp();
-    consume_unit<V>(a, smem_raw, wo, ident_off, sc, lane);
+    consume_unit<V, kK>(a, smem_raw, wo, ident_off, sc, lane);
     __syncwarp();
     j = jn;
     dw = dwn;
@@ -540,7 +609,7 @@ __global__ void __launch_bounds__(32 * Geom<V>::kWarps, 1) spmv_kernel(const __g
 }
 
 // Adds the parts of every block row cut into several units, in part order, and writes y.
-template <class Acc, int kMaxP>
+template <class Acc, int kMaxP, int kK>
 __global__ void __launch_bounds__(256) combine_kernel(const __grid_constant__ BatchArgs<kMaxP> b) {
   const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t srg = g >> 4, r = g & 15u;
@@ -557,38 +626,51 @@ __global__ void __launch_bounds__(256) combine_kernel(const __grid_constant__ Ba
   const RunArgs& a = b.p[q];
   const CbSplitRow s = a.split_rows[srg - b.split_base[q]];
   if (r >= s.rows) return;
-  const Acc* p = static_cast<const Acc*>(a.partial) + (size_t)s.slot0 * 16 + r;
-  Acc sum = Acc(0);
-  for (uint32_t k = 0; k < s.nparts; ++k) sum += p[(size_t)k * 16];
   const int64_t gr = (int64_t)s.brow * CB_BLK + r;
-  Acc* y = static_cast<Acc*>(a.y);
-  Acc v = a.alpha_one ? sum : (Acc)a.alpha * sum;
-  if (a.beta_nonzero) v = fma((Acc)a.beta, y[gr], v);
-  y[gr] = v;
+#pragma unroll
+  for (int j = 0; j < kK; ++j) {
+    const Acc* p = static_cast<const Acc*>(a.partial) + ((size_t)s.slot0 * 16 + r) * kK + j;
+    Acc sum = Acc(0);
+    for (uint32_t k = 0; k < s.nparts; ++k) sum += p[(size_t)k * 16 * kK];
+    Acc* y = static_cast<Acc*>(a.y) + (int64_t)j * a.ldy;
+    Acc v = a.alpha_one ? sum : (Acc)a.alpha * sum;
+    if (a.beta_nonzero) v = fma((Acc)a.beta, y[gr], v);
+    y[gr] = v;
+  }
 }
 
-template <class V, int kMaxP>
-cudaError_t launch_typed(const BatchArgs<kMaxP>& b, int grid, cudaStream_t stream, cudaEvent_t* ev) {
-  using Acc = typename ValT<V>::Acc;
+// Raises the run kernel's dynamic shared-memory limit on the current device (once per
+// device and instantiation).
+template <class V, int kMaxP, int kK>
+cudaError_t configure_typed() {
   static bool configured[64] = {false};
-  const size_t smem = Geom<V>::kSmem;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64 || !configured[dev]) {
-    e = cudaFuncSetAttribute(spmv_kernel<V, kMaxP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(spmv_kernel<V, kMaxP, kK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Geom<V, kK>::kSmem);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) configured[dev] = true;
   }
+  return cudaSuccess;
+}
+
+template <class V, int kMaxP, int kK>
+cudaError_t launch_typed(const BatchArgs<kMaxP>& b, int grid, cudaStream_t stream, cudaEvent_t* ev) {
+  using Acc = typename ValT<V>::Acc;
+  const size_t smem = Geom<V, kK>::kSmem;
+  cudaError_t e = configure_typed<V, kMaxP, kK>();
+  if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[0], stream)) != cudaSuccess) return e;
-  spmv_kernel<V, kMaxP><<<grid, 32 * Geom<V>::kWarps, smem, stream>>>(b);
+  spmv_kernel<V, kMaxP, kK><<<grid, 32 * Geom<V, kK>::kWarps, smem, stream>>>(b);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[1], stream)) != cudaSuccess) return e;
   const uint32_t nsplit = b.split_base[b.count];
   if (nsplit) {
     const uint32_t threads = 16u * nsplit;
-    combine_kernel<Acc, kMaxP><<<(threads + 255) / 256, 256, 0, stream>>>(b);
+    combine_kernel<Acc, kMaxP, kK><<<(threads + 255) / 256, 256, 0, stream>>>(b);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -596,13 +678,27 @@ cudaError_t launch_typed(const BatchArgs<kMaxP>& b, int grid, cudaStream_t strea
   return e;
 }
 
+template <class V, int kMaxP>
+cudaError_t launch_nvec(const BatchArgs<kMaxP>& b, int grid, cudaStream_t stream, cudaEvent_t* ev) {
+  if constexpr (kMaxP == 1) {     // several vectors per pass: single products only
+    switch (b.p[0].nvec) {
+      case 1: return launch_typed<V, 1, 1>(b, grid, stream, ev);
+      case 2: return launch_typed<V, 1, 2>(b, grid, stream, ev);
+      case 4: return launch_typed<V, 1, 4>(b, grid, stream, ev);
+      default: return cudaErrorInvalidValue;
+    }
+  } else {
+    return b.p[0].nvec == 1 ? launch_typed<V, kMaxP, 1>(b, grid, stream, ev) : cudaErrorInvalidValue;
+  }
+}
+
 template <int kMaxP>
 cudaError_t launch_dispatch(const BatchArgs<kMaxP>& b, int grid, cudaStream_t stream, cudaEvent_t* ev) {
   switch (b.p[0].value_dtype) {
-    case CBSPMV_F64: return launch_typed<double, kMaxP>(b, grid, stream, ev);
-    case CBSPMV_F32: return launch_typed<float, kMaxP>(b, grid, stream, ev);
-    case CBSPMV_BF16: return launch_typed<__nv_bfloat16, kMaxP>(b, grid, stream, ev);
-    case CBSPMV_F16: return launch_typed<__half, kMaxP>(b, grid, stream, ev);
+    case CBSPMV_F64: return launch_nvec<double, kMaxP>(b, grid, stream, ev);
+    case CBSPMV_F32: return launch_nvec<float, kMaxP>(b, grid, stream, ev);
+    case CBSPMV_BF16: return launch_nvec<__nv_bfloat16, kMaxP>(b, grid, stream, ev);
+    case CBSPMV_F16: return launch_nvec<__half, kMaxP>(b, grid, stream, ev);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -621,6 +717,23 @@ int spmv_warps(int value_dtype) {
   }
 }
 
+template <class V>
+cudaError_t configure_value_type() {
+  cudaError_t e = configure_typed<V, 1, 1>();
+  if (e == cudaSuccess) e = configure_typed<V, kMaxBatch, 1>();
+  if (e == cudaSuccess) e = configure_typed<V, 1, 2>();
+  if (e == cudaSuccess) e = configure_typed<V, 1, 4>();
+  return e;
+}
+
+cudaError_t configure_kernels() {
+  cudaError_t e = configure_value_type<double>();
+  if (e == cudaSuccess) e = configure_value_type<float>();
+  if (e == cudaSuccess) e = configure_value_type<__nv_bfloat16>();
+  if (e == cudaSuccess) e = configure_value_type<__half>();
+  return e;
+}
+
 cudaError_t launch_spmv(const RunArgs& a, int grid, cudaStream_t stream, cudaEvent_t* ev) {
   BatchArgs<1> b;
   b.count = 1;
@@ -632,7 +745,7 @@ cudaError_t launch_spmv(const RunArgs& a, int grid, cudaStream_t stream, cudaEve
 
 cudaError_t launch_spmv_batch(const RunArgs* a, int count, int grid, cudaStream_t stream) {
   for (int i = 0; i < count; ++i)
-    if (a[i].value_dtype != a[0].value_dtype) return cudaErrorInvalidValue;
+    if (a[i].value_dtype != a[0].value_dtype || a[i].nvec != 1) return cudaErrorInvalidValue;
   for (int base = 0; base < count; base += kMaxBatch) {
     const int c = count - base < kMaxBatch ? count - base : kMaxBatch;
     static thread_local BatchArgs<kMaxBatch> b;

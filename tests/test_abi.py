@@ -42,3 +42,10 @@ def test_binding_covers_the_header():
     from paper_2605_18515_gb300 import binding
     assert set(binding.SIGNATURES) == declared_functions()
     assert binding.version().startswith("cbspmv")
+    # the Python-level API over those entry points
+    for name in ("BlockedMatrix", "Server", "Graph", "analyze_batched", "run_batched", "analyze_tuned"):
+        assert callable(getattr(binding, name)), name
+    for meth in ("run", "run_multi", "run_host", "time_kernels", "export_csr", "export_blocked", "stats"):
+        assert callable(getattr(binding.BlockedMatrix, meth)), meth
+    for meth in ("register", "submit_spmv", "submit_cg", "wait", "poll", "stats", "close"):
+        assert callable(getattr(binding.Server, meth)), meth

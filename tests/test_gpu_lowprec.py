@@ -121,12 +121,12 @@ def test_lowprec_split_rows_deterministic(env, fmt):
     check_lowprec(A, fmt, x, outs[0])
 
 
-def test_lowprec_run_multi_and_host(env):
+@pytest.mark.parametrize("fmt,k", [("bf16", 3), ("f32", 4), ("f16", 7)])
+def test_lowprec_run_multi_and_host(env, fmt, k):
     bd, torch = env
     A = I.fem_block_band(n_rows=6000, n_block_rows=2000, half_band=300, seed=3)
-    k = 3
     X = np.stack([f32(I.vector_x(A.n, 50 + j)) for j in range(k)])
-    with bd.BlockedMatrix(A, value_dtype="bf16") as M:
+    with bd.BlockedMatrix(A, value_dtype=fmt) as M:
         Xd = torch.from_numpy(X).cuda()
         Yd = torch.zeros((k, A.m), dtype=torch.float32, device="cuda")
         M.run_multi(Xd, Yd, 1.0, 0.0)
@@ -134,7 +134,7 @@ def test_lowprec_run_multi_and_host(env):
         for j in range(k):
             yh = M.run_host(X[j], np.zeros(A.m, np.float32))
             assert np.array_equal(yh, Y[j])
-            check_lowprec(A, "bf16", X[j], Y[j])
+            check_lowprec(A, fmt, X[j], Y[j])
 
 
 @pytest.mark.slow

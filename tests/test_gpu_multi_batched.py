@@ -26,7 +26,7 @@ def check(A, x, y, alpha=1.0, beta=0.0, y0=None):
     assert ok, f"worst normalised error {worst:.3e}"
 
 
-@pytest.mark.parametrize("k", [1, 3, 8])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6, 8])
 def test_run_multi_strided(env, k):
     bd, torch = env
     A = I.fem_block_band(n_rows=6000, n_block_rows=2000, half_band=300, seed=3)
@@ -110,3 +110,33 @@ def test_device_resident_csr_input(env):
         Mh.run(xd, y2)
         assert torch.equal(y1, y2)
         check(A, x, y1.cpu().numpy())
+
+
+@pytest.mark.parametrize("name", ["rmat12", "dense_70x45", "split_rows"])
+def test_run_multi_structures(env, name):
+    """4- and 2-vector passes on power-law rows, Dense tiles and split block rows."""
+    bd, torch = env
+    if name == "rmat12":
+        A = I.rmat(12, 16, seed=4)
+    elif name == "dense_70x45":
+        A = I.random_csr(70, 45, 0.85, 6)
+    else:
+        r = np.repeat(np.arange(16), 900)
+        c = np.tile(np.arange(900) * 3, 16)
+        A = I.csr_from_coo(16, 2700, r, c, I.normal(5, I.TAG_VAL, r.size))
+    k = 7
+    X = np.stack([I.vector_x(A.n, 80 + j) for j in range(k)])
+    Y0 = np.stack([I.uniform_pm1(90 + j, I.TAG_Y, A.m) for j in range(k)])
+    with bd.BlockedMatrix(A, unit_work=256 if name == "split_rows" else 0) as M:
+        if name == "split_rows":
+            assert M.stats()["n_split_rows"] > 0
+        Xd = torch.from_numpy(X).cuda()
+        Yd = torch.from_numpy(Y0.copy()).cuda()
+        M.run_multi(Xd, Yd, 0.75, -1.25)
+        Y = Yd.cpu().numpy()
+        for j in range(k):
+            yj = torch.from_numpy(Y0[j].copy()).cuda()
+            M.run(torch.from_numpy(X[j].copy()).cuda(), yj, 0.75, -1.25)
+            assert np.array_equal(Y[j], yj.cpu().numpy())
+            check(A, X[j], Y[j], 0.75, -1.25, Y0[j])
+        M.check_device()
