@@ -496,12 +496,20 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
       for (int64_t i = lo; i < hi; ++i) {
         const CbUnit& u = p.units[i];
         const int64_t R = std::min<int64_t>((int64_t)CB_BLK * u.nbr, A.m - (int64_t)u.brow_lo * CB_BLK);
-        uint64_t nch = 0;
+        uint64_t nch = 0, nent = 0;
         for (uint32_t t = 0; t < u.ntiles; ++t) {
           const int64_t brl = (int64_t)p.tiles[u.tile_lo + t].brow - u.brow_lo;
           for (int rr = 0; rr < 16; ++rr)
-            if (brl * 16 + rr < R) nch += (rowcnt[(size_t)(u.tile_lo + t) * 16 + rr] + CB_CHUNK - 1) / CB_CHUNK;
+            if (brl * 16 + rr < R) {
+              const uint32_t c = rowcnt[(size_t)(u.tile_lo + t) * 16 + rr];
+              nch += (c + CB_CHUNK - 1) / CB_CHUNK;
+              nent += c;
+            }
         }
+        // sparse pieces: schedule single entries (see CB_ENTRY_MODE_FILL)
+        const bool entry_mode = nch > 0 && (double)nent < CB_ENTRY_MODE_FILL * CB_CHUNK * (double)nch;
+        p.units[i].mode = entry_mode ? CB_MODE_ENTRY : 0u;
+        if (entry_mode) nch = nent;
         chunks_of[i] = nch;
         // descriptor rows: chunks of the longest run, rounded up to an even count because
         // the kernel reads the chunks of a run in pairs
@@ -545,8 +553,9 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
                 s0 = 0;
                 for (int q = 0; q < rr; ++q) s0 += rowcnt[tg * 16 + q];
               }
-              for (uint32_t o = 0; o < c; o += CB_CHUNK) {
-                const uint32_t len = std::min<uint32_t>(CB_CHUNK, c - o);
+              const uint32_t cap = (u.mode & CB_MODE_ENTRY) ? 1u : (uint32_t)CB_CHUNK;
+              for (uint32_t o = 0; o < c; o += cap) {
+                const uint32_t len = std::min<uint32_t>(cap, c - o);
                 chunk.push_back((uint16_t)(t | ((s0 + o) << 5) | (len << 13)));
                 chunk_row.push_back((uint8_t)row);
                 chunk_first.push_back(first ? 1 : 0);
@@ -568,13 +577,24 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
           }
         }
         const uint64_t nch = chunk.size();
+        int first_lane[CB_R_MAX], last_lane[CB_R_MAX];   // lanes holding chunks of each row
+        for (int r = 0; r < CB_R_MAX; ++r) first_lane[r] = last_lane[r] = -1;
         for (uint32_t l = 0; l < CB_VLANES; ++l) {
           const uint64_t c0 = (l * nch) / CB_VLANES, c1 = ((l + 1) * nch) / CB_VLANES;
           if (c1 == c0) { hdr[l] = 0; continue; }
           const uint32_t hs = chunk_first[c0] ? 0u : 1u;
           hdr[l] = (uint16_t)(chunk_row[c0] | (hs << 8) | ((uint32_t)(c1 - c0) << 9));
-          for (uint64_t k = c0; k < c1; ++k) desc[(k - c0) * CB_VLANES + l] = chunk[k];
+          for (uint64_t k = c0; k < c1; ++k) {
+            desc[(k - c0) * CB_VLANES + l] = chunk[k];
+            const int r = chunk_row[k];
+            if (first_lane[r] < 0) first_lane[r] = (int)l;
+            last_lane[r] = (int)l;
+          }
         }
+        int span_max = 0;
+        for (int r = 0; r < CB_R_MAX; ++r)
+          if (first_lane[r] >= 0) span_max = std::max(span_max, last_lane[r] - first_lane[r] + 1);
+        if (span_max > CB_SCAN_SPAN) u.mode |= CB_MODE_SCAN;
         u.sched16 = (uint32_t)(off[i] / 16);
         u.sched_bytes = (uint32_t)sbytes[i];
       }
@@ -698,6 +718,7 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
   int64_t nsplit_units = 0;
   for (auto& u : p.units) nsplit_units += u.split >= 0;
   s.n_split_units = nsplit_units;
+  for (auto& u : p.units) s.n_entry_mode_units += (u.mode & CB_MODE_ENTRY) ? 1 : 0;
   s.n_split_rows = p.n_split_rows;
   s.n_workers = n_workers;
   double lmax = 0, lsum = 0, lsq = 0;

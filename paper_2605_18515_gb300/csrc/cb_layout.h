@@ -59,8 +59,11 @@ struct CbUnit {
   uint32_t sched_bytes;  // bytes of the schedule (multiple of 16)
   uint32_t blob16;    // offset of the unit blob in the blob array / 16
   uint32_t blob_bytes;   // 16 * ntiles + 4 * rc_n + sched_bytes
-  uint32_t pad;
+  uint32_t mode;         // CB_MODE_* flags of the unit's lane schedule
 };
+#define CB_MODE_ENTRY 1u     // schedule of single entries instead of chunks of up to CB_CHUNK
+#define CB_MODE_SCAN 2u      // some row spans more than CB_SCAN_SPAN lanes: resolve carries by a scan
+#define CB_SCAN_SPAN 4
 
 // Unit blob: the unit's tile records, its restore_cols slice and its lane schedule, stored
 // back to back (each part a multiple of 16 bytes) so that the kernel stages all of the
@@ -94,6 +97,12 @@ struct CbSplitRow {
 //     of the record: row-major; Dense: row * 16 + col), [13,15) length 1..CB_CHUNK (0 = no
 //     chunk), bit 15 set when the chunk ends its row.
 #define CB_CHUNK 3
+// A unit whose chunks of up to CB_CHUNK entries would fill less than this share of their
+// FMA slots (sparse tiles, rows with one or two entries per tile) is scheduled in single
+// entries instead (mode 1): fewer wasted FMA slots and loads per entry.
+#ifndef CB_ENTRY_MODE_FILL
+#define CB_ENTRY_MODE_FILL 0.6
+#endif
 #define CB_VLANES 32
 #define CB_SCHED_HDR(R) ((2u * CB_VLANES + (uint32_t)(R) + 15u) & ~15u)
 #define CB_STEPS_MAX ((((CB_UNIT_WORK_MAX + CB_VLANES - 1) / CB_VLANES) + 1) & ~1)

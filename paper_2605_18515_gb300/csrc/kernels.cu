@@ -124,7 +124,7 @@ template <class Acc, int kK>
 struct Scratch {
   uint4 tinfo[CB_T_MAX];        // per tile: value base, coordinate base, x-row base (smem offsets)
   Acc srow[CB_R_MAX * kK];      // row sums, kK per row
-  Acc cval[CB_VLANES * kK];     // per-run carry values
+  Acc cval[CB_VLANES * kK];     // per-run carry values (short-carry path)
   int32_t crow[CB_VLANES];      // per-run carry row (-1 none, -2 no chunks)
 };
 
@@ -166,7 +166,7 @@ struct Geom {
   static constexpr uint32_t kXRow = 16u * (uint32_t)sizeof(Acc) * kK;   // bytes of a tile's x values
   static constexpr uint32_t kOffScratch = align128(kOffXs + CB_T_MAX * kXRow);
   static constexpr uint32_t kOffBar = kOffScratch + (((uint32_t)sizeof(Scratch<Acc, kK>) + 15u) & ~15u);
-  static constexpr uint32_t kWarpBytes = align128(kOffBar + 16);
+  static constexpr uint32_t kWarpBytes = align128(kOffBar + 16);   // two mbarriers: blob, records
   static constexpr uint32_t kFit = (kSmemMax - kHeaderBytes) / kWarpBytes;
   static constexpr int kWarps = kFit > 32 ? 32 : (int)kFit;
   static constexpr uint32_t kSmem = kHeaderBytes + kWarps * kWarpBytes;
@@ -236,9 +236,10 @@ __device__ __forceinline__ uint32_t load_desc_word(const CbUnit* units, uint32_t
   return (k < nu && lane < 16) ? __ldg(reinterpret_cast<const uint32_t*>(units + k) + lane) : 0u;
 }
 
-// Gathers the unit's x values into the warp's buffer: 16 per tile (column c of tile t at
-// index 16 t + c), x[restore_cols[xbase + c]] when aggregated, x[xbase + c] otherwise;
-// columns outside [0, n) (padding of the last block column) read as zero.
+// Starts gathering the unit's x values into the warp's buffer: 16 per tile (column c of
+// tile t at index 16 t + c), x[restore_cols[xbase + c]] when aggregated, x[xbase + c]
+// otherwise; columns outside [0, n) (padding of the last block column) read as zero. The
+// cp.async copies are waited for by consume_unit after its set-up.
 template <class V, int kK>
 __device__ __forceinline__ void gather_x(const RunArgs& a, const uint8_t* W, uint32_t w_smem, int lane) {
   using G = Geom<V, kK>;
@@ -271,7 +272,7 @@ __device__ __forceinline__ void gather_x(const RunArgs& a, const uint8_t* W, uin
                            valid ? kXs : 0u);
     }
   }
-  cp_async_wait_all();
+  // the copies complete while the unit's set-up runs; consume_unit waits for them
 }
 
 // ---- consumer -----------------------------------------------------------------------------
@@ -312,9 +313,14 @@ __device__ __forceinline__ void load_xk(const uint8_t* sm, uint32_t off, Acc (&x
 
 // sm: base of the CTA's shared memory; so: offset of the unit's buffer in it. Computes the
 // unit's rows for kK vectors (x values of column c of tile t at x-row t, slot c * kK + j).
-template <class V, int kK>
-__device__ void consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_t ident_off,
-                             Scratch<typename ValT<V>::Acc, kK>& sc, int lane) {
+// kC: entries per chunk of the unit's schedule, CB_CHUNK (mode 0) or 1 (mode 1).
+// bar_s / phase: the mbarrier phase on which the unit's records land (waited for after the
+// set-up). Returns false if that bounded wait gave up (nothing is written then).
+template <class V, int kK, int kC>
+__device__ bool consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_t ident_off,
+                             Scratch<typename ValT<V>::Acc, kK>& sc, int lane, uint64_t* bar_s,
+                             uint32_t phase) {
+  static_assert(kC == CB_CHUNK || kC == 1, "chunk size");
   using Acc = typename ValT<V>::Acc;
   using G = Geom<V, kK>;
   constexpr uint32_t kOffUnit = G::kOffUnit, kOffStream = G::kOffStream, kOffBlob = G::kOffBlob,
@@ -332,6 +338,7 @@ __device__ void consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_
   const int64_t rows_unit = (int64_t)CB_BLK * u.nbr;
   const uint32_t R = (uint32_t)(rows_unit < rows_left ? rows_unit : rows_left);
   const CbTile* tiles = reinterpret_cast<const CbTile*>(S + kOffBlob);
+  const bool scan_carries = (u.mode & CB_MODE_SCAN) != 0;
 
   // 1. per-tile bases (lane = tile) and zeroed row sums
   if ((uint32_t)lane < T) {
@@ -351,6 +358,8 @@ __device__ void consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_
     sc.tinfo[lane] = make_uint4(vb, cb, so + kOffXs + G::kXRow * lane, 0u);
   }
   for (uint32_t r = lane; r < R * kK; r += 32) sc.srow[r] = Acc(0);
+  if (!__all_sync(0xffffffffu, mbar_wait(bar_s, phase))) return false;   // the records
+  cp_async_wait_all();     // this lane's x copies (issued by gather_x before the set-up)
   __syncwarp();
 
   // 2. one run per lane: a sequence of chunks of up to three entries; even chunks go to
@@ -390,15 +399,20 @@ __device__ void consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_
     const uint4 ti_ = sc.tinfo[(d) & 31u];                                         \
     const uint32_t o_ = ((d) >> 5) & 255u;                                         \
     const uint32_t va_ = ti_.x + kVs * o_, ca_ = ti_.y + o_, xr_ = ti_.z;          \
-    const uint32_t cw_ = ca_ & ~3u;                                                \
-    const uint32_t cb_ = __funnelshift_r(*reinterpret_cast<const uint32_t*>(sm + cw_), \
-                                         *reinterpret_cast<const uint32_t*>(sm + cw_ + 4u), \
-                                         8u * (ca_ & 3u));                         \
-    const uint32_t b0_ = cb_ & 0xffu, b1_ = (cb_ >> 8) & 0xffu, b2_ = (cb_ >> 16) & 0xffu; \
-    ValT<V>::load3(sm, va_, v0, v1, v2);                                           \
-    load_xk<Acc, kK>(sm, xr_ + CB_XOFF(b0_), x0);                                  \
-    load_xk<Acc, kK>(sm, xr_ + CB_XOFF(b1_), x1);                                  \
-    load_xk<Acc, kK>(sm, xr_ + CB_XOFF(b2_), x2);                                  \
+    if constexpr (kC == 1) {                                                       \
+      v0 = ValT<V>::load(sm + va_);                                                \
+      load_xk<Acc, kK>(sm, xr_ + CB_XOFF((uint32_t)sm[ca_]), x0);                  \
+    } else {                                                                       \
+      const uint32_t cw_ = ca_ & ~3u;                                              \
+      const uint32_t cb_ = __funnelshift_r(*reinterpret_cast<const uint32_t*>(sm + cw_), \
+                                           *reinterpret_cast<const uint32_t*>(sm + cw_ + 4u), \
+                                           8u * (ca_ & 3u));                       \
+      const uint32_t b0_ = cb_ & 0xffu, b1_ = (cb_ >> 8) & 0xffu, b2_ = (cb_ >> 16) & 0xffu; \
+      ValT<V>::load3(sm, va_, v0, v1, v2);                                         \
+      load_xk<Acc, kK>(sm, xr_ + CB_XOFF(b0_), x0);                                \
+      load_xk<Acc, kK>(sm, xr_ + CB_XOFF(b1_), x1);                                \
+      load_xk<Acc, kK>(sm, xr_ + CB_XOFF(b2_), x2);                                \
+    }                                                                              \
   }
   if (steps) {
     dA = desc[lane];
@@ -409,7 +423,7 @@ __device__ void consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_
   for (uint32_t i = 0; i < steps; ++i) {
     const uint32_t nb = (i + 1 < steps ? 2u * (i + 1) : 2u * i) * CB_VLANES;
     const uint32_t dA_n = desc[nb + lane], dB_n = desc[nb + CB_VLANES + lane];
-    Acc nvA0, nvA1, nvA2, nvB0, nvB1, nvB2;
+    Acc nvA0, nvA1 = Acc(0), nvA2 = Acc(0), nvB0, nvB1 = Acc(0), nvB2 = Acc(0);
     Acc nxA0[kK], nxA1[kK], nxA2[kK], nxB0[kK], nxB1[kK], nxB2[kK];
     CB_LOAD_CHUNK(dA_n, nvA0, nvA1, nvA2, nxA0, nxA1, nxA2);
     CB_LOAD_CHUNK(dB_n, nvB0, nvB1, nvB2, nxB0, nxB1, nxB2);
@@ -423,10 +437,12 @@ __device__ void consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_
       Acc b = eA ? Acc(0) : a1[j];
       a0[j] = pfma(lA > 0, vA0, xA0[j], a0[j]);
       b = pfma(lB > 0, vB0, xB0[j], b);
-      a0[j] = pfma(lA > 1, vA1, xA1[j], a0[j]);
-      b = pfma(lB > 1, vB1, xB1[j], b);
-      a0[j] = pfma(lA > 2, vA2, xA2[j], a0[j]);
-      b = pfma(lB > 2, vB2, xB2[j], b);
+      if constexpr (kC > 1) {
+        a0[j] = pfma(lA > 1, vA1, xA1[j], a0[j]);
+        b = pfma(lB > 1, vB1, xB1[j], b);
+        a0[j] = pfma(lA > 2, vA2, xA2[j], a0[j]);
+        b = pfma(lB > 2, vB2, xB2[j], b);
+      }
       a1[j] = b;
     }
     if (lA | lB) open = true;
@@ -471,23 +487,60 @@ __device__ void consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_
   }
 #undef CB_LOAD_CHUNK
 #undef CB_XOFF
-  sc.crow[lane] = nch == 0 ? -2 : (open ? (int32_t)row : -1);
+  // Rows crossing runs: a lane whose run ends inside a row carries that row's partial sum;
+  // the lane where the row ends (own_row) adds the carries of the lanes before it, in a
+  // fixed order. Rows spanning a few lanes: the owner walks back over them (skipping lanes
+  // without chunks). Units where a row spans more than CB_SCAN_SPAN lanes (analyser flag
+  // CB_MODE_SCAN): a segmented inclusive scan over lanes (Hillis-Steele, 5 steps); lanes
+  // without chunks take the key of the last lane with chunks before them and carry zero.
+  if (!scan_carries) {
+    sc.crow[lane] = nch == 0 ? -2 : (open ? (int32_t)row : -1);
 #pragma unroll
-  for (int j = 0; j < kK; ++j) sc.cval[lane * kK + j] = open ? a0[j] + a1[j] : Acc(0);
-  __syncwarp();
-  if (own_row >= 0) {
-    Acc sum[kK];
+    for (int j = 0; j < kK; ++j) sc.cval[lane * kK + j] = open ? a0[j] + a1[j] : Acc(0);
+    __syncwarp();
+    if (own_row >= 0) {
+      Acc sum[kK];
 #pragma unroll
-    for (int j = 0; j < kK; ++j) sum[j] = own_val[j];
-    for (int l = (int)lane - 1; l >= 0; --l) {
-      const int32_t cr = sc.crow[l];
-      if (cr == -2) continue;
-      if (cr != own_row) break;
+      for (int j = 0; j < kK; ++j) sum[j] = own_val[j];
+      for (int l = (int)lane - 1; l >= 0; --l) {
+        const int32_t cr = sc.crow[l];
+        if (cr == -2) continue;
+        if (cr != own_row) break;
 #pragma unroll
-      for (int j = 0; j < kK; ++j) sum[j] += sc.cval[l * kK + j];
+        for (int j = 0; j < kK; ++j) sum[j] += sc.cval[l * kK + j];
+      }
+#pragma unroll
+      for (int j = 0; j < kK; ++j) sc.srow[own_row * kK + j] = sum[j];
     }
+  } else {
+    constexpr uint32_t kFull = 0xffffffffu;
+    const int32_t key0 = nch == 0 ? -2 : (open ? (int32_t)row : -1);
+    int last = nch == 0 ? -1 : lane;               // last lane with chunks up to this one
 #pragma unroll
-    for (int j = 0; j < kK; ++j) sc.srow[own_row * kK + j] = sum[j];
+    for (int d = 1; d < 32; d <<= 1) {
+      const int o = __shfl_up_sync(kFull, last, d);
+      if (lane >= d && o > last) last = o;
+    }
+    const int32_t key = __shfl_sync(kFull, key0, last < 0 ? lane : last);
+    Acc cv[kK];
+#pragma unroll
+    for (int j = 0; j < kK; ++j) cv[j] = open ? a0[j] + a1[j] : Acc(0);
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int32_t ko = __shfl_up_sync(kFull, key, d);
+      const bool take = lane >= d && ko == key;
+#pragma unroll
+      for (int j = 0; j < kK; ++j) {
+        const Acc vo = __shfl_up_sync(kFull, cv[j], d);
+        if (take) cv[j] += vo;
+      }
+    }
+    const int32_t kprev = __shfl_up_sync(kFull, key, 1);
+#pragma unroll
+    for (int j = 0; j < kK; ++j) {
+      const Acc prev = __shfl_up_sync(kFull, cv[j], 1);
+      if (own_row >= 0) sc.srow[own_row * kK + j] = own_val[j] + (kprev == own_row ? prev : Acc(0));
+    }
   }
   __syncwarp();
 
@@ -516,6 +569,7 @@ __device__ void consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_
         partial[((size_t)u.slot * 16 + lane) * kK + j] = (uint32_t)lane < R ? sc.srow[lane * kK + j] : Acc(0);
     }
   }
+  return true;
 }
 
 template <class V, int kMaxP, int kK>
@@ -528,7 +582,8 @@ __global__ void __launch_bounds__(32 * Geom<V, kK>::kWarps, 1) spmv_kernel(const
   const uint32_t wo = kHeaderBytes + (uint32_t)warp * G::kWarpBytes;   // this warp's buffer
   uint8_t* W = smem_raw + wo;
   const uint32_t w_smem = smem_u32(W);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(W + G::kOffBar);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(W + G::kOffBar);   // the unit's blob landed
+  uint64_t* bar_s = bar + 1;                                      // the unit's records landed
   Scratch<Acc, kK>& sc = *reinterpret_cast<Scratch<Acc, kK>*>(W + G::kOffScratch);
   // this CTA's unit lists of the batch's problems (stored contiguously per CTA), one after
   // another in ticket order
@@ -543,6 +598,7 @@ __global__ void __launch_bounds__(32 * Geom<V, kK>::kWarps, 1) spmv_kernel(const
   for (uint32_t i = threadIdx.x; i < 256u; i += blockDim.x) hd.ident[i] = (uint8_t)((i & 15u) << 4);
   if (lane == 0) {
     mbar_init(bar, 1);
+    mbar_init(bar_s, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
@@ -580,29 +636,39 @@ __global__ void __launch_bounds__(32 * Geom<V, kK>::kWarps, 1) spmv_kernel(const
     const RunArgs& a = b.p[problem_of(j)];
     if (lane < 16) reinterpret_cast<uint32_t*>(W + G::kOffUnit)[lane] = dw;
     __syncwarp();
-    // the next unit's descriptor is fetched while this one is staged and computed
-    const uint32_t jn = grab();
-    const uint32_t dwn = desc_word(jn);
     if (lane == 0) {
       // the buffer was last read and written through the generic proxy
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       const CbUnit& u = *reinterpret_cast<const CbUnit*>(W + G::kOffUnit);
-      mbar_arrive_expect_tx(bar, u.nbytes + u.blob_bytes);
-      if (u.nbytes) bulk_g2s(W + G::kOffStream, a.stream + (size_t)u.byte_lo16 * 16, u.nbytes, bar);
+      mbar_arrive_expect_tx(bar, u.blob_bytes);
       if (u.blob_bytes) bulk_g2s(W + G::kOffBlob, a.blob + (size_t)u.blob16 * 16, u.blob_bytes, bar);
+      mbar_arrive_expect_tx(bar_s, u.nbytes);
+      if (u.nbytes) bulk_g2s(W + G::kOffStream, a.stream + (size_t)u.byte_lo16 * 16, u.nbytes, bar_s);
     }
-    const bool ok = __all_sync(0xffffffffu, mbar_wait(bar, phase));
-    phase ^= 1u;
+    // the next unit's descriptor is fetched while this one is staged and computed
+    const uint32_t jn = grab();
+    const uint32_t dwn = desc_word(jn);
+    // the blob (tile records, restore_cols slice, schedule) is enough to start the x
+    // gather and the unit's set-up; the records are waited for just before the walk
+    bool ok = __all_sync(0xffffffffu, mbar_wait(bar, phase));
+    if (ok) {
+      gather_x<V, kK>(a, W, w_smem, lane);
+      __syncwarp();
+      if (reinterpret_cast<const CbUnit*>(W + G::kOffUnit)->mode & CB_MODE_ENTRY)
+        ok = consume_unit<V, kK, 1>(a, smem_raw, wo, ident_off, sc, lane, bar_s, phase);
+      else
+        ok = consume_unit<V, kK, CB_CHUNK>(a, smem_raw, wo, ident_off, sc, lane, bar_s, phase);
+      __syncwarp();
+    }
     if (!ok) {
       if (lane == 0) set_error(a, 2u);
-      // the copies may still land in the buffer: give them a second bounded wait
-      mbar_wait(bar, phase ^ 1u);
+      // copies may still land in the buffer: give them a second bounded wait, then stop
+      mbar_wait(bar, phase);
+      mbar_wait(bar_s, phase);
+      cp_async_wait_all();
       break;
     }
-    gather_x<V, kK>(a, W, w_smem, lane);
-    __syncwarp();
-    consume_unit<V, kK>(a, smem_raw, wo, ident_off, sc, lane);
-    __syncwarp();
+    phase ^= 1u;
     j = jn;
     dw = dwn;
   }
@@ -630,8 +696,18 @@ __global__ void __launch_bounds__(256) combine_kernel(const __grid_constant__ Ba
 #pragma unroll
   for (int j = 0; j < kK; ++j) {
     const Acc* p = static_cast<const Acc*>(a.partial) + ((size_t)s.slot0 * 16 + r) * kK + j;
-    Acc sum = Acc(0);
-    for (uint32_t k = 0; k < s.nparts; ++k) sum += p[(size_t)k * 16 * kK];
+    // parts k = q (mod 4) into four independent sums, then a fixed tree: rows of power-law
+    // matrices can have hundreds of parts, and one chain of dependent adds would be slow
+    Acc t[4] = {Acc(0), Acc(0), Acc(0), Acc(0)};
+    uint32_t k = 0;
+    for (; k + 4 <= s.nparts; k += 4) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) t[q] += p[(size_t)(k + q) * 16 * kK];
+    }
+    if (k < s.nparts) t[0] += p[(size_t)k * 16 * kK];
+    if (k + 1 < s.nparts) t[1] += p[(size_t)(k + 1) * 16 * kK];
+    if (k + 2 < s.nparts) t[2] += p[(size_t)(k + 2) * 16 * kK];
+    const Acc sum = s.nparts <= 2 ? t[0] + t[1] : (t[0] + t[1]) + (t[2] + t[3]);
     Acc* y = static_cast<Acc*>(a.y) + (int64_t)j * a.ldy;
     Acc v = a.alpha_one ? sum : (Acc)a.alpha * sum;
     if (a.beta_nonzero) v = fma((Acc)a.beta, y[gr], v);

@@ -186,3 +186,14 @@ def test_storage_model_matches_oracle_formula(bd):
         assert st["model_bytes_csr"] == ref["csr"]
         assert st["model_bytes_bsr16"] == ref["bsr16"]
         assert st["n_fmt"][0] == S.tile_nnz.size
+
+
+def test_schedule_mode_follows_piece_sizes(bd):
+    """Units whose rows hold one or two entries per tile get single-entry schedules; the
+    FEM matrix's 3x3 blocks (pieces of about three entries) keep 3-entry chunks."""
+    with host(bd, I.rmat(13, 16, seed=2)) as M:
+        st = M.stats()
+        assert st["n_entry_mode_units"] > 0.15 * st["n_units"]
+    with host(bd, I.fem_block_band(n_rows=6000, n_block_rows=2000, half_band=300, seed=3)) as M:
+        st = M.stats()
+        assert st["n_entry_mode_units"] < 0.1 * st["n_units"]
