@@ -37,6 +37,7 @@ WORKLOADS = {
     "fem3x3_band_256k": "FP64 FEM-like 3x3 block band, quarter size (262,144 rows), for profiling",
     "rmat_s21": "FP64 R-MAT scale 21, edge factor 16, (a,b,c,d) = (.57,.19,.19,.05), duplicates summed, "
                 "U[-1,1] values, seed 2",
+    "rmat_s19": "FP64 R-MAT scale 19 (R-MAT recipe above), for profiling",
     "laplace2d_64": "FP64 2D 5-point Laplacian on a 64x64 grid, x U[-1,1], seed 0",
 }
 # FP64 FMA issue rate of a GB300 SM: each of the 4 SM sub-partitions completes one warp-wide
@@ -152,6 +153,35 @@ def multi_rhs_bench(M, A, x, vec, stream, ks=(1, 8, 32), reps=20):
         ms = e0.elapsed_time(e1) / reps
         out.append({"k": k, "ms": round(ms, 4), "gflops": round(2.0 * A.nnz * k / (ms * 1e-3) / 1e9, 1)})
         del X, Y
+    return out
+
+
+# The ablation of Sec. 4.4 (Fig. 12) as analysis options: I = intra-block data aggregation
+# only (packed records, no column aggregation, one sub-block format: COO below 256 entries),
+# II = + column aggregation and format selection (the paper's th0, th1, th2), full = II +
+# the load balance of Algorithm 2 (I and II deal units to CTAs round-robin).
+ABLATION = [
+    ("CB-SpMV-I", dict(col_agg=0, th1=256, th2=256, load_balance=False)),
+    ("CB-SpMV-II", dict(col_agg=-1, th1=32, th2=128, load_balance=False)),
+    ("CB-SpMV (full)", dict(col_agg=-1, th1=32, th2=128, load_balance=True)),
+]
+
+
+def ablation_bench(bd, A, x, vec, dtype, stream, reps=200):
+    import torch
+    out = []
+    xd = torch.from_numpy(x.astype(vec)).cuda()
+    yd = torch.empty(A.m, dtype=xd.dtype, device="cuda")
+    for name, opts in ABLATION:
+        with bd.BlockedMatrix(A, value_dtype=dtype, stream=stream, **opts) as M:
+            kt = M.time_kernels(xd, yd, reps, stream=stream)
+            ms = kt["ms_main"] + kt["ms_combine"]
+            st = M.stats()
+            out.append({"config": name, "ms": round(ms, 4), "gflops": round(2.0 * A.nnz / (ms * 1e-3) / 1e9, 1),
+                        "aggregated": bool(st["aggregated"]), "formats_coo_csr_dense": st["n_fmt"],
+                        "worker_load_max_over_mean": round(st["worker_load_max"] / max(st["worker_load_mean"], 1), 3)})
+    for i in range(1, len(out)):
+        out[i]["speedup_vs_previous"] = round(out[i - 1]["ms"] / out[i]["ms"], 3)
     return out
 
 
@@ -349,6 +379,7 @@ def main():
     ap.add_argument("--cusparse-steps", type=int, default=200)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-multi", action="store_true", help="skip the k right-hand-side measurement")
+    ap.add_argument("--no-ablation", action="store_true", help="skip the ablation (Sec. 4.4) measurement")
     ap.add_argument("--serve-full", action="store_true",
                     help="serving measurement on the full pool (17 Laplacians, 15 R-MAT, 10,000 requests)")
     ap.add_argument("--traffic-bytes", type=float, default=None,
@@ -431,6 +462,7 @@ def main():
         del flush
         y_ours = yd.cpu().numpy().astype(np.float64)
         multi = multi_rhs_bench(M, A, x, vec, stream) if not args.no_multi else None
+        abl = ablation_bench(bd, A, x, vec, args.dtype, stream) if not args.no_ablation else None
         M.check_device(stream)
         sms = torch.cuda.get_device_properties(local).multi_processor_count
 
@@ -519,6 +551,8 @@ def main():
             line["cusparse_csr"] = cus
         if multi:
             line["multi_rhs"] = {"api": "cbspmv_run_multi (passes of 4 vectors)", "results": multi}
+        if abl:
+            line["ablation"] = abl
         if not args.no_serve and ws == 1:
             line["serving"] = serve_bench("full" if args.serve_full else "small")
         if err:

@@ -268,4 +268,8 @@ def config_matrix(name: str) -> tuple[CSR, np.ndarray]:
     if name == "rmat_s21":
         A = rmat(21, 16, seed=2)
         return A, vector_x(A.n, 2)
+    if name == "rmat_s19":
+        # smaller profiling case of the R-MAT family (packed stream still > L2)
+        A = rmat(19, 16, seed=2)
+        return A, vector_x(A.n, 2)
     raise KeyError(name)
