@@ -46,6 +46,22 @@ WORKLOADS = {
 FP64_FMA_LANES_PER_SM_CYCLE = 2.0
 L2_BYTES = 129 * 2 ** 20
 
+# DRAM bytes (read + write) per launch of the run kernel from one ncu capture of the same
+# kernel revision (profiles/): the quarter-size FEM case and R-MAT scale 19, scaled to the
+# full workload by its number of stored entries. Used only when the loaded library reports
+# the same revision; otherwise the roofline's traffic is null.
+KERNEL_TRAFFIC = {
+    "run kernel rev 8": {("fem3x3_band_1m", "f64"): 1.0929e9, ("fem3x3_band_1m", "bf16"): 0.5832e9,
+                         ("rmat_s21", "f64"): 0.5630e9},
+}
+
+
+def measured_traffic(version: str, workload: str, dtype: str):
+    for rev, table in KERNEL_TRAFFIC.items():
+        if version.endswith(rev + ")"):
+            return table.get((workload, dtype))
+    return None
+
 
 def fp64_peak_gflops(sms: int, sm_max_mhz: float) -> float:
     return sms * FP64_FMA_LANES_PER_SM_CYCLE * 2.0 * sm_max_mhz / 1e3
@@ -500,12 +516,14 @@ def main():
         fmax = clocks.get("sm_max_mhz") or 2070.0
         peak_alu = round(fp64_peak_gflops(sms, fmax), 1)
         k_ms = kt["ms_main"]
+        traffic = args.traffic_bytes if args.traffic_bytes is not None else \
+            measured_traffic(bd.version(), args.workload, args.dtype)
         k_gf = flops / (k_ms * 1e-3) / 1e9
         k_gbs = algo_bytes / (k_ms * 1e-3) / 1e9
         if lp:
             roof = {"bound": "hbm", "kernel": "spmv_kernel<%s>" % args.dtype, "achieved": round(k_gbs, 2),
                     "peak": peak, "unit": "GB/s", "frac": round(k_gbs / peak, 4), "peak_kind": peak_kind,
-                    "traffic": args.traffic_bytes, "kernel_ms": round(k_ms, 5),
+                    "traffic": traffic, "kernel_ms": round(k_ms, 5),
                     "combine_ms": round(kt["ms_combine"], 5), "bytes_per_launch": int(algo_bytes),
                     "gflops": round(k_gf, 2),
                     "note": "FP32 FMA is far from binding; the bytes model (values + coordinates + "
@@ -513,7 +531,7 @@ def main():
         else:
             roof = {"bound": "alu", "kernel": "spmv_kernel<f64>", "achieved": round(k_gf, 2),
                     "peak": peak_alu, "unit": "GFLOP/s", "frac": round(k_gf / peak_alu, 4),
-                    "traffic": args.traffic_bytes,
+                    "traffic": traffic,
                     "kernel_ms": round(k_ms, 5), "combine_ms": round(kt["ms_combine"], 5),
                     "flops_per_launch": int(flops),
                     "note": "FP64 FMA pipe bound: peak = SMs x 2 FP64 FMA lanes/cycle x 2 flops x max SM "

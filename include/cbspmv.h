@@ -83,7 +83,8 @@ typedef struct {
  *   load_balance: 1 (default) spread units over workers by the longest-first
  *        priority-queue rule; 0 deal them out round-robin in matrix order (ablation).
  *   device: CUDA device ordinal for the handle's memory; -1 builds a host-only handle
- *        (analysis, export and statistics work; run calls return CBSPMV_ERR_INVALID). */
+ *        (analysis, export and statistics work; run calls return CBSPMV_ERR_INVALID).
+ *   keep_value_map: 0 (default) or 1, see cbspmv_update_values. */
 typedef struct {
   double th0;
   int th1, th2;
@@ -92,7 +93,9 @@ typedef struct {
   int unit_work;
   int load_balance;
   int device;
-  int reserved[8];
+  int keep_value_map;       /* 1: record each entry's value slot (4 bytes per entry on the
+                               device) so cbspmv_update_values can re-pack new values */
+  int reserved[7];
 } cbspmv_opts_t;
 
 /* Statistics of an analysed matrix. Byte counts follow the storage model of Sec. 4.4.1
@@ -247,6 +250,19 @@ cbspmv_status_t cbspmv_analyze_tuned(const cbspmv_csr_t* A, const cbspmv_opts_t*
                                      void* stream, int reps, cbspmv_handle_t* out,
                                      cbspmv_tune_report_t* report);
 
+/* Replaces the values of an analysed matrix whose sparsity pattern is unchanged (the case
+ * that amortises the analysis of Sec. 3 over repeated products, Sec. 4.5): val holds the
+ * new FP64 values in the order of the CSR given to cbspmv_analyze (nnz entries; host
+ * pointer when on_device = 0, device pointer when 1). The values are converted to the
+ * handle's storage type exactly as the analysis converts them and written into the packed
+ * records on the device by one kernel; the blocked structure is unchanged, so every later
+ * product and export is that of a fresh analysis of the new values. Requires a device
+ * handle analysed with opts.keep_value_map = 1. Asynchronous on `stream` (a host array
+ * is copied through a staging buffer owned by the handle, allocated on first use).
+ * Errors: CBSPMV_ERR_INVALID (NULL val with nnz > 0, no value map), CBSPMV_ERR_CUDA. */
+cbspmv_status_t cbspmv_update_values(cbspmv_handle_t h, const double* val, int on_device,
+                                     void* stream);
+
 /* Measurement support (the paper has no counterpart): runs the product of cbspmv_run
  * `reps` times (1..100000) on `stream`, with CUDA events recorded on that stream around
  * each of its kernel launches, and returns the mean device time per run of the main run
@@ -370,7 +386,7 @@ cbspmv_status_t cbspmv_destroy(cbspmv_handle_t h);
 /* Message of the last failed call on this host thread ("" if none). */
 const char* cbspmv_last_error(void);
 
-/* Library version string. */
+/* Library version string, including the run kernel's revision ("run kernel rev N"). */
 const char* cbspmv_version(void);
 
 #ifdef __cplusplus

@@ -37,7 +37,8 @@ class Csr(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("th0", ctypes.c_double), ("th1", ctypes.c_int), ("th2", ctypes.c_int),
                 ("col_agg", ctypes.c_int), ("value_dtype", ctypes.c_int), ("unit_work", ctypes.c_int),
-                ("load_balance", ctypes.c_int), ("device", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
+                ("load_balance", ctypes.c_int), ("device", ctypes.c_int), ("keep_value_map", ctypes.c_int),
+                ("reserved", ctypes.c_int * 7)]
 
 
 class Stats(ctypes.Structure):
@@ -112,6 +113,7 @@ SIGNATURES = {
     "cbspmv_analyze_batched": [_I, _P, ctypes.POINTER(Opts), _P, _P],
     "cbspmv_run_batched": [_I, _P, _P, _P, _P, _P, _P, _P],
     "cbspmv_check_device": [_P, _P],
+    "cbspmv_update_values": [_P, _P, _I, _P],
     "cbspmv_export_csr": [_P, _P, _P, _P],
     "cbspmv_export_blocked": [_P, _P, _P, _P, _P, _P, _P],
     "cbspmv_get_stats": [_P, ctypes.POINTER(Stats)],
@@ -215,13 +217,14 @@ def _csr_struct(A):
 
 
 def _make_opts(th0=0.15, th1=32, th2=128, col_agg=-1, value_dtype="f64", unit_work=0,
-               load_balance=True, device=0) -> Opts:
+               load_balance=True, device=0, keep_value_map=False) -> Opts:
     o = default_opts()
     o.th0, o.th1, o.th2, o.col_agg = th0, th1, th2, col_agg
     o.value_dtype = DTYPES[value_dtype]
     o.unit_work = unit_work
     o.load_balance = 1 if load_balance else 0
     o.device = device
+    o.keep_value_map = 1 if keep_value_map else 0
     return o
 
 
@@ -243,12 +246,12 @@ class BlockedMatrix:
     (e.g. inputs.CSR). device=-1 gives a host-only handle (analysis and export only)."""
 
     def __init__(self, A, *, th0=0.15, th1=32, th2=128, col_agg=-1, value_dtype="f64",
-                 unit_work=0, load_balance=True, device=0, stream=None):
+                 unit_work=0, load_balance=True, device=0, stream=None, keep_value_map=False):
         """A's arrays may be host arrays or CUDA torch tensors (device-resident input)."""
         self._h = ctypes.c_void_p(None)
         self.m, self.n = int(A.m), int(A.n)
         csr, _keep, self.nnz = _csr_struct(A)
-        o = _make_opts(th0, th1, th2, col_agg, value_dtype, unit_work, load_balance, device)
+        o = _make_opts(th0, th1, th2, col_agg, value_dtype, unit_work, load_balance, device, keep_value_map)
         self.device = device
         self.value_dtype = value_dtype
         self.vec = "f64" if value_dtype == "f64" else "f32"
@@ -312,6 +315,27 @@ class BlockedMatrix:
         _check(lib().cbspmv_run_host(self._h, x.ctypes.data, y.ctypes.data, float(alpha), float(beta),
                                      _stream_ptr(stream)))
         return y
+
+    def update_values(self, val, stream=None):
+        """New values (CSR order of the analysed matrix, FP64): a numpy array (copied in) or a
+        float64 CUDA tensor, re-packed on the device (requires keep_value_map=True)."""
+        try:
+            import torch
+            dev = isinstance(val, torch.Tensor) and val.is_cuda
+        except ImportError:
+            dev = False
+        if dev:
+            if val.dtype != torch.float64 or not val.is_contiguous() or val.numel() < self.nnz:
+                raise TypeError("val must be a contiguous float64 CUDA tensor with nnz entries")
+            ptr = val.data_ptr() or None
+        else:
+            val = np.ascontiguousarray(val, dtype=np.float64)
+            if val.size < self.nnz:
+                raise ValueError("val must hold nnz entries")
+            self._val_keep = val
+            ptr = val.ctypes.data
+        s = _stream_ptr(stream) if self.device >= 0 else None
+        _check(lib().cbspmv_update_values(self._h, ptr, 1 if dev else 0, s))
 
     def check_device(self, stream=None):
         _check(lib().cbspmv_check_device(self._h, _stream_ptr(stream)))

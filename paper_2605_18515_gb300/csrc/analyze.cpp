@@ -19,6 +19,7 @@
 #include <thread>
 
 #include "cb_plan.h"
+#include "cb_round.h"
 
 namespace cb {
 namespace {
@@ -76,6 +77,7 @@ struct BlockRowOut {
   std::vector<uint8_t> fmt;
   std::vector<uint8_t> rowcnt;     // 16 per tile: multiply-adds of each tile row
   std::vector<int32_t> distinct;   // distinct columns in order (aggregated only)
+  std::vector<std::pair<int64_t, uint32_t>> vslot;   // (CSR position, value byte offset in `bytes`)
 };
 
 // Entries of one block row as (key = col << 4 | local row, CSR position), sorted by key.
@@ -88,65 +90,11 @@ void gather_block_row(const cbspmv_csr_t& A, int64_t b, std::vector<std::pair<ui
   std::sort(e.begin(), e.end());
 }
 
-}  // namespace
-
-// v rounded to the nearest number of a binary floating-point format with p significand
-// bits (implicit bit included), smallest normal exponent emin and largest exponent emax;
-// ties go to the even significand, magnitudes beyond the largest finite number become
-// infinities, below the smallest normal the quantum stays 2^(emin - p + 1) (gradual
-// underflow); NaN and signed zeros pass through (IEEE 754 roundTiesToEven). The result
-// is exact in double.
-double round_to_format(double v, int p, int emin, int emax) {
-  if (!std::isfinite(v) || v == 0.0) return v;
-  int e = std::ilogb(v);                         // floor(log2 |v|)
-  if (e > emax) return std::copysign(INFINITY, v);
-  if (e < emin) e = emin;
-  const int q = e - (p - 1);                     // exponent of the quantum
-  const double r = std::nearbyint(std::ldexp(v, -q)) ;   // the default mode rounds ties to even
-  const double out = std::ldexp(r, q);
-  if (std::ilogb(out) > emax) return std::copysign(INFINITY, v);
-  return out;
-}
-
-namespace {
-
-// IEEE binary16 bits of a double that is exactly representable in binary16 (or +-inf).
-uint16_t half_bits(double h) {
-  const uint16_t sign = std::signbit(h) ? 0x8000u : 0u;
-  if (std::isnan(h)) return 0x7e00u;
-  if (std::isinf(h)) return sign | 0x7c00u;
-  const double a = std::fabs(h);
-  if (a == 0.0) return sign;
-  const int e = std::ilogb(a);
-  if (e < -14) return sign | (uint16_t)std::ldexp(a, 24);          // subnormal: a / 2^-24
-  const uint32_t mant = (uint32_t)std::ldexp(a, 10 - e) - 1024u;   // 10 fraction bits
-  return sign | (uint16_t)((uint32_t)(e + 15) << 10) | (uint16_t)mant;
-}
-
 // Stores v in the handle's value type, rounded to nearest (ties to even) directly from
 // the FP64 input; the rounded value is exact in the stored type.
 void write_value(uint8_t* dst, double v, int dtype) {
-  switch (dtype) {
-    case CBSPMV_F64: std::memcpy(dst, &v, 8); break;
-    case CBSPMV_F32: {
-      const float f = (float)round_to_format(v, 24, -126, 127);
-      std::memcpy(dst, &f, 4);
-      break;
-    }
-    case CBSPMV_BF16: {
-      const float f = (float)round_to_format(v, 8, -126, 127);     // exact in binary32
-      uint32_t b;
-      std::memcpy(&b, &f, 4);
-      const uint16_t h = std::isnan(f) ? (uint16_t)0x7fc0u : (uint16_t)(b >> 16);
-      std::memcpy(dst, &h, 2);
-      break;
-    }
-    default: {
-      const uint16_t h = half_bits(round_to_format(v, 11, -14, 15));
-      std::memcpy(dst, &h, 2);
-      break;
-    }
-  }
+  const uint64_t bits = storage_bits(v, dtype);
+  std::memcpy(dst, &bits, dtype == CBSPMV_F64 ? 8 : dtype == CBSPMV_F32 ? 4 : 2);   // little endian
 }
 
 // The stored value at src widened exactly to double.
@@ -173,7 +121,7 @@ double read_value(const uint8_t* src, int dtype) {
 
 int value_size(int dtype) { return dtype == CBSPMV_F64 ? 8 : dtype == CBSPMV_F32 ? 4 : 2; }
 
-void build_block_row(const cbspmv_csr_t& A, int64_t b, bool agg, int th1, int th2, int dtype,
+void build_block_row(const cbspmv_csr_t& A, int64_t b, bool agg, int th1, int th2, int dtype, bool keep_slots,
                      std::vector<std::pair<uint64_t, int64_t>>& e, BlockRowOut& out) {
   const int vsize = value_size(dtype);
   gather_block_row(A, b, e);
@@ -228,6 +176,7 @@ void build_block_row(const cbspmv_csr_t& A, int64_t b, bool agg, int th1, int th
         uint32_t pos = t.first;  // row * 16 + col
         rec[pos >> 3] |= (uint8_t)(1u << (pos & 7));
         write_value(rec + 32 + pos * vsize, A.val[t.second], dtype);
+        if (keep_slots) out.vslot.emplace_back(t.second, base + 32 + pos * vsize);
       }
     } else {
       uint8_t* idx = rec;
@@ -244,6 +193,7 @@ void build_block_row(const cbspmv_csr_t& A, int64_t b, bool agg, int th1, int th
         uint32_t lr = tile[i].first >> 4, lc = tile[i].first & 15u;
         idx[i] = (uint8_t)(lr | (lc << 4));          // row low nibble, col high nibble
         write_value(rec + voff + (uint32_t)i * vsize, A.val[tile[i].second], dtype);
+        if (keep_slots) out.vslot.emplace_back(tile[i].second, base + voff + (uint32_t)i * vsize);
       }
     }
     out.off.push_back(base);
@@ -303,6 +253,7 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
     return CBSPMV_ERR_INVALID;
   }
   if (opts.col_agg < -1 || opts.col_agg > 1) { *msg = "col_agg must be -1, 0 or 1"; return CBSPMV_ERR_INVALID; }
+  if (opts.keep_value_map != 0 && opts.keep_value_map != 1) { *msg = "keep_value_map must be 0 or 1"; return CBSPMV_ERR_INVALID; }
   if (n_workers <= 0) { *msg = "no workers"; return CBSPMV_ERR_INVALID; }
   cbspmv_status_t st = validate(A, msg);
   if (st != CBSPMV_OK) return st;
@@ -347,7 +298,7 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
   parallel_for(nbr, 64, [&](int64_t lo, int64_t hi) {
     std::vector<std::pair<uint64_t, int64_t>> e;
     for (int64_t b = lo; b < hi; ++b)
-      build_block_row(A, b, p.aggregated, opts.th1, opts.th2, p.value_dtype, e, rows[b]);
+      build_block_row(A, b, p.aggregated, opts.th1, opts.th2, p.value_dtype, opts.keep_value_map != 0, e, rows[b]);
   });
   // prefix sums over block rows: tiles, stream bytes, distinct columns
   std::vector<int64_t> tile_off(nbr + 1, 0), byte_off(nbr + 1, 0);
@@ -359,6 +310,18 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
   }
   const int64_t ntiles = tile_off[nbr];
   if (byte_off[nbr] / 16 >= (1LL << 32)) { *msg = "packed stream exceeds 64 GiB"; return CBSPMV_ERR_UNSUPPORTED; }
+  if (opts.keep_value_map && byte_off[nbr] / p.vsize >= (1LL << 32)) {
+    *msg = "packed stream too large for a value map";
+    return CBSPMV_ERR_UNSUPPORTED;
+  }
+  if (opts.keep_value_map) {
+    try {
+      p.value_slot.assign((size_t)A.nnz, 0);
+    } catch (...) {
+      *msg = "host allocation failed";
+      return CBSPMV_ERR_OOM;
+    }
+  }
   p.restore_cols_len = p.aggregated ? p.cols_offset[nbr] : 0;
   std::vector<uint8_t> rowcnt;
   try {
@@ -388,6 +351,8 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
       if (p.aggregated && !o.distinct.empty())
         std::memcpy(p.restore_cols.data() + p.cols_offset[b], o.distinct.data(), o.distinct.size() * 4);
       if (!o.rowcnt.empty()) std::memcpy(rowcnt.data() + (size_t)tile_off[b] * 16, o.rowcnt.data(), o.rowcnt.size());
+      for (const auto& vs : o.vslot) p.value_slot[vs.first] = (uint32_t)((byte_off[b] + vs.second) / p.vsize);
+      std::vector<std::pair<int64_t, uint32_t>>().swap(o.vslot);
       BlockRowOut().bytes.swap(o.bytes);
       std::vector<uint8_t>().swap(o.rowcnt);
     }

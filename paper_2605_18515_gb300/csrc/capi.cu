@@ -79,6 +79,8 @@ struct cbspmv_handle_s {
   void* d_xstage = nullptr;
   void* d_ystage = nullptr;
   void* d_partial_multi = nullptr;   // partial sums of 4-vector passes (allocated on first use)
+  uint32_t* d_vslot = nullptr;       // value slot per CSR entry (keep_value_map)
+  double* d_valstage = nullptr;      // staging of host values for cbspmv_update_values
   // bytes of one x or y element: double for FP64 values, float for the reduced types
   size_t esize() const { return plan.value_dtype == CBSPMV_F64 ? 8 : 4; }
 
@@ -87,7 +89,7 @@ struct cbspmv_handle_s {
     DeviceGuard g(device);
     cudaDeviceSynchronize();
     void* ptrs[] = {d_stream, d_tiles, d_rcols, d_units, d_blob, d_wunits, d_woff, d_partial, d_split_rows,
-                    d_err, d_xstage, d_ystage, d_partial_multi};
+                    d_err, d_xstage, d_ystage, d_partial_multi, d_vslot, d_valstage};
     for (void* p : ptrs)
       if (p) cudaFree(p);
     d_stream = nullptr;
@@ -103,6 +105,8 @@ struct cbspmv_handle_s {
     d_xstage = nullptr;
     d_ystage = nullptr;
     d_partial_multi = nullptr;
+    d_vslot = nullptr;
+    d_valstage = nullptr;
   }
 };
 
@@ -221,6 +225,7 @@ cbspmv_status_t cbspmv_analyze(const cbspmv_csr_t* A, const cbspmv_opts_t* opts_
   step(upload(&h->d_woff, p.worker_off.data(), p.worker_off.size(), s));
   if (e == cudaSuccess) e = cudaMalloc(&h->d_partial, (size_t)(p.n_slots ? p.n_slots : 1) * 16 * h->esize());
   step(upload(&h->d_split_rows, p.split_rows.data(), p.split_rows.size(), s));
+  if (!p.value_slot.empty()) step(upload(&h->d_vslot, p.value_slot.data(), p.value_slot.size(), s));
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_err, 4);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, 4, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -230,8 +235,9 @@ cbspmv_status_t cbspmv_analyze(const cbspmv_csr_t* A, const cbspmv_opts_t* opts_
     return fail(e == cudaErrorMemoryAllocation ? CBSPMV_ERR_OOM : CBSPMV_ERR_CUDA, "upload failed: %s",
                 cudaGetErrorString(e));
   }
-  // the packed stream now lives on the device; export reads it back from there
+  // the packed stream and the value map now live on the device; export reads it back
   std::vector<uint8_t>().swap(p.stream);
+  std::vector<uint32_t>().swap(p.value_slot);
   *out = h;
   return ok();
 }
@@ -464,6 +470,26 @@ cbspmv_status_t cbspmv_run_host(cbspmv_handle_t h, const void* x_host, void* y_h
   if (st != CBSPMV_OK) return st;
   if (p.m) CB_CUDA(cudaMemcpyAsync(y_host, h->d_ystage, (size_t)p.m * es, cudaMemcpyDeviceToHost, s));
   CB_CUDA(cudaStreamSynchronize(s));
+  return ok();
+}
+
+cbspmv_status_t cbspmv_update_values(cbspmv_handle_t h, const double* val, int on_device, void* stream) {
+  if (!valid_handle(h)) return fail(CBSPMV_ERR_INVALID, "invalid handle");
+  if (h->device < 0) return fail(CBSPMV_ERR_INVALID, "host-only handle");
+  const cb::Plan& p = h->plan;
+  if (!h->d_vslot) return fail(CBSPMV_ERR_INVALID, "the handle was analysed without keep_value_map");
+  if (p.nnz == 0) return ok();
+  if (!val) return fail(CBSPMV_ERR_INVALID, "NULL values");
+  DeviceGuard g(h->device);
+  CB_CUDA(g.err);
+  cudaStream_t s = (cudaStream_t)stream;
+  const double* dval = val;
+  if (!on_device) {
+    if (!h->d_valstage) CB_CUDA(cudaMalloc((void**)&h->d_valstage, (size_t)p.nnz * 8));
+    CB_CUDA(cudaMemcpyAsync(h->d_valstage, val, (size_t)p.nnz * 8, cudaMemcpyHostToDevice, s));
+    dval = h->d_valstage;
+  }
+  CB_CUDA(cb::launch_repack(h->d_stream, h->d_vslot, dval, p.nnz, p.value_dtype, h->grid, s));
   return ok();
 }
 
@@ -730,7 +756,9 @@ cbspmv_status_t cbspmv_destroy(cbspmv_handle_t h) {
 
 const char* cbspmv_last_error(void) { return g_err.c_str(); }
 
-const char* cbspmv_version(void) { return "cbspmv 0.1 (sm_103a)"; }
+// The run-kernel revision changes whenever the kernel's code changes (measurements taken
+// with a profiler are tied to it).
+const char* cbspmv_version(void) { return "cbspmv 0.3 (sm_103a; run kernel rev 8)"; }
 
 }  // extern "C"
 

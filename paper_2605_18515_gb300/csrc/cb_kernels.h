@@ -47,6 +47,10 @@ cudaError_t launch_spmv_batch(const RunArgs* a, int count, int grid, cudaStream_
 // Sets every run-kernel instantiation's shared-memory limit on the current device (done
 // lazily by the launches too; needed before a stream capture).
 cudaError_t configure_kernels();
+// Re-packs nnz new FP64 values (CSR order) into the packed stream at the recorded value
+// slots, converted to the storage type dtype.
+cudaError_t launch_repack(uint8_t* stream, const uint32_t* slot, const double* val, int64_t nnz, int dtype,
+                          int grid, cudaStream_t s);
 
 }  // namespace cb
 #endif

@@ -33,6 +33,7 @@ struct Plan {
   std::vector<CbSplitRow> split_rows;  // block rows cut into several units
   std::vector<uint32_t> worker_units;  // unit ids grouped by worker (CTA)
   std::vector<uint32_t> worker_off;    // n_workers + 1
+  std::vector<uint32_t> value_slot;    // per CSR entry: stream offset of its value / vsize (optional)
   int n_workers = 0;
   int n_split_rows = 0;
   int n_slots = 0;
@@ -53,10 +54,6 @@ cbspmv_status_t decode_to_csr(int64_t m, int64_t n, int value_dtype, bool aggreg
                               size_t stream_size, const int32_t* restore_cols,
                               size_t restore_len, int64_t* row_ptr, int32_t* col, double* val,
                               int64_t nnz_expected, std::string* msg);
-
-// v rounded to nearest, ties to even, in a binary format with p significand bits and
-// exponent range [emin, emax] (the conversion of FP64 input values to the storage type).
-double round_to_format(double v, int p, int emin, int emax);
 
 }  // namespace cb
 #endif

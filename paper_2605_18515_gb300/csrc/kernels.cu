@@ -45,6 +45,7 @@
 
 #include "cb_layout.h"
 #include "cb_kernels.h"
+#include "cb_round.h"
 
 namespace cb {
 namespace {
@@ -779,7 +780,32 @@ cudaError_t launch_dispatch(const BatchArgs<kMaxP>& b, int grid, cudaStream_t st
   }
 }
 
+// New values into the packed records: value k (CSR order, FP64) goes to value slot
+// slot[k] of the stream, converted to the storage type like the analysis converts it.
+__global__ void __launch_bounds__(256) repack_values_kernel(uint8_t* stream, const uint32_t* slot,
+                                                            const double* val, int64_t nnz, int dtype) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += stride) {
+    const uint64_t bits = storage_bits(val[k], dtype);
+    const size_t s = slot[k];
+    switch (dtype) {
+      case CBSPMV_F64: reinterpret_cast<uint64_t*>(stream)[s] = bits; break;
+      case CBSPMV_F32: reinterpret_cast<uint32_t*>(stream)[s] = (uint32_t)bits; break;
+      default: reinterpret_cast<uint16_t*>(stream)[s] = (uint16_t)bits; break;
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_repack(uint8_t* stream, const uint32_t* slot, const double* val, int64_t nnz, int dtype,
+                          int grid, cudaStream_t s) {
+  if (nnz == 0) return cudaSuccess;
+  const int64_t blocks = (nnz + 255) / 256;
+  repack_values_kernel<<<(int)(blocks < 8 * (int64_t)grid ? blocks : 8 * (int64_t)grid), 256, 0, s>>>(
+      stream, slot, val, nnz, dtype);
+  return cudaGetLastError();
+}
 
 size_t spmv_smem_bytes() {
   const uint32_t a = Geom<double>::kSmem, b = Geom<float>::kSmem, c = Geom<__half>::kSmem;

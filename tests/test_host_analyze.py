@@ -197,3 +197,15 @@ def test_schedule_mode_follows_piece_sizes(bd):
     with host(bd, I.fem_block_band(n_rows=6000, n_block_rows=2000, half_band=300, seed=3)) as M:
         st = M.stats()
         assert st["n_entry_mode_units"] < 0.1 * st["n_units"]
+
+
+def test_value_map_option_keeps_the_structure(bd):
+    A = I.random_csr(203, 157, 0.07, 5)
+    with host(bd, A) as M0, host(bd, A, keep_value_map=True) as M1:
+        a, b = M0.export_blocked(), M1.export_blocked()
+        for key in ("blk_row", "blk_col", "nnz", "type", "cols_offset", "restore_cols"):
+            assert np.array_equal(a[key], b[key])
+        assert_roundtrip(M1, A)
+        # a host-only handle cannot re-pack on a device
+        with pytest.raises(bd.CbspmvError):
+            M1.update_values(A.val)
