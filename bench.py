@@ -129,6 +129,23 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(use), "in_window": len(inwin)}
 
 
+def max_over_ranks(values, dist=None, device="cpu"):
+    """Element-wise maximum of per-rank values over all ranks (a replica job is as slow as
+    its slowest rank); the values themselves for a single process."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t]
+
+
+def job_gflops(world_size: int, flops_per_rank: float, ms_max: float) -> float:
+    """Whole-job throughput of independent replicas: every rank's flops over the slowest
+    rank's time."""
+    return world_size * flops_per_rank / (ms_max * 1e-3) / 1e9
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -492,15 +509,10 @@ def main():
                "api": "torch.mv on torch.sparse_csr_tensor (cuSPARSE SpMV, CSR, %s)" % ("FP32" if lp else "FP64"),
                "agrees_with_ours": agree}
 
-    ms_max = ms
-    e2e_max = e2e_ms
-    if dist:
-        t = torch.tensor([ms, e2e_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max, e2e_max = float(t[0]), float(t[1])
+    ms_max, e2e_max = max_over_ranks([ms, e2e_ms], dist, "cuda")
 
     flops = float(st["flops_per_run"])
-    gflops_total = ws * flops / (ms_max * 1e-3) / 1e9
+    gflops_total = job_gflops(ws, flops, ms_max)
     algo_bytes = float(st["algo_bytes_per_run"])
     gbs = algo_bytes / (ms * 1e-3) / 1e9
     peak, peak_kind = load_peaks()
@@ -556,7 +568,7 @@ def main():
             "roofline": roof,
             "per_step": per_step,
             "per_step_l2_flushed": per_step_flushed,
-            "e2e": {"value": round(ws * flops / (e2e_max * 1e-3) / 1e9, 3), "unit": "GFLOP/s",
+            "e2e": {"value": round(job_gflops(ws, flops, e2e_max), 3), "unit": "GFLOP/s",
                     "ms_per_step": round(e2e_max, 4), "h2d_bytes_per_step": esz * A.n,
                     "d2h_bytes_per_step": esz * A.m, "api": "cbspmv_run_host"},
             "gpu_launches": args.steps * kt["launches_per_run"],
