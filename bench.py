@@ -563,7 +563,8 @@ def main():
                              % (st["stream_bytes"] / 1e9),
                        "aggregated": bool(st["aggregated"]), "tiles": st["n_tiles"],
                        "formats_coo_csr_dense": st["n_fmt"], "units": st["n_units"],
-                       "split_units": st["n_split_units"], "entry_mode_units": st["n_entry_mode_units"]},
+                       "split_units": st["n_split_units"], "entry_mode_units": st["n_entry_mode_units"],
+                       "xseq_units": st["n_xseq_units"]},
             "hbm_gbs": round(gbs, 2),
             "roofline": roof,
             "per_step": per_step,

@@ -126,6 +126,7 @@ typedef struct {
   double tb8_load_std;             /* per-thread-block (8 sub-blocks) nnz std, Algorithm 2 order */
   double analyze_ms;               /* host time of cbspmv_analyze */
   int64_t n_entry_mode_units;      /* units scheduled in single entries (sparse pieces) */
+  int64_t n_xseq_units;            /* units whose chunks all cover consecutive columns */
 } cbspmv_stats_t;
 
 /* Fills *opts with the paper's settings: th0 0.15, th1 32, th2 128, col_agg -1,

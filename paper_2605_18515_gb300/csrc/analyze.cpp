@@ -90,6 +90,40 @@ void gather_block_row(const cbspmv_csr_t& A, int64_t b, std::vector<std::pair<ui
   std::sort(e.begin(), e.end());
 }
 
+}  // namespace
+
+// Column (0..15, in the tile) of entry e of tile tg, from its packed record (row-major
+// entry order; Dense entry e is row e / 16, column e % 16).
+static inline uint32_t entry_col(const Plan& p, size_t tg, uint32_t e) {
+  const CbTile& t = p.tiles[tg];
+  if (t.fmt == CB_FMT_DENSE) return e & 15u;
+  const uint8_t* rec = p.stream.data() + (size_t)t.vp16 * 16;
+  const uint8_t* idx = rec + (t.fmt == CB_FMT_CSR ? 17 : 0);
+  return idx[e] >> 4;
+}
+
+// Entries of the chunk starting at entry e (at most len) whose columns are consecutive.
+static inline uint32_t xseq_run(const Plan& p, size_t tg, uint32_t e, uint32_t len) {
+  uint32_t k = 1;
+  const uint32_t c0 = entry_col(p, tg, e);
+  while (k < len && entry_col(p, tg, e + k) == c0 + k) ++k;
+  return k;
+}
+
+// Chunks of the piece (tile tg, row rr, entries s0 .. s0 + c - 1) when chunks of up to
+// CB_CHUNK entries also stop at column gaps.
+static inline uint64_t xseq_chunks(const Plan& p, size_t tg, int rr, uint32_t s0, uint32_t c) {
+  (void)rr;
+  uint64_t n = 0;
+  for (uint32_t o = 0; o < c;) {
+    o += xseq_run(p, tg, s0 + o, std::min<uint32_t>(CB_CHUNK, c - o));
+    ++n;
+  }
+  return n;
+}
+
+namespace {
+
 // Stores v in the handle's value type, rounded to nearest (ties to even) directly from
 // the FP64 input; the rounded value is exact in the stored type.
 void write_value(uint8_t* dst, double v, int dtype) {
@@ -461,20 +495,35 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
       for (int64_t i = lo; i < hi; ++i) {
         const CbUnit& u = p.units[i];
         const int64_t R = std::min<int64_t>((int64_t)CB_BLK * u.nbr, A.m - (int64_t)u.brow_lo * CB_BLK);
-        uint64_t nch = 0, nent = 0;
+        uint64_t nch = 0, nent = 0, nchx = 0;
         for (uint32_t t = 0; t < u.ntiles; ++t) {
-          const int64_t brl = (int64_t)p.tiles[u.tile_lo + t].brow - u.brow_lo;
-          for (int rr = 0; rr < 16; ++rr)
+          const size_t tg = (size_t)(u.tile_lo + t);
+          const int64_t brl = (int64_t)p.tiles[tg].brow - u.brow_lo;
+          uint32_t s0 = 0;
+          for (int rr = 0; rr < 16; ++rr) {
+            const uint32_t c = rowcnt[tg * 16 + rr];
             if (brl * 16 + rr < R) {
-              const uint32_t c = rowcnt[(size_t)(u.tile_lo + t) * 16 + rr];
               nch += (c + CB_CHUNK - 1) / CB_CHUNK;
               nent += c;
+              nchx += xseq_chunks(p, tg, rr, s0, c);
             }
+            s0 += c;
+          }
         }
-        // sparse pieces: schedule single entries (see CB_ENTRY_MODE_FILL)
-        const bool entry_mode = nch > 0 && (double)nent < CB_ENTRY_MODE_FILL * CB_CHUNK * (double)nch;
-        p.units[i].mode = entry_mode ? CB_MODE_ENTRY : 0u;
-        if (entry_mode) nch = nent;
+        // Schedule mode (see cb_layout.h): consecutive-column chunks when they fill their
+        // FMA slots about as well as plain chunks; plain chunks; single entries for sparse
+        // pieces (CB_ENTRY_MODE_FILL).
+        const double fill3 = nch ? (double)nent / (CB_CHUNK * (double)nch) : 0.0;
+        const double fillx = nchx ? (double)nent / (CB_CHUNK * (double)nchx) : 0.0;
+        uint32_t mode = 0;
+        if (nch > 0 && fillx >= CB_ENTRY_MODE_FILL && fillx >= 0.9 * fill3) {
+          mode = CB_MODE_XSEQ;
+          nch = nchx;
+        } else if (nch > 0 && fill3 < CB_ENTRY_MODE_FILL) {
+          mode = CB_MODE_ENTRY;
+          nch = nent;
+        }
+        p.units[i].mode = mode;
         chunks_of[i] = nch;
         // descriptor rows: chunks of the longest run, rounded up to an even count because
         // the kernel reads the chunks of a run in pairs
@@ -519,12 +568,15 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
                 for (int q = 0; q < rr; ++q) s0 += rowcnt[tg * 16 + q];
               }
               const uint32_t cap = (u.mode & CB_MODE_ENTRY) ? 1u : (uint32_t)CB_CHUNK;
-              for (uint32_t o = 0; o < c; o += cap) {
-                const uint32_t len = std::min<uint32_t>(cap, c - o);
+              const bool xseq = (u.mode & CB_MODE_XSEQ) != 0;
+              for (uint32_t o = 0; o < c;) {
+                uint32_t len = std::min<uint32_t>(cap, c - o);
+                if (xseq) len = xseq_run(p, tg, s0 + o, len);   // stop at a column gap
                 chunk.push_back((uint16_t)(t | ((s0 + o) << 5) | (len << 13)));
                 chunk_row.push_back((uint8_t)row);
                 chunk_first.push_back(first ? 1 : 0);
                 first = false;
+                o += len;
               }
             }
             if (!first) chunk.back() |= (uint16_t)0x8000u;    // last chunk of the row
@@ -683,7 +735,10 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
   int64_t nsplit_units = 0;
   for (auto& u : p.units) nsplit_units += u.split >= 0;
   s.n_split_units = nsplit_units;
-  for (auto& u : p.units) s.n_entry_mode_units += (u.mode & CB_MODE_ENTRY) ? 1 : 0;
+  for (auto& u : p.units) {
+    s.n_entry_mode_units += (u.mode & CB_MODE_ENTRY) ? 1 : 0;
+    s.n_xseq_units += (u.mode & CB_MODE_XSEQ) ? 1 : 0;
+  }
   s.n_split_rows = p.n_split_rows;
   s.n_workers = n_workers;
   double lmax = 0, lsum = 0, lsq = 0;

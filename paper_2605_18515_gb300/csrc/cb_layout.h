@@ -63,6 +63,8 @@ struct CbUnit {
 };
 #define CB_MODE_ENTRY 1u     // schedule of single entries instead of chunks of up to CB_CHUNK
 #define CB_MODE_SCAN 2u      // some row spans more than CB_SCAN_SPAN lanes: resolve carries by a scan
+#define CB_MODE_XSEQ 4u      // every chunk covers consecutive columns of its tile (pieces cut at
+                             // column gaps): one coordinate byte and contiguous x per chunk
 #define CB_SCAN_SPAN 4
 
 // Unit blob: the unit's tile records, its restore_cols slice and its lane schedule, stored

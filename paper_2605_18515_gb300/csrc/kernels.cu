@@ -314,14 +314,17 @@ __device__ __forceinline__ void load_xk(const uint8_t* sm, uint32_t off, Acc (&x
 
 // sm: base of the CTA's shared memory; so: offset of the unit's buffer in it. Computes the
 // unit's rows for kK vectors (x values of column c of tile t at x-row t, slot c * kK + j).
-// kC: entries per chunk of the unit's schedule, CB_CHUNK (mode 0) or 1 (mode 1).
+// kC: entries per chunk of the unit's schedule, CB_CHUNK or 1 (CB_MODE_ENTRY). kX = 1: the
+// unit's chunks cover consecutive columns (CB_MODE_XSEQ; single vector), so the chunk's x
+// values are contiguous in the tile's x row and are read like its values.
 // bar_s / phase: the mbarrier phase on which the unit's records land (waited for after the
 // set-up). Returns false if that bounded wait gave up (nothing is written then).
-template <class V, int kK, int kC>
+template <class V, int kK, int kC, int kX>
 __device__ bool consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_t ident_off,
                              Scratch<typename ValT<V>::Acc, kK>& sc, int lane, uint64_t* bar_s,
                              uint32_t phase) {
   static_assert(kC == CB_CHUNK || kC == 1, "chunk size");
+  static_assert(kX == 0 || (kC == CB_CHUNK && kK == 1), "contiguous x chunks: single vector");
   using Acc = typename ValT<V>::Acc;
   using G = Geom<V, kK>;
   constexpr uint32_t kOffUnit = G::kOffUnit, kOffStream = G::kOffStream, kOffBlob = G::kOffBlob,
@@ -403,6 +406,9 @@ __device__ bool consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_
     if constexpr (kC == 1) {                                                       \
       v0 = ValT<V>::load(sm + va_);                                                \
       load_xk<Acc, kK>(sm, xr_ + CB_XOFF((uint32_t)sm[ca_]), x0);                  \
+    } else if constexpr (kX == 1) {                                                \
+      ValT<V>::load3(sm, va_, v0, v1, v2);                                         \
+      ValT<Acc>::load3(sm, xr_ + CB_XOFF((uint32_t)sm[ca_]), x0[0], x1[0], x2[0]); \
     } else {                                                                       \
       const uint32_t cw_ = ca_ & ~3u;                                              \
       const uint32_t cb_ = __funnelshift_r(*reinterpret_cast<const uint32_t*>(sm + cw_), \
@@ -655,10 +661,13 @@ __global__ void __launch_bounds__(32 * Geom<V, kK>::kWarps, 1) spmv_kernel(const
     if (ok) {
       gather_x<V, kK>(a, W, w_smem, lane);
       __syncwarp();
-      if (reinterpret_cast<const CbUnit*>(W + G::kOffUnit)->mode & CB_MODE_ENTRY)
-        ok = consume_unit<V, kK, 1>(a, smem_raw, wo, ident_off, sc, lane, bar_s, phase);
+      const uint32_t mode = reinterpret_cast<const CbUnit*>(W + G::kOffUnit)->mode;
+      if (mode & CB_MODE_ENTRY)
+        ok = consume_unit<V, kK, 1, 0>(a, smem_raw, wo, ident_off, sc, lane, bar_s, phase);
+      else if (kK == 1 && (mode & CB_MODE_XSEQ))
+        ok = consume_unit<V, kK, CB_CHUNK, (kK == 1 ? 1 : 0)>(a, smem_raw, wo, ident_off, sc, lane, bar_s, phase);
       else
-        ok = consume_unit<V, kK, CB_CHUNK>(a, smem_raw, wo, ident_off, sc, lane, bar_s, phase);
+        ok = consume_unit<V, kK, CB_CHUNK, 0>(a, smem_raw, wo, ident_off, sc, lane, bar_s, phase);
       __syncwarp();
     }
     if (!ok) {

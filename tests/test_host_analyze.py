@@ -197,6 +197,9 @@ def test_schedule_mode_follows_piece_sizes(bd):
     with host(bd, I.fem_block_band(n_rows=6000, n_block_rows=2000, half_band=300, seed=3)) as M:
         st = M.stats()
         assert st["n_entry_mode_units"] < 0.1 * st["n_units"]
+        # 3x3 blocks: the chunks of (nearly) every unit cover consecutive columns
+        assert st["n_xseq_units"] > 0.8 * st["n_units"]
+        assert_roundtrip(M, I.fem_block_band(n_rows=6000, n_block_rows=2000, half_band=300, seed=3))
 
 
 def test_value_map_option_keeps_the_structure(bd):
