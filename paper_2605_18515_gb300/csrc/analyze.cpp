@@ -484,6 +484,11 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
   }
   if (have_open) finish_unit(open);
   p.n_split_rows = split_id;
+  // split rows with many parts last (they are added by a wider combine)
+  std::stable_partition(p.split_rows.begin(), p.split_rows.end(),
+                        [](const CbSplitRow& r) { return r.nparts <= CB_COMBINE_WIDE_PARTS; });
+  p.n_split_wide = 0;
+  for (const CbSplitRow& r : p.split_rows) p.n_split_wide += r.nparts > CB_COMBINE_WIDE_PARTS;
   p.n_slots = (int)slot;
 
   // --- step 4a': lane schedule of every unit (chunks of <= CB_CHUNK entries, see cb_layout.h)

@@ -257,6 +257,7 @@ static cb::RunArgs run_args(cbspmv_handle_t h, const void* x, void* y, double al
   a.partial = h->d_partial;
   a.split_rows = h->d_split_rows;
   a.n_split_rows = (uint32_t)p.split_rows.size();
+  a.n_split_wide = (uint32_t)p.n_split_wide;
   a.err = h->d_err;
   a.m = p.m;
   a.n = p.n;
@@ -319,7 +320,11 @@ cbspmv_status_t cbspmv_time_kernels(cbspmv_handle_t h, const void* x, void* y, d
   if (reps < 1 || reps > 100000) return fail(CBSPMV_ERR_INVALID, "reps must be in [1, 100000]");
   if (!ms_main || !ms_combine || !launches_per_run) return fail(CBSPMV_ERR_INVALID, "NULL output");
   *ms_main = *ms_combine = 0.0;
-  *launches_per_run = h->plan.m == 0 ? 0 : (h->plan.split_rows.empty() ? 1 : 2);
+  {
+    const cb::Plan& pl = h->plan;
+    const int narrow = (int)pl.split_rows.size() - pl.n_split_wide;
+    *launches_per_run = pl.m == 0 ? 0 : 1 + (narrow > 0 ? 1 : 0) + (pl.n_split_wide > 0 ? 1 : 0);
+  }
   if (h->plan.m == 0) return ok();
   DeviceGuard g(h->device);
   CB_CUDA(g.err);
@@ -758,7 +763,7 @@ const char* cbspmv_last_error(void) { return g_err.c_str(); }
 
 // The run-kernel revision changes whenever the kernel's code changes (measurements taken
 // with a profiler are tied to it).
-const char* cbspmv_version(void) { return "cbspmv 0.3 (sm_103a; run kernel rev 8)"; }
+const char* cbspmv_version(void) { return "cbspmv 0.3 (sm_103a; run kernel rev 9)"; }
 
 }  // extern "C"
 
@@ -791,6 +796,7 @@ bool noalloc_view(cbspmv_handle_t h, NoallocView* v) {
   a.err = h->d_err;
   a.split_rows = h->d_split_rows;
   a.n_split_rows = (uint32_t)h->plan.split_rows.size();
+  a.n_split_wide = (uint32_t)h->plan.n_split_wide;
   a.m = h->plan.m;
   a.n = h->plan.n;
   a.aggregated = h->plan.aggregated ? 1 : 0;

@@ -22,6 +22,7 @@ struct RunArgs {
   void* partial;                // partial sums of split block rows (16 per slot, vector type)
   const CbSplitRow* split_rows; // block rows cut into several units
   uint32_t n_split_rows;
+  uint32_t n_split_wide;        // the last n_split_wide split rows have many parts
   uint32_t* err;                // device error word
   int64_t m, n;
   double alpha, beta;

@@ -73,7 +73,10 @@ struct CbUnit {
 //   [0, 16 * ntiles) tile records | [.., + 4 * rc_n) restore_cols | [.., + sched_bytes) schedule
 
 // A block row cut into several units: its parts store 16 partial row sums each in
-// consecutive slots slot0 .. slot0 + nparts - 1; a second kernel adds them in part order.
+// consecutive slots slot0 .. slot0 + nparts - 1; a second kernel adds them in a fixed order.
+// Rows with more than CB_COMBINE_WIDE_PARTS parts are stored last and added by 16 lanes
+// per row instead of one.
+#define CB_COMBINE_WIDE_PARTS 16
 struct CbSplitRow {
   uint32_t slot0;
   uint32_t brow;

@@ -36,6 +36,7 @@ struct Plan {
   std::vector<uint32_t> value_slot;    // per CSR entry: stream offset of its value / vsize (optional)
   int n_workers = 0;
   int n_split_rows = 0;
+  int n_split_wide = 0;                // the last split rows, with > CB_COMBINE_WIDE_PARTS parts
   int n_slots = 0;
 
   cbspmv_stats_t stats{};

@@ -137,7 +137,8 @@ __host__ __device__ constexpr uint32_t align128(uint32_t v) { return (v + 127u) 
 template <int kMaxP>
 struct BatchArgs {
   int count;
-  uint32_t split_base[kMaxP + 1];
+  uint32_t split_base[kMaxP + 1];   // prefix sums of the problems' split rows with few parts
+  uint32_t wide_base[kMaxP + 1];    // prefix sums of their split rows with many parts
   RunArgs p[kMaxP];
 };
 constexpr int kMaxBatch = 64;
@@ -700,14 +701,13 @@ __global__ void __launch_bounds__(256) combine_kernel(const __grid_constant__ Ba
     q = lo;
   }
   const RunArgs& a = b.p[q];
-  const CbSplitRow s = a.split_rows[srg - b.split_base[q]];
+  const CbSplitRow s = a.split_rows[srg - b.split_base[q]];   // rows with few parts come first
   if (r >= s.rows) return;
   const int64_t gr = (int64_t)s.brow * CB_BLK + r;
 #pragma unroll
   for (int j = 0; j < kK; ++j) {
     const Acc* p = static_cast<const Acc*>(a.partial) + ((size_t)s.slot0 * 16 + r) * kK + j;
-    // parts k = q (mod 4) into four independent sums, then a fixed tree: rows of power-law
-    // matrices can have hundreds of parts, and one chain of dependent adds would be slow
+    // parts k = q (mod 4) into four independent sums, then a fixed tree
     Acc t[4] = {Acc(0), Acc(0), Acc(0), Acc(0)};
     uint32_t k = 0;
     for (; k + 4 <= s.nparts; k += 4) {
@@ -722,6 +722,53 @@ __global__ void __launch_bounds__(256) combine_kernel(const __grid_constant__ Ba
     Acc v = a.alpha_one ? sum : (Acc)a.alpha * sum;
     if (a.beta_nonzero) v = fma((Acc)a.beta, y[gr], v);
     y[gr] = v;
+  }
+}
+
+// Split rows with many parts (the last n_split_wide of each problem): one block of 256
+// threads per row, 16 lanes per row of the block row; lane l adds parts l, l + 16, ... in
+// four independent sums, then the 16 lanes' sums are added by a fixed shuffle tree. Rows of
+// power-law matrices can have hundreds of parts: with one thread per row, every iteration
+// would wait a full memory latency.
+template <class Acc, int kMaxP, int kK>
+__global__ void __launch_bounds__(256) combine_wide_kernel(const __grid_constant__ BatchArgs<kMaxP> b) {
+  const uint32_t srg = blockIdx.x;
+  const uint32_t r = threadIdx.x >> 4, lane = threadIdx.x & 15u;
+  int q = 0;
+  if (kMaxP > 1) {
+    int lo = 0, hi = b.count - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (b.wide_base[mid] <= srg) lo = mid; else hi = mid - 1;
+    }
+    q = lo;
+  }
+  const RunArgs& a = b.p[q];
+  const CbSplitRow s = a.split_rows[a.n_split_rows - a.n_split_wide + (srg - b.wide_base[q])];
+  const int64_t gr = (int64_t)s.brow * CB_BLK + r;
+#pragma unroll
+  for (int j = 0; j < kK; ++j) {
+    const Acc* p = static_cast<const Acc*>(a.partial) + ((size_t)s.slot0 * 16 + r) * kK + j;
+    Acc t[4] = {Acc(0), Acc(0), Acc(0), Acc(0)};
+    uint32_t k = lane;
+    for (; k + 48 < s.nparts; k += 64) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) t[u] += p[(size_t)(k + 16 * u) * 16 * kK];
+    }
+    for (int u = 0; k < s.nparts; k += 16, ++u) {
+      if (u == 0) t[0] += p[(size_t)k * 16 * kK];
+      else if (u == 1) t[1] += p[(size_t)k * 16 * kK];
+      else t[2] += p[(size_t)k * 16 * kK];
+    }
+    Acc sum = (t[0] + t[1]) + (t[2] + t[3]);
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o, 16);
+    if (lane == 0 && r < s.rows) {
+      Acc* y = static_cast<Acc*>(a.y) + (int64_t)j * a.ldy;
+      Acc v = a.alpha_one ? sum : (Acc)a.alpha * sum;
+      if (a.beta_nonzero) v = fma((Acc)a.beta, y[gr], v);
+      y[gr] = v;
+    }
   }
 }
 
@@ -753,10 +800,15 @@ cudaError_t launch_typed(const BatchArgs<kMaxP>& b, int grid, cudaStream_t strea
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[1], stream)) != cudaSuccess) return e;
-  const uint32_t nsplit = b.split_base[b.count];
+  const uint32_t nsplit = b.split_base[b.count], nwide = b.wide_base[b.count];
   if (nsplit) {
     const uint32_t threads = 16u * nsplit;
     combine_kernel<Acc, kMaxP, kK><<<(threads + 255) / 256, 256, 0, stream>>>(b);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (nwide) {
+    combine_wide_kernel<Acc, kMaxP, kK><<<nwide, 256, 0, stream>>>(b);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -849,7 +901,9 @@ cudaError_t launch_spmv(const RunArgs& a, int grid, cudaStream_t stream, cudaEve
   BatchArgs<1> b;
   b.count = 1;
   b.split_base[0] = 0;
-  b.split_base[1] = a.n_split_rows;
+  b.split_base[1] = a.n_split_rows - a.n_split_wide;
+  b.wide_base[0] = 0;
+  b.wide_base[1] = a.n_split_wide;
   b.p[0] = a;
   return launch_dispatch<1>(b, grid, stream, ev);
 }
@@ -862,9 +916,11 @@ cudaError_t launch_spmv_batch(const RunArgs* a, int count, int grid, cudaStream_
     static thread_local BatchArgs<kMaxBatch> b;
     b.count = c;
     b.split_base[0] = 0;
+    b.wide_base[0] = 0;
     for (int i = 0; i < c; ++i) {
       b.p[i] = a[base + i];
-      b.split_base[i + 1] = b.split_base[i] + a[base + i].n_split_rows;
+      b.split_base[i + 1] = b.split_base[i] + (a[base + i].n_split_rows - a[base + i].n_split_wide);
+      b.wide_base[i + 1] = b.wide_base[i] + a[base + i].n_split_wide;
     }
     const cudaError_t e = launch_dispatch<kMaxBatch>(b, grid, stream, nullptr);
     if (e != cudaSuccess) return e;
