@@ -87,10 +87,11 @@ struct CbSplitRow {
 
 // Lane schedule of a unit (built by the analyser, staged with the unit). The unit's
 // multiply-adds are taken in row-major order (row, then tile, then entry) and cut into
-// chunks of at most CB_CHUNK consecutive entries of one (tile, row) piece; the chunk list
-// is dealt to CB_VLANES runs of (nearly) equal length, one per lane. A lane sends the
+// chunks of at most CB_CHUNK consecutive entries of one (tile, row) piece (single entries
+// in CB_MODE_ENTRY units; chunks also end at column gaps in CB_MODE_XSEQ units); the chunk
+// list is dealt to CB_VLANES runs of (nearly) equal length, one per lane. A lane sends the
 // even chunks of its run to one accumulator and the odd ones to another, so it keeps two
-// independent FP64 accumulation chains.
+// independent accumulation chains.
 // Layout:
 //   CB_VLANES x uint16 run header: bits [0,8) row of the run's first chunk, bit 8 set when
 //     that row began in an earlier run, bits [9,16) number of chunks of the run;

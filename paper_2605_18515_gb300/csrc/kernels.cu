@@ -277,7 +277,7 @@ __device__ __forceinline__ void gather_x(const RunArgs& a, const uint8_t* W, uin
   // the copies complete while the unit's set-up runs; consume_unit waits for them
 }
 
-// ---- consumer -----------------------------------------------------------------------------
+// ---- a unit's rows ----------------------------------------------------------------------
 // acc + v * x when p holds, acc otherwise (a predicated FP64 FMA, no branch).
 __device__ __forceinline__ double pfma(bool p, double v, double x, double acc) {
   asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\t@q fma.rn.f64 %0, %1, %2, %0;\n\t}"
