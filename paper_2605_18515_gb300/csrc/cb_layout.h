@@ -133,7 +133,11 @@ struct CbSplitRow {
 #define CB_R_MAX (CB_NBR_MAX * CB_BLK)
 #define CB_RC_MAX (CB_T_MAX * 16 + 16)   // restore_cols entries per unit (incl. alignment)
 #define CB_RC_PAD 32            // zero entries appended to restore_cols
+#ifndef CB_UNIT_WORK_DEFAULT
 #define CB_UNIT_WORK_DEFAULT 1024
+#endif
+#ifndef CB_UNIT_WORK_MAX
 #define CB_UNIT_WORK_MAX 1024   // multiply-adds per unit (bounds the chunks per unit)
+#endif
 
 #endif
