@@ -256,8 +256,13 @@ def cusparse_reference(A, x, stream, steps: int, vec=np.float64):
         e1.synchronize()
         ms = e0.elapsed_time(e1) / steps
         yc = y.cpu().numpy()
+        # sum_k |a_ik x_k| per row, the scale of both results' rounding errors
+        Aabs = torch.sparse_csr_tensor(Acsr.crow_indices(), Acsr.col_indices(), Acsr.values().abs(),
+                                       size=(A.m, A.n))
+        sabs = torch.mv(Aabs, xd.abs()).double().cpu().numpy()
+        del Aabs
     del Acsr
-    return ms, yc
+    return ms, yc, sabs
 
 
 def error_vs_fp64_oracle(A, x, y, n_rows: int = 20000):
@@ -501,13 +506,22 @@ def main():
 
     cus = None
     if rank == 0 and not args.no_cusparse:
-        cus_ms, y_cus = cusparse_reference(A, x, stream, args.cusparse_steps, vec)
-        tol = 1e-3 if lp else 1e-10
-        agree = bool(np.all(np.abs(y_cus.astype(np.float64) - y_ours) <= tol * (np.abs(y_ours) + 1.0)))
+        cus_ms, y_cus, sabs = cusparse_reference(A, x, stream, args.cusparse_steps, vec)
+        # Both results lie within (storage roundoff + gamma_{k+10} of their arithmetic) of
+        # sum_k a_ik x_k, relative to sum_k |a_ik x_k|: cuSPARSE rounds the values to FP32
+        # (or keeps FP64), this library to the --dtype format; both add in FP32 (FP64).
+        u_store = {"f64": 0.0, "f32": 2.0 ** -24, "bf16": 2.0 ** -8, "f16": 2.0 ** -11}[args.dtype]
+        u_cus = 2.0 ** -24 if lp else 0.0
+        u_ar = 2.0 ** -24 if lp else 2.0 ** -53
+        kk = np.diff(A.row_ptr).astype(np.float64) + 10.0
+        gam = kk * u_ar / (1.0 - kk * u_ar)
+        bound = (u_store + u_cus + 2.0 * gam) * sabs * 1.01
+        agree = bool(np.all(np.abs(y_cus.astype(np.float64) - y_ours) <= bound))
         cus = {"gflops": round(2.0 * A.nnz / (cus_ms * 1e-3) / 1e9, 3), "ms_per_step": round(cus_ms, 5),
                "csr_model_bytes": int((A.m + 1) * 8 + A.nnz * (4 + esz) + A.n * esz + A.m * esz),
                "api": "torch.mv on torch.sparse_csr_tensor (cuSPARSE SpMV, CSR, %s)" % ("FP32" if lp else "FP64"),
-               "agrees_with_ours": agree}
+               "agrees_with_ours": agree,
+               "agreement_bound": "per row (u_storage + u_cusparse_values + 2 gamma_{k+10}) sum_k |a_ik x_k|"}
 
     ms_max, e2e_max = max_over_ranks([ms, e2e_ms], dist, "cuda")
 
