@@ -127,6 +127,9 @@ typedef struct {
   double analyze_ms;               /* host time of cbspmv_analyze */
   int64_t n_entry_mode_units;      /* units scheduled in single entries (sparse pieces) */
   int64_t n_xseq_units;            /* units whose chunks all cover consecutive columns */
+  int64_t fma_slots;               /* FMA slots the run kernel's walks issue per vector (32 lanes x
+                                      chunk steps x chunk size, summed over units); nnz / fma_slots
+                                      is the fraction of FMA issue that does useful work */
 } cbspmv_stats_t;
 
 /* Fills *opts with the paper's settings: th0 0.15, th1 32, th2 128, col_agg -1,

@@ -57,7 +57,8 @@ class Stats(ctypes.Structure):
                 ("n_workers", ctypes.c_int64), ("worker_load_max", ctypes.c_double),
                 ("worker_load_mean", ctypes.c_double), ("worker_load_std", ctypes.c_double),
                 ("tb8_load_std", ctypes.c_double), ("analyze_ms", ctypes.c_double),
-                ("n_entry_mode_units", ctypes.c_int64), ("n_xseq_units", ctypes.c_int64)]
+                ("n_entry_mode_units", ctypes.c_int64), ("n_xseq_units", ctypes.c_int64),
+                ("fma_slots", ctypes.c_int64)]
 
 
 class ServerOpts(ctypes.Structure):

@@ -538,6 +538,13 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
     });
     std::vector<uint64_t> off(nun + 1, 0);
     for (size_t i = 0; i < nun; ++i) off[i + 1] = off[i] + sbytes[i];
+    // every lane of a unit's warp runs (descriptor rows) chunk steps of (chunk size) slots
+    p.fma_slots = 0;
+    for (size_t i = 0; i < nun; ++i) {
+      const uint64_t rows = ((chunks_of[i] + CB_VLANES - 1) / CB_VLANES + 1) & ~1ULL;
+      const uint64_t cap = (p.units[i].mode & CB_MODE_ENTRY) ? 1u : (uint64_t)CB_CHUNK;
+      p.fma_slots += (int64_t)(CB_VLANES * rows * cap);
+    }
     if (off[nun] / 16 >= (1ULL << 32)) { *msg = "schedule array too large"; return CBSPMV_ERR_UNSUPPORTED; }
     p.sched.assign(off[nun] / 4, 0);
     parallel_for((int64_t)nun, 128, [&](int64_t lo, int64_t hi) {
@@ -607,7 +614,8 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
           const uint32_t hs = chunk_first[c0] ? 0u : 1u;
           hdr[l] = (uint16_t)(chunk_row[c0] | (hs << 8) | ((uint32_t)(c1 - c0) << 9));
           for (uint64_t k = c0; k < c1; ++k) {
-            desc[(k - c0) * CB_VLANES + l] = chunk[k];
+            const uint64_t j = k - c0;      // pairs of chunks (2i, 2i + 1) share one 32-bit word
+            desc[((j >> 1) * CB_VLANES + l) * 2 + (j & 1)] = chunk[k];
             const int r = chunk_row[k];
             if (first_lane[r] < 0) first_lane[r] = (int)l;
             last_lane[r] = (int)l;
@@ -744,6 +752,7 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
     s.n_entry_mode_units += (u.mode & CB_MODE_ENTRY) ? 1 : 0;
     s.n_xseq_units += (u.mode & CB_MODE_XSEQ) ? 1 : 0;
   }
+  s.fma_slots = p.fma_slots;
   s.n_split_rows = p.n_split_rows;
   s.n_workers = n_workers;
   double lmax = 0, lsum = 0, lsq = 0;

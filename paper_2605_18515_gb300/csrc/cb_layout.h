@@ -89,16 +89,16 @@ struct CbSplitRow {
 // multiply-adds are taken in row-major order (row, then tile, then entry) and cut into
 // chunks of at most CB_CHUNK consecutive entries of one (tile, row) piece (single entries
 // in CB_MODE_ENTRY units; chunks also end at column gaps in CB_MODE_XSEQ units); the chunk
-// list is dealt to CB_VLANES runs of (nearly) equal length, one per lane. A lane sends the
-// even chunks of its run to one accumulator and the odd ones to another, so it keeps two
-// independent accumulation chains.
+// list is dealt to CB_VLANES runs of (nearly) equal length, one per lane. A lane takes its
+// run's chunks two at a time (chunk A, chunk B) into one accumulator per vector.
 // Layout:
 //   CB_VLANES x uint16 run header: bits [0,8) row of the run's first chunk, bit 8 set when
 //     that row began in an earlier run, bits [9,16) number of chunks of the run;
 //   R x uint8 next row: for each row of the unit, the next row holding entries;
 //   padding to a multiple of 16 bytes from the start;
-//   rows x CB_VLANES x uint16 chunk descriptors, row-major by (chunk index, run), rows =
-//   the longest run's chunk count rounded up to an even number:
+//   rows / 2 x CB_VLANES x uint32 chunk-descriptor pairs, row-major by (pair index, run):
+//   the low half holds chunk 2i of the run, the high half chunk 2i + 1; rows = the longest
+//   run's chunk count rounded up to an even number. A 16-bit chunk descriptor:
 //     bits [0,5) tile in the unit, [5,13) first entry inside the tile record (entry order
 //     of the record: row-major; Dense: row * 16 + col), [13,15) length 1..CB_CHUNK (0 = no
 //     chunk), bit 15 set when the chunk ends its row.

@@ -37,6 +37,7 @@ struct Plan {
   int n_workers = 0;
   int n_split_rows = 0;
   int n_split_wide = 0;                // the last split rows, with > CB_COMBINE_WIDE_PARTS parts
+  int64_t fma_slots = 0;               // FMA slots the walks of all units issue (one vector)
   int n_slots = 0;
 
   cbspmv_stats_t stats{};

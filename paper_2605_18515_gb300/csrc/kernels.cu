@@ -52,6 +52,7 @@ namespace {
 
 constexpr long long kWaitBudget = 4000000000LL;   // clock64 cycles (~2 s) per wait
 constexpr uint32_t kSmemMax = 232448;             // dynamic shared memory per CTA (227 KB)
+static_assert(kSmemMax <= (1u << 18), "tile bases are packed as 14 + 18 bits of shared-memory offset");
 
 // Stored value types: V is the storage type, Acc the type of x, y and the accumulators.
 template <class V> struct ValT;
@@ -123,7 +124,13 @@ template <> struct ValT<__half> {
 // kK: vectors computed per pass (the product on kK right-hand sides at once).
 template <class Acc, int kK>
 struct Scratch {
-  uint4 tinfo[CB_T_MAX];        // per tile: value base, coordinate base, x-row base (smem offsets)
+  // per tile, shared-memory offsets of its value base, coordinate base and x row, in one of
+  // two forms: q = (value base, coordinate base, x row, 0); w = value base / 16 (bits 0-13)
+  // | coordinate base (bits 14-31), the x row following from the tile index
+  union {
+    uint4 q[CB_T_MAX];
+    uint32_t w[CB_T_MAX];
+  } tinfo;
   Acc srow[CB_R_MAX * kK];      // row sums, kK per row
   Acc cval[CB_VLANES * kK];     // per-run carry values (short-carry path)
   int32_t crow[CB_VLANES];      // per-run carry row (-1 none, -2 no chunks)
@@ -344,6 +351,11 @@ __device__ bool consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_
   const uint32_t R = (uint32_t)(rows_unit < rows_left ? rows_unit : rows_left);
   const CbTile* tiles = reinterpret_cast<const CbTile*>(S + kOffBlob);
   const bool scan_carries = (u.mode & CB_MODE_SCAN) != 0;
+  // Tile bases as one 32-bit word (one conflict-free load per chunk when a warp's lanes read
+  // many tiles), except for FP64 consecutive-column units: their lanes mostly share a few
+  // tiles, the 16-byte load is then a broadcast, and the word's decode on the load chain
+  // measured slower.
+  constexpr bool kPacked = !(sizeof(V) == 8 && kX == 1);
 
   // 1. per-tile bases (lane = tile) and zeroed row sums
   if ((uint32_t)lane < T) {
@@ -360,19 +372,22 @@ __device__ bool consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_
       vb = soff + align16u(rec.nnz);
       cb = soff;
     }
-    sc.tinfo[lane] = make_uint4(vb, cb, so + kOffXs + G::kXRow * lane, 0u);
+    if constexpr (kPacked) sc.tinfo.w[lane] = (vb >> 4) | (cb << 14);
+    else sc.tinfo.q[lane] = make_uint4(vb, cb, so + kOffXs + G::kXRow * lane, 0u);
   }
   for (uint32_t r = lane; r < R * kK; r += 32) sc.srow[r] = Acc(0);
   if (!__all_sync(0xffffffffu, mbar_wait(bar_s, phase))) return false;   // the records
   cp_async_wait_all();     // this lane's x copies (issued by gather_x before the set-up)
   __syncwarp();
 
-  // 2. one run per lane: a sequence of chunks of up to three entries; even chunks go to
-  //    accumulator a0, odd chunks to a1 (two independent chains per vector)
+  // 2. one run per lane: a sequence of chunks of up to three entries, accumulated in one
+  //    chain per vector. A second chain would hide no latency (a warp-wide FP64 FMA holds
+  //    its sub-partition's pipe for 64 cycles, longer than the FMA's latency) and would
+  //    cost an FP64 add at every row end.
   const uint8_t* sched = S + kOffBlob + 16u * T + 4u * u.rc_n;
   const uint16_t* hdr = reinterpret_cast<const uint16_t*>(sched);
   const uint8_t* nxt = sched + 2 * CB_VLANES;
-  const uint16_t* desc = reinterpret_cast<const uint16_t*>(sched + CB_SCHED_HDR(R));
+  const uint32_t* desc = reinterpret_cast<const uint32_t*>(sched + CB_SCHED_HDR(R));
   const uint32_t h = hdr[lane];
   const uint32_t nch = h >> 9;
   const uint32_t nmax = __reduce_max_sync(0xffffffffu, nch);
@@ -381,9 +396,9 @@ __device__ bool consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_
   const bool hs = (h >> 8) & 1u;
   bool first = true, open = false;
   int32_t own_row = -1;
-  Acc own_val[kK], a0[kK], a1[kK];
+  Acc own_val[kK], acc[kK];
 #pragma unroll
-  for (int j = 0; j < kK; ++j) own_val[j] = a0[j] = a1[j] = Acc(0);
+  for (int j = 0; j < kK; ++j) own_val[j] = acc[j] = Acc(0);
   // Software pipeline: the operands of step i + 1 are loaded before the FMAs of step i.
   // Loads are unconditional (a chunk shorter than three entries reads at most two entries,
   // plus up to 4 value bytes and 5 coordinate bytes of alignment slack, past its piece;
@@ -401,9 +416,19 @@ __device__ bool consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_
                                 : (((b_) & 0xF0u) << (kXLog > 4 ? kXLog - 4 : 0)))
 #define CB_LOAD_CHUNK(d, v0, v1, v2, x0, x1, x2)                                   \
   {                                                                                \
-    const uint4 ti_ = sc.tinfo[(d) & 31u];                                         \
     const uint32_t o_ = ((d) >> 5) & 255u;                                         \
-    const uint32_t va_ = ti_.x + kVs * o_, ca_ = ti_.y + o_, xr_ = ti_.z;          \
+    uint32_t va_, ca_, xr_;                                                        \
+    if constexpr (kPacked) {                                                       \
+      const uint32_t ti_ = sc.tinfo.w[(d) & 31u];                                  \
+      va_ = ((ti_ & 0x3fffu) << 4) + kVs * o_;                                     \
+      ca_ = (ti_ >> 14) + o_;                                                      \
+      xr_ = xrow0 + G::kXRow * ((d) & 31u);                                        \
+    } else {                                                                       \
+      const uint4 ti_ = sc.tinfo.q[(d) & 31u];                                     \
+      va_ = ti_.x + kVs * o_;                                                      \
+      ca_ = ti_.y + o_;                                                            \
+      xr_ = ti_.z;                                                                 \
+    }                                                                              \
     if constexpr (kC == 1) {                                                       \
       v0 = ValT<V>::load(sm + va_);                                                \
       load_xk<Acc, kK>(sm, xr_ + CB_XOFF((uint32_t)sm[ca_]), x0);                  \
@@ -422,47 +447,50 @@ __device__ bool consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_
       load_xk<Acc, kK>(sm, xr_ + CB_XOFF(b2_), x2);                                \
     }                                                                              \
   }
+  const uint32_t xrow0 = so + kOffXs;      // x row of tile 0
   if (steps) {
-    dA = desc[lane];
-    dB = desc[CB_VLANES + lane];
+    const uint32_t dd = desc[lane];
+    dA = dd & 0xffffu;
+    dB = dd >> 16;
     CB_LOAD_CHUNK(dA, vA0, vA1, vA2, xA0, xA1, xA2);
     CB_LOAD_CHUNK(dB, vB0, vB1, vB2, xB0, xB1, xB2);
   }
   for (uint32_t i = 0; i < steps; ++i) {
-    const uint32_t nb = (i + 1 < steps ? 2u * (i + 1) : 2u * i) * CB_VLANES;
-    const uint32_t dA_n = desc[nb + lane], dB_n = desc[nb + CB_VLANES + lane];
+    const uint32_t dd_n = desc[(i + 1 < steps ? i + 1 : i) * CB_VLANES + lane];
+    const uint32_t dA_n = dd_n & 0xffffu, dB_n = dd_n >> 16;
     Acc nvA0, nvA1 = Acc(0), nvA2 = Acc(0), nvB0, nvB1 = Acc(0), nvB2 = Acc(0);
     Acc nxA0[kK], nxA1[kK], nxA2[kK], nxB0[kK], nxB1[kK], nxB2[kK];
     CB_LOAD_CHUNK(dA_n, nvA0, nvA1, nvA2, nxA0, nxA1, nxA2);
     CB_LOAD_CHUNK(dB_n, nvB0, nvB1, nvB2, nxB0, nxB1, nxB2);
     const uint32_t lA = (dA >> 13) & 3u, lB = (dB >> 13) & 3u;
     const bool eA = (dA & 0x8000u) != 0, eB = (dB & 0x8000u) != 0;
-    // chunk B starts a new row when chunk A ends one: its chain then starts from zero
-    Acc a1_old[kK];
+    // chunk A, then chunk B, into the chain; when chunk A ends its row, its sum is kept
+    // aside and chunk B starts a new row from zero
+    Acc sA[kK];
 #pragma unroll
     for (int j = 0; j < kK; ++j) {
-      a1_old[j] = a1[j];
-      Acc b = eA ? Acc(0) : a1[j];
-      a0[j] = pfma(lA > 0, vA0, xA0[j], a0[j]);
-      b = pfma(lB > 0, vB0, xB0[j], b);
+      Acc c = pfma(lA > 0, vA0, xA0[j], acc[j]);
       if constexpr (kC > 1) {
-        a0[j] = pfma(lA > 1, vA1, xA1[j], a0[j]);
-        b = pfma(lB > 1, vB1, xB1[j], b);
-        a0[j] = pfma(lA > 2, vA2, xA2[j], a0[j]);
-        b = pfma(lB > 2, vB2, xB2[j], b);
+        c = pfma(lA > 1, vA1, xA1[j], c);
+        c = pfma(lA > 2, vA2, xA2[j], c);
       }
-      a1[j] = b;
+      sA[j] = c;
+      c = eA ? Acc(0) : c;
+      c = pfma(lB > 0, vB0, xB0[j], c);
+      if constexpr (kC > 1) {
+        c = pfma(lB > 1, vB1, xB1[j], c);
+        c = pfma(lB > 2, vB2, xB2[j], c);
+      }
+      acc[j] = c;
     }
     if (lA | lB) open = true;
-    if (eA) {                              // chunk A ends its row: a0 + (a1 before chunk B)
+    if (eA) {                              // chunk A ends its row
       const bool own = first && hs;
       if (own) own_row = (int32_t)row;
 #pragma unroll
       for (int j = 0; j < kK; ++j) {
-        const Acc sum = a0[j] + a1_old[j];
-        if (own) own_val[j] = sum;
-        else sc.srow[row * kK + j] = sum;
-        a0[j] = Acc(0);
+        if (own) own_val[j] = sA[j];
+        else sc.srow[row * kK + j] = sA[j];
       }
       first = false;
       open = lB != 0;
@@ -473,11 +501,9 @@ __device__ bool consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_
       if (own) own_row = (int32_t)row;
 #pragma unroll
       for (int j = 0; j < kK; ++j) {
-        const Acc sum = a0[j] + a1[j];
-        if (own) own_val[j] = sum;
-        else sc.srow[row * kK + j] = sum;
-        a0[j] = Acc(0);
-        a1[j] = Acc(0);
+        if (own) own_val[j] = acc[j];
+        else sc.srow[row * kK + j] = acc[j];
+        acc[j] = Acc(0);
       }
       first = false;
       open = false;
@@ -504,7 +530,7 @@ __device__ bool consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_
   if (!scan_carries) {
     sc.crow[lane] = nch == 0 ? -2 : (open ? (int32_t)row : -1);
 #pragma unroll
-    for (int j = 0; j < kK; ++j) sc.cval[lane * kK + j] = open ? a0[j] + a1[j] : Acc(0);
+    for (int j = 0; j < kK; ++j) sc.cval[lane * kK + j] = open ? acc[j] : Acc(0);
     __syncwarp();
     if (own_row >= 0) {
       Acc sum[kK];
@@ -532,7 +558,7 @@ __device__ bool consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_
     const int32_t key = __shfl_sync(kFull, key0, last < 0 ? lane : last);
     Acc cv[kK];
 #pragma unroll
-    for (int j = 0; j < kK; ++j) cv[j] = open ? a0[j] + a1[j] : Acc(0);
+    for (int j = 0; j < kK; ++j) cv[j] = open ? acc[j] : Acc(0);
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
       const int32_t ko = __shfl_up_sync(kFull, key, d);

@@ -212,3 +212,23 @@ def test_value_map_option_keeps_the_structure(bd):
         # a host-only handle cannot re-pack on a device
         with pytest.raises(bd.CbspmvError):
             M1.update_values(A.val)
+
+
+def test_fma_slot_count(bd):
+    """fma_slots counts whole lanes (32 per chunk row) and at least one slot per entry; two
+    hand-counted cases: a 16x16 diagonal is one unit of 16 single-entry chunks (rounded up to
+    2 descriptor rows of 32 lanes, 1 slot each); a dense 16x16 block is 16 rows of six
+    consecutive-column chunks (96 chunks: 4 descriptor rows of 32 lanes, 3 slots each)."""
+    for A in (I.rmat(12, 16, seed=4), I.laplacian2d(64), I.random_csr(333, 517, 0.2, 11),
+              I.fem_block_band(n_rows=6000, n_block_rows=2000, half_band=300, seed=3)):
+        with host(bd, A) as M:
+            st = M.stats()
+        assert st["fma_slots"] % 32 == 0 and st["fma_slots"] >= A.nnz
+    r = np.arange(16)
+    with host(bd, I.csr_from_coo(16, 16, r, r, np.ones(16))) as M:
+        st = M.stats()
+    assert st["n_entry_mode_units"] == 1 and st["fma_slots"] == 64
+    r, c = np.repeat(np.arange(16), 16), np.tile(np.arange(16), 16)
+    with host(bd, I.csr_from_coo(16, 16, r, c, np.ones(256))) as M:
+        st = M.stats()
+    assert st["n_xseq_units"] == 1 and st["fma_slots"] == 384
