@@ -733,17 +733,27 @@ __global__ void __launch_bounds__(256) combine_kernel(const __grid_constant__ Ba
 #pragma unroll
   for (int j = 0; j < kK; ++j) {
     const Acc* p = static_cast<const Acc*>(a.partial) + ((size_t)s.slot0 * 16 + r) * kK + j;
-    // parts k = q (mod 4) into four independent sums, then a fixed tree
-    Acc t[4] = {Acc(0), Acc(0), Acc(0), Acc(0)};
-    uint32_t k = 0;
-    for (; k + 4 <= s.nparts; k += 4) {
+    constexpr size_t kPart = 16 * kK;   // distance between parts
+    // Up to four parts: added in part order, nparts - 1 adds (an FP64 add holds the FP64
+    // pipe as long as an FMA does, so none is spent on adding zeros). More parts:
+    // parts k = q (mod 4) into four chains started from the first four parts, then a fixed
+    // tree.
+    Acc sum;
+    if (s.nparts <= 4) {
+      sum = p[0];
+      for (uint32_t k = 1; k < s.nparts; ++k) sum += p[k * kPart];
+    } else {
+      Acc t[4] = {p[0], p[kPart], p[2 * kPart], p[3 * kPart]};
+      uint32_t k = 4;
+      for (; k + 4 <= s.nparts; k += 4) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) t[q] += p[(size_t)(k + q) * 16 * kK];
+        for (int q = 0; q < 4; ++q) t[q] += p[(size_t)(k + q) * kPart];
+      }
+      if (k < s.nparts) t[0] += p[(size_t)k * kPart];
+      if (k + 1 < s.nparts) t[1] += p[(size_t)(k + 1) * kPart];
+      if (k + 2 < s.nparts) t[2] += p[(size_t)(k + 2) * kPart];
+      sum = (t[0] + t[1]) + (t[2] + t[3]);
     }
-    if (k < s.nparts) t[0] += p[(size_t)k * 16 * kK];
-    if (k + 1 < s.nparts) t[1] += p[(size_t)(k + 1) * 16 * kK];
-    if (k + 2 < s.nparts) t[2] += p[(size_t)(k + 2) * 16 * kK];
-    const Acc sum = s.nparts <= 2 ? t[0] + t[1] : (t[0] + t[1]) + (t[2] + t[3]);
     Acc* y = static_cast<Acc*>(a.y) + (int64_t)j * a.ldy;
     Acc v = a.alpha_one ? sum : (Acc)a.alpha * sum;
     if (a.beta_nonzero) v = fma((Acc)a.beta, y[gr], v);
