@@ -130,6 +130,7 @@ typedef struct {
   int64_t fma_slots;               /* FMA slots the run kernel's walks issue per vector (32 lanes x
                                       chunk steps x chunk size, summed over units); nnz / fma_slots
                                       is the fraction of FMA issue that does useful work */
+  int64_t n_direct_units;          /* units whose chunk descriptors hold value offsets and columns */
 } cbspmv_stats_t;
 
 /* Fills *opts with the paper's settings: th0 0.15, th1 32, th2 128, col_agg -1,

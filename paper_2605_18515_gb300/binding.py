@@ -58,7 +58,7 @@ class Stats(ctypes.Structure):
                 ("worker_load_mean", ctypes.c_double), ("worker_load_std", ctypes.c_double),
                 ("tb8_load_std", ctypes.c_double), ("analyze_ms", ctypes.c_double),
                 ("n_entry_mode_units", ctypes.c_int64), ("n_xseq_units", ctypes.c_int64),
-                ("fma_slots", ctypes.c_int64)]
+                ("fma_slots", ctypes.c_int64), ("n_direct_units", ctypes.c_int64)]
 
 
 class ServerOpts(ctypes.Structure):

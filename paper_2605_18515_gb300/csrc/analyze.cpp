@@ -92,6 +92,9 @@ void gather_block_row(const cbspmv_csr_t& A, int64_t b, std::vector<std::pair<ui
 
 }  // namespace
 
+static_assert(CB_B_MAX <= 8192 && CB_B_MAX_4 <= 8192 && CB_B_MAX_2 <= 8192,
+              "direct chunk descriptors hold 13-bit value offsets within a unit's stream bytes");
+
 // Column (0..15, in the tile) of entry e of tile tg, from its packed record (row-major
 // entry order; Dense entry e is row e / 16, column e % 16).
 static inline uint32_t entry_col(const Plan& p, size_t tg, uint32_t e) {
@@ -528,12 +531,18 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
           mode = CB_MODE_ENTRY;
           nch = nent;
         }
+        // Direct descriptors where the chunks' columns are known per chunk: two fewer
+        // dependent shared-memory loads per chunk for twice the descriptor bytes. FP64
+        // consecutive-column units keep the 16-bit form: their lanes mostly share a few
+        // tiles (the tile-base load is a broadcast) and the direct form measured slower.
+        const bool direct_ok = (mode & CB_MODE_ENTRY) || ((mode & CB_MODE_XSEQ) && p.vsize < 8);
+        if (direct_ok && nch <= CB_DIRECT_MAX_CHUNKS) mode |= CB_MODE_DIRECT;
         p.units[i].mode = mode;
         chunks_of[i] = nch;
         // descriptor rows: chunks of the longest run, rounded up to an even count because
         // the kernel reads the chunks of a run in pairs
         const uint64_t rows = ((nch + CB_VLANES - 1) / CB_VLANES + 1) & ~1ULL;
-        sbytes[i] = CB_SCHED_HDR(R) + 2 * CB_VLANES * rows;
+        sbytes[i] = CB_SCHED_HDR(R) + ((mode & CB_MODE_DIRECT) ? 4 : 2) * CB_VLANES * rows;
       }
     });
     std::vector<uint64_t> off(nun + 1, 0);
@@ -549,6 +558,7 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
     p.sched.assign(off[nun] / 4, 0);
     parallel_for((int64_t)nun, 128, [&](int64_t lo, int64_t hi) {
       std::vector<uint16_t> chunk;      // descriptors in row-major order
+      std::vector<uint32_t> chunk32;    // direct descriptors (CB_MODE_DIRECT units)
       std::vector<uint8_t> chunk_row;   // row of each chunk
       std::vector<uint8_t> chunk_first; // chunk starts its row
       for (int64_t i = lo; i < hi; ++i) {
@@ -558,7 +568,8 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
         uint16_t* hdr = reinterpret_cast<uint16_t*>(base);
         uint8_t* nxt = base + 2 * CB_VLANES;
         uint16_t* desc = reinterpret_cast<uint16_t*>(base + CB_SCHED_HDR(R));
-        chunk.clear(); chunk_row.clear(); chunk_first.clear();
+        chunk.clear(); chunk32.clear(); chunk_row.clear(); chunk_first.clear();
+        const bool direct = (u.mode & CB_MODE_DIRECT) != 0;
         // tiles of each block row of the unit are consecutive; walk rows in order
         uint32_t t_begin = 0;
         for (int64_t brl = 0; brl < u.nbr; ++brl) {
@@ -585,13 +596,24 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
                 uint32_t len = std::min<uint32_t>(cap, c - o);
                 if (xseq) len = xseq_run(p, tg, s0 + o, len);   // stop at a column gap
                 chunk.push_back((uint16_t)(t | ((s0 + o) << 5) | (len << 13)));
+                if (direct) {
+                  const CbTile& tr = p.tiles[tg];
+                  const uint32_t area = tr.fmt == CB_FMT_COO   ? align16(tr.nnz)
+                                        : tr.fmt == CB_FMT_CSR ? align16(17u + tr.nnz)
+                                                               : 32u;
+                  const uint32_t voff = (tr.vp16 - u.byte_lo16) * 16u + area + (s0 + o) * (uint32_t)p.vsize;
+                  chunk32.push_back(voff | (t << 13) | (entry_col(p, tg, s0 + o) << 18) | (len << 22));
+                }
                 chunk_row.push_back((uint8_t)row);
                 chunk_first.push_back(first ? 1 : 0);
                 first = false;
                 o += len;
               }
             }
-            if (!first) chunk.back() |= (uint16_t)0x8000u;    // last chunk of the row
+            if (!first) {                                      // last chunk of the row
+              chunk.back() |= (uint16_t)0x8000u;
+              if (direct) chunk32.back() |= 1u << 24;
+            }
           }
           t_begin = t_end;
         }
@@ -614,8 +636,11 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
           const uint32_t hs = chunk_first[c0] ? 0u : 1u;
           hdr[l] = (uint16_t)(chunk_row[c0] | (hs << 8) | ((uint32_t)(c1 - c0) << 9));
           for (uint64_t k = c0; k < c1; ++k) {
-            const uint64_t j = k - c0;      // pairs of chunks (2i, 2i + 1) share one 32-bit word
-            desc[((j >> 1) * CB_VLANES + l) * 2 + (j & 1)] = chunk[k];
+            const uint64_t j = k - c0;      // pairs of chunks (2i, 2i + 1) side by side
+            if (direct)
+              reinterpret_cast<uint32_t*>(desc)[((j >> 1) * CB_VLANES + l) * 2 + (j & 1)] = chunk32[k];
+            else
+              desc[((j >> 1) * CB_VLANES + l) * 2 + (j & 1)] = chunk[k];
             const int r = chunk_row[k];
             if (first_lane[r] < 0) first_lane[r] = (int)l;
             last_lane[r] = (int)l;
@@ -751,6 +776,7 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
   for (auto& u : p.units) {
     s.n_entry_mode_units += (u.mode & CB_MODE_ENTRY) ? 1 : 0;
     s.n_xseq_units += (u.mode & CB_MODE_XSEQ) ? 1 : 0;
+    s.n_direct_units += (u.mode & CB_MODE_DIRECT) ? 1 : 0;
   }
   s.fma_slots = p.fma_slots;
   s.n_split_rows = p.n_split_rows;

@@ -65,6 +65,8 @@ struct CbUnit {
 #define CB_MODE_SCAN 2u      // some row spans more than CB_SCAN_SPAN lanes: resolve carries by a scan
 #define CB_MODE_XSEQ 4u      // every chunk covers consecutive columns of its tile (pieces cut at
                              // column gaps): one coordinate byte and contiguous x per chunk
+#define CB_MODE_DIRECT 8u    // (with ENTRY or XSEQ) 32-bit chunk descriptors that hold the
+                             // chunk's value offset and first column (layout below)
 #define CB_SCAN_SPAN 4
 
 // Unit blob: the unit's tile records, its restore_cols slice and its lane schedule, stored
@@ -102,6 +104,13 @@ struct CbSplitRow {
 //     bits [0,5) tile in the unit, [5,13) first entry inside the tile record (entry order
 //     of the record: row-major; Dense: row * 16 + col), [13,15) length 1..CB_CHUNK (0 = no
 //     chunk), bit 15 set when the chunk ends its row.
+//   CB_MODE_DIRECT units (single-entry chunks, or consecutive-column chunks of 4- and 2-byte
+//   values; at most CB_DIRECT_MAX_CHUNKS chunks) instead hold rows / 2 x CB_VLANES x (2 x uint32) pairs of
+//   32-bit direct descriptors: bits [0,13) byte offset of the chunk's first value from the
+//   start of the unit's stream bytes, [13,18) tile in the unit, [18,22) column of the first
+//   entry in the tile, [22,24) length (0 = no chunk), bit 24 set when the chunk ends its row.
+//   The run kernel then needs neither the tile bases nor the coordinate bytes to find a
+//   chunk's values and x values.
 #define CB_CHUNK 3
 // A unit whose chunks of up to CB_CHUNK entries would fill less than this share of their
 // FMA slots (sparse tiles, rows with one or two entries per tile) is scheduled in single
@@ -110,6 +119,8 @@ struct CbSplitRow {
 #define CB_ENTRY_MODE_FILL 0.6
 #endif
 #define CB_VLANES 32
+#define CB_DIRECT_MAX_CHUNKS 512   // direct descriptors: 16 rows of 32 lanes x 4 bytes fit the
+                                   // schedule space of 32 rows x 2 bytes
 #define CB_SCHED_HDR(R) ((2u * CB_VLANES + (uint32_t)(R) + 15u) & ~15u)
 #define CB_STEPS_MAX ((((CB_UNIT_WORK_MAX + CB_VLANES - 1) / CB_VLANES) + 1) & ~1)
 #define CB_SCHED_MAX (CB_SCHED_HDR(CB_R_MAX) + 2 * CB_VLANES * CB_STEPS_MAX)

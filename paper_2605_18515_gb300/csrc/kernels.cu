@@ -327,12 +327,14 @@ __device__ __forceinline__ void load_xk(const uint8_t* sm, uint32_t off, Acc (&x
 // values are contiguous in the tile's x row and are read like its values.
 // bar_s / phase: the mbarrier phase on which the unit's records land (waited for after the
 // set-up). Returns false if that bounded wait gave up (nothing is written then).
-template <class V, int kK, int kC, int kX>
+template <class V, int kK, int kC, int kX, int kD>
 __device__ bool consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_t ident_off,
                              Scratch<typename ValT<V>::Acc, kK>& sc, int lane, uint64_t* bar_s,
                              uint32_t phase) {
   static_assert(kC == CB_CHUNK || kC == 1, "chunk size");
-  static_assert(kX == 0 || (kC == CB_CHUNK && kK == 1), "contiguous x chunks: single vector");
+  static_assert(kX == 0 || (kC == CB_CHUNK && (kK == 1 || kD == 1)),
+                "contiguous x chunks: single vector unless the descriptors are direct");
+  static_assert(kD == 0 || kC == 1 || kX == 1, "direct descriptors: single entries or consecutive columns");
   using Acc = typename ValT<V>::Acc;
   using G = Geom<V, kK>;
   constexpr uint32_t kOffUnit = G::kOffUnit, kOffStream = G::kOffStream, kOffBlob = G::kOffBlob,
@@ -357,8 +359,8 @@ __device__ bool consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_
   // measured slower.
   constexpr bool kPacked = !(sizeof(V) == 8 && kX == 1);
 
-  // 1. per-tile bases (lane = tile) and zeroed row sums
-  if ((uint32_t)lane < T) {
+  // 1. per-tile bases (lane = tile; not needed with direct descriptors) and zeroed row sums
+  if (!kD && (uint32_t)lane < T) {
     const CbTile rec = tiles[lane];
     const uint32_t soff = so + kOffStream + rec.vp16 * 16u - byte_lo;
     uint32_t vb, cb;
@@ -387,7 +389,10 @@ __device__ bool consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_
   const uint8_t* sched = S + kOffBlob + 16u * T + 4u * u.rc_n;
   const uint16_t* hdr = reinterpret_cast<const uint16_t*>(sched);
   const uint8_t* nxt = sched + 2 * CB_VLANES;
+  // descriptor pairs: two 16-bit descriptors in one 32-bit word, or (direct) two 32-bit
+  // descriptors in one 64-bit word
   const uint32_t* desc = reinterpret_cast<const uint32_t*>(sched + CB_SCHED_HDR(R));
+  const uint2* desc2 = reinterpret_cast<const uint2*>(sched + CB_SCHED_HDR(R));
   const uint32_t h = hdr[lane];
   const uint32_t nch = h >> 9;
   const uint32_t nmax = __reduce_max_sync(0xffffffffu, nch);
@@ -415,7 +420,23 @@ __device__ bool consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_
 #define CB_XOFF(b_) (kXLog <= 4 ? (((b_) >> (4 - (kXLog <= 4 ? kXLog : 4))) & (15u << kXLog)) \
                                 : (((b_) & 0xF0u) << (kXLog > 4 ? kXLog - 4 : 0)))
 #define CB_LOAD_CHUNK(d, v0, v1, v2, x0, x1, x2)                                   \
-  {                                                                                \
+  if constexpr (kD) {                                                              \
+    const uint32_t va_ = vrec0 + ((d) & 0x1fffu);                                  \
+    const uint32_t xa_ = xrow0 + G::kXRow * (((d) >> 13) & 31u) + kXStride * (((d) >> 18) & 15u); \
+    if constexpr (kC == 1) {                                                       \
+      v0 = ValT<V>::load(sm + va_);                                                \
+      load_xk<Acc, kK>(sm, xa_, x0);                                               \
+    } else {                                                                       \
+      ValT<V>::load3(sm, va_, v0, v1, v2);                                         \
+      if constexpr (kK == 1) {                                                     \
+        ValT<Acc>::load3(sm, xa_, x0[0], x1[0], x2[0]);                            \
+      } else {                                                                     \
+        load_xk<Acc, kK>(sm, xa_, x0);                                             \
+        load_xk<Acc, kK>(sm, xa_ + kXStride, x1);                                  \
+        load_xk<Acc, kK>(sm, xa_ + 2u * kXStride, x2);                             \
+      }                                                                            \
+    }                                                                              \
+  } else {                                                                         \
     const uint32_t o_ = ((d) >> 5) & 255u;                                         \
     uint32_t va_, ca_, xr_;                                                        \
     if constexpr (kPacked) {                                                       \
@@ -448,22 +469,35 @@ __device__ bool consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_
     }                                                                              \
   }
   const uint32_t xrow0 = so + kOffXs;      // x row of tile 0
+  const uint32_t vrec0 = so + kOffStream;  // the unit's first stream byte
+  // the pair of descriptors of step i
+  auto desc_pair = [&](uint32_t i, uint32_t& da, uint32_t& db) {
+    if constexpr (kD) {
+      const uint2 dd = desc2[i * CB_VLANES + lane];
+      da = dd.x;
+      db = dd.y;
+    } else {
+      const uint32_t dd = desc[i * CB_VLANES + lane];
+      da = dd & 0xffffu;
+      db = dd >> 16;
+    }
+  };
+  // length (0..3) and row-end flag of a descriptor
+  constexpr uint32_t kLenShift = kD ? 22 : 13, kEndBit = kD ? (1u << 24) : 0x8000u;
   if (steps) {
-    const uint32_t dd = desc[lane];
-    dA = dd & 0xffffu;
-    dB = dd >> 16;
+    desc_pair(0, dA, dB);
     CB_LOAD_CHUNK(dA, vA0, vA1, vA2, xA0, xA1, xA2);
     CB_LOAD_CHUNK(dB, vB0, vB1, vB2, xB0, xB1, xB2);
   }
   for (uint32_t i = 0; i < steps; ++i) {
-    const uint32_t dd_n = desc[(i + 1 < steps ? i + 1 : i) * CB_VLANES + lane];
-    const uint32_t dA_n = dd_n & 0xffffu, dB_n = dd_n >> 16;
+    uint32_t dA_n, dB_n;
+    desc_pair(i + 1 < steps ? i + 1 : i, dA_n, dB_n);
     Acc nvA0, nvA1 = Acc(0), nvA2 = Acc(0), nvB0, nvB1 = Acc(0), nvB2 = Acc(0);
     Acc nxA0[kK], nxA1[kK], nxA2[kK], nxB0[kK], nxB1[kK], nxB2[kK];
     CB_LOAD_CHUNK(dA_n, nvA0, nvA1, nvA2, nxA0, nxA1, nxA2);
     CB_LOAD_CHUNK(dB_n, nvB0, nvB1, nvB2, nxB0, nxB1, nxB2);
-    const uint32_t lA = (dA >> 13) & 3u, lB = (dB >> 13) & 3u;
-    const bool eA = (dA & 0x8000u) != 0, eB = (dB & 0x8000u) != 0;
+    const uint32_t lA = (dA >> kLenShift) & 3u, lB = (dB >> kLenShift) & 3u;
+    const bool eA = (dA & kEndBit) != 0, eB = (dB & kEndBit) != 0;
     // chunk A, then chunk B, into the chain; when chunk A ends its row, its sum is kept
     // aside and chunk B starts a new row from zero
     Acc sA[kK];
@@ -689,12 +723,19 @@ __global__ void __launch_bounds__(32 * Geom<V, kK>::kWarps, 1) spmv_kernel(const
       gather_x<V, kK>(a, W, w_smem, lane);
       __syncwarp();
       const uint32_t mode = reinterpret_cast<const CbUnit*>(W + G::kOffUnit)->mode;
-      if (mode & CB_MODE_ENTRY)
-        ok = consume_unit<V, kK, 1, 0>(a, smem_raw, wo, ident_off, sc, lane, bar_s, phase);
-      else if (kK == 1 && (mode & CB_MODE_XSEQ))
-        ok = consume_unit<V, kK, CB_CHUNK, (kK == 1 ? 1 : 0)>(a, smem_raw, wo, ident_off, sc, lane, bar_s, phase);
-      else
-        ok = consume_unit<V, kK, CB_CHUNK, 0>(a, smem_raw, wo, ident_off, sc, lane, bar_s, phase);
+      if (mode & CB_MODE_DIRECT) {
+        if (mode & CB_MODE_ENTRY)
+          ok = consume_unit<V, kK, 1, 0, 1>(a, smem_raw, wo, ident_off, sc, lane, bar_s, phase);
+        else
+          ok = consume_unit<V, kK, CB_CHUNK, 1, 1>(a, smem_raw, wo, ident_off, sc, lane, bar_s, phase);
+      } else if (mode & CB_MODE_ENTRY) {
+        ok = consume_unit<V, kK, 1, 0, 0>(a, smem_raw, wo, ident_off, sc, lane, bar_s, phase);
+      } else if (kK == 1 && (mode & CB_MODE_XSEQ)) {
+        ok = consume_unit<V, kK, CB_CHUNK, (kK == 1 ? 1 : 0), 0>(a, smem_raw, wo, ident_off, sc, lane, bar_s,
+                                                                phase);
+      } else {
+        ok = consume_unit<V, kK, CB_CHUNK, 0, 0>(a, smem_raw, wo, ident_off, sc, lane, bar_s, phase);
+      }
       __syncwarp();
     }
     if (!ok) {

@@ -232,3 +232,24 @@ def test_fma_slot_count(bd):
     with host(bd, I.csr_from_coo(16, 16, r, c, np.ones(256))) as M:
         st = M.stats()
     assert st["n_xseq_units"] == 1 and st["fma_slots"] == 384
+
+
+def test_direct_descriptors_where_columns_are_known_per_chunk(bd):
+    """Single-entry units and consecutive-column units of 4- and 2-byte values (at most 512
+    chunks each) carry direct (value offset, tile, column) descriptors; FP64
+    consecutive-column units keep 16-bit descriptors."""
+    A = I.fem_block_band(n_rows=6000, n_block_rows=2000, half_band=300, seed=3)
+    with host(bd, A, value_dtype="bf16") as M:
+        st = M.stats()
+        rp, col, _ = M.export_csr()
+        assert np.array_equal(rp, A.row_ptr) and np.array_equal(col, A.col)
+    assert st["n_direct_units"] == st["n_xseq_units"] + st["n_entry_mode_units"] > 0
+    with host(bd, A) as M:
+        st = M.stats()
+    assert st["n_direct_units"] == st["n_entry_mode_units"]
+    with host(bd, I.rmat(13, 16, seed=2)) as M:
+        st = M.stats()
+    assert 0 < st["n_direct_units"] <= st["n_entry_mode_units"] + st["n_xseq_units"]
+    r, c = np.repeat(np.arange(16), 16), np.tile(np.arange(16), 16)
+    with host(bd, I.csr_from_coo(16, 16, r, c, np.ones(256)), value_dtype="f32") as M:
+        assert M.stats()["n_direct_units"] == 1
