@@ -51,8 +51,8 @@ L2_BYTES = 129 * 2 ** 20
 # full workload by its number of stored entries. Used only when the loaded library reports
 # the same revision; otherwise the roofline's traffic is null.
 KERNEL_TRAFFIC = {
-    "run kernel rev 10": {("fem3x3_band_1m", "f64"): 1.0913e9, ("fem3x3_band_1m", "bf16"): 0.5845e9,
-                          ("rmat_s21", "f64"): 0.5638e9},
+    "run kernel rev 11": {("fem3x3_band_1m", "f64"): 1.0922e9, ("fem3x3_band_1m", "bf16"): 0.6533e9,
+                          ("rmat_s21", "f64"): 0.5884e9},
 }
 
 
