@@ -273,3 +273,17 @@ def config_matrix(name: str) -> tuple[CSR, np.ndarray]:
         A = rmat(19, 16, seed=2)
         return A, vector_x(A.n, 2)
     raise KeyError(name)
+
+
+def isolated_entries_block_row(tiles: int = 20, rows_with_two: int = 11, seed: int = 9):
+    """One block row of `tiles` 16x16 tiles (16 rows, 16 * tiles columns) whose first
+    `rows_with_two` rows hold two isolated entries per tile (tile columns 0 and 8) and the
+    other rows one (tile column 4): pieces of one or two entries, N(0,1) values."""
+    r, c = [], []
+    for t in range(tiles):
+        for row in range(16):
+            for cc in ((0, 8) if row < rows_with_two else (4,)):
+                r.append(row)
+                c.append(16 * t + cc)
+    r, c = np.array(r, dtype=np.int64), np.array(c, dtype=np.int64)
+    return csr_from_coo(16, 16 * tiles, r, c, normal(seed, TAG_VAL, r.size))

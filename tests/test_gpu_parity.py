@@ -251,3 +251,28 @@ def test_full_size_configs(env, name):
     absrow = np.bincount(r, weights=np.abs(A.val), minlength=A.m)
     rowsum = np.bincount(r, weights=A.val, minlength=A.m)
     assert np.all(np.abs(y_ones - rowsum) <= 1e-12 * absrow)
+
+
+@pytest.mark.parametrize("kind", ["long_entry_unit", "short_entry_unit"])
+def test_single_entry_units_with_and_without_direct_descriptors(env, kind):
+    """A single-entry unit of 540 chunks keeps 16-bit descriptors (tile bases and coordinate
+    bytes); one of 320 chunks carries direct descriptors. Both against the oracle, FP64,
+    alpha/beta, and with several vectors per pass."""
+    bd, torch = env
+    # 540 entries (11 rows of two per tile), or 320 (every row one per tile)
+    A = I.isolated_entries_block_row(rows_with_two=11 if kind == "long_entry_unit" else 0)
+    x = I.vector_x(A.n, 41)
+    y0 = I.uniform_pm1(42, I.TAG_Y, A.m)
+    y, st = gpu_spmv(env, A, x, 1.5, -0.5, y0, col_agg=0)
+    assert st["n_entry_mode_units"] == 1
+    assert st["n_direct_units"] == (0 if kind == "long_entry_unit" else 1)
+    check(A, x, y, 1.5, -0.5, y0)
+    with bd.BlockedMatrix(A, col_agg=0) as M:
+        X = np.stack([I.vector_x(A.n, 50 + j) for j in range(7)])
+        Xd = torch.from_numpy(X).cuda()
+        Yd = torch.zeros((7, A.m), dtype=torch.float64, device="cuda")
+        M.run_multi(Xd, Yd, 1.0, 0.0)
+        Y = Yd.cpu().numpy()
+        M.check_device()
+    for j in range(7):
+        check(A, X[j], Y[j])

@@ -253,3 +253,14 @@ def test_direct_descriptors_where_columns_are_known_per_chunk(bd):
     r, c = np.repeat(np.arange(16), 16), np.tile(np.arange(16), 16)
     with host(bd, I.csr_from_coo(16, 16, r, c, np.ones(256)), value_dtype="f32") as M:
         assert M.stats()["n_direct_units"] == 1
+
+
+def test_long_single_entry_unit_keeps_16bit_descriptors(bd):
+    """540 single-entry chunks in one unit (27 per tile, pieces of 1.7 entries): more than
+    direct descriptors cover, so the unit keeps 16-bit descriptors."""
+    A = I.isolated_entries_block_row()
+    with host(bd, A, col_agg=0) as M:
+        st = M.stats()
+        assert_roundtrip(M, A)
+    assert st["n_units"] == 1 and st["n_entry_mode_units"] == 1 and st["n_direct_units"] == 0
+    assert st["fma_slots"] == 32 * 18       # 540 chunks: 17 per lane, 18 descriptor rows
