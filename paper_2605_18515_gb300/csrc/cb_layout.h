@@ -126,15 +126,17 @@ struct CbSplitRow {
 #define CB_SCHED_MAX (CB_SCHED_HDR(CB_R_MAX) + 2 * CB_VLANES * CB_STEPS_MAX)
 
 // Limits the analyser must respect when it cuts units: every unit must fit one warp buffer
-// of the run kernel. (Each can be overridden at compile time for geometry sweeps.)
+// of the run kernel, so they also set how many worker warps fit an SM (FP64 14, FP32 22,
+// BF16/FP16 24). Each was chosen by timing the FEM and R-MAT workloads over a few sizes
+// and can be overridden at compile time for such sweeps.
 #ifndef CB_B_MAX
 #define CB_B_MAX 8192           // stream bytes per unit, 8-byte values
 #endif
 #ifndef CB_B_MAX_4
-#define CB_B_MAX_4 6144         // stream bytes per unit, 4-byte values
+#define CB_B_MAX_4 4096         // stream bytes per unit, 4-byte values
 #endif
 #ifndef CB_B_MAX_2
-#define CB_B_MAX_2 4096         // stream bytes per unit, 2-byte values
+#define CB_B_MAX_2 3072         // stream bytes per unit, 2-byte values
 #endif
 #define CB_B_MAX_FOR(vsize) ((vsize) == 8 ? CB_B_MAX : (vsize) == 4 ? CB_B_MAX_4 : CB_B_MAX_2)
 #ifndef CB_T_MAX
