@@ -51,10 +51,7 @@ L2_BYTES = 129 * 2 ** 20
 # full workload by its number of stored entries. Used only when the loaded library reports
 # the same revision; otherwise the roofline's traffic is null.
 KERNEL_TRAFFIC = {
-    # rev 12 changed only the unit sizes and warp counts of 4- and 2-byte values: the FP64
-    # figures were captured on rev 11, whose FP64 kernel and unit cutting are the same
-    "run kernel rev 12": {("fem3x3_band_1m", "f64"): 1.0922e9, ("fem3x3_band_1m", "bf16"): 0.6511e9,
-                          ("rmat_s21", "f64"): 0.5884e9},
+    "run kernel rev 13": {},
 }
 
 

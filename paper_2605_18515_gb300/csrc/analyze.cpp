@@ -93,7 +93,7 @@ void gather_block_row(const cbspmv_csr_t& A, int64_t b, std::vector<std::pair<ui
 }  // namespace
 
 static_assert(CB_B_MAX <= 8192 && CB_B_MAX_4 <= 8192 && CB_B_MAX_2 <= 8192,
-              "direct chunk descriptors hold 13-bit value offsets within a unit's stream bytes");
+              "direct chunk descriptors hold value offsets / 2 in 12 bits within a unit's stream bytes");
 
 // Column (0..15, in the tile) of entry e of tile tg, from its packed record (row-major
 // entry order; Dense entry e is row e / 16, column e % 16).
@@ -532,11 +532,9 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
           nch = nent;
         }
         // Direct descriptors where the chunks' columns are known per chunk: two fewer
-        // dependent shared-memory loads per chunk for twice the descriptor bytes. FP64
-        // consecutive-column units keep the 16-bit form: their lanes mostly share a few
-        // tiles (the tile-base load is a broadcast) and the direct form measured slower.
-        const bool direct_ok = (mode & CB_MODE_ENTRY) || ((mode & CB_MODE_XSEQ) && p.vsize < 8);
-        if (direct_ok && nch <= CB_DIRECT_MAX_CHUNKS) mode |= CB_MODE_DIRECT;
+        // dependent shared-memory loads per chunk for twice the descriptor bytes, and the
+        // unit's values re-laid in load order (below).
+        if ((mode & (CB_MODE_ENTRY | CB_MODE_XSEQ)) && nch <= CB_DIRECT_MAX_CHUNKS) mode |= CB_MODE_DIRECT;
         p.units[i].mode = mode;
         chunks_of[i] = nch;
         // descriptor rows: chunks of the longest run, rounded up to an even count because
@@ -556,6 +554,8 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
     }
     if (off[nun] / 16 >= (1ULL << 32)) { *msg = "schedule array too large"; return CBSPMV_ERR_UNSUPPORTED; }
     p.sched.assign(off[nun] / 4, 0);
+    // new value slot of every value slot a direct unit re-lays (only for the value map)
+    std::vector<uint32_t> moved(p.value_slot.empty() ? 0 : p.stream.size() / p.vsize, UINT32_MAX);
     parallel_for((int64_t)nun, 128, [&](int64_t lo, int64_t hi) {
       std::vector<uint16_t> chunk;      // descriptors in row-major order
       std::vector<uint32_t> chunk32;    // direct descriptors (CB_MODE_DIRECT units)
@@ -602,7 +602,8 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
                                         : tr.fmt == CB_FMT_CSR ? align16(17u + tr.nnz)
                                                                : 32u;
                   const uint32_t voff = (tr.vp16 - u.byte_lo16) * 16u + area + (s0 + o) * (uint32_t)p.vsize;
-                  chunk32.push_back(voff | (t << 13) | (entry_col(p, tg, s0 + o) << 18) | (len << 22));
+                  chunk32.push_back((voff >> 1) | (t << 12) | (entry_col(p, tg, s0 + o) << 17) | (len << 21) |
+                                    ((s0 + o) << 24));
                 }
                 chunk_row.push_back((uint8_t)row);
                 chunk_first.push_back(first ? 1 : 0);
@@ -612,7 +613,7 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
             }
             if (!first) {                                      // last chunk of the row
               chunk.back() |= (uint16_t)0x8000u;
-              if (direct) chunk32.back() |= 1u << 24;
+              if (direct) chunk32.back() |= 1u << 23;
             }
           }
           t_begin = t_end;
@@ -628,6 +629,42 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
           }
         }
         const uint64_t nch = chunk.size();
+        if (direct) {
+          // Re-lay the unit's stream bytes: the tiles' coordinate parts first (compacted,
+          // 16-byte aligned), then the values in load order -- chunk index within a run,
+          // then lane -- so that the lanes of one load instruction read consecutive bytes
+          // instead of addresses one run length apart (which fall on few shared-memory
+          // banks). The direct descriptors are retargeted; the coordinate parts keep the
+          // record layout for export.
+          const size_t ub = (size_t)u.byte_lo16 * 16;
+          std::vector<uint8_t> old(p.stream.begin() + ub, p.stream.begin() + ub + u.nbytes);
+          std::vector<uint8_t> neu(u.nbytes, 0);
+          uint32_t w = 0;
+          for (uint32_t t = 0; t < u.ntiles; ++t) {
+            CbTile& tr = p.tiles[u.tile_lo + t];
+            const uint32_t cpart = tr.fmt == CB_FMT_COO   ? align16(tr.nnz)
+                                   : tr.fmt == CB_FMT_CSR ? align16(17u + tr.nnz)
+                                                          : 32u;
+            std::memcpy(neu.data() + w, old.data() + ((size_t)tr.vp16 * 16 - ub), cpart);
+            tr.vp16 = (uint32_t)((ub + w) / 16);
+            w += cpart;
+          }
+          const uint32_t vs = (uint32_t)p.vsize;
+          const uint64_t run_max = (nch + CB_VLANES - 1) / CB_VLANES;
+          for (uint64_t j = 0; j < run_max; ++j)
+            for (uint32_t l = 0; l < CB_VLANES; ++l) {
+              const uint64_t c0 = (l * nch) / CB_VLANES, c1 = ((l + 1) * nch) / CB_VLANES;
+              if (c0 + j >= c1) continue;
+              uint32_t& d = chunk32[c0 + j];
+              const uint32_t len = (d >> 21) & 3u, vo = (d & 0xfffu) << 1;
+              std::memcpy(neu.data() + w, old.data() + vo, (size_t)len * vs);
+              if (!moved.empty())
+                for (uint32_t q = 0; q < len; ++q) moved[(ub + vo) / vs + q] = (uint32_t)((ub + w) / vs + q);
+              d = (d & ~0xfffu) | (w >> 1);
+              w += len * vs;
+            }
+          std::memcpy(p.stream.data() + ub, neu.data(), u.nbytes);
+        }
         int first_lane[CB_R_MAX], last_lane[CB_R_MAX];   // lanes holding chunks of each row
         for (int r = 0; r < CB_R_MAX; ++r) first_lane[r] = last_lane[r] = -1;
         for (uint32_t l = 0; l < CB_VLANES; ++l) {
@@ -654,6 +691,9 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
         u.sched_bytes = (uint32_t)sbytes[i];
       }
     });
+    if (!moved.empty())
+      for (uint32_t& s : p.value_slot)
+        if (moved[s] != UINT32_MAX) s = moved[s];
   }
 
   // --- unit blobs: tile records, restore_cols slice and schedule of each unit, back to back
@@ -802,14 +842,58 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
 }
 
 cbspmv_status_t decode_to_csr(int64_t m, int64_t n, int dtype, bool aggregated,
-                              const std::vector<CbTile>& tiles, const uint8_t* stream,
+                              const std::vector<CbTile>& tiles, const std::vector<CbUnit>& units,
+                              const uint8_t* blob, size_t blob_size, const uint8_t* stream,
                               size_t stream_size, const int32_t* restore_cols, size_t restore_len,
                               int64_t* row_ptr, int32_t* col, double* val, int64_t nnz_expected,
                               std::string* msg) {
   if (dtype < CBSPMV_F64 || dtype > CBSPMV_F16) { *msg = "unknown value type"; return CBSPMV_ERR_INVALID; }
   const int vsize = value_size(dtype);
   std::vector<int64_t> cnt(m + 1, 0);
-  auto for_entries = [&](const CbTile& t, const std::function<void(int64_t, int64_t, const uint8_t*)>& f) -> bool {
+  // Direct units keep their values in load order after the coordinate parts: the stream
+  // offset of every value of their tiles, from the direct descriptors (first entry, length,
+  // value offset) of the unit's lane schedule.
+  std::vector<int64_t> vfirst(tiles.size(), -1);   // tile -> first slot in vpos
+  std::vector<uint64_t> vpos;
+  for (const CbUnit& u : units) {
+    if (!(u.mode & CB_MODE_DIRECT)) continue;
+    const int64_t R = std::min<int64_t>((int64_t)CB_BLK * u.nbr, m - (int64_t)u.brow_lo * CB_BLK);
+    const size_t so = (size_t)u.blob16 * 16 + 16u * u.ntiles + 4u * u.rc_n;
+    if (R <= 0 || so + u.sched_bytes > blob_size || u.sched_bytes < CB_SCHED_HDR(R)) {
+      *msg = "corrupt unit schedule";
+      return CBSPMV_ERR_INVALID;
+    }
+    for (uint32_t t = 0; t < u.ntiles; ++t) {
+      const CbTile& tr = tiles[u.tile_lo + t];
+      vfirst[u.tile_lo + t] = (int64_t)vpos.size();
+      vpos.resize(vpos.size() + (tr.fmt == CB_FMT_DENSE ? 256u : tr.nnz), UINT64_MAX);
+    }
+    const uint32_t* d = reinterpret_cast<const uint32_t*>(blob + so + CB_SCHED_HDR(R));
+    const size_t nd = (u.sched_bytes - CB_SCHED_HDR(R)) / 4;
+    for (size_t k = 0; k < nd; ++k) {
+      const uint32_t len = (d[k] >> 21) & 3u, t = (d[k] >> 12) & 31u, e = d[k] >> 24;
+      if (!len) continue;
+      const uint64_t vo = (uint64_t)u.byte_lo16 * 16 + ((d[k] & 0xfffu) << 1);
+      if (t >= u.ntiles) {
+        *msg = "corrupt direct descriptor";
+        return CBSPMV_ERR_INVALID;
+      }
+      const CbTile& tr = tiles[u.tile_lo + t];
+      const uint32_t cap = tr.fmt == CB_FMT_DENSE ? 256u : tr.nnz;
+      if (e + len > cap || vo + (uint64_t)len * vsize > stream_size) {
+        *msg = "corrupt direct descriptor";
+        return CBSPMV_ERR_INVALID;
+      }
+      for (uint32_t q = 0; q < len; ++q) vpos[vfirst[u.tile_lo + t] + e + q] = vo + (uint64_t)q * vsize;
+    }
+  }
+  auto value_at = [&](size_t ti, uint32_t e, const uint8_t* plain) -> const uint8_t* {
+    if (vfirst[ti] < 0) return plain;
+    const uint64_t p = vpos[vfirst[ti] + e];
+    return p == UINT64_MAX ? nullptr : stream + p;
+  };
+  auto for_entries = [&](size_t ti, const std::function<void(int64_t, int64_t, const uint8_t*)>& f) -> bool {
+    const CbTile& t = tiles[ti];
     size_t off = (size_t)t.vp16 * 16;
     uint32_t rb = record_bytes(t.fmt, t.nnz, vsize);
     if (off + rb > stream_size) return false;
@@ -828,30 +912,32 @@ cbspmv_status_t decode_to_csr(int64_t m, int64_t n, int dtype, bool aggregated,
       for (uint32_t pos = 0; pos < 256; ++pos) {
         if (!(rec[pos >> 3] & (1u << (pos & 7)))) continue;
         int64_t r = (int64_t)t.brow * 16 + (pos >> 4), c;
-        if (r >= m || !colof(pos & 15u, &c)) return false;
-        f(r, c, rec + 32 + pos * vsize);
+        const uint8_t* v = value_at(ti, pos, rec + 32 + pos * vsize);
+        if (r >= m || !colof(pos & 15u, &c) || !v) return false;
+        f(r, c, v);
       }
     } else {
       const uint8_t* idx = rec + (t.fmt == CB_FMT_CSR ? 17 : 0);
       uint32_t voff = align16((uint32_t)(idx - rec) + t.nnz);
       for (uint32_t i = 0; i < t.nnz; ++i) {
         int64_t r = (int64_t)t.brow * 16 + (idx[i] & 15u), c;
-        if (r >= m || !colof(idx[i] >> 4, &c)) return false;
-        f(r, c, rec + voff + i * vsize);
+        const uint8_t* v = value_at(ti, i, rec + voff + i * vsize);
+        if (r >= m || !colof(idx[i] >> 4, &c) || !v) return false;
+        f(r, c, v);
       }
     }
     return true;
   };
-  for (const CbTile& t : tiles)
-    if (!for_entries(t, [&](int64_t r, int64_t, const uint8_t*) { cnt[r + 1]++; })) {
+  for (size_t ti = 0; ti < tiles.size(); ++ti)
+    if (!for_entries(ti, [&](int64_t r, int64_t, const uint8_t*) { cnt[r + 1]++; })) {
       *msg = "corrupt blocked layout";
       return CBSPMV_ERR_INVALID;
     }
   for (int64_t r = 0; r < m; ++r) cnt[r + 1] += cnt[r];
   if (cnt[m] != nnz_expected) { *msg = "entry count mismatch in blocked layout"; return CBSPMV_ERR_INVALID; }
   std::vector<int64_t> cur(cnt.begin(), cnt.end() - 1);
-  for (const CbTile& t : tiles)
-    for_entries(t, [&](int64_t r, int64_t c, const uint8_t* v) {
+  for (size_t ti = 0; ti < tiles.size(); ++ti)
+    for_entries(ti, [&](int64_t r, int64_t c, const uint8_t* v) {
       int64_t k = cur[r]++;
       col[k] = (int32_t)c;
       val[k] = read_value(v, dtype);

@@ -521,8 +521,9 @@ cbspmv_status_t cbspmv_export_csr(cbspmv_handle_t h, int64_t* row_ptr, int32_t* 
   std::string msg;
   cbspmv_status_t st;
   if (h->device < 0) {
-    st = cb::decode_to_csr(p.m, p.n, p.value_dtype, p.aggregated, p.tiles, p.stream.data(), p.stream.size(),
-                           p.restore_cols.data(), p.restore_cols.size(), row_ptr, col_idx, val, p.nnz, &msg);
+    st = cb::decode_to_csr(p.m, p.n, p.value_dtype, p.aggregated, p.tiles, p.units, p.blob.data(), p.blob.size(),
+                           p.stream.data(), p.stream.size(), p.restore_cols.data(), p.restore_cols.size(), row_ptr,
+                           col_idx, val, p.nnz, &msg);
   } else {
     DeviceGuard g(h->device);
     CB_CUDA(g.err);
@@ -533,8 +534,9 @@ cbspmv_status_t cbspmv_export_csr(cbspmv_handle_t h, int64_t* row_ptr, int32_t* 
     if (!stream.empty()) CB_CUDA(cudaMemcpy(stream.data(), h->d_stream, stream.size(), cudaMemcpyDeviceToHost));
     if (!tiles.empty()) CB_CUDA(cudaMemcpy(tiles.data(), h->d_tiles, tiles.size() * sizeof(CbTile), cudaMemcpyDeviceToHost));
     if (!rcols.empty()) CB_CUDA(cudaMemcpy(rcols.data(), h->d_rcols, rcols.size() * 4, cudaMemcpyDeviceToHost));
-    st = cb::decode_to_csr(p.m, p.n, p.value_dtype, p.aggregated, tiles, stream.data(), stream.size(), rcols.data(),
-                           rcols.size(), row_ptr, col_idx, val, p.nnz, &msg);
+    st = cb::decode_to_csr(p.m, p.n, p.value_dtype, p.aggregated, tiles, p.units, p.blob.data(), p.blob.size(),
+                           stream.data(), stream.size(), rcols.data(), rcols.size(), row_ptr, col_idx, val, p.nnz,
+                           &msg);
   }
   if (st != CBSPMV_OK) return fail(st, "%s", msg.c_str());
   return ok();
@@ -763,7 +765,7 @@ const char* cbspmv_last_error(void) { return g_err.c_str(); }
 
 // The run-kernel revision changes whenever the kernel's code changes (measurements taken
 // with a profiler are tied to it).
-const char* cbspmv_version(void) { return "cbspmv 0.3 (sm_103a; run kernel rev 12)"; }
+const char* cbspmv_version(void) { return "cbspmv 0.3 (sm_103a; run kernel rev 13)"; }
 
 }  // extern "C"
 

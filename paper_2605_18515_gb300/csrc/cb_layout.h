@@ -104,13 +104,17 @@ struct CbSplitRow {
 //     bits [0,5) tile in the unit, [5,13) first entry inside the tile record (entry order
 //     of the record: row-major; Dense: row * 16 + col), [13,15) length 1..CB_CHUNK (0 = no
 //     chunk), bit 15 set when the chunk ends its row.
-//   CB_MODE_DIRECT units (single-entry chunks, or consecutive-column chunks of 4- and 2-byte
-//   values; at most CB_DIRECT_MAX_CHUNKS chunks) instead hold rows / 2 x CB_VLANES x (2 x uint32) pairs of
-//   32-bit direct descriptors: bits [0,13) byte offset of the chunk's first value from the
-//   start of the unit's stream bytes, [13,18) tile in the unit, [18,22) column of the first
-//   entry in the tile, [22,24) length (0 = no chunk), bit 24 set when the chunk ends its row.
-//   The run kernel then needs neither the tile bases nor the coordinate bytes to find a
-//   chunk's values and x values.
+//   CB_MODE_DIRECT units (single-entry or consecutive-column chunks; at most
+//   CB_DIRECT_MAX_CHUNKS chunks) instead hold rows / 2 x CB_VLANES x (2 x uint32) pairs of
+//   32-bit direct descriptors: bits [0,12) byte offset / 2 of the chunk's first value from
+//   the start of the unit's stream bytes, [12,17) tile in the unit, [17,21) column of the
+//   first entry in the tile, [21,23) length (0 = no chunk), bit 23 set when the chunk ends
+//   its row, [24,32) first entry inside the tile record. The run kernel then needs neither
+//   the tile bases nor the coordinate bytes to find a chunk's values and x values. A direct
+//   unit's stream bytes hold its tiles' coordinate parts (index bytes, CSR row pointer or
+//   Dense bitmap; 16-byte aligned, tile order) followed by its values in load order: for
+//   each chunk index j within a run, the chunks j of lanes 0..31, each chunk's values
+//   consecutive.
 #define CB_CHUNK 3
 // A unit whose chunks of up to CB_CHUNK entries would fill less than this share of their
 // FMA slots (sparse tiles, rows with one or two entries per tile) is scheduled in single

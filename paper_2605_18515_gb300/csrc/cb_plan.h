@@ -51,8 +51,11 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
 
 // Rebuilds CSR from the packed layout (host arrays). Used by export on both host-only
 // handles and on data read back from the device. Stored values are widened exactly to FP64.
+// units and blob (the unit blobs with their lane schedules) locate the values of direct
+// units, which are stored in load order after the coordinate parts.
 cbspmv_status_t decode_to_csr(int64_t m, int64_t n, int value_dtype, bool aggregated,
-                              const std::vector<CbTile>& tiles, const uint8_t* stream,
+                              const std::vector<CbTile>& tiles, const std::vector<CbUnit>& units,
+                              const uint8_t* blob, size_t blob_size, const uint8_t* stream,
                               size_t stream_size, const int32_t* restore_cols,
                               size_t restore_len, int64_t* row_ptr, int32_t* col, double* val,
                               int64_t nnz_expected, std::string* msg);

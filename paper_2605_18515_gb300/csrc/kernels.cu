@@ -421,8 +421,8 @@ __device__ bool consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_
                                 : (((b_) & 0xF0u) << (kXLog > 4 ? kXLog - 4 : 0)))
 #define CB_LOAD_CHUNK(d, v0, v1, v2, x0, x1, x2)                                   \
   if constexpr (kD) {                                                              \
-    const uint32_t va_ = vrec0 + ((d) & 0x1fffu);                                  \
-    const uint32_t xa_ = xrow0 + G::kXRow * (((d) >> 13) & 31u) + kXStride * (((d) >> 18) & 15u); \
+    const uint32_t va_ = vrec0 + (((d) & 0xfffu) << 1);                            \
+    const uint32_t xa_ = xrow0 + G::kXRow * (((d) >> 12) & 31u) + kXStride * (((d) >> 17) & 15u); \
     if constexpr (kC == 1) {                                                       \
       v0 = ValT<V>::load(sm + va_);                                                \
       load_xk<Acc, kK>(sm, xa_, x0);                                               \
@@ -483,7 +483,7 @@ __device__ bool consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_
     }
   };
   // length (0..3) and row-end flag of a descriptor
-  constexpr uint32_t kLenShift = kD ? 22 : 13, kEndBit = kD ? (1u << 24) : 0x8000u;
+  constexpr uint32_t kLenShift = kD ? 21 : 13, kEndBit = kD ? (1u << 23) : 0x8000u;
   if (steps) {
     desc_pair(0, dA, dB);
     CB_LOAD_CHUNK(dA, vA0, vA1, vA2, xA0, xA1, xA2);

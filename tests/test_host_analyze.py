@@ -235,24 +235,32 @@ def test_fma_slot_count(bd):
 
 
 def test_direct_descriptors_where_columns_are_known_per_chunk(bd):
-    """Single-entry units and consecutive-column units of 4- and 2-byte values (at most 512
-    chunks each) carry direct (value offset, tile, column) descriptors; FP64
-    consecutive-column units keep 16-bit descriptors."""
+    """Single-entry and consecutive-column units of at most 512 chunks carry direct (value
+    offset, tile, column, entry) descriptors and keep their values in load order after
+    the coordinate parts; export still returns every value bit-exactly (FP64) or as the
+    oracle's rounding of it (BF16)."""
+    from oracle import lowprec as L
     A = I.fem_block_band(n_rows=6000, n_block_rows=2000, half_band=300, seed=3)
-    with host(bd, A, value_dtype="bf16") as M:
-        st = M.stats()
-        rp, col, _ = M.export_csr()
-        assert np.array_equal(rp, A.row_ptr) and np.array_equal(col, A.col)
-    assert st["n_direct_units"] == st["n_xseq_units"] + st["n_entry_mode_units"] > 0
     with host(bd, A) as M:
         st = M.stats()
-    assert st["n_direct_units"] == st["n_entry_mode_units"]
-    with host(bd, I.rmat(13, 16, seed=2)) as M:
+        assert_roundtrip(M, A)
+    assert st["n_direct_units"] == st["n_xseq_units"] + st["n_entry_mode_units"] > 0
+    with host(bd, A, value_dtype="bf16") as M:
         st = M.stats()
+        rp, col, val = M.export_csr()
+    assert st["n_direct_units"] == st["n_xseq_units"] + st["n_entry_mode_units"] > 0
+    assert np.array_equal(rp, A.row_ptr) and np.array_equal(col, A.col)
+    assert np.array_equal(val.view(np.uint64), L.round_to_format(A.val, "bf16").view(np.uint64))
+    R = I.rmat(13, 16, seed=2)
+    with host(bd, R) as M:
+        st = M.stats()
+        assert_roundtrip(M, R)
     assert 0 < st["n_direct_units"] <= st["n_entry_mode_units"] + st["n_xseq_units"]
     r, c = np.repeat(np.arange(16), 16), np.tile(np.arange(16), 16)
-    with host(bd, I.csr_from_coo(16, 16, r, c, np.ones(256)), value_dtype="f32") as M:
-        assert M.stats()["n_direct_units"] == 1
+    D = I.csr_from_coo(16, 16, r, c, I.normal(4, I.TAG_VAL, 256))
+    with host(bd, D) as M:      # one Dense tile
+        assert M.stats()["n_direct_units"] == 1 and M.stats()["n_fmt"][2] == 1
+        assert_roundtrip(M, D)
 
 
 def test_long_single_entry_unit_keeps_16bit_descriptors(bd):
