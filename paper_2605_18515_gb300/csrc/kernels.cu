@@ -23,14 +23,18 @@
 //     wait for one another: the latency of one warp's copies is hidden by the other
 //     warps' arithmetic, and the descriptor of a warp's next unit is fetched while it
 //     computes the current one.
-//   * A warp computes each tile's base addresses from its record (CSR row pointer, COO
-//     coordinate bytes of Algorithm 3, the fixed rows of Algorithm 4). The analyser's lane
-//     schedule cuts the unit's entries, in row-major order, into chunks of at most CB_CHUNK
-//     entries of one (tile, row) piece and deals them to the 32 lanes in equal runs. Every
-//     lane then runs the same number of steps; a step reads one 16-bit chunk descriptor,
-//     decodes up to three coordinate bytes and issues up to three FMAs into the lane's row
-//     accumulator. No FMA slot is spent on reductions: a row sum is stored when its last
-//     chunk is done.
+//   * The analyser's lane schedule cuts the unit's entries, in row-major order, into chunks
+//     of at most CB_CHUNK entries of one (tile, row) piece and deals them to the 32 lanes
+//     in equal runs. Every lane then runs the same number of steps; a step reads the
+//     descriptors of two chunks with one load and issues up to six FMAs into the lane's
+//     single row accumulator. No FMA slot is spent on reductions: a row sum is stored when
+//     its last chunk is done. For plain units the warp first computes each tile's base
+//     addresses from its record (CSR row pointer, COO coordinate bytes of Algorithm 3, the
+//     fixed rows of Algorithm 4) and a chunk's 16-bit descriptor names its tile and first
+//     entry, whose coordinate bytes give the x columns. Single-entry and consecutive-column
+//     units instead carry 32-bit direct descriptors (value offset, tile, first column), and
+//     the analyser stores their values in load order, so a chunk needs no tile-base or
+//     coordinate load and the lanes of one load read consecutive bytes.
 //   * Rows that cross run boundaries are completed by the run holding the row's end
 //     (adding the earlier runs' carries in a fixed order); units that cover whole block
 //     rows write y directly (no atomics, y read once when beta != 0). Block rows cut into
