@@ -51,7 +51,8 @@ L2_BYTES = 129 * 2 ** 20
 # full workload by its number of stored entries. Used only when the loaded library reports
 # the same revision; otherwise the roofline's traffic is null.
 KERNEL_TRAFFIC = {
-    "run kernel rev 13": {("fem3x3_band_1m", "f64"): 1.1617e9, ("fem3x3_band_1m", "bf16"): 0.6535e9},
+    "run kernel rev 13": {("fem3x3_band_1m", "f64"): 1.1617e9, ("fem3x3_band_1m", "bf16"): 0.6535e9,
+                          ("rmat_s21", "f64"): 0.5897e9},
 }
 
 
