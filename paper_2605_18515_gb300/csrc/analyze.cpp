@@ -80,14 +80,35 @@ struct BlockRowOut {
   std::vector<std::pair<int64_t, uint32_t>> vslot;   // (CSR position, value byte offset in `bytes`)
 };
 
+// Sorts v, made of nruns consecutive ascending runs (run i = [bounds[i], bounds[i + 1])),
+// by merging the runs pairwise; tmp is scratch. Same result as std::sort for unique keys.
+template <class T>
+void merge_sorted_runs(std::vector<T>& v, std::vector<T>& tmp, const size_t* bounds, int nruns) {
+  tmp.resize(v.size());
+  for (int w = 1; w < nruns; w *= 2) {
+    for (int i = 0; i < nruns; i += 2 * w) {
+      const size_t lo = bounds[i], mid = bounds[std::min(i + w, nruns)], hi = bounds[std::min(i + 2 * w, nruns)];
+      std::merge(v.begin() + lo, v.begin() + mid, v.begin() + mid, v.begin() + hi, tmp.begin() + lo);
+    }
+    v.swap(tmp);
+  }
+}
+
 // Entries of one block row as (key = col << 4 | local row, CSR position), sorted by key.
-void gather_block_row(const cbspmv_csr_t& A, int64_t b, std::vector<std::pair<uint64_t, int64_t>>& e) {
+// Each row's columns ascend (canonical CSR), so the rows are sorted runs to be merged.
+void gather_block_row(const cbspmv_csr_t& A, int64_t b, std::vector<std::pair<uint64_t, int64_t>>& e,
+                      std::vector<std::pair<uint64_t, int64_t>>& tmp) {
   e.clear();
   int64_t r0 = b * CB_BLK, r1 = std::min<int64_t>(A.m, r0 + CB_BLK);
-  for (int64_t r = r0; r < r1; ++r)
+  size_t bounds[CB_BLK + 1];
+  int nr = 0;
+  bounds[0] = 0;
+  for (int64_t r = r0; r < r1; ++r) {
     for (int64_t k = A.row_ptr[r]; k < A.row_ptr[r + 1]; ++k)
       e.emplace_back(((uint64_t)(uint32_t)A.col_idx[k] << 4) | (uint64_t)(r - r0), k);
-  std::sort(e.begin(), e.end());
+    bounds[++nr] = e.size();
+  }
+  merge_sorted_runs(e, tmp, bounds, nr);
 }
 
 }  // namespace
@@ -159,9 +180,10 @@ double read_value(const uint8_t* src, int dtype) {
 int value_size(int dtype) { return dtype == CBSPMV_F64 ? 8 : dtype == CBSPMV_F32 ? 4 : 2; }
 
 void build_block_row(const cbspmv_csr_t& A, int64_t b, bool agg, int th1, int th2, int dtype, bool keep_slots,
-                     std::vector<std::pair<uint64_t, int64_t>>& e, BlockRowOut& out) {
+                     std::vector<std::pair<uint64_t, int64_t>>& e, std::vector<std::pair<uint64_t, int64_t>>& tmp,
+                     BlockRowOut& out) {
   const int vsize = value_size(dtype);
-  gather_block_row(A, b, e);
+  gather_block_row(A, b, e, tmp);
   out = BlockRowOut();
   const size_t ne = e.size();
   if (ne == 0) return;
@@ -188,13 +210,17 @@ void build_block_row(const cbspmv_csr_t& A, int64_t b, bool agg, int th1, int th
   while (a < ne) {
     uint32_t bj = acol[a] >> 4;
     size_t z = a;
-    tile.clear();
-    while (z < ne && (acol[z] >> 4) == bj) {
-      uint32_t lr = (uint32_t)(e[z].first & 15u), lc = acol[z] & 15u;
-      tile.emplace_back(lr * 16u + lc, e[z].second);
-      ++z;
+    while (z < ne && (acol[z] >> 4) == bj) ++z;
+    // row-major order inside the tile: the entries come by (column, row), so a stable
+    // counting sort by row leaves each row's columns ascending
+    uint32_t start[17] = {0};
+    for (size_t k = a; k < z; ++k) start[(e[k].first & 15u) + 1]++;
+    for (int r = 0; r < 16; ++r) start[r + 1] += start[r];
+    tile.resize(z - a);
+    for (size_t k = a; k < z; ++k) {
+      const uint32_t lr = (uint32_t)(e[k].first & 15u), lc = acol[k] & 15u;
+      tile[start[lr]++] = {lr * 16u + lc, e[k].second};
     }
-    std::sort(tile.begin(), tile.end());
     int nnz = (int)tile.size();
     int fmt = select_format(nnz, th1, th2);
     {
@@ -307,14 +333,19 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
   // --- step 2: plain 16x16 tiles and the super-sparse share (Sec. 3.3.1)
   std::atomic<int64_t> plain_tiles(0), plain_sparse(0);
   parallel_for(nbr, 256, [&](int64_t lo, int64_t hi) {
-    std::vector<uint32_t> bj;
+    std::vector<uint32_t> bj, tmp;
     int64_t pt = 0, ps = 0;
     for (int64_t b = lo; b < hi; ++b) {
       bj.clear();
       int64_t r0 = b * CB_BLK, r1 = std::min<int64_t>(A.m, r0 + CB_BLK);
-      for (int64_t r = r0; r < r1; ++r)
+      size_t bounds[CB_BLK + 1];
+      int nr = 0;
+      bounds[0] = 0;
+      for (int64_t r = r0; r < r1; ++r) {
         for (int64_t k = A.row_ptr[r]; k < A.row_ptr[r + 1]; ++k) bj.push_back((uint32_t)A.col_idx[k] >> 4);
-      std::sort(bj.begin(), bj.end());
+        bounds[++nr] = bj.size();
+      }
+      merge_sorted_runs(bj, tmp, bounds, nr);   // each row's block columns ascend
       size_t i = 0;
       while (i < bj.size()) {
         size_t j = i;
@@ -333,9 +364,10 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
   // --- step 3: per block row aggregation, tiling, format selection and packing
   std::vector<BlockRowOut> rows(nbr);
   parallel_for(nbr, 64, [&](int64_t lo, int64_t hi) {
-    std::vector<std::pair<uint64_t, int64_t>> e;
+    std::vector<std::pair<uint64_t, int64_t>> e, tmp;
     for (int64_t b = lo; b < hi; ++b)
-      build_block_row(A, b, p.aggregated, opts.th1, opts.th2, p.value_dtype, opts.keep_value_map != 0, e, rows[b]);
+      build_block_row(A, b, p.aggregated, opts.th1, opts.th2, p.value_dtype, opts.keep_value_map != 0, e, tmp,
+                      rows[b]);
   });
   // prefix sums over block rows: tiles, stream bytes, distinct columns
   std::vector<int64_t> tile_off(nbr + 1, 0), byte_off(nbr + 1, 0);
@@ -559,6 +591,7 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
     parallel_for((int64_t)nun, 128, [&](int64_t lo, int64_t hi) {
       std::vector<uint16_t> chunk;      // descriptors in row-major order
       std::vector<uint32_t> chunk32;    // direct descriptors (CB_MODE_DIRECT units)
+      std::vector<uint8_t> old, neu;    // a direct unit's stream bytes before / after re-laying
       std::vector<uint8_t> chunk_row;   // row of each chunk
       std::vector<uint8_t> chunk_first; // chunk starts its row
       for (int64_t i = lo; i < hi; ++i) {
@@ -637,8 +670,8 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
           // banks). The direct descriptors are retargeted; the coordinate parts keep the
           // record layout for export.
           const size_t ub = (size_t)u.byte_lo16 * 16;
-          std::vector<uint8_t> old(p.stream.begin() + ub, p.stream.begin() + ub + u.nbytes);
-          std::vector<uint8_t> neu(u.nbytes, 0);
+          old.assign(p.stream.begin() + ub, p.stream.begin() + ub + u.nbytes);
+          neu.assign(u.nbytes, 0);
           uint32_t w = 0;
           for (uint32_t t = 0; t < u.ntiles; ++t) {
             CbTile& tr = p.tiles[u.tile_lo + t];

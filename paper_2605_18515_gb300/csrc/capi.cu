@@ -236,7 +236,7 @@ cbspmv_status_t cbspmv_analyze(const cbspmv_csr_t* A, const cbspmv_opts_t* opts_
                 cudaGetErrorString(e));
   }
   // the packed stream and the value map now live on the device; export reads it back
-  std::vector<uint8_t>().swap(p.stream);
+  cb::ByteBuf().swap(p.stream);
   std::vector<uint32_t>().swap(p.value_slot);
   *out = h;
   return ok();
