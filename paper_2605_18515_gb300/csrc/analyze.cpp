@@ -585,7 +585,7 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
       p.fma_slots += (int64_t)(CB_VLANES * rows * cap);
     }
     if (off[nun] / 16 >= (1ULL << 32)) { *msg = "schedule array too large"; return CBSPMV_ERR_UNSUPPORTED; }
-    p.sched.assign(off[nun] / 4, 0);
+    p.sched.resize(off[nun] / 4);   // zeroed unit by unit below (descriptors past a run's end are 0)
     // new value slot of every value slot a direct unit re-lays (only for the value map)
     std::vector<uint32_t> moved(p.value_slot.empty() ? 0 : p.stream.size() / p.vsize, UINT32_MAX);
     parallel_for((int64_t)nun, 128, [&](int64_t lo, int64_t hi) {
@@ -598,6 +598,7 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
         CbUnit& u = p.units[i];
         const int64_t R = std::min<int64_t>((int64_t)CB_BLK * u.nbr, A.m - (int64_t)u.brow_lo * CB_BLK);
         uint8_t* base = reinterpret_cast<uint8_t*>(p.sched.data()) + off[i];
+        std::memset(base, 0, sbytes[i]);
         uint16_t* hdr = reinterpret_cast<uint16_t*>(base);
         uint8_t* nxt = base + 2 * CB_VLANES;
         uint16_t* desc = reinterpret_cast<uint16_t*>(base + CB_SCHED_HDR(R));
@@ -739,7 +740,7 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
       boff[i + 1] = boff[i] + u.blob_bytes;
     }
     if (boff[nun] / 16 >= (1ULL << 32)) { *msg = "unit blob array too large"; return CBSPMV_ERR_UNSUPPORTED; }
-    p.blob.assign(boff[nun], 0);
+    p.blob.resize(boff[nun]);       // tile records + restore_cols slice + schedule fill each blob
     parallel_for((int64_t)nun, 256, [&](int64_t lo, int64_t hi) {
       for (int64_t i = lo; i < hi; ++i) {
         CbUnit& u = p.units[i];

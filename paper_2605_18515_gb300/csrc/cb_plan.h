@@ -49,8 +49,9 @@ struct Plan {
   int64_t restore_cols_len = 0;
 
   std::vector<CbUnit> units;
-  std::vector<uint32_t> sched;         // lane schedules of all units (see cb_layout.h)
-  std::vector<uint8_t> blob;           // unit blobs (see cb_layout.h)
+  std::vector<uint32_t, NoInitAlloc<uint32_t>> sched;   // lane schedules of all units (see cb_layout.h;
+                                                      // each unit zeroes its own range)
+  ByteBuf blob;                        // unit blobs (see cb_layout.h; every byte written)
   std::vector<CbSplitRow> split_rows;  // block rows cut into several units
   std::vector<uint32_t> worker_units;  // unit ids grouped by worker (CTA)
   std::vector<uint32_t> worker_off;    // n_workers + 1
