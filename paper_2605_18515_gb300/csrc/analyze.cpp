@@ -591,7 +591,7 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
     parallel_for((int64_t)nun, 128, [&](int64_t lo, int64_t hi) {
       std::vector<uint16_t> chunk;      // descriptors in row-major order
       std::vector<uint32_t> chunk32;    // direct descriptors (CB_MODE_DIRECT units)
-      std::vector<uint8_t> old, neu;    // a direct unit's stream bytes before / after re-laying
+      std::vector<uint8_t> old;         // a direct unit's stream bytes before re-laying
       std::vector<uint8_t> chunk_row;   // row of each chunk
       std::vector<uint8_t> chunk_first; // chunk starts its row
       for (int64_t i = lo; i < hi; ++i) {
@@ -672,14 +672,14 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
           // record layout for export.
           const size_t ub = (size_t)u.byte_lo16 * 16;
           old.assign(p.stream.begin() + ub, p.stream.begin() + ub + u.nbytes);
-          neu.assign(u.nbytes, 0);
+          uint8_t* neu = p.stream.data() + ub;   // re-laid in place from the copy
           uint32_t w = 0;
           for (uint32_t t = 0; t < u.ntiles; ++t) {
             CbTile& tr = p.tiles[u.tile_lo + t];
             const uint32_t cpart = tr.fmt == CB_FMT_COO   ? align16(tr.nnz)
                                    : tr.fmt == CB_FMT_CSR ? align16(17u + tr.nnz)
                                                           : 32u;
-            std::memcpy(neu.data() + w, old.data() + ((size_t)tr.vp16 * 16 - ub), cpart);
+            std::memcpy(neu + w, old.data() + ((size_t)tr.vp16 * 16 - ub), cpart);
             tr.vp16 = (uint32_t)((ub + w) / 16);
             w += cpart;
           }
@@ -691,13 +691,13 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
               if (c0 + j >= c1) continue;
               uint32_t& d = chunk32[c0 + j];
               const uint32_t len = (d >> 21) & 3u, vo = (d & 0xfffu) << 1;
-              std::memcpy(neu.data() + w, old.data() + vo, (size_t)len * vs);
+              std::memcpy(neu + w, old.data() + vo, (size_t)len * vs);
               if (!moved.empty())
                 for (uint32_t q = 0; q < len; ++q) moved[(ub + vo) / vs + q] = (uint32_t)((ub + w) / vs + q);
               d = (d & ~0xfffu) | (w >> 1);
               w += len * vs;
             }
-          std::memcpy(p.stream.data() + ub, neu.data(), u.nbytes);
+          std::memset(neu + w, 0, u.nbytes - w);   // the record padding the re-layout freed
         }
         int first_lane[CB_R_MAX], last_lane[CB_R_MAX];   // lanes holding chunks of each row
         for (int r = 0; r < CB_R_MAX; ++r) first_lane[r] = last_lane[r] = -1;
