@@ -888,7 +888,8 @@ cbspmv_status_t decode_to_csr(int64_t m, int64_t n, int dtype, bool aggregated,
   // offset of every value of their tiles, from the direct descriptors (first entry, length,
   // value offset) of the unit's lane schedule.
   std::vector<int64_t> vfirst(tiles.size(), -1);   // tile -> first slot in vpos
-  std::vector<uint64_t> vpos;
+  std::vector<uint64_t> vunit(tiles.size(), 0);    // tile -> stream offset of its unit
+  std::vector<uint16_t> vpos;                      // value offset inside the unit (< CB_B_MAX)
   for (const CbUnit& u : units) {
     if (!(u.mode & CB_MODE_DIRECT)) continue;
     const int64_t R = std::min<int64_t>((int64_t)CB_BLK * u.nbr, m - (int64_t)u.brow_lo * CB_BLK);
@@ -900,14 +901,16 @@ cbspmv_status_t decode_to_csr(int64_t m, int64_t n, int dtype, bool aggregated,
     for (uint32_t t = 0; t < u.ntiles; ++t) {
       const CbTile& tr = tiles[u.tile_lo + t];
       vfirst[u.tile_lo + t] = (int64_t)vpos.size();
-      vpos.resize(vpos.size() + (tr.fmt == CB_FMT_DENSE ? 256u : tr.nnz), UINT64_MAX);
+      vunit[u.tile_lo + t] = (uint64_t)u.byte_lo16 * 16;
+      vpos.resize(vpos.size() + (tr.fmt == CB_FMT_DENSE ? 256u : tr.nnz), UINT16_MAX);
     }
     const uint32_t* d = reinterpret_cast<const uint32_t*>(blob + so + CB_SCHED_HDR(R));
     const size_t nd = (u.sched_bytes - CB_SCHED_HDR(R)) / 4;
     for (size_t k = 0; k < nd; ++k) {
       const uint32_t len = (d[k] >> 21) & 3u, t = (d[k] >> 12) & 31u, e = d[k] >> 24;
       if (!len) continue;
-      const uint64_t vo = (uint64_t)u.byte_lo16 * 16 + ((d[k] & 0xfffu) << 1);
+      const uint32_t vo_rel = (d[k] & 0xfffu) << 1;
+      const uint64_t vo = (uint64_t)u.byte_lo16 * 16 + vo_rel;
       if (t >= u.ntiles) {
         *msg = "corrupt direct descriptor";
         return CBSPMV_ERR_INVALID;
@@ -918,13 +921,13 @@ cbspmv_status_t decode_to_csr(int64_t m, int64_t n, int dtype, bool aggregated,
         *msg = "corrupt direct descriptor";
         return CBSPMV_ERR_INVALID;
       }
-      for (uint32_t q = 0; q < len; ++q) vpos[vfirst[u.tile_lo + t] + e + q] = vo + (uint64_t)q * vsize;
+      for (uint32_t q = 0; q < len; ++q) vpos[vfirst[u.tile_lo + t] + e + q] = (uint16_t)(vo_rel + q * vsize);
     }
   }
   auto value_at = [&](size_t ti, uint32_t e, const uint8_t* plain) -> const uint8_t* {
     if (vfirst[ti] < 0) return plain;
-    const uint64_t p = vpos[vfirst[ti] + e];
-    return p == UINT64_MAX ? nullptr : stream + p;
+    const uint16_t p = vpos[vfirst[ti] + e];
+    return p == UINT16_MAX ? nullptr : stream + vunit[ti] + p;
   };
   auto for_entries = [&](size_t ti, const std::function<void(int64_t, int64_t, const uint8_t*)>& f) -> bool {
     const CbTile& t = tiles[ti];
