@@ -142,6 +142,8 @@ cbspmv_status_t cbspmv_default_opts(cbspmv_opts_t* opts);
  * into one byte stream with 16-byte aligned virtual pointers, units of work and their
  * load-balanced assignment to the kernel's workers; then one upload per device array.
  * stream: upload stream (void* cudaStream_t); the call synchronises it before returning.
+ * The host analysis runs on all hardware threads (at most 64), or on the number given by
+ * the environment variable CBSPMV_HOST_THREADS (1..64); its result does not depend on it.
  * On success *out is a new handle. Errors: CBSPMV_ERR_INVALID (NULL pointers, sizes),
  * CBSPMV_ERR_NOT_CANONICAL, CBSPMV_ERR_OOM, CBSPMV_ERR_CUDA, CBSPMV_ERR_UNSUPPORTED. */
 cbspmv_status_t cbspmv_analyze(const cbspmv_csr_t* A, const cbspmv_opts_t* opts, void* stream,

@@ -13,6 +13,7 @@
 #include <atomic>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <queue>
@@ -24,7 +25,13 @@
 namespace cb {
 namespace {
 
+// Analysis threads: the host's hardware threads (at most 64), or CBSPMV_HOST_THREADS
+// (1..64) when set. The result does not depend on the count.
 int host_threads() {
+  if (const char* env = std::getenv("CBSPMV_HOST_THREADS")) {
+    const long v = std::strtol(env, nullptr, 10);
+    if (v >= 1 && v <= 64) return (int)v;
+  }
   unsigned h = std::thread::hardware_concurrency();
   if (h == 0) h = 1;
   return (int)std::min(h, 64u);

@@ -272,3 +272,42 @@ def test_long_single_entry_unit_keeps_16bit_descriptors(bd):
         assert_roundtrip(M, A)
     assert st["n_units"] == 1 and st["n_entry_mode_units"] == 1 and st["n_direct_units"] == 0
     assert st["fma_slots"] == 32 * 18       # 540 chunks: 17 per lane, 18 descriptor rows
+
+
+def test_analysis_does_not_depend_on_the_thread_count(bd, tmp_path):
+    """The same analysis with one host thread (CBSPMV_HOST_THREADS=1, in a child process)
+    and with all of them: equal statistics (apart from the time) and equal exports."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = """
+import json, sys
+import numpy as np
+sys.path.insert(0, ROOT)
+from paper_2605_18515_gb300 import build, inputs as I
+build.build()
+from paper_2605_18515_gb300 import binding as bd
+out = {}
+for name, A in (("fem", I.fem_block_band(n_rows=6000, n_block_rows=2000, half_band=300, seed=3)),
+                ("rmat", I.rmat(12, 16, seed=4))):
+    with bd.BlockedMatrix(A, device=-1, keep_value_map=True) as M:
+        st = M.stats(); st.pop("analyze_ms")
+        rp, col, val = M.export_csr()
+        blk = M.export_blocked()
+    out[name] = {"stats": st, "val": val.view(np.uint64).tolist()[:5000],
+                 "valsum": int(val.view(np.uint64).sum() % (1 << 61)),
+                 "blk": {k: np.asarray(v).tolist() for k, v in blk.items()}}
+print(json.dumps(out))
+""".replace("ROOT", repr(root))
+    res = {}
+    for threads in ("1", None):
+        env = dict(os.environ)
+        env.pop("CBSPMV_HOST_THREADS", None)
+        if threads:
+            env["CBSPMV_HOST_THREADS"] = threads
+        p = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        assert p.returncode == 0, p.stderr[-2000:]
+        res[threads] = json.loads(p.stdout.strip().splitlines()[-1])
+    assert res["1"] == res[None]
