@@ -84,7 +84,11 @@ typedef struct {
  *        priority-queue rule; 0 deal them out round-robin in matrix order (ablation).
  *   device: CUDA device ordinal for the handle's memory; -1 builds a host-only handle
  *        (analysis, export and statistics work; run calls return CBSPMV_ERR_INVALID).
- *   keep_value_map: 0 (default) or 1, see cbspmv_update_values. */
+ *   keep_value_map: 0 (default) or 1, see cbspmv_update_values.
+ *   record_layout: 0 (default): FP64 values are packed per unit in lane order (the
+ *        lane-stream layout of the FP64 run kernel); 1: FP64 values use the per-sub-block
+ *        record layout of the reduced types and their kernel (for comparison). The
+ *        reduced types always use the record layout. Results agree within the tolerance. */
 typedef struct {
   double th0;
   int th1, th2;
@@ -95,7 +99,8 @@ typedef struct {
   int device;
   int keep_value_map;       /* 1: record each entry's value slot (4 bytes per entry on the
                                device) so cbspmv_update_values can re-pack new values */
-  int reserved[7];
+  int record_layout;        /* 1: FP64 values in the record layout (see above) */
+  int reserved[6];
 } cbspmv_opts_t;
 
 /* Statistics of an analysed matrix. Byte counts follow the storage model of Sec. 4.4.1
@@ -131,6 +136,7 @@ typedef struct {
                                       chunk steps x chunk size, summed over units); nnz / fma_slots
                                       is the fraction of FMA issue that does useful work */
   int64_t n_direct_units;          /* units whose chunk descriptors hold value offsets and columns */
+  int64_t lane_layout;             /* 1: FP64 lane-stream layout (see record_layout), 0: records */
 } cbspmv_stats_t;
 
 /* Fills *opts with the paper's settings: th0 0.15, th1 32, th2 128, col_agg -1,
@@ -350,7 +356,9 @@ cbspmv_status_t cbspmv_server_create(const cbspmv_server_opts_t* opts, cbspmv_se
 cbspmv_status_t cbspmv_server_register(cbspmv_server_t s, const cbspmv_csr_t* A,
                                        const cbspmv_opts_t* opts, int* matrix_id);
 /* Queues a request; *ticket identifies it. Errors: CBSPMV_ERR_INVALID (unknown matrix,
- * NULL buffers, CG on a non-square matrix, tol <= 0), CBSPMV_ERR_CUDA (engine stopped). */
+ * NULL buffers, CG on a non-square matrix, tol <= 0), CBSPMV_ERR_OOM (the request's device
+ * workspace is larger than the whole memory budget, so it could never be admitted; nothing
+ * is queued), CBSPMV_ERR_CUDA (engine stopped). */
 cbspmv_status_t cbspmv_server_submit(cbspmv_server_t s, const cbspmv_request_t* req,
                                      uint64_t* ticket);
 /* Non-blocking: *res = the request's state (res->done = 0 while it runs). A finished

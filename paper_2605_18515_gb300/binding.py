@@ -38,7 +38,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("th0", ctypes.c_double), ("th1", ctypes.c_int), ("th2", ctypes.c_int),
                 ("col_agg", ctypes.c_int), ("value_dtype", ctypes.c_int), ("unit_work", ctypes.c_int),
                 ("load_balance", ctypes.c_int), ("device", ctypes.c_int), ("keep_value_map", ctypes.c_int),
-                ("reserved", ctypes.c_int * 7)]
+                ("record_layout", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
 
 
 class Stats(ctypes.Structure):
@@ -58,7 +58,8 @@ class Stats(ctypes.Structure):
                 ("worker_load_mean", ctypes.c_double), ("worker_load_std", ctypes.c_double),
                 ("tb8_load_std", ctypes.c_double), ("analyze_ms", ctypes.c_double),
                 ("n_entry_mode_units", ctypes.c_int64), ("n_xseq_units", ctypes.c_int64),
-                ("fma_slots", ctypes.c_int64), ("n_direct_units", ctypes.c_int64)]
+                ("fma_slots", ctypes.c_int64), ("n_direct_units", ctypes.c_int64),
+                ("lane_layout", ctypes.c_int64)]
 
 
 class ServerOpts(ctypes.Structure):
@@ -218,7 +219,7 @@ def _csr_struct(A):
 
 
 def _make_opts(th0=0.15, th1=32, th2=128, col_agg=-1, value_dtype="f64", unit_work=0,
-               load_balance=True, device=0, keep_value_map=False) -> Opts:
+               load_balance=True, device=0, keep_value_map=False, record_layout=False) -> Opts:
     o = default_opts()
     o.th0, o.th1, o.th2, o.col_agg = th0, th1, th2, col_agg
     o.value_dtype = DTYPES[value_dtype]
@@ -226,6 +227,7 @@ def _make_opts(th0=0.15, th1=32, th2=128, col_agg=-1, value_dtype="f64", unit_wo
     o.load_balance = 1 if load_balance else 0
     o.device = device
     o.keep_value_map = 1 if keep_value_map else 0
+    o.record_layout = 1 if record_layout else 0
     return o
 
 
@@ -247,12 +249,14 @@ class BlockedMatrix:
     (e.g. inputs.CSR). device=-1 gives a host-only handle (analysis and export only)."""
 
     def __init__(self, A, *, th0=0.15, th1=32, th2=128, col_agg=-1, value_dtype="f64",
-                 unit_work=0, load_balance=True, device=0, stream=None, keep_value_map=False):
+                 unit_work=0, load_balance=True, device=0, stream=None, keep_value_map=False,
+                 record_layout=False):
         """A's arrays may be host arrays or CUDA torch tensors (device-resident input)."""
         self._h = ctypes.c_void_p(None)
         self.m, self.n = int(A.m), int(A.n)
         csr, _keep, self.nnz = _csr_struct(A)
-        o = _make_opts(th0, th1, th2, col_agg, value_dtype, unit_work, load_balance, device, keep_value_map)
+        o = _make_opts(th0, th1, th2, col_agg, value_dtype, unit_work, load_balance, device, keep_value_map,
+                       record_layout)
         self.device = device
         self.value_dtype = value_dtype
         self.vec = "f64" if value_dtype == "f64" else "f32"

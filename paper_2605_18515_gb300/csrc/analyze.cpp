@@ -311,6 +311,142 @@ cbspmv_status_t validate(const cbspmv_csr_t& A, std::string* msg) {
 
 }  // namespace
 
+// Lane-stream programs of every unit (layout in cb_layout.h), built from the packed records
+// after the load balance (so each worker's units are contiguous in the arrays). rowcnt:
+// entries of each (tile, row) of the records (16 per row for Dense tiles, whose present
+// entries come from the presence bitmap). Also composes the value map with the move of
+// every value from its record to its lane position, and counts the FMA slots.
+static cbspmv_status_t build_lane_programs(const cbspmv_csr_t& A, Plan& p, const std::vector<uint8_t>& rowcnt,
+                                           std::string* msg) {
+  const size_t nun = p.units.size();
+  std::vector<uint64_t> voff(nun + 1, 0), woff(nun + 1, 0), goff(nun + 1, 0);
+  for (size_t i = 0; i < nun; ++i) {
+    const CbUnit& u = p.units[i];
+    uint64_t W = 0;
+    for (uint32_t t = 0; t < u.ntiles; ++t) W += p.tiles[u.tile_lo + t].nnz;
+    const uint64_t S = (W + CB_VLANES - 1) / CB_VLANES;
+    voff[i + 1] = voff[i] + S;
+    woff[i + 1] = woff[i] + (S + 3) / 4;
+    goff[i + 1] = goff[i] + 16ull * u.ntiles;
+  }
+  if (voff[nun] >= (1ull << 32) || woff[nun] >= (1ull << 32) || goff[nun] >= (1ull << 32)) {
+    *msg = "lane stream too large";
+    return CBSPMV_ERR_UNSUPPORTED;
+  }
+  try {
+    p.lane_units.resize(nun);
+    p.lane_vals.resize((size_t)voff[nun] * CB_VLANES);
+    p.lane_words.resize((size_t)woff[nun] * CB_VLANES);
+    p.lane_gcols.resize((size_t)goff[nun]);
+  } catch (...) {
+    *msg = "host allocation failed";
+    return CBSPMV_ERR_OOM;
+  }
+  // value index in the record stream -> value index in the lane stream (value map only)
+  std::vector<uint32_t> moved(p.value_slot.empty() ? 0 : p.stream.size() / 8, UINT32_MAX);
+  parallel_for((int64_t)nun, 128, [&](int64_t lo, int64_t hi) {
+    struct Ent { uint16_t word; uint32_t vidx; };   // entry word, value index in the record stream
+    std::vector<Ent> ent;
+    for (int64_t i = lo; i < hi; ++i) {
+      const CbUnit& u = p.units[i];
+      const int64_t R = std::min<int64_t>((int64_t)CB_BLK * u.nbr, A.m - (int64_t)u.brow_lo * CB_BLK);
+      ent.clear();
+      // entries row by row: block row of the unit, row nibble, tile, column
+      uint32_t t_begin = 0;
+      for (int64_t brl = 0; brl < u.nbr; ++brl) {
+        uint32_t t_end = t_begin;
+        while (t_end < u.ntiles && (int64_t)p.tiles[u.tile_lo + t_end].brow - u.brow_lo == brl) ++t_end;
+        for (int rr = 0; rr < 16; ++rr) {
+          const int64_t row = brl * 16 + rr;
+          if (row >= R) break;
+          for (uint32_t t = t_begin; t < t_end; ++t) {
+            const size_t tg = (size_t)(u.tile_lo + t);
+            const CbTile& tr = p.tiles[tg];
+            const size_t rec = (size_t)tr.vp16 * 16;
+            if (tr.fmt == CB_FMT_DENSE) {
+              const uint8_t* bm = p.stream.data() + rec;
+              for (uint32_t c = 0; c < 16; ++c) {
+                const uint32_t pos = 16u * rr + c;
+                if (bm[pos >> 3] & (1u << (pos & 7)))
+                  ent.push_back({(uint16_t)((16u * t + c) | ((uint32_t)row << 9)), (uint32_t)((rec + 32 + 8 * pos) / 8)});
+              }
+            } else {
+              const uint32_t c = rowcnt[tg * 16 + rr];
+              if (!c) continue;
+              uint32_t s0 = 0;
+              for (int q = 0; q < rr; ++q) s0 += rowcnt[tg * 16 + q];
+              const uint32_t ib = tr.fmt == CB_FMT_CSR ? 17u : 0u;
+              const uint32_t va = align16(ib + tr.nnz);
+              for (uint32_t e = s0; e < s0 + c; ++e) {
+                const uint32_t col = p.stream[rec + ib + e] >> 4;
+                ent.push_back({(uint16_t)((16u * t + col) | ((uint32_t)row << 9)), (uint32_t)((rec + va + 8 * e) / 8)});
+              }
+            }
+          }
+        }
+        t_begin = t_end;
+      }
+      const uint64_t W = ent.size();
+      const uint64_t S = voff[i + 1] - voff[i];
+      double* vals = p.lane_vals.data() + (size_t)voff[i] * CB_VLANES;
+      uint64_t* words = p.lane_words.data() + (size_t)woff[i] * CB_VLANES;
+      std::fill(vals, vals + S * CB_VLANES, 0.0);
+      std::fill(words, words + ((S + 3) / 4) * CB_VLANES, ~0ull);
+      int first_lane[CB_R_MAX], last_lane[CB_R_MAX];
+      for (int r = 0; r < CB_R_MAX; ++r) first_lane[r] = last_lane[r] = -1;
+      for (uint32_t l = 0; l < CB_VLANES; ++l) {
+        const uint64_t c0 = (l * W) / CB_VLANES, c1 = ((l + 1) * W) / CB_VLANES;
+        for (uint64_t k = c0; k < c1; ++k) {
+          const uint64_t st = k - c0;
+          const Ent& e = ent[k];
+          std::memcpy(vals + st * CB_VLANES + l, p.stream.data() + (size_t)e.vidx * 8, 8);
+          uint64_t& w = words[(st / 4) * CB_VLANES + l];
+          const uint32_t sh = 16u * (uint32_t)(st % 4);
+          w = (w & ~(0xffffull << sh)) | ((uint64_t)e.word << sh);
+          if (!moved.empty()) moved[e.vidx] = (uint32_t)(((size_t)voff[i] + st) * CB_VLANES + l);
+          const int r = e.word >> 9;
+          if (first_lane[r] < 0) first_lane[r] = (int)l;
+          last_lane[r] = (int)l;
+        }
+      }
+      int span_max = 0;
+      for (int r = 0; r < CB_R_MAX; ++r)
+        if (first_lane[r] >= 0) span_max = std::max(span_max, last_lane[r] - first_lane[r] + 1);
+      // gather list: the x column of every slot
+      int32_t* g = p.lane_gcols.data() + goff[i];
+      for (uint32_t t = 0; t < u.ntiles; ++t) {
+        const CbTile& tr = p.tiles[u.tile_lo + t];
+        for (uint32_t c = 0; c < 16; ++c) {
+          int64_t col = -1;
+          if (p.aggregated) {
+            const int64_t k = (int64_t)tr.xbase + c;
+            if (k < p.cols_offset[tr.brow + 1]) col = p.restore_cols[k];
+          } else {
+            const int64_t k = (int64_t)tr.xbase + c;
+            if (k < A.n) col = k;
+          }
+          g[16 * t + c] = (int32_t)col;
+        }
+      }
+      CbLaneUnit& L = p.lane_units[i];
+      L = CbLaneUnit{};
+      L.vals = (uint32_t)voff[i];
+      L.words = (uint32_t)woff[i];
+      L.gcols = (uint32_t)goff[i];
+      L.brow_lo = u.brow_lo;
+      L.steps = (uint16_t)S;
+      L.nslots = (uint16_t)(16 * u.ntiles);
+      L.nrows = (uint16_t)R;
+      L.flags = span_max > CB_SCAN_SPAN ? CB_LUNIT_SCAN : 0;
+      L.slot = u.split >= 0 ? u.slot : 0xffffffffu;
+    }
+  });
+  if (!moved.empty())
+    for (uint32_t& sl : p.value_slot) sl = moved[sl];
+  p.fma_slots = (int64_t)voff[nun] * CB_VLANES;
+  return CBSPMV_OK;
+}
+
 cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, int n_workers,
                              Plan* P, std::string* msg) {
   auto t_start = std::chrono::steady_clock::now();
@@ -324,6 +460,7 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
   }
   if (opts.col_agg < -1 || opts.col_agg > 1) { *msg = "col_agg must be -1, 0 or 1"; return CBSPMV_ERR_INVALID; }
   if (opts.keep_value_map != 0 && opts.keep_value_map != 1) { *msg = "keep_value_map must be 0 or 1"; return CBSPMV_ERR_INVALID; }
+  if (opts.record_layout != 0 && opts.record_layout != 1) { *msg = "record_layout must be 0 or 1"; return CBSPMV_ERR_INVALID; }
   if (n_workers <= 0) { *msg = "no workers"; return CBSPMV_ERR_INVALID; }
   cbspmv_status_t st = validate(A, msg);
   if (st != CBSPMV_OK) return st;
@@ -335,6 +472,7 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
   p.value_dtype = opts.value_dtype;
   p.vsize = value_size(opts.value_dtype);
   p.th0 = opts.th0; p.th1 = opts.th1; p.th2 = opts.th2;
+  p.lanes = p.value_dtype == CBSPMV_F64 && opts.record_layout == 0;
   const int64_t nbr = p.nbr;
 
   // --- step 2: plain 16x16 tiles and the super-sparse share (Sec. 3.3.1)
@@ -434,13 +572,23 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
     }
   });
 
-  // --- step 4a: units of work
-  const uint32_t BMAX = CB_B_MAX_FOR(p.vsize);   // stream bytes per unit for this value size
-  const uint32_t U = opts.unit_work > 0 ? std::min<uint32_t>((uint32_t)opts.unit_work, CB_UNIT_WORK_MAX)
-                                        : CB_UNIT_WORK_DEFAULT;
-  auto tile_work = [&](int64_t t) -> uint32_t { return p.tiles[t].fmt == CB_FMT_DENSE ? 256u : p.tiles[t].nnz; };
+  // --- step 4a: units of work. Record layout: every unit must fit one warp's shared-memory
+  // buffer (stream bytes, tiles, multiply-adds incl. Dense zero fill). Lane-stream layout:
+  // the values stream through registers, so only the x slots (tiles) and rows bound a
+  // unit, and its work is its stored entries.
+  const bool lanes = p.lanes;
+  const uint32_t BMAX = lanes ? UINT32_MAX : CB_B_MAX_FOR(p.vsize);   // stream bytes per unit
+  const uint32_t U = lanes ? (opts.unit_work > 0 ? std::min<uint32_t>((uint32_t)opts.unit_work, CB_LANE_WORK_MAX)
+                                                 : CB_LANE_WORK_DEFAULT)
+                           : (opts.unit_work > 0 ? std::min<uint32_t>((uint32_t)opts.unit_work, CB_UNIT_WORK_MAX)
+                                                 : CB_UNIT_WORK_DEFAULT);
+  const int64_t TMAX = lanes ? CB_LANE_T_MAX : CB_T_MAX;
+  const uint32_t NBRMAX = lanes ? CB_LANE_NBR_MAX : CB_NBR_MAX;
+  auto tile_work = [&](int64_t t) -> uint32_t {
+    return (!lanes && p.tiles[t].fmt == CB_FMT_DENSE) ? 256u : p.tiles[t].nnz;
+  };
   auto tile_bytes = [&](int64_t t) -> uint32_t {
-    return record_bytes(p.tiles[t].fmt, p.tiles[t].nnz, p.vsize);
+    return lanes ? 0u : record_bytes(p.tiles[t].fmt, p.tiles[t].nnz, p.vsize);
   };
   auto finish_unit = [&](CbUnit& u) {
     if (p.aggregated && u.ntiles > 0) {
@@ -464,10 +612,10 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
     uint64_t W = 0, B = 0;
     for (int64_t t = t0; t < t1; ++t) { W += tile_work(t); B += tile_bytes(t); }
     int64_t T = t1 - t0;
-    bool big = W > U || B > BMAX || T > CB_T_MAX;
+    bool big = W > U || B > BMAX || T > TMAX;
     if (!big) {
       if (have_open && open.work + W <= U && open.nbytes + B <= BMAX &&
-          open.ntiles + T <= CB_T_MAX && open.nbr < CB_NBR_MAX) {
+          open.ntiles + T <= TMAX && open.nbr < NBRMAX) {
         open.ntiles = (uint16_t)(open.ntiles + T);
         open.nbr = (uint16_t)(open.nbr + 1);
         open.nbytes += (uint32_t)B;
@@ -491,14 +639,14 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
     if (have_open) { finish_unit(open); have_open = false; }
     // cut the block row into parts of about equal work within the unit limits
     uint64_t nparts_est = std::max<uint64_t>({(W + U - 1) / U, (B + BMAX - 1) / BMAX,
-                                              (uint64_t)((T + CB_T_MAX - 1) / CB_T_MAX), 2});
+                                              (uint64_t)((T + TMAX - 1) / TMAX), 2});
     uint64_t target = (W + nparts_est - 1) / nparts_est;
     size_t first_unit = p.units.size();
     CbUnit u{};
     u.tile_lo = (uint32_t)t0; u.nbr = 1; u.brow_lo = (uint32_t)b; u.split = split_id;
     for (int64_t t = t0; t < t1; ++t) {
       uint32_t wt = tile_work(t), bt = tile_bytes(t);
-      if (u.ntiles > 0 && (u.work + wt > U || u.nbytes + bt > BMAX || u.ntiles + 1 > CB_T_MAX ||
+      if (u.ntiles > 0 && (u.work + wt > U || u.nbytes + bt > BMAX || u.ntiles + 1 > TMAX ||
                            u.work >= target)) {
         finish_unit(u);
         CbUnit v{};
@@ -534,7 +682,7 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
   p.n_slots = (int)slot;
 
   // --- step 4a': lane schedule of every unit (chunks of <= CB_CHUNK entries, see cb_layout.h)
-  {
+  if (!lanes) {
     const size_t nun = p.units.size();
     // bytes of each unit's schedule: header + steps * 64
     std::vector<uint64_t> sbytes(nun), chunks_of(nun);
@@ -738,7 +886,7 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
   }
 
   // --- unit blobs: tile records, restore_cols slice and schedule of each unit, back to back
-  {
+  if (!lanes) {
     const size_t nun = p.units.size();
     std::vector<uint64_t> boff(nun + 1, 0);
     for (size_t i = 0; i < nun; ++i) {
@@ -764,9 +912,13 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
 
   // every unit must fit one shared-memory stage of the kernel
   for (const CbUnit& u : p.units) {
-    if (u.nbytes > BMAX || u.ntiles > CB_T_MAX || u.rc_n > CB_RC_MAX || u.sched_bytes > CB_SCHED_MAX ||
-        u.blob_bytes > 16u * CB_T_MAX + 4u * CB_RC_MAX + CB_SCHED_MAX ||
-        u.nbr > CB_NBR_MAX || u.nbr == 0) {
+    const bool bad = lanes ? (u.ntiles > CB_LANE_T_MAX || (u.work + 31) / 32 > 0xffffu ||
+                              u.nbr > CB_LANE_NBR_MAX || u.nbr == 0)
+                           : (u.nbytes > BMAX || u.ntiles > CB_T_MAX || u.rc_n > CB_RC_MAX ||
+                              u.sched_bytes > CB_SCHED_MAX ||
+                              u.blob_bytes > 16u * CB_T_MAX + 4u * CB_RC_MAX + CB_SCHED_MAX ||
+                              u.nbr > CB_NBR_MAX || u.nbr == 0);
+    if (bad) {
       *msg = "internal error: a unit exceeds the run kernel buffer limits";
       return CBSPMV_ERR_INVALID;
     }
@@ -779,7 +931,9 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
   std::vector<double> cost(nu);
   for (int64_t i = 0; i < nu; ++i) {
     const CbUnit& u = p.units[i];
-    cost[i] = (double)u.work + 8.0 * u.ntiles + 2.0 * CB_BLK * u.nbr + 64.0;
+    // lane-stream units: the FP64 FMA slots of the walk (32 per step) plus the gather
+    cost[i] = lanes ? 32.0 * ((u.work + 31) / 32) + 16.0 * u.ntiles + 2.0 * CB_BLK * u.nbr + 64.0
+                    : (double)u.work + 8.0 * u.ntiles + 2.0 * CB_BLK * u.nbr + 64.0;
   }
   std::vector<std::vector<uint32_t>> lists(n_workers);
   std::vector<double> load(n_workers, 0.0);
@@ -818,6 +972,11 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
     for (int64_t i = 0; i < nu; ++i) ordered[i] = p.units[p.worker_units[i]];
     p.units.swap(ordered);
   }
+  if (lanes) {
+    st = build_lane_programs(A, p, rowcnt, msg);
+    if (st != CBSPMV_OK) return st;
+    cb::ByteBuf().swap(p.stream);   // the record stream is not part of the lane-stream layout
+  }
 
   // --- statistics
   cbspmv_stats_t& s = p.stats;
@@ -839,9 +998,16 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
     mults += x.fmt == CB_FMT_DENSE ? 256 : x.nnz;
   }
   s.restore_cols_len = p.restore_cols_len;
-  s.stream_bytes = (int64_t)p.stream.size();
-  s.metadata_bytes = ntiles * (int64_t)sizeof(CbTile) + (int64_t)p.sched.size() * 4 +
-                     (int64_t)p.units.size() * (int64_t)sizeof(CbUnit);
+  if (lanes) {
+    s.stream_bytes = (int64_t)(p.lane_vals.size() + p.lane_words.size()) * 8;
+    s.metadata_bytes = ntiles * (int64_t)sizeof(CbTile) + (int64_t)p.lane_gcols.size() * 4 +
+                       (int64_t)p.lane_units.size() * (int64_t)sizeof(CbLaneUnit);
+  } else {
+    s.stream_bytes = (int64_t)p.stream.size();
+    s.metadata_bytes = ntiles * (int64_t)sizeof(CbTile) + (int64_t)p.sched.size() * 4 +
+                       (int64_t)p.units.size() * (int64_t)sizeof(CbUnit);
+  }
+  s.lane_layout = lanes ? 1 : 0;
   s.model_bytes_cb = ntiles * 21 + A.nnz * 9;
   s.model_bytes_csr = (A.m + 1) * 4 + A.nnz * 12;
   s.model_bytes_bsr16 = 2048 * ntiles + (nbr + 1) * 4 + 4 * ntiles;
@@ -991,6 +1157,68 @@ cbspmv_status_t decode_to_csr(int64_t m, int64_t n, int dtype, bool aggregated,
   for (int64_t r = 0; r < m; ++r)
     for (int64_t k = row_ptr[r] + 1; k < row_ptr[r + 1]; ++k)
       if (col[k] <= col[k - 1]) { *msg = "blocked layout decodes to unsorted rows"; return CBSPMV_ERR_INVALID; }
+  return CBSPMV_OK;
+}
+
+cbspmv_status_t decode_lanes_to_csr(int64_t m, int64_t n, const std::vector<CbLaneUnit>& units,
+                                    const double* vals, size_t nvals, const uint64_t* words, size_t nwords,
+                                    const int32_t* gcols, size_t ngcols, int64_t* row_ptr, int32_t* col,
+                                    double* val, int64_t nnz_expected, std::string* msg) {
+  // every entry once: (global row, column, value), counted per row first
+  std::vector<int64_t> cnt((size_t)m + 1, 0);
+  auto for_each = [&](const std::function<bool(int64_t, int32_t, double)>& f) -> bool {
+    for (const CbLaneUnit& u : units) {
+      const size_t v0 = (size_t)u.vals * CB_VLANES, w0 = (size_t)u.words * CB_VLANES;
+      if (v0 + (size_t)u.steps * CB_VLANES > nvals || w0 + (size_t)((u.steps + 3) / 4) * CB_VLANES > nwords ||
+          (size_t)u.gcols + u.nslots > ngcols)
+        return false;
+      for (uint32_t s = 0; s < u.steps; ++s)
+        for (uint32_t l = 0; l < CB_VLANES; ++l) {
+          const uint32_t w = (uint32_t)(words[w0 + (s / 4) * CB_VLANES + l] >> (16 * (s % 4))) & 0xffffu;
+          if (w == CB_LANE_NONE) continue;
+          const uint32_t slot = w & 511u, r = w >> 9;
+          if (slot >= u.nslots || r >= u.nrows) return false;
+          const int32_t c = gcols[u.gcols + slot];
+          const int64_t row = (int64_t)u.brow_lo * CB_BLK + r;
+          if (c < 0 || c >= n || row >= m) return false;
+          if (!f(row, c, vals[v0 + (size_t)s * CB_VLANES + l])) return false;
+        }
+    }
+    return true;
+  };
+  int64_t total = 0;
+  if (!for_each([&](int64_t r, int32_t, double) { cnt[(size_t)r + 1]++; ++total; return true; }) ||
+      total != nnz_expected) {
+    *msg = "lane stream is inconsistent with the matrix";
+    return CBSPMV_ERR_INVALID;
+  }
+  for (int64_t r = 0; r < m; ++r) cnt[(size_t)r + 1] += cnt[(size_t)r];
+  for (int64_t r = 0; r <= m; ++r) row_ptr[r] = cnt[(size_t)r];
+  std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+  std::vector<std::pair<int32_t, double>> tmp;
+  for_each([&](int64_t r, int32_t c, double v) {
+    const int64_t k = fill[(size_t)r]++;
+    col[k] = c;
+    val[k] = v;
+    return true;
+  });
+  // entries of a row come from its units in worker order: sort each row by column
+  for (int64_t r = 0; r < m; ++r) {
+    const int64_t a = row_ptr[r], b = row_ptr[r + 1];
+    tmp.resize((size_t)(b - a));
+    for (int64_t k = a; k < b; ++k) tmp[(size_t)(k - a)] = {col[k], val[k]};
+    std::sort(tmp.begin(), tmp.end(), [](const std::pair<int32_t, double>& x, const std::pair<int32_t, double>& y) {
+      return x.first < y.first;
+    });
+    for (int64_t k = a; k < b; ++k) {
+      col[k] = tmp[(size_t)(k - a)].first;
+      val[k] = tmp[(size_t)(k - a)].second;
+      if (k > a && col[k] == col[k - 1]) {
+        *msg = "lane stream holds an entry twice";
+        return CBSPMV_ERR_INVALID;
+      }
+    }
+  }
   return CBSPMV_OK;
 }
 

@@ -81,6 +81,12 @@ struct cbspmv_handle_s {
   void* d_partial_multi = nullptr;   // partial sums of 4-vector passes (allocated on first use)
   uint32_t* d_vslot = nullptr;       // value slot per CSR entry (keep_value_map)
   double* d_valstage = nullptr;      // staging of host values for cbspmv_update_values
+  // lane-stream layout (FP64 values)
+  CbLaneUnit* d_lunits = nullptr;
+  double* d_lvals = nullptr;
+  uint64_t* d_lwords = nullptr;
+  int32_t* d_lgcols = nullptr;
+  size_t lvals_count = 0, lwords_count = 0, lgcols_count = 0;
   // bytes of one x or y element: double for FP64 values, float for the reduced types
   size_t esize() const { return plan.value_dtype == CBSPMV_F64 ? 8 : 4; }
 
@@ -89,7 +95,8 @@ struct cbspmv_handle_s {
     DeviceGuard g(device);
     cudaDeviceSynchronize();
     void* ptrs[] = {d_stream, d_tiles, d_rcols, d_units, d_blob, d_wunits, d_woff, d_partial, d_split_rows,
-                    d_err, d_xstage, d_ystage, d_partial_multi, d_vslot, d_valstage};
+                    d_err, d_xstage, d_ystage, d_partial_multi, d_vslot, d_valstage,
+                    d_lunits, d_lvals, d_lwords, d_lgcols};
     for (void* p : ptrs)
       if (p) cudaFree(p);
     d_stream = nullptr;
@@ -107,6 +114,10 @@ struct cbspmv_handle_s {
     d_partial_multi = nullptr;
     d_vslot = nullptr;
     d_valstage = nullptr;
+    d_lunits = nullptr;
+    d_lvals = nullptr;
+    d_lwords = nullptr;
+    d_lgcols = nullptr;
   }
 };
 
@@ -216,11 +227,21 @@ cbspmv_status_t cbspmv_analyze(const cbspmv_csr_t* A, const cbspmv_opts_t* opts_
   h->stream_bytes = p.stream.size();
   cudaError_t e = cudaSuccess;
   auto step = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
-  step(upload(&h->d_stream, p.stream.data(), p.stream.size(), s));
-  step(upload(&h->d_tiles, p.tiles.data(), p.tiles.size(), s));
-  step(upload(&h->d_rcols, p.restore_cols.data(), p.restore_cols.size(), s));
-  step(upload(&h->d_units, p.units.data(), p.units.size(), s));
-  step(upload(&h->d_blob, p.blob.data(), p.blob.size(), s));
+  if (p.lanes) {
+    step(upload(&h->d_lunits, p.lane_units.data(), p.lane_units.size(), s));
+    step(upload(&h->d_lvals, p.lane_vals.data(), p.lane_vals.size(), s));
+    step(upload(&h->d_lwords, p.lane_words.data(), p.lane_words.size(), s));
+    step(upload(&h->d_lgcols, p.lane_gcols.data(), p.lane_gcols.size(), s));
+    h->lvals_count = p.lane_vals.size();
+    h->lwords_count = p.lane_words.size();
+    h->lgcols_count = p.lane_gcols.size();
+  } else {
+    step(upload(&h->d_stream, p.stream.data(), p.stream.size(), s));
+    step(upload(&h->d_tiles, p.tiles.data(), p.tiles.size(), s));
+    step(upload(&h->d_rcols, p.restore_cols.data(), p.restore_cols.size(), s));
+    step(upload(&h->d_units, p.units.data(), p.units.size(), s));
+    step(upload(&h->d_blob, p.blob.data(), p.blob.size(), s));
+  }
   step(upload(&h->d_wunits, p.worker_units.data(), p.worker_units.size(), s));
   step(upload(&h->d_woff, p.worker_off.data(), p.worker_off.size(), s));
   if (e == cudaSuccess) e = cudaMalloc(&h->d_partial, (size_t)(p.n_slots ? p.n_slots : 1) * 16 * h->esize());
@@ -235,9 +256,13 @@ cbspmv_status_t cbspmv_analyze(const cbspmv_csr_t* A, const cbspmv_opts_t* opts_
     return fail(e == cudaErrorMemoryAllocation ? CBSPMV_ERR_OOM : CBSPMV_ERR_CUDA, "upload failed: %s",
                 cudaGetErrorString(e));
   }
-  // the packed stream and the value map now live on the device; export reads it back
+  // the packed stream (or the lane stream) and the value map now live on the device;
+  // export reads them back
   cb::ByteBuf().swap(p.stream);
   std::vector<uint32_t>().swap(p.value_slot);
+  decltype(p.lane_vals)().swap(p.lane_vals);
+  decltype(p.lane_words)().swap(p.lane_words);
+  decltype(p.lane_gcols)().swap(p.lane_gcols);
   *out = h;
   return ok();
 }
@@ -270,6 +295,11 @@ static cb::RunArgs run_args(cbspmv_handle_t h, const void* x, void* y, double al
   a.nvec = 1;
   a.ldx = p.n;
   a.ldy = p.m;
+  a.lanes = p.lanes ? 1 : 0;
+  a.lunits = h->d_lunits;
+  a.lvals = h->d_lvals;
+  a.lwords = h->d_lwords;
+  a.lgcols = h->d_lgcols;
   return a;
 }
 
@@ -494,7 +524,8 @@ cbspmv_status_t cbspmv_update_values(cbspmv_handle_t h, const double* val, int o
     CB_CUDA(cudaMemcpyAsync(h->d_valstage, val, (size_t)p.nnz * 8, cudaMemcpyHostToDevice, s));
     dval = h->d_valstage;
   }
-  CB_CUDA(cb::launch_repack(h->d_stream, h->d_vslot, dval, p.nnz, p.value_dtype, h->grid, s));
+  uint8_t* dst = p.lanes ? reinterpret_cast<uint8_t*>(h->d_lvals) : h->d_stream;
+  CB_CUDA(cb::launch_repack(dst, h->d_vslot, dval, p.nnz, p.value_dtype, h->grid, s));
   return ok();
 }
 
@@ -520,7 +551,24 @@ cbspmv_status_t cbspmv_export_csr(cbspmv_handle_t h, int64_t* row_ptr, int32_t* 
   if (!row_ptr || (p.nnz && (!col_idx || !val))) return fail(CBSPMV_ERR_INVALID, "NULL output array");
   std::string msg;
   cbspmv_status_t st;
-  if (h->device < 0) {
+  if (p.lanes && h->device < 0) {
+    st = cb::decode_lanes_to_csr(p.m, p.n, p.lane_units, p.lane_vals.data(), p.lane_vals.size(), p.lane_words.data(),
+                                 p.lane_words.size(), p.lane_gcols.data(), p.lane_gcols.size(), row_ptr, col_idx, val,
+                                 p.nnz, &msg);
+  } else if (p.lanes) {
+    // read the device-resident lane stream back and decode it
+    DeviceGuard g(h->device);
+    CB_CUDA(g.err);
+    std::vector<double> vals(h->lvals_count);
+    std::vector<uint64_t> words(h->lwords_count);
+    std::vector<int32_t> gcols(h->lgcols_count);
+    CB_CUDA(cudaDeviceSynchronize());
+    if (!vals.empty()) CB_CUDA(cudaMemcpy(vals.data(), h->d_lvals, vals.size() * 8, cudaMemcpyDeviceToHost));
+    if (!words.empty()) CB_CUDA(cudaMemcpy(words.data(), h->d_lwords, words.size() * 8, cudaMemcpyDeviceToHost));
+    if (!gcols.empty()) CB_CUDA(cudaMemcpy(gcols.data(), h->d_lgcols, gcols.size() * 4, cudaMemcpyDeviceToHost));
+    st = cb::decode_lanes_to_csr(p.m, p.n, p.lane_units, vals.data(), vals.size(), words.data(), words.size(),
+                                 gcols.data(), gcols.size(), row_ptr, col_idx, val, p.nnz, &msg);
+  } else if (h->device < 0) {
     st = cb::decode_to_csr(p.m, p.n, p.value_dtype, p.aggregated, p.tiles, p.units, p.blob.data(), p.blob.size(),
                            p.stream.data(), p.stream.size(), p.restore_cols.data(), p.restore_cols.size(), row_ptr,
                            col_idx, val, p.nnz, &msg);
@@ -765,7 +813,7 @@ const char* cbspmv_last_error(void) { return g_err.c_str(); }
 
 // The run-kernel revision changes whenever the kernel's code changes (measurements taken
 // with a profiler are tied to it).
-const char* cbspmv_version(void) { return "cbspmv 0.3 (sm_103a; run kernel rev 13)"; }
+const char* cbspmv_version(void) { return "cbspmv 0.4 (sm_103a; run kernel rev 14)"; }
 
 }  // extern "C"
 
@@ -806,10 +854,20 @@ bool noalloc_view(cbspmv_handle_t h, NoallocView* v) {
   a.nvec = 1;
   a.ldx = h->plan.n;
   a.ldy = h->plan.m;
+  a.lanes = h->plan.lanes ? 1 : 0;
+  a.lunits = h->d_lunits;
+  a.lvals = h->d_lvals;
+  a.lwords = h->d_lwords;
+  a.lgcols = h->d_lgcols;
   v->args = a;
   return true;
 }
 
 void set_last_error(const std::string& msg) { g_err = msg; }
+
+cbspmv_status_t check_product_args(cbspmv_handle_t h, const void* x, const void* y) {
+  const bool v = valid_handle(h);
+  return check_run_args(h, 1, x, v ? h->plan.n : 0, y, v ? h->plan.m : 0);
+}
 
 }  // namespace cb

@@ -32,6 +32,12 @@ struct RunArgs {
   int value_dtype;              // cbspmv_dtype_t of the stored values
   int nvec;                     // vectors computed in one pass: 1, 2 or 4 (single product only)
   int64_t ldx, ldy;             // distance in elements between consecutive vectors of x and y
+  // lane-stream layout (FP64; lanes = 1): these replace stream, units and blob
+  int lanes;
+  const CbLaneUnit* lunits;     // units in worker order
+  const double* lvals;          // values, steps x 32 per unit
+  const uint64_t* lwords;       // entry words, 4 per uint64
+  const int32_t* lgcols;        // gather lists
 };
 
 size_t spmv_smem_bytes();      // dynamic shared memory of the largest instantiation

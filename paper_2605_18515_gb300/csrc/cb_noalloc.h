@@ -18,5 +18,8 @@ struct NoallocView {
 bool noalloc_view(cbspmv_handle_t h, NoallocView* v);
 // Sets the calling thread's message returned by cbspmv_last_error().
 void set_last_error(const std::string& msg);
+// The argument checks of cbspmv_run (valid device handle, x and y present, aligned to their
+// element size and not overlapping); sets the message and returns the status on failure.
+cbspmv_status_t check_product_args(cbspmv_handle_t h, const void* x, const void* y);
 }  // namespace cb
 #endif

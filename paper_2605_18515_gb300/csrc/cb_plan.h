@@ -62,6 +62,15 @@ struct Plan {
   int64_t fma_slots = 0;               // FMA slots the walks of all units issue (one vector)
   int n_slots = 0;
 
+  // Lane-stream layout (FP64 values; see cb_layout.h): replaces the record stream, the lane
+  // schedules and the unit blobs on the device. lane_units are in worker order like units;
+  // the three arrays are host copies, released once uploaded to a device.
+  bool lanes = false;
+  std::vector<CbLaneUnit> lane_units;
+  std::vector<double, NoInitAlloc<double>> lane_vals;
+  std::vector<uint64_t, NoInitAlloc<uint64_t>> lane_words;
+  std::vector<int32_t, NoInitAlloc<int32_t>> lane_gcols;
+
   cbspmv_stats_t stats{};
 };
 
@@ -81,6 +90,13 @@ cbspmv_status_t decode_to_csr(int64_t m, int64_t n, int value_dtype, bool aggreg
                               size_t stream_size, const int32_t* restore_cols,
                               size_t restore_len, int64_t* row_ptr, int32_t* col, double* val,
                               int64_t nnz_expected, std::string* msg);
+
+// Rebuilds CSR from the lane-stream layout (host arrays: the units in worker order and
+// their values, entry words and gather lists, as described in cb_layout.h).
+cbspmv_status_t decode_lanes_to_csr(int64_t m, int64_t n, const std::vector<CbLaneUnit>& units,
+                                    const double* vals, size_t nvals, const uint64_t* words, size_t nwords,
+                                    const int32_t* gcols, size_t ngcols, int64_t* row_ptr, int32_t* col,
+                                    double* val, int64_t nnz_expected, std::string* msg);
 
 }  // namespace cb
 #endif

@@ -47,6 +47,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+#include <vector>
+
 #include "cb_layout.h"
 #include "cb_kernels.h"
 #include "cb_round.h"
@@ -853,21 +856,425 @@ __global__ void __launch_bounds__(256) combine_wide_kernel(const __grid_constant
   }
 }
 
+// ---- lane-stream run kernel (FP64 values, layout in cb_layout.h) -------------------------
+// Persistent grid, one CTA per SM; every warp is an independent worker that takes its CTA's
+// units by ticket, like the record kernel. Per unit a warp
+//   * gathers the unit's x values (16 per sub-block, through restore_cols when aggregated:
+//     the x preload of Algorithms 3/4) into one of its two x buffers with cp.async, one unit
+//     ahead, so the gather of the next unit overlaps the walk of this one;
+//   * walks its lane runs: each step is one coalesced 8-byte value load per lane, one 16-bit
+//     entry word (x slot and row) and one FP64 FMA into the lane's row accumulator; values
+//     and words are loaded a group of 8 steps ahead into registers (the next unit's first
+//     group while the last group of this unit is computed), so the FMA chain never waits on
+//     memory and no shared-memory staging of the matrix is needed;
+//   * finishes rows that cross lane runs: the lane where a row ends adds the partial sums of
+//     the lanes before it in lane order (a segmented scan when a row spans many lanes), and
+//     writes y once per row (block rows cut into parts: 16 partial sums per part, added by
+//     the combine kernel in part order). Results do not depend on scheduling.
+#ifndef CB_LANE_WARPS
+#define CB_LANE_WARPS 20       // worker warps per SM (measured on the FEM band: 16 -> 20 -> 24)
+#endif
+template <int kK>
+struct LaneGeom {
+  static constexpr uint32_t kSlot = 8u * kK;                        // bytes of one x slot
+  static constexpr uint32_t kXBuf = CB_LANE_SLOTS * kSlot;          // one x buffer
+  static constexpr uint32_t kOffRow = 2 * kXBuf;                    // row sums, CB_R_MAX x kK
+  static constexpr uint32_t kOffCv = kOffRow + CB_R_MAX * 8u * kK;  // carry values, 32 x kK
+  static constexpr uint32_t kOffCr = kOffCv + CB_VLANES * 8u * kK;  // carry rows, 32
+  static constexpr uint32_t kWarpBytes = align128(kOffCr + 4u * CB_VLANES);
+  static constexpr uint32_t kFit = (kSmemMax - kHeaderBytes) / kWarpBytes;
+  static constexpr int kWarps = kFit < (uint32_t)CB_LANE_WARPS ? (int)kFit : CB_LANE_WARPS;
+  static constexpr uint32_t kSmem = kHeaderBytes + kWarps * kWarpBytes;
+  static_assert(kWarps >= 4, "lane kernel warp buffers too large");
+};
+constexpr int kLaneGroup = 8;   // steps per prefetch group (two words of four entries)
+
+__device__ __forceinline__ double ldg_stream_f64(const double* p) {
+  double v;
+  asm volatile("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ uint64_t ldg_stream_u64(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.global.nc.L1::no_allocate.u64 %0, [%1];" : "=l"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+template <int kMaxP, int kK>
+__global__ void __launch_bounds__(32 * LaneGeom<kK>::kWarps, 1)
+    spmv_lanes_kernel(const __grid_constant__ BatchArgs<kMaxP> b) {
+  using G = LaneGeom<kK>;
+  constexpr uint32_t kFull = 0xffffffffu;
+  constexpr uint32_t kNone = 0xffffffffu;
+  extern __shared__ __align__(128) uint8_t smem_raw[];
+  CtaHeader& hd = *reinterpret_cast<CtaHeader*>(smem_raw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint8_t* W = smem_raw + kHeaderBytes + (uint32_t)warp * G::kWarpBytes;
+  const uint32_t w_smem = smem_u32(W);
+  double* srow = reinterpret_cast<double*>(W + G::kOffRow);
+  double* cval = reinterpret_cast<double*>(W + G::kOffCv);
+  int32_t* crow = reinterpret_cast<int32_t*>(W + G::kOffCr);
+  const int P = b.count;
+  if ((int)threadIdx.x < P) {
+    const RunArgs& a = b.p[threadIdx.x];
+    const uint32_t w0 = a.worker_off[blockIdx.x];
+    hd.first[threadIdx.x] = w0;
+    hd.pref[threadIdx.x + 1] = a.worker_off[blockIdx.x + 1] - w0;
+  }
+  if (threadIdx.x == 0) hd.ticket = 0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    hd.pref[0] = 0;
+    for (int q = 0; q < P; ++q) hd.pref[q + 1] += hd.pref[q];
+  }
+  __syncthreads();
+  const uint32_t total = hd.pref[P];
+  auto grab = [&]() -> uint32_t {
+    uint32_t t = 0;
+    if (lane == 0) t = atomicAdd(&hd.ticket, 1u);
+    return __shfl_sync(kFull, t, 0);
+  };
+  auto problem_of = [&](uint32_t t) -> int {
+    if (kMaxP == 1) return 0;
+    int lo = 0, hi = P - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (hd.pref[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+  };
+  // the 32-byte descriptor of ticket t (every lane loads it: one broadcast request)
+  auto fetch = [&](uint32_t t, int& q, CbLaneUnit& u) {
+    q = problem_of(t);
+    const uint4* d = reinterpret_cast<const uint4*>(b.p[q].lunits + hd.first[q] + (t - hd.pref[q]));
+    const uint4 d0 = __ldg(d), d1 = __ldg(d + 1);
+    u.vals = d0.x; u.words = d0.y; u.gcols = d0.z; u.brow_lo = d0.w;
+    u.steps = (uint16_t)(d1.x & 0xffffu); u.nslots = (uint16_t)(d1.x >> 16);
+    u.nrows = (uint16_t)(d1.y & 0xffffu); u.flags = (uint16_t)(d1.y >> 16);
+    u.slot = d1.z; u.pad = 0;
+  };
+  // cp.async of the unit's x values into buffer `buf`: slot k gets x[gcols[k]] (kK vectors
+  // side by side); slots outside [0, n) read zero
+  auto gather = [&](int q, const CbLaneUnit& u, uint32_t buf) {
+    constexpr int kPer = CB_LANE_SLOTS / 32;
+    const RunArgs& a = b.p[q];
+    const double* x = static_cast<const double*>(a.x);
+    const int32_t* gc = a.lgcols + u.gcols;
+    int32_t c[kPer];
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const uint32_t k = (uint32_t)lane + 32u * i;
+      c[i] = k < u.nslots ? __ldg(gc + k) : -1;
+    }
+    const uint32_t dst = w_smem + buf * G::kXBuf;
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const uint32_t k = (uint32_t)lane + 32u * i;
+      if (k < u.nslots) {
+        const bool ok = c[i] >= 0 && (int64_t)c[i] < a.n;
+#pragma unroll
+        for (int j = 0; j < kK; ++j)
+          cp_async_elem<8>(dst + G::kSlot * k + 8u * j, x + (ok ? (int64_t)c[i] + j * a.ldx : 0), ok ? 8u : 0u);
+      }
+    }
+  };
+  // values and entry words of steps 8g .. 8g + 7 of this lane (absent steps: 0.0, no entry)
+  auto load_group = [&](int q, const CbLaneUnit& u, uint32_t g, double (&v)[kLaneGroup], uint64_t& w0,
+                        uint64_t& w1) {
+    const RunArgs& a = b.p[q];
+    const double* vp = a.lvals + ((size_t)u.vals + kLaneGroup * g) * CB_VLANES + lane;
+    const uint64_t* wp = a.lwords + ((size_t)u.words + 2u * g) * CB_VLANES + lane;
+    const uint32_t S = u.steps, Q = (S + 3u) / 4u;
+#pragma unroll
+    for (int j = 0; j < kLaneGroup; ++j) v[j] = (kLaneGroup * g + j < S) ? ldg_stream_f64(vp + CB_VLANES * j) : 0.0;
+    w0 = (2u * g < Q) ? ldg_stream_u64(wp) : ~0ull;
+    w1 = (2u * g + 1u < Q) ? ldg_stream_u64(wp + CB_VLANES) : ~0ull;
+  };
+
+  uint32_t t = grab();
+  if (t >= total) return;
+  int q = 0, qn = 0;
+  CbLaneUnit u, un{};
+  fetch(t, q, u);
+  gather(q, u, 0);
+  cp_async_commit();
+  double cv[kLaneGroup], nv[kLaneGroup];
+  uint64_t cw0, cw1, nw0 = ~0ull, nw1 = ~0ull;
+  load_group(q, u, 0, cv, cw0, cw1);
+  uint32_t tn = grab();
+  if (tn < total) fetch(tn, qn, un);
+  uint32_t buf = 0;
+  for (;;) {
+    if (tn < total) gather(qn, un, buf ^ 1u);   // the next unit's x, during this unit's walk
+    cp_async_commit();
+    const uint32_t tnn = grab();
+    int qnn = 0;
+    CbLaneUnit unn{};
+    if (tnn < total) fetch(tnn, qnn, unn);
+    const RunArgs& a = b.p[q];
+    const uint32_t R = u.nrows;
+    for (uint32_t r = lane; r < R * kK; r += 32) srow[r] = 0.0;
+    cp_async_wait_one();                       // this unit's x values have landed
+    __syncwarp();
+    const uint8_t* xs = W + buf * G::kXBuf;
+
+    // walk
+    double acc[kK], head[kK];
+#pragma unroll
+    for (int j = 0; j < kK; ++j) acc[j] = head[j] = 0.0;
+    uint32_t cur = kNone, first_row = kNone;
+    bool have_head = false;
+    const uint32_t ngroups = (u.steps + kLaneGroup - 1u) / kLaneGroup;
+    for (uint32_t g = 0; g < ngroups; ++g) {
+      if (g + 1 < ngroups) load_group(q, u, g + 1, nv, nw0, nw1);
+      else if (tn < total) load_group(qn, un, 0, nv, nw0, nw1);
+      double xv[kLaneGroup][kK];
+#pragma unroll
+      for (int j = 0; j < kLaneGroup; ++j) {
+        const uint32_t w = (uint32_t)((j < 4 ? cw0 : cw1) >> (16 * (j & 3))) & 0xffffu;
+        const uint32_t slot = w == CB_LANE_NONE ? 0u : (w & 511u);
+        if constexpr (kK == 1) {
+          xv[j][0] = *reinterpret_cast<const double*>(xs + 8u * slot);
+        } else {
+#pragma unroll
+          for (int h = 0; h < kK / 2; ++h) {
+            const double2 d2 = *reinterpret_cast<const double2*>(xs + G::kSlot * slot + 16u * h);
+            xv[j][2 * h] = d2.x;
+            xv[j][2 * h + 1] = d2.y;
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kLaneGroup; ++j) {
+        const uint32_t w = (uint32_t)((j < 4 ? cw0 : cw1) >> (16 * (j & 3))) & 0xffffu;
+        if (w != CB_LANE_NONE) {
+          const uint32_t r = w >> 9;
+          if (r != cur) {
+            if (cur == kNone) {
+              first_row = r;
+            } else if (!have_head) {
+#pragma unroll
+              for (int h = 0; h < kK; ++h) head[h] = acc[h];
+              have_head = true;
+            } else {
+#pragma unroll
+              for (int h = 0; h < kK; ++h) srow[cur * kK + h] = acc[h];
+            }
+#pragma unroll
+            for (int h = 0; h < kK; ++h) acc[h] = 0.0;
+            cur = r;
+          }
+#pragma unroll
+          for (int h = 0; h < kK; ++h) acc[h] = fma(cv[j], xv[j][h], acc[h]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kLaneGroup; ++j) cv[j] = nv[j];
+      cw0 = nw0;
+      cw1 = nw1;
+    }
+    if (ngroups == 0) {        // (no entries: never produced by the analysis) keep the prefetch in step
+      if (tn < total) load_group(qn, un, 0, cv, cw0, cw1);
+    }
+
+    // rows that cross lane runs: neighbours are the nearest lanes with entries
+    const bool nonempty = cur != kNone;
+    int prev = nonempty ? lane : -1, next = nonempty ? lane : 32;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int o = __shfl_up_sync(kFull, prev, d);
+      if (lane >= d && o > prev) prev = o;
+      const int p2 = __shfl_down_sync(kFull, next, d);
+      if (lane + d < 32 && p2 < next) next = p2;
+    }
+    int prev_ne = __shfl_up_sync(kFull, prev, 1);
+    int next_ne = __shfl_down_sync(kFull, next, 1);
+    if (lane == 0) prev_ne = -1;
+    if (lane == 31) next_ne = 32;
+    const int32_t my_first = nonempty ? (int32_t)first_row : -1, my_last = nonempty ? (int32_t)cur : -1;
+    const int32_t prev_last = __shfl_sync(kFull, my_last, prev_ne < 0 ? 0 : prev_ne);
+    const int32_t next_first = __shfl_sync(kFull, my_first, next_ne > 31 ? 0 : next_ne);
+    const bool hs = nonempty && prev_ne >= 0 && prev_last == my_first;     // first row began earlier
+    const bool open = nonempty && next_ne <= 31 && next_first == my_last;  // last row continues
+    int32_t own_row = -1, carry_row = -1;
+    double own_val[kK], carry_val[kK];
+#pragma unroll
+    for (int h = 0; h < kK; ++h) own_val[h] = carry_val[h] = 0.0;
+    if (nonempty) {
+      if (have_head) {           // two or more rows in this run
+        if (hs) {
+          own_row = my_first;
+#pragma unroll
+          for (int h = 0; h < kK; ++h) own_val[h] = head[h];
+        } else {
+#pragma unroll
+          for (int h = 0; h < kK; ++h) srow[my_first * kK + h] = head[h];
+        }
+        if (open) {
+          carry_row = my_last;
+#pragma unroll
+          for (int h = 0; h < kK; ++h) carry_val[h] = acc[h];
+        } else {
+#pragma unroll
+          for (int h = 0; h < kK; ++h) srow[my_last * kK + h] = acc[h];
+        }
+      } else if (open) {         // one row that continues (begun here or earlier)
+        carry_row = my_last;
+#pragma unroll
+        for (int h = 0; h < kK; ++h) carry_val[h] = acc[h];
+      } else if (hs) {           // one row begun earlier that ends here
+        own_row = my_first;
+#pragma unroll
+        for (int h = 0; h < kK; ++h) own_val[h] = acc[h];
+      } else {
+#pragma unroll
+        for (int h = 0; h < kK; ++h) srow[my_last * kK + h] = acc[h];
+      }
+    }
+    if (!(u.flags & CB_LUNIT_SCAN)) {
+      crow[lane] = nonempty ? carry_row : -2;
+#pragma unroll
+      for (int h = 0; h < kK; ++h) cval[lane * kK + h] = carry_val[h];
+      __syncwarp();
+      if (own_row >= 0) {
+        double sum[kK];
+#pragma unroll
+        for (int h = 0; h < kK; ++h) sum[h] = own_val[h];
+        for (int l = lane - 1; l >= 0; --l) {
+          const int32_t cr = crow[l];
+          if (cr == -2) continue;
+          if (cr != own_row) break;
+#pragma unroll
+          for (int h = 0; h < kK; ++h) sum[h] += cval[l * kK + h];
+        }
+#pragma unroll
+        for (int h = 0; h < kK; ++h) srow[own_row * kK + h] = sum[h];
+      }
+    } else {
+      // segmented inclusive scan of the carries over lanes, keyed by the carried row; lanes
+      // without entries take the key of the nearest lane with entries before them
+      const int32_t key0 = nonempty ? carry_row : -2;
+      const int32_t key = __shfl_sync(kFull, key0, prev < 0 ? lane : prev);
+      double c2[kK];
+#pragma unroll
+      for (int h = 0; h < kK; ++h) c2[h] = carry_val[h];
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int32_t ko = __shfl_up_sync(kFull, key, d);
+        const bool take = lane >= d && ko == key;
+#pragma unroll
+        for (int h = 0; h < kK; ++h) {
+          const double vo = __shfl_up_sync(kFull, c2[h], d);
+          if (take) c2[h] += vo;
+        }
+      }
+      const int32_t kprev = __shfl_up_sync(kFull, key, 1);
+#pragma unroll
+      for (int h = 0; h < kK; ++h) {
+        const double pv = __shfl_up_sync(kFull, c2[h], 1);
+        if (own_row >= 0) srow[own_row * kK + h] = own_val[h] + (lane > 0 && kprev == own_row ? pv : 0.0);
+      }
+    }
+    __syncwarp();
+
+    // outputs
+    if (u.slot == 0xffffffffu) {
+      double* y = static_cast<double*>(a.y);
+      const int64_t row0 = (int64_t)u.brow_lo * CB_BLK;
+      for (uint32_t r = lane; r < R; r += 32) {
+#pragma unroll
+        for (int h = 0; h < kK; ++h) {
+          double* yh = y + (int64_t)h * a.ldy + row0 + r;
+          double v = srow[r * kK + h];
+          if (!a.alpha_one) v = a.alpha * v;
+          if (a.beta_nonzero) v = fma(a.beta, *yh, v);
+          *yh = v;
+        }
+      }
+    } else {
+      double* partial = static_cast<double*>(a.partial);
+      if (lane < 16) {
+#pragma unroll
+        for (int h = 0; h < kK; ++h)
+          partial[((size_t)u.slot * 16 + lane) * kK + h] = (uint32_t)lane < R ? srow[lane * kK + h] : 0.0;
+      }
+    }
+    __syncwarp();
+    if (tn >= total) break;
+    t = tn; q = qn; u = un;
+    tn = tnn; qn = qnn; un = unn;
+    buf ^= 1u;
+  }
+  cp_async_wait_all();
+}
+
 // Raises the run kernel's dynamic shared-memory limit on the current device (once per
 // device and instantiation).
+// The flags are atomics: the server's engine thread and user threads launch concurrently.
+// Two threads that both see a flag unset both set the (idempotent) attribute.
 template <class V, int kMaxP, int kK>
 cudaError_t configure_typed() {
-  static bool configured[64] = {false};
+  static std::atomic<bool> configured[64];
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 64 || !configured[dev]) {
+  if (dev < 0 || dev >= 64 || !configured[dev].load(std::memory_order_acquire)) {
     e = cudaFuncSetAttribute(spmv_kernel<V, kMaxP, kK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)Geom<V, kK>::kSmem);
     if (e != cudaSuccess) return e;
-    if (dev >= 0 && dev < 64) configured[dev] = true;
+    if (dev >= 0 && dev < 64) configured[dev].store(true, std::memory_order_release);
   }
   return cudaSuccess;
+}
+
+template <int kMaxP, int kK>
+cudaError_t configure_lanes() {
+  static std::atomic<bool> configured[64];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64 || !configured[dev].load(std::memory_order_acquire)) {
+    e = cudaFuncSetAttribute(spmv_lanes_kernel<kMaxP, kK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)LaneGeom<kK>::kSmem);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) configured[dev].store(true, std::memory_order_release);
+  }
+  return cudaSuccess;
+}
+
+// The kernels that add the parts of split block rows (after the run kernel, same stream).
+template <class Acc, int kMaxP, int kK>
+cudaError_t launch_combine(const BatchArgs<kMaxP>& b, cudaStream_t stream) {
+  cudaError_t e = cudaSuccess;
+  const uint32_t nsplit = b.split_base[b.count], nwide = b.wide_base[b.count];
+  if (nsplit) {
+    const uint32_t threads = 16u * nsplit;
+    combine_kernel<Acc, kMaxP, kK><<<(threads + 255) / 256, 256, 0, stream>>>(b);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (nwide) {
+    combine_wide_kernel<Acc, kMaxP, kK><<<nwide, 256, 0, stream>>>(b);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+template <int kMaxP, int kK>
+cudaError_t launch_lanes(const BatchArgs<kMaxP>& b, int grid, cudaStream_t stream, cudaEvent_t* ev) {
+  cudaError_t e = configure_lanes<kMaxP, kK>();
+  if (e != cudaSuccess) return e;
+  if (ev && (e = cudaEventRecord(ev[0], stream)) != cudaSuccess) return e;
+  spmv_lanes_kernel<kMaxP, kK><<<grid, 32 * LaneGeom<kK>::kWarps, LaneGeom<kK>::kSmem, stream>>>(b);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (ev && (e = cudaEventRecord(ev[1], stream)) != cudaSuccess) return e;
+  e = launch_combine<double, kMaxP, kK>(b, stream);
+  if (e != cudaSuccess) return e;
+  if (ev) e = cudaEventRecord(ev[2], stream);
+  return e;
 }
 
 template <class V, int kMaxP, int kK>
@@ -912,7 +1319,23 @@ cudaError_t launch_nvec(const BatchArgs<kMaxP>& b, int grid, cudaStream_t stream
 }
 
 template <int kMaxP>
+cudaError_t launch_lanes_nvec(const BatchArgs<kMaxP>& b, int grid, cudaStream_t stream, cudaEvent_t* ev) {
+  if constexpr (kMaxP == 1) {
+    switch (b.p[0].nvec) {
+      case 1: return launch_lanes<1, 1>(b, grid, stream, ev);
+      case 2: return launch_lanes<1, 2>(b, grid, stream, ev);
+      case 4: return launch_lanes<1, 4>(b, grid, stream, ev);
+      default: return cudaErrorInvalidValue;
+    }
+  } else {
+    return b.p[0].nvec == 1 ? launch_lanes<kMaxP, 1>(b, grid, stream, ev) : cudaErrorInvalidValue;
+  }
+}
+
+template <int kMaxP>
 cudaError_t launch_dispatch(const BatchArgs<kMaxP>& b, int grid, cudaStream_t stream, cudaEvent_t* ev) {
+  if (b.p[0].lanes) return b.p[0].value_dtype == CBSPMV_F64 ? launch_lanes_nvec<kMaxP>(b, grid, stream, ev)
+                                                            : cudaErrorInvalidValue;
   switch (b.p[0].value_dtype) {
     case CBSPMV_F64: return launch_nvec<double, kMaxP>(b, grid, stream, ev);
     case CBSPMV_F32: return launch_nvec<float, kMaxP>(b, grid, stream, ev);
@@ -950,8 +1373,12 @@ cudaError_t launch_repack(uint8_t* stream, const uint32_t* slot, const double* v
 }
 
 size_t spmv_smem_bytes() {
-  const uint32_t a = Geom<double>::kSmem, b = Geom<float>::kSmem, c = Geom<__half>::kSmem;
-  return a > b ? (a > c ? a : c) : (b > c ? b : c);
+  const uint32_t v[] = {Geom<double>::kSmem, Geom<float>::kSmem, Geom<__half>::kSmem, Geom<double, 4>::kSmem,
+                        Geom<float, 4>::kSmem, Geom<__half, 4>::kSmem, LaneGeom<1>::kSmem, LaneGeom<2>::kSmem,
+                        LaneGeom<4>::kSmem};
+  uint32_t m = 0;
+  for (uint32_t x : v) m = x > m ? x : m;
+  return m;
 }
 int spmv_warps(int value_dtype) {
   switch (value_dtype) {
@@ -971,7 +1398,11 @@ cudaError_t configure_value_type() {
 }
 
 cudaError_t configure_kernels() {
-  cudaError_t e = configure_value_type<double>();
+  cudaError_t e = configure_lanes<1, 1>();
+  if (e == cudaSuccess) e = configure_lanes<kMaxBatch, 1>();
+  if (e == cudaSuccess) e = configure_lanes<1, 2>();
+  if (e == cudaSuccess) e = configure_lanes<1, 4>();
+  if (e == cudaSuccess) e = configure_value_type<double>();
   if (e == cudaSuccess) e = configure_value_type<float>();
   if (e == cudaSuccess) e = configure_value_type<__nv_bfloat16>();
   if (e == cudaSuccess) e = configure_value_type<__half>();
@@ -992,6 +1423,14 @@ cudaError_t launch_spmv(const RunArgs& a, int grid, cudaStream_t stream, cudaEve
 cudaError_t launch_spmv_batch(const RunArgs* a, int count, int grid, cudaStream_t stream) {
   for (int i = 0; i < count; ++i)
     if (a[i].value_dtype != a[0].value_dtype || a[i].nvec != 1) return cudaErrorInvalidValue;
+  // one layout per launch: problems of the other layout go to launches of their own
+  for (int i = 1; i < count; ++i)
+    if (a[i].lanes != a[0].lanes) {
+      std::vector<RunArgs> l, r;
+      for (int k = 0; k < count; ++k) (a[k].lanes ? l : r).push_back(a[k]);
+      cudaError_t e = launch_spmv_batch(l.data(), (int)l.size(), grid, stream);
+      return e == cudaSuccess ? launch_spmv_batch(r.data(), (int)r.size(), grid, stream) : e;
+    }
   for (int base = 0; base < count; base += kMaxBatch) {
     const int c = count - base < kMaxBatch ? count - base : kMaxBatch;
     static thread_local BatchArgs<kMaxBatch> b;

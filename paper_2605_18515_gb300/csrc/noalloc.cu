@@ -55,15 +55,9 @@ extern "C" cbspmv_status_t cbspmv_run_noalloc(cbspmv_handle_t h, const void* x, 
     cb::set_last_error(buf);
     return CBSPMV_ERR_INVALID;
   }
-  if ((!x && p.n > 0) || (!y && p.m > 0)) {
-    cb::set_last_error("NULL x or y");
-    return CBSPMV_ERR_INVALID;
-  }
-  const uintptr_t es = p.value_dtype == CBSPMV_F64 ? 8 : 4;   // x, y element size
-  if (((uintptr_t)x & (es - 1)) || ((uintptr_t)y & (es - 1))) {
-    cb::set_last_error("x and y must be aligned to their element size");
-    return CBSPMV_ERR_INVALID;
-  }
+  // the checks of cbspmv_run: x and y present, aligned to their element size, not overlapping
+  const cbspmv_status_t chk = cb::check_product_args(h, x, y);
+  if (chk != CBSPMV_OK) return chk;
   int prev = -1;
   cudaError_t e = cudaGetDevice(&prev);
   if (e == cudaSuccess && prev != v.device) e = cudaSetDevice(v.device);

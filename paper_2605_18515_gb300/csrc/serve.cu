@@ -331,21 +331,35 @@ static int handle_slots(cbspmv_handle_t h) {
   return ns;
 }
 
+// Device workspace of one request of `kind` on matrix M (the layout admit_one carves out of
+// the arena): x and y for a product; x, r, b in FP64, the inner CG vectors and the block
+// partials for a solve; plus the partial sums of split block rows of each product.
+static size_t workspace_bytes(const Matrix& M, int kind, size_t es_in, int* nblk, size_t* part_hi_out,
+                              size_t* part_lo_out) {
+  const int64_t m = M.m, n = M.n;
+  const size_t part_hi = (size_t)std::max(handle_slots(M.hi), 1) * 16 * 8;
+  size_t part_lo = 0;
+  size_t need = 0;
+  *nblk = 0;
+  if (kind == CBSPMV_REQ_SPMV) {
+    need = align256(n * 8) + align256(m * 8) + align256(part_hi);
+  } else {
+    part_lo = (size_t)std::max(handle_slots(M.lo), 1) * 16 * es_in;
+    *nblk = (int)((n + kVecBlock - 1) / kVecBlock);
+    need = 3 * align256(n * 8) + 4 * align256(n * es_in) + align256(part_hi) + align256(part_lo) +
+           align256((size_t)std::max(*nblk, 1) * 8);
+  }
+  if (part_hi_out) *part_hi_out = part_hi;
+  if (part_lo_out) *part_lo_out = part_lo;
+  return need;
+}
+
 bool cbspmv_server_s::admit_one(const std::shared_ptr<Req>& r) {
   const Matrix& M = mats[r->q.matrix];
   const size_t es_in = (o.cg_inner_dtype == CBSPMV_F64) ? 8 : 4;
   const int64_t m = M.m, n = M.n;
-  size_t need = 0;
-  const size_t part_hi = (size_t)std::max(handle_slots(M.hi), 1) * 16 * 8;
-  size_t part_lo = 0;
-  if (r->q.kind == CBSPMV_REQ_SPMV) {
-    need = align256(n * 8) + align256(m * 8) + align256(part_hi);
-  } else {
-    part_lo = (size_t)std::max(handle_slots(M.lo), 1) * 16 * es_in;
-    r->nblk = (int)((n + kVecBlock - 1) / kVecBlock);
-    need = 3 * align256(n * 8) + 4 * align256(n * es_in) + align256(part_hi) + align256(part_lo) +
-           align256((size_t)std::max(r->nblk, 1) * 8);
-  }
+  size_t part_hi = 0, part_lo = 0;
+  const size_t need = workspace_bytes(M, r->q.kind, es_in, &r->nblk, &part_hi, &part_lo);
   int slot = -1;
   for (int s = 0; s < o.max_inflight && s < kMaxSlots; ++s)
     if (!slots_used[s]) { slot = s; break; }
@@ -707,6 +721,16 @@ cbspmv_status_t cbspmv_server_submit(cbspmv_server_t s, const cbspmv_request_t* 
     return sfail(CBSPMV_ERR_INVALID, "unknown request kind");
   }
   if (!s->engine_error.empty()) return sfail(CBSPMV_ERR_CUDA, "server stopped: %s", s->engine_error.c_str());
+  {
+    // a request that would not fit the whole memory budget could never be admitted and
+    // would hold every later request behind it in the arrival-order queue
+    const size_t es_in = (s->o.cg_inner_dtype == CBSPMV_F64) ? 8 : 4;
+    int nblk = 0;
+    const size_t need = workspace_bytes(M, q->kind, es_in, &nblk, nullptr, nullptr);
+    if (need > s->arena.capacity())
+      return sfail(CBSPMV_ERR_OOM, "request needs %zu bytes of workspace, the memory budget holds %zu", need,
+                   s->arena.capacity());
+  }
   auto r = std::make_shared<Req>();
   r->id = s->next_id++;
   r->q = *q;

@@ -63,10 +63,12 @@ SMALL = {
 
 @pytest.mark.parametrize("name", list(SMALL))
 @pytest.mark.parametrize("col_agg", [-1, 0, 1])
-def test_parity_small(env, name, col_agg):
+@pytest.mark.parametrize("layout", ["lanes", "records"])
+def test_parity_small(env, name, col_agg, layout):
     A = SMALL[name]()
     x = I.vector_x(A.n, 100)
-    y, st = gpu_spmv(env, A, x, col_agg=col_agg)
+    y, st = gpu_spmv(env, A, x, col_agg=col_agg, record_layout=layout == "records")
+    assert st["lane_layout"] == (layout == "lanes")
     check(A, x, y)
 
 
@@ -126,8 +128,9 @@ def test_format_boundaries(env, k):
     A = I.csr_from_coo(80, 128, np.concatenate(r), np.concatenate(c), I.uniform_pm1(3, 2, 40 * k))
     x = I.vector_x(A.n, 50)
     for agg in (0, 1):
-        y, st = gpu_spmv(env, A, x, col_agg=agg)
-        check(A, x, y)
+        for rec in (False, True):
+            y, st = gpu_spmv(env, A, x, col_agg=agg, record_layout=rec)
+            check(A, x, y)
 
 
 def test_empty_inputs(env):
@@ -163,14 +166,47 @@ def heavy_rows_matrix():
                           sum_duplicates=False)
 
 
-def test_split_block_rows_and_determinism(env):
+@pytest.mark.parametrize("layout", ["lanes", "records"])
+def test_split_block_rows_and_determinism(env, layout):
     A = heavy_rows_matrix()
     x = I.vector_x(A.n, 60)
-    ys, st = gpu_spmv(env, A, x, 1.5, 0.0, reps=3)
+    ys, st = gpu_spmv(env, A, x, 1.5, 0.0, reps=3, record_layout=layout == "records")
     assert st["n_split_rows"] >= 3
     for y in ys:
         check(A, x, y, 1.5)
     assert all(np.array_equal(ys[0], y) for y in ys[1:])    # no scheduling dependence
+
+
+def long_row_unit_matrix():
+    # one block row of 512 columns (32 sub-blocks: one lane-stream unit) whose row 3 is full
+    # (a row across every lane run: the segmented-scan carry path) and whose other rows hold
+    # 0, 1 or a few entries; plus a second block row with empty rows between short ones
+    r, c = [np.full(512, 3)], [np.arange(512)]
+    for row in (0, 1, 7, 15):
+        cols = np.arange(row, 512, 37 + row)
+        r.append(np.full(cols.size, row)); c.append(cols)
+    r.append(np.array([17, 17, 30])); c.append(np.array([0, 500, 250]))
+    r, c = np.concatenate(r), np.concatenate(c)
+    return I.csr_from_coo(32, 512, r, c, I.uniform_pm1(19, 2, r.size))
+
+
+def test_row_across_all_lanes(env):
+    bd, torch = env
+    A = long_row_unit_matrix()
+    x = I.vector_x(A.n, 61)
+    y0 = I.uniform_pm1(62, I.TAG_Y, A.m)
+    for agg in (0, 1):
+        y, st = gpu_spmv(env, A, x, 0.75, 0.5, y0, col_agg=agg)
+        assert st["lane_layout"] == 1
+        check(A, x, y, 0.75, 0.5, y0)
+    with bd.BlockedMatrix(A) as M:
+        for k in (2, 4, 7):
+            X = np.stack([I.vector_x(A.n, 70 + j) for j in range(k)])
+            Yd = torch.zeros((k, A.m), dtype=torch.float64, device="cuda")
+            M.run_multi(torch.from_numpy(X).cuda(), Yd, 1.0, 0.0)
+            Y = Yd.cpu().numpy()
+            for j in range(k):
+                check(A, X[j], Y[j])
 
 
 @pytest.mark.parametrize("unit_work", [64, 300, 4000])
@@ -263,11 +299,14 @@ def test_single_entry_units_with_and_without_direct_descriptors(env, kind):
     A = I.isolated_entries_block_row(rows_with_two=11 if kind == "long_entry_unit" else 0)
     x = I.vector_x(A.n, 41)
     y0 = I.uniform_pm1(42, I.TAG_Y, A.m)
-    y, st = gpu_spmv(env, A, x, 1.5, -0.5, y0, col_agg=0)
+    y, st = gpu_spmv(env, A, x, 1.5, -0.5, y0, col_agg=0, record_layout=True)
     assert st["n_entry_mode_units"] == 1
     assert st["n_direct_units"] == (0 if kind == "long_entry_unit" else 1)
     check(A, x, y, 1.5, -0.5, y0)
-    with bd.BlockedMatrix(A, col_agg=0) as M:
+    y, st = gpu_spmv(env, A, x, 1.5, -0.5, y0, col_agg=0)
+    assert st["lane_layout"] == 1
+    check(A, x, y, 1.5, -0.5, y0)
+    with bd.BlockedMatrix(A, col_agg=0, record_layout=True) as M:
         X = np.stack([I.vector_x(A.n, 50 + j) for j in range(7)])
         Xd = torch.from_numpy(X).cuda()
         Yd = torch.zeros((7, A.m), dtype=torch.float64, device="cuda")

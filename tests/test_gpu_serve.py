@@ -138,3 +138,23 @@ def test_request_errors(env):
             S.submit_cg(mid, np.ones(40))                 # not square
         with pytest.raises(bd.CbspmvError):
             S.submit_spmv(mid + 5, np.ones(40))            # unknown matrix
+
+
+def test_oversized_request_is_refused_at_submit(env):
+    """A request whose workspace exceeds the whole memory budget is refused when it is
+    submitted (it could never be admitted, and the arrival-order queue would hold every
+    later request behind it); a small request after it still completes."""
+    bd, torch = env
+    big = I.laplacian3d(40)                      # 64,000 rows: a CG request needs ~2.8 MB
+    small = I.random_csr(300, 200, 0.05, 4)
+    with bd.Server(memory_budget=1 << 20) as S:
+        mb, ms = S.register(big), S.register(small)
+        with pytest.raises(bd.CbspmvError) as ei:
+            S.submit_cg(mb, I.uniform_pm1(30, I.TAG_RHS, big.n), TOL)
+        assert ei.value.status == 3               # CBSPMV_ERR_OOM
+        x = I.vector_x(small.n, 31)
+        t, y = S.submit_spmv(ms, x)
+        r = S.wait(t, 60000)
+        assert r["done"] and r["status"] == 0
+        assert S.stats()["submitted"] == 1
+    np.testing.assert_array_equal(y, solo_product(bd, torch, small, x))

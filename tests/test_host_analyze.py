@@ -61,9 +61,11 @@ def assert_roundtrip(M, A):
 
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("col_agg", [-1, 0, 1])
-def test_structure_and_roundtrip(bd, name, col_agg):
+@pytest.mark.parametrize("layout", ["lanes", "records"])
+def test_structure_and_roundtrip(bd, name, col_agg, layout):
     A = CASES[name]()
-    with host(bd, A, col_agg=col_agg) as M:
+    with host(bd, A, col_agg=col_agg, record_layout=layout == "records") as M:
+        assert M.stats()["lane_layout"] == (layout == "lanes")
         assert_same_structure(bd, A, M, col_agg=col_agg)
         assert_roundtrip(M, A)
 
@@ -86,9 +88,10 @@ def test_explicit_zeros_survive_dense_tiles(bd):
     # drop two entries so that the tile has absent positions too
     keep = np.ones(256, bool); keep[[10, 11]] = False
     A = I.csr_from_coo(16, 16, (idx // 16)[keep], (idx % 16)[keep], v[keep], sum_duplicates=False)
-    with host(bd, A) as M:
-        assert M.stats()["n_fmt"][B.FMT_DENSE] == 1
-        assert_roundtrip(M, A)
+    for rec in (False, True):
+        with host(bd, A, record_layout=rec) as M:
+            assert M.stats()["n_fmt"][B.FMT_DENSE] == 1
+            assert_roundtrip(M, A)
 
 
 def test_worked_example(bd):
@@ -191,10 +194,11 @@ def test_storage_model_matches_oracle_formula(bd):
 def test_schedule_mode_follows_piece_sizes(bd):
     """Units whose rows hold one or two entries per tile get single-entry schedules; the
     FEM matrix's 3x3 blocks (pieces of about three entries) keep 3-entry chunks."""
-    with host(bd, I.rmat(13, 16, seed=2)) as M:
+    with host(bd, I.rmat(13, 16, seed=2), record_layout=True) as M:
         st = M.stats()
         assert st["n_entry_mode_units"] > 0.15 * st["n_units"]
-    with host(bd, I.fem_block_band(n_rows=6000, n_block_rows=2000, half_band=300, seed=3)) as M:
+    with host(bd, I.fem_block_band(n_rows=6000, n_block_rows=2000, half_band=300, seed=3),
+              record_layout=True) as M:
         st = M.stats()
         assert st["n_entry_mode_units"] < 0.1 * st["n_units"]
         # 3x3 blocks: the chunks of (nearly) every unit cover consecutive columns
@@ -215,23 +219,64 @@ def test_value_map_option_keeps_the_structure(bd):
 
 
 def test_fma_slot_count(bd):
-    """fma_slots counts whole lanes (32 per chunk row) and at least one slot per entry; two
-    hand-counted cases: a 16x16 diagonal is one unit of 16 single-entry chunks (rounded up to
-    2 descriptor rows of 32 lanes, 1 slot each); a dense 16x16 block is 16 rows of six
-    consecutive-column chunks (96 chunks: 4 descriptor rows of 32 lanes, 3 slots each)."""
+    """Record layout: fma_slots counts whole lanes (32 per chunk row) and at least one slot
+    per entry; two hand-counted cases: a 16x16 diagonal is one unit of 16 single-entry chunks
+    (rounded up to 2 descriptor rows of 32 lanes, 1 slot each); a dense 16x16 block is 16
+    rows of six consecutive-column chunks (96 chunks: 4 descriptor rows of 32 lanes, 3 slots
+    each)."""
     for A in (I.rmat(12, 16, seed=4), I.laplacian2d(64), I.random_csr(333, 517, 0.2, 11),
               I.fem_block_band(n_rows=6000, n_block_rows=2000, half_band=300, seed=3)):
-        with host(bd, A) as M:
+        with host(bd, A, record_layout=True) as M:
             st = M.stats()
         assert st["fma_slots"] % 32 == 0 and st["fma_slots"] >= A.nnz
     r = np.arange(16)
-    with host(bd, I.csr_from_coo(16, 16, r, r, np.ones(16))) as M:
+    with host(bd, I.csr_from_coo(16, 16, r, r, np.ones(16)), record_layout=True) as M:
         st = M.stats()
     assert st["n_entry_mode_units"] == 1 and st["fma_slots"] == 64
     r, c = np.repeat(np.arange(16), 16), np.tile(np.arange(16), 16)
-    with host(bd, I.csr_from_coo(16, 16, r, c, np.ones(256))) as M:
+    with host(bd, I.csr_from_coo(16, 16, r, c, np.ones(256)), record_layout=True) as M:
         st = M.stats()
     assert st["n_xseq_units"] == 1 and st["fma_slots"] == 384
+
+
+def test_lane_layout_fma_slots_and_units(bd):
+    """Lane-stream layout: every unit issues 32 x ceil(entries / 32) FMA slots (no Dense
+    zero fill, no chunk rounding). Hand-counted: a 16x16 diagonal is one unit of 16
+    entries (one step: 32 slots); a full 16x16 block is one Dense sub-block of 256 entries
+    (8 steps: 256 slots, every slot useful); a FEM block row of the 3x3 band (16 rows x 81
+    entries = 1,296) fits one unit of 41 steps."""
+    r = np.arange(16)
+    with host(bd, I.csr_from_coo(16, 16, r, r, np.ones(16))) as M:
+        st = M.stats()
+    assert st["lane_layout"] == 1 and st["n_units"] == 1 and st["fma_slots"] == 32
+    r, c = np.repeat(np.arange(16), 16), np.tile(np.arange(16), 16)
+    with host(bd, I.csr_from_coo(16, 16, r, c, np.ones(256))) as M:
+        st = M.stats()
+    assert st["n_fmt"][B.FMT_DENSE] == 1 and st["fma_slots"] == 256
+    F = I.fem_block_band(n_rows=6000, n_block_rows=2000, half_band=300, seed=3)
+    with host(bd, F) as M:
+        st = M.stats()
+        assert_roundtrip(M, F)
+    # whole block rows of the band hold 1,296 entries: well over 97% of the slots are useful
+    assert st["n_split_units"] == 0
+    assert F.nnz / st["fma_slots"] > 0.97
+    for A in (I.rmat(12, 16, seed=4), I.laplacian2d(64), I.random_csr(333, 517, 0.2, 11)):
+        with host(bd, A) as M:
+            st = M.stats()
+            assert_roundtrip(M, A)
+        assert st["fma_slots"] % 32 == 0 and A.nnz <= st["fma_slots"] < A.nnz + 32 * st["n_units"]
+
+
+def test_lane_layout_cuts_long_block_rows(bd):
+    """A block row with more sub-blocks than one unit's x slots (32) is cut into parts whose
+    partial sums the combine adds; the parts keep every entry once (round trip)."""
+    A = I.isolated_entries_block_row(tiles=70)
+    with host(bd, A, col_agg=0) as M:
+        st = M.stats()
+        assert_roundtrip(M, A)
+        blk = M.export_blocked()
+    ntiles = len(blk["nnz"])
+    assert ntiles > 32 and st["n_split_units"] >= (ntiles + 31) // 32 and st["n_split_rows"] == 1
 
 
 def test_direct_descriptors_where_columns_are_known_per_chunk(bd):
@@ -241,7 +286,7 @@ def test_direct_descriptors_where_columns_are_known_per_chunk(bd):
     oracle's rounding of it (BF16)."""
     from oracle import lowprec as L
     A = I.fem_block_band(n_rows=6000, n_block_rows=2000, half_band=300, seed=3)
-    with host(bd, A) as M:
+    with host(bd, A, record_layout=True) as M:
         st = M.stats()
         assert_roundtrip(M, A)
     assert st["n_direct_units"] == st["n_xseq_units"] + st["n_entry_mode_units"] > 0
@@ -252,13 +297,13 @@ def test_direct_descriptors_where_columns_are_known_per_chunk(bd):
     assert np.array_equal(rp, A.row_ptr) and np.array_equal(col, A.col)
     assert np.array_equal(val.view(np.uint64), L.round_to_format(A.val, "bf16").view(np.uint64))
     R = I.rmat(13, 16, seed=2)
-    with host(bd, R) as M:
+    with host(bd, R, record_layout=True) as M:
         st = M.stats()
         assert_roundtrip(M, R)
     assert 0 < st["n_direct_units"] <= st["n_entry_mode_units"] + st["n_xseq_units"]
     r, c = np.repeat(np.arange(16), 16), np.tile(np.arange(16), 16)
     D = I.csr_from_coo(16, 16, r, c, I.normal(4, I.TAG_VAL, 256))
-    with host(bd, D) as M:      # one Dense tile
+    with host(bd, D, record_layout=True) as M:      # one Dense tile
         assert M.stats()["n_direct_units"] == 1 and M.stats()["n_fmt"][2] == 1
         assert_roundtrip(M, D)
 
@@ -267,7 +312,7 @@ def test_long_single_entry_unit_keeps_16bit_descriptors(bd):
     """540 single-entry chunks in one unit (27 per tile, pieces of 1.7 entries): more than
     direct descriptors cover, so the unit keeps 16-bit descriptors."""
     A = I.isolated_entries_block_row()
-    with host(bd, A, col_agg=0) as M:
+    with host(bd, A, col_agg=0, record_layout=True) as M:
         st = M.stats()
         assert_roundtrip(M, A)
     assert st["n_units"] == 1 and st["n_entry_mode_units"] == 1 and st["n_direct_units"] == 0
@@ -275,39 +320,45 @@ def test_long_single_entry_unit_keeps_16bit_descriptors(bd):
 
 
 def test_analysis_does_not_depend_on_the_thread_count(bd, tmp_path):
-    """The same analysis with one host thread (CBSPMV_HOST_THREADS=1, in a child process)
-    and with all of them: equal statistics (apart from the time) and equal exports."""
+    """The same analysis with one host thread, eight and all of them (CBSPMV_HOST_THREADS,
+    each in a child process): equal statistics (apart from the time) and byte-equal
+    exports. The inputs are large enough that every chunked loop of the analysis (block
+    rows, units, schedules, the in-place re-layout) runs as many chunks."""
     import json
     import os
     import subprocess
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     code = """
-import json, sys
+import hashlib, json, sys
 import numpy as np
 sys.path.insert(0, ROOT)
 from paper_2605_18515_gb300 import build, inputs as I
 build.build()
 from paper_2605_18515_gb300 import binding as bd
 out = {}
-for name, A in (("fem", I.fem_block_band(n_rows=6000, n_block_rows=2000, half_band=300, seed=3)),
-                ("rmat", I.rmat(12, 16, seed=4))):
-    with bd.BlockedMatrix(A, device=-1, keep_value_map=True) as M:
-        st = M.stats(); st.pop("analyze_ms")
-        rp, col, val = M.export_csr()
-        blk = M.export_blocked()
-    out[name] = {"stats": st, "val": val.view(np.uint64).tolist()[:5000],
-                 "valsum": int(val.view(np.uint64).sum() % (1 << 61)),
-                 "blk": {k: np.asarray(v).tolist() for k, v in blk.items()}}
+for name, A in (("fem", I.fem_block_band(n_rows=60000, n_block_rows=20000, half_band=800, seed=3)),
+                ("rmat", I.rmat(15, 16, seed=4))):
+    for dt in ("f64", "bf16"):
+        with bd.BlockedMatrix(A, device=-1, keep_value_map=True, value_dtype=dt) as M:
+            st = M.stats(); st.pop("analyze_ms")
+            rp, col, val = M.export_csr()
+            blk = M.export_blocked()
+        h = hashlib.sha256()
+        for arr in (rp, col, val, *[np.asarray(blk[k]) for k in sorted(blk)]):
+            h.update(np.ascontiguousarray(arr).tobytes())
+        out[name + "_" + dt] = {"stats": st, "digest": h.hexdigest(), "nnz": int(col.size)}
 print(json.dumps(out))
 """.replace("ROOT", repr(root))
     res = {}
-    for threads in ("1", None):
+    for threads in ("1", "8", None):
         env = dict(os.environ)
         env.pop("CBSPMV_HOST_THREADS", None)
         if threads:
             env["CBSPMV_HOST_THREADS"] = threads
-        p = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        p = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
         assert p.returncode == 0, p.stderr[-2000:]
         res[threads] = json.loads(p.stdout.strip().splitlines()[-1])
-    assert res["1"] == res[None]
+    assert res["1"]["fem_f64"]["stats"]["n_block_rows"] > 3000
+    assert res["1"]["rmat_f64"]["stats"]["n_units"] > 1000
+    assert res["1"] == res["8"] == res[None]

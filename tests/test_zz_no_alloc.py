@@ -75,3 +75,8 @@ def test_noalloc_rejects_bad_arguments(env):
     with bd.BlockedMatrix(A, device=-1) as H:
         assert L.cbspmv_run_noalloc(H.handle, None, None, 1.0, 0.0, None) == 1   # host-only handle
         assert b"device" in L.cbspmv_last_error()
+    with bd.BlockedMatrix(A) as M:                  # x and y overlapping: rejected like cbspmv_run
+        buf = torch.zeros(2 * A.n, dtype=torch.float64, device="cuda")
+        assert L.cbspmv_run_noalloc(M.handle, buf.data_ptr(), buf.data_ptr() + 8 * 8, 1.0, 0.0, None) == 1
+        assert b"overlap" in L.cbspmv_last_error()
+        assert L.cbspmv_run_noalloc(M.handle, buf.data_ptr() + 4, buf.data_ptr() + 8 * A.n, 1.0, 0.0, None) == 1
