@@ -864,9 +864,9 @@ __global__ void __launch_bounds__(256) combine_wide_kernel(const __grid_constant
 //     ahead, so the gather of the next unit overlaps the walk of this one;
 //   * walks its lane runs: each step is one coalesced 8-byte value load per lane, one 16-bit
 //     entry word (x slot and row) and one FP64 FMA into the lane's row accumulator; values
-//     and words are loaded a group of 8 steps ahead into registers (the next unit's first
-//     group while the last group of this unit is computed), so the FMA chain never waits on
-//     memory and no shared-memory staging of the matrix is needed;
+//     and words are loaded a group of 8 steps ahead into two register sets used in turn
+//     (the next unit's first group while the last group of this unit is computed), so no
+//     shared-memory staging of the matrix is needed;
 //   * finishes rows that cross lane runs: the lane where a row ends adds the partial sums of
 //     the lanes before it in lane order (a segmented scan when a row spans many lanes), and
 //     writes y once per row (block rows cut into parts: 16 partial sums per part, added by
@@ -889,14 +889,16 @@ struct LaneGeom {
 };
 constexpr int kLaneGroup = 8;   // steps per prefetch group (two words of four entries)
 
+// streaming loads of read-only data that bypass L1 (plain asm: the compiler may predicate
+// and schedule them)
 __device__ __forceinline__ double ldg_stream_f64(const double* p) {
   double v;
-  asm volatile("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  asm("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
   return v;
 }
 __device__ __forceinline__ uint64_t ldg_stream_u64(const uint64_t* p) {
   uint64_t v;
-  asm volatile("ld.global.nc.L1::no_allocate.u64 %0, [%1];" : "=l"(v) : "l"(p));
+  asm("ld.global.nc.L1::no_allocate.u64 %0, [%1];" : "=l"(v) : "l"(p));
   return v;
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
@@ -980,17 +982,21 @@ __global__ void __launch_bounds__(32 * LaneGeom<kK>::kWarps, 1)
       }
     }
   };
-  // values and entry words of steps 8g .. 8g + 7 of this lane (absent steps: 0.0, no entry)
-  auto load_group = [&](int q, const CbLaneUnit& u, uint32_t g, double (&v)[kLaneGroup], uint64_t& w0,
-                        uint64_t& w1) {
-    const RunArgs& a = b.p[q];
-    const double* vp = a.lvals + ((size_t)u.vals + kLaneGroup * g) * CB_VLANES + lane;
-    const uint64_t* wp = a.lwords + ((size_t)u.words + 2u * g) * CB_VLANES + lane;
-    const uint32_t S = u.steps, Q = (S + 3u) / 4u;
+  // this lane's value and word streams of a unit
+  auto vbase = [&](int q, const CbLaneUnit& u) { return b.p[q].lvals + (size_t)u.vals * CB_VLANES + lane; };
+  auto wbase = [&](int q, const CbLaneUnit& u) { return b.p[q].lwords + (size_t)u.words * CB_VLANES + lane; };
+  // values and entry words of steps 8g .. 8g + 7 (absent steps: no entry); plain loads the
+  // compiler can predicate, with immediate offsets from the group's base
+  auto load_group = [&](const double* vp, const uint64_t* wp, uint32_t S, uint32_t g, double (&v)[kLaneGroup],
+                        uint64_t& w0, uint64_t& w1) {
+    const double* p = vp + kLaneGroup * CB_VLANES * g;
+    const int rem = (int)S - (int)(kLaneGroup * g);
 #pragma unroll
-    for (int j = 0; j < kLaneGroup; ++j) v[j] = (kLaneGroup * g + j < S) ? ldg_stream_f64(vp + CB_VLANES * j) : 0.0;
-    w0 = (2u * g < Q) ? ldg_stream_u64(wp) : ~0ull;
-    w1 = (2u * g + 1u < Q) ? ldg_stream_u64(wp + CB_VLANES) : ~0ull;
+    for (int j = 0; j < kLaneGroup; ++j)
+      if (j < rem) v[j] = ldg_stream_f64(p + CB_VLANES * j);
+    const uint64_t* pw = wp + 2u * CB_VLANES * g;
+    w0 = rem > 0 ? ldg_stream_u64(pw) : ~0ull;
+    w1 = rem > 4 ? ldg_stream_u64(pw + CB_VLANES) : ~0ull;
   };
 
   uint32_t t = grab();
@@ -1000,9 +1006,11 @@ __global__ void __launch_bounds__(32 * LaneGeom<kK>::kWarps, 1)
   fetch(t, q, u);
   gather(q, u, 0);
   cp_async_commit();
-  double cv[kLaneGroup], nv[kLaneGroup];
-  uint64_t cw0, cw1, nw0 = ~0ull, nw1 = ~0ull;
-  load_group(q, u, 0, cv, cw0, cw1);
+  double va[kLaneGroup], vb[kLaneGroup];
+  uint64_t wa0, wa1, wb0 = ~0ull, wb1 = ~0ull;
+#pragma unroll
+  for (int j = 0; j < kLaneGroup; ++j) va[j] = vb[j] = 0.0;
+  load_group(vbase(q, u), wbase(q, u), u.steps, 0, va, wa0, wa1);
   uint32_t tn = grab();
   if (tn < total) fetch(tn, qn, un);
   uint32_t buf = 0;
@@ -1027,14 +1035,19 @@ __global__ void __launch_bounds__(32 * LaneGeom<kK>::kWarps, 1)
     uint32_t cur = kNone, first_row = kNone;
     bool have_head = false;
     const uint32_t ngroups = (u.steps + kLaneGroup - 1u) / kLaneGroup;
-    for (uint32_t g = 0; g < ngroups; ++g) {
-      if (g + 1 < ngroups) load_group(q, u, g + 1, nv, nw0, nw1);
-      else if (tn < total) load_group(qn, un, 0, nv, nw0, nw1);
+    const double* vp = vbase(q, u);
+    const uint64_t* wp = wbase(q, u);
+    const double* vpn = tn < total ? vbase(qn, un) : vp;
+    const uint64_t* wpn = tn < total ? wbase(qn, un) : wp;
+    const uint32_t Sn = tn < total ? un.steps : 0u;
+    // the entries of one group: x operands first (slot 511 of an absent entry lies inside the
+    // buffer and is not used), then the FMA chain with the rare row switch
+    auto compute = [&](const double (&v)[kLaneGroup], uint64_t w0, uint64_t w1) {
       double xv[kLaneGroup][kK];
 #pragma unroll
       for (int j = 0; j < kLaneGroup; ++j) {
-        const uint32_t w = (uint32_t)((j < 4 ? cw0 : cw1) >> (16 * (j & 3))) & 0xffffu;
-        const uint32_t slot = w == CB_LANE_NONE ? 0u : (w & 511u);
+        const uint32_t w = (uint32_t)((j < 4 ? w0 : w1) >> (16 * (j & 3))) & 0xffffu;
+        const uint32_t slot = w & 511u;
         if constexpr (kK == 1) {
           xv[j][0] = *reinterpret_cast<const double*>(xs + 8u * slot);
         } else {
@@ -1048,36 +1061,49 @@ __global__ void __launch_bounds__(32 * LaneGeom<kK>::kWarps, 1)
       }
 #pragma unroll
       for (int j = 0; j < kLaneGroup; ++j) {
-        const uint32_t w = (uint32_t)((j < 4 ? cw0 : cw1) >> (16 * (j & 3))) & 0xffffu;
-        if (w != CB_LANE_NONE) {
-          const uint32_t r = w >> 9;
-          if (r != cur) {
-            if (cur == kNone) {
-              first_row = r;
-            } else if (!have_head) {
+        const uint32_t w = (uint32_t)((j < 4 ? w0 : w1) >> (16 * (j & 3))) & 0xffffu;
+        const uint32_t r = w >> 9;
+        if (r != cur && w != CB_LANE_NONE) {
+          if (cur == kNone) {
+            first_row = r;
+          } else if (!have_head) {
 #pragma unroll
-              for (int h = 0; h < kK; ++h) head[h] = acc[h];
-              have_head = true;
-            } else {
+            for (int h = 0; h < kK; ++h) head[h] = acc[h];
+            have_head = true;
+          } else {
 #pragma unroll
-              for (int h = 0; h < kK; ++h) srow[cur * kK + h] = acc[h];
-            }
-#pragma unroll
-            for (int h = 0; h < kK; ++h) acc[h] = 0.0;
-            cur = r;
+            for (int h = 0; h < kK; ++h) srow[cur * kK + h] = acc[h];
           }
 #pragma unroll
-          for (int h = 0; h < kK; ++h) acc[h] = fma(cv[j], xv[j][h], acc[h]);
+          for (int h = 0; h < kK; ++h) acc[h] = 0.0;
+          cur = r;
+        }
+        if (w != CB_LANE_NONE) {
+#pragma unroll
+          for (int h = 0; h < kK; ++h) acc[h] = fma(v[j], xv[j][h], acc[h]);
         }
       }
+    };
+    // two register sets in turn: the group after the current one (or the next unit's first
+    // group) is loaded while the current one is computed
+    uint32_t g = 0;
+    while (g < ngroups) {
+      if (g + 1 < ngroups) load_group(vp, wp, u.steps, g + 1, vb, wb0, wb1);
+      else load_group(vpn, wpn, Sn, 0, vb, wb0, wb1);
+      compute(va, wa0, wa1);
+      if (++g >= ngroups) {
 #pragma unroll
-      for (int j = 0; j < kLaneGroup; ++j) cv[j] = nv[j];
-      cw0 = nw0;
-      cw1 = nw1;
+        for (int j = 0; j < kLaneGroup; ++j) va[j] = vb[j];
+        wa0 = wb0;
+        wa1 = wb1;
+        break;
+      }
+      if (g + 1 < ngroups) load_group(vp, wp, u.steps, g + 1, va, wa0, wa1);
+      else load_group(vpn, wpn, Sn, 0, va, wa0, wa1);
+      compute(vb, wb0, wb1);
+      ++g;
     }
-    if (ngroups == 0) {        // (no entries: never produced by the analysis) keep the prefetch in step
-      if (tn < total) load_group(qn, un, 0, cv, cw0, cw1);
-    }
+    if (ngroups == 0) load_group(vpn, wpn, Sn, 0, va, wa0, wa1);   // (no entries) keep the prefetch in step
 
     // rows that cross lane runs: neighbours are the nearest lanes with entries
     const bool nonempty = cur != kNone;
@@ -1201,6 +1227,11 @@ __global__ void __launch_bounds__(32 * LaneGeom<kK>::kWarps, 1)
           partial[((size_t)u.slot * 16 + lane) * kK + h] = (uint32_t)lane < R ? srow[lane * kK + h] : 0.0;
       }
     }
+    // the gather list of the unit after next into L2 (one bulk prefetch by the TMA unit
+    // instead of 16 scattered cold loads per lane when its gather is issued)
+    if (tnn < total && lane == 0 && unn.nslots)
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(b.p[qnn].lgcols + unn.gcols),
+                   "r"(4u * unn.nslots) : "memory");
     __syncwarp();
     if (tn >= total) break;
     t = tn; q = qn; u = un;
