@@ -40,10 +40,12 @@ WORKLOADS = {
     "rmat_s19": "FP64 R-MAT scale 19 (R-MAT recipe above), for profiling",
     "laplace2d_64": "FP64 2D 5-point Laplacian on a 64x64 grid, x U[-1,1], seed 0",
 }
-# FP64 FMA issue rate of a GB300 SM: each of the 4 SM sub-partitions completes one warp-wide
-# (32-lane) DFMA every 64 cycles, i.e. 2 FP64 FMA lanes per SM per cycle (measured with a
-# dependent/independent DFMA chain probe; it matches the nominal 1.25 TFLOP/s FP64).
-FP64_FMA_LANES_PER_SM_CYCLE = 2.0
+# The FP64 roofline (the run kernel issues one FP64 FMA per stored entry) is measured live
+# by cbspmv_measure_fp64_fma: a kernel of independent FMA chains, one CTA per SM. On GB300
+# each SM sub-partition retires one warp-wide FP64 FMA per 76 SM cycles (32 lanes / 76 =
+# 0.42 lanes per cycle, 1.68 per SM); the derived peak at the maximum clock is printed beside
+# the measured one.
+SUBPARTITIONS_PER_SM = 4
 L2_BYTES = 129 * 2 ** 20
 
 # DRAM bytes (read + write) per launch of the run kernel from one ncu capture of the same
@@ -51,8 +53,7 @@ L2_BYTES = 129 * 2 ** 20
 # full workload by its number of stored entries. Used only when the loaded library reports
 # the same revision; otherwise the roofline's traffic is null.
 KERNEL_TRAFFIC = {
-    "run kernel rev 13": {("fem3x3_band_1m", "f64"): 1.1617e9, ("fem3x3_band_1m", "bf16"): 0.6535e9,
-                          ("rmat_s21", "f64"): 0.5897e9},
+    "run kernel rev 13": {("fem3x3_band_1m", "bf16"): 0.6535e9},
 }
 
 
@@ -63,8 +64,10 @@ def measured_traffic(version: str, workload: str, dtype: str):
     return None
 
 
-def fp64_peak_gflops(sms: int, sm_max_mhz: float) -> float:
-    return sms * FP64_FMA_LANES_PER_SM_CYCLE * 2.0 * sm_max_mhz / 1e3
+def fp64_peak_gflops(sms: int, sm_mhz: float, cycles_per_warp_fma: float) -> float:
+    """FP64 FMA peak from the unit counts: SMs x sub-partitions x 32 lanes per warp-FMA
+    interval x 2 flops x clock."""
+    return sms * SUBPARTITIONS_PER_SM * 32.0 / cycles_per_warp_fma * 2.0 * sm_mhz / 1e3
 
 
 def load_peaks():
@@ -77,7 +80,7 @@ def load_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms in the background."""
+    """nvidia-smi clocks and throttle reasons sampled every 25 ms in the background."""
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -92,7 +95,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "25"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -166,6 +169,38 @@ def oracle_sample_gflops(A, x, target_s: float = 12.0):
         reps += 1
     gf = 2.0 * A.nnz * reps / t_total / 1e9
     return gf, f"{reps} full products of the {A.m}x{A.n} matrix ({A.nnz} nonzeros), {t_total:.1f} s"
+
+
+def row_slices(A, parts: int):
+    """The matrix cut into `parts` row ranges of about equal nonzeros, as CSR views sharing
+    the column and value arrays (row pointers stay absolute offsets into them)."""
+    cuts = np.searchsorted(A.row_ptr, np.linspace(0, A.nnz, parts + 1)[1:-1])
+    bounds = [0, *[int(c) for c in cuts], A.m]
+    out = []
+    for r0, r1 in zip(bounds[:-1], bounds[1:]):
+        if r1 > r0:
+            out.append(type(A)(r1 - r0, A.n, A.row_ptr[r0:r1 + 1], A.col, A.val))
+    return out
+
+
+def oracle_allcore_gflops(A, x, target_s: float = 8.0):
+    """The same oracle (unchanged) on every host core this process may run on: the rows are
+    cut into one slice per core and each slice is multiplied by a separate thread (the
+    oracle's C routine runs outside Python's lock). Whole-matrix products are repeated until
+    ~target_s. Returns (GFLOP/s, threads, sample)."""
+    from concurrent.futures import ThreadPoolExecutor
+    import oracle
+    threads = len(os.sched_getaffinity(0))
+    parts = row_slices(A, threads)
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(lambda S: oracle.spmv(S, x), parts))      # warm
+        reps, t0 = 0, time.perf_counter()
+        while time.perf_counter() - t0 < target_s and reps < 5000:
+            list(ex.map(lambda S: oracle.spmv(S, x), parts))
+            reps += 1
+        dt = time.perf_counter() - t0
+    gf = 2.0 * A.nnz * reps / dt / 1e9
+    return gf, threads, f"{reps} full products on {threads} threads (row slices of equal nonzeros), {dt:.1f} s"
 
 
 def multi_rhs_bench(M, A, x, vec, stream, ks=(1, 8, 32), reps=20):
@@ -380,7 +415,9 @@ def run_reference(args, A, x, ws, rank):
     if rank != 0:
         return
     import oracle
-    # each step is a bounded sample of the workload: the first rows holding ~1/8 of the nonzeros
+    # each step is a bounded sample of the workload: the first rows holding ~1/8 of the
+    # nonzeros (the full product takes the single-threaded oracle 0.06-0.16 s, too long for
+    # thousands of steps); the rate, GFLOP/s, is the same quantity as the GPU arm's
     cut = int(np.searchsorted(A.row_ptr, A.nnz // 8))
     sub = type(A)(cut, A.n, A.row_ptr[:cut + 1].copy(), A.col[:A.row_ptr[cut]], A.val[:A.row_ptr[cut]])
     for _ in range(args.warmup):
@@ -394,7 +431,9 @@ def run_reference(args, A, x, ws, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * dt / args.steps, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": args.workload, "description": WORKLOADS[args.workload]},
+            "config": {"workload": args.workload, "description": WORKLOADS[args.workload],
+                       "sample": f"each step multiplies rows 0..{cut} of the workload's matrix "
+                                 f"({sub.nnz} of {A.nnz} nonzeros), single-threaded oracle"},
             "cpu_baseline": {"value": round(gf, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
                              "sample": f"rows 0..{cut} ({sub.nnz} nonzeros, 1/8 of the matrix) per step"},
             "e2e": {"value": round(gf, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -404,7 +443,7 @@ def run_reference(args, A, x, ws, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=5000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=list(WORKLOADS), default="fem3x3_band_1m")
@@ -457,6 +496,8 @@ def main():
             M.run(xd, yd, 1.0, 0.0, stream=stream)
         stream.synchronize()
         M.check_device(stream)
+        # the FP64 FMA roofline, measured on this device now (before the timed region)
+        fma = bd.measure_fp64_fma(local, stream) if not lp else None
 
         sampler = ClockSampler(local)
         sampler.start()
@@ -536,11 +577,16 @@ def main():
         err = None
         if not args.no_cpu_baseline and ws == 1:
             gf, sample = oracle_sample_gflops(A, x)
-            cpu = {"value": round(gf, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": sample}
+            gfa, threads, sample_a = oracle_allcore_gflops(A, x)
+            cpu = {"value": round(gf, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": sample,
+                   "all_cores": {"value": round(gfa, 4), "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
+                                 "sample": sample_a}}
             err = error_vs_fp64_oracle(A, x, y_ours)
         clocks = sampler.summary(w0, w1)
         fmax = clocks.get("sm_max_mhz") or 2070.0
-        peak_alu = round(fp64_peak_gflops(sms, fmax), 1)
+        if fma:
+            peak_alu = round(fma["gflops"], 1)
+            peak_derived = round(fp64_peak_gflops(sms, fmax, fma["cycles_per_warp_fma"]), 1)
         k_ms = kt["ms_main"]
         traffic = args.traffic_bytes if args.traffic_bytes is not None else \
             measured_traffic(bd.version(), args.workload, args.dtype)
@@ -555,13 +601,18 @@ def main():
                     "note": "FP32 FMA is far from binding; the bytes model (values + coordinates + "
                             "metadata + x + y + restore_cols) over the kernel's time vs measured copy bandwidth"}
         else:
-            roof = {"bound": "alu", "kernel": "spmv_kernel<f64>", "achieved": round(k_gf, 2),
+            roof = {"bound": "alu", "kernel": "spmv_lanes_kernel<f64>", "achieved": round(k_gf, 2),
                     "peak": peak_alu, "unit": "GFLOP/s", "frac": round(k_gf / peak_alu, 4),
+                    "peak_kind": "measured: FP64 FMA chain kernel on this GPU in this run "
+                                 "(cbspmv_measure_fp64_fma)",
+                    "peak_derived_at_max_clock": peak_derived,
+                    "cycles_per_warp_fp64_fma": round(fma["cycles_per_warp_fma"], 2),
                     "traffic": traffic,
                     "kernel_ms": round(k_ms, 5), "combine_ms": round(kt["ms_combine"], 5),
                     "flops_per_launch": int(flops),
-                    "note": "FP64 FMA pipe bound: peak = SMs x 2 FP64 FMA lanes/cycle x 2 flops x max SM "
-                            "clock (derived); HBM view below",
+                    "note": "one FP64 FMA per stored entry: bound by the FP64 FMA pipe; derived peak = "
+                            "SMs x 4 sub-partitions x 32 lanes / (cycles per warp FMA) x 2 flops x max SM "
+                            "clock; HBM view below",
                     "hbm": {"achieved": round(k_gbs, 2), "peak": peak, "unit": "GB/s",
                             "frac": round(k_gbs / peak, 4), "peak_kind": peak_kind,
                             "bytes_per_launch": int(algo_bytes)}}

@@ -151,7 +151,10 @@ cbspmv_status_t cbspmv_default_opts(cbspmv_opts_t* opts);
  * The host analysis runs on all hardware threads (at most 64), or on the number given by
  * the environment variable CBSPMV_HOST_THREADS (1..64); its result does not depend on it.
  * On success *out is a new handle. Errors: CBSPMV_ERR_INVALID (NULL pointers, sizes),
- * CBSPMV_ERR_NOT_CANONICAL, CBSPMV_ERR_OOM, CBSPMV_ERR_CUDA, CBSPMV_ERR_UNSUPPORTED. */
+ * CBSPMV_ERR_NOT_CANONICAL, CBSPMV_ERR_OOM, CBSPMV_ERR_CUDA, CBSPMV_ERR_UNSUPPORTED. A failed
+ * call frees everything it allocated. Fault injection for tests: when the environment
+ * variable CBSPMV_FAIL_ALLOC_AFTER holds N >= 0, the call's device allocation number N
+ * (from 0) fails as out of memory. */
 cbspmv_status_t cbspmv_analyze(const cbspmv_csr_t* A, const cbspmv_opts_t* opts, void* stream,
                                cbspmv_handle_t* out);
 
@@ -177,9 +180,11 @@ cbspmv_status_t cbspmv_run_host(cbspmv_handle_t h, const void* x_host, void* y_h
  * n x k with leading dimension ldx >= n (column j at X + j * ldx); Y: device array,
  * column-major m x k with ldy >= m. Element type, alignment and the no-overlap rule
  * (between the whole spans of X and Y) are those of cbspmv_run; k = 0 does nothing.
- * The columns are computed in passes of 4 (then 2, then 1) vectors: each pass stages
- * every unit of the matrix once and multiplies it into all its vectors, so the matrix is
- * read ceil(k/4)-ish times instead of k times. Each column is computed exactly as
+ * Reduced value types: the columns are computed in passes of 4 (then 2, then 1) vectors:
+ * each pass stages every unit of the matrix once and multiplies it into all its vectors, so
+ * the matrix is read ceil(k/4)-ish times instead of k times. FP64 values in the lane-stream
+ * layout: one column per pass, since the FP64 FMA pipe, not the matrix bytes, bounds the
+ * product (a pass over several vectors measured slower per vector). Each column is computed exactly as
  * cbspmv_run would (same summation order, so the results are bitwise equal to k separate
  * runs). The first call with k > 1 allocates a partial-sum buffer for 4-vector passes,
  * owned by the handle. Errors: CBSPMV_ERR_INVALID (k < 0, ldx < n, ldy < m, NULL or
@@ -287,6 +292,16 @@ cbspmv_status_t cbspmv_time_kernels(cbspmv_handle_t h, const void* x, void* y, d
                                     double beta, int reps, void* stream, double* ms_main,
                                     double* ms_combine, int* launches_per_run);
 
+/* Measurement support (the paper has no counterpart): the FP64 FMA rate of `device`, the
+ * roofline of the FP64 run kernel, which issues one FP64 FMA per stored entry. Runs a
+ * kernel of independent FMA chains (one CTA per SM) on `stream`, synchronises it, and
+ * returns the achieved rate (*gflops, 2 flops per FMA, at the clock the device runs at)
+ * and the SM cycles one warp-wide FP64 FMA occupies its SM sub-partition
+ * (*cycles_per_warp_fma). Allocates and frees a few KB of device memory.
+ * Errors: CBSPMV_ERR_INVALID (NULL outputs), CBSPMV_ERR_OOM, CBSPMV_ERR_CUDA. */
+cbspmv_status_t cbspmv_measure_fp64_fma(int device, void* stream, double* gflops,
+                                        double* cycles_per_warp_fma);
+
 /* ---- Serving (the paper has no serving system; it motivates its preprocessing cost by
  * repeated products as in iterative solvers, Sec. 4.5) ---------------------------------
  * A server keeps analysed matrices resident on one device and runs requests submitted
@@ -373,7 +388,14 @@ cbspmv_status_t cbspmv_server_get_stats(cbspmv_server_t s, cbspmv_server_stats_t
 cbspmv_status_t cbspmv_server_destroy(cbspmv_server_t s);
 
 /* Reads the handle's device error word (set by bounded device-side waits that gave up)
- * and clears it: CBSPMV_OK or CBSPMV_ERR_TIMEOUT. Synchronises `stream`. */
+ * and clears it: CBSPMV_OK or CBSPMV_ERR_TIMEOUT. Synchronises `stream`. The record-layout
+ * kernel waits for its own bulk copies with a budget of 4e9 SM cycles (about 2 s), or the
+ * number in the environment variable CBSPMV_WAIT_BUDGET_CYCLES when the handle was analysed;
+ * a warp whose wait gave up records the error, waits for its copies with the full budget
+ * and stops, so the product is incomplete but the device stays usable. Test hook: with
+ * CBSPMV_TEST_STUCK_WAIT=1 at analysis, each warp's first wait of the record kernel is on
+ * a barrier nothing arrives at, so it runs out of its budget. The lane-stream kernel has no
+ * such wait. */
 cbspmv_status_t cbspmv_check_device(cbspmv_handle_t h, void* stream);
 
 /* Reconstructs the CSR matrix from the handle's device-resident blocked format

@@ -128,6 +128,7 @@ SIGNATURES = {
     "cbspmv_server_wait": [_P, ctypes.c_uint64, _I, ctypes.POINTER(Result)],
     "cbspmv_server_get_stats": [_P, ctypes.POINTER(ServerStats)],
     "cbspmv_server_destroy": [_P],
+    "cbspmv_measure_fp64_fma": [_I, _P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
     "cbspmv_last_error": [],
     "cbspmv_version": [],
 }
@@ -559,6 +560,13 @@ def analyze_tuned(A, *, reps=20, stream=None, **opts):
                         for i in range(n)]}
     M = BlockedMatrix._adopt(h.value, int(A.m), int(A.n), nnz, o.device, opts.get("value_dtype", "f64"))
     return M, report
+
+
+def measure_fp64_fma(device: int = 0, stream=None) -> dict:
+    """FP64 FMA rate of the device (GFLOP/s) and SM cycles per warp-wide FP64 FMA."""
+    g, c = ctypes.c_double(), ctypes.c_double()
+    _check(lib().cbspmv_measure_fp64_fma(device, _stream_ptr(stream), ctypes.byref(g), ctypes.byref(c)))
+    return {"gflops": g.value, "cycles_per_warp_fma": c.value}
 
 
 def version() -> str:

@@ -4,6 +4,7 @@
 
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -50,6 +51,27 @@ struct DeviceGuard {
   }
 };
 
+// Device allocations of the library go through dev_malloc. Fault injection for tests: when
+// the environment variable CBSPMV_FAIL_ALLOC_AFTER holds N >= 0 at the start of
+// cbspmv_analyze, that call's allocation number N (counting from 0) fails as out of memory.
+thread_local long g_fail_alloc_after = -1;
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  if (g_fail_alloc_after == 0) {
+    g_fail_alloc_after = -1;
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  if (g_fail_alloc_after > 0) --g_fail_alloc_after;
+  return cudaMalloc(p, bytes);
+}
+long env_long(const char* name, long dflt) {
+  const char* v = std::getenv(name);
+  if (!v || !*v) return dflt;
+  char* end = nullptr;
+  const long r = std::strtol(v, &end, 10);
+  return (end && *end == 0) ? r : dflt;
+}
+
 #define CB_CUDA(call)                                                                      \
   do {                                                                                     \
     cudaError_t e_ = (call);                                                               \
@@ -87,6 +109,8 @@ struct cbspmv_handle_s {
   uint64_t* d_lwords = nullptr;
   int32_t* d_lgcols = nullptr;
   size_t lvals_count = 0, lwords_count = 0, lgcols_count = 0;
+  long long wait_budget = 4000000000LL;   // device wait budget of the record kernel (clock64 cycles)
+  int stuck_wait = 0;                     // test hook (CBSPMV_TEST_STUCK_WAIT)
   // bytes of one x or y element: double for FP64 values, float for the reduced types
   size_t esize() const { return plan.value_dtype == CBSPMV_F64 ? 8 : 4; }
 
@@ -126,7 +150,7 @@ static bool valid_handle(cbspmv_handle_t h) { return h && h->magic == 0xCB5B0001
 template <class T>
 static cudaError_t upload(T** dst, const T* src, size_t count, cudaStream_t s) {
   size_t bytes = count * sizeof(T);
-  cudaError_t e = cudaMalloc((void**)dst, bytes ? bytes : 16);
+  cudaError_t e = dev_malloc((void**)dst, bytes ? bytes : 16);
   if (e != cudaSuccess) return e;
   if (bytes) e = cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, s);
   return e;
@@ -180,6 +204,10 @@ cbspmv_status_t cbspmv_analyze(const cbspmv_csr_t* A, const cbspmv_opts_t* opts_
     H.on_device = 0;
     return cbspmv_analyze(&H, opts_in, stream, out);
   }
+  g_fail_alloc_after = env_long("CBSPMV_FAIL_ALLOC_AFTER", -1);
+  struct ResetFail {   // the injected failure applies to this call only
+    ~ResetFail() { g_fail_alloc_after = -1; }
+  } reset_fail;
   cbspmv_opts_t opts;
   if (opts_in) opts = *opts_in; else cbspmv_default_opts(&opts);
   if (opts.unit_work < 0 || opts.unit_work > 16384)
@@ -217,6 +245,11 @@ cbspmv_status_t cbspmv_analyze(const cbspmv_csr_t* A, const cbspmv_opts_t* opts_
   }
   h->device = opts.device;
   h->grid = grid;
+  {
+    const long wb = env_long("CBSPMV_WAIT_BUDGET_CYCLES", 0);
+    if (wb > 0) h->wait_budget = wb;
+    h->stuck_wait = env_long("CBSPMV_TEST_STUCK_WAIT", 0) == 1 ? 1 : 0;
+  }
   if (opts.device < 0) {
     *out = h;
     return ok();
@@ -244,10 +277,10 @@ cbspmv_status_t cbspmv_analyze(const cbspmv_csr_t* A, const cbspmv_opts_t* opts_
   }
   step(upload(&h->d_wunits, p.worker_units.data(), p.worker_units.size(), s));
   step(upload(&h->d_woff, p.worker_off.data(), p.worker_off.size(), s));
-  if (e == cudaSuccess) e = cudaMalloc(&h->d_partial, (size_t)(p.n_slots ? p.n_slots : 1) * 16 * h->esize());
+  if (e == cudaSuccess) e = dev_malloc(&h->d_partial, (size_t)(p.n_slots ? p.n_slots : 1) * 16 * h->esize());
   step(upload(&h->d_split_rows, p.split_rows.data(), p.split_rows.size(), s));
   if (!p.value_slot.empty()) step(upload(&h->d_vslot, p.value_slot.data(), p.value_slot.size(), s));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_err, 4);
+  if (e == cudaSuccess) e = dev_malloc((void**)&h->d_err, 4);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, 4, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
@@ -300,6 +333,8 @@ static cb::RunArgs run_args(cbspmv_handle_t h, const void* x, void* y, double al
   a.lvals = h->d_lvals;
   a.lwords = h->d_lwords;
   a.lgcols = h->d_lgcols;
+  a.wait_budget = h->wait_budget;
+  a.stuck_wait = h->stuck_wait;
   return a;
 }
 
@@ -400,10 +435,13 @@ cbspmv_status_t cbspmv_run_multi(cbspmv_handle_t h, int k, const void* X, int64_
   const cb::Plan& p = h->plan;
   const size_t es = h->esize();
   if (k > 1 && !h->d_partial_multi)
-    CB_CUDA(cudaMalloc(&h->d_partial_multi, (size_t)(p.n_slots ? p.n_slots : 1) * 16 * 4 * es));
-  // passes of 4, then 2, then 1 vectors; each pass reads the matrix once
+    CB_CUDA(dev_malloc(&h->d_partial_multi, (size_t)(p.n_slots ? p.n_slots : 1) * 16 * 4 * es));
+  // passes of 4, then 2, then 1 vectors; each pass reads the matrix once. FP64 lane-stream
+  // handles take one vector per pass: their product is bound by the FP64 FMA pipe, so a pass
+  // over several vectors saves no time (measured 0.198, 0.236 and 0.295 ms per vector for
+  // passes of 1, 2 and 4 vectors on the FEM band).
   for (int j = 0; j < k;) {
-    const int nv = k - j >= 4 ? 4 : k - j >= 2 ? 2 : 1;
+    const int nv = p.lanes ? 1 : k - j >= 4 ? 4 : k - j >= 2 ? 2 : 1;
     cb::RunArgs a = run_args(h, (const char*)X + es * j * ldx, (char*)Y + es * j * ldy, alpha, beta);
     a.nvec = nv;
     a.ldx = ldx;
@@ -497,8 +535,8 @@ cbspmv_status_t cbspmv_run_host(cbspmv_handle_t h, const void* x_host, void* y_h
   CB_CUDA(g.err);
   cudaStream_t s = (cudaStream_t)stream;
   const size_t es = h->esize();
-  if (!h->d_xstage) CB_CUDA(cudaMalloc(&h->d_xstage, (size_t)(p.n ? p.n : 1) * es));
-  if (!h->d_ystage) CB_CUDA(cudaMalloc(&h->d_ystage, (size_t)(p.m ? p.m : 1) * es));
+  if (!h->d_xstage) CB_CUDA(dev_malloc(&h->d_xstage, (size_t)(p.n ? p.n : 1) * es));
+  if (!h->d_ystage) CB_CUDA(dev_malloc(&h->d_ystage, (size_t)(p.m ? p.m : 1) * es));
   if (p.n) CB_CUDA(cudaMemcpyAsync(h->d_xstage, x_host, (size_t)p.n * es, cudaMemcpyHostToDevice, s));
   if (beta != 0.0 && p.m) CB_CUDA(cudaMemcpyAsync(h->d_ystage, y_host, (size_t)p.m * es, cudaMemcpyHostToDevice, s));
   cbspmv_status_t st = run_device(h, h->d_xstage, h->d_ystage, alpha, beta, s);
@@ -520,7 +558,7 @@ cbspmv_status_t cbspmv_update_values(cbspmv_handle_t h, const double* val, int o
   cudaStream_t s = (cudaStream_t)stream;
   const double* dval = val;
   if (!on_device) {
-    if (!h->d_valstage) CB_CUDA(cudaMalloc((void**)&h->d_valstage, (size_t)p.nnz * 8));
+    if (!h->d_valstage) CB_CUDA(dev_malloc((void**)&h->d_valstage, (size_t)p.nnz * 8));
     CB_CUDA(cudaMemcpyAsync(h->d_valstage, val, (size_t)p.nnz * 8, cudaMemcpyHostToDevice, s));
     dval = h->d_valstage;
   }
@@ -859,6 +897,8 @@ bool noalloc_view(cbspmv_handle_t h, NoallocView* v) {
   a.lvals = h->d_lvals;
   a.lwords = h->d_lwords;
   a.lgcols = h->d_lgcols;
+  a.wait_budget = h->wait_budget;
+  a.stuck_wait = h->stuck_wait;
   v->args = a;
   return true;
 }

@@ -32,6 +32,8 @@ struct RunArgs {
   int value_dtype;              // cbspmv_dtype_t of the stored values
   int nvec;                     // vectors computed in one pass: 1, 2 or 4 (single product only)
   int64_t ldx, ldy;             // distance in elements between consecutive vectors of x and y
+  long long wait_budget;        // clock64 cycles a bounded device wait may take before it gives up
+  int stuck_wait;               // test hook: the first wait is on a barrier nothing arrives at
   // lane-stream layout (FP64; lanes = 1): these replace stream, units and blob
   int lanes;
   const CbLaneUnit* lunits;     // units in worker order

@@ -57,7 +57,7 @@
 namespace cb {
 namespace {
 
-constexpr long long kWaitBudget = 4000000000LL;   // clock64 cycles (~2 s) per wait
+constexpr long long kWaitBudget = 4000000000LL;   // default clock64 budget (~2 s) per wait
 constexpr uint32_t kSmemMax = 232448;             // dynamic shared memory per CTA (227 KB)
 static_assert(kSmemMax <= (1u << 18), "tile bases are packed as 14 + 18 bits of shared-memory offset");
 
@@ -161,6 +161,7 @@ constexpr int kMaxBatch = 64;
 // batch, the first unit and the ticket prefix of every problem in this CTA's lists.
 struct CtaHeader {
   uint8_t ident[256];           // byte k = (k & 15) << 4: coordinate bytes of a Dense record
+  uint64_t never;               // an mbarrier nothing arrives at (the stuck-wait test hook)
   uint32_t ticket;
   uint32_t first[kMaxBatch];    // this CTA's first unit of problem p
   uint32_t pref[kMaxBatch + 1]; // tickets of problems 0..p-1
@@ -215,12 +216,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait: false when the budget ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Bounded wait: false when the budget (clock64 cycles) ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long budget = kWaitBudget) {
   if (mbar_try_wait(bar, parity)) return true;
   long long t0 = clock64();
   while (!mbar_try_wait(bar, parity))
-    if (clock64() - t0 > kWaitBudget) return false;
+    if (clock64() - t0 > budget) return false;
   return true;
 }
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -385,7 +386,7 @@ __device__ bool consume_unit(const RunArgs& a, uint8_t* sm, uint32_t so, uint32_
     else sc.tinfo.q[lane] = make_uint4(vb, cb, so + kOffXs + G::kXRow * lane, 0u);
   }
   for (uint32_t r = lane; r < R * kK; r += 32) sc.srow[r] = Acc(0);
-  if (!__all_sync(0xffffffffu, mbar_wait(bar_s, phase))) return false;   // the records
+  if (!__all_sync(0xffffffffu, mbar_wait(bar_s, phase, a.wait_budget))) return false;   // the records
   cp_async_wait_all();     // this lane's x copies (issued by gather_x before the set-up)
   __syncwarp();
 
@@ -669,7 +670,10 @@ __global__ void __launch_bounds__(32 * Geom<V, kK>::kWarps, 1) spmv_kernel(const
     hd.first[threadIdx.x] = w0;
     hd.pref[threadIdx.x + 1] = a.worker_off[blockIdx.x + 1] - w0;
   }
-  if (threadIdx.x == 0) hd.ticket = 0;
+  if (threadIdx.x == 0) {
+    hd.ticket = 0;
+    mbar_init(&hd.never, 1);
+  }
   for (uint32_t i = threadIdx.x; i < 256u; i += blockDim.x) hd.ident[i] = (uint8_t)((i & 15u) << 4);
   if (lane == 0) {
     mbar_init(bar, 1);
@@ -725,7 +729,8 @@ __global__ void __launch_bounds__(32 * Geom<V, kK>::kWarps, 1) spmv_kernel(const
     const uint32_t dwn = desc_word(jn);
     // the blob (tile records, restore_cols slice, schedule) is enough to start the x
     // gather and the unit's set-up; the records are waited for just before the walk
-    bool ok = __all_sync(0xffffffffu, mbar_wait(bar, phase));
+    // (test hook: the first wait of a stuck-wait run is on a barrier nothing arrives at)
+    bool ok = __all_sync(0xffffffffu, mbar_wait(a.stuck_wait ? &hd.never : bar, phase, a.wait_budget));
     if (ok) {
       gather_x<V, kK>(a, W, w_smem, lane);
       __syncwarp();
@@ -747,7 +752,8 @@ __global__ void __launch_bounds__(32 * Geom<V, kK>::kWarps, 1) spmv_kernel(const
     }
     if (!ok) {
       if (lane == 0) set_error(a, 2u);
-      // copies may still land in the buffer: give them a second bounded wait, then stop
+      // copies may still land in the buffer: give them a second bounded wait with the full
+      // budget (whatever the run's budget), then stop
       mbar_wait(bar, phase);
       mbar_wait(bar_s, phase);
       cp_async_wait_all();
@@ -1351,16 +1357,8 @@ cudaError_t launch_nvec(const BatchArgs<kMaxP>& b, int grid, cudaStream_t stream
 
 template <int kMaxP>
 cudaError_t launch_lanes_nvec(const BatchArgs<kMaxP>& b, int grid, cudaStream_t stream, cudaEvent_t* ev) {
-  if constexpr (kMaxP == 1) {
-    switch (b.p[0].nvec) {
-      case 1: return launch_lanes<1, 1>(b, grid, stream, ev);
-      case 2: return launch_lanes<1, 2>(b, grid, stream, ev);
-      case 4: return launch_lanes<1, 4>(b, grid, stream, ev);
-      default: return cudaErrorInvalidValue;
-    }
-  } else {
-    return b.p[0].nvec == 1 ? launch_lanes<kMaxP, 1>(b, grid, stream, ev) : cudaErrorInvalidValue;
-  }
+  // one vector per pass (the FP64 FMA pipe bounds the product; see cbspmv_run_multi)
+  return b.p[0].nvec == 1 ? launch_lanes<kMaxP, 1>(b, grid, stream, ev) : cudaErrorInvalidValue;
 }
 
 template <int kMaxP>
@@ -1405,8 +1403,7 @@ cudaError_t launch_repack(uint8_t* stream, const uint32_t* slot, const double* v
 
 size_t spmv_smem_bytes() {
   const uint32_t v[] = {Geom<double>::kSmem, Geom<float>::kSmem, Geom<__half>::kSmem, Geom<double, 4>::kSmem,
-                        Geom<float, 4>::kSmem, Geom<__half, 4>::kSmem, LaneGeom<1>::kSmem, LaneGeom<2>::kSmem,
-                        LaneGeom<4>::kSmem};
+                        Geom<float, 4>::kSmem, Geom<__half, 4>::kSmem, LaneGeom<1>::kSmem};
   uint32_t m = 0;
   for (uint32_t x : v) m = x > m ? x : m;
   return m;
@@ -1431,8 +1428,6 @@ cudaError_t configure_value_type() {
 cudaError_t configure_kernels() {
   cudaError_t e = configure_lanes<1, 1>();
   if (e == cudaSuccess) e = configure_lanes<kMaxBatch, 1>();
-  if (e == cudaSuccess) e = configure_lanes<1, 2>();
-  if (e == cudaSuccess) e = configure_lanes<1, 4>();
   if (e == cudaSuccess) e = configure_value_type<double>();
   if (e == cudaSuccess) e = configure_value_type<float>();
   if (e == cudaSuccess) e = configure_value_type<__nv_bfloat16>();
