@@ -139,8 +139,10 @@ typedef struct {
   int64_t lane_layout;             /* 1: FP64 lane-stream layout (see record_layout), 0: records */
 } cbspmv_stats_t;
 
-/* Fills *opts with the paper's settings: th0 0.15, th1 32, th2 128, col_agg -1,
- * FP64 values, default unit size, load balance on, device 0. */
+/* Fills *opts with the paper's settings: th0 0.15 (Sec. 3.3.1), th1 32 and th2 128
+ * (Sec. 3.3.2), col_agg -1 (the paper's rule), FP64 values (its evaluation, Sec. 4.1),
+ * default unit size, load balance on (Sec. 3.4), device 0. Errors: CBSPMV_ERR_INVALID
+ * (NULL). */
 cbspmv_status_t cbspmv_default_opts(cbspmv_opts_t* opts);
 
 /* Analyses a CSR matrix (Sec. 3 overview; Sec. 3.1-3.4): validation, 16x16 tiling, the
@@ -168,7 +170,8 @@ cbspmv_status_t cbspmv_analyze(const cbspmv_csr_t* A, const cbspmv_opts_t* opts,
 cbspmv_status_t cbspmv_run(cbspmv_handle_t h, const void* x, void* y, double alpha, double beta,
                            void* stream);
 
-/* The same product end to end from host memory: copies x (n values of the handle's
+/* The product of Sec. 3.5 end to end from host memory (the paper times the kernel alone;
+ * this is the call a host-side user makes): copies x (n values of the handle's
  * vector type) to the device, runs, copies y back (m values; read first when beta != 0),
  * then synchronises the stream. x_host / y_host may be pageable or pinned. Uses staging
  * buffers owned by the handle (allocated on first use). */
@@ -192,7 +195,9 @@ cbspmv_status_t cbspmv_run_host(cbspmv_handle_t h, const void* x_host, void* y_h
 cbspmv_status_t cbspmv_run_multi(cbspmv_handle_t h, int k, const void* X, int64_t ldx, void* Y,
                                  int64_t ldy, double alpha, double beta, void* stream);
 
-/* Analyses count matrices with the same options (cbspmv_analyze on each of A[0..count)).
+/* Batched analysis (the paper analyses one matrix; this is the many-matrix form of
+ * cbspmv_analyze, Sec. 3): count matrices with the same options (cbspmv_analyze on each of
+ * A[0..count)).
  * out: array of count handles, all set to NULL first. On failure every handle created by
  * the call is destroyed, out[] stays NULL and the message names the failing matrix.
  * count = 0 does nothing. Errors: those of cbspmv_analyze, CBSPMV_ERR_INVALID for
@@ -201,7 +206,8 @@ cbspmv_status_t cbspmv_analyze_batched(int count, const cbspmv_csr_t* A,
                                        const cbspmv_opts_t* opts, void* stream,
                                        cbspmv_handle_t* out);
 
-/* Runs count independent products on one stream: for problem i,
+/* Batched product (the paper runs one product per launch; this is the many-matrix form of
+ * the product of Sec. 3.5): count independent products on one stream; for problem i,
  * Y[i] = alpha[i] * A_i * X[i] + beta[i] * Y[i] with k[i] right-hand sides stored
  * column-major and packed (leading dimensions n_i and m_i); k may be NULL (one vector
  * each). Every problem's arguments are checked before any work is enqueued; a failing
@@ -243,10 +249,14 @@ cbspmv_status_t cbspmv_run_noalloc(cbspmv_handle_t h, const void* x, void* y, do
  * pointers: replays read the current contents of X and overwrite Y. The handles must
  * outlive the graph. Errors: those of cbspmv_run_batched, CBSPMV_ERR_CUDA. */
 typedef struct cbspmv_graph_s* cbspmv_graph_t;
+/* Capture (no counterpart in the paper). */
 cbspmv_status_t cbspmv_graph_create(int count, const cbspmv_handle_t* h, const int* k,
                                     const void* const* X, void* const* Y, const double* alpha,
                                     const double* beta, cbspmv_graph_t* out);
+/* Replays the captured products on `stream` (no counterpart in the paper). Errors:
+ * CBSPMV_ERR_INVALID (invalid graph), CBSPMV_ERR_CUDA. */
 cbspmv_status_t cbspmv_graph_launch(cbspmv_graph_t g, void* stream);
+/* Frees the graph (no counterpart in the paper); NULL is accepted. */
 cbspmv_status_t cbspmv_graph_destroy(cbspmv_graph_t g);
 
 /* ---- Autotuned analysis ------------------------------------------------------------------
@@ -264,6 +274,7 @@ typedef struct {
   double tried_ms[16];
   int tried_unit_work[16], tried_col_agg[16], tried_th1[16], tried_th2[16];
 } cbspmv_tune_report_t;
+/* Tuned analysis: the heuristics of Sec. 3.3 searched by timing (the paper fixes them). */
 cbspmv_status_t cbspmv_analyze_tuned(const cbspmv_csr_t* A, const cbspmv_opts_t* base,
                                      void* stream, int reps, cbspmv_handle_t* out,
                                      cbspmv_tune_report_t* report);
@@ -359,35 +370,42 @@ typedef struct {
   int64_t max_inflight_seen, arena_used_max, arena_capacity, queued, inflight;
 } cbspmv_server_stats_t;
 
-/* Defaults: device 0, 4 GiB budget, 64 in flight, BF16 inner values, inner_tol 1e-4,
- * 2000 inner iterations, 30 refinements. */
+/* Server defaults (no counterpart in the paper): device 0, 4 GiB budget, 64 in flight,
+ * BF16 inner values, inner_tol 1e-4, 2000 inner iterations, 30 refinements. */
 cbspmv_status_t cbspmv_server_default_opts(cbspmv_server_opts_t* opts);
-/* Creates a server (allocates the memory budget, a stream and the engine thread).
+/* Creates a server (no counterpart in the paper; the repeated products that amortise the
+ * analysis, Sec. 4.5): allocates the memory budget, a stream and the engine thread.
  * Errors: CBSPMV_ERR_INVALID (options), CBSPMV_ERR_OOM, CBSPMV_ERR_CUDA. */
 cbspmv_status_t cbspmv_server_create(const cbspmv_server_opts_t* opts, cbspmv_server_t* out);
-/* Analyses A (opts as cbspmv_analyze; device and value type are the server's) with FP64
+/* Registers a matrix with the server (the analysis of Sec. 3, kept resident): analyses A
+ * (opts as cbspmv_analyze; device and value type are the server's) with FP64
  * values and, for a square A, also with cg_inner_dtype values; the matrices stay
  * resident until cbspmv_server_destroy. *matrix_id names it in requests (at most 1024). */
 cbspmv_status_t cbspmv_server_register(cbspmv_server_t s, const cbspmv_csr_t* A,
                                        const cbspmv_opts_t* opts, int* matrix_id);
-/* Queues a request; *ticket identifies it. Errors: CBSPMV_ERR_INVALID (unknown matrix,
+/* Queues a request (no counterpart in the paper); *ticket identifies it. Errors: CBSPMV_ERR_INVALID (unknown matrix,
  * NULL buffers, CG on a non-square matrix, tol <= 0), CBSPMV_ERR_OOM (the request's device
  * workspace is larger than the whole memory budget, so it could never be admitted; nothing
  * is queued), CBSPMV_ERR_CUDA (engine stopped). */
 cbspmv_status_t cbspmv_server_submit(cbspmv_server_t s, const cbspmv_request_t* req,
                                      uint64_t* ticket);
-/* Non-blocking: *res = the request's state (res->done = 0 while it runs). A finished
+/* Polls a request (no counterpart in the paper). Non-blocking: *res = the request's state (res->done = 0 while it runs). A finished
  * request's ticket is released by the call that reports it done. */
 cbspmv_status_t cbspmv_server_poll(cbspmv_server_t s, uint64_t ticket, cbspmv_result_t* res);
-/* Waits up to timeout_ms for the request; CBSPMV_ERR_TIMEOUT if it is still running (the
+/* Waits for a request (no counterpart in the paper): up to timeout_ms; CBSPMV_ERR_TIMEOUT if it is still running (the
  * ticket stays valid). */
 cbspmv_status_t cbspmv_server_wait(cbspmv_server_t s, uint64_t ticket, int timeout_ms,
                                    cbspmv_result_t* res);
+/* Counters of the server (no counterpart in the paper): requests submitted, admitted and
+ * completed, engine ticks and launches, the most requests in flight and the arena use.
+ * Errors: CBSPMV_ERR_INVALID (invalid server or NULL stats). */
 cbspmv_status_t cbspmv_server_get_stats(cbspmv_server_t s, cbspmv_server_stats_t* stats);
-/* Stops the engine (requests still queued or in flight are abandoned), frees everything. */
+/* Stops the engine (requests still queued or in flight are abandoned), frees everything
+ * (no counterpart in the paper). NULL is accepted. */
 cbspmv_status_t cbspmv_server_destroy(cbspmv_server_t s);
 
-/* Reads the handle's device error word (set by bounded device-side waits that gave up)
+/* Failure detection (no counterpart in the paper): reads the handle's device error word
+ * (set by bounded device-side waits that gave up)
  * and clears it: CBSPMV_OK or CBSPMV_ERR_TIMEOUT. Synchronises `stream`. The record-layout
  * kernel waits for its own bulk copies with a budget of 4e9 SM cycles (about 2 s), or the
  * number in the environment variable CBSPMV_WAIT_BUDGET_CYCLES when the handle was analysed;
@@ -398,10 +416,13 @@ cbspmv_status_t cbspmv_server_destroy(cbspmv_server_t s);
  * such wait. */
 cbspmv_status_t cbspmv_check_device(cbspmv_handle_t h, void* stream);
 
-/* Reconstructs the CSR matrix from the handle's device-resident blocked format
- * (bit-exact round trip of row_ptr, col_idx and the value bits for FP64 values; for the
- * reduced types, the stored values widened exactly to double).
- * Host output arrays of m+1, nnz, nnz entries. Synchronous. */
+/* Reconstructs the CSR matrix from the handle's device-resident blocked format: the
+ * inverse of the packing of Sec. 3.2-3.3, which loses no entry (bit-exact round trip of
+ * row_ptr, col_idx and the value bits for FP64 values; for the reduced types, the stored
+ * values widened exactly to double). Host output arrays of m+1, nnz, nnz entries; the
+ * caller owns them. Synchronous (reads the device arrays back). Errors:
+ * CBSPMV_ERR_INVALID (invalid handle, NULL arrays, an inconsistent layout),
+ * CBSPMV_ERR_CUDA. */
 cbspmv_status_t cbspmv_export_csr(cbspmv_handle_t h, int64_t* row_ptr, int32_t* col_idx,
                                   double* val);
 
@@ -414,16 +435,26 @@ cbspmv_status_t cbspmv_export_blocked(cbspmv_handle_t h, int32_t* blk_row, int32
                                       int32_t* nnz_per_blk, uint8_t* type_per_blk,
                                       int64_t* cols_offset, int32_t* restore_cols);
 
+/* Statistics of the analysis into *stats (host struct, caller-owned): the storage model
+ * of Sec. 4.4.1 (CB, CSR and 16x16 BSR bytes), the sub-block nnz histogram of Fig. 3, the
+ * per-thread-block load spread of Fig. 4 and Algorithm 2, the format mix of Sec. 3.3.2,
+ * the column-aggregation decision of Sec. 3.3.1, the host analysis time of Sec. 4.5, and
+ * this library's units, workers, bytes model and FMA slot count. No device access.
+ * Errors: CBSPMV_ERR_INVALID (invalid handle or NULL stats). */
 cbspmv_status_t cbspmv_get_stats(cbspmv_handle_t h, cbspmv_stats_t* stats);
 
-/* Frees the handle and all its device memory (synchronises the device first).
- * NULL is accepted. */
+/* Frees the handle and all its device memory (synchronises the device first); the paper
+ * has no counterpart (handle lifetime of this library). NULL is accepted.
+ * Errors: CBSPMV_ERR_INVALID (a pointer that is not a live handle). */
 cbspmv_status_t cbspmv_destroy(cbspmv_handle_t h);
 
-/* Message of the last failed call on this host thread ("" if none). */
+/* Message of the last failed call on this host thread ("" if none); the paper has no
+ * counterpart (error reporting of this library). The string is owned by the library and
+ * valid until the thread's next call. */
 const char* cbspmv_last_error(void);
 
-/* Library version string, including the run kernel's revision ("run kernel rev N"). */
+/* Library version string, including the run kernel's revision ("run kernel rev N"); the
+ * paper has no counterpart. Owned by the library. */
 const char* cbspmv_version(void);
 
 #ifdef __cplusplus
