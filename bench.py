@@ -224,6 +224,43 @@ def multi_rhs_bench(M, A, x, vec, stream, ks=(1, 8, 32), reps=20):
     return out
 
 
+def spmm_bench(bd, A, x, stream, ks=(1, 8, 32), reps=20):
+    """Tensor-core multi-vector product (cbspmv_spmm) on a BF16 copy of the matrix: X (n x k)
+    and Y (m x k) row-major FP32. Returns per k the time, GFLOP/s (2 nnz k / t) and the HBM
+    fraction of its bytes model (values and coordinates, sub-block metadata, restore_cols,
+    X read once, Y written once), beside the BF16 single-vector product of the record kernel."""
+    import torch
+    peak, _ = load_peaks()
+    out = {"api": "cbspmv_spmm (mma.sync.m16n8k16 BF16 x BF16 -> FP32, x split into 3 BF16 parts)",
+           "values": "bf16", "results": []}
+    with bd.BlockedMatrix(A, value_dtype="bf16", plain_records=True, stream=stream) as M:
+        st = M.stats()
+        mat_bytes = A.nnz * 3 + st["n_tiles"] * 21 + 4 * st["restore_cols_len"]
+        xd = torch.from_numpy(x.astype(np.float32)).cuda()
+        yd = torch.empty(A.m, dtype=torch.float32, device="cuda")
+        kt = M.time_kernels(xd, yd, 200, stream=stream)
+        ms1 = kt["ms_main"] + kt["ms_combine"]
+        out["spmv_bf16_k1"] = {"ms": round(ms1, 4), "gflops": round(2.0 * A.nnz / (ms1 * 1e-3) / 1e9, 1)}
+        for k in ks:
+            X = torch.from_numpy(np.tile(x.astype(np.float32)[:, None], (1, k))).cuda()
+            Y = torch.empty((A.m, k), dtype=torch.float32, device="cuda")
+            for _ in range(3):
+                M.spmm(X, Y, stream=stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                M.spmm(X, Y, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            byts = mat_bytes + 4 * k * (A.n + A.m)
+            out["results"].append({"k": k, "ms": round(ms, 4), "gflops": round(2.0 * A.nnz * k / (ms * 1e-3) / 1e9, 1),
+                                   "vs_spmv_bf16_k1": round(ms1 * k / ms, 2),
+                                   "hbm_frac": round(byts / (ms * 1e-3) / 1e9 / peak, 4)})
+            del X, Y
+    return out
+
+
 # The ablation of Sec. 4.4 (Fig. 12) as analysis options: I = intra-block data aggregation
 # only (packed records, no column aggregation, one sub-block format: COO below 256 entries),
 # II = + column aggregation and format selection (the paper's th0, th1, th2), full = II +
@@ -457,6 +494,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-multi", action="store_true", help="skip the k right-hand-side measurement")
     ap.add_argument("--no-ablation", action="store_true", help="skip the ablation (Sec. 4.4) measurement")
+    ap.add_argument("--no-spmm", action="store_true", help="skip the tensor-core multi-vector measurement")
     ap.add_argument("--serve-full", action="store_true",
                     help="serving measurement on the full pool (17 Laplacians, 15 R-MAT, 10,000 requests)")
     ap.add_argument("--traffic-bytes", type=float, default=None,
@@ -541,6 +579,7 @@ def main():
         del flush
         y_ours = yd.cpu().numpy().astype(np.float64)
         multi = multi_rhs_bench(M, A, x, vec, stream) if not args.no_multi else None
+        spmm = spmm_bench(bd, A, x, stream) if not args.no_spmm else None
         abl = ablation_bench(bd, A, x, vec, args.dtype, stream) if not args.no_ablation else None
         M.check_device(stream)
         sms = torch.cuda.get_device_properties(local).multi_processor_count
@@ -646,7 +685,10 @@ def main():
         if cus:
             line["cusparse_csr"] = cus
         if multi:
-            line["multi_rhs"] = {"api": "cbspmv_run_multi (passes of 4 vectors)", "results": multi}
+            line["multi_rhs"] = {"api": "cbspmv_run_multi (FP64: one column per pass; reduced types: passes "
+                                        "of 4 vectors)", "results": multi}
+        if spmm:
+            line["multi_rhs_tensor"] = spmm
         if abl:
             line["ablation"] = abl
         if not args.no_serve and ws == 1:

@@ -100,7 +100,9 @@ typedef struct {
   int keep_value_map;       /* 1: record each entry's value slot (4 bytes per entry on the
                                device) so cbspmv_update_values can re-pack new values */
   int record_layout;        /* 1: FP64 values in the record layout (see above) */
-  int reserved[6];
+  int plain_records;        /* 1: every sub-block record keeps the layout of Sec. 3.2 (no
+                               values re-laid in load order): needed by cbspmv_spmm */
+  int reserved[5];
 } cbspmv_opts_t;
 
 /* Statistics of an analysed matrix. Byte counts follow the storage model of Sec. 4.4.1
@@ -194,6 +196,26 @@ cbspmv_status_t cbspmv_run_host(cbspmv_handle_t h, const void* x_host, void* y_h
  * misaligned arrays, overlap), CBSPMV_ERR_OOM, CBSPMV_ERR_CUDA. */
 cbspmv_status_t cbspmv_run_multi(cbspmv_handle_t h, int k, const void* X, int64_t ldx, void* Y,
                                  int64_t ldy, double alpha, double beta, void* stream);
+
+/* Y = alpha * A * X + beta * Y for k right-hand sides on the tensor cores (the multi-vector
+ * form of the product of Sec. 3.5; with k vectors each 16x16 sub-block of Sec. 3.1 becomes
+ * a contraction of shape 16 x 16 x k). X: device array, row-major n x k with leading
+ * dimension ldx >= k (element (i, j) at X[i * ldx + j]); Y: row-major m x k, ldy >= k; FP32
+ * (the vector type of BF16 handles), 4-byte aligned, not overlapping. Requires a device
+ * handle with BF16 values analysed with opts.plain_records = 1 (CBSPMV_ERR_UNSUPPORTED
+ * otherwise; other value types use cbspmv_run_multi). Each sub-block is expanded to a
+ * zero-filled 16x16 BF16 tile and multiplied with mma.sync.m16n8k16 (BF16 inputs, FP32
+ * accumulation); every x is split exactly into three BF16 parts (|x - sum| <= 2^-25 |x|) so
+ * the products keep FP32 accuracy; a row's result has error at most gamma_{6r + 16} with
+ * u = 2^-23 times sum_j |a_ij x_j| (r = stored entries of the row), see the design notes.
+ * Up to 32 columns per launch (the matrix is read once per 32 columns), plus one small
+ * launch that adds the segments of block rows with more than 64 sub-blocks. The first call
+ * builds the segment list and allocates a partial-sum buffer (owned by the handle). Like
+ * Dense zero fill, a non-finite x reaches every row of a sub-block holding its column.
+ * Asynchronous on `stream`. Errors: CBSPMV_ERR_INVALID (arguments), CBSPMV_ERR_UNSUPPORTED,
+ * CBSPMV_ERR_OOM, CBSPMV_ERR_CUDA. */
+cbspmv_status_t cbspmv_spmm(cbspmv_handle_t h, int k, const void* X, int64_t ldx, void* Y,
+                            int64_t ldy, double alpha, double beta, void* stream);
 
 /* Batched analysis (the paper analyses one matrix; this is the many-matrix form of
  * cbspmv_analyze, Sec. 3): count matrices with the same options (cbspmv_analyze on each of

@@ -38,7 +38,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("th0", ctypes.c_double), ("th1", ctypes.c_int), ("th2", ctypes.c_int),
                 ("col_agg", ctypes.c_int), ("value_dtype", ctypes.c_int), ("unit_work", ctypes.c_int),
                 ("load_balance", ctypes.c_int), ("device", ctypes.c_int), ("keep_value_map", ctypes.c_int),
-                ("record_layout", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+                ("record_layout", ctypes.c_int), ("plain_records", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
 
 
 class Stats(ctypes.Structure):
@@ -129,6 +129,7 @@ SIGNATURES = {
     "cbspmv_server_get_stats": [_P, ctypes.POINTER(ServerStats)],
     "cbspmv_server_destroy": [_P],
     "cbspmv_measure_fp64_fma": [_I, _P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
+    "cbspmv_spmm": [_P, _I, _P, _I64, _P, _I64, _D, _D, _P],
     "cbspmv_last_error": [],
     "cbspmv_version": [],
 }
@@ -220,7 +221,8 @@ def _csr_struct(A):
 
 
 def _make_opts(th0=0.15, th1=32, th2=128, col_agg=-1, value_dtype="f64", unit_work=0,
-               load_balance=True, device=0, keep_value_map=False, record_layout=False) -> Opts:
+               load_balance=True, device=0, keep_value_map=False, record_layout=False,
+               plain_records=False) -> Opts:
     o = default_opts()
     o.th0, o.th1, o.th2, o.col_agg = th0, th1, th2, col_agg
     o.value_dtype = DTYPES[value_dtype]
@@ -229,6 +231,7 @@ def _make_opts(th0=0.15, th1=32, th2=128, col_agg=-1, value_dtype="f64", unit_wo
     o.device = device
     o.keep_value_map = 1 if keep_value_map else 0
     o.record_layout = 1 if record_layout else 0
+    o.plain_records = 1 if plain_records else 0
     return o
 
 
@@ -251,13 +254,13 @@ class BlockedMatrix:
 
     def __init__(self, A, *, th0=0.15, th1=32, th2=128, col_agg=-1, value_dtype="f64",
                  unit_work=0, load_balance=True, device=0, stream=None, keep_value_map=False,
-                 record_layout=False):
+                 record_layout=False, plain_records=False):
         """A's arrays may be host arrays or CUDA torch tensors (device-resident input)."""
         self._h = ctypes.c_void_p(None)
         self.m, self.n = int(A.m), int(A.n)
         csr, _keep, self.nnz = _csr_struct(A)
         o = _make_opts(th0, th1, th2, col_agg, value_dtype, unit_work, load_balance, device, keep_value_map,
-                       record_layout)
+                       record_layout, plain_records)
         self.device = device
         self.value_dtype = value_dtype
         self.vec = "f64" if value_dtype == "f64" else "f32"
@@ -297,6 +300,19 @@ class BlockedMatrix:
         py, ldy = _dev_cols(Y, k, self.m, "Y", self.vec)
         _check(lib().cbspmv_run_multi(self._h, k, px, ldx, py, ldy, float(alpha), float(beta),
                                       _stream_ptr(stream)))
+        return Y
+
+    def spmm(self, X, Y, alpha: float = 1.0, beta: float = 0.0, stream=None):
+        """Y <- alpha*A*X + beta*Y on the tensor cores (BF16 handles analysed with
+        plain_records): X of shape (n, k), Y of shape (m, k), row-major float32 CUDA tensors
+        (row stride = leading dimension, unit column stride)."""
+        if X.dim() != 2 or Y.dim() != 2 or X.shape[1] != Y.shape[1] or X.shape[0] < self.n or Y.shape[0] < self.m:
+            raise ValueError("X must be (n, k) and Y (m, k)")
+        if X.stride(1) != 1 or Y.stride(1) != 1 or X.dtype != Y.dtype:
+            raise ValueError("X and Y must have unit column stride and one dtype")
+        k = int(X.shape[1])
+        _check(lib().cbspmv_spmm(self._h, k, X.data_ptr(), int(X.stride(0)), Y.data_ptr(), int(Y.stride(0)),
+                                 float(alpha), float(beta), _stream_ptr(stream)))
         return Y
 
     def time_kernels(self, x, y, reps: int, alpha: float = 1.0, beta: float = 0.0, stream=None) -> dict:

@@ -461,6 +461,7 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
   if (opts.col_agg < -1 || opts.col_agg > 1) { *msg = "col_agg must be -1, 0 or 1"; return CBSPMV_ERR_INVALID; }
   if (opts.keep_value_map != 0 && opts.keep_value_map != 1) { *msg = "keep_value_map must be 0 or 1"; return CBSPMV_ERR_INVALID; }
   if (opts.record_layout != 0 && opts.record_layout != 1) { *msg = "record_layout must be 0 or 1"; return CBSPMV_ERR_INVALID; }
+  if (opts.plain_records != 0 && opts.plain_records != 1) { *msg = "plain_records must be 0 or 1"; return CBSPMV_ERR_INVALID; }
   if (n_workers <= 0) { *msg = "no workers"; return CBSPMV_ERR_INVALID; }
   cbspmv_status_t st = validate(A, msg);
   if (st != CBSPMV_OK) return st;
@@ -721,7 +722,8 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
         // Direct descriptors where the chunks' columns are known per chunk: two fewer
         // dependent shared-memory loads per chunk for twice the descriptor bytes, and the
         // unit's values re-laid in load order (below).
-        if ((mode & (CB_MODE_ENTRY | CB_MODE_XSEQ)) && nch <= CB_DIRECT_MAX_CHUNKS) mode |= CB_MODE_DIRECT;
+        if ((mode & (CB_MODE_ENTRY | CB_MODE_XSEQ)) && nch <= CB_DIRECT_MAX_CHUNKS && !opts.plain_records)
+          mode |= CB_MODE_DIRECT;
         p.units[i].mode = mode;
         chunks_of[i] = nch;
         // descriptor rows: chunks of the longest run, rounded up to an even count because

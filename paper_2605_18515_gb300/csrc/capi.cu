@@ -2,6 +2,7 @@
 // kernel launches. All errors become status codes plus a thread-local message.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -14,6 +15,7 @@
 #include "cb_kernels.h"
 #include "cb_noalloc.h"
 #include "cb_plan.h"
+#include "cb_spmm.h"
 
 namespace {
 
@@ -109,6 +111,13 @@ struct cbspmv_handle_s {
   uint64_t* d_lwords = nullptr;
   int32_t* d_lgcols = nullptr;
   size_t lvals_count = 0, lwords_count = 0, lgcols_count = 0;
+  // tensor-core multi-vector product (cbspmv_spmm), built on first use
+  cb::SpmmSeg* d_spmm_segs = nullptr;
+  cb::SpmmSplit* d_spmm_splits = nullptr;
+  float* d_spmm_partial = nullptr;
+  uint32_t* d_spmm_counter = nullptr;
+  uint32_t spmm_nseg = 0, spmm_nsplit = 0;
+  bool spmm_ready = false;
   long long wait_budget = 4000000000LL;   // device wait budget of the record kernel (clock64 cycles)
   int stuck_wait = 0;                     // test hook (CBSPMV_TEST_STUCK_WAIT)
   // bytes of one x or y element: double for FP64 values, float for the reduced types
@@ -120,7 +129,8 @@ struct cbspmv_handle_s {
     cudaDeviceSynchronize();
     void* ptrs[] = {d_stream, d_tiles, d_rcols, d_units, d_blob, d_wunits, d_woff, d_partial, d_split_rows,
                     d_err, d_xstage, d_ystage, d_partial_multi, d_vslot, d_valstage,
-                    d_lunits, d_lvals, d_lwords, d_lgcols};
+                    d_lunits, d_lvals, d_lwords, d_lgcols,
+                    d_spmm_segs, d_spmm_splits, d_spmm_partial, d_spmm_counter};
     for (void* p : ptrs)
       if (p) cudaFree(p);
     d_stream = nullptr;
@@ -142,6 +152,11 @@ struct cbspmv_handle_s {
     d_lvals = nullptr;
     d_lwords = nullptr;
     d_lgcols = nullptr;
+    d_spmm_segs = nullptr;
+    d_spmm_splits = nullptr;
+    d_spmm_partial = nullptr;
+    d_spmm_counter = nullptr;
+    spmm_ready = false;
   }
 };
 
@@ -449,6 +464,110 @@ cbspmv_status_t cbspmv_run_multi(cbspmv_handle_t h, int k, const void* X, int64_
     if (nv > 1) a.partial = h->d_partial_multi;
     CB_CUDA(cb::launch_spmv(a, h->grid, (cudaStream_t)stream));
     j += nv;
+  }
+  return ok();
+}
+
+// Segments of the tensor-core product: every block row's sub-blocks in runs of at most
+// kSpmmSegTiles (block rows without sub-blocks still get a segment, which writes their y),
+// longest first; block rows cut into several segments get consecutive partial-sum slots.
+static constexpr uint32_t kSpmmSegTiles = 64;
+static cbspmv_status_t spmm_prepare(cbspmv_handle_t h, cudaStream_t s) {
+  const cb::Plan& p = h->plan;
+  std::vector<cb::SpmmSeg> segs;
+  std::vector<cb::SpmmSplit> splits;
+  uint32_t slot = 0;
+  size_t t = 0;
+  for (int64_t b = 0; b < p.nbr; ++b) {
+    const size_t t0 = t;
+    while (t < p.tiles.size() && p.tiles[t].brow == (uint32_t)b) ++t;
+    const uint32_t T = (uint32_t)(t - t0);
+    const uint32_t parts = T <= kSpmmSegTiles ? 1u : (T + kSpmmSegTiles - 1) / kSpmmSegTiles;
+    if (parts > 1) splits.push_back({(uint32_t)b, slot, parts, 0u});
+    for (uint32_t q = 0; q < parts; ++q) {
+      const uint32_t lo = (uint32_t)t0 + q * kSpmmSegTiles;
+      const uint32_t n = std::min<uint32_t>(kSpmmSegTiles, (uint32_t)t - lo);
+      segs.push_back({lo, parts > 1 ? n : T, (uint32_t)b, parts > 1 ? slot++ : 0xffffffffu});
+    }
+  }
+  std::stable_sort(segs.begin(), segs.end(),
+                   [](const cb::SpmmSeg& x, const cb::SpmmSeg& y) { return x.ntiles > y.ntiles; });
+  cudaError_t e = cudaSuccess;
+  auto step = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+  step(upload(&h->d_spmm_segs, segs.data(), segs.size(), s));
+  step(upload(&h->d_spmm_splits, splits.data(), splits.size(), s));
+  if (e == cudaSuccess) e = dev_malloc((void**)&h->d_spmm_partial, (size_t)(slot ? slot : 1) * 16 * 32 * sizeof(float));
+  if (e == cudaSuccess) e = dev_malloc((void**)&h->d_spmm_counter, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    void* ptrs[] = {h->d_spmm_segs, h->d_spmm_splits, h->d_spmm_partial, h->d_spmm_counter};
+    for (void* q : ptrs)
+      if (q) cudaFree(q);
+    h->d_spmm_segs = nullptr;
+    h->d_spmm_splits = nullptr;
+    h->d_spmm_partial = nullptr;
+    h->d_spmm_counter = nullptr;
+    return fail(e == cudaErrorMemoryAllocation ? CBSPMV_ERR_OOM : CBSPMV_ERR_CUDA, "cbspmv_spmm set-up: %s",
+                cudaGetErrorString(e));
+  }
+  h->spmm_nseg = (uint32_t)segs.size();
+  h->spmm_nsplit = (uint32_t)splits.size();
+  h->spmm_ready = true;
+  return ok();
+}
+
+cbspmv_status_t cbspmv_spmm(cbspmv_handle_t h, int k, const void* X, int64_t ldx, void* Y, int64_t ldy,
+                            double alpha, double beta, void* stream) {
+  if (!valid_handle(h)) return fail(CBSPMV_ERR_INVALID, "invalid handle");
+  if (h->device < 0) return fail(CBSPMV_ERR_INVALID, "host-only handle cannot run");
+  const cb::Plan& p = h->plan;
+  if (k < 0) return fail(CBSPMV_ERR_INVALID, "k must be >= 0");
+  if (ldx < k || ldy < k) return fail(CBSPMV_ERR_INVALID, "leading dimensions must be >= k");
+  if (k == 0 || p.m == 0) return ok();
+  if (p.value_dtype != CBSPMV_BF16)
+    return fail(CBSPMV_ERR_UNSUPPORTED, "cbspmv_spmm needs BF16 values (tensor-core path); use cbspmv_run_multi");
+  if (p.stats.n_direct_units != 0)
+    return fail(CBSPMV_ERR_UNSUPPORTED, "cbspmv_spmm needs a handle analysed with opts.plain_records = 1");
+  if ((!X && p.n > 0) || !Y) return fail(CBSPMV_ERR_INVALID, "NULL X or Y");
+  if (((uintptr_t)X & 3) || ((uintptr_t)Y & 3)) return fail(CBSPMV_ERR_INVALID, "X and Y must be 4-byte aligned");
+  if (X && p.n > 0) {
+    const char* xb = (const char*)X;
+    const char* yb = (const char*)Y;
+    const int64_t xspan = 4 * ((p.n - 1) * ldx + k), yspan = 4 * ((p.m - 1) * ldy + k);
+    if (xb < yb + yspan && yb < xb + xspan) return fail(CBSPMV_ERR_INVALID, "X and Y overlap");
+  }
+  DeviceGuard g(h->device);
+  CB_CUDA(g.err);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!h->spmm_ready) {
+    const cbspmv_status_t st = spmm_prepare(h, s);
+    if (st != CBSPMV_OK) return st;
+  }
+  // 32 columns per launch (the 16 x 32 accumulators of a segment stay in registers)
+  for (int j0 = 0; j0 < k; j0 += 32) {
+    cb::SpmmArgs a{};
+    a.stream = h->d_stream;
+    a.tiles = h->d_tiles;
+    a.rcols = h->d_rcols;
+    a.segs = h->d_spmm_segs;
+    a.nseg = h->spmm_nseg;
+    a.splits = h->d_spmm_splits;
+    a.nsplit = h->spmm_nsplit;
+    a.partial = h->d_spmm_partial;
+    a.counter = h->d_spmm_counter;
+    a.x = (const float*)X + j0;
+    a.y = (float*)Y + j0;
+    a.m = p.m;
+    a.n = p.n;
+    a.ldx = ldx;
+    a.ldy = ldy;
+    a.k = k - j0 < 32 ? k - j0 : 32;
+    a.alpha = (float)alpha;
+    a.beta = (float)beta;
+    a.alpha_one = alpha == 1.0;
+    a.beta_nonzero = beta != 0.0;
+    a.aggregated = p.aggregated ? 1 : 0;
+    CB_CUDA(cb::launch_spmm_bf16(a, h->grid, s));
   }
   return ok();
 }
