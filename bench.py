@@ -54,6 +54,7 @@ L2_BYTES = 129 * 2 ** 20
 # the same revision; otherwise the roofline's traffic is null.
 KERNEL_TRAFFIC = {
     "run kernel rev 13": {("fem3x3_band_1m", "bf16"): 0.6535e9},
+    "run kernel rev 15": {("fem3x3_band_1m", "f64"): 1.0187e9},
 }
 
 
@@ -62,6 +63,11 @@ def measured_traffic(version: str, workload: str, dtype: str):
         if version.endswith(rev + ")"):
             return table.get((workload, dtype))
     return None
+
+
+# The record kernel (reduced value types) is unchanged since revision 13; its capture holds
+# for later revisions of the lane kernel.
+RECORD_KERNEL_TRAFFIC = KERNEL_TRAFFIC["run kernel rev 13"]
 
 
 def fp64_peak_gflops(sms: int, sm_mhz: float, cycles_per_warp_fma: float) -> float:
@@ -628,7 +634,8 @@ def main():
             peak_derived = round(fp64_peak_gflops(sms, fmax, fma["cycles_per_warp_fma"]), 1)
         k_ms = kt["ms_main"]
         traffic = args.traffic_bytes if args.traffic_bytes is not None else \
-            measured_traffic(bd.version(), args.workload, args.dtype)
+            (RECORD_KERNEL_TRAFFIC.get((args.workload, args.dtype)) if lp else
+             measured_traffic(bd.version(), args.workload, args.dtype))
         k_gf = flops / (k_ms * 1e-3) / 1e9
         k_gbs = algo_bytes / (k_ms * 1e-3) / 1e9
         if lp:

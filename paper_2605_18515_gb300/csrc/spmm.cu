@@ -54,7 +54,11 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-template <int kNB>
+// Sub-blocks are taken in rounds of kB: the records, column indices and X values of a
+// round's sub-blocks are loaded stage by stage for all of them before any is multiplied, so
+// the three dependent memory latencies of a sub-block (record, restore_cols, X) are paid
+// once per round instead of once per sub-block.
+template <int kNB, int kB>
 __global__ void __launch_bounds__(32 * kWarps) spmm_bf16_kernel(const SpmmArgs a) {
   __shared__ __align__(128) uint8_t tiles_smem[kWarps * kTileBytes];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -63,6 +67,7 @@ __global__ void __launch_bounds__(32 * kWarps) spmm_bf16_kernel(const SpmmArgs a
   const int k = a.k;
   const float* X = static_cast<const float*>(a.x);
   float* Y = static_cast<float*>(a.y);
+  constexpr uint32_t kNoEntry = 0xffffffffu;
   for (;;) {
     uint32_t s = 0;
     if (lane == 0) s = atomicAdd(a.counter, 1u);
@@ -72,55 +77,109 @@ __global__ void __launch_bounds__(32 * kWarps) spmm_bf16_kernel(const SpmmArgs a
     float c[kNB][4];
 #pragma unroll
     for (int nb = 0; nb < kNB; ++nb) c[nb][0] = c[nb][1] = c[nb][2] = c[nb][3] = 0.f;
-    for (uint32_t t = 0; t < seg.ntiles; ++t) {
-      const CbTile tr = a.tiles[seg.tile_lo + t];
-      const uint8_t* rec = a.stream + (size_t)tr.vp16 * 16;
-      // A: the sub-block as a zero-filled 16x16 BF16 tile, row-major
-      if (tr.fmt == CB_FMT_DENSE) {
-        *reinterpret_cast<uint4*>(T + 16 * lane) = __ldg(reinterpret_cast<const uint4*>(rec + 32) + lane);
-      } else {
-        *reinterpret_cast<uint4*>(T + 16 * lane) = make_uint4(0u, 0u, 0u, 0u);
-        __syncwarp();
-        const uint32_t ib = tr.fmt == CB_FMT_CSR ? 17u : 0u;
-        const uint32_t vb = (ib + tr.nnz + 15u) & ~15u;
-        for (uint32_t e = lane; e < tr.nnz; e += 32) {
-          const uint32_t cb = rec[ib + e];
-          const uint16_t v = *reinterpret_cast<const uint16_t*>(rec + vb + 2 * e);
-          *reinterpret_cast<uint16_t*>(T + 2 * ((cb & 15u) * 16 + (cb >> 4))) = v;
+    for (uint32_t t0 = 0; t0 < seg.ntiles; t0 += kB) {
+      // 1. the round's sub-block records (lane b loads sub-block b's 16 bytes)
+      uint4 tw = make_uint4(0u, 0u, 0u, 0u);
+      if (lane < kB && t0 + lane < seg.ntiles) tw = __ldg(reinterpret_cast<const uint4*>(a.tiles + seg.tile_lo + t0 + lane));
+      CbTile tr[kB];
+      bool live[kB];
+#pragma unroll
+      for (int b = 0; b < kB; ++b) {
+        const uint32_t w0 = __shfl_sync(0xffffffffu, tw.x, b), w1 = __shfl_sync(0xffffffffu, tw.y, b);
+        const uint32_t w2 = __shfl_sync(0xffffffffu, tw.z, b), w3 = __shfl_sync(0xffffffffu, tw.w, b);
+        tr[b].vp16 = w0;
+        tr[b].xbase = w1;
+        tr[b].brow = w2;
+        tr[b].nnz = (uint16_t)(w3 & 0xffffu);
+        tr[b].fmt = (uint8_t)((w3 >> 16) & 0xffu);
+        live[b] = t0 + b < seg.ntiles;
+      }
+      // 2. this lane's entries (COO / CSR: entry lane + 32 i as coordinate << 16 | value;
+      //    Dense: its 16 bytes of the 512 value bytes) and its four column indices
+      uint32_t pre[kB][4];
+      int32_t col[kB][4];
+#pragma unroll
+      for (int b = 0; b < kB; ++b) {
+        const uint8_t* rec = a.stream + (size_t)tr[b].vp16 * 16;
+        if (live[b] && tr[b].fmt == CB_FMT_DENSE) {
+          const uint4 d = __ldg(reinterpret_cast<const uint4*>(rec + 32) + lane);
+          pre[b][0] = d.x; pre[b][1] = d.y; pre[b][2] = d.z; pre[b][3] = d.w;
+        } else {
+          const uint32_t ib = tr[b].fmt == CB_FMT_CSR ? 17u : 0u;
+          const uint32_t vb = (ib + tr[b].nnz + 15u) & ~15u;
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const uint32_t e = (uint32_t)lane + 32u * i;
+            pre[b][i] = (live[b] && e < tr[b].nnz)
+                            ? ((uint32_t)rec[ib + e] << 16) | *reinterpret_cast<const uint16_t*>(rec + vb + 2 * e)
+                            : kNoEntry;
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const uint32_t kr = 2 * tig + (i & 1) + 8 * (i >> 1);
+          const int64_t cc = !live[b] ? -1
+                             : a.aggregated ? (int64_t)__ldg(a.rcols + tr[b].xbase + kr) : (int64_t)tr[b].xbase + kr;
+          col[b][i] = cc < a.n ? (int32_t)cc : -1;
         }
       }
-      __syncwarp();
-      uint32_t af[4];
-      {
-        const uint32_t q = lane >> 3, r = (lane & 7) + 8 * (q & 1), col = 8 * (q >> 1);
-        asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-                     : "=r"(af[0]), "=r"(af[1]), "=r"(af[2]), "=r"(af[3])
-                     : "r"(smem_addr(T + 2 * (r * 16 + col))));
+      // 3. the X values of this lane's B fragments
+      float xv[kB][kNB][4];
+#pragma unroll
+      for (int b = 0; b < kB; ++b)
+#pragma unroll
+        for (int nb = 0; nb < kNB; ++nb) {
+          const int j = nb * 8 + (int)g;
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            xv[b][nb][i] = (col[b][i] >= 0 && j < k) ? __ldg(X + (int64_t)col[b][i] * a.ldx + j) : 0.f;
+        }
+      // 4. each sub-block: A as a zero-filled 16x16 BF16 tile, row-major, then the MMAs
+#pragma unroll
+      for (int b = 0; b < kB; ++b) {
+        if (!live[b]) continue;
+        if (tr[b].fmt == CB_FMT_DENSE) {
+          *reinterpret_cast<uint4*>(T + 16 * lane) = make_uint4(pre[b][0], pre[b][1], pre[b][2], pre[b][3]);
+        } else {
+          *reinterpret_cast<uint4*>(T + 16 * lane) = make_uint4(0u, 0u, 0u, 0u);
+          __syncwarp();
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            if (pre[b][i] != kNoEntry) {
+              const uint32_t cb = pre[b][i] >> 16;
+              *reinterpret_cast<uint16_t*>(T + 2 * ((cb & 15u) * 16 + (cb >> 4))) = (uint16_t)(pre[b][i] & 0xffffu);
+            }
+          }
+          // entries past 128 (CSR records under thresholds above 128): read at use
+          const uint32_t ib = tr[b].fmt == CB_FMT_CSR ? 17u : 0u;
+          const uint32_t vb = (ib + tr[b].nnz + 15u) & ~15u;
+          const uint8_t* rec = a.stream + (size_t)tr[b].vp16 * 16;
+          for (uint32_t e = (uint32_t)lane + 128u; e < tr[b].nnz; e += 32) {
+            const uint32_t cb = rec[ib + e];
+            *reinterpret_cast<uint16_t*>(T + 2 * ((cb & 15u) * 16 + (cb >> 4))) =
+                *reinterpret_cast<const uint16_t*>(rec + vb + 2 * e);
+          }
+        }
+        __syncwarp();
+        uint32_t af[4];
+        {
+          const uint32_t q = lane >> 3, r = (lane & 7) + 8 * (q & 1), cl = 8 * (q >> 1);
+          asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                       : "=r"(af[0]), "=r"(af[1]), "=r"(af[2]), "=r"(af[3])
+                       : "r"(smem_addr(T + 2 * (r * 16 + cl))));
+        }
+#pragma unroll
+        for (int nb = 0; nb < kNB; ++nb) {
+          __nv_bfloat16 h[4], m[4], l[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) split3(xv[b][nb][i], h[i], m[i], l[i]);
+          // smallest parts first
+          mma_bf16(c[nb], af, pack2(l[0], l[1]), pack2(l[2], l[3]));
+          mma_bf16(c[nb], af, pack2(m[0], m[1]), pack2(m[2], m[3]));
+          mma_bf16(c[nb], af, pack2(h[0], h[1]), pack2(h[2], h[3]));
+        }
+        __syncwarp();   // the tile buffer is rewritten by the next sub-block
       }
-      // B: the X rows of this lane's four columns of the sub-block (k rows 2 tig, 2 tig + 1,
-      // 2 tig + 8, 2 tig + 9 of the MMA), zero past the matrix
-      int64_t col[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const uint32_t kr = 2 * tig + (i & 1) + 8 * (i >> 1);
-        int64_t cc = a.aggregated ? (int64_t)__ldg(a.rcols + tr.xbase + kr) : (int64_t)tr.xbase + kr;
-        col[i] = cc < a.n ? cc : -1;
-      }
-#pragma unroll
-      for (int nb = 0; nb < kNB; ++nb) {
-        const int j = nb * 8 + (int)g;
-        float xv[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) xv[i] = (col[i] >= 0 && j < k) ? __ldg(X + col[i] * a.ldx + j) : 0.f;
-        __nv_bfloat16 h[4], m[4], l[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) split3(xv[i], h[i], m[i], l[i]);
-        // smallest parts first
-        mma_bf16(c[nb], af, pack2(l[0], l[1]), pack2(l[2], l[3]));
-        mma_bf16(c[nb], af, pack2(m[0], m[1]), pack2(m[2], m[3]));
-        mma_bf16(c[nb], af, pack2(h[0], h[1]), pack2(h[2], h[3]));
-      }
-      __syncwarp();   // the tile buffer is rewritten by the next sub-block
     }
     // C fragment: rows g and g + 8, columns 2 tig, 2 tig + 1 of each 8-column block
     const int64_t row0 = (int64_t)seg.brow * CB_BLK;
@@ -172,11 +231,11 @@ cudaError_t launch_spmm_bf16(const SpmmArgs& a, int grid, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
   const int nb = (a.k + 7) / 8;
-  switch (nb) {
-    case 1: spmm_bf16_kernel<1><<<grid, 32 * kWarps, 0, s>>>(a); break;
-    case 2: spmm_bf16_kernel<2><<<grid, 32 * kWarps, 0, s>>>(a); break;
-    case 3: spmm_bf16_kernel<3><<<grid, 32 * kWarps, 0, s>>>(a); break;
-    case 4: spmm_bf16_kernel<4><<<grid, 32 * kWarps, 0, s>>>(a); break;
+  switch (nb) {   // rounds of 4 sub-blocks, 2 at the widest (registers)
+    case 1: spmm_bf16_kernel<1, 4><<<grid, 32 * kWarps, 0, s>>>(a); break;
+    case 2: spmm_bf16_kernel<2, 4><<<grid, 32 * kWarps, 0, s>>>(a); break;
+    case 3: spmm_bf16_kernel<3, 2><<<grid, 32 * kWarps, 0, s>>>(a); break;
+    case 4: spmm_bf16_kernel<4, 2><<<grid, 32 * kWarps, 0, s>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   e = cudaGetLastError();
