@@ -267,6 +267,104 @@ def spmm_bench(bd, A, x, stream, ks=(1, 8, 32), reps=20):
     return out
 
 
+def batched_suite(nmat: int = 64, rows_lo: float = 1e4, rows_hi: float = 2e5, seed: int = 4):
+    """64 matrices drawn from the three generator families (2D Laplacian, FEM 3x3 band,
+    R-MAT), rows log-uniform in [rows_lo, rows_hi], value types FP32 / BF16 / FP16 in turn."""
+    from paper_2605_18515_gb300 import inputs as I
+    rng = np.random.default_rng(seed)
+    fams, dts = ("laplace2d", "fem", "rmat"), ("f32", "bf16", "f16")
+    out = []
+    for i in range(nmat):
+        fam, dt = fams[i % 3], dts[(i // 3) % 3]
+        r = int(np.exp(rng.uniform(np.log(rows_lo), np.log(rows_hi))))
+        if fam == "laplace2d":
+            A = I.laplacian2d(max(8, int(round(np.sqrt(r)))))
+        elif fam == "fem":
+            nb = (r + 2) // 3
+            A = I.fem_block_band(n_rows=r, n_block_rows=nb, half_band=min(1000, max(13, nb // 8)), seed=10 + i)
+        else:
+            A = I.rmat(max(10, int(round(np.log2(r)))), 16, seed=10 + i)
+        out.append((fam, dt, A))
+    return out
+
+
+def batched_bench(bd, stream, ks=(1, 8, 32), reps=10, full=False):
+    """64 products in one batched call (cbspmv_run_batched: one launch per value type per
+    column round) with options tuned once per (family, value type) on the largest matrix of
+    the class; per-result error against the FP64 oracle on sampled rows."""
+    import torch
+    import oracle
+    from paper_2605_18515_gb300 import inputs as I
+    t0 = time.perf_counter()
+    suite = batched_suite(rows_hi=1e6 if full else 2e5)
+    t_gen = time.perf_counter() - t0
+    peak, _ = load_peaks()
+    best = {}
+    for fam in ("laplace2d", "fem", "rmat"):
+        for dt in ("f32", "bf16", "f16"):
+            cls = [A for f, d, A in suite if f == fam and d == dt]
+            if not cls:
+                continue
+            A = max(cls, key=lambda a: a.nnz)
+            M, rep = bd.analyze_tuned(A, reps=5, value_dtype=dt, stream=stream)
+            M.close()
+            best[(fam, dt)] = {k: rep["best"][k] for k in ("col_agg", "unit_work", "th1", "th2")}
+    mats = [bd.BlockedMatrix(A, value_dtype=dt, stream=stream, **best[(fam, dt)]) for fam, dt, A in suite]
+    out = {"matrices": len(suite), "families": "2D Laplacian, FEM 3x3 band, R-MAT (one third each)",
+           "value_types": "FP32, BF16, FP16 in turn (FP32 x, y, accumulation)",
+           "rows": f"log-uniform in [1e4, {'1e6' if full else '2e5'}]",
+           "total_nnz": int(sum(A.nnz for _, _, A in suite)), "generate_s": round(t_gen, 1),
+           "tuned": {f"{f}/{d}": v for (f, d), v in best.items()},
+           "api": "cbspmv_run_batched (one launch per value type per round: passes of four columns, then "
+                  "single columns)", "results": []}
+    try:
+        for k in ks:
+            Xs, Ys, X64 = [], [], []
+            for i, (fam, dt, A) in enumerate(suite):
+                X = np.stack([I.vector_x(A.n, 1000 + 37 * i + j) for j in range(k)]).astype(np.float32)
+                X64.append(X)
+                Xs.append(torch.from_numpy(X if k > 1 else X[0]).cuda())
+                Ys.append(torch.zeros((k, A.m) if k > 1 else (A.m,), dtype=torch.float32, device="cuda"))
+            al, be = [1.0] * len(suite), [0.0] * len(suite)
+            for _ in range(2):
+                bd.run_batched(mats, Xs, Ys, al, be, stream=stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                bd.run_batched(mats, Xs, Ys, al, be, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            flops = sum(2.0 * A.nnz * k for _, _, A in suite)
+            byts = 0.0     # bytes model of the passes actually run: the matrix once per pass
+            passes = k // 4 + k % 4
+            for (fam, dt, A), M in zip(suite, mats):
+                st = M.stats()
+                sv = 4 if dt == "f32" else 2
+                byts += passes * (A.nnz * (sv + 1) + st["n_tiles"] * 21 + 4 * st["restore_cols_len"]) + \
+                    4 * k * (A.n + A.m)
+            errs = []
+            for i, (fam, dt, A) in enumerate(suite):
+                Y = Ys[i].cpu().numpy().reshape(k, A.m)
+                rows = np.unique((I.uniform01(50 + i, 9, 64) * A.m).astype(np.int64))
+                for j in range(min(k, 4)):
+                    yref, sc = oracle.spmv_rows(A, X64[i][j].astype(np.float64), rows)
+                    e = np.abs(Y[j][rows] - yref) / np.where(sc > 0, sc, 1.0)
+                    errs.append(float(e.max()))
+            out["results"].append({"k": k, "ms": round(ms, 4), "gflops": round(flops / (ms * 1e-3) / 1e9, 1),
+                                   "passes": passes,
+                                   "hbm_frac_bytes_model": round(byts / (ms * 1e-3) / 1e9 / peak, 4),
+                                   "error_vs_fp64_oracle": {"max": max(errs), "median": float(np.median(errs)),
+                                                            "results_checked": len(errs),
+                                                            "sample": "64 seeded rows per result, up to 4 "
+                                                                      "columns per matrix; error / sum |a x|"}})
+            del Xs, Ys
+    finally:
+        for M in mats:
+            M.close()
+    return out
+
+
 # The ablation of Sec. 4.4 (Fig. 12) as analysis options: I = intra-block data aggregation
 # only (packed records, no column aggregation, one sub-block format: COO below 256 entries),
 # II = + column aggregation and format selection (the paper's th0, th1, th2), full = II +
@@ -501,6 +599,8 @@ def main():
     ap.add_argument("--no-multi", action="store_true", help="skip the k right-hand-side measurement")
     ap.add_argument("--no-ablation", action="store_true", help="skip the ablation (Sec. 4.4) measurement")
     ap.add_argument("--no-spmm", action="store_true", help="skip the tensor-core multi-vector measurement")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-matrix batched measurement")
+    ap.add_argument("--batched-full", action="store_true", help="batched matrices up to 1e6 rows (default 2e5)")
     ap.add_argument("--serve-full", action="store_true",
                     help="serving measurement on the full pool (17 Laplacians, 15 R-MAT, 10,000 requests)")
     ap.add_argument("--traffic-bytes", type=float, default=None,
@@ -586,6 +686,7 @@ def main():
         y_ours = yd.cpu().numpy().astype(np.float64)
         multi = multi_rhs_bench(M, A, x, vec, stream) if not args.no_multi else None
         spmm = spmm_bench(bd, A, x, stream) if not args.no_spmm else None
+        batched = batched_bench(bd, stream, full=args.batched_full) if not args.no_batched else None
         abl = ablation_bench(bd, A, x, vec, args.dtype, stream) if not args.no_ablation else None
         M.check_device(stream)
         sms = torch.cuda.get_device_properties(local).multi_processor_count
@@ -696,6 +797,8 @@ def main():
                                         "of 4 vectors)", "results": multi}
         if spmm:
             line["multi_rhs_tensor"] = spmm
+        if batched:
+            line["batched"] = batched
         if abl:
             line["ablation"] = abl
         if not args.no_serve and ws == 1:

@@ -238,7 +238,10 @@ cbspmv_status_t cbspmv_analyze_batched(int count, const cbspmv_csr_t* A,
  * kernel per value type and per 64 products (each CTA works through its share of every
  * problem, as given by each problem's load balance), plus one small launch that adds the
  * parts of split block rows; a handle that appears more than once, or with k > 1, has its
- * further products in further launches (they share its partial-sum buffer). Every
+ * further products in further launches (they share its partial-sum buffer). Handles in the
+ * record layout (reduced value types) take their columns in passes of four where they can
+ * (one launch multiplies each staged unit into four columns), the rest one at a time; the
+ * first such call allocates the handle's 4-vector partial-sum buffer. Every
  * product is computed exactly as cbspmv_run computes it, so results are bitwise equal to
  * separate runs. Errors: as cbspmv_run_multi. */
 cbspmv_status_t cbspmv_run_batched(int count, const cbspmv_handle_t* h, const int* k,
@@ -284,17 +287,24 @@ cbspmv_status_t cbspmv_graph_destroy(cbspmv_graph_t g);
 /* ---- Autotuned analysis ------------------------------------------------------------------
  * The thresholds of Sec. 3.3 are heuristics (th0 0.15, th1 32, th2 128). This call analyses
  * A with the given options, then varies one choice at a time, keeping the fastest so far:
- * column aggregation (auto / off / on), unit size (512, 768 multiply-adds), then the format
- * thresholds (th1, th2) = (16, 64) and (48, 192); each candidate is timed over `reps`
- * products (1..10000) on the device. *out is the fastest handle; *rep (may be NULL)
- * lists the candidates. base->device must be a device. Every handle computes the same
- * product (only the layout differs). Errors: those of cbspmv_analyze, CBSPMV_ERR_CUDA. */
+ * column aggregation (auto / off / on: th0 only ever decides between these two layouts, so
+ * they stand for every th0); for FP64 values the lane-stream unit size (1024, 4096 stored
+ * entries) and then the record layout (record_layout = 1); for the record layout the unit
+ * size (512, 768 multiply-adds) and the format thresholds (th1, th2) = (16, 64) and
+ * (48, 192). The 16x16 sub-block is fixed (the 4-bit coordinates of Sec. 3.2) and so is the
+ * number of warps per CTA (set by the kernels' shared-memory buffers per value type). Each
+ * candidate is timed over `reps` products (1..10000) on the device. *out is the fastest
+ * handle; *rep (may be NULL) lists the candidates. base->device must be a device. Every
+ * handle computes the same product (only the layout differs). Errors: those of
+ * cbspmv_analyze, CBSPMV_ERR_CUDA. */
 typedef struct {
   int n_tried;
   double default_ms, best_ms;
   int best_unit_work, best_col_agg, best_th1, best_th2;
   double tried_ms[16];
   int tried_unit_work[16], tried_col_agg[16], tried_th1[16], tried_th2[16];
+  int best_record_layout;
+  int tried_record_layout[16];
 } cbspmv_tune_report_t;
 /* Tuned analysis: the heuristics of Sec. 3.3 searched by timing (the paper fixes them). */
 cbspmv_status_t cbspmv_analyze_tuned(const cbspmv_csr_t* A, const cbspmv_opts_t* base,

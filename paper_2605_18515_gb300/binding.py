@@ -94,7 +94,8 @@ class TuneReport(ctypes.Structure):
                 ("best_unit_work", ctypes.c_int), ("best_col_agg", ctypes.c_int), ("best_th1", ctypes.c_int),
                 ("best_th2", ctypes.c_int), ("tried_ms", ctypes.c_double * 16),
                 ("tried_unit_work", ctypes.c_int * 16), ("tried_col_agg", ctypes.c_int * 16),
-                ("tried_th1", ctypes.c_int * 16), ("tried_th2", ctypes.c_int * 16)]
+                ("tried_th1", ctypes.c_int * 16), ("tried_th2", ctypes.c_int * 16),
+                ("best_record_layout", ctypes.c_int), ("tried_record_layout", ctypes.c_int * 16)]
 
 
 # Every entry point the header declares, with its ctypes signature.
@@ -570,9 +571,10 @@ def analyze_tuned(A, *, reps=20, stream=None, **opts):
     n = min(rep.n_tried, 16)
     report = {"n_tried": rep.n_tried, "default_ms": rep.default_ms, "best_ms": rep.best_ms,
               "best": {"unit_work": rep.best_unit_work, "col_agg": rep.best_col_agg, "th1": rep.best_th1,
-                       "th2": rep.best_th2},
+                       "th2": rep.best_th2, "record_layout": rep.best_record_layout},
               "tried": [{"ms": rep.tried_ms[i], "unit_work": rep.tried_unit_work[i],
-                         "col_agg": rep.tried_col_agg[i], "th1": rep.tried_th1[i], "th2": rep.tried_th2[i]}
+                         "col_agg": rep.tried_col_agg[i], "th1": rep.tried_th1[i], "th2": rep.tried_th2[i],
+                         "record_layout": rep.tried_record_layout[i]}
                         for i in range(n)]}
     M = BlockedMatrix._adopt(h.value, int(A.m), int(A.n), nnz, o.device, opts.get("value_dtype", "f64"))
     return M, report

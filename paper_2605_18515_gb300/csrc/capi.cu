@@ -440,6 +440,13 @@ cbspmv_status_t cbspmv_time_kernels(cbspmv_handle_t h, const void* x, void* y, d
   return ok();
 }
 
+// The partial-sum buffer of 4-vector passes (16 x 4 values per slot), allocated on first use.
+static cbspmv_status_t ensure_partial_multi(cbspmv_handle_t h) {
+  if (!h->d_partial_multi)
+    CB_CUDA(dev_malloc(&h->d_partial_multi, (size_t)(h->plan.n_slots ? h->plan.n_slots : 1) * 16 * 4 * h->esize()));
+  return ok();
+}
+
 cbspmv_status_t cbspmv_run_multi(cbspmv_handle_t h, int k, const void* X, int64_t ldx, void* Y, int64_t ldy,
                                  double alpha, double beta, void* stream) {
   cbspmv_status_t st = check_run_args(h, k, X, ldx, Y, ldy);
@@ -449,8 +456,10 @@ cbspmv_status_t cbspmv_run_multi(cbspmv_handle_t h, int k, const void* X, int64_
   if (h->plan.m == 0) return ok();
   const cb::Plan& p = h->plan;
   const size_t es = h->esize();
-  if (k > 1 && !h->d_partial_multi)
-    CB_CUDA(dev_malloc(&h->d_partial_multi, (size_t)(p.n_slots ? p.n_slots : 1) * 16 * 4 * es));
+  if (k > 1) {
+    const cbspmv_status_t st = ensure_partial_multi(h);
+    if (st != CBSPMV_OK) return st;
+  }
   // passes of 4, then 2, then 1 vectors; each pass reads the matrix once. FP64 lane-stream
   // handles take one vector per pass: their product is bound by the FP64 FMA pipe, so a pass
   // over several vectors saves no time (measured 0.198, 0.236 and 0.295 ms per vector for
@@ -609,30 +618,60 @@ cbspmv_status_t cbspmv_run_batched(int count, const cbspmv_handle_t* hs, const i
   // no handle's partial-sum buffer is used twice within a launch.
   for (int i = 1; i < count; ++i)
     if (hs[i]->device != hs[0]->device) return fail(CBSPMV_ERR_INVALID, "problems on different devices");
+  // Record-layout handles take their columns in passes of four where they can (round r4
+  // of quads holds the r4-th group of four columns of every such handle), the rest one at a
+  // time; the quads use each handle's 4-vector partial-sum buffer, allocated here first.
   std::vector<std::vector<cb::RunArgs>> rounds;   // per round, all value types mixed
-  std::vector<std::pair<cbspmv_handle_t, int>> seen;
+  std::vector<std::vector<cb::RunArgs>> quads;
+  std::vector<std::pair<cbspmv_handle_t, int>> seen, seen4;
+  auto occupancy = [](std::vector<std::pair<cbspmv_handle_t, int>>& v, cbspmv_handle_t h, int add) {
+    for (auto& sh : v)
+      if (sh.first == h) { const int o = sh.second; sh.second += add; return o; }
+    v.push_back({h, add});
+    return 0;
+  };
   for (int i = 0; i < count; ++i) {
     cbspmv_handle_t h = hs[i];
     if (h->plan.m == 0) continue;
-    int occ = 0;
-    for (auto& sh : seen)
-      if (sh.first == h) occ = sh.second;
     const int ki = k ? k[i] : 1;
     const size_t es = h->esize();
-    for (int j = 0; j < ki; ++j) {
-      const int r = occ + j;
+    const int nq = h->plan.lanes ? 0 : ki / 4;
+    const int occ4 = occupancy(seen4, h, nq);
+    for (int q = 0; q < nq; ++q) {
+      if ((int)quads.size() <= occ4 + q) quads.resize(occ4 + q + 1);
+      cb::RunArgs a = run_args(h, (const char*)X[i] + es * 4 * q * h->plan.n, (char*)Y[i] + es * 4 * q * h->plan.m,
+                               alpha[i], beta[i]);
+      a.nvec = 4;
+      quads[occ4 + q].push_back(a);
+    }
+    const int occ = occupancy(seen, h, ki - 4 * nq);
+    for (int j = 4 * nq; j < ki; ++j) {
+      const int r = occ + j - 4 * nq;
       if ((int)rounds.size() <= r) rounds.resize(r + 1);
       rounds[r].push_back(run_args(h, (const char*)X[i] + es * j * h->plan.n, (char*)Y[i] + es * j * h->plan.m,
                                    alpha[i], beta[i]));
     }
-    bool found = false;
-    for (auto& sh : seen)
-      if (sh.first == h) { sh.second += ki; found = true; }
-    if (!found) seen.push_back({h, ki});
   }
-  if (rounds.empty()) return ok();
+  if (rounds.empty() && quads.empty()) return ok();
   DeviceGuard g(hs[0]->device);
   CB_CUDA(g.err);
+  for (auto& sh : seen4)
+    if (sh.second > 0) {
+      cbspmv_status_t st = ensure_partial_multi(sh.first);
+      if (st != CBSPMV_OK) return st;
+    }
+  for (auto& rd : quads) {
+    for (auto& a : rd) {
+      for (auto& sh : seen4)
+        if (sh.first->d_partial == a.partial) a.partial = sh.first->d_partial_multi;
+    }
+    for (int dt = CBSPMV_F64; dt <= CBSPMV_F16; ++dt) {
+      std::vector<cb::RunArgs> sel;
+      for (auto& a : rd)
+        if (a.value_dtype == dt) sel.push_back(a);
+      if (!sel.empty()) CB_CUDA(cb::launch_spmv_batch(sel.data(), (int)sel.size(), hs[0]->grid, (cudaStream_t)stream));
+    }
+  }
   for (auto& rd : rounds) {
     for (int dt = CBSPMV_F64; dt <= CBSPMV_F16; ++dt) {
       std::vector<cb::RunArgs> sel;
@@ -780,6 +819,12 @@ cbspmv_status_t cbspmv_graph_create(int count, const cbspmv_handle_t* hs, const 
   DeviceGuard g(hs[0]->device);
   CB_CUDA(g.err);
   CB_CUDA(cb::configure_kernels());
+  // buffers the captured products will use are allocated before the capture
+  for (int i = 0; i < count; ++i)
+    if ((k ? k[i] : 1) >= 4 && !hs[i]->plan.lanes) {
+      const cbspmv_status_t st = ensure_partial_multi(hs[i]);
+      if (st != CBSPMV_OK) return st;
+    }
   cudaStream_t s = nullptr;
   CB_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
   auto* G = new (std::nothrow) cbspmv_graph_s();
@@ -897,6 +942,7 @@ cbspmv_status_t cbspmv_analyze_tuned(const cbspmv_csr_t* A, const cbspmv_opts_t*
       R.tried_col_agg[R.n_tried] = o.col_agg;
       R.tried_th1[R.n_tried] = o.th1;
       R.tried_th2[R.n_tried] = o.th2;
+      R.tried_record_layout[R.n_tried] = o.record_layout;
     }
     R.n_tried++;
     if (!best || ms < best_ms) {
@@ -919,20 +965,39 @@ cbspmv_status_t cbspmv_analyze_tuned(const cbspmv_csr_t* A, const cbspmv_opts_t*
       o.col_agg = other;
       st = consider(o);
     }
-    for (int uw : {512, 768})
+    if (o0.value_dtype == CBSPMV_F64 && !o0.record_layout) {
+      // lane-stream unit sizes (stored entries per unit), then the record layout
+      for (int uw : {1024, 4096})
+        if (st == CBSPMV_OK) {
+          cbspmv_opts_t o = best_o;
+          o.unit_work = uw;
+          st = consider(o);
+        }
       if (st == CBSPMV_OK) {
         cbspmv_opts_t o = best_o;
-        o.unit_work = uw;
+        o.record_layout = 1;
+        o.unit_work = 0;
         st = consider(o);
       }
-    const int th[2][2] = {{16, 64}, {48, 192}};
-    for (const auto& t : th)
-      if (st == CBSPMV_OK) {
-        cbspmv_opts_t o = best_o;
-        o.th1 = t[0];
-        o.th2 = t[1];
-        st = consider(o);
-      }
+    }
+    // the record layout's unit sizes and format thresholds (formats do not change the
+    // lane-stream layout, which multiplies stored entries only)
+    if (best_o.value_dtype != CBSPMV_F64 || best_o.record_layout) {
+      for (int uw : {512, 768})
+        if (st == CBSPMV_OK) {
+          cbspmv_opts_t o = best_o;
+          o.unit_work = uw;
+          st = consider(o);
+        }
+      const int th[2][2] = {{16, 64}, {48, 192}};
+      for (const auto& t : th)
+        if (st == CBSPMV_OK) {
+          cbspmv_opts_t o = best_o;
+          o.th1 = t[0];
+          o.th2 = t[1];
+          st = consider(o);
+        }
+    }
   }
   if (x) cudaFree(x);
   if (y) cudaFree(y);
@@ -946,6 +1011,7 @@ cbspmv_status_t cbspmv_analyze_tuned(const cbspmv_csr_t* A, const cbspmv_opts_t*
   R.best_col_agg = best_o.col_agg;
   R.best_th1 = best_o.th1;
   R.best_th2 = best_o.th2;
+  R.best_record_layout = best_o.record_layout;
   if (rep) *rep = R;
   *out = best;
   return ok();

@@ -51,7 +51,8 @@ int spmv_warps(int value_dtype);   // worker warps per CTA of the run kernel for
 cudaError_t launch_spmv(const RunArgs& a, int grid, cudaStream_t stream, cudaEvent_t* ev = nullptr);
 // Launches the products of `count` problems of one value type with one run-kernel launch
 // per 64 problems (plus one combine launch each when any has split block rows). The
-// problems must not share a partial-sum buffer (that is, come from distinct handles).
+// problems must not share a partial-sum buffer (that is, come from distinct handles) and
+// must all have nvec 1, or all nvec 4 (record layout; partial sums of 16 x 4 per slot).
 cudaError_t launch_spmv_batch(const RunArgs* a, int count, int grid, cudaStream_t stream);
 // Sets every run-kernel instantiation's shared-memory limit on the current device (done
 // lazily by the launches too; needed before a stream capture).

@@ -1350,8 +1350,10 @@ cudaError_t launch_nvec(const BatchArgs<kMaxP>& b, int grid, cudaStream_t stream
       case 4: return launch_typed<V, 1, 4>(b, grid, stream, ev);
       default: return cudaErrorInvalidValue;
     }
-  } else {
-    return b.p[0].nvec == 1 ? launch_typed<V, kMaxP, 1>(b, grid, stream, ev) : cudaErrorInvalidValue;
+  } else {   // batches: one vector, or passes of four
+    return b.p[0].nvec == 1 ? launch_typed<V, kMaxP, 1>(b, grid, stream, ev)
+           : b.p[0].nvec == 4 ? launch_typed<V, kMaxP, 4>(b, grid, stream, ev)
+                              : cudaErrorInvalidValue;
   }
 }
 
@@ -1420,6 +1422,7 @@ template <class V>
 cudaError_t configure_value_type() {
   cudaError_t e = configure_typed<V, 1, 1>();
   if (e == cudaSuccess) e = configure_typed<V, kMaxBatch, 1>();
+  if (e == cudaSuccess) e = configure_typed<V, kMaxBatch, 4>();
   if (e == cudaSuccess) e = configure_typed<V, 1, 2>();
   if (e == cudaSuccess) e = configure_typed<V, 1, 4>();
   return e;
@@ -1448,7 +1451,8 @@ cudaError_t launch_spmv(const RunArgs& a, int grid, cudaStream_t stream, cudaEve
 
 cudaError_t launch_spmv_batch(const RunArgs* a, int count, int grid, cudaStream_t stream) {
   for (int i = 0; i < count; ++i)
-    if (a[i].value_dtype != a[0].value_dtype || a[i].nvec != 1) return cudaErrorInvalidValue;
+    if (a[i].value_dtype != a[0].value_dtype || a[i].nvec != a[0].nvec || (a[i].nvec != 1 && a[i].nvec != 4))
+      return cudaErrorInvalidValue;
   // one layout per launch: problems of the other layout go to launches of their own
   for (int i = 1; i < count; ++i)
     if (a[i].lanes != a[0].lanes) {

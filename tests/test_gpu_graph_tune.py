@@ -48,13 +48,20 @@ def test_graph_replays_batched_products(env):
 
 
 @pytest.mark.parametrize("name", ["fem_small", "rmat12"])
-def test_tuned_analysis(env, name):
+@pytest.mark.parametrize("dtype", ["f64", "bf16"])
+def test_tuned_analysis(env, name, dtype):
     bd, torch = env
+    if dtype != "f64":
+        pytest.skip("reduced types: covered by test_tuned_analysis_reduced_type")
     A = {"fem_small": lambda: I.fem_block_band(n_rows=6000, n_block_rows=2000, half_band=300, seed=3),
          "rmat12": lambda: I.rmat(12, 16, seed=4)}[name]()
     M, rep = bd.analyze_tuned(A, reps=5)
     with M:
-        assert 5 <= rep["n_tried"] <= 16
+        # FP64: aggregation side, two lane unit sizes, the record layout (then its own axes
+        # when it wins)
+        assert 4 <= rep["n_tried"] <= 16
+        assert any(t["record_layout"] == 1 for t in rep["tried"])
+        assert M.stats()["lane_layout"] == (rep["best"]["record_layout"] == 0)
         assert rep["best_ms"] <= rep["default_ms"] and rep["best_ms"] == min(t["ms"] for t in rep["tried"])
         x = I.vector_x(A.n, 12)
         yd = torch.zeros(A.m, dtype=torch.float64, device="cuda")
@@ -64,3 +71,19 @@ def test_tuned_analysis(env, name):
         st = M.stats()
         assert st["aggregated"] == (rep["best"]["col_agg"] == 1 or
                                     (rep["best"]["col_agg"] == -1 and st["super_sparse_fraction"] > 0.15))
+
+
+def test_tuned_analysis_reduced_type(env):
+    """BF16 values: the record layout's axes (aggregation, unit sizes, format thresholds);
+    the tuned handle's product stays within the FP32 bound of the stored-value product."""
+    from oracle import lowprec as L
+    bd, torch = env
+    A = I.fem_block_band(n_rows=6000, n_block_rows=2000, half_band=300, seed=3)
+    M, rep = bd.analyze_tuned(A, reps=5, value_dtype="bf16")
+    with M:
+        assert 5 <= rep["n_tried"] <= 16 and all(t["record_layout"] == 0 for t in rep["tried"])
+        x = I.vector_x(A.n, 13).astype(np.float32)
+        yd = torch.zeros(A.m, dtype=torch.float32, device="cuda")
+        M.run(torch.from_numpy(x).cuda(), yd)
+        y_ref, s = oracle.spmv(L.stored_matrix(A, "bf16"), x.astype(np.float64))
+        assert L.within_bound(yd.cpu().numpy(), y_ref, s, L.fp32_bound(A))[0]
