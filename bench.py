@@ -394,6 +394,30 @@ def ablation_bench(bd, A, x, vec, dtype, stream, reps=200):
     return out
 
 
+def value_types_bench(bd, A, x, stream, reps=200):
+    """The reduced value types (FP32 / BF16 / FP16 storage, FP32 x, y and accumulation) in
+    both layouts on this workload: kernel time, the bytes model of the type over it, and
+    that bandwidth as a fraction of the measured HBM copy bandwidth."""
+    import torch
+    peak, kind = load_peaks()
+    xd = torch.from_numpy(x.astype(np.float32)).cuda()
+    yd = torch.empty(A.m, dtype=torch.float32, device="cuda")
+    out = {"hbm_peak_gbs": peak, "peak_kind": kind, "results": []}
+    for dt in ("bf16", "f16", "f32"):
+        for lay, name in ((1, "records"), (2, "lanes")):
+            with bd.BlockedMatrix(A, value_dtype=dt, record_layout=lay, stream=stream) as M:
+                kt = M.time_kernels(xd, yd, reps, stream=stream)
+                ms = kt["ms_main"] + kt["ms_combine"]
+                st = M.stats()
+            gbs = st["algo_bytes_per_run"] / (ms * 1e-3) / 1e9
+            out["results"].append({"dtype": dt, "layout": name, "ms": round(ms, 4),
+                                   "gflops": round(2.0 * A.nnz / (ms * 1e-3) / 1e9, 1),
+                                   "model_bytes": st["algo_bytes_per_run"], "model_gbs": round(gbs, 1),
+                                   "frac_of_hbm": round(gbs / peak, 3),
+                                   "stored_bytes": st["stream_bytes"] + st["metadata_bytes"]})
+    return out
+
+
 def step_distribution(run, stream, n: int, flush_buf=None):
     """Device time of n single steps, each between its own pair of events on the run's
     stream; with flush_buf, a buffer larger than L2 is overwritten before every step."""
@@ -452,6 +476,36 @@ def error_vs_fp64_oracle(A, x, y, n_rows: int = 20000):
     norm = np.where(s > 0, err / np.where(s > 0, s, 1.0), np.where(err > 0, np.inf, 0.0))
     return {"max": float(norm.max()), "median": float(np.median(norm)), "rows": int(rows.size),
             "sample": f"{rows.size} seeded rows, error / sum_k |a_ik x_k|"}
+
+
+# ---- preprocessing cost (Sec. 4.5): host analysis of a host CSR vs device analysis ------------
+def device_analysis_bench(bd, torch, A, st_host, host_call_ms, ms_per_product, device, stream):
+    """Wall time of cbspmv_analyze for the same matrix given as host arrays (analysis on the
+    host cores, then upload) and as device arrays (analysis on the GPU); the second device
+    call is reported (the first one also loads the analysis kernels)."""
+    import types
+    Ad = types.SimpleNamespace(m=A.m, n=A.n, row_ptr=torch.from_numpy(A.row_ptr).cuda(),
+                               col=torch.from_numpy(A.col).cuda(), val=torch.from_numpy(A.val).cuda())
+    torch.cuda.synchronize()
+    calls = []
+    for _ in range(2):
+        t0 = time.perf_counter()
+        Md = bd.BlockedMatrix(Ad, device=device, stream=stream)
+        stream.synchronize()
+        calls.append((time.perf_counter() - t0) * 1e3)
+        sd = Md.stats()
+        Md.close()
+    del Ad
+    torch.cuda.empty_cache()
+    same = all(sd[k] == st_host[k] for k in st_host if k not in ("analyze_ms", "analyzed_on_device"))
+    return {"host_analyze_ms": round(st_host["analyze_ms"], 2), "host_call_ms": round(host_call_ms, 2),
+            "device_analyze_ms": round(sd["analyze_ms"], 2), "device_call_ms": round(calls[-1], 2),
+            "device_first_call_ms": round(calls[0], 2), "analyzed_on_device": int(sd["analyzed_on_device"]),
+            "same_plan_as_host": bool(same),
+            "products_to_amortize_host": round(st_host["analyze_ms"] / ms_per_product, 1),
+            "products_to_amortize_device": round(sd["analyze_ms"] / ms_per_product, 1),
+            "note": "analyze_ms: the analysis itself; call_ms: the whole cbspmv_analyze call "
+                    "(host path: analysis + upload of the lane arrays)"}
 
 
 # ---- serving: Poisson mix of y = Ax and CG solves over a resident pool ------------------------
@@ -525,30 +579,40 @@ def serve_run(S, ids, mats, n_req, rate, seed):
             "launches": st["launches"] - st0["launches"]}
 
 
-def serve_mode(bd, mats, n_req, seed, **server_opts):
-    """Burst capacity, then Poisson arrivals at 70% of it, on one server."""
-    with bd.Server(**server_opts) as S:
-        ids = [S.register(A) for _, A, _ in mats]
-        cap = serve_run(S, ids, mats, n_req, float("inf"), seed)
-        load = serve_run(S, ids, mats, n_req, 0.7 * cap["req_per_s"], seed + 1)
-    return cap, load
-
-
-def serve_bench(pool_name, seed=5):
+def serve_bench(pool_name, seed=5, inner_steps=8):
+    """Both modes' burst capacity; then Poisson arrivals at one common rate (70% of the
+    one-at-a-time capacity, a load both modes sustain) for both, and the served mode also at
+    70% of its own capacity."""
     from paper_2605_18515_gb300 import binding as bd
     mats, spec = serve_pool(pool_name)
-    cap, load = serve_mode(bd, mats, spec["requests"], seed, max_inflight=64, cg_inner_dtype="bf16",
-                           inner_tol=1e-4, memory_budget=8 << 30)
-    bcap, bload = serve_mode(bd, mats, spec["baseline_requests"], seed, max_inflight=1, cg_inner_dtype="f64",
-                             inner_tol=1e-9, memory_budget=8 << 30)
-    return {"pool": f"{len(spec['lap'])} SPD 3D Laplacians {spec['lap'][0]}^3..{spec['lap'][-1]}^3 + "
-                    f"{len(spec['rmat'])} R-MAT (scales {spec['rmat'][0][0]}-{spec['rmat'][-1][0]})",
-            "mix": "70% y=Ax (FP64), 30% CG to 1e-8 relative residual",
-            "served": {"mode": "continuous batching, 64 in flight, BF16-value CG with FP64 refinement",
-                       "capacity": cap, "poisson_at_70pct": load},
-            "one_at_a_time_fp64": {"mode": "one request at a time, FP64 products and FP64 CG",
-                                   "capacity": bcap, "poisson_at_70pct": bload},
-            "capacity_ratio": round(cap["req_per_s"] / max(bcap["req_per_s"], 1e-9), 2)}
+    served_opts = dict(max_inflight=64, cg_inner_dtype="bf16", inner_tol=1e-4, memory_budget=8 << 30,
+                       inner_steps=inner_steps)
+    base_opts = dict(max_inflight=1, cg_inner_dtype="f64", inner_tol=1e-9, memory_budget=8 << 30)
+    with bd.Server(**base_opts) as S:
+        ids = [S.register(A) for _, A, _ in mats]
+        bcap = serve_run(S, ids, mats, spec["baseline_requests"], float("inf"), seed)
+        common = 0.7 * bcap["req_per_s"]
+        bload = serve_run(S, ids, mats, spec["baseline_requests"], common, seed + 1)
+    with bd.Server(**served_opts) as S:
+        ids = [S.register(A) for _, A, _ in mats]
+        cap = serve_run(S, ids, mats, spec["requests"], float("inf"), seed)
+        same = serve_run(S, ids, mats, spec["requests"], common, seed + 1)
+        load = serve_run(S, ids, mats, spec["requests"], 0.7 * cap["req_per_s"], seed + 2)
+    out = {"pool": f"{len(spec['lap'])} SPD 3D Laplacians {spec['lap'][0]}^3..{spec['lap'][-1]}^3 + "
+                   f"{len(spec['rmat'])} R-MAT (scales {spec['rmat'][0][0]}-{spec['rmat'][-1][0]})",
+           "mix": "70% y=Ax (FP64), 30% CG to 1e-8 relative residual",
+           "served": {"mode": "continuous batching, 64 in flight, BF16-value CG with FP64 refinement, "
+                              f"{inner_steps} inner CG iterations per tick",
+                      "capacity": cap, "poisson_same_load": same, "poisson_at_70pct": load},
+           "one_at_a_time_fp64": {"mode": "one request at a time, FP64 products and FP64 CG",
+                                  "capacity": bcap, "poisson_same_load": bload},
+           "same_load_req_per_s": round(common, 1),
+           "capacity_ratio": round(cap["req_per_s"] / max(bcap["req_per_s"], 1e-9), 2),
+           "p99_ratio_same_load": round(same["p99_ms"] / max(bload["p99_ms"], 1e-9), 3)}
+    if pool_name != "full":
+        out["note"] = ("default run: 9-matrix pool; the full pool of 32 matrices and 10,000 requests "
+                       "(about 80 s to generate, minutes to serve) runs with --serve-full")
+    return out
 
 
 def run_reference(args, A, x, ws, rank):
@@ -600,9 +664,12 @@ def main():
     ap.add_argument("--no-ablation", action="store_true", help="skip the ablation (Sec. 4.4) measurement")
     ap.add_argument("--no-spmm", action="store_true", help="skip the tensor-core multi-vector measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-matrix batched measurement")
+    ap.add_argument("--no-value-types", action="store_true", help="skip the reduced value types measurement")
     ap.add_argument("--batched-full", action="store_true", help="batched matrices up to 1e6 rows (default 2e5)")
     ap.add_argument("--serve-full", action="store_true",
                     help="serving measurement on the full pool (17 Laplacians, 15 R-MAT, 10,000 requests)")
+    ap.add_argument("--serve-inner-steps", type=int, default=8,
+                    help="inner CG iterations per tick of the served mode (1..64)")
     ap.add_argument("--traffic-bytes", type=float, default=None,
                     help="ncu DRAM bytes per launch of the timed kernel, if captured for this build")
     args = ap.parse_args()
@@ -632,7 +699,10 @@ def main():
     esz = 4 if lp else 8
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
+        t_an = time.perf_counter()
         M = bd.BlockedMatrix(A, device=local, stream=stream, value_dtype=args.dtype)
+        stream.synchronize()
+        host_call_ms = (time.perf_counter() - t_an) * 1e3
         st = M.stats()
         xd = torch.from_numpy(x.astype(vec)).cuda()
         yd = torch.empty(A.m, dtype=tvec, device="cuda")
@@ -801,8 +871,12 @@ def main():
             line["batched"] = batched
         if abl:
             line["ablation"] = abl
+        if not lp and ws == 1:
+            line["analysis"] = device_analysis_bench(bd, torch, A, st, host_call_ms, ms_max, local, stream)
+        if not lp and ws == 1 and not args.no_value_types:
+            line["value_types"] = value_types_bench(bd, A, x, stream)
         if not args.no_serve and ws == 1:
-            line["serving"] = serve_bench("full" if args.serve_full else "small")
+            line["serving"] = serve_bench("full" if args.serve_full else "small", inner_steps=args.serve_inner_steps)
         if err:
             line["error_vs_fp64_oracle"] = err
         print(json.dumps(line), flush=True)

@@ -61,8 +61,12 @@ enum { CBSPMV_FMT_COO = 0, CBSPMV_FMT_CSR = 1, CBSPMV_FMT_DENSE = 2 };
 /* A CSR matrix given by the caller. Values are always FP64 here; cbspmv_analyze copies
  * everything it needs, so the caller may free the arrays when the call returns.
  * on_device = 0: the three arrays are host pointers; on_device = 1: they are device
- * pointers (any device; the analysis copies them to the host on the given stream first,
- * since the analysis itself runs on the host). */
+ * pointers. For the lane-stream layout on a device (value_dtype CBSPMV_F64 with
+ * record_layout 0, or any value type with record_layout 2; device >= 0) with the arrays
+ * in that device's memory, the analysis runs on that device from these arrays on the
+ * given stream (GPU merge, tiling, aggregation and lane programs; units and load balance
+ * on the host from the tile counts; Sec. 3.2-3.4, cost of Sec. 4.5). Otherwise the arrays
+ * are copied to the host on the given stream and analysed there. */
 typedef struct {
   int64_t m, n, nnz;
   const int64_t* row_ptr;   /* m + 1 entries */
@@ -86,9 +90,10 @@ typedef struct {
  *        (analysis, export and statistics work; run calls return CBSPMV_ERR_INVALID).
  *   keep_value_map: 0 (default) or 1, see cbspmv_update_values.
  *   record_layout: 0 (default): FP64 values are packed per unit in lane order (the
- *        lane-stream layout of the FP64 run kernel); 1: FP64 values use the per-sub-block
- *        record layout of the reduced types and their kernel (for comparison). The
- *        reduced types always use the record layout. Results agree within the tolerance. */
+ *        lane-stream layout of the lane run kernel), the reduced types use the
+ *        per-sub-block record layout and its kernel; 1: every value type uses the record
+ *        layout; 2: every value type uses the lane-stream layout. Results agree within
+ *        the tolerance of the value type. */
 typedef struct {
   double th0;
   int th1, th2;
@@ -99,7 +104,7 @@ typedef struct {
   int device;
   int keep_value_map;       /* 1: record each entry's value slot (4 bytes per entry on the
                                device) so cbspmv_update_values can re-pack new values */
-  int record_layout;        /* 1: FP64 values in the record layout (see above) */
+  int record_layout;        /* 0 default, 1 records, 2 lane streams (see above) */
   int plain_records;        /* 1: every sub-block record keeps the layout of Sec. 3.2 (no
                                values re-laid in load order): needed by cbspmv_spmm */
   int reserved[5];
@@ -131,14 +136,15 @@ typedef struct {
   int64_t n_units, n_split_units, n_split_rows, n_workers;
   double worker_load_max, worker_load_mean, worker_load_std;  /* multiply-adds per worker */
   double tb8_load_std;             /* per-thread-block (8 sub-blocks) nnz std, Algorithm 2 order */
-  double analyze_ms;               /* host time of cbspmv_analyze */
+  double analyze_ms;               /* wall time of the analysis (host, or GPU kernels and host steps) */
   int64_t n_entry_mode_units;      /* units scheduled in single entries (sparse pieces) */
   int64_t n_xseq_units;            /* units whose chunks all cover consecutive columns */
   int64_t fma_slots;               /* FMA slots the run kernel's walks issue per vector (32 lanes x
                                       chunk steps x chunk size, summed over units); nnz / fma_slots
                                       is the fraction of FMA issue that does useful work */
   int64_t n_direct_units;          /* units whose chunk descriptors hold value offsets and columns */
-  int64_t lane_layout;             /* 1: FP64 lane-stream layout (see record_layout), 0: records */
+  int64_t lane_layout;             /* 1: lane-stream layout (see record_layout), 0: records */
+  int64_t analyzed_on_device;      /* 1: built on the GPU from a device CSR (cbspmv_csr_t) */
 } cbspmv_stats_t;
 
 /* Fills *opts with the paper's settings: th0 0.15 (Sec. 3.3.1), th1 32 and th2 128
@@ -202,8 +208,8 @@ cbspmv_status_t cbspmv_run_multi(cbspmv_handle_t h, int k, const void* X, int64_
  * a contraction of shape 16 x 16 x k). X: device array, row-major n x k with leading
  * dimension ldx >= k (element (i, j) at X[i * ldx + j]); Y: row-major m x k, ldy >= k; FP32
  * (the vector type of BF16 handles), 4-byte aligned, not overlapping. Requires a device
- * handle with BF16 values analysed with opts.plain_records = 1 (CBSPMV_ERR_UNSUPPORTED
- * otherwise; other value types use cbspmv_run_multi). Each sub-block is expanded to a
+ * handle with BF16 values in the record layout analysed with opts.plain_records = 1
+ * (CBSPMV_ERR_UNSUPPORTED otherwise; other value types and layouts use cbspmv_run_multi). Each sub-block is expanded to a
  * zero-filled 16x16 BF16 tile and multiplied with mma.sync.m16n8k16 (BF16 inputs, FP32
  * accumulation); every x is split exactly into three BF16 parts (|x - sum| <= 2^-25 |x|) so
  * the products keep FP32 accuracy; a row's result has error at most gamma_{6r + 16} with
@@ -353,8 +359,10 @@ cbspmv_status_t cbspmv_measure_fp64_fma(int device, void* stream, double* gflops
  * arrival order while a slot (max_inflight) and device memory (memory_budget, a pool the
  * server allocates once) are free, and advances every in-flight request by one step per
  * tick: the products of all in-flight requests run as one batched launch of the run kernel
- * per value type (see cbspmv_run_batched), the CG vector steps as batched kernels. Each
- * result is the same whether the request runs alone or among others.
+ * per value type (see cbspmv_run_batched), the CG vector steps as batched kernels; a solve
+ * in its inner CG phase runs up to inner_steps inner iterations per tick (its scalars stay
+ * on the device, and the steps after its inner convergence do nothing). Each result is the
+ * same whether the request runs alone or among others.
  * CG (mixed precision with FP64 refinement): r = b - A x and x += d in FP64 with the
  * FP64-value product; each correction A d = r is solved by CG on cg_inner_dtype values
  * (FP32 vectors and accumulation for the reduced types; FP64 for CBSPMV_F64) to
@@ -369,7 +377,8 @@ typedef struct {
   double inner_tol;         /* inner CG: stop at ||r|| <= inner_tol ||r0|| (default 1e-4) */
   int inner_max_iter;       /* inner CG iterations per correction (default 2000) */
   int max_outer;            /* refinement steps before a solve fails (default 30) */
-  int reserved[8];
+  int inner_steps;          /* inner CG iterations per engine tick, 1..64 (default 8; 0 = 8) */
+  int reserved[7];
 } cbspmv_server_opts_t;
 
 enum { CBSPMV_REQ_SPMV = 0, CBSPMV_REQ_CG = 1 };
@@ -403,7 +412,8 @@ typedef struct {
 } cbspmv_server_stats_t;
 
 /* Server defaults (no counterpart in the paper): device 0, 4 GiB budget, 64 in flight,
- * BF16 inner values, inner_tol 1e-4, 2000 inner iterations, 30 refinements. */
+ * BF16 inner values, inner_tol 1e-4, 2000 inner iterations, 30 refinements, 8 inner
+ * iterations per tick. */
 cbspmv_status_t cbspmv_server_default_opts(cbspmv_server_opts_t* opts);
 /* Creates a server (no counterpart in the paper; the repeated products that amortise the
  * analysis, Sec. 4.5): allocates the memory budget, a stream and the engine thread.
@@ -411,8 +421,9 @@ cbspmv_status_t cbspmv_server_default_opts(cbspmv_server_opts_t* opts);
 cbspmv_status_t cbspmv_server_create(const cbspmv_server_opts_t* opts, cbspmv_server_t* out);
 /* Registers a matrix with the server (the analysis of Sec. 3, kept resident): analyses A
  * (opts as cbspmv_analyze; device and value type are the server's) with FP64
- * values and, for a square A, also with cg_inner_dtype values; the matrices stay
- * resident until cbspmv_server_destroy. *matrix_id names it in requests (at most 1024). */
+ * values and, for a square A, also with cg_inner_dtype values (in the lane-stream layout
+ * unless opts.record_layout asks otherwise); the matrices stay resident until
+ * cbspmv_server_destroy. *matrix_id names it in requests (at most 1024). */
 cbspmv_status_t cbspmv_server_register(cbspmv_server_t s, const cbspmv_csr_t* A,
                                        const cbspmv_opts_t* opts, int* matrix_id);
 /* Queues a request (no counterpart in the paper); *ticket identifies it. Errors: CBSPMV_ERR_INVALID (unknown matrix,

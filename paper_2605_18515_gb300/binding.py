@@ -59,14 +59,14 @@ class Stats(ctypes.Structure):
                 ("tb8_load_std", ctypes.c_double), ("analyze_ms", ctypes.c_double),
                 ("n_entry_mode_units", ctypes.c_int64), ("n_xseq_units", ctypes.c_int64),
                 ("fma_slots", ctypes.c_int64), ("n_direct_units", ctypes.c_int64),
-                ("lane_layout", ctypes.c_int64)]
+                ("lane_layout", ctypes.c_int64), ("analyzed_on_device", ctypes.c_int64)]
 
 
 class ServerOpts(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("memory_budget", ctypes.c_int64), ("max_inflight", ctypes.c_int),
                 ("cg_inner_dtype", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("inner_max_iter", ctypes.c_int), ("max_outer", ctypes.c_int),
-                ("reserved", ctypes.c_int * 8)]
+                ("inner_steps", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
 
 
 class Request(ctypes.Structure):
@@ -231,7 +231,7 @@ def _make_opts(th0=0.15, th1=32, th2=128, col_agg=-1, value_dtype="f64", unit_wo
     o.load_balance = 1 if load_balance else 0
     o.device = device
     o.keep_value_map = 1 if keep_value_map else 0
-    o.record_layout = 1 if record_layout else 0
+    o.record_layout = int(record_layout)   # False/0 default, True/1 records, 2 lane streams
     o.plain_records = 1 if plain_records else 0
     return o
 
@@ -438,12 +438,13 @@ class Server:
     continuous batching of in-flight requests on the device."""
 
     def __init__(self, device=0, memory_budget=4 << 30, max_inflight=64, cg_inner_dtype="bf16",
-                 inner_tol=1e-4, inner_max_iter=2000, max_outer=30):
+                 inner_tol=1e-4, inner_max_iter=2000, max_outer=30, inner_steps=8):
         o = ServerOpts()
         _check(lib().cbspmv_server_default_opts(ctypes.byref(o)))
         o.device, o.memory_budget, o.max_inflight = device, int(memory_budget), max_inflight
         o.cg_inner_dtype = DTYPES[cg_inner_dtype]
         o.inner_tol, o.inner_max_iter, o.max_outer = inner_tol, inner_max_iter, max_outer
+        o.inner_steps = inner_steps
         self._s = ctypes.c_void_p(None)
         _check(lib().cbspmv_server_create(ctypes.byref(o), ctypes.byref(self._s)))
         self._keep: dict[int, tuple] = {}

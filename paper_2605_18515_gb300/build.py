@@ -23,7 +23,7 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompil
               "--expt-relaxed-constexpr", "-I" + INCLUDE]
 CXX_FLAGS = ["-O3", "-std=c++17", "-fPIC", "-pthread", "-I" + INCLUDE]
 
-SOURCES_CU = ["kernels.cu", "capi.cu", "noalloc.cu", "serve.cu", "measure.cu", "spmm.cu"]
+SOURCES_CU = ["kernels.cu", "capi.cu", "noalloc.cu", "serve.cu", "measure.cu", "spmm.cu", "analyze_dev.cu"]
 SOURCES_CXX = ["analyze.cpp"]
 _lock = threading.Lock()
 

@@ -274,7 +274,16 @@ void build_block_row(const cbspmv_csr_t& A, int64_t b, bool agg, int th1, int th
   }
 }
 
-cbspmv_status_t validate(const cbspmv_csr_t& A, std::string* msg) {
+}  // namespace
+
+void host_parallel_for(int64_t n, int64_t grain, const std::function<void(int64_t, int64_t)>& f) {
+  parallel_for(n, grain, f);
+}
+int tile_format(int nnz, int th1, int th2) { return select_format(nnz, th1, th2); }
+
+// Sizes and array pointers of a CSR (the contents are checked by validate on the host and
+// by the device analysis on the GPU).
+cbspmv_status_t validate_shape(const cbspmv_csr_t& A, std::string* msg) {
   if (A.m < 0 || A.n < 0 || A.nnz < 0 || A.m >= (1LL << 31) || A.n >= (1LL << 31) ||
       A.nnz >= (1LL << 31)) {
     *msg = "matrix dimensions out of range";
@@ -284,6 +293,14 @@ cbspmv_status_t validate(const cbspmv_csr_t& A, std::string* msg) {
     *msg = "NULL CSR array";
     return CBSPMV_ERR_INVALID;
   }
+  return CBSPMV_OK;
+}
+
+namespace {
+
+cbspmv_status_t validate(const cbspmv_csr_t& A, std::string* msg) {
+  const cbspmv_status_t st0 = validate_shape(A, msg);
+  if (st0 != CBSPMV_OK) return st0;
   if (A.row_ptr[0] != 0 || A.row_ptr[A.m] != A.nnz) {
     *msg = "row_ptr must start at 0 and end at nnz";
     return CBSPMV_ERR_NOT_CANONICAL;
@@ -316,18 +333,34 @@ cbspmv_status_t validate(const cbspmv_csr_t& A, std::string* msg) {
 // entries of each (tile, row) of the records (16 per row for Dense tiles, whose present
 // entries come from the presence bitmap). Also composes the value map with the move of
 // every value from its record to its lane position, and counts the FMA slots.
-static cbspmv_status_t build_lane_programs(const cbspmv_csr_t& A, Plan& p, const std::vector<uint8_t>& rowcnt,
-                                           std::string* msg) {
+// Offsets of every unit's values, entry words and gather list in the lane-stream arrays
+// (units in worker order), and the unit descriptors without their flags. The sizes of the
+// three arrays go to p.n_lane_vals, p.n_lane_words and p.n_lane_gcols; p.fma_slots is the
+// value count.
+cbspmv_status_t lane_offsets(Plan& p, std::vector<uint64_t>* voff_out, std::vector<uint64_t>* woff_out,
+                             std::vector<uint64_t>* goff_out, std::string* msg) {
   const size_t nun = p.units.size();
-  std::vector<uint64_t> voff(nun + 1, 0), woff(nun + 1, 0), goff(nun + 1, 0);
+  std::vector<uint64_t>& voff = *voff_out;
+  std::vector<uint64_t>& woff = *woff_out;
+  std::vector<uint64_t>& goff = *goff_out;
+  voff.assign(nun + 1, 0);
+  woff.assign(nun + 1, 0);
+  goff.assign(nun + 1, 0);
+  const bool grouped = p.vsize != 8;    // the reduced-type layout: steps in groups of 8
+  // one gather-list entry per plain sub-block (4- and 2-byte value types; the FP64 kernel
+  // keeps one entry per x slot, which measured faster there)
+  const bool plainx = !p.aggregated && grouped;
+  std::vector<uint64_t> steps(nun);
   for (size_t i = 0; i < nun; ++i) {
     const CbUnit& u = p.units[i];
     uint64_t W = 0;
     for (uint32_t t = 0; t < u.ntiles; ++t) W += p.tiles[u.tile_lo + t].nnz;
     const uint64_t S = (W + CB_VLANES - 1) / CB_VLANES;
-    voff[i + 1] = voff[i] + S;
-    woff[i + 1] = woff[i] + (S + 3) / 4;
-    goff[i + 1] = goff[i] + 16ull * u.ntiles;
+    const uint64_t Sp = grouped ? (S + CB_LANE_GROUP - 1) / CB_LANE_GROUP * CB_LANE_GROUP : S;
+    steps[i] = S;
+    voff[i + 1] = voff[i] + Sp;
+    woff[i + 1] = woff[i] + (Sp + 3) / 4;
+    goff[i + 1] = goff[i] + (plainx ? (u.ntiles + 3ull) / 4 * 4 : 16ull * u.ntiles);
   }
   if (voff[nun] >= (1ull << 32) || woff[nun] >= (1ull << 32) || goff[nun] >= (1ull << 32)) {
     *msg = "lane stream too large";
@@ -335,15 +368,54 @@ static cbspmv_status_t build_lane_programs(const cbspmv_csr_t& A, Plan& p, const
   }
   try {
     p.lane_units.resize(nun);
-    p.lane_vals.resize((size_t)voff[nun] * CB_VLANES);
-    p.lane_words.resize((size_t)woff[nun] * CB_VLANES);
-    p.lane_gcols.resize((size_t)goff[nun]);
   } catch (...) {
     *msg = "host allocation failed";
     return CBSPMV_ERR_OOM;
   }
+  for (size_t i = 0; i < nun; ++i) {
+    const CbUnit& u = p.units[i];
+    CbLaneUnit& L = p.lane_units[i];
+    L = CbLaneUnit{};
+    L.vals = (uint32_t)voff[i];
+    L.words = (uint32_t)woff[i];
+    L.gcols = (uint32_t)goff[i];
+    L.brow_lo = u.brow_lo;
+    L.steps = (uint16_t)steps[i];
+    L.nslots = (uint16_t)(16 * u.ntiles);
+    L.nrows = (uint16_t)std::min<int64_t>((int64_t)CB_BLK * u.nbr, p.m - (int64_t)u.brow_lo * CB_BLK);
+    L.flags = plainx ? CB_LUNIT_PLAINX : 0;
+    L.slot = u.split >= 0 ? u.slot : 0xffffffffu;
+  }
+  p.n_lane_vals = (size_t)voff[nun] * CB_VLANES;
+  p.n_lane_words = (size_t)woff[nun] * CB_VLANES;
+  p.n_lane_gcols = (size_t)goff[nun];
+  p.fma_slots = (int64_t)voff[nun] * CB_VLANES;
+  return CBSPMV_OK;
+}
+
+// Lane-stream programs of every unit (layout in cb_layout.h), built from the packed records
+// after the load balance (so each worker's units are contiguous in the arrays). rowcnt:
+// entries of each (tile, row) of the records (16 per row for Dense tiles, whose present
+// entries come from the presence bitmap). Also composes the value map with the move of
+// every value from its record to its lane position, and counts the FMA slots.
+static cbspmv_status_t build_lane_programs(const cbspmv_csr_t& A, Plan& p, const std::vector<uint8_t>& rowcnt,
+                                           std::string* msg) {
+  const size_t nun = p.units.size();
+  std::vector<uint64_t> voff, woff, goff;
+  cbspmv_status_t st = lane_offsets(p, &voff, &woff, &goff, msg);
+  if (st != CBSPMV_OK) return st;
+  try {
+    p.lane_vals.resize(p.n_lane_vals * (size_t)p.vsize);
+    p.lane_words.resize(p.n_lane_words);
+    p.lane_gcols.resize(p.n_lane_gcols);
+  } catch (...) {
+    *msg = "host allocation failed";
+    return CBSPMV_ERR_OOM;
+  }
+  const uint32_t vs = (uint32_t)p.vsize;
+  const bool grouped = vs != 8;
   // value index in the record stream -> value index in the lane stream (value map only)
-  std::vector<uint32_t> moved(p.value_slot.empty() ? 0 : p.stream.size() / 8, UINT32_MAX);
+  std::vector<uint32_t> moved(p.value_slot.empty() ? 0 : p.stream.size() / vs, UINT32_MAX);
   parallel_for((int64_t)nun, 128, [&](int64_t lo, int64_t hi) {
     struct Ent { uint16_t word; uint32_t vidx; };   // entry word, value index in the record stream
     std::vector<Ent> ent;
@@ -368,7 +440,7 @@ static cbspmv_status_t build_lane_programs(const cbspmv_csr_t& A, Plan& p, const
               for (uint32_t c = 0; c < 16; ++c) {
                 const uint32_t pos = 16u * rr + c;
                 if (bm[pos >> 3] & (1u << (pos & 7)))
-                  ent.push_back({(uint16_t)((16u * t + c) | ((uint32_t)row << 9)), (uint32_t)((rec + 32 + 8 * pos) / 8)});
+                  ent.push_back({(uint16_t)((16u * t + c) | ((uint32_t)row << 9)), (uint32_t)((rec + 32 + vs * pos) / vs)});
               }
             } else {
               const uint32_t c = rowcnt[tg * 16 + rr];
@@ -379,7 +451,7 @@ static cbspmv_status_t build_lane_programs(const cbspmv_csr_t& A, Plan& p, const
               const uint32_t va = align16(ib + tr.nnz);
               for (uint32_t e = s0; e < s0 + c; ++e) {
                 const uint32_t col = p.stream[rec + ib + e] >> 4;
-                ent.push_back({(uint16_t)((16u * t + col) | ((uint32_t)row << 9)), (uint32_t)((rec + va + 8 * e) / 8)});
+                ent.push_back({(uint16_t)((16u * t + col) | ((uint32_t)row << 9)), (uint32_t)((rec + va + vs * e) / vs)});
               }
             }
           }
@@ -387,11 +459,10 @@ static cbspmv_status_t build_lane_programs(const cbspmv_csr_t& A, Plan& p, const
         t_begin = t_end;
       }
       const uint64_t W = ent.size();
-      const uint64_t S = voff[i + 1] - voff[i];
-      double* vals = p.lane_vals.data() + (size_t)voff[i] * CB_VLANES;
+      uint8_t* vals = p.lane_vals.data() + (size_t)voff[i] * CB_VLANES * vs;
       uint64_t* words = p.lane_words.data() + (size_t)woff[i] * CB_VLANES;
-      std::fill(vals, vals + S * CB_VLANES, 0.0);
-      std::fill(words, words + ((S + 3) / 4) * CB_VLANES, ~0ull);
+      std::fill(vals, vals + (size_t)(voff[i + 1] - voff[i]) * CB_VLANES * vs, (uint8_t)0);
+      std::fill(words, words + (size_t)(woff[i + 1] - woff[i]) * CB_VLANES, ~0ull);
       int first_lane[CB_R_MAX], last_lane[CB_R_MAX];
       for (int r = 0; r < CB_R_MAX; ++r) first_lane[r] = last_lane[r] = -1;
       for (uint32_t l = 0; l < CB_VLANES; ++l) {
@@ -399,11 +470,12 @@ static cbspmv_status_t build_lane_programs(const cbspmv_csr_t& A, Plan& p, const
         for (uint64_t k = c0; k < c1; ++k) {
           const uint64_t st = k - c0;
           const Ent& e = ent[k];
-          std::memcpy(vals + st * CB_VLANES + l, p.stream.data() + (size_t)e.vidx * 8, 8);
-          uint64_t& w = words[(st / 4) * CB_VLANES + l];
+          const uint32_t vi = cb_lane_val_index(grouped, (uint32_t)st, l);
+          std::memcpy(vals + (size_t)vi * vs, p.stream.data() + (size_t)e.vidx * vs, vs);
+          uint64_t& w = words[cb_lane_word_index(grouped, (uint32_t)st, l)];
           const uint32_t sh = 16u * (uint32_t)(st % 4);
           w = (w & ~(0xffffull << sh)) | ((uint64_t)e.word << sh);
-          if (!moved.empty()) moved[e.vidx] = (uint32_t)(((size_t)voff[i] + st) * CB_VLANES + l);
+          if (!moved.empty()) moved[e.vidx] = (uint32_t)((size_t)voff[i] * CB_VLANES + vi);
           const int r = e.word >> 9;
           if (first_lane[r] < 0) first_lane[r] = (int)l;
           last_lane[r] = (int)l;
@@ -412,9 +484,13 @@ static cbspmv_status_t build_lane_programs(const cbspmv_csr_t& A, Plan& p, const
       int span_max = 0;
       for (int r = 0; r < CB_R_MAX; ++r)
         if (first_lane[r] >= 0) span_max = std::max(span_max, last_lane[r] - first_lane[r] + 1);
-      // gather list: the x column of every slot
+      // gather list: the first column of every plain sub-block, or the x column of every slot
       int32_t* g = p.lane_gcols.data() + goff[i];
-      for (uint32_t t = 0; t < u.ntiles; ++t) {
+      if (p.lane_units[i].flags & CB_LUNIT_PLAINX) {
+        for (uint64_t k = 0; k < goff[i + 1] - goff[i]; ++k)
+          g[k] = k < u.ntiles ? (int32_t)p.tiles[u.tile_lo + k].xbase : 0;
+      }
+      for (uint32_t t = 0; t < u.ntiles && !(p.lane_units[i].flags & CB_LUNIT_PLAINX); ++t) {
         const CbTile& tr = p.tiles[u.tile_lo + t];
         for (uint32_t c = 0; c < 16; ++c) {
           int64_t col = -1;
@@ -428,28 +504,280 @@ static cbspmv_status_t build_lane_programs(const cbspmv_csr_t& A, Plan& p, const
           g[16 * t + c] = (int32_t)col;
         }
       }
-      CbLaneUnit& L = p.lane_units[i];
-      L = CbLaneUnit{};
-      L.vals = (uint32_t)voff[i];
-      L.words = (uint32_t)woff[i];
-      L.gcols = (uint32_t)goff[i];
-      L.brow_lo = u.brow_lo;
-      L.steps = (uint16_t)S;
-      L.nslots = (uint16_t)(16 * u.ntiles);
-      L.nrows = (uint16_t)R;
-      L.flags = span_max > CB_SCAN_SPAN ? CB_LUNIT_SCAN : 0;
-      L.slot = u.split >= 0 ? u.slot : 0xffffffffu;
+      p.lane_units[i].flags |= span_max > CB_SCAN_SPAN ? CB_LUNIT_SCAN : 0;
     }
   });
   if (!moved.empty())
     for (uint32_t& sl : p.value_slot) sl = moved[sl];
-  p.fma_slots = (int64_t)voff[nun] * CB_VLANES;
   return CBSPMV_OK;
 }
 
-cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, int n_workers,
-                             Plan* P, std::string* msg) {
-  auto t_start = std::chrono::steady_clock::now();
+// Step 4a of the analysis: units of work over the tiles of p (p.tiles in block-row order,
+// tile_off: nbr + 1 tile offsets of the block rows). Fills p.units (matrix order),
+// p.split_rows, p.n_split_rows, p.n_split_wide and p.n_slots.
+void cut_units(Plan& p, const std::vector<int64_t>& tile_off, const cbspmv_opts_t& opts) {
+  const int64_t nbr = p.nbr;
+  // Record layout: every unit must fit one warp's shared-memory
+  // buffer (stream bytes, tiles, multiply-adds incl. Dense zero fill). Lane-stream layout:
+  // the values stream through registers, so only the x slots (tiles) and rows bound a
+  // unit, and its work is its stored entries.
+  const bool lanes = p.lanes;
+  const uint32_t BMAX = lanes ? UINT32_MAX : CB_B_MAX_FOR(p.vsize);   // stream bytes per unit
+  const uint32_t U = lanes ? (opts.unit_work > 0 ? std::min<uint32_t>((uint32_t)opts.unit_work, CB_LANE_WORK_MAX)
+                                                 : CB_LANE_WORK_DEFAULT)
+                           : (opts.unit_work > 0 ? std::min<uint32_t>((uint32_t)opts.unit_work, CB_UNIT_WORK_MAX)
+                                                 : CB_UNIT_WORK_DEFAULT);
+  const int64_t TMAX = lanes ? CB_LANE_T_MAX : CB_T_MAX;
+  const uint32_t NBRMAX = lanes ? CB_LANE_NBR_MAX : CB_NBR_MAX;
+  auto tile_work = [&](int64_t t) -> uint32_t {
+    return (!lanes && p.tiles[t].fmt == CB_FMT_DENSE) ? 256u : p.tiles[t].nnz;
+  };
+  auto tile_bytes = [&](int64_t t) -> uint32_t {
+    return lanes ? 0u : record_bytes(p.tiles[t].fmt, p.tiles[t].nnz, p.vsize);
+  };
+  auto finish_unit = [&](CbUnit& u) {
+    if (p.aggregated && u.ntiles > 0) {
+      uint32_t first = p.tiles[u.tile_lo].xbase;
+      uint32_t last = p.tiles[u.tile_lo + u.ntiles - 1].xbase + 16;
+      u.rc_lo = first & ~3u;
+      u.rc_n = (last - u.rc_lo + 3u) & ~3u;
+    } else {
+      u.rc_lo = 0;
+      u.rc_n = 0;
+    }
+    if (u.ntiles > 0) u.byte_lo16 = p.tiles[u.tile_lo].vp16;
+    p.units.push_back(u);
+  };
+  CbUnit open{};
+  bool have_open = false;
+  int32_t split_id = 0;
+  uint32_t slot = 0;
+  for (int64_t b = 0; b < nbr; ++b) {
+    int64_t t0 = tile_off[b], t1 = tile_off[b + 1];
+    uint64_t W = 0, B = 0;
+    for (int64_t t = t0; t < t1; ++t) { W += tile_work(t); B += tile_bytes(t); }
+    int64_t T = t1 - t0;
+    bool big = W > U || B > BMAX || T > TMAX;
+    if (!big) {
+      if (have_open && open.work + W <= U && open.nbytes + B <= BMAX &&
+          open.ntiles + T <= TMAX && open.nbr < NBRMAX) {
+        open.ntiles = (uint16_t)(open.ntiles + T);
+        open.nbr = (uint16_t)(open.nbr + 1);
+        open.nbytes += (uint32_t)B;
+        open.work += (uint32_t)W;
+        if (open.ntiles == T) open.tile_lo = (uint32_t)t0;
+        continue;
+      }
+      if (have_open) finish_unit(open);
+      open = CbUnit{};
+      open.tile_lo = (uint32_t)t0;
+      open.ntiles = (uint16_t)T;
+      open.nbr = 1;
+      open.brow_lo = (uint32_t)b;
+      open.nbytes = (uint32_t)B;
+      open.work = (uint32_t)W;
+      open.split = -1;
+      open.nparts = 1;
+      have_open = true;
+      continue;
+    }
+    if (have_open) { finish_unit(open); have_open = false; }
+    // cut the block row into parts of about equal work within the unit limits
+    uint64_t nparts_est = std::max<uint64_t>({(W + U - 1) / U, (B + BMAX - 1) / BMAX,
+                                              (uint64_t)((T + TMAX - 1) / TMAX), 2});
+    uint64_t target = (W + nparts_est - 1) / nparts_est;
+    size_t first_unit = p.units.size();
+    CbUnit u{};
+    u.tile_lo = (uint32_t)t0; u.nbr = 1; u.brow_lo = (uint32_t)b; u.split = split_id;
+    for (int64_t t = t0; t < t1; ++t) {
+      uint32_t wt = tile_work(t), bt = tile_bytes(t);
+      if (u.ntiles > 0 && (u.work + wt > U || u.nbytes + bt > BMAX || u.ntiles + 1 > TMAX ||
+                           u.work >= target)) {
+        finish_unit(u);
+        CbUnit v{};
+        v.tile_lo = (uint32_t)t; v.nbr = 1; v.brow_lo = (uint32_t)b; v.split = split_id;
+        u = v;
+      }
+      u.ntiles++;
+      u.work += wt;
+      u.nbytes += bt;
+    }
+    finish_unit(u);
+    uint16_t np = (uint16_t)(p.units.size() - first_unit);
+    CbSplitRow sr{};
+    sr.slot0 = slot;
+    sr.brow = (uint32_t)b;
+    sr.nparts = np;
+    sr.rows = (uint16_t)std::min<int64_t>(CB_BLK, p.m - b * CB_BLK);
+    p.split_rows.push_back(sr);
+    for (size_t i = first_unit; i < p.units.size(); ++i) {
+      p.units[i].part = (uint16_t)(i - first_unit);
+      p.units[i].nparts = np;
+      p.units[i].slot = slot++;
+    }
+    ++split_id;
+  }
+  if (have_open) finish_unit(open);
+  p.n_split_rows = split_id;
+  // split rows with many parts last (they are added by a wider combine)
+  std::stable_partition(p.split_rows.begin(), p.split_rows.end(),
+                        [](const CbSplitRow& r) { return r.nparts <= CB_COMBINE_WIDE_PARTS; });
+  p.n_split_wide = 0;
+  for (const CbSplitRow& r : p.split_rows) p.n_split_wide += r.nparts > CB_COMBINE_WIDE_PARTS;
+  p.n_slots = (int)slot;
+}
+
+// Every unit must fit the run kernel's buffers (the shared-memory stage of the record
+// kernel, the step and row limits of the lane kernel).
+cbspmv_status_t check_units(const Plan& p, std::string* msg) {
+  const bool lanes = p.lanes;
+  const uint32_t BMAX = lanes ? UINT32_MAX : CB_B_MAX_FOR(p.vsize);
+  for (const CbUnit& u : p.units) {
+    const bool bad = lanes ? (u.ntiles > CB_LANE_T_MAX || (u.work + 31) / 32 > 0xffffu ||
+                              u.nbr > CB_LANE_NBR_MAX || u.nbr == 0)
+                           : (u.nbytes > BMAX || u.ntiles > CB_T_MAX || u.rc_n > CB_RC_MAX ||
+                              u.sched_bytes > CB_SCHED_MAX ||
+                              u.blob_bytes > 16u * CB_T_MAX + 4u * CB_RC_MAX + CB_SCHED_MAX ||
+                              u.nbr > CB_NBR_MAX || u.nbr == 0);
+    if (bad) {
+      *msg = "internal error: a unit exceeds the run kernel buffer limits";
+      return CBSPMV_ERR_INVALID;
+    }
+  }
+  return CBSPMV_OK;
+}
+
+// Step 4b: load balance of the units over the persistent thread blocks (Sec. 3.4):
+// longest-processing-time order, min-heap of (load, worker id). Reorders p.units into
+// worker order and fills p.worker_units, p.worker_off and *load_out (cost per worker).
+void balance_units(Plan& p, const cbspmv_opts_t& opts, int n_workers, std::vector<double>* load_out) {
+  const bool lanes = p.lanes;
+  const int64_t nu = (int64_t)p.units.size();
+  p.n_workers = n_workers;
+  std::vector<double> cost(nu);
+  for (int64_t i = 0; i < nu; ++i) {
+    const CbUnit& u = p.units[i];
+    // lane-stream units: the FP64 FMA slots of the walk (32 per step) plus the gather
+    cost[i] = lanes ? 32.0 * ((u.work + 31) / 32) + 16.0 * u.ntiles + 2.0 * CB_BLK * u.nbr + 64.0
+                    : (double)u.work + 8.0 * u.ntiles + 2.0 * CB_BLK * u.nbr + 64.0;
+  }
+  std::vector<std::vector<uint32_t>> lists(n_workers);
+  std::vector<double>& load = *load_out;
+  load.assign(n_workers, 0.0);
+  if (opts.load_balance) {
+    std::vector<uint32_t> order(nu);
+    for (int64_t i = 0; i < nu; ++i) order[i] = (uint32_t)i;
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return cost[a] > cost[b]; });
+    typedef std::pair<double, int> Item;
+    std::priority_queue<Item, std::vector<Item>, std::greater<Item>> pq;
+    for (int w = 0; w < n_workers; ++w) pq.push(Item(0.0, w));
+    for (uint32_t u : order) {
+      Item top = pq.top();
+      pq.pop();
+      lists[top.second].push_back(u);
+      top.first += cost[u];
+      load[top.second] = top.first;
+      pq.push(top);
+    }
+    for (auto& l : lists) std::sort(l.begin(), l.end());   // matrix order inside a worker
+  } else {
+    for (int64_t i = 0; i < nu; ++i) {
+      lists[i % n_workers].push_back((uint32_t)i);
+      load[i % n_workers] += cost[i];
+    }
+  }
+  // store the units in worker order: each CTA's units are one contiguous range
+  p.worker_off.assign(n_workers + 1, 0);
+  p.worker_units.reserve(nu);
+  for (int w = 0; w < n_workers; ++w) {
+    p.worker_off[w + 1] = p.worker_off[w] + (uint32_t)lists[w].size();
+    p.worker_units.insert(p.worker_units.end(), lists[w].begin(), lists[w].end());
+  }
+  {
+    std::vector<CbUnit> ordered(nu);
+    static_assert(sizeof(CbUnit) == 64, "unit descriptor is 64 bytes");
+    for (int64_t i = 0; i < nu; ++i) ordered[i] = p.units[p.worker_units[i]];
+    p.units.swap(ordered);
+  }
+}
+
+// Statistics of a finished plan (analysis time excepted): plain_tiles and frac are the
+// plain 16x16 tile count and super-sparse share of step 2, load the cost per worker.
+void fill_stats(Plan& p, int64_t plain_tiles, double frac, const std::vector<double>& load) {
+  const bool lanes = p.lanes;
+  const int64_t nbr = p.nbr;
+  const int64_t ntiles = (int64_t)p.tiles.size();
+  const int n_workers = p.n_workers;
+  const int64_t nu = (int64_t)p.units.size();
+  cbspmv_stats_t& s = p.stats;
+  s = cbspmv_stats_t{};
+  s.m = p.m; s.n = p.n; s.nnz = p.nnz;
+  s.n_block_rows = nbr;
+  s.n_tiles = ntiles;
+  s.n_tiles_plain = plain_tiles;
+  s.super_sparse_fraction = frac;
+  s.aggregated = p.aggregated ? 1 : 0;
+  s.value_dtype = p.value_dtype;
+  int64_t mults = 0;
+  for (int64_t t = 0; t < ntiles; ++t) {
+    const CbTile& x = p.tiles[t];
+    s.n_fmt[x.fmt]++;
+    s.nnz_fmt[x.fmt] += x.nnz;
+    s.hist_coarse[std::min(7, (x.nnz - 1) / 32)]++;
+    if (x.nnz <= 32) s.hist_fine[(x.nnz - 1) / 8]++;
+    mults += x.fmt == CB_FMT_DENSE ? 256 : x.nnz;
+  }
+  s.restore_cols_len = p.restore_cols_len;
+  if (lanes) {
+    s.stream_bytes = (int64_t)p.n_lane_vals * p.vsize + (int64_t)p.n_lane_words * 8;
+    s.metadata_bytes = ntiles * (int64_t)sizeof(CbTile) + (int64_t)p.n_lane_gcols * 4 +
+                       (int64_t)p.lane_units.size() * (int64_t)sizeof(CbLaneUnit);
+  } else {
+    s.stream_bytes = (int64_t)p.stream.size();
+    s.metadata_bytes = ntiles * (int64_t)sizeof(CbTile) + (int64_t)p.sched.size() * 4 +
+                       (int64_t)p.units.size() * (int64_t)sizeof(CbUnit);
+  }
+  s.lane_layout = lanes ? 1 : 0;
+  s.model_bytes_cb = ntiles * 21 + p.nnz * 9;
+  s.model_bytes_csr = (p.m + 1) * 4 + p.nnz * 12;
+  s.model_bytes_bsr16 = 2048 * ntiles + (nbr + 1) * 4 + 4 * ntiles;
+  const int64_t es = p.value_dtype == CBSPMV_F64 ? 8 : 4;   // x, y element size
+  s.algo_bytes_per_run = p.nnz * (int64_t)(p.vsize + 1) + ntiles * 21 + p.n * es + p.m * es +
+                         (p.aggregated ? 4 * p.restore_cols_len : 0);
+  s.flops_per_run = 2 * p.nnz;
+  s.mults_per_run = mults;
+  s.n_units = nu;
+  int64_t nsplit_units = 0;
+  for (auto& u : p.units) nsplit_units += u.split >= 0;
+  s.n_split_units = nsplit_units;
+  for (auto& u : p.units) {
+    s.n_entry_mode_units += (u.mode & CB_MODE_ENTRY) ? 1 : 0;
+    s.n_xseq_units += (u.mode & CB_MODE_XSEQ) ? 1 : 0;
+    s.n_direct_units += (u.mode & CB_MODE_DIRECT) ? 1 : 0;
+  }
+  s.fma_slots = p.fma_slots;
+  s.n_split_rows = p.n_split_rows;
+  s.n_workers = n_workers;
+  double lmax = 0, lsum = 0, lsq = 0;
+  for (double l : load) { lmax = std::max(lmax, l); lsum += l; lsq += l * l; }
+  s.worker_load_max = lmax;
+  s.worker_load_mean = lsum / n_workers;
+  s.worker_load_std = std::sqrt(std::max(0.0, lsq / n_workers - s.worker_load_mean * s.worker_load_mean));
+  {
+    int64_t ng = (ntiles + 7) / 8;
+    double gs = 0, gq = 0;
+    for (int64_t g = 0; g < ng; ++g) {
+      double v = 0;
+      for (int64_t t = 8 * g; t < std::min(ntiles, 8 * g + 8); ++t) v += p.tiles[t].nnz;
+      gs += v; gq += v * v;
+    }
+    double mean = ng ? gs / ng : 0;
+    s.tb8_load_std = ng ? std::sqrt(std::max(0.0, gq / ng - mean * mean)) : 0.0;
+  }
+}
+
+// Options shared by the host and the device analysis.
+cbspmv_status_t check_opts(const cbspmv_opts_t& opts, int n_workers, std::string* msg) {
   if (opts.th1 < 0 || opts.th2 < opts.th1 || opts.th2 > 256 || !(opts.th0 >= 0.0)) {
     *msg = "thresholds must satisfy th0 >= 0 and 0 <= th1 <= th2 <= 256";
     return CBSPMV_ERR_INVALID;
@@ -460,10 +788,18 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
   }
   if (opts.col_agg < -1 || opts.col_agg > 1) { *msg = "col_agg must be -1, 0 or 1"; return CBSPMV_ERR_INVALID; }
   if (opts.keep_value_map != 0 && opts.keep_value_map != 1) { *msg = "keep_value_map must be 0 or 1"; return CBSPMV_ERR_INVALID; }
-  if (opts.record_layout != 0 && opts.record_layout != 1) { *msg = "record_layout must be 0 or 1"; return CBSPMV_ERR_INVALID; }
+  if (opts.record_layout < 0 || opts.record_layout > 2) { *msg = "record_layout must be 0, 1 or 2"; return CBSPMV_ERR_INVALID; }
   if (opts.plain_records != 0 && opts.plain_records != 1) { *msg = "plain_records must be 0 or 1"; return CBSPMV_ERR_INVALID; }
   if (n_workers <= 0) { *msg = "no workers"; return CBSPMV_ERR_INVALID; }
-  cbspmv_status_t st = validate(A, msg);
+  return CBSPMV_OK;
+}
+
+cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, int n_workers,
+                             Plan* P, std::string* msg) {
+  auto t_start = std::chrono::steady_clock::now();
+  cbspmv_status_t st = check_opts(opts, n_workers, msg);
+  if (st != CBSPMV_OK) return st;
+  st = validate(A, msg);
   if (st != CBSPMV_OK) return st;
 
   Plan& p = *P;
@@ -473,7 +809,7 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
   p.value_dtype = opts.value_dtype;
   p.vsize = value_size(opts.value_dtype);
   p.th0 = opts.th0; p.th1 = opts.th1; p.th2 = opts.th2;
-  p.lanes = p.value_dtype == CBSPMV_F64 && opts.record_layout == 0;
+  p.lanes = (p.value_dtype == CBSPMV_F64 && opts.record_layout == 0) || opts.record_layout == 2;
   const int64_t nbr = p.nbr;
 
   // --- step 2: plain 16x16 tiles and the super-sparse share (Sec. 3.3.1)
@@ -573,114 +909,9 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
     }
   });
 
-  // --- step 4a: units of work. Record layout: every unit must fit one warp's shared-memory
-  // buffer (stream bytes, tiles, multiply-adds incl. Dense zero fill). Lane-stream layout:
-  // the values stream through registers, so only the x slots (tiles) and rows bound a
-  // unit, and its work is its stored entries.
+  cut_units(p, tile_off, opts);
   const bool lanes = p.lanes;
-  const uint32_t BMAX = lanes ? UINT32_MAX : CB_B_MAX_FOR(p.vsize);   // stream bytes per unit
-  const uint32_t U = lanes ? (opts.unit_work > 0 ? std::min<uint32_t>((uint32_t)opts.unit_work, CB_LANE_WORK_MAX)
-                                                 : CB_LANE_WORK_DEFAULT)
-                           : (opts.unit_work > 0 ? std::min<uint32_t>((uint32_t)opts.unit_work, CB_UNIT_WORK_MAX)
-                                                 : CB_UNIT_WORK_DEFAULT);
-  const int64_t TMAX = lanes ? CB_LANE_T_MAX : CB_T_MAX;
-  const uint32_t NBRMAX = lanes ? CB_LANE_NBR_MAX : CB_NBR_MAX;
-  auto tile_work = [&](int64_t t) -> uint32_t {
-    return (!lanes && p.tiles[t].fmt == CB_FMT_DENSE) ? 256u : p.tiles[t].nnz;
-  };
-  auto tile_bytes = [&](int64_t t) -> uint32_t {
-    return lanes ? 0u : record_bytes(p.tiles[t].fmt, p.tiles[t].nnz, p.vsize);
-  };
-  auto finish_unit = [&](CbUnit& u) {
-    if (p.aggregated && u.ntiles > 0) {
-      uint32_t first = p.tiles[u.tile_lo].xbase;
-      uint32_t last = p.tiles[u.tile_lo + u.ntiles - 1].xbase + 16;
-      u.rc_lo = first & ~3u;
-      u.rc_n = (last - u.rc_lo + 3u) & ~3u;
-    } else {
-      u.rc_lo = 0;
-      u.rc_n = 0;
-    }
-    if (u.ntiles > 0) u.byte_lo16 = p.tiles[u.tile_lo].vp16;
-    p.units.push_back(u);
-  };
-  CbUnit open{};
-  bool have_open = false;
-  int32_t split_id = 0;
-  uint32_t slot = 0;
-  for (int64_t b = 0; b < nbr; ++b) {
-    int64_t t0 = tile_off[b], t1 = tile_off[b + 1];
-    uint64_t W = 0, B = 0;
-    for (int64_t t = t0; t < t1; ++t) { W += tile_work(t); B += tile_bytes(t); }
-    int64_t T = t1 - t0;
-    bool big = W > U || B > BMAX || T > TMAX;
-    if (!big) {
-      if (have_open && open.work + W <= U && open.nbytes + B <= BMAX &&
-          open.ntiles + T <= TMAX && open.nbr < NBRMAX) {
-        open.ntiles = (uint16_t)(open.ntiles + T);
-        open.nbr = (uint16_t)(open.nbr + 1);
-        open.nbytes += (uint32_t)B;
-        open.work += (uint32_t)W;
-        if (open.ntiles == T) open.tile_lo = (uint32_t)t0;
-        continue;
-      }
-      if (have_open) finish_unit(open);
-      open = CbUnit{};
-      open.tile_lo = (uint32_t)t0;
-      open.ntiles = (uint16_t)T;
-      open.nbr = 1;
-      open.brow_lo = (uint32_t)b;
-      open.nbytes = (uint32_t)B;
-      open.work = (uint32_t)W;
-      open.split = -1;
-      open.nparts = 1;
-      have_open = true;
-      continue;
-    }
-    if (have_open) { finish_unit(open); have_open = false; }
-    // cut the block row into parts of about equal work within the unit limits
-    uint64_t nparts_est = std::max<uint64_t>({(W + U - 1) / U, (B + BMAX - 1) / BMAX,
-                                              (uint64_t)((T + TMAX - 1) / TMAX), 2});
-    uint64_t target = (W + nparts_est - 1) / nparts_est;
-    size_t first_unit = p.units.size();
-    CbUnit u{};
-    u.tile_lo = (uint32_t)t0; u.nbr = 1; u.brow_lo = (uint32_t)b; u.split = split_id;
-    for (int64_t t = t0; t < t1; ++t) {
-      uint32_t wt = tile_work(t), bt = tile_bytes(t);
-      if (u.ntiles > 0 && (u.work + wt > U || u.nbytes + bt > BMAX || u.ntiles + 1 > TMAX ||
-                           u.work >= target)) {
-        finish_unit(u);
-        CbUnit v{};
-        v.tile_lo = (uint32_t)t; v.nbr = 1; v.brow_lo = (uint32_t)b; v.split = split_id;
-        u = v;
-      }
-      u.ntiles++;
-      u.work += wt;
-      u.nbytes += bt;
-    }
-    finish_unit(u);
-    uint16_t np = (uint16_t)(p.units.size() - first_unit);
-    CbSplitRow sr{};
-    sr.slot0 = slot;
-    sr.brow = (uint32_t)b;
-    sr.nparts = np;
-    sr.rows = (uint16_t)std::min<int64_t>(CB_BLK, A.m - b * CB_BLK);
-    p.split_rows.push_back(sr);
-    for (size_t i = first_unit; i < p.units.size(); ++i) {
-      p.units[i].part = (uint16_t)(i - first_unit);
-      p.units[i].nparts = np;
-      p.units[i].slot = slot++;
-    }
-    ++split_id;
-  }
-  if (have_open) finish_unit(open);
-  p.n_split_rows = split_id;
-  // split rows with many parts last (they are added by a wider combine)
-  std::stable_partition(p.split_rows.begin(), p.split_rows.end(),
-                        [](const CbSplitRow& r) { return r.nparts <= CB_COMBINE_WIDE_PARTS; });
-  p.n_split_wide = 0;
-  for (const CbSplitRow& r : p.split_rows) p.n_split_wide += r.nparts > CB_COMBINE_WIDE_PARTS;
-  p.n_slots = (int)slot;
+  const uint32_t BMAX = lanes ? UINT32_MAX : CB_B_MAX_FOR(p.vsize);
 
   // --- step 4a': lane schedule of every unit (chunks of <= CB_CHUNK entries, see cb_layout.h)
   if (!lanes) {
@@ -912,141 +1143,19 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
     });
   }
 
-  // every unit must fit one shared-memory stage of the kernel
-  for (const CbUnit& u : p.units) {
-    const bool bad = lanes ? (u.ntiles > CB_LANE_T_MAX || (u.work + 31) / 32 > 0xffffu ||
-                              u.nbr > CB_LANE_NBR_MAX || u.nbr == 0)
-                           : (u.nbytes > BMAX || u.ntiles > CB_T_MAX || u.rc_n > CB_RC_MAX ||
-                              u.sched_bytes > CB_SCHED_MAX ||
-                              u.blob_bytes > 16u * CB_T_MAX + 4u * CB_RC_MAX + CB_SCHED_MAX ||
-                              u.nbr > CB_NBR_MAX || u.nbr == 0);
-    if (bad) {
-      *msg = "internal error: a unit exceeds the run kernel buffer limits";
-      return CBSPMV_ERR_INVALID;
-    }
-  }
+  st = check_units(p, msg);
+  if (st != CBSPMV_OK) return st;
 
-  // --- step 4b: load balance of units over the persistent thread blocks (Sec. 3.4):
-  // longest-processing-time order, min-heap of (load, worker id).
-  const int64_t nu = (int64_t)p.units.size();
-  p.n_workers = n_workers;
-  std::vector<double> cost(nu);
-  for (int64_t i = 0; i < nu; ++i) {
-    const CbUnit& u = p.units[i];
-    // lane-stream units: the FP64 FMA slots of the walk (32 per step) plus the gather
-    cost[i] = lanes ? 32.0 * ((u.work + 31) / 32) + 16.0 * u.ntiles + 2.0 * CB_BLK * u.nbr + 64.0
-                    : (double)u.work + 8.0 * u.ntiles + 2.0 * CB_BLK * u.nbr + 64.0;
-  }
-  std::vector<std::vector<uint32_t>> lists(n_workers);
-  std::vector<double> load(n_workers, 0.0);
-  if (opts.load_balance) {
-    std::vector<uint32_t> order(nu);
-    for (int64_t i = 0; i < nu; ++i) order[i] = (uint32_t)i;
-    std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return cost[a] > cost[b]; });
-    typedef std::pair<double, int> Item;
-    std::priority_queue<Item, std::vector<Item>, std::greater<Item>> pq;
-    for (int w = 0; w < n_workers; ++w) pq.push(Item(0.0, w));
-    for (uint32_t u : order) {
-      Item top = pq.top();
-      pq.pop();
-      lists[top.second].push_back(u);
-      top.first += cost[u];
-      load[top.second] = top.first;
-      pq.push(top);
-    }
-    for (auto& l : lists) std::sort(l.begin(), l.end());   // matrix order inside a worker
-  } else {
-    for (int64_t i = 0; i < nu; ++i) {
-      lists[i % n_workers].push_back((uint32_t)i);
-      load[i % n_workers] += cost[i];
-    }
-  }
-  // store the units in worker order: each CTA's units are one contiguous range
-  p.worker_off.assign(n_workers + 1, 0);
-  p.worker_units.reserve(nu);
-  for (int w = 0; w < n_workers; ++w) {
-    p.worker_off[w + 1] = p.worker_off[w] + (uint32_t)lists[w].size();
-    p.worker_units.insert(p.worker_units.end(), lists[w].begin(), lists[w].end());
-  }
-  {
-    std::vector<CbUnit> ordered(nu);
-    static_assert(sizeof(CbUnit) == 64, "unit descriptor is 64 bytes");
-    for (int64_t i = 0; i < nu; ++i) ordered[i] = p.units[p.worker_units[i]];
-    p.units.swap(ordered);
-  }
+  std::vector<double> load;
+  balance_units(p, opts, n_workers, &load);
   if (lanes) {
     st = build_lane_programs(A, p, rowcnt, msg);
     if (st != CBSPMV_OK) return st;
     cb::ByteBuf().swap(p.stream);   // the record stream is not part of the lane-stream layout
   }
 
-  // --- statistics
-  cbspmv_stats_t& s = p.stats;
-  s = cbspmv_stats_t{};
-  s.m = A.m; s.n = A.n; s.nnz = A.nnz;
-  s.n_block_rows = nbr;
-  s.n_tiles = ntiles;
-  s.n_tiles_plain = plain_tiles.load();
-  s.super_sparse_fraction = frac;
-  s.aggregated = p.aggregated ? 1 : 0;
-  s.value_dtype = p.value_dtype;
-  int64_t mults = 0;
-  for (int64_t t = 0; t < ntiles; ++t) {
-    const CbTile& x = p.tiles[t];
-    s.n_fmt[x.fmt]++;
-    s.nnz_fmt[x.fmt] += x.nnz;
-    s.hist_coarse[std::min(7, (x.nnz - 1) / 32)]++;
-    if (x.nnz <= 32) s.hist_fine[(x.nnz - 1) / 8]++;
-    mults += x.fmt == CB_FMT_DENSE ? 256 : x.nnz;
-  }
-  s.restore_cols_len = p.restore_cols_len;
-  if (lanes) {
-    s.stream_bytes = (int64_t)(p.lane_vals.size() + p.lane_words.size()) * 8;
-    s.metadata_bytes = ntiles * (int64_t)sizeof(CbTile) + (int64_t)p.lane_gcols.size() * 4 +
-                       (int64_t)p.lane_units.size() * (int64_t)sizeof(CbLaneUnit);
-  } else {
-    s.stream_bytes = (int64_t)p.stream.size();
-    s.metadata_bytes = ntiles * (int64_t)sizeof(CbTile) + (int64_t)p.sched.size() * 4 +
-                       (int64_t)p.units.size() * (int64_t)sizeof(CbUnit);
-  }
-  s.lane_layout = lanes ? 1 : 0;
-  s.model_bytes_cb = ntiles * 21 + A.nnz * 9;
-  s.model_bytes_csr = (A.m + 1) * 4 + A.nnz * 12;
-  s.model_bytes_bsr16 = 2048 * ntiles + (nbr + 1) * 4 + 4 * ntiles;
-  const int64_t es = p.value_dtype == CBSPMV_F64 ? 8 : 4;   // x, y element size
-  s.algo_bytes_per_run = A.nnz * (int64_t)(p.vsize + 1) + ntiles * 21 + A.n * es + A.m * es +
-                         (p.aggregated ? 4 * p.restore_cols_len : 0);
-  s.flops_per_run = 2 * A.nnz;
-  s.mults_per_run = mults;
-  s.n_units = nu;
-  int64_t nsplit_units = 0;
-  for (auto& u : p.units) nsplit_units += u.split >= 0;
-  s.n_split_units = nsplit_units;
-  for (auto& u : p.units) {
-    s.n_entry_mode_units += (u.mode & CB_MODE_ENTRY) ? 1 : 0;
-    s.n_xseq_units += (u.mode & CB_MODE_XSEQ) ? 1 : 0;
-    s.n_direct_units += (u.mode & CB_MODE_DIRECT) ? 1 : 0;
-  }
-  s.fma_slots = p.fma_slots;
-  s.n_split_rows = p.n_split_rows;
-  s.n_workers = n_workers;
-  double lmax = 0, lsum = 0, lsq = 0;
-  for (double l : load) { lmax = std::max(lmax, l); lsum += l; lsq += l * l; }
-  s.worker_load_max = lmax;
-  s.worker_load_mean = lsum / n_workers;
-  s.worker_load_std = std::sqrt(std::max(0.0, lsq / n_workers - s.worker_load_mean * s.worker_load_mean));
-  {
-    int64_t ng = (ntiles + 7) / 8;
-    double gs = 0, gq = 0;
-    for (int64_t g = 0; g < ng; ++g) {
-      double v = 0;
-      for (int64_t t = 8 * g; t < std::min(ntiles, 8 * g + 8); ++t) v += p.tiles[t].nnz;
-      gs += v; gq += v * v;
-    }
-    double mean = ng ? gs / ng : 0;
-    s.tb8_load_std = ng ? std::sqrt(std::max(0.0, gq / ng - mean * mean)) : 0.0;
-  }
-  s.analyze_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  fill_stats(p, plain_tiles.load(), frac, load);
+  p.stats.analyze_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
   return CBSPMV_OK;
 }
 
@@ -1162,28 +1271,33 @@ cbspmv_status_t decode_to_csr(int64_t m, int64_t n, int dtype, bool aggregated,
   return CBSPMV_OK;
 }
 
-cbspmv_status_t decode_lanes_to_csr(int64_t m, int64_t n, const std::vector<CbLaneUnit>& units,
-                                    const double* vals, size_t nvals, const uint64_t* words, size_t nwords,
+cbspmv_status_t decode_lanes_to_csr(int64_t m, int64_t n, int dtype, const std::vector<CbLaneUnit>& units,
+                                    const uint8_t* vals, size_t nvals, const uint64_t* words, size_t nwords,
                                     const int32_t* gcols, size_t ngcols, int64_t* row_ptr, int32_t* col,
                                     double* val, int64_t nnz_expected, std::string* msg) {
+  const int vs = value_size(dtype);
+  const bool grouped = vs != 8;
   // every entry once: (global row, column, value), counted per row first
   std::vector<int64_t> cnt((size_t)m + 1, 0);
   auto for_each = [&](const std::function<bool(int64_t, int32_t, double)>& f) -> bool {
     for (const CbLaneUnit& u : units) {
       const size_t v0 = (size_t)u.vals * CB_VLANES, w0 = (size_t)u.words * CB_VLANES;
-      if (v0 + (size_t)u.steps * CB_VLANES > nvals || w0 + (size_t)((u.steps + 3) / 4) * CB_VLANES > nwords ||
-          (size_t)u.gcols + u.nslots > ngcols)
+      const uint32_t S = u.steps, Sp = grouped ? (S + CB_LANE_GROUP - 1) / CB_LANE_GROUP * CB_LANE_GROUP : S;
+      const bool plainx = (u.flags & CB_LUNIT_PLAINX) != 0;
+      const uint32_t ng = plainx ? (u.nslots / 16 + 3) / 4 * 4 : u.nslots;
+      if (v0 + (size_t)Sp * CB_VLANES > nvals || w0 + (size_t)((Sp + 3) / 4) * CB_VLANES > nwords ||
+          (size_t)u.gcols + ng > ngcols)
         return false;
-      for (uint32_t s = 0; s < u.steps; ++s)
+      for (uint32_t s = 0; s < S; ++s)
         for (uint32_t l = 0; l < CB_VLANES; ++l) {
-          const uint32_t w = (uint32_t)(words[w0 + (s / 4) * CB_VLANES + l] >> (16 * (s % 4))) & 0xffffu;
+          const uint32_t w = (uint32_t)(words[w0 + cb_lane_word_index(grouped, s, l)] >> (16 * (s % 4))) & 0xffffu;
           if (w == CB_LANE_NONE) continue;
           const uint32_t slot = w & 511u, r = w >> 9;
           if (slot >= u.nslots || r >= u.nrows) return false;
-          const int32_t c = gcols[u.gcols + slot];
+          const int64_t c = plainx ? (int64_t)gcols[u.gcols + slot / 16] + slot % 16 : (int64_t)gcols[u.gcols + slot];
           const int64_t row = (int64_t)u.brow_lo * CB_BLK + r;
           if (c < 0 || c >= n || row >= m) return false;
-          if (!f(row, c, vals[v0 + (size_t)s * CB_VLANES + l])) return false;
+          if (!f(row, (int32_t)c, read_value(vals + (v0 + cb_lane_val_index(grouped, s, l)) * vs, dtype))) return false;
         }
     }
     return true;

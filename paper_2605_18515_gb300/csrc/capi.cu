@@ -13,6 +13,7 @@
 
 #include "../../include/cbspmv.h"
 #include "cb_kernels.h"
+#include "cb_analyze_dev.h"
 #include "cb_noalloc.h"
 #include "cb_plan.h"
 #include "cb_spmm.h"
@@ -107,7 +108,7 @@ struct cbspmv_handle_s {
   double* d_valstage = nullptr;      // staging of host values for cbspmv_update_values
   // lane-stream layout (FP64 values)
   CbLaneUnit* d_lunits = nullptr;
-  double* d_lvals = nullptr;
+  uint8_t* d_lvals = nullptr;        // lvals_count values of the storage type
   uint64_t* d_lwords = nullptr;
   int32_t* d_lgcols = nullptr;
   size_t lvals_count = 0, lwords_count = 0, lgcols_count = 0;
@@ -187,12 +188,33 @@ cbspmv_status_t cbspmv_default_opts(cbspmv_opts_t* o) {
   return ok();
 }
 
+// True when the device analysis builds the handle of a device CSR: the lane-stream layout on
+// a device, and the three arrays in device memory of that device.
+static bool device_analysis_applies(const cbspmv_csr_t& A, const cbspmv_opts_t& o) {
+  const bool lanes = (o.value_dtype == CBSPMV_F64 && o.record_layout == 0) || o.record_layout == 2;
+  if (!A.on_device || o.device < 0 || !lanes) return false;
+  const void* ptrs[3] = {A.row_ptr, A.col_idx, A.val};
+  for (int i = 0; i < (A.nnz > 0 ? 3 : 1); ++i) {
+    cudaPointerAttributes at{};
+    if (!ptrs[i] || cudaPointerGetAttributes(&at, ptrs[i]) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    if ((at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) || at.device != o.device) return false;
+  }
+  return true;
+}
+
 cbspmv_status_t cbspmv_analyze(const cbspmv_csr_t* A, const cbspmv_opts_t* opts_in, void* stream,
                                cbspmv_handle_t* out) {
   if (!A || !out) return fail(CBSPMV_ERR_INVALID, "NULL argument");
   *out = nullptr;
-  if (A->on_device) {
-    // the analysis runs on the host: copy the three arrays down, then analyse the copy
+  cbspmv_opts_t opts;
+  if (opts_in) opts = *opts_in; else cbspmv_default_opts(&opts);
+  const bool dev_analysis = device_analysis_applies(*A, opts);
+  if (A->on_device && !dev_analysis) {
+    // the record layouts are analysed on the host: copy the three arrays down, then analyse
+    // the copy
     if (A->m < 0 || A->n < 0 || A->nnz < 0) return fail(CBSPMV_ERR_INVALID, "negative size");
     if (!A->row_ptr || (A->nnz > 0 && (!A->col_idx || !A->val))) return fail(CBSPMV_ERR_INVALID, "NULL CSR array");
     std::vector<int64_t> rp;
@@ -223,8 +245,6 @@ cbspmv_status_t cbspmv_analyze(const cbspmv_csr_t* A, const cbspmv_opts_t* opts_
   struct ResetFail {   // the injected failure applies to this call only
     ~ResetFail() { g_fail_alloc_after = -1; }
   } reset_fail;
-  cbspmv_opts_t opts;
-  if (opts_in) opts = *opts_in; else cbspmv_default_opts(&opts);
   if (opts.unit_work < 0 || opts.unit_work > 16384)
     return fail(CBSPMV_ERR_INVALID, "unit_work must be in [0, 16384]");
   int grid = 1;
@@ -248,8 +268,16 @@ cbspmv_status_t cbspmv_analyze(const cbspmv_csr_t* A, const cbspmv_opts_t* opts_
   if (!h) return fail(CBSPMV_ERR_OOM, "host allocation failed");
   std::string msg;
   cbspmv_status_t st;
+  cb::DevLanes dl;
   try {
-    st = cb::analyze_host(*A, opts, grid, &h->plan, &msg);
+    if (dev_analysis) {
+      DeviceGuard g(opts.device);
+      st = g.err == cudaSuccess ? cb::analyze_device(*A, opts, grid, (cudaStream_t)stream, dev_malloc, &h->plan, &dl, &msg)
+                                : CBSPMV_ERR_CUDA;
+      if (g.err != cudaSuccess) msg = cudaGetErrorString(g.err);
+    } else {
+      st = cb::analyze_host(*A, opts, grid, &h->plan, &msg);
+    }
   } catch (const std::bad_alloc&) {
     st = CBSPMV_ERR_OOM;
     msg = "host allocation failed during analysis";
@@ -275,12 +303,23 @@ cbspmv_status_t cbspmv_analyze(const cbspmv_csr_t* A, const cbspmv_opts_t* opts_
   h->stream_bytes = p.stream.size();
   cudaError_t e = cudaSuccess;
   auto step = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
-  if (p.lanes) {
+  if (dev_analysis) {
+    // the lane stream, restore_cols and the value map were built on the device
+    h->d_lunits = dl.lunits;
+    h->d_lvals = dl.lvals;
+    h->d_lwords = dl.lwords;
+    h->d_lgcols = dl.lgcols;
+    h->d_rcols = dl.rcols;
+    h->d_vslot = dl.vslot;
+    h->lvals_count = dl.lvals_count;
+    h->lwords_count = dl.lwords_count;
+    h->lgcols_count = dl.lgcols_count;
+  } else if (p.lanes) {
     step(upload(&h->d_lunits, p.lane_units.data(), p.lane_units.size(), s));
     step(upload(&h->d_lvals, p.lane_vals.data(), p.lane_vals.size(), s));
     step(upload(&h->d_lwords, p.lane_words.data(), p.lane_words.size(), s));
     step(upload(&h->d_lgcols, p.lane_gcols.data(), p.lane_gcols.size(), s));
-    h->lvals_count = p.lane_vals.size();
+    h->lvals_count = p.n_lane_vals;
     h->lwords_count = p.lane_words.size();
     h->lgcols_count = p.lane_gcols.size();
   } else {
@@ -535,8 +574,9 @@ cbspmv_status_t cbspmv_spmm(cbspmv_handle_t h, int k, const void* X, int64_t ldx
   if (k == 0 || p.m == 0) return ok();
   if (p.value_dtype != CBSPMV_BF16)
     return fail(CBSPMV_ERR_UNSUPPORTED, "cbspmv_spmm needs BF16 values (tensor-core path); use cbspmv_run_multi");
-  if (p.stats.n_direct_units != 0)
-    return fail(CBSPMV_ERR_UNSUPPORTED, "cbspmv_spmm needs a handle analysed with opts.plain_records = 1");
+  if (p.lanes || p.stats.n_direct_units != 0)
+    return fail(CBSPMV_ERR_UNSUPPORTED,
+                "cbspmv_spmm needs the record layout with opts.plain_records = 1 (not record_layout 2)");
   if ((!X && p.n > 0) || !Y) return fail(CBSPMV_ERR_INVALID, "NULL X or Y");
   if (((uintptr_t)X & 3) || ((uintptr_t)Y & 3)) return fail(CBSPMV_ERR_INVALID, "X and Y must be 4-byte aligned");
   if (X && p.n > 0) {
@@ -720,7 +760,7 @@ cbspmv_status_t cbspmv_update_values(cbspmv_handle_t h, const double* val, int o
     CB_CUDA(cudaMemcpyAsync(h->d_valstage, val, (size_t)p.nnz * 8, cudaMemcpyHostToDevice, s));
     dval = h->d_valstage;
   }
-  uint8_t* dst = p.lanes ? reinterpret_cast<uint8_t*>(h->d_lvals) : h->d_stream;
+  uint8_t* dst = p.lanes ? h->d_lvals : h->d_stream;
   CB_CUDA(cb::launch_repack(dst, h->d_vslot, dval, p.nnz, p.value_dtype, h->grid, s));
   return ok();
 }
@@ -748,22 +788,22 @@ cbspmv_status_t cbspmv_export_csr(cbspmv_handle_t h, int64_t* row_ptr, int32_t* 
   std::string msg;
   cbspmv_status_t st;
   if (p.lanes && h->device < 0) {
-    st = cb::decode_lanes_to_csr(p.m, p.n, p.lane_units, p.lane_vals.data(), p.lane_vals.size(), p.lane_words.data(),
-                                 p.lane_words.size(), p.lane_gcols.data(), p.lane_gcols.size(), row_ptr, col_idx, val,
-                                 p.nnz, &msg);
+    st = cb::decode_lanes_to_csr(p.m, p.n, p.value_dtype, p.lane_units, p.lane_vals.data(), p.n_lane_vals,
+                                 p.lane_words.data(), p.lane_words.size(), p.lane_gcols.data(), p.lane_gcols.size(),
+                                 row_ptr, col_idx, val, p.nnz, &msg);
   } else if (p.lanes) {
     // read the device-resident lane stream back and decode it
     DeviceGuard g(h->device);
     CB_CUDA(g.err);
-    std::vector<double> vals(h->lvals_count);
+    std::vector<uint8_t> vals(h->lvals_count * (size_t)p.vsize);
     std::vector<uint64_t> words(h->lwords_count);
     std::vector<int32_t> gcols(h->lgcols_count);
     CB_CUDA(cudaDeviceSynchronize());
-    if (!vals.empty()) CB_CUDA(cudaMemcpy(vals.data(), h->d_lvals, vals.size() * 8, cudaMemcpyDeviceToHost));
+    if (!vals.empty()) CB_CUDA(cudaMemcpy(vals.data(), h->d_lvals, vals.size(), cudaMemcpyDeviceToHost));
     if (!words.empty()) CB_CUDA(cudaMemcpy(words.data(), h->d_lwords, words.size() * 8, cudaMemcpyDeviceToHost));
     if (!gcols.empty()) CB_CUDA(cudaMemcpy(gcols.data(), h->d_lgcols, gcols.size() * 4, cudaMemcpyDeviceToHost));
-    st = cb::decode_lanes_to_csr(p.m, p.n, p.lane_units, vals.data(), vals.size(), words.data(), words.size(),
-                                 gcols.data(), gcols.size(), row_ptr, col_idx, val, p.nnz, &msg);
+    st = cb::decode_lanes_to_csr(p.m, p.n, p.value_dtype, p.lane_units, vals.data(), h->lvals_count, words.data(),
+                                 words.size(), gcols.data(), gcols.size(), row_ptr, col_idx, val, p.nnz, &msg);
   } else if (h->device < 0) {
     st = cb::decode_to_csr(p.m, p.n, p.value_dtype, p.aggregated, p.tiles, p.units, p.blob.data(), p.blob.size(),
                            p.stream.data(), p.stream.size(), p.restore_cols.data(), p.restore_cols.size(), row_ptr,
@@ -797,7 +837,16 @@ cbspmv_status_t cbspmv_export_blocked(cbspmv_handle_t h, int32_t* blk_row, int32
     if (type_per_blk) type_per_blk[t] = p.tiles[t].fmt;
   }
   if (cols_offset && p.aggregated) std::memcpy(cols_offset, p.cols_offset.data(), p.cols_offset.size() * 8);
-  if (restore_cols && p.aggregated) std::memcpy(restore_cols, p.restore_cols.data(), (size_t)p.restore_cols_len * 4);
+  if (restore_cols && p.aggregated) {
+    if ((int64_t)p.restore_cols.size() >= p.restore_cols_len) {
+      std::memcpy(restore_cols, p.restore_cols.data(), (size_t)p.restore_cols_len * 4);
+    } else {   // built by the device analysis: resident on the device only
+      DeviceGuard g(h->device);
+      CB_CUDA(g.err);
+      CB_CUDA(cudaDeviceSynchronize());
+      CB_CUDA(cudaMemcpy(restore_cols, h->d_rcols, (size_t)p.restore_cols_len * 4, cudaMemcpyDeviceToHost));
+    }
+  }
   return ok();
 }
 

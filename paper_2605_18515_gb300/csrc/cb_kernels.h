@@ -37,7 +37,7 @@ struct RunArgs {
   // lane-stream layout (FP64; lanes = 1): these replace stream, units and blob
   int lanes;
   const CbLaneUnit* lunits;     // units in worker order
-  const double* lvals;          // values, steps x 32 per unit
+  const void* lvals;            // values in the storage type (layout in cb_layout.h)
   const uint64_t* lwords;       // entry words, 4 per uint64
   const int32_t* lgcols;        // gather lists
 };

@@ -157,7 +157,7 @@ struct CbSplitRow {
 #define CB_UNIT_WORK_MAX 1024   // multiply-adds per unit (bounds the chunks per unit)
 #endif
 
-// ---- Lane-stream layout (FP64 values) ------------------------------------------------------
+// ---- Lane-stream layout (FP64 values; every value type with record_layout 2) -------------
 // On GB300 a warp-wide FP64 FMA holds its SM sub-partition's FP64 pipe for 76 cycles (the
 // pipe retires 32 lanes in that time whether they are active or not), so the FP64 kernel's
 // bound is the number of FMA slots it issues, and every issue slot not spent on a useful
@@ -167,17 +167,24 @@ struct CbSplitRow {
 // consumes them: the unit's stored entries, taken row by row (row, then sub-block, then
 // column), are dealt to the 32 lanes in runs of (nearly) equal length; step s of lane l is
 // entry c0(l) + s, c0(l) = floor(l * W / 32), W = the unit's entries.
-//   values: steps x 32 doubles, step-major (one coalesced 256-byte load per step);
+//   values, FP64: steps x 32 doubles, step-major (one coalesced 256-byte load per step);
 //           absent entries (past a lane's run) hold +0.0.
-//   words:  ceil(steps / 4) x 32 x uint64, each the four 16-bit entry words of steps
+//   values, FP32 / BF16 / FP16: the steps rounded up to groups of 8; per group 32 lanes x
+//           8 values, each lane's 8 steps contiguous (one 16-byte load per lane and group
+//           for the 2-byte types, two for FP32); absent entries hold +0.
+//   words, FP64: ceil(steps / 4) x 32 x uint64, each the four 16-bit entry words of steps
 //           4q .. 4q + 3 of one lane: bits [0, 9) x slot of the entry (16 * sub-block in
 //           the unit + column in the sub-block, the coordinate nibble of Sec. 3.2),
 //           bits [9, 16) row in the unit (16 * block row in the unit + row nibble; a
 //           unit holds at most 7 block rows, so a word of an entry is below 0xe000);
 //           0xffff = no entry.
-//   gather list: 16 per sub-block of the unit, the x column of every x slot
-//           (restore_cols[xbase + c] when aggregated, 16 * block column + c otherwise),
-//           -1 for slots past the block row's kept columns or past n.
+//   words, FP32 / BF16 / FP16: per group of 8 steps 32 lanes x 2 uint64 (steps 8g .. 8g+3,
+//           then 8g+4 .. 8g+7), the same 16-bit entry words.
+//   gather list, aggregated units: 16 per sub-block of the unit, the x column of every x
+//           slot (restore_cols[xbase + c]), -1 for slots past the block row's kept columns.
+//   gather list, plain units (CB_LUNIT_PLAINX, no aggregation): one per sub-block, its
+//           first column 16 * block column; slot 16 t + c reads x[gcols[t] + c] (zero at or
+//           past n). Padded to a multiple of 4 entries (16 bytes).
 // Every format keeps its stored entries only: Dense zero fill (Algorithm 4) would cost a
 // full FP64 FMA slot per zero. The sub-block records, formats and restore_cols stay the
 // analysis result (export_blocked, statistics); the record stream is not uploaded.
@@ -188,8 +195,28 @@ struct CbSplitRow {
 #define CB_LANE_NBR_MAX 7            // block rows per unit: rows <= 111, so no entry word is 0xffff
 #define CB_LANE_NONE 0xffffu
 #define CB_LUNIT_SCAN 1u             // some row spans more than CB_SCAN_SPAN lanes
+#define CB_LUNIT_PLAINX 2u           // plain sub-blocks: one gather-list entry per sub-block
+#define CB_LANE_GROUP 8              // steps per group of the reduced-type layout
+
+#ifdef __CUDACC__
+#define CB_LAYOUT_HD __host__ __device__
+#else
+#define CB_LAYOUT_HD
+#endif
+// Element index, from the unit's first value (vals * 32), of step st of lane l; grouped:
+// the reduced-type layout.
+CB_LAYOUT_HD inline uint32_t cb_lane_val_index(bool grouped, uint32_t st, uint32_t l) {
+  return grouped ? (st / CB_LANE_GROUP) * (CB_LANE_GROUP * CB_VLANES) + l * CB_LANE_GROUP + st % CB_LANE_GROUP
+                 : st * CB_VLANES + l;
+}
+// uint64 index, from the unit's first word row (words * 32), of the word holding step st of
+// lane l (at bit 16 * (st % 4)).
+CB_LAYOUT_HD inline uint32_t cb_lane_word_index(bool grouped, uint32_t st, uint32_t l) {
+  return grouped ? (st / CB_LANE_GROUP) * (2 * CB_VLANES) + 2 * l + (st % CB_LANE_GROUP) / 4
+                 : (st / 4) * CB_VLANES + l;
+}
 struct CbLaneUnit {                  // 32 bytes
-  uint32_t vals;        // first step of the unit's values (in steps of 32 doubles)
+  uint32_t vals;        // first step of the unit's values (in steps of 32 values)
   uint32_t words;       // first word row (in rows of 32 uint64)
   uint32_t gcols;       // first gather-list entry
   uint32_t brow_lo;     // first block row

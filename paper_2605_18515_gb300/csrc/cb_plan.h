@@ -8,6 +8,7 @@
 #include <string>
 #include <type_traits>
 #include <utility>
+#include <functional>
 #include <vector>
 
 #include "../../include/cbspmv.h"
@@ -67,9 +68,10 @@ struct Plan {
   // the three arrays are host copies, released once uploaded to a device.
   bool lanes = false;
   std::vector<CbLaneUnit> lane_units;
-  std::vector<double, NoInitAlloc<double>> lane_vals;
+  ByteBuf lane_vals;                    // values in the storage type (n_lane_vals of them)
   std::vector<uint64_t, NoInitAlloc<uint64_t>> lane_words;
   std::vector<int32_t, NoInitAlloc<int32_t>> lane_gcols;
+  size_t n_lane_vals = 0, n_lane_words = 0, n_lane_gcols = 0;   // element counts of the three arrays
 
   cbspmv_stats_t stats{};
 };
@@ -79,6 +81,22 @@ struct Plan {
 // *msg set.
 cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, int n_workers,
                              Plan* plan, std::string* msg);
+
+// Steps of the analysis shared by the host analysis and the device analysis of
+// analyze_dev.cu (which builds p.tiles, the block-row tile offsets and the aggregation on
+// the GPU, and the lane programs there too).
+void cut_units(Plan& p, const std::vector<int64_t>& tile_off, const cbspmv_opts_t& opts);
+cbspmv_status_t check_units(const Plan& p, std::string* msg);
+void balance_units(Plan& p, const cbspmv_opts_t& opts, int n_workers, std::vector<double>* load);
+cbspmv_status_t lane_offsets(Plan& p, std::vector<uint64_t>* voff, std::vector<uint64_t>* woff,
+                             std::vector<uint64_t>* goff, std::string* msg);
+void fill_stats(Plan& p, int64_t plain_tiles, double frac, const std::vector<double>& load);
+cbspmv_status_t validate_shape(const cbspmv_csr_t& A, std::string* msg);
+// f(lo, hi) over [0, n) in chunks of grain on all host cores
+void host_parallel_for(int64_t n, int64_t grain, const std::function<void(int64_t, int64_t)>& f);
+// sub-block format of a tile with nnz entries (Sec. 3.3.2): COO below th1, Dense above th2
+int tile_format(int nnz, int th1, int th2);
+cbspmv_status_t check_opts(const cbspmv_opts_t& opts, int n_workers, std::string* msg);
 
 // Rebuilds CSR from the packed layout (host arrays). Used by export on both host-only
 // handles and on data read back from the device. Stored values are widened exactly to FP64.
@@ -92,9 +110,10 @@ cbspmv_status_t decode_to_csr(int64_t m, int64_t n, int value_dtype, bool aggreg
                               int64_t nnz_expected, std::string* msg);
 
 // Rebuilds CSR from the lane-stream layout (host arrays: the units in worker order and
-// their values, entry words and gather lists, as described in cb_layout.h).
-cbspmv_status_t decode_lanes_to_csr(int64_t m, int64_t n, const std::vector<CbLaneUnit>& units,
-                                    const double* vals, size_t nvals, const uint64_t* words, size_t nwords,
+// their values (nvals of the storage type), entry words and gather lists, as described in
+// cb_layout.h). Stored values are widened exactly to FP64.
+cbspmv_status_t decode_lanes_to_csr(int64_t m, int64_t n, int value_dtype, const std::vector<CbLaneUnit>& units,
+                                    const uint8_t* vals, size_t nvals, const uint64_t* words, size_t nwords,
                                     const int32_t* gcols, size_t ngcols, int64_t* row_ptr, int32_t* col,
                                     double* val, int64_t nnz_expected, std::string* msg);
 

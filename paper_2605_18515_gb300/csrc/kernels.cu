@@ -880,20 +880,32 @@ __global__ void __launch_bounds__(256) combine_wide_kernel(const __grid_constant
 #ifndef CB_LANE_WARPS
 #define CB_LANE_WARPS 20       // worker warps per SM (measured on the FEM band: 16 -> 20 -> 24)
 #endif
-template <int kK>
+#ifndef CB_LANE_WARPS_LP
+#define CB_LANE_WARPS_LP 28    // the same for the 4- and 2-byte value types (20 -> 24 -> 28)
+#endif
+template <class Acc, int kK>
 struct LaneGeom {
-  static constexpr uint32_t kSlot = 8u * kK;                        // bytes of one x slot
-  static constexpr uint32_t kXBuf = CB_LANE_SLOTS * kSlot;          // one x buffer
-  static constexpr uint32_t kOffRow = 2 * kXBuf;                    // row sums, CB_R_MAX x kK
-  static constexpr uint32_t kOffCv = kOffRow + CB_R_MAX * 8u * kK;  // carry values, 32 x kK
-  static constexpr uint32_t kOffCr = kOffCv + CB_VLANES * 8u * kK;  // carry rows, 32
+  static constexpr uint32_t kSlot = (uint32_t)sizeof(Acc) * kK;       // bytes of one x slot
+  static constexpr uint32_t kXBuf = CB_LANE_SLOTS * kSlot;            // one x buffer
+  static constexpr uint32_t kOffRow = 2 * kXBuf;                      // row sums, CB_R_MAX x kK
+  static constexpr uint32_t kOffCv = kOffRow + CB_R_MAX * kSlot;      // carry values, 32 x kK
+  static constexpr uint32_t kOffCr = kOffCv + CB_VLANES * kSlot;      // carry rows, 32
   static constexpr uint32_t kWarpBytes = align128(kOffCr + 4u * CB_VLANES);
   static constexpr uint32_t kFit = (kSmemMax - kHeaderBytes) / kWarpBytes;
-  static constexpr int kWarps = kFit < (uint32_t)CB_LANE_WARPS ? (int)kFit : CB_LANE_WARPS;
+  // the FP64 walk is bound by the FP64 FMA pipe (20 warps measured best); the reduced types'
+  // walk by latency, where more warps per SM help (registers shrink to fit)
+  static constexpr int kWant = sizeof(Acc) == 8 ? CB_LANE_WARPS : CB_LANE_WARPS_LP;
+  static constexpr int kWarps = kFit < (uint32_t)kWant ? (int)kFit : kWant;
   static constexpr uint32_t kSmem = kHeaderBytes + kWarps * kWarpBytes;
   static_assert(kWarps >= 4, "lane kernel warp buffers too large");
 };
-constexpr int kLaneGroup = 8;   // steps per prefetch group (two words of four entries)
+constexpr int kLaneGroup = CB_LANE_GROUP;   // steps per prefetch group (two words of four entries)
+#ifndef CB_LANE_BATCH
+#define CB_LANE_BATCH 1        // groups per prefetch batch of the 4- and 2-byte value types
+#endif
+#ifndef CB_LANE_FASTROW
+#define CB_LANE_FASTROW 1      // reduced types: one row test per group of 8 entries
+#endif
 
 // streaming loads of read-only data that bypass L1 (plain asm: the compiler may predicate
 // and schedule them)
@@ -907,13 +919,63 @@ __device__ __forceinline__ uint64_t ldg_stream_u64(const uint64_t* p) {
   asm("ld.global.nc.L1::no_allocate.u64 %0, [%1];" : "=l"(v) : "l"(p));
   return v;
 }
+__device__ __forceinline__ uint4 ldg_stream_v4(const void* p) {
+  uint4 v;
+  asm("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+      : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+      : "l"(p));
+  return v;
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+// 16 bytes into shared memory, the first src_bytes of them from global memory, the rest zero
+__device__ __forceinline__ void cp_async_16(uint32_t dst_smem, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst_smem), "l"(src), "r"(src_bytes) : "memory");
+}
 
-template <int kMaxP, int kK>
-__global__ void __launch_bounds__(32 * LaneGeom<kK>::kWarps, 1)
+// The values of one group of 8 steps of a lane, as loaded: FP64 eight doubles (one per
+// step row), the reduced types their 16 or 32 contiguous bytes.
+template <class V> struct LaneVals;
+template <> struct LaneVals<double> {
+  double v[kLaneGroup];
+  __device__ __forceinline__ double at(int j) const { return v[j]; }
+};
+template <> struct LaneVals<float> {
+  uint4 a, b;
+  __device__ __forceinline__ float at(int j) const {
+    const uint4& q = j < 4 ? a : b;
+    const uint32_t w = (j & 3) == 0 ? q.x : (j & 3) == 1 ? q.y : (j & 3) == 2 ? q.z : q.w;
+    return __uint_as_float(w);
+  }
+};
+__device__ __forceinline__ uint32_t half_word(const uint4& a, int j) {
+  const uint32_t w = (j >> 1) == 0 ? a.x : (j >> 1) == 1 ? a.y : (j >> 1) == 2 ? a.z : a.w;
+  return (j & 1) ? w >> 16 : w & 0xffffu;
+}
+template <> struct LaneVals<__nv_bfloat16> {
+  uint4 a;
+  __device__ __forceinline__ float at(int j) const { return __uint_as_float(half_word(a, j) << 16); }
+};
+template <> struct LaneVals<__half> {
+  uint4 a;
+  __device__ __forceinline__ float at(int j) const {
+    return __half2float(__ushort_as_half((unsigned short)half_word(a, j)));
+  }
+};
+
+// Lane-stream run kernel (layout in cb_layout.h): a persistent CTA per SM; its warps take
+// the CTA's units in turn. Per unit a warp gathers the unit's x values into shared memory
+// (cp.async, one unit ahead), then every lane walks its run of entries with one FMA per
+// entry, keeping the partial sum of its current row in a register; row sums go to
+// shared memory, rows that cross lane runs are joined through the neighbouring lanes, and
+// the unit's rows are written to y (or to the partial-sum slot of a block-row part).
+template <class V, int kMaxP, int kK>
+__global__ void __launch_bounds__(32 * LaneGeom<typename ValT<V>::Acc, kK>::kWarps, 1)
     spmv_lanes_kernel(const __grid_constant__ BatchArgs<kMaxP> b) {
-  using G = LaneGeom<kK>;
+  using Acc = typename ValT<V>::Acc;
+  using G = LaneGeom<Acc, kK>;
+  constexpr bool kGrouped = sizeof(V) != 8;
+  constexpr int kB = kGrouped ? CB_LANE_BATCH : 1;
   constexpr uint32_t kFull = 0xffffffffu;
   constexpr uint32_t kNone = 0xffffffffu;
   extern __shared__ __align__(128) uint8_t smem_raw[];
@@ -921,8 +983,8 @@ __global__ void __launch_bounds__(32 * LaneGeom<kK>::kWarps, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint8_t* W = smem_raw + kHeaderBytes + (uint32_t)warp * G::kWarpBytes;
   const uint32_t w_smem = smem_u32(W);
-  double* srow = reinterpret_cast<double*>(W + G::kOffRow);
-  double* cval = reinterpret_cast<double*>(W + G::kOffCv);
+  Acc* srow = reinterpret_cast<Acc*>(W + G::kOffRow);
+  Acc* cval = reinterpret_cast<Acc*>(W + G::kOffCv);
   int32_t* crow = reinterpret_cast<int32_t*>(W + G::kOffCr);
   const int P = b.count;
   if ((int)threadIdx.x < P) {
@@ -963,20 +1025,56 @@ __global__ void __launch_bounds__(32 * LaneGeom<kK>::kWarps, 1)
     u.nrows = (uint16_t)(d1.y & 0xffffu); u.flags = (uint16_t)(d1.y >> 16);
     u.slot = d1.z; u.pad = 0;
   };
-  // cp.async of the unit's x values into buffer `buf`: slot k gets x[gcols[k]] (kK vectors
-  // side by side); slots outside [0, n) read zero
+  // cp.async of the unit's x values into buffer `buf`: slot k gets x[column of slot k] (kK
+  // vectors side by side); slots outside [0, n) read zero. Plain sub-blocks: 16
+  // consecutive x values per sub-block in 16-byte copies when x is 16-byte aligned.
   auto gather = [&](int q, const CbLaneUnit& u, uint32_t buf) {
     constexpr int kPer = CB_LANE_SLOTS / 32;
     const RunArgs& a = b.p[q];
-    const double* x = static_cast<const double*>(a.x);
+    const Acc* x = static_cast<const Acc*>(a.x);
     const int32_t* gc = a.lgcols + u.gcols;
+    const uint32_t dst = w_smem + buf * G::kXBuf;
+    if (kGrouped && (u.flags & CB_LUNIT_PLAINX)) {   // (the FP64 layout keeps per-slot lists)
+      const uint32_t nt = u.nslots / 16u;
+      const int32_t c0 = (uint32_t)lane < nt ? __ldg(gc + lane) : 0;
+      if (kK == 1 && (reinterpret_cast<uintptr_t>(x) & 15u) == 0) {
+        constexpr uint32_t kPerChunk = 16u / sizeof(Acc);          // x values per 16-byte copy
+        constexpr uint32_t kChunks = 16u / kPerChunk;              // copies per sub-block
+        const uint32_t total_chunks = nt * kChunks;
+        for (uint32_t k0 = 0; k0 < total_chunks; k0 += 32u) {
+          const uint32_t k = k0 + (uint32_t)lane;
+          const uint32_t t = k / kChunks, h = k % kChunks;
+          const int32_t ct = __shfl_sync(kFull, c0, (int)(t & 31u));
+          if (k < total_chunks) {
+            const int64_t col = (int64_t)ct + h * kPerChunk;
+            const int64_t left = a.n - col;
+            const uint32_t nb = left <= 0 ? 0u : left >= (int64_t)kPerChunk ? 16u : (uint32_t)left * (uint32_t)sizeof(Acc);
+            cp_async_16(dst + 16u * k, x + (nb ? col : 0), nb);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+          const uint32_t k = (uint32_t)lane + 32u * i;
+          const int32_t ct = __shfl_sync(kFull, c0, (int)((k / 16u) & 31u));
+          if (k < u.nslots) {
+            const int64_t col = (int64_t)ct + (k & 15u);
+            const bool ok = col < a.n;
+#pragma unroll
+            for (int j = 0; j < kK; ++j)
+              cp_async_elem<sizeof(Acc)>(dst + G::kSlot * k + (uint32_t)sizeof(Acc) * j,
+                                         x + (ok ? col + j * a.ldx : 0), ok ? (uint32_t)sizeof(Acc) : 0u);
+          }
+        }
+      }
+      return;
+    }
     int32_t c[kPer];
 #pragma unroll
     for (int i = 0; i < kPer; ++i) {
       const uint32_t k = (uint32_t)lane + 32u * i;
       c[i] = k < u.nslots ? __ldg(gc + k) : -1;
     }
-    const uint32_t dst = w_smem + buf * G::kXBuf;
 #pragma unroll
     for (int i = 0; i < kPer; ++i) {
       const uint32_t k = (uint32_t)lane + 32u * i;
@@ -984,25 +1082,46 @@ __global__ void __launch_bounds__(32 * LaneGeom<kK>::kWarps, 1)
         const bool ok = c[i] >= 0 && (int64_t)c[i] < a.n;
 #pragma unroll
         for (int j = 0; j < kK; ++j)
-          cp_async_elem<8>(dst + G::kSlot * k + 8u * j, x + (ok ? (int64_t)c[i] + j * a.ldx : 0), ok ? 8u : 0u);
+          cp_async_elem<sizeof(Acc)>(dst + G::kSlot * k + (uint32_t)sizeof(Acc) * j,
+                                     x + (ok ? (int64_t)c[i] + j * a.ldx : 0), ok ? (uint32_t)sizeof(Acc) : 0u);
       }
     }
   };
   // this lane's value and word streams of a unit
-  auto vbase = [&](int q, const CbLaneUnit& u) { return b.p[q].lvals + (size_t)u.vals * CB_VLANES + lane; };
-  auto wbase = [&](int q, const CbLaneUnit& u) { return b.p[q].lwords + (size_t)u.words * CB_VLANES + lane; };
+  auto vbase = [&](int q, const CbLaneUnit& u) -> const V* {
+    const V* v = static_cast<const V*>(b.p[q].lvals) + (size_t)u.vals * CB_VLANES;
+    return kGrouped ? v + (uint32_t)lane * kLaneGroup : v + lane;
+  };
+  auto wbase = [&](int q, const CbLaneUnit& u) -> const uint64_t* {
+    const uint64_t* w = b.p[q].lwords + (size_t)u.words * CB_VLANES;
+    return kGrouped ? w + 2u * (uint32_t)lane : w + lane;
+  };
   // values and entry words of steps 8g .. 8g + 7 (absent steps: no entry); plain loads the
   // compiler can predicate, with immediate offsets from the group's base
-  auto load_group = [&](const double* vp, const uint64_t* wp, uint32_t S, uint32_t g, double (&v)[kLaneGroup],
-                        uint64_t& w0, uint64_t& w1) {
-    const double* p = vp + kLaneGroup * CB_VLANES * g;
+  auto load_group = [&](const V* vp, const uint64_t* wp, uint32_t S, uint32_t g, LaneVals<V>& v, uint64_t& w0,
+                        uint64_t& w1) {
     const int rem = (int)S - (int)(kLaneGroup * g);
+    if constexpr (!kGrouped) {
+      const double* p = reinterpret_cast<const double*>(vp) + kLaneGroup * CB_VLANES * g;
 #pragma unroll
-    for (int j = 0; j < kLaneGroup; ++j)
-      if (j < rem) v[j] = ldg_stream_f64(p + CB_VLANES * j);
-    const uint64_t* pw = wp + 2u * CB_VLANES * g;
-    w0 = rem > 0 ? ldg_stream_u64(pw) : ~0ull;
-    w1 = rem > 4 ? ldg_stream_u64(pw + CB_VLANES) : ~0ull;
+      for (int j = 0; j < kLaneGroup; ++j)
+        if (j < rem) v.v[j] = ldg_stream_f64(p + CB_VLANES * j);
+      const uint64_t* pw = wp + 2u * CB_VLANES * g;
+      w0 = rem > 0 ? ldg_stream_u64(pw) : ~0ull;
+      w1 = rem > 4 ? ldg_stream_u64(pw + CB_VLANES) : ~0ull;
+    } else {
+      const V* p = vp + kLaneGroup * CB_VLANES * g;
+      const uint64_t* pw = wp + 2u * CB_VLANES * g;
+      if (rem > 0) {
+        v.a = ldg_stream_v4(p);
+        if constexpr (sizeof(V) == 4) v.b = ldg_stream_v4(p + 4);
+        const uint4 ww = ldg_stream_v4(pw);
+        w0 = ((uint64_t)ww.y << 32) | ww.x;
+        w1 = ((uint64_t)ww.w << 32) | ww.z;
+      } else {
+        w0 = w1 = ~0ull;
+      }
+    }
   };
 
   uint32_t t = grab();
@@ -1012,11 +1131,29 @@ __global__ void __launch_bounds__(32 * LaneGeom<kK>::kWarps, 1)
   fetch(t, q, u);
   gather(q, u, 0);
   cp_async_commit();
-  double va[kLaneGroup], vb[kLaneGroup];
-  uint64_t wa0, wa1, wb0 = ~0ull, wb1 = ~0ull;
+  // kB groups per prefetch batch: the reduced types' groups hold few bytes, so more of them
+  // are kept in flight per warp
+  struct Batch {
+    LaneVals<V> v[kB];
+    uint64_t w[2 * kB];
+  };
+  auto load_batch = [&](const V* vp, const uint64_t* wp, uint32_t S, uint32_t bi, Batch& bt) {
 #pragma unroll
-  for (int j = 0; j < kLaneGroup; ++j) va[j] = vb[j] = 0.0;
-  load_group(vbase(q, u), wbase(q, u), u.steps, 0, va, wa0, wa1);
+    for (int i = 0; i < kB; ++i) load_group(vp, wp, S, bi * kB + i, bt.v[i], bt.w[2 * i], bt.w[2 * i + 1]);
+  };
+  Batch ba, bb;
+#pragma unroll
+  for (int i = 0; i < kB; ++i) {
+    if constexpr (!kGrouped) {
+#pragma unroll
+      for (int j = 0; j < kLaneGroup; ++j) ba.v[i].v[j] = bb.v[i].v[j] = 0.0;
+    } else {
+      ba.v[i].a = bb.v[i].a = make_uint4(0, 0, 0, 0);
+      if constexpr (sizeof(V) == 4) ba.v[i].b = bb.v[i].b = make_uint4(0, 0, 0, 0);
+    }
+    bb.w[2 * i] = bb.w[2 * i + 1] = ~0ull;
+  }
+  load_batch(vbase(q, u), wbase(q, u), u.steps, 0, ba);
   uint32_t tn = grab();
   if (tn < total) fetch(tn, qn, un);
   uint32_t buf = 0;
@@ -1029,40 +1166,57 @@ __global__ void __launch_bounds__(32 * LaneGeom<kK>::kWarps, 1)
     if (tnn < total) fetch(tnn, qnn, unn);
     const RunArgs& a = b.p[q];
     const uint32_t R = u.nrows;
-    for (uint32_t r = lane; r < R * kK; r += 32) srow[r] = 0.0;
+    for (uint32_t r = lane; r < R * kK; r += 32) srow[r] = (Acc)0;
     cp_async_wait_one();                       // this unit's x values have landed
     __syncwarp();
     const uint8_t* xs = W + buf * G::kXBuf;
 
     // walk
-    double acc[kK], head[kK];
+    Acc acc[kK], head[kK];
 #pragma unroll
-    for (int j = 0; j < kK; ++j) acc[j] = head[j] = 0.0;
+    for (int j = 0; j < kK; ++j) acc[j] = head[j] = (Acc)0;
     uint32_t cur = kNone, first_row = kNone;
     bool have_head = false;
     const uint32_t ngroups = (u.steps + kLaneGroup - 1u) / kLaneGroup;
-    const double* vp = vbase(q, u);
+    const V* vp = vbase(q, u);
     const uint64_t* wp = wbase(q, u);
-    const double* vpn = tn < total ? vbase(qn, un) : vp;
+    const V* vpn = tn < total ? vbase(qn, un) : vp;
     const uint64_t* wpn = tn < total ? wbase(qn, un) : wp;
     const uint32_t Sn = tn < total ? un.steps : 0u;
     // the entries of one group: x operands first (slot 511 of an absent entry lies inside the
     // buffer and is not used), then the FMA chain with the rare row switch
-    auto compute = [&](const double (&v)[kLaneGroup], uint64_t w0, uint64_t w1) {
-      double xv[kLaneGroup][kK];
+    auto compute = [&](const LaneVals<V>& v, uint64_t w0, uint64_t w1) {
+#if CB_LANE_FASTROW
+      if constexpr (kGrouped && kK == 1) {
+        // the common case of the reduced types, whose walk is bound by instruction issue:
+        // all 8 entries of the group continue the current row (row bits of every word
+        // equal cur), so no row switch is tested per entry and two partial sums break the
+        // FMA dependency chain
+        const uint64_t row_bits = 0xFE00FE00FE00FE00ull;
+        const uint64_t pat = (uint64_t)cur * 0x0200020002000200ull;
+        if (cur < 128u && (w0 & row_bits) == pat && (w1 & row_bits) == pat) {
+          Acc s0 = (Acc)0, s1 = (Acc)0;
+#pragma unroll
+          for (int j = 0; j < kLaneGroup; ++j) {
+            const uint32_t slot = (uint32_t)((j < 4 ? w0 : w1) >> (16 * (j & 3))) & 511u;
+            const Acc xj = *reinterpret_cast<const Acc*>(xs + (uint32_t)sizeof(Acc) * slot);
+            if (j & 1) s1 = fma(v.at(j), xj, s1); else s0 = fma(v.at(j), xj, s0);
+          }
+          acc[0] += s0 + s1;
+          return;
+        }
+      }
+#endif
+      Acc xv[kLaneGroup][kK];
 #pragma unroll
       for (int j = 0; j < kLaneGroup; ++j) {
         const uint32_t w = (uint32_t)((j < 4 ? w0 : w1) >> (16 * (j & 3))) & 0xffffu;
         const uint32_t slot = w & 511u;
         if constexpr (kK == 1) {
-          xv[j][0] = *reinterpret_cast<const double*>(xs + 8u * slot);
+          xv[j][0] = *reinterpret_cast<const Acc*>(xs + (uint32_t)sizeof(Acc) * slot);
         } else {
 #pragma unroll
-          for (int h = 0; h < kK / 2; ++h) {
-            const double2 d2 = *reinterpret_cast<const double2*>(xs + G::kSlot * slot + 16u * h);
-            xv[j][2 * h] = d2.x;
-            xv[j][2 * h + 1] = d2.y;
-          }
+          for (int h = 0; h < kK; ++h) xv[j][h] = *reinterpret_cast<const Acc*>(xs + G::kSlot * slot + sizeof(Acc) * h);
         }
       }
 #pragma unroll
@@ -1081,35 +1235,38 @@ __global__ void __launch_bounds__(32 * LaneGeom<kK>::kWarps, 1)
             for (int h = 0; h < kK; ++h) srow[cur * kK + h] = acc[h];
           }
 #pragma unroll
-          for (int h = 0; h < kK; ++h) acc[h] = 0.0;
+          for (int h = 0; h < kK; ++h) acc[h] = (Acc)0;
           cur = r;
         }
         if (w != CB_LANE_NONE) {
+          const Acc vj = v.at(j);
 #pragma unroll
-          for (int h = 0; h < kK; ++h) acc[h] = fma(v[j], xv[j][h], acc[h]);
+          for (int h = 0; h < kK; ++h) acc[h] = fma(vj, xv[j][h], acc[h]);
         }
       }
     };
-    // two register sets in turn: the group after the current one (or the next unit's first
-    // group) is loaded while the current one is computed
-    uint32_t g = 0;
-    while (g < ngroups) {
-      if (g + 1 < ngroups) load_group(vp, wp, u.steps, g + 1, vb, wb0, wb1);
-      else load_group(vpn, wpn, Sn, 0, vb, wb0, wb1);
-      compute(va, wa0, wa1);
-      if (++g >= ngroups) {
+    auto compute_batch = [&](const Batch& bt) {
 #pragma unroll
-        for (int j = 0; j < kLaneGroup; ++j) va[j] = vb[j];
-        wa0 = wb0;
-        wa1 = wb1;
+      for (int i = 0; i < kB; ++i) compute(bt.v[i], bt.w[2 * i], bt.w[2 * i + 1]);
+    };
+    // two register sets in turn: the batch after the current one (or the next unit's first
+    // batch) is loaded while the current one is computed
+    const uint32_t nbatch = (ngroups + kB - 1u) / kB;
+    uint32_t g = 0;
+    while (g < nbatch) {
+      if (g + 1 < nbatch) load_batch(vp, wp, u.steps, g + 1, bb);
+      else load_batch(vpn, wpn, Sn, 0, bb);
+      compute_batch(ba);
+      if (++g >= nbatch) {
+        ba = bb;
         break;
       }
-      if (g + 1 < ngroups) load_group(vp, wp, u.steps, g + 1, va, wa0, wa1);
-      else load_group(vpn, wpn, Sn, 0, va, wa0, wa1);
-      compute(vb, wb0, wb1);
+      if (g + 1 < nbatch) load_batch(vp, wp, u.steps, g + 1, ba);
+      else load_batch(vpn, wpn, Sn, 0, ba);
+      compute_batch(bb);
       ++g;
     }
-    if (ngroups == 0) load_group(vpn, wpn, Sn, 0, va, wa0, wa1);   // (no entries) keep the prefetch in step
+    if (nbatch == 0) load_batch(vpn, wpn, Sn, 0, ba);   // (no entries) keep the prefetch in step
 
     // rows that cross lane runs: neighbours are the nearest lanes with entries
     const bool nonempty = cur != kNone;
@@ -1131,9 +1288,9 @@ __global__ void __launch_bounds__(32 * LaneGeom<kK>::kWarps, 1)
     const bool hs = nonempty && prev_ne >= 0 && prev_last == my_first;     // first row began earlier
     const bool open = nonempty && next_ne <= 31 && next_first == my_last;  // last row continues
     int32_t own_row = -1, carry_row = -1;
-    double own_val[kK], carry_val[kK];
+    Acc own_val[kK], carry_val[kK];
 #pragma unroll
-    for (int h = 0; h < kK; ++h) own_val[h] = carry_val[h] = 0.0;
+    for (int h = 0; h < kK; ++h) own_val[h] = carry_val[h] = (Acc)0;
     if (nonempty) {
       if (have_head) {           // two or more rows in this run
         if (hs) {
@@ -1171,7 +1328,7 @@ __global__ void __launch_bounds__(32 * LaneGeom<kK>::kWarps, 1)
       for (int h = 0; h < kK; ++h) cval[lane * kK + h] = carry_val[h];
       __syncwarp();
       if (own_row >= 0) {
-        double sum[kK];
+        Acc sum[kK];
 #pragma unroll
         for (int h = 0; h < kK; ++h) sum[h] = own_val[h];
         for (int l = lane - 1; l >= 0; --l) {
@@ -1189,7 +1346,7 @@ __global__ void __launch_bounds__(32 * LaneGeom<kK>::kWarps, 1)
       // without entries take the key of the nearest lane with entries before them
       const int32_t key0 = nonempty ? carry_row : -2;
       const int32_t key = __shfl_sync(kFull, key0, prev < 0 ? lane : prev);
-      double c2[kK];
+      Acc c2[kK];
 #pragma unroll
       for (int h = 0; h < kK; ++h) c2[h] = carry_val[h];
 #pragma unroll
@@ -1198,46 +1355,49 @@ __global__ void __launch_bounds__(32 * LaneGeom<kK>::kWarps, 1)
         const bool take = lane >= d && ko == key;
 #pragma unroll
         for (int h = 0; h < kK; ++h) {
-          const double vo = __shfl_up_sync(kFull, c2[h], d);
+          const Acc vo = __shfl_up_sync(kFull, c2[h], d);
           if (take) c2[h] += vo;
         }
       }
       const int32_t kprev = __shfl_up_sync(kFull, key, 1);
 #pragma unroll
       for (int h = 0; h < kK; ++h) {
-        const double pv = __shfl_up_sync(kFull, c2[h], 1);
-        if (own_row >= 0) srow[own_row * kK + h] = own_val[h] + (lane > 0 && kprev == own_row ? pv : 0.0);
+        const Acc pv = __shfl_up_sync(kFull, c2[h], 1);
+        if (own_row >= 0) srow[own_row * kK + h] = own_val[h] + (lane > 0 && kprev == own_row ? pv : (Acc)0);
       }
     }
     __syncwarp();
 
-    // outputs
+    // outputs (alpha and beta in the accumulation type)
     if (u.slot == 0xffffffffu) {
-      double* y = static_cast<double*>(a.y);
+      Acc* y = static_cast<Acc*>(a.y);
+      const Acc alpha = (Acc)a.alpha, beta = (Acc)a.beta;
       const int64_t row0 = (int64_t)u.brow_lo * CB_BLK;
       for (uint32_t r = lane; r < R; r += 32) {
 #pragma unroll
         for (int h = 0; h < kK; ++h) {
-          double* yh = y + (int64_t)h * a.ldy + row0 + r;
-          double v = srow[r * kK + h];
-          if (!a.alpha_one) v = a.alpha * v;
-          if (a.beta_nonzero) v = fma(a.beta, *yh, v);
+          Acc* yh = y + (int64_t)h * a.ldy + row0 + r;
+          Acc v = srow[r * kK + h];
+          if (!a.alpha_one) v = alpha * v;
+          if (a.beta_nonzero) v = fma(beta, *yh, v);
           *yh = v;
         }
       }
     } else {
-      double* partial = static_cast<double*>(a.partial);
+      Acc* partial = static_cast<Acc*>(a.partial);
       if (lane < 16) {
 #pragma unroll
         for (int h = 0; h < kK; ++h)
-          partial[((size_t)u.slot * 16 + lane) * kK + h] = (uint32_t)lane < R ? srow[lane * kK + h] : 0.0;
+          partial[((size_t)u.slot * 16 + lane) * kK + h] = (uint32_t)lane < R ? srow[lane * kK + h] : (Acc)0;
       }
     }
     // the gather list of the unit after next into L2 (one bulk prefetch by the TMA unit
-    // instead of 16 scattered cold loads per lane when its gather is issued)
-    if (tnn < total && lane == 0 && unn.nslots)
-      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(b.p[qnn].lgcols + unn.gcols),
-                   "r"(4u * unn.nslots) : "memory");
+    // instead of scattered cold loads when its gather is issued)
+    if (tnn < total && lane == 0 && unn.nslots) {
+      const uint32_t ng = (kGrouped && (unn.flags & CB_LUNIT_PLAINX)) ? (unn.nslots / 16u + 3u) & ~3u : unn.nslots;
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(b.p[qnn].lgcols + unn.gcols), "r"(4u * ng)
+                   : "memory");
+    }
     __syncwarp();
     if (tn >= total) break;
     t = tn; q = qn; u = un;
@@ -1266,15 +1426,15 @@ cudaError_t configure_typed() {
   return cudaSuccess;
 }
 
-template <int kMaxP, int kK>
+template <class V, int kMaxP, int kK>
 cudaError_t configure_lanes() {
   static std::atomic<bool> configured[64];
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64 || !configured[dev].load(std::memory_order_acquire)) {
-    e = cudaFuncSetAttribute(spmv_lanes_kernel<kMaxP, kK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)LaneGeom<kK>::kSmem);
+    e = cudaFuncSetAttribute(spmv_lanes_kernel<V, kMaxP, kK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)LaneGeom<typename ValT<V>::Acc, kK>::kSmem);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) configured[dev].store(true, std::memory_order_release);
   }
@@ -1299,16 +1459,18 @@ cudaError_t launch_combine(const BatchArgs<kMaxP>& b, cudaStream_t stream) {
   return e;
 }
 
-template <int kMaxP, int kK>
+template <class V, int kMaxP, int kK>
 cudaError_t launch_lanes(const BatchArgs<kMaxP>& b, int grid, cudaStream_t stream, cudaEvent_t* ev) {
-  cudaError_t e = configure_lanes<kMaxP, kK>();
+  using Acc = typename ValT<V>::Acc;
+  using G = LaneGeom<Acc, kK>;
+  cudaError_t e = configure_lanes<V, kMaxP, kK>();
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[0], stream)) != cudaSuccess) return e;
-  spmv_lanes_kernel<kMaxP, kK><<<grid, 32 * LaneGeom<kK>::kWarps, LaneGeom<kK>::kSmem, stream>>>(b);
+  spmv_lanes_kernel<V, kMaxP, kK><<<grid, 32 * G::kWarps, G::kSmem, stream>>>(b);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[1], stream)) != cudaSuccess) return e;
-  e = launch_combine<double, kMaxP, kK>(b, stream);
+  e = launch_combine<Acc, kMaxP, kK>(b, stream);
   if (e != cudaSuccess) return e;
   if (ev) e = cudaEventRecord(ev[2], stream);
   return e;
@@ -1357,16 +1519,23 @@ cudaError_t launch_nvec(const BatchArgs<kMaxP>& b, int grid, cudaStream_t stream
   }
 }
 
-template <int kMaxP>
+template <class V, int kMaxP>
 cudaError_t launch_lanes_nvec(const BatchArgs<kMaxP>& b, int grid, cudaStream_t stream, cudaEvent_t* ev) {
   // one vector per pass (the FP64 FMA pipe bounds the product; see cbspmv_run_multi)
-  return b.p[0].nvec == 1 ? launch_lanes<kMaxP, 1>(b, grid, stream, ev) : cudaErrorInvalidValue;
+  return b.p[0].nvec == 1 ? launch_lanes<V, kMaxP, 1>(b, grid, stream, ev) : cudaErrorInvalidValue;
 }
 
 template <int kMaxP>
 cudaError_t launch_dispatch(const BatchArgs<kMaxP>& b, int grid, cudaStream_t stream, cudaEvent_t* ev) {
-  if (b.p[0].lanes) return b.p[0].value_dtype == CBSPMV_F64 ? launch_lanes_nvec<kMaxP>(b, grid, stream, ev)
-                                                            : cudaErrorInvalidValue;
+  if (b.p[0].lanes) {
+    switch (b.p[0].value_dtype) {
+      case CBSPMV_F64: return launch_lanes_nvec<double, kMaxP>(b, grid, stream, ev);
+      case CBSPMV_F32: return launch_lanes_nvec<float, kMaxP>(b, grid, stream, ev);
+      case CBSPMV_BF16: return launch_lanes_nvec<__nv_bfloat16, kMaxP>(b, grid, stream, ev);
+      case CBSPMV_F16: return launch_lanes_nvec<__half, kMaxP>(b, grid, stream, ev);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (b.p[0].value_dtype) {
     case CBSPMV_F64: return launch_nvec<double, kMaxP>(b, grid, stream, ev);
     case CBSPMV_F32: return launch_nvec<float, kMaxP>(b, grid, stream, ev);
@@ -1405,7 +1574,8 @@ cudaError_t launch_repack(uint8_t* stream, const uint32_t* slot, const double* v
 
 size_t spmv_smem_bytes() {
   const uint32_t v[] = {Geom<double>::kSmem, Geom<float>::kSmem, Geom<__half>::kSmem, Geom<double, 4>::kSmem,
-                        Geom<float, 4>::kSmem, Geom<__half, 4>::kSmem, LaneGeom<1>::kSmem};
+                        Geom<float, 4>::kSmem, Geom<__half, 4>::kSmem, LaneGeom<double, 1>::kSmem,
+                        LaneGeom<float, 1>::kSmem};
   uint32_t m = 0;
   for (uint32_t x : v) m = x > m ? x : m;
   return m;
@@ -1429,8 +1599,14 @@ cudaError_t configure_value_type() {
 }
 
 cudaError_t configure_kernels() {
-  cudaError_t e = configure_lanes<1, 1>();
-  if (e == cudaSuccess) e = configure_lanes<kMaxBatch, 1>();
+  cudaError_t e = configure_lanes<double, 1, 1>();
+  if (e == cudaSuccess) e = configure_lanes<double, kMaxBatch, 1>();
+  if (e == cudaSuccess) e = configure_lanes<float, 1, 1>();
+  if (e == cudaSuccess) e = configure_lanes<float, kMaxBatch, 1>();
+  if (e == cudaSuccess) e = configure_lanes<__nv_bfloat16, 1, 1>();
+  if (e == cudaSuccess) e = configure_lanes<__nv_bfloat16, kMaxBatch, 1>();
+  if (e == cudaSuccess) e = configure_lanes<__half, 1, 1>();
+  if (e == cudaSuccess) e = configure_lanes<__half, kMaxBatch, 1>();
   if (e == cudaSuccess) e = configure_value_type<double>();
   if (e == cudaSuccess) e = configure_value_type<float>();
   if (e == cudaSuccess) e = configure_value_type<__nv_bfloat16>();

@@ -4,7 +4,8 @@
 //
 // The paper motivates its preprocessing cost by repeated products, as in iterative
 // solvers (Sec. 4.5); it has no serving system. This engine keeps analysed matrices on
-// the device and advances every in-flight request by one step per tick:
+// the device and advances every in-flight request by one step per tick (a solve in its
+// inner CG phase by up to inner_steps iterations, which need no host decision):
 //   * a y = alpha*A*x + beta*y request needs one product;
 //   * a CG request for an SPD matrix solves A x = b by iterative refinement: the true
 //     residual r = b - A x and the solution update stay in FP64 (FP64-value product);
@@ -114,6 +115,9 @@ __global__ void __launch_bounds__(kVecThreads) vec_kernel(const __grid_constant_
   const int64_t i0 = (int64_t)blk * kVecBlock;
   const int64_t i1 = i0 + kVecBlock < v.n ? i0 + kVecBlock : v.n;
   const Scalars& s = sc[v.slot];
+  // the inner steps of a solve whose inner CG has converged do nothing (a tick may run
+  // several inner iterations; the device knows when a solve converged, the host later)
+  if ((v.op == kOpPQ || v.op == kOpUpdate || v.op == kOpDirection) && s.inner_done) return;
   T* d = static_cast<T*>(v.d);
   T* r = static_cast<T*>(v.r);
   T* p = static_cast<T*>(v.p);
@@ -184,6 +188,7 @@ __global__ void finalize_kernel(const __grid_constant__ VecBatch b, Scalars* sc,
   for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
   if (lane != 0) return;
   Scalars& s = sc[v.slot];
+  if ((v.op == kOpPQ || v.op == kOpUpdate) && s.inner_done) return;   // (see vec_kernel)
   const bool first_outer = q < 32 ? ((first_outer_mask_lo >> q) & 1u) : ((first_outer_mask_hi >> (q - 32)) & 1u);
   switch (v.op) {
     case kOpRefineDot:
@@ -269,6 +274,7 @@ struct Req {
   Phase ph = kPhSpmv;
   bool fresh = true;   // admitted this tick: inputs to copy in
   int outer = 0;
+  int inner_seen = 0;   // inner iterations of the current correction already counted
   size_t off = 0, bytes = 0;
   // device workspace (inside the arena)
   double *x64 = nullptr, *r64 = nullptr, *b64 = nullptr, *y64 = nullptr;
@@ -513,6 +519,35 @@ cbspmv_status_t cbspmv_server_s::tick(std::vector<std::shared_ptr<Req>>& act, st
   for (auto& r : act)
     if (r->ph == kPhInner) add(v3, r, kOpDirection);
   cu(vec(v3), "direction step");
+  // 4b. further inner iterations of the solves in their inner phase: q = A p, alpha,
+  //     updates, direction; a solve whose inner CG converged meanwhile skips them (device)
+  {
+    std::vector<cb::RunArgs> lo2;
+    VecBatch vpq{}, vup{}, vdir{};
+    for (auto& r : act) {
+      if (r->ph != kPhInner) continue;
+      const Matrix& M = mats[r->q.matrix];
+      cb::RunArgs a{};
+      int g = 0, ns = 0, dt = 0;
+      cb::server_run_args(M.lo, r->p, r->qv, 1.0, 0.0, r->part_lo, &a, &g, &ns, &dt);
+      if (M.m) lo2.push_back(a);
+      grid = g;
+      add(vpq, r, kOpPQ);
+      add(vup, r, kOpUpdate);
+      add(vdir, r, kOpDirection);
+    }
+    for (int it = 1; it < o.inner_steps && vpq.count; ++it) {
+      if (!lo2.empty()) cu(cb::launch_spmv_batch(lo2.data(), (int)lo2.size(), grid, s), "batched product (inner)");
+      stats.launches += lo2.empty() ? 0 : 1;
+      cu(vec(vpq), "inner p.q");
+      finalize_kernel<<<(vpq.count + 3) / 4, 128, 0, s>>>(vpq, d_sc, 0u, 0u);
+      cu(cudaGetLastError(), "inner finalize 1");
+      cu(vec(vup), "inner update");
+      finalize_kernel<<<(vup.count + 3) / 4, 128, 0, s>>>(vup, d_sc, 0u, 0u);
+      cu(cudaGetLastError(), "inner finalize 2");
+      cu(vec(vdir), "inner direction");
+    }
+  }
   // 5. scalars back to the host, then decide every request's next step
   cu(cudaMemcpyAsync(h_sc, d_sc, sizeof(Scalars) * kMaxSlots, cudaMemcpyDeviceToHost, s), "copy scalars back");
   cu(cudaStreamSynchronize(s), "tick");
@@ -535,9 +570,11 @@ cbspmv_status_t cbspmv_server_s::tick(std::vector<std::shared_ptr<Req>>& act, st
         r->outer++;
         r->res.refinements = r->outer;
         r->ph = sc.inner_done ? kPhRefine : kPhInner;
+        r->inner_seen = 0;    // the refinement start reset the device's count
       }
     } else {
-      r->res.iterations++;
+      r->res.iterations += sc.inner_it - r->inner_seen;
+      r->inner_seen = sc.inner_it;
       if (sc.inner_done) r->ph = kPhRefine;
     }
   }
@@ -625,6 +662,7 @@ cbspmv_status_t cbspmv_server_default_opts(cbspmv_server_opts_t* o) {
   o->inner_tol = 1e-4;
   o->inner_max_iter = 2000;
   o->max_outer = 30;
+  o->inner_steps = 8;
   cb::set_last_error("");
   return CBSPMV_OK;
 }
@@ -641,6 +679,7 @@ cbspmv_status_t cbspmv_server_create(const cbspmv_server_opts_t* opts, cbspmv_se
     return sfail(CBSPMV_ERR_INVALID, "unknown cg_inner_dtype");
   if (!(o.inner_tol > 0.0 && o.inner_tol < 1.0) || o.inner_max_iter < 1 || o.max_outer < 1)
     return sfail(CBSPMV_ERR_INVALID, "inner_tol in (0, 1), inner_max_iter >= 1, max_outer >= 1");
+  if (o.inner_steps < 0 || o.inner_steps > 64) return sfail(CBSPMV_ERR_INVALID, "inner_steps must be in [0, 64]");
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
   if (e != cudaSuccess) return sfail(CBSPMV_ERR_CUDA, "cudaGetDeviceCount: %s", cudaGetErrorString(e));
@@ -650,6 +689,7 @@ cbspmv_status_t cbspmv_server_create(const cbspmv_server_opts_t* opts, cbspmv_se
   cudaSetDevice(o.device);
   auto* s = new (std::nothrow) cbspmv_server_s();
   if (!s) return sfail(CBSPMV_ERR_OOM, "host allocation failed");
+  if (o.inner_steps == 0) o.inner_steps = 8;
   s->o = o;
   e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMalloc((void**)&s->arena_base, (size_t)o.memory_budget);
@@ -689,6 +729,7 @@ cbspmv_status_t cbspmv_server_register(cbspmv_server_t s, const cbspmv_csr_t* A,
   if (st != CBSPMV_OK) return st;
   if (A->m == A->n) {    // square: CG requests possible; analyse the inner-solve values too
     o.value_dtype = s->o.cg_inner_dtype;
+    if (o.record_layout == 0) o.record_layout = 2;   // lane streams for the inner values too
     st = cbspmv_analyze(A, &o, s->stream, &M.lo);
     if (st != CBSPMV_OK) {
       cbspmv_destroy(M.hi);

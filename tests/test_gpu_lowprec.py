@@ -81,34 +81,40 @@ CASES = {
 }
 
 
+LAYOUTS = {"records": 0, "lanes": 2}
+
+
 @pytest.mark.parametrize("fmt", FMTS)
 @pytest.mark.parametrize("name", list(CASES))
-def test_lowprec_parity(env, fmt, name):
+@pytest.mark.parametrize("layout", list(LAYOUTS))
+def test_lowprec_parity(env, fmt, name, layout):
     A = CASES[name]()
     x = I.vector_x(A.n, 31)
-    y = run_lp(env, A, fmt, x)
+    y = run_lp(env, A, fmt, x, record_layout=LAYOUTS[layout])
     check_lowprec(A, fmt, x, y)
 
 
 @pytest.mark.parametrize("fmt", FMTS)
 @pytest.mark.parametrize("col_agg", [0, 1])
 @pytest.mark.parametrize("alpha,beta", [(2.5, 0.0), (-0.5, 0.25), (0.0, 2.0)])
-def test_lowprec_alpha_beta_aggregation(env, fmt, col_agg, alpha, beta):
+@pytest.mark.parametrize("layout", list(LAYOUTS))
+def test_lowprec_alpha_beta_aggregation(env, fmt, col_agg, alpha, beta, layout):
     A = I.random_csr(333, 517, 0.05, 13)
     x = I.vector_x(A.n, 32)
     y0 = I.uniform_pm1(33, I.TAG_Y, A.m)
-    y = run_lp(env, A, fmt, x, alpha, beta, y0, col_agg=col_agg)
+    y = run_lp(env, A, fmt, x, alpha, beta, y0, col_agg=col_agg, record_layout=LAYOUTS[layout])
     check_lowprec(A, fmt, x, y, alpha, beta, y0)
 
 
 @pytest.mark.parametrize("fmt", FMTS)
-def test_lowprec_split_rows_deterministic(env, fmt):
+@pytest.mark.parametrize("layout", list(LAYOUTS))
+def test_lowprec_split_rows_deterministic(env, fmt, layout):
     bd, torch = env
     r = np.repeat(np.arange(16), 900)
     c = np.tile(np.arange(900) * 3, 16)
     A = I.csr_from_coo(16, 2700, r, c, I.normal(5, I.TAG_VAL, r.size))
     x = I.vector_x(A.n, 34)
-    with bd.BlockedMatrix(A, value_dtype=fmt, unit_work=256) as M:
+    with bd.BlockedMatrix(A, value_dtype=fmt, unit_work=256, record_layout=LAYOUTS[layout]) as M:
         assert M.stats()["n_split_rows"] > 0
         xd = torch.from_numpy(f32(x)).cuda()
         outs = []
@@ -122,11 +128,12 @@ def test_lowprec_split_rows_deterministic(env, fmt):
 
 
 @pytest.mark.parametrize("fmt,k", [("bf16", 3), ("f32", 4), ("f16", 7)])
-def test_lowprec_run_multi_and_host(env, fmt, k):
+@pytest.mark.parametrize("layout", list(LAYOUTS))
+def test_lowprec_run_multi_and_host(env, fmt, k, layout):
     bd, torch = env
     A = I.fem_block_band(n_rows=6000, n_block_rows=2000, half_band=300, seed=3)
     X = np.stack([f32(I.vector_x(A.n, 50 + j)) for j in range(k)])
-    with bd.BlockedMatrix(A, value_dtype=fmt) as M:
+    with bd.BlockedMatrix(A, value_dtype=fmt, record_layout=LAYOUTS[layout]) as M:
         Xd = torch.from_numpy(X).cuda()
         Yd = torch.zeros((k, A.m), dtype=torch.float32, device="cuda")
         M.run_multi(Xd, Yd, 1.0, 0.0)
@@ -144,8 +151,8 @@ def test_lowprec_full_size_fem(env):
     deg = np.diff(A.row_ptr)
     rows = np.unique(np.concatenate([np.arange(64), np.arange(A.m - 64, A.m),
                                      (I.uniform01(6, 9, 20000) * A.m).astype(np.int64), np.argsort(deg)[-200:]]))
-    for fmt in FMTS:
-        with bd.BlockedMatrix(A, value_dtype=fmt) as M:
+    for fmt, layout in [(f, l) for f in FMTS for l in LAYOUTS.values()]:
+        with bd.BlockedMatrix(A, value_dtype=fmt, record_layout=layout) as M:
             xd = torch.from_numpy(f32(x)).cuda()
             yd = torch.empty(A.m, dtype=torch.float32, device="cuda")
             M.run(xd, yd)

@@ -133,6 +133,10 @@ def test_spmm_rejects_other_handles(env):
                 M.spmm(torch.zeros((R.n, 8), dtype=torch.float32, device="cuda"),
                        torch.zeros((R.m, 8), dtype=torch.float32, device="cuda"))
             assert ei.value.status == 6
+    with bd.BlockedMatrix(A, value_dtype="bf16", record_layout=2) as M:   # lane streams
+        with pytest.raises(bd.CbspmvError) as ei:
+            M.spmm(X, Y)
+        assert ei.value.status == 6
     with bd.BlockedMatrix(A, value_dtype="bf16", plain_records=True) as M:
         buf = torch.zeros((60, 8), dtype=torch.float32, device="cuda")
         with pytest.raises(bd.CbspmvError):

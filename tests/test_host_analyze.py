@@ -362,3 +362,48 @@ print(json.dumps(out))
     assert res["1"]["fem_f64"]["stats"]["n_block_rows"] > 3000
     assert res["1"]["rmat_f64"]["stats"]["n_units"] > 1000
     assert res["1"] == res["8"] == res[None]
+
+
+@pytest.mark.parametrize("fmt", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("name", ["random_ragged", "random_dense", "laplace2d_64", "rmat10"])
+@pytest.mark.parametrize("col_agg", [0, 1])
+def test_reduced_type_lane_layout_roundtrip(bd, fmt, name, col_agg):
+    """record_layout 2: the lane-stream layout for the 4- and 2-byte value types (steps in
+    groups of 8, plain sub-blocks with one gather entry each). The blocked structure is the
+    oracle's; export returns every value as the oracle's rounding of it to the storage type."""
+    from oracle import lowprec as L
+    A = CASES[name]() if name in CASES else I.rmat(10, 16, seed=3)
+    with host(bd, A, value_dtype=fmt, record_layout=2, col_agg=col_agg) as M:
+        st = M.stats()
+        assert st["lane_layout"] == 1
+        assert_same_structure(bd, A, M, col_agg=col_agg)
+        rp, col, val = M.export_csr()
+    assert np.array_equal(rp, A.row_ptr) and np.array_equal(col, A.col)
+    assert np.array_equal(val, L.round_to_format(A.val, fmt))
+    # values: steps rounded up to groups of 8 per unit, 32 lanes; words 2 bytes per value slot
+    vs = {"f32": 4, "bf16": 2, "f16": 2}[fmt]
+    assert st["stream_bytes"] == st["fma_slots"] * (vs + 2)
+    assert st["fma_slots"] % 256 == 0
+
+
+def test_plain_gather_lists_hold_one_column_per_sub_block(bd):
+    """Reduced-type lane units without aggregation keep the first column of each plain
+    sub-block in their gather list (padded to 4 entries); with aggregation, and in the FP64
+    lane layout, 16 columns per sub-block."""
+    from oracle import lowprec as L
+    A = I.random_csr(300, 280, 0.1, 4)
+    with host(bd, A, col_agg=0, value_dtype="bf16", record_layout=2) as M0, \
+            host(bd, A, col_agg=1, value_dtype="bf16", record_layout=2) as M1, host(bd, A, col_agg=0) as M2:
+        s0, s1, s2 = M0.stats(), M1.stats(), M2.stats()
+        for M in (M0, M1):
+            rp, col, val = M.export_csr()
+            assert np.array_equal(rp, A.row_ptr) and np.array_equal(col, A.col)
+            assert np.array_equal(val, L.round_to_format(A.val, "bf16"))
+        assert_roundtrip(M2, A)
+    g2 = s2["metadata_bytes"] - s2["n_tiles"] * 16 - 32 * s2["n_units"]
+    assert g2 == 4 * 16 * s2["n_tiles"]
+    tile_bytes = 16  # one CbTile record per sub-block
+    g0 = s0["metadata_bytes"] - s0["n_tiles"] * tile_bytes - 32 * s0["n_units"]
+    g1 = s1["metadata_bytes"] - s1["n_tiles"] * tile_bytes - 32 * s1["n_units"]
+    assert g1 == 4 * 16 * s1["n_tiles"]
+    assert s0["n_tiles"] * 4 <= g0 < (s0["n_tiles"] + 3 * s0["n_units"]) * 4 + 1
