@@ -294,11 +294,12 @@ cbspmv_status_t cbspmv_graph_destroy(cbspmv_graph_t g);
  * The thresholds of Sec. 3.3 are heuristics (th0 0.15, th1 32, th2 128). This call analyses
  * A with the given options, then varies one choice at a time, keeping the fastest so far:
  * column aggregation (auto / off / on: th0 only ever decides between these two layouts, so
- * they stand for every th0); for FP64 values the lane-stream unit size (1024, 4096 stored
- * entries) and then the record layout (record_layout = 1); for the record layout the unit
- * size (512, 768 multiply-adds) and the format thresholds (th1, th2) = (16, 64) and
- * (48, 192). The 16x16 sub-block is fixed (the 4-bit coordinates of Sec. 3.2) and so is the
- * number of warps per CTA (set by the kernels' shared-memory buffers per value type). Each
+ * they stand for every th0); for the reduced value types the lane-stream layout
+ * (record_layout = 2) against the records; for a lane-stream layout the unit size (1024,
+ * 4096 stored entries); for FP64 values the record layout (record_layout = 1); for the
+ * record layout the unit size (512, 768 multiply-adds) and the format thresholds
+ * (th1, th2) = (16, 64) and (48, 192). The 16x16 sub-block is fixed (the 4-bit coordinates
+ * of Sec. 3.2) and so is the number of warps per CTA (set per kernel and value type). Each
  * candidate is timed over `reps` products (1..10000) on the device. *out is the fastest
  * handle; *rep (may be NULL) lists the candidates. base->device must be a device. Every
  * handle computes the same product (only the layout differs). Errors: those of

@@ -1014,24 +1014,32 @@ cbspmv_status_t cbspmv_analyze_tuned(const cbspmv_csr_t* A, const cbspmv_opts_t*
       o.col_agg = other;
       st = consider(o);
     }
-    if (o0.value_dtype == CBSPMV_F64 && !o0.record_layout) {
-      // lane-stream unit sizes (stored entries per unit), then the record layout
+    if (o0.value_dtype != CBSPMV_F64 && !o0.record_layout && st == CBSPMV_OK) {
+      // the reduced types: the lane-stream layout against the default record layout
+      cbspmv_opts_t o = best_o;
+      o.record_layout = 2;
+      o.unit_work = 0;
+      st = consider(o);
+    }
+    if (best->plan.lanes && st == CBSPMV_OK) {
+      // lane-stream unit sizes (stored entries per unit)
       for (int uw : {1024, 4096})
         if (st == CBSPMV_OK) {
           cbspmv_opts_t o = best_o;
           o.unit_work = uw;
           st = consider(o);
         }
-      if (st == CBSPMV_OK) {
-        cbspmv_opts_t o = best_o;
-        o.record_layout = 1;
-        o.unit_work = 0;
-        st = consider(o);
-      }
+    }
+    if (o0.value_dtype == CBSPMV_F64 && !o0.record_layout && st == CBSPMV_OK) {
+      // FP64: the record layout against the lane-stream layout
+      cbspmv_opts_t o = best_o;
+      o.record_layout = 1;
+      o.unit_work = 0;
+      st = consider(o);
     }
     // the record layout's unit sizes and format thresholds (formats do not change the
     // lane-stream layout, which multiplies stored entries only)
-    if (best_o.value_dtype != CBSPMV_F64 || best_o.record_layout) {
+    if (st == CBSPMV_OK && !best->plan.lanes) {
       for (int uw : {512, 768})
         if (st == CBSPMV_OK) {
           cbspmv_opts_t o = best_o;

@@ -881,7 +881,7 @@ __global__ void __launch_bounds__(256) combine_wide_kernel(const __grid_constant
 #define CB_LANE_WARPS 20       // worker warps per SM (measured on the FEM band: 16 -> 20 -> 24)
 #endif
 #ifndef CB_LANE_WARPS_LP
-#define CB_LANE_WARPS_LP 28    // the same for the 4- and 2-byte value types (20 -> 24 -> 28)
+#define CB_LANE_WARPS_LP 32    // the same for the 4- and 2-byte value types (20 -> 24 -> 28 -> 32)
 #endif
 template <class Acc, int kK>
 struct LaneGeom {
@@ -895,6 +895,7 @@ struct LaneGeom {
   // the FP64 walk is bound by the FP64 FMA pipe (20 warps measured best); the reduced types'
   // walk by latency, where more warps per SM help (registers shrink to fit)
   static constexpr int kWant = sizeof(Acc) == 8 ? CB_LANE_WARPS : CB_LANE_WARPS_LP;
+  static_assert(kWant <= 32, "at most 1024 threads per CTA");
   static constexpr int kWarps = kFit < (uint32_t)kWant ? (int)kFit : kWant;
   static constexpr uint32_t kSmem = kHeaderBytes + kWarps * kWarpBytes;
   static_assert(kWarps >= 4, "lane kernel warp buffers too large");

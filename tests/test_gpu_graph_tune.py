@@ -74,14 +74,17 @@ def test_tuned_analysis(env, name, dtype):
 
 
 def test_tuned_analysis_reduced_type(env):
-    """BF16 values: the record layout's axes (aggregation, unit sizes, format thresholds);
-    the tuned handle's product stays within the FP32 bound of the stored-value product."""
+    """BF16 values: aggregation, the lane-stream layout against the records, then the
+    winning layout's axes (unit sizes; for records also the format thresholds); the tuned
+    handle's product stays within the FP32 bound of the stored-value product."""
     from oracle import lowprec as L
     bd, torch = env
     A = I.fem_block_band(n_rows=6000, n_block_rows=2000, half_band=300, seed=3)
     M, rep = bd.analyze_tuned(A, reps=5, value_dtype="bf16")
     with M:
-        assert 5 <= rep["n_tried"] <= 16 and all(t["record_layout"] == 0 for t in rep["tried"])
+        assert 5 <= rep["n_tried"] <= 16
+        assert any(t["record_layout"] == 2 for t in rep["tried"]) and rep["tried"][0]["record_layout"] == 0
+        assert rep["best_ms"] == min(t["ms"] for t in rep["tried"])
         x = I.vector_x(A.n, 13).astype(np.float32)
         yd = torch.zeros(A.m, dtype=torch.float32, device="cuda")
         M.run(torch.from_numpy(x).cuda(), yd)
