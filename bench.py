@@ -55,6 +55,7 @@ L2_BYTES = 129 * 2 ** 20
 KERNEL_TRAFFIC = {
     "run kernel rev 13": {("fem3x3_band_1m", "bf16"): 0.6535e9},
     "run kernel rev 15": {("fem3x3_band_1m", "f64"): 1.0187e9},
+    "run kernel rev 16": {("fem3x3_band_1m", "f64"): 1.0192e9},
 }
 
 
@@ -308,7 +309,7 @@ def batched_bench(bd, stream, ks=(1, 8, 32), reps=10, full=False):
             A = max(cls, key=lambda a: a.nnz)
             M, rep = bd.analyze_tuned(A, reps=5, value_dtype=dt, stream=stream)
             M.close()
-            best[(fam, dt)] = {k: rep["best"][k] for k in ("col_agg", "unit_work", "th1", "th2")}
+            best[(fam, dt)] = {k: rep["best"][k] for k in ("col_agg", "unit_work", "th1", "th2", "record_layout")}
     mats = [bd.BlockedMatrix(A, value_dtype=dt, stream=stream, **best[(fam, dt)]) for fam, dt, A in suite]
     out = {"matrices": len(suite), "families": "2D Laplacian, FEM 3x3 band, R-MAT (one third each)",
            "value_types": "FP32, BF16, FP16 in turn (FP32 x, y, accumulation)",
@@ -579,14 +580,14 @@ def serve_run(S, ids, mats, n_req, rate, seed):
             "launches": st["launches"] - st0["launches"]}
 
 
-def serve_bench(pool_name, seed=5, inner_steps=8):
+def serve_bench(pool_name, seed=5, inner_steps=8, max_cg=0):
     """Both modes' burst capacity; then Poisson arrivals at one common rate (70% of the
     one-at-a-time capacity, a load both modes sustain) for both, and the served mode also at
     70% of its own capacity."""
     from paper_2605_18515_gb300 import binding as bd
     mats, spec = serve_pool(pool_name)
     served_opts = dict(max_inflight=64, cg_inner_dtype="bf16", inner_tol=1e-4, memory_budget=8 << 30,
-                       inner_steps=inner_steps)
+                       inner_steps=inner_steps, max_inflight_cg=max_cg)
     base_opts = dict(max_inflight=1, cg_inner_dtype="f64", inner_tol=1e-9, memory_budget=8 << 30)
     with bd.Server(**base_opts) as S:
         ids = [S.register(A) for _, A, _ in mats]
@@ -602,7 +603,8 @@ def serve_bench(pool_name, seed=5, inner_steps=8):
                    f"{len(spec['rmat'])} R-MAT (scales {spec['rmat'][0][0]}-{spec['rmat'][-1][0]})",
            "mix": "70% y=Ax (FP64), 30% CG to 1e-8 relative residual",
            "served": {"mode": "continuous batching, 64 in flight, BF16-value CG with FP64 refinement, "
-                              f"{inner_steps} inner CG iterations per tick",
+                              f"{inner_steps} inner CG iterations per tick, "
+                              f"{max_cg or 64} CG solves in flight at most",
                       "capacity": cap, "poisson_same_load": same, "poisson_at_70pct": load},
            "one_at_a_time_fp64": {"mode": "one request at a time, FP64 products and FP64 CG",
                                   "capacity": bcap, "poisson_same_load": bload},
@@ -665,9 +667,14 @@ def main():
     ap.add_argument("--no-spmm", action="store_true", help="skip the tensor-core multi-vector measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-matrix batched measurement")
     ap.add_argument("--no-value-types", action="store_true", help="skip the reduced value types measurement")
+    ap.add_argument("--layout", choices=["default", "records", "lanes"], default="default",
+                    help="layout of the timed handle: default (FP64 lane streams, reduced types records), "
+                         "records, or lane streams for every value type")
     ap.add_argument("--batched-full", action="store_true", help="batched matrices up to 1e6 rows (default 2e5)")
     ap.add_argument("--serve-full", action="store_true",
                     help="serving measurement on the full pool (17 Laplacians, 15 R-MAT, 10,000 requests)")
+    ap.add_argument("--serve-max-cg", type=int, default=0,
+                    help="CG solves in flight at most in the served mode (0: no separate limit)")
     ap.add_argument("--serve-inner-steps", type=int, default=8,
                     help="inner CG iterations per tick of the served mode (1..64)")
     ap.add_argument("--traffic-bytes", type=float, default=None,
@@ -700,7 +707,8 @@ def main():
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         t_an = time.perf_counter()
-        M = bd.BlockedMatrix(A, device=local, stream=stream, value_dtype=args.dtype)
+        M = bd.BlockedMatrix(A, device=local, stream=stream, value_dtype=args.dtype,
+                             record_layout={"default": 0, "records": 1, "lanes": 2}[args.layout])
         stream.synchronize()
         host_call_ms = (time.perf_counter() - t_an) * 1e3
         st = M.stats()
@@ -876,7 +884,8 @@ def main():
         if not lp and ws == 1 and not args.no_value_types:
             line["value_types"] = value_types_bench(bd, A, x, stream)
         if not args.no_serve and ws == 1:
-            line["serving"] = serve_bench("full" if args.serve_full else "small", inner_steps=args.serve_inner_steps)
+            line["serving"] = serve_bench("full" if args.serve_full else "small", inner_steps=args.serve_inner_steps,
+                                          max_cg=args.serve_max_cg)
         if err:
             line["error_vs_fp64_oracle"] = err
         print(json.dumps(line), flush=True)

@@ -358,7 +358,8 @@ cbspmv_status_t cbspmv_measure_fp64_fma(int device, void* stream, double* gflops
  * from any host thread: y = alpha*A*x + beta*y products and CG solves of A x = b for
  * symmetric positive definite A. A background engine thread admits queued requests in
  * arrival order while a slot (max_inflight) and device memory (memory_budget, a pool the
- * server allocates once) are free, and advances every in-flight request by one step per
+ * server allocates once) are free (a CG request beyond max_inflight_cg solves in flight
+ * keeps its place while later products are admitted), and advances every in-flight request by one step per
  * tick: the products of all in-flight requests run as one batched launch of the run kernel
  * per value type (see cbspmv_run_batched), the CG vector steps as batched kernels; a solve
  * in its inner CG phase runs up to inner_steps inner iterations per tick (its scalars stay
@@ -379,7 +380,9 @@ typedef struct {
   int inner_max_iter;       /* inner CG iterations per correction (default 2000) */
   int max_outer;            /* refinement steps before a solve fails (default 30) */
   int inner_steps;          /* inner CG iterations per engine tick, 1..64 (default 8; 0 = 8) */
-  int reserved[7];
+  int max_inflight_cg;      /* CG solves in flight at most (0 = max_inflight); products keep
+                               being admitted past CG requests that wait for this limit */
+  int reserved[6];
 } cbspmv_server_opts_t;
 
 enum { CBSPMV_REQ_SPMV = 0, CBSPMV_REQ_CG = 1 };
@@ -414,7 +417,7 @@ typedef struct {
 
 /* Server defaults (no counterpart in the paper): device 0, 4 GiB budget, 64 in flight,
  * BF16 inner values, inner_tol 1e-4, 2000 inner iterations, 30 refinements, 8 inner
- * iterations per tick. */
+ * iterations per tick, no separate limit on CG solves in flight. */
 cbspmv_status_t cbspmv_server_default_opts(cbspmv_server_opts_t* opts);
 /* Creates a server (no counterpart in the paper; the repeated products that amortise the
  * analysis, Sec. 4.5): allocates the memory budget, a stream and the engine thread.

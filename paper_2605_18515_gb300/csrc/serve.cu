@@ -614,10 +614,21 @@ void cbspmv_server_s::engine() {
       std::unique_lock<std::mutex> lk(mu);
       cv_work.wait_for(lk, std::chrono::milliseconds(50), [&] { return stop || !queue.empty() || !inflight.empty(); });
       if (stop) break;
-      // admission in arrival order while a slot and memory are free
-      while (!queue.empty() && admit_one(queue.front())) {
-        inflight.push_back(queue.front());
-        queue.pop_front();
+      // admission in arrival order while a slot and memory are free; a CG request beyond
+      // the limit on solves in flight keeps its place, later products go past it
+      int cg_in = 0;
+      for (auto& r : inflight) cg_in += r->q.kind == CBSPMV_REQ_CG;
+      const int cg_cap = o.max_inflight_cg > 0 ? o.max_inflight_cg : kMaxSlots;
+      for (auto it = queue.begin(); it != queue.end();) {
+        const bool cg = (*it)->q.kind == CBSPMV_REQ_CG;
+        if (cg && cg_in >= cg_cap) {
+          ++it;
+          continue;
+        }
+        if (!admit_one(*it)) break;
+        cg_in += cg;
+        inflight.push_back(*it);
+        it = queue.erase(it);
       }
       act = inflight;
       stats.max_inflight_seen = std::max<int64_t>(stats.max_inflight_seen, (int64_t)act.size());
@@ -680,6 +691,8 @@ cbspmv_status_t cbspmv_server_create(const cbspmv_server_opts_t* opts, cbspmv_se
   if (!(o.inner_tol > 0.0 && o.inner_tol < 1.0) || o.inner_max_iter < 1 || o.max_outer < 1)
     return sfail(CBSPMV_ERR_INVALID, "inner_tol in (0, 1), inner_max_iter >= 1, max_outer >= 1");
   if (o.inner_steps < 0 || o.inner_steps > 64) return sfail(CBSPMV_ERR_INVALID, "inner_steps must be in [0, 64]");
+  if (o.max_inflight_cg < 0 || o.max_inflight_cg > kMaxSlots)
+    return sfail(CBSPMV_ERR_INVALID, "max_inflight_cg must be in [0, %d]", kMaxSlots);
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
   if (e != cudaSuccess) return sfail(CBSPMV_ERR_CUDA, "cudaGetDeviceCount: %s", cudaGetErrorString(e));

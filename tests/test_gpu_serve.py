@@ -158,3 +158,31 @@ def test_oversized_request_is_refused_at_submit(env):
         assert r["done"] and r["status"] == 0
         assert S.stats()["submitted"] == 1
     np.testing.assert_array_equal(y, solo_product(bd, torch, small, x))
+
+
+def test_cg_limit_lets_products_pass(env):
+    """max_inflight_cg = 1: solves run one at a time in arrival order while products
+    submitted behind a waiting solve are admitted and finish first; every result equals the
+    unlimited server's bit for bit (a request's result does not depend on the mix)."""
+    bd, torch = env
+    L = I.laplacian3d(16)
+    bs = [I.uniform_pm1(90 + i, I.TAG_RHS, L.n) for i in range(3)]
+    xs = [I.uniform_pm1(95 + i, I.TAG_X, L.n) for i in range(4)]
+    res = {}
+    for cap in (1, 0):
+        with bd.Server(max_inflight_cg=cap) as S:
+            mid = S.register(L)
+            cg = [S.submit_cg(mid, b, TOL) for b in bs]
+            pr = [S.submit_spmv(mid, x) for x in xs]
+            rp = [S.wait(t) for t, _ in pr]
+            rc = [S.wait(t) for t, _ in cg]
+            res[cap] = ([y for _, y in pr], [x for _, x in cg])
+            assert all(r["status"] == 0 for r in rp + rc)
+            if cap == 1:
+                # the products, submitted after three solves, finished before the last solve
+                assert max(r["t_done"] for r in rp) < rc[-1]["t_done"]
+                assert rc[0]["t_done"] <= rc[1]["t_done"] <= rc[2]["t_done"]
+    for a, b in zip(res[1][0] + res[1][1], res[0][0] + res[0][1]):
+        assert np.array_equal(a, b)
+    for x, b in zip(res[1][1], bs):
+        assert true_rel_residual(L, x, b) <= TOL * 1.0001
