@@ -145,6 +145,8 @@ typedef struct {
   int64_t n_direct_units;          /* units whose chunk descriptors hold value offsets and columns */
   int64_t lane_layout;             /* 1: lane-stream layout (see record_layout), 0: records */
   int64_t analyzed_on_device;      /* 1: built on the GPU from a device CSR (cbspmv_csr_t) */
+  int64_t n_g16_units;             /* lane-stream units whose gather lists are uint16 offsets */
+  int64_t gather_list_bytes;       /* lane-stream gather-list bytes one product reads */
 } cbspmv_stats_t;
 
 /* Fills *opts with the paper's settings: th0 0.15 (Sec. 3.3.1), th1 32 and th2 128

@@ -59,7 +59,8 @@ class Stats(ctypes.Structure):
                 ("tb8_load_std", ctypes.c_double), ("analyze_ms", ctypes.c_double),
                 ("n_entry_mode_units", ctypes.c_int64), ("n_xseq_units", ctypes.c_int64),
                 ("fma_slots", ctypes.c_int64), ("n_direct_units", ctypes.c_int64),
-                ("lane_layout", ctypes.c_int64), ("analyzed_on_device", ctypes.c_int64)]
+                ("lane_layout", ctypes.c_int64), ("analyzed_on_device", ctypes.c_int64),
+                ("n_g16_units", ctypes.c_int64), ("gather_list_bytes", ctypes.c_int64)]
 
 
 class ServerOpts(ctypes.Structure):

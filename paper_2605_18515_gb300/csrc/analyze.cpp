@@ -346,7 +346,7 @@ cbspmv_status_t lane_offsets(Plan& p, std::vector<uint64_t>* voff_out, std::vect
   voff.assign(nun + 1, 0);
   woff.assign(nun + 1, 0);
   goff.assign(nun + 1, 0);
-  const bool grouped = p.vsize != 8;    // the reduced-type layout: steps in groups of 8
+  const bool grouped = p.vsize != 8;    // the reduced-type layout: full groups of 8 steps
   // one gather-list entry per plain sub-block (4- and 2-byte value types; the FP64 kernel
   // keeps one entry per x slot, which measured faster there)
   const bool plainx = !p.aggregated && grouped;
@@ -356,10 +356,9 @@ cbspmv_status_t lane_offsets(Plan& p, std::vector<uint64_t>* voff_out, std::vect
     uint64_t W = 0;
     for (uint32_t t = 0; t < u.ntiles; ++t) W += p.tiles[u.tile_lo + t].nnz;
     const uint64_t S = (W + CB_VLANES - 1) / CB_VLANES;
-    const uint64_t Sp = grouped ? (S + CB_LANE_GROUP - 1) / CB_LANE_GROUP * CB_LANE_GROUP : S;
     steps[i] = S;
-    voff[i + 1] = voff[i] + Sp;
-    woff[i + 1] = woff[i] + (Sp + 3) / 4;
+    voff[i + 1] = voff[i] + S;
+    woff[i + 1] = woff[i] + (S + 3) / 4;
     goff[i + 1] = goff[i] + (plainx ? (u.ntiles + 3ull) / 4 * 4 : 16ull * u.ntiles);
   }
   if (voff[nun] >= (1ull << 32) || woff[nun] >= (1ull << 32) || goff[nun] >= (1ull << 32)) {
@@ -391,6 +390,25 @@ cbspmv_status_t lane_offsets(Plan& p, std::vector<uint64_t>* voff_out, std::vect
   p.n_lane_gcols = (size_t)goff[nun];
   p.fma_slots = (int64_t)voff[nun] * CB_VLANES;
   return CBSPMV_OK;
+}
+
+// A unit's per-slot gather list g (u.nslots columns, -1 for none) rewritten in place as
+// uint16 offsets from its smallest column when its columns span fewer than 65,535 values
+// (CB_LUNIT_G16; 0xffff for none): the list's bytes halve for banded matrices. The words
+// after the uint16 list keep their old contents (the list's space is not reclaimed).
+static void compact_gather_list(CbLaneUnit& u, int32_t* g) {
+  int64_t lo = INT64_MAX, hi = -1;
+  for (uint32_t k = 0; k < u.nslots; ++k)
+    if (g[k] >= 0) {
+      lo = std::min<int64_t>(lo, g[k]);
+      hi = std::max<int64_t>(hi, g[k]);
+    }
+  if (hi < 0 || hi - lo >= 0xffff) return;
+  uint16_t h[CB_LANE_SLOTS];
+  for (uint32_t k = 0; k < u.nslots; ++k) h[k] = g[k] < 0 ? (uint16_t)0xffffu : (uint16_t)(g[k] - lo);
+  std::memcpy(g, h, 2u * u.nslots);
+  u.flags |= CB_LUNIT_G16;
+  u.gbase = (uint32_t)lo;
 }
 
 // Lane-stream programs of every unit (layout in cb_layout.h), built from the packed records
@@ -470,9 +488,10 @@ static cbspmv_status_t build_lane_programs(const cbspmv_csr_t& A, Plan& p, const
         for (uint64_t k = c0; k < c1; ++k) {
           const uint64_t st = k - c0;
           const Ent& e = ent[k];
-          const uint32_t vi = cb_lane_val_index(grouped, (uint32_t)st, l);
+          const uint32_t S = p.lane_units[i].steps;
+          const uint32_t vi = cb_lane_val_index(grouped, (uint32_t)st, l, S);
           std::memcpy(vals + (size_t)vi * vs, p.stream.data() + (size_t)e.vidx * vs, vs);
-          uint64_t& w = words[cb_lane_word_index(grouped, (uint32_t)st, l)];
+          uint64_t& w = words[cb_lane_word_index(grouped, (uint32_t)st, l, S)];
           const uint32_t sh = 16u * (uint32_t)(st % 4);
           w = (w & ~(0xffffull << sh)) | ((uint64_t)e.word << sh);
           if (!moved.empty()) moved[e.vidx] = (uint32_t)((size_t)voff[i] * CB_VLANES + vi);
@@ -504,6 +523,7 @@ static cbspmv_status_t build_lane_programs(const cbspmv_csr_t& A, Plan& p, const
           g[16 * t + c] = (int32_t)col;
         }
       }
+      if (!(p.lane_units[i].flags & CB_LUNIT_PLAINX)) compact_gather_list(p.lane_units[i], g);
       p.lane_units[i].flags |= span_max > CB_SCAN_SPAN ? CB_LUNIT_SCAN : 0;
     }
   });
@@ -756,6 +776,11 @@ void fill_stats(Plan& p, int64_t plain_tiles, double frac, const std::vector<dou
     s.n_direct_units += (u.mode & CB_MODE_DIRECT) ? 1 : 0;
   }
   s.fma_slots = p.fma_slots;
+  for (const CbLaneUnit& L : p.lane_units) {
+    const bool plainx = (L.flags & CB_LUNIT_PLAINX) != 0, g16 = (L.flags & CB_LUNIT_G16) != 0;
+    s.n_g16_units += g16 ? 1 : 0;
+    s.gather_list_bytes += plainx ? 4 * (int64_t)((L.nslots / 16 + 3) / 4 * 4) : (g16 ? 2 : 4) * (int64_t)L.nslots;
+  }
   s.n_split_rows = p.n_split_rows;
   s.n_workers = n_workers;
   double lmax = 0, lsum = 0, lsq = 0;
@@ -1282,22 +1307,26 @@ cbspmv_status_t decode_lanes_to_csr(int64_t m, int64_t n, int dtype, const std::
   auto for_each = [&](const std::function<bool(int64_t, int32_t, double)>& f) -> bool {
     for (const CbLaneUnit& u : units) {
       const size_t v0 = (size_t)u.vals * CB_VLANES, w0 = (size_t)u.words * CB_VLANES;
-      const uint32_t S = u.steps, Sp = grouped ? (S + CB_LANE_GROUP - 1) / CB_LANE_GROUP * CB_LANE_GROUP : S;
-      const bool plainx = (u.flags & CB_LUNIT_PLAINX) != 0;
+      const uint32_t S = u.steps;
+      const bool plainx = (u.flags & CB_LUNIT_PLAINX) != 0, g16 = (u.flags & CB_LUNIT_G16) != 0;
       const uint32_t ng = plainx ? (u.nslots / 16 + 3) / 4 * 4 : u.nslots;
-      if (v0 + (size_t)Sp * CB_VLANES > nvals || w0 + (size_t)((Sp + 3) / 4) * CB_VLANES > nwords ||
+      if (v0 + (size_t)S * CB_VLANES > nvals || w0 + (size_t)((S + 3) / 4) * CB_VLANES > nwords ||
           (size_t)u.gcols + ng > ngcols)
         return false;
+      const uint16_t* g16p = reinterpret_cast<const uint16_t*>(gcols + u.gcols);
       for (uint32_t s = 0; s < S; ++s)
         for (uint32_t l = 0; l < CB_VLANES; ++l) {
-          const uint32_t w = (uint32_t)(words[w0 + cb_lane_word_index(grouped, s, l)] >> (16 * (s % 4))) & 0xffffu;
+          const uint32_t w = (uint32_t)(words[w0 + cb_lane_word_index(grouped, s, l, S)] >> (16 * (s % 4))) & 0xffffu;
           if (w == CB_LANE_NONE) continue;
           const uint32_t slot = w & 511u, r = w >> 9;
           if (slot >= u.nslots || r >= u.nrows) return false;
-          const int64_t c = plainx ? (int64_t)gcols[u.gcols + slot / 16] + slot % 16 : (int64_t)gcols[u.gcols + slot];
+          int64_t c;
+          if (plainx) c = (int64_t)gcols[u.gcols + slot / 16] + slot % 16;
+          else if (g16) c = g16p[slot] == 0xffffu ? -1 : (int64_t)u.gbase + g16p[slot];
+          else c = (int64_t)gcols[u.gcols + slot];
           const int64_t row = (int64_t)u.brow_lo * CB_BLK + r;
           if (c < 0 || c >= n || row >= m) return false;
-          if (!f(row, (int32_t)c, read_value(vals + (v0 + cb_lane_val_index(grouped, s, l)) * vs, dtype))) return false;
+          if (!f(row, (int32_t)c, read_value(vals + (v0 + cb_lane_val_index(grouped, s, l, S)) * vs, dtype))) return false;
         }
     }
     return true;

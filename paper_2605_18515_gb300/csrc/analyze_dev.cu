@@ -380,9 +380,31 @@ __global__ void __launch_bounds__(32 * kBuildWarps) lane_build_kernel(LaneBuildA
         cc = xb < a.n ? (int32_t)xb : -1;
       }
       w.g[k] = cc;
-      if (!plainx) a.lgcols[(size_t)L.gcols + k] = cc;
     }
     __syncwarp();
+    // per-slot list: uint16 offsets from the smallest column when the columns span fewer
+    // than 65,535 values (CB_LUNIT_G16), else the columns themselves
+    uint32_t g16 = 0, gbase = 0;
+    if (!plainx) {
+      int32_t lo = INT32_MAX, hi = -1;
+      for (int k = lane; k < 16 * ntiles; k += 32)
+        if (w.g[k] >= 0) {
+          lo = min(lo, w.g[k]);
+          hi = max(hi, w.g[k]);
+        }
+      for (int o = 16; o; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(kFull, lo, o));
+        hi = max(hi, __shfl_xor_sync(kFull, hi, o));
+      }
+      if (hi >= 0 && (int64_t)hi - lo < 0xffff) {
+        g16 = CB_LUNIT_G16;
+        gbase = (uint32_t)lo;
+        uint16_t* h = reinterpret_cast<uint16_t*>(a.lgcols + L.gcols);
+        for (int k = lane; k < 16 * ntiles; k += 32) h[k] = w.g[k] < 0 ? (uint16_t)0xffffu : (uint16_t)(w.g[k] - lo);
+      } else {
+        for (int k = lane; k < 16 * ntiles; k += 32) a.lgcols[(size_t)L.gcols + k] = w.g[k];
+      }
+    }
     int carry = 0;
     for (int r0 = 0; r0 < R; r0 += 32) {   // CSR range of every row and their prefix
       const int lr = r0 + lane;
@@ -437,10 +459,9 @@ __global__ void __launch_bounds__(32 * kBuildWarps) lane_build_kernel(LaneBuildA
     }
     const int vs = a.dtype == CBSPMV_F64 ? 8 : a.dtype == CBSPMV_F32 ? 4 : 2;
     const bool grouped = vs != 8;
-    const int Sp = grouped ? (S + CB_LANE_GROUP - 1) / CB_LANE_GROUP * CB_LANE_GROUP : S;
     uint64_t wacc = ~0ull;
     bool bad = false;
-    for (int st = 0; st < Sp; ++st) {
+    for (int st = 0; st < S; ++st) {
       const int k = c0 + st;
       uint64_t v = 0;   // stored bits
       uint32_t word = 0xffffu;
@@ -458,16 +479,16 @@ __global__ void __launch_bounds__(32 * kBuildWarps) lane_build_kernel(LaneBuildA
         }
         bad |= lo >= s1 || w.g[lo] != cc;
         word = (uint32_t)lo | ((uint32_t)lr << 9);
-        if (a.vslot) a.vslot[pos] = L.vals * CB_VLANES + cb_lane_val_index(grouped, (uint32_t)st, (uint32_t)lane);
+        if (a.vslot) a.vslot[pos] = L.vals * CB_VLANES + cb_lane_val_index(grouped, (uint32_t)st, (uint32_t)lane, S);
       }
-      const size_t vi = (size_t)L.vals * CB_VLANES + cb_lane_val_index(grouped, (uint32_t)st, (uint32_t)lane);
+      const size_t vi = (size_t)L.vals * CB_VLANES + cb_lane_val_index(grouped, (uint32_t)st, (uint32_t)lane, S);
       if (vs == 8) reinterpret_cast<uint64_t*>(a.lvals)[vi] = v;
       else if (vs == 4) reinterpret_cast<uint32_t*>(a.lvals)[vi] = (uint32_t)v;
       else reinterpret_cast<uint16_t*>(a.lvals)[vi] = (uint16_t)v;
       const int sh = 16 * (st & 3);
       wacc = (wacc & ~(0xffffull << sh)) | ((uint64_t)word << sh);
-      if ((st & 3) == 3 || st == Sp - 1) {
-        a.lwords[(size_t)L.words * CB_VLANES + cb_lane_word_index(grouped, (uint32_t)st, (uint32_t)lane)] = wacc;
+      if ((st & 3) == 3 || st == S - 1) {
+        a.lwords[(size_t)L.words * CB_VLANES + cb_lane_word_index(grouped, (uint32_t)st, (uint32_t)lane, S)] = wacc;
         wacc = ~0ull;
       }
     }
@@ -478,8 +499,11 @@ __global__ void __launch_bounds__(32 * kBuildWarps) lane_build_kernel(LaneBuildA
       if (e1 > e0) span = max(span, (32 * e1 - 1) / W - (32 * (e0 + 1) - 1) / W + 1);
     }
     for (int o = 16; o; o >>= 1) span = max(span, __shfl_xor_sync(kFull, span, o));
-    if (lane == 0)
-      a.lunits[u].flags = (uint16_t)((L.flags & ~CB_LUNIT_SCAN) | (span > CB_SCAN_SPAN ? CB_LUNIT_SCAN : 0));
+    if (lane == 0) {
+      a.lunits[u].flags =
+          (uint16_t)((L.flags & ~(CB_LUNIT_SCAN | CB_LUNIT_G16)) | (span > CB_SCAN_SPAN ? CB_LUNIT_SCAN : 0) | g16);
+      a.lunits[u].gbase = gbase;
+    }
     __syncwarp();
   }
 }

@@ -169,19 +169,25 @@ struct CbSplitRow {
 // entry c0(l) + s, c0(l) = floor(l * W / 32), W = the unit's entries.
 //   values, FP64: steps x 32 doubles, step-major (one coalesced 256-byte load per step);
 //           absent entries (past a lane's run) hold +0.0.
-//   values, FP32 / BF16 / FP16: the steps rounded up to groups of 8; per group 32 lanes x
-//           8 values, each lane's 8 steps contiguous (one 16-byte load per lane and group
-//           for the 2-byte types, two for FP32); absent entries hold +0.
+//   values, FP32 / BF16 / FP16: full groups of 8 steps, per group 32 lanes x 8 values,
+//           each lane's 8 steps contiguous (one 16-byte load per lane and group for the
+//           2-byte types, two for FP32); then the last t = steps mod 8 steps (if any) as
+//           32 lanes x t values, each lane's t contiguous (no padding to a full group);
+//           absent entries hold +0.
 //   words, FP64: ceil(steps / 4) x 32 x uint64, each the four 16-bit entry words of steps
 //           4q .. 4q + 3 of one lane: bits [0, 9) x slot of the entry (16 * sub-block in
 //           the unit + column in the sub-block, the coordinate nibble of Sec. 3.2),
 //           bits [9, 16) row in the unit (16 * block row in the unit + row nibble; a
 //           unit holds at most 7 block rows, so a word of an entry is below 0xe000);
 //           0xffff = no entry.
-//   words, FP32 / BF16 / FP16: per group of 8 steps 32 lanes x 2 uint64 (steps 8g .. 8g+3,
-//           then 8g+4 .. 8g+7), the same 16-bit entry words.
+//   words, FP32 / BF16 / FP16: per full group of 8 steps 32 lanes x 2 uint64 (steps
+//           8g .. 8g+3, then 8g+4 .. 8g+7), the same 16-bit entry words; the last t steps:
+//           32 lanes x ceil(t / 4) uint64.
 //   gather list, aggregated units: 16 per sub-block of the unit, the x column of every x
 //           slot (restore_cols[xbase + c]), -1 for slots past the block row's kept columns.
+//           When the unit's columns span fewer than 65,535 values (CB_LUNIT_G16), the
+//           same list as uint16 offsets from the unit's first column (gbase), 0xffff for
+//           -1, in the first half of the list's 32-bit space (half the bytes to read).
 //   gather list, plain units (CB_LUNIT_PLAINX, no aggregation): one per sub-block, its
 //           first column 16 * block column; slot 16 t + c reads x[gcols[t] + c] (zero at or
 //           past n). Padded to a multiple of 4 entries (16 bytes).
@@ -196,6 +202,7 @@ struct CbSplitRow {
 #define CB_LANE_NONE 0xffffu
 #define CB_LUNIT_SCAN 1u             // some row spans more than CB_SCAN_SPAN lanes
 #define CB_LUNIT_PLAINX 2u           // plain sub-blocks: one gather-list entry per sub-block
+#define CB_LUNIT_G16 4u              // per-slot gather list as uint16 offsets from gbase
 #define CB_LANE_GROUP 8              // steps per group of the reduced-type layout
 
 #ifdef __CUDACC__
@@ -203,17 +210,21 @@ struct CbSplitRow {
 #else
 #define CB_LAYOUT_HD
 #endif
-// Element index, from the unit's first value (vals * 32), of step st of lane l; grouped:
-// the reduced-type layout.
-CB_LAYOUT_HD inline uint32_t cb_lane_val_index(bool grouped, uint32_t st, uint32_t l) {
-  return grouped ? (st / CB_LANE_GROUP) * (CB_LANE_GROUP * CB_VLANES) + l * CB_LANE_GROUP + st % CB_LANE_GROUP
-                 : st * CB_VLANES + l;
+// Element index, from the unit's first value (vals * 32), of step st of lane l in a unit of
+// S steps; grouped: the reduced-type layout.
+CB_LAYOUT_HD inline uint32_t cb_lane_val_index(bool grouped, uint32_t st, uint32_t l, uint32_t S) {
+  if (!grouped) return st * CB_VLANES + l;
+  const uint32_t full = S / CB_LANE_GROUP * CB_LANE_GROUP;   // steps in full groups
+  if (st < full) return (st / CB_LANE_GROUP) * (CB_LANE_GROUP * CB_VLANES) + l * CB_LANE_GROUP + st % CB_LANE_GROUP;
+  return full * CB_VLANES + l * (S - full) + (st - full);
 }
 // uint64 index, from the unit's first word row (words * 32), of the word holding step st of
-// lane l (at bit 16 * (st % 4)).
-CB_LAYOUT_HD inline uint32_t cb_lane_word_index(bool grouped, uint32_t st, uint32_t l) {
-  return grouped ? (st / CB_LANE_GROUP) * (2 * CB_VLANES) + 2 * l + (st % CB_LANE_GROUP) / 4
-                 : (st / 4) * CB_VLANES + l;
+// lane l (at bit 16 * (st % 4)) in a unit of S steps.
+CB_LAYOUT_HD inline uint32_t cb_lane_word_index(bool grouped, uint32_t st, uint32_t l, uint32_t S) {
+  if (!grouped) return (st / 4) * CB_VLANES + l;
+  const uint32_t full = S / CB_LANE_GROUP * CB_LANE_GROUP;
+  if (st < full) return (st / CB_LANE_GROUP) * (2 * CB_VLANES) + 2 * l + (st % CB_LANE_GROUP) / 4;
+  return (full / 4) * CB_VLANES + l * ((S - full + 3) / 4) + (st - full) / 4;
 }
 struct CbLaneUnit {                  // 32 bytes
   uint32_t vals;        // first step of the unit's values (in steps of 32 values)
@@ -225,7 +236,7 @@ struct CbLaneUnit {                  // 32 bytes
   uint16_t nrows;       // rows of the unit inside the matrix (<= 128)
   uint16_t flags;       // CB_LUNIT_*
   uint32_t slot;        // partial-sum slot of a block-row part, 0xffffffff for whole block rows
-  uint32_t pad;
+  uint32_t gbase;       // CB_LUNIT_G16: column that the uint16 gather offsets start from
 };
 
 #endif

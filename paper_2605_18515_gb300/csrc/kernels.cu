@@ -1024,7 +1024,7 @@ __global__ void __launch_bounds__(32 * LaneGeom<typename ValT<V>::Acc, kK>::kWar
     u.vals = d0.x; u.words = d0.y; u.gcols = d0.z; u.brow_lo = d0.w;
     u.steps = (uint16_t)(d1.x & 0xffffu); u.nslots = (uint16_t)(d1.x >> 16);
     u.nrows = (uint16_t)(d1.y & 0xffffu); u.flags = (uint16_t)(d1.y >> 16);
-    u.slot = d1.z; u.pad = 0;
+    u.slot = d1.z; u.gbase = d1.w;
   };
   // cp.async of the unit's x values into buffer `buf`: slot k gets x[column of slot k] (kK
   // vectors side by side); slots outside [0, n) read zero. Plain sub-blocks: 16
@@ -1071,10 +1071,20 @@ __global__ void __launch_bounds__(32 * LaneGeom<typename ValT<V>::Acc, kK>::kWar
       return;
     }
     int32_t c[kPer];
+    if (u.flags & CB_LUNIT_G16) {   // uint16 offsets from gbase, 0xffff for none
+      const uint16_t* g16 = reinterpret_cast<const uint16_t*>(gc);
 #pragma unroll
-    for (int i = 0; i < kPer; ++i) {
-      const uint32_t k = (uint32_t)lane + 32u * i;
-      c[i] = k < u.nslots ? __ldg(gc + k) : -1;
+      for (int i = 0; i < kPer; ++i) {
+        const uint32_t k = (uint32_t)lane + 32u * i;
+        const uint32_t o = k < u.nslots ? (uint32_t)__ldg(g16 + k) : 0xffffu;
+        c[i] = o == 0xffffu ? -1 : (int32_t)(u.gbase + o);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < kPer; ++i) {
+        const uint32_t k = (uint32_t)lane + 32u * i;
+        c[i] = k < u.nslots ? __ldg(gc + k) : -1;
+      }
     }
 #pragma unroll
     for (int i = 0; i < kPer; ++i) {
@@ -1113,12 +1123,41 @@ __global__ void __launch_bounds__(32 * LaneGeom<typename ValT<V>::Acc, kK>::kWar
     } else {
       const V* p = vp + kLaneGroup * CB_VLANES * g;
       const uint64_t* pw = wp + 2u * CB_VLANES * g;
-      if (rem > 0) {
+      if (rem >= kLaneGroup) {
         v.a = ldg_stream_v4(p);
         if constexpr (sizeof(V) == 4) v.b = ldg_stream_v4(p + 4);
         const uint4 ww = ldg_stream_v4(pw);
         w0 = ((uint64_t)ww.y << 32) | ww.x;
         w1 = ((uint64_t)ww.w << 32) | ww.z;
+      } else if (rem > 0) {
+        // the unit's last rem < 8 steps: each lane's rem values and ceil(rem / 4) words are
+        // contiguous after the full groups (vp and wp point at this lane's full-group data)
+        const int l = lane;
+        const V* pt = p + l * (rem - kLaneGroup);
+        uint32_t e[kLaneGroup];
+#pragma unroll
+        for (int j = 0; j < kLaneGroup; ++j) {
+          e[j] = 0u;
+          if (j < rem) {
+            if constexpr (sizeof(V) == 4) e[j] = __ldg(reinterpret_cast<const uint32_t*>(pt) + j);
+            else e[j] = (uint32_t)__ldg(reinterpret_cast<const unsigned short*>(pt) + j);
+          }
+        }
+        if constexpr (sizeof(V) == 4) {
+          v.a = make_uint4(e[0], e[1], e[2], e[3]);
+          v.b = make_uint4(e[4], e[5], e[6], e[7]);
+        } else {
+          v.a = make_uint4(e[0] | e[1] << 16, e[2] | e[3] << 16, e[4] | e[5] << 16, e[6] | e[7] << 16);
+        }
+        const uint64_t* pwt = pw + l * (rem > 4 ? 0 : -1);   // 2 words per lane, or 1
+        if (rem > 4) {
+          const uint4 ww = ldg_stream_v4(pwt);
+          w0 = ((uint64_t)ww.y << 32) | ww.x;
+          w1 = ((uint64_t)ww.w << 32) | ww.z;
+        } else {
+          w0 = __ldg(pwt);
+          w1 = ~0ull;
+        }
       } else {
         w0 = w1 = ~0ull;
       }
@@ -1395,7 +1434,8 @@ __global__ void __launch_bounds__(32 * LaneGeom<typename ValT<V>::Acc, kK>::kWar
     // the gather list of the unit after next into L2 (one bulk prefetch by the TMA unit
     // instead of scattered cold loads when its gather is issued)
     if (tnn < total && lane == 0 && unn.nslots) {
-      const uint32_t ng = (kGrouped && (unn.flags & CB_LUNIT_PLAINX)) ? (unn.nslots / 16u + 3u) & ~3u : unn.nslots;
+      const uint32_t ng = (kGrouped && (unn.flags & CB_LUNIT_PLAINX)) ? (unn.nslots / 16u + 3u) & ~3u
+                          : (unn.flags & CB_LUNIT_G16) ? unn.nslots / 2u : unn.nslots;
       asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(b.p[qnn].lgcols + unn.gcols), "r"(4u * ng)
                    : "memory");
     }

@@ -159,3 +159,28 @@ def test_lowprec_full_size_fem(env):
             y = yd.cpu().numpy()
             M.check_device()
         check_lowprec(A, fmt, x, y, rows=rows)
+
+
+@pytest.mark.parametrize("fmt", FMTS)
+@pytest.mark.parametrize("steps", [1, 3, 4, 5, 7, 8, 9, 12, 15, 16, 17, 23])
+@pytest.mark.parametrize("short", [0, 5])
+def test_lane_layout_every_tail_length(env, fmt, steps, short):
+    """Lane-stream units of every length modulo the 8-step group: one block row of 16 rows
+    with 32 * steps - short entries (short > 0: some lanes' runs one step shorter), so the
+    unit's last steps % 8 steps take the compact tail of the layout (no padding to a group),
+    and a unit shorter than a group is nothing but a tail."""
+    W = 32 * steps - short
+    per = np.full(16, W // 16)
+    per[: W % 16] += 1
+    r = np.repeat(np.arange(16), per)
+    c = np.concatenate([np.linspace(0, 511, k).astype(np.int64) for k in per])   # distinct per row
+    A = I.csr_from_coo(16, 4000, r, c, I.normal(40 + steps, I.TAG_VAL, r.size))
+    assert A.nnz == W
+    x = I.vector_x(A.n, 35)
+    for agg in (0, 1):
+        bd, _ = env
+        with bd.BlockedMatrix(A, value_dtype=fmt, record_layout=2, col_agg=agg) as M:
+            st = M.stats()
+            assert st["lane_layout"] == 1 and st["n_units"] == 1 and st["fma_slots"] == 32 * steps
+        y = run_lp(env, A, fmt, x, record_layout=2, col_agg=agg)
+        check_lowprec(A, fmt, x, y)

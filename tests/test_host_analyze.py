@@ -380,10 +380,12 @@ def test_reduced_type_lane_layout_roundtrip(bd, fmt, name, col_agg):
         rp, col, val = M.export_csr()
     assert np.array_equal(rp, A.row_ptr) and np.array_equal(col, A.col)
     assert np.array_equal(val, L.round_to_format(A.val, fmt))
-    # values: steps rounded up to groups of 8 per unit, 32 lanes; words 2 bytes per value slot
+    # values: one slot per lane and step (no padding of the last group to 8 steps), 32 lanes;
+    # words 2 bytes per slot, each unit's rounded up to 4 steps
     vs = {"f32": 4, "bf16": 2, "f16": 2}[fmt]
-    assert st["stream_bytes"] == st["fma_slots"] * (vs + 2)
-    assert st["fma_slots"] % 256 == 0
+    assert st["fma_slots"] % 32 == 0 and A.nnz <= st["fma_slots"] < A.nnz + 32 * st["n_units"]
+    words = st["stream_bytes"] - st["fma_slots"] * vs
+    assert 2 * st["fma_slots"] <= words <= 2 * st["fma_slots"] + 3 * 64 * st["n_units"] and words % 256 == 0
 
 
 def test_plain_gather_lists_hold_one_column_per_sub_block(bd):
@@ -407,3 +409,38 @@ def test_plain_gather_lists_hold_one_column_per_sub_block(bd):
     g1 = s1["metadata_bytes"] - s1["n_tiles"] * tile_bytes - 32 * s1["n_units"]
     assert g1 == 4 * 16 * s1["n_tiles"]
     assert s0["n_tiles"] * 4 <= g0 < (s0["n_tiles"] + 3 * s0["n_units"]) * 4 + 1
+
+
+@pytest.mark.parametrize("fmt", ["f64", "bf16"])
+def test_uint16_gather_lists(bd, fmt):
+    """Per-slot gather lists become uint16 offsets from the unit's first column when the
+    unit's columns span fewer than 65,535 values (a FEM band with aggregation: every unit),
+    and stay 32-bit when they do not (a matrix whose rows each reach both ends of 200,000
+    columns). Both decode back to the input CSR bit for bit; the gather bytes count 2 or 4
+    per slot."""
+    from oracle import lowprec as L
+    fem = I.fem_block_band(n_rows=6000, n_block_rows=2000, half_band=300, seed=3)
+    # 64 rows, each with entries at columns 0..7 and 199,990..199,999
+    rr = np.repeat(np.arange(64), 16)
+    cc = np.tile(np.r_[np.arange(8), 199_990 + np.arange(10)[:8]], 64)
+    wide = I.csr_from_coo(64, 200_000, rr, cc, I.uniform_pm1(5, 1, rr.size))
+    lay = {} if fmt == "f64" else {"record_layout": 2}
+    for A, agg, want in ((fem, 1, "all"), (wide, 0, "none"), (wide, 1, "none")):
+        with host(bd, A, value_dtype=fmt, col_agg=agg, **lay) as M:
+            st = M.stats()
+            assert st["lane_layout"] == 1
+            if want == "all":
+                assert st["n_g16_units"] == st["n_units"] > 0
+                assert st["gather_list_bytes"] == 2 * 16 * st["n_tiles"]
+            elif fmt != "f64" and agg == 0:   # plain sub-blocks: one 32-bit entry each
+                assert st["n_g16_units"] == 0
+                assert st["gather_list_bytes"] == 4 * ((st["n_tiles"] + 3) // 4 * 4) and st["n_units"] == 1
+            else:
+                assert st["n_g16_units"] == 0
+                assert st["gather_list_bytes"] == 4 * 16 * st["n_tiles"]
+            rp, col, val = M.export_csr()
+        assert np.array_equal(rp, A.row_ptr) and np.array_equal(col, A.col)
+        if fmt == "f64":
+            assert np.array_equal(val.view(np.uint64), A.val.view(np.uint64))
+        else:
+            assert np.array_equal(val, L.round_to_format(A.val, fmt))
