@@ -56,13 +56,19 @@ KERNEL_TRAFFIC = {
     "run kernel rev 13": {("fem3x3_band_1m", "bf16"): 0.6535e9},
     "run kernel rev 15": {("fem3x3_band_1m", "f64"): 1.0187e9},
     "run kernel rev 16": {("fem3x3_band_1m", "f64"): 1.0192e9},
+    "run kernel rev 17": {("fem3x3_band_1m", "f64"): 0.9617e9, ("fem3x3_band_1m", "bf16", "lanes"): 0.4427e9},
 }
 
 
-def measured_traffic(version: str, workload: str, dtype: str):
+def measured_traffic(version: str, workload: str, dtype: str, lanes: bool = True):
+    """Captured DRAM bytes of the lane kernel (FP64: its default layout; reduced types: the
+    lane-stream layout), or None."""
+    key = (workload, dtype) if dtype == "f64" else (workload, dtype, "lanes")
+    if not lanes:
+        return None
     for rev, table in KERNEL_TRAFFIC.items():
         if version.endswith(rev + ")"):
-            return table.get((workload, dtype))
+            return table.get(key)
     return None
 
 
@@ -813,12 +819,13 @@ def main():
             peak_derived = round(fp64_peak_gflops(sms, fmax, fma["cycles_per_warp_fma"]), 1)
         k_ms = kt["ms_main"]
         traffic = args.traffic_bytes if args.traffic_bytes is not None else \
-            (RECORD_KERNEL_TRAFFIC.get((args.workload, args.dtype)) if lp else
-             measured_traffic(bd.version(), args.workload, args.dtype))
+            (RECORD_KERNEL_TRAFFIC.get((args.workload, args.dtype)) if lp and not st["lane_layout"] else
+             measured_traffic(bd.version(), args.workload, args.dtype, bool(st["lane_layout"])))
         k_gf = flops / (k_ms * 1e-3) / 1e9
         k_gbs = algo_bytes / (k_ms * 1e-3) / 1e9
         if lp:
-            roof = {"bound": "hbm", "kernel": "spmv_kernel<%s>" % args.dtype, "achieved": round(k_gbs, 2),
+            kname = ("spmv_lanes_kernel<%s>" if st["lane_layout"] else "spmv_kernel<%s>") % args.dtype
+            roof = {"bound": "hbm", "kernel": kname, "achieved": round(k_gbs, 2),
                     "peak": peak, "unit": "GB/s", "frac": round(k_gbs / peak, 4), "peak_kind": peak_kind,
                     "traffic": traffic, "kernel_ms": round(k_ms, 5),
                     "combine_ms": round(kt["ms_combine"], 5), "bytes_per_launch": int(algo_bytes),

@@ -1093,7 +1093,7 @@ const char* cbspmv_last_error(void) { return g_err.c_str(); }
 
 // The run-kernel revision changes whenever the kernel's code changes (measurements taken
 // with a profiler are tied to it).
-const char* cbspmv_version(void) { return "cbspmv 0.5 (sm_103a; run kernel rev 16)"; }
+const char* cbspmv_version(void) { return "cbspmv 0.5 (sm_103a; run kernel rev 17)"; }
 
 }  // extern "C"
 
