@@ -241,19 +241,22 @@ def spmm_bench(bd, A, x, stream, ks=(1, 8, 32), reps=20):
     """Tensor-core multi-vector product (cbspmv_spmm) on a BF16 copy of the matrix: X (n x k)
     and Y (m x k) row-major FP32. Returns per k the time, GFLOP/s (2 nnz k / t) and the HBM
     fraction of its bytes model (values and coordinates, sub-block metadata, restore_cols,
-    X read once, Y written once), beside the BF16 single-vector product of the record kernel."""
+    X read once, Y written once), beside the BF16 single-vector product of the default
+    (lane-stream) handle."""
     import torch
     peak, _ = load_peaks()
     out = {"api": "cbspmv_spmm (mma.sync.m16n8k16 BF16 x BF16 -> FP32, x split into 3 BF16 parts)",
            "values": "bf16", "results": []}
+    xd = torch.from_numpy(x.astype(np.float32)).cuda()
+    yd = torch.empty(A.m, dtype=torch.float32, device="cuda")
+    with bd.BlockedMatrix(A, value_dtype="bf16", stream=stream) as M1:
+        kt = M1.time_kernels(xd, yd, 200, stream=stream)
+        ms1 = kt["ms_main"] + kt["ms_combine"]
+    out["spmv_bf16_k1"] = {"ms": round(ms1, 4), "gflops": round(2.0 * A.nnz / (ms1 * 1e-3) / 1e9, 1),
+                           "handle": "default BF16 handle (lane kernel)"}
     with bd.BlockedMatrix(A, value_dtype="bf16", plain_records=True, stream=stream) as M:
         st = M.stats()
         mat_bytes = A.nnz * 3 + st["n_tiles"] * 21 + 4 * st["restore_cols_len"]
-        xd = torch.from_numpy(x.astype(np.float32)).cuda()
-        yd = torch.empty(A.m, dtype=torch.float32, device="cuda")
-        kt = M.time_kernels(xd, yd, 200, stream=stream)
-        ms1 = kt["ms_main"] + kt["ms_combine"]
-        out["spmv_bf16_k1"] = {"ms": round(ms1, 4), "gflops": round(2.0 * A.nnz / (ms1 * 1e-3) / 1e9, 1)}
         for k in ks:
             X = torch.from_numpy(np.tile(x.astype(np.float32)[:, None], (1, k))).cuda()
             Y = torch.empty((A.m, k), dtype=torch.float32, device="cuda")
@@ -674,8 +677,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-matrix batched measurement")
     ap.add_argument("--no-value-types", action="store_true", help="skip the reduced value types measurement")
     ap.add_argument("--layout", choices=["default", "records", "lanes"], default="default",
-                    help="layout of the timed handle: default (FP64 lane streams, reduced types records), "
-                         "records, or lane streams for every value type")
+                    help="layout of the timed handle: default (lane streams for every value type), "
+                         "records, or lane streams")
     ap.add_argument("--batched-full", action="store_true", help="batched matrices up to 1e6 rows (default 2e5)")
     ap.add_argument("--serve-full", action="store_true",
                     help="serving measurement on the full pool (17 Laplacians, 15 R-MAT, 10,000 requests)")
@@ -880,6 +883,9 @@ def main():
         if multi:
             line["multi_rhs"] = {"api": "cbspmv_run_multi (FP64: one column per pass; reduced types: passes "
                                         "of 4 vectors)", "results": multi}
+            if not lp and ws == 1:
+                with bd.BlockedMatrix(A, value_dtype="bf16", stream=stream) as Mb:
+                    line["multi_rhs"]["bf16_lane_streams"] = multi_rhs_bench(Mb, A, x, np.float32, stream)
         if spmm:
             line["multi_rhs_tensor"] = spmm
         if batched:

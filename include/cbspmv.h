@@ -61,8 +61,8 @@ enum { CBSPMV_FMT_COO = 0, CBSPMV_FMT_CSR = 1, CBSPMV_FMT_DENSE = 2 };
 /* A CSR matrix given by the caller. Values are always FP64 here; cbspmv_analyze copies
  * everything it needs, so the caller may free the arrays when the call returns.
  * on_device = 0: the three arrays are host pointers; on_device = 1: they are device
- * pointers. For the lane-stream layout on a device (value_dtype CBSPMV_F64 with
- * record_layout 0, or any value type with record_layout 2; device >= 0) with the arrays
+ * pointers. For the lane-stream layout on a device (record_layout 0 without
+ * plain_records, or record_layout 2; device >= 0) with the arrays
  * in that device's memory, the analysis runs on that device from these arrays on the
  * given stream (GPU merge, tiling, aggregation and lane programs; units and load balance
  * on the host from the tile counts; Sec. 3.2-3.4, cost of Sec. 4.5). Otherwise the arrays
@@ -89,11 +89,10 @@ typedef struct {
  *   device: CUDA device ordinal for the handle's memory; -1 builds a host-only handle
  *        (analysis, export and statistics work; run calls return CBSPMV_ERR_INVALID).
  *   keep_value_map: 0 (default) or 1, see cbspmv_update_values.
- *   record_layout: 0 (default): FP64 values are packed per unit in lane order (the
- *        lane-stream layout of the lane run kernel), the reduced types use the
- *        per-sub-block record layout and its kernel; 1: every value type uses the record
- *        layout; 2: every value type uses the lane-stream layout. Results agree within
- *        the tolerance of the value type. */
+ *   record_layout: 0 (default): every value type is packed per unit in lane order (the
+ *        lane-stream layout of the lane run kernel), except with plain_records = 1, which
+ *        selects the record layout; 1: the per-sub-block record layout and its kernel;
+ *        2: the lane-stream layout. Results agree within the tolerance of the value type. */
 typedef struct {
   double th0;
   int th1, th2;
@@ -193,9 +192,10 @@ cbspmv_status_t cbspmv_run_host(cbspmv_handle_t h, const void* x_host, void* y_h
  * n x k with leading dimension ldx >= n (column j at X + j * ldx); Y: device array,
  * column-major m x k with ldy >= m. Element type, alignment and the no-overlap rule
  * (between the whole spans of X and Y) are those of cbspmv_run; k = 0 does nothing.
- * Reduced value types: the columns are computed in passes of 4 (then 2, then 1) vectors:
- * each pass stages every unit of the matrix once and multiplies it into all its vectors, so
- * the matrix is read ceil(k/4)-ish times instead of k times. FP64 values in the lane-stream
+ * Reduced value types: the columns are computed in passes of 4 (then 2, then 1) vectors
+ * in the record layout, of 4 (then 1) in the lane-stream layout: each pass reads every unit
+ * of the matrix once and multiplies it into all its vectors, so the matrix is read
+ * ceil(k/4)-ish times instead of k times. FP64 values in the lane-stream
  * layout: one column per pass, since the FP64 FMA pipe, not the matrix bytes, bounds the
  * product (a pass over several vectors measured slower per vector). Each column is computed exactly as
  * cbspmv_run would (same summation order, so the results are bitwise equal to k separate
@@ -246,9 +246,9 @@ cbspmv_status_t cbspmv_analyze_batched(int count, const cbspmv_csr_t* A,
  * kernel per value type and per 64 products (each CTA works through its share of every
  * problem, as given by each problem's load balance), plus one small launch that adds the
  * parts of split block rows; a handle that appears more than once, or with k > 1, has its
- * further products in further launches (they share its partial-sum buffer). Handles in the
- * record layout (reduced value types) take their columns in passes of four where they can
- * (one launch multiplies each staged unit into four columns), the rest one at a time; the
+ * further products in further launches (they share its partial-sum buffer). Handles other
+ * than FP64 lane streams take their columns in passes of four where they can (one launch
+ * multiplies each unit into four columns), the rest one at a time; the
  * first such call allocates the handle's 4-vector partial-sum buffer. Every
  * product is computed exactly as cbspmv_run computes it, so results are bitwise equal to
  * separate runs. Errors: as cbspmv_run_multi. */
@@ -296,10 +296,9 @@ cbspmv_status_t cbspmv_graph_destroy(cbspmv_graph_t g);
  * The thresholds of Sec. 3.3 are heuristics (th0 0.15, th1 32, th2 128). This call analyses
  * A with the given options, then varies one choice at a time, keeping the fastest so far:
  * column aggregation (auto / off / on: th0 only ever decides between these two layouts, so
- * they stand for every th0); for the reduced value types the lane-stream layout
- * (record_layout = 2) against the records; for a lane-stream layout the unit size (1024,
- * 4096 stored entries); for FP64 values the record layout (record_layout = 1); for the
- * record layout the unit size (512, 768 multiply-adds) and the format thresholds
+ * they stand for every th0); for a lane-stream layout the unit size (1024, 4096 stored
+ * entries); the record layout (record_layout = 1) against the default lane streams; for
+ * the record layout the unit size (512, 768 multiply-adds) and the format thresholds
  * (th1, th2) = (16, 64) and (48, 192). The 16x16 sub-block is fixed (the 4-bit coordinates
  * of Sec. 3.2) and so is the number of warps per CTA (set per kernel and value type). Each
  * candidate is timed over `reps` products (1..10000) on the device. *out is the fastest

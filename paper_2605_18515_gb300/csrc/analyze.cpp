@@ -834,7 +834,7 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
   p.value_dtype = opts.value_dtype;
   p.vsize = value_size(opts.value_dtype);
   p.th0 = opts.th0; p.th1 = opts.th1; p.th2 = opts.th2;
-  p.lanes = (p.value_dtype == CBSPMV_F64 && opts.record_layout == 0) || opts.record_layout == 2;
+  p.lanes = uses_lanes(opts);
   const int64_t nbr = p.nbr;
 
   // --- step 2: plain 16x16 tiles and the super-sparse share (Sec. 3.3.1)

@@ -560,7 +560,7 @@ cbspmv_status_t analyze_device(const cbspmv_csr_t& A, const cbspmv_opts_t& opts,
   if (st != CBSPMV_OK) return st;
   st = validate_shape(A, msg);
   if (st != CBSPMV_OK) return st;
-  if (!((opts.value_dtype == CBSPMV_F64 && opts.record_layout == 0) || opts.record_layout == 2)) {
+  if (!uses_lanes(opts)) {
     *msg = "the device analysis builds the lane-stream layout only";
     return CBSPMV_ERR_INVALID;
   }

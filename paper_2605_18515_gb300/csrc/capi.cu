@@ -191,7 +191,7 @@ cbspmv_status_t cbspmv_default_opts(cbspmv_opts_t* o) {
 // True when the device analysis builds the handle of a device CSR: the lane-stream layout on
 // a device, and the three arrays in device memory of that device.
 static bool device_analysis_applies(const cbspmv_csr_t& A, const cbspmv_opts_t& o) {
-  const bool lanes = (o.value_dtype == CBSPMV_F64 && o.record_layout == 0) || o.record_layout == 2;
+  const bool lanes = cb::uses_lanes(o);
   if (!A.on_device || o.device < 0 || !lanes) return false;
   const void* ptrs[3] = {A.row_ptr, A.col_idx, A.val};
   for (int i = 0; i < (A.nnz > 0 ? 3 : 1); ++i) {
@@ -502,9 +502,11 @@ cbspmv_status_t cbspmv_run_multi(cbspmv_handle_t h, int k, const void* X, int64_
   // passes of 4, then 2, then 1 vectors; each pass reads the matrix once. FP64 lane-stream
   // handles take one vector per pass: their product is bound by the FP64 FMA pipe, so a pass
   // over several vectors saves no time (measured 0.198, 0.236 and 0.295 ms per vector for
-  // passes of 1, 2 and 4 vectors on the FEM band).
+  // passes of 1, 2 and 4 vectors on the FEM band). Lane-stream handles of the reduced types
+  // take passes of 4, then single vectors.
+  const bool lanes64 = p.lanes && p.vsize == 8;
   for (int j = 0; j < k;) {
-    const int nv = p.lanes ? 1 : k - j >= 4 ? 4 : k - j >= 2 ? 2 : 1;
+    const int nv = lanes64 ? 1 : k - j >= 4 ? 4 : p.lanes ? 1 : k - j >= 2 ? 2 : 1;
     cb::RunArgs a = run_args(h, (const char*)X + es * j * ldx, (char*)Y + es * j * ldy, alpha, beta);
     a.nvec = nv;
     a.ldx = ldx;
@@ -576,7 +578,7 @@ cbspmv_status_t cbspmv_spmm(cbspmv_handle_t h, int k, const void* X, int64_t ldx
     return fail(CBSPMV_ERR_UNSUPPORTED, "cbspmv_spmm needs BF16 values (tensor-core path); use cbspmv_run_multi");
   if (p.lanes || p.stats.n_direct_units != 0)
     return fail(CBSPMV_ERR_UNSUPPORTED,
-                "cbspmv_spmm needs the record layout with opts.plain_records = 1 (not record_layout 2)");
+                "cbspmv_spmm needs the record layout with opts.plain_records = 1 (not the lane-stream layout)");
   if ((!X && p.n > 0) || !Y) return fail(CBSPMV_ERR_INVALID, "NULL X or Y");
   if (((uintptr_t)X & 3) || ((uintptr_t)Y & 3)) return fail(CBSPMV_ERR_INVALID, "X and Y must be 4-byte aligned");
   if (X && p.n > 0) {
@@ -658,9 +660,10 @@ cbspmv_status_t cbspmv_run_batched(int count, const cbspmv_handle_t* hs, const i
   // no handle's partial-sum buffer is used twice within a launch.
   for (int i = 1; i < count; ++i)
     if (hs[i]->device != hs[0]->device) return fail(CBSPMV_ERR_INVALID, "problems on different devices");
-  // Record-layout handles take their columns in passes of four where they can (round r4
-  // of quads holds the r4-th group of four columns of every such handle), the rest one at a
-  // time; the quads use each handle's 4-vector partial-sum buffer, allocated here first.
+  // Handles other than FP64 lane streams take their columns in passes of four where they
+  // can (round r4 of quads holds the r4-th group of four columns of every such handle), the
+  // rest one at a time; the quads use each handle's 4-vector partial-sum buffer, allocated
+  // here first.
   std::vector<std::vector<cb::RunArgs>> rounds;   // per round, all value types mixed
   std::vector<std::vector<cb::RunArgs>> quads;
   std::vector<std::pair<cbspmv_handle_t, int>> seen, seen4;
@@ -675,7 +678,7 @@ cbspmv_status_t cbspmv_run_batched(int count, const cbspmv_handle_t* hs, const i
     if (h->plan.m == 0) continue;
     const int ki = k ? k[i] : 1;
     const size_t es = h->esize();
-    const int nq = h->plan.lanes ? 0 : ki / 4;
+    const int nq = h->plan.lanes && h->plan.vsize == 8 ? 0 : ki / 4;
     const int occ4 = occupancy(seen4, h, nq);
     for (int q = 0; q < nq; ++q) {
       if ((int)quads.size() <= occ4 + q) quads.resize(occ4 + q + 1);
@@ -1014,13 +1017,6 @@ cbspmv_status_t cbspmv_analyze_tuned(const cbspmv_csr_t* A, const cbspmv_opts_t*
       o.col_agg = other;
       st = consider(o);
     }
-    if (o0.value_dtype != CBSPMV_F64 && !o0.record_layout && st == CBSPMV_OK) {
-      // the reduced types: the lane-stream layout against the default record layout
-      cbspmv_opts_t o = best_o;
-      o.record_layout = 2;
-      o.unit_work = 0;
-      st = consider(o);
-    }
     if (best->plan.lanes && st == CBSPMV_OK) {
       // lane-stream unit sizes (stored entries per unit)
       for (int uw : {1024, 4096})
@@ -1030,8 +1026,8 @@ cbspmv_status_t cbspmv_analyze_tuned(const cbspmv_csr_t* A, const cbspmv_opts_t*
           st = consider(o);
         }
     }
-    if (o0.value_dtype == CBSPMV_F64 && !o0.record_layout && st == CBSPMV_OK) {
-      // FP64: the record layout against the lane-stream layout
+    if (!o0.record_layout && !o0.plain_records && st == CBSPMV_OK) {
+      // the record layout against the default lane-stream layout
       cbspmv_opts_t o = best_o;
       o.record_layout = 1;
       o.unit_work = 0;
@@ -1093,7 +1089,7 @@ const char* cbspmv_last_error(void) { return g_err.c_str(); }
 
 // The run-kernel revision changes whenever the kernel's code changes (measurements taken
 // with a profiler are tied to it).
-const char* cbspmv_version(void) { return "cbspmv 0.5 (sm_103a; run kernel rev 17)"; }
+const char* cbspmv_version(void) { return "cbspmv 0.6 (sm_103a; run kernel rev 18)"; }
 
 }  // extern "C"
 

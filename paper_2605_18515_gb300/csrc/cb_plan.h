@@ -15,6 +15,14 @@
 #include "cb_layout.h"
 
 namespace cb {
+// The lane-stream layout unless the options ask for the record layout (record_layout 1, or
+// the default with plain_records, which only the record layout has).
+inline bool uses_lanes(const cbspmv_opts_t& o) {
+  return o.record_layout == 2 || (o.record_layout == 0 && !o.plain_records);
+}
+}  // namespace cb
+
+namespace cb {
 
 // Allocator whose value-initialisation of new elements is a no-op: for buffers that are
 // written in full before they are read (the packed stream is 0.8 GB for the FEM workload;

@@ -1227,22 +1227,38 @@ __global__ void __launch_bounds__(32 * LaneGeom<typename ValT<V>::Acc, kK>::kWar
     // buffer and is not used), then the FMA chain with the rare row switch
     auto compute = [&](const LaneVals<V>& v, uint64_t w0, uint64_t w1) {
 #if CB_LANE_FASTROW
-      if constexpr (kGrouped && kK == 1) {
+      if constexpr (kGrouped) {
         // the common case of the reduced types, whose walk is bound by instruction issue:
         // all 8 entries of the group continue the current row (row bits of every word
-        // equal cur), so no row switch is tested per entry and two partial sums break the
-        // FMA dependency chain
+        // equal cur), so no row switch is tested per entry and two partial sums per vector
+        // break the FMA dependency chain
         const uint64_t row_bits = 0xFE00FE00FE00FE00ull;
         const uint64_t pat = (uint64_t)cur * 0x0200020002000200ull;
         if (cur < 128u && (w0 & row_bits) == pat && (w1 & row_bits) == pat) {
-          Acc s0 = (Acc)0, s1 = (Acc)0;
+          Acc s0[kK], s1[kK];
+#pragma unroll
+          for (int h = 0; h < kK; ++h) s0[h] = s1[h] = (Acc)0;
 #pragma unroll
           for (int j = 0; j < kLaneGroup; ++j) {
             const uint32_t slot = (uint32_t)((j < 4 ? w0 : w1) >> (16 * (j & 3))) & 511u;
-            const Acc xj = *reinterpret_cast<const Acc*>(xs + (uint32_t)sizeof(Acc) * slot);
-            if (j & 1) s1 = fma(v.at(j), xj, s1); else s0 = fma(v.at(j), xj, s0);
+            const Acc vj = v.at(j);
+            if constexpr (kK == 4) {   // the slot's four x values in one 16-byte load
+              const float4 x4 = *reinterpret_cast<const float4*>(xs + G::kSlot * slot);
+              const Acc xh[4] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+              for (int h = 0; h < 4; ++h) {
+                if (j & 1) s1[h] = fma(vj, xh[h], s1[h]); else s0[h] = fma(vj, xh[h], s0[h]);
+              }
+            } else {
+#pragma unroll
+              for (int h = 0; h < kK; ++h) {
+                const Acc xj = *reinterpret_cast<const Acc*>(xs + G::kSlot * slot + sizeof(Acc) * h);
+                if (j & 1) s1[h] = fma(vj, xj, s1[h]); else s0[h] = fma(vj, xj, s0[h]);
+              }
+            }
           }
-          acc[0] += s0 + s1;
+#pragma unroll
+          for (int h = 0; h < kK; ++h) acc[h] += s0[h] + s1[h];
           return;
         }
       }
@@ -1562,7 +1578,10 @@ cudaError_t launch_nvec(const BatchArgs<kMaxP>& b, int grid, cudaStream_t stream
 
 template <class V, int kMaxP>
 cudaError_t launch_lanes_nvec(const BatchArgs<kMaxP>& b, int grid, cudaStream_t stream, cudaEvent_t* ev) {
-  // one vector per pass (the FP64 FMA pipe bounds the product; see cbspmv_run_multi)
+  // FP64: one vector per pass (the FP64 FMA pipe bounds the product; see cbspmv_run_multi);
+  // the reduced types also in passes of four vectors, which read the streams once
+  if constexpr (sizeof(V) != 8)
+    if (b.p[0].nvec == 4) return launch_lanes<V, kMaxP, 4>(b, grid, stream, ev);
   return b.p[0].nvec == 1 ? launch_lanes<V, kMaxP, 1>(b, grid, stream, ev) : cudaErrorInvalidValue;
 }
 

@@ -142,17 +142,26 @@ __global__ void __launch_bounds__(kVecThreads) vec_kernel(const __grid_constant_
         acc = fma((double)ri, (double)ri, acc);
       }
       break;
-    case kOpPQ:
-      for (int64_t i = i0 + threadIdx.x; i < i1; i += kVecThreads) acc = fma((double)p[i], (double)q[i], acc);
+    // The inner solve's dot products accumulate in the inner vectors' type: FP32 for the
+    // mixed-precision solve (an FP64 FMA, or a conversion to FP64, per element would hold
+    // GB300's slow FP64 pipe longer than the whole FP32 step; the inner solve only needs a
+    // residual reduction of inner_tol), FP64 for the FP64 solve. Each block's sum is FP64.
+    case kOpPQ: {
+      T a = T(0);
+      for (int64_t i = i0 + threadIdx.x; i < i1; i += kVecThreads) a = fma(p[i], q[i], a);
+      acc = (double)a;
       break;
+    }
     case kOpUpdate: {
       const T al = (T)s.alpha;
+      T a = T(0);
       for (int64_t i = i0 + threadIdx.x; i < i1; i += kVecThreads) {
         d[i] = fma(al, p[i], d[i]);
         const T ri = fma(-al, q[i], r[i]);
         r[i] = ri;
-        acc = fma((double)ri, (double)ri, acc);
+        a = fma(ri, ri, a);
       }
+      acc = (double)a;
       break;
     }
     case kOpDirection: {

@@ -51,7 +51,8 @@ def test_random_products(env, seed):
     th1 = int(rng.choice([0, 8, 32, 64]))
     th2 = max(th1, int(rng.choice([128, 200, 256])))
     opts = dict(col_agg=int(rng.choice([-1, 0, 1])), th1=th1, th2=th2,
-                unit_work=int(rng.choice([0, 64, 300, 1024])), load_balance=bool(rng.integers(2)))
+                unit_work=int(rng.choice([0, 64, 300, 1024])), load_balance=bool(rng.integers(2)),
+                record_layout=int(rng.choice([0, 1])))
     fmt = str(rng.choice(["f64", "f64", "f32", "bf16", "f16"]))
     alpha, beta = float(rng.choice([1.0, -0.75])), float(rng.choice([0.0, 0.5]))
     k = int(rng.integers(1, 6))

@@ -74,8 +74,9 @@ def test_tuned_analysis(env, name, dtype):
 
 
 def test_tuned_analysis_reduced_type(env):
-    """BF16 values: aggregation, the lane-stream layout against the records, then the
-    winning layout's axes (unit sizes; for records also the format thresholds); the tuned
+    """BF16 values: aggregation, the lane-stream unit sizes, the record layout against the
+    default lane streams, then, when the records win, their axes (unit sizes and the format
+    thresholds); the tuned
     handle's product stays within the FP32 bound of the stored-value product."""
     from oracle import lowprec as L
     bd, torch = env
@@ -83,7 +84,8 @@ def test_tuned_analysis_reduced_type(env):
     M, rep = bd.analyze_tuned(A, reps=5, value_dtype="bf16")
     with M:
         assert 5 <= rep["n_tried"] <= 16
-        assert any(t["record_layout"] == 2 for t in rep["tried"]) and rep["tried"][0]["record_layout"] == 0
+        assert any(t["record_layout"] == 1 for t in rep["tried"]) and rep["tried"][0]["record_layout"] == 0
+        assert M.stats()["lane_layout"] == (rep["best"]["record_layout"] == 0)
         assert rep["best_ms"] == min(t["ms"] for t in rep["tried"])
         x = I.vector_x(A.n, 13).astype(np.float32)
         yd = torch.zeros(A.m, dtype=torch.float32, device="cuda")

@@ -81,7 +81,7 @@ CASES = {
 }
 
 
-LAYOUTS = {"records": 0, "lanes": 2}
+LAYOUTS = {"records": 1, "lanes": 0}
 
 
 @pytest.mark.parametrize("fmt", FMTS)
@@ -184,3 +184,42 @@ def test_lane_layout_every_tail_length(env, fmt, steps, short):
             assert st["lane_layout"] == 1 and st["n_units"] == 1 and st["fma_slots"] == 32 * steps
         y = run_lp(env, A, fmt, x, record_layout=2, col_agg=agg)
         check_lowprec(A, fmt, x, y)
+
+
+@pytest.mark.parametrize("fmt", FMTS)
+@pytest.mark.parametrize("name", ["rmat12", "split_rows", "plain_333x517"])
+def test_lane_layout_four_vector_passes(env, fmt, name):
+    """Lane-stream handles of the reduced types take their columns in passes of four (then
+    single columns), in cbspmv_run_multi and cbspmv_run_batched: every column equals its
+    single-vector run bit for bit (same summation order) and meets the oracle's bound. Cases:
+    power-law rows with 32-bit gather lists, block rows cut into parts (combine of four
+    columns), plain sub-blocks without aggregation, with alpha and beta."""
+    bd, torch = env
+    if name == "rmat12":
+        A, kw = I.rmat(12, 16, seed=4), {}
+    elif name == "split_rows":
+        r = np.repeat(np.arange(16), 900)
+        c = np.tile(np.arange(900) * 3, 16)
+        A, kw = I.csr_from_coo(16, 2700, r, c, I.normal(5, I.TAG_VAL, r.size)), {"unit_work": 256}
+    else:
+        A, kw = I.random_csr(333, 517, 0.2, 11), {"col_agg": 0}
+    k, alpha, beta = 6, 0.75, -1.25
+    X = np.stack([f32(I.vector_x(A.n, 80 + j)) for j in range(k)])
+    Y0 = np.stack([f32(I.uniform_pm1(90 + j, I.TAG_Y, A.m)) for j in range(k)])
+    with bd.BlockedMatrix(A, value_dtype=fmt, record_layout=2, **kw) as M:
+        assert M.stats()["lane_layout"] == 1
+        if name == "split_rows":
+            assert M.stats()["n_split_rows"] > 0
+        Xd = torch.from_numpy(X).cuda()
+        Yd = torch.from_numpy(Y0.copy()).cuda()
+        M.run_multi(Xd, Yd, alpha, beta)
+        Y = Yd.cpu().numpy()
+        Yb = torch.from_numpy(Y0.copy()).cuda()
+        bd.run_batched([M], [Xd], [Yb], [alpha], [beta])
+        assert np.array_equal(Yb.cpu().numpy(), Y)
+        for j in range(k):
+            yj = torch.from_numpy(Y0[j].copy()).cuda()
+            M.run(torch.from_numpy(X[j].copy()).cuda(), yj, alpha, beta)
+            assert np.array_equal(Y[j], yj.cpu().numpy())
+            check_lowprec(A, fmt, X[j], Y[j], alpha, beta, Y0[j])
+        M.check_device()

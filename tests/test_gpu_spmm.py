@@ -127,13 +127,13 @@ def test_spmm_rejects_other_handles(env):
             M.spmm(X, Y)
         assert ei.value.status == 6
     R = I.fem_block_band(n_rows=600, n_block_rows=200, half_band=50, seed=3)
-    with bd.BlockedMatrix(R, value_dtype="bf16") as M:
+    with bd.BlockedMatrix(R, value_dtype="bf16", record_layout=1) as M:   # records with direct units
         if M.stats()["n_direct_units"]:
             with pytest.raises(bd.CbspmvError) as ei:
                 M.spmm(torch.zeros((R.n, 8), dtype=torch.float32, device="cuda"),
                        torch.zeros((R.m, 8), dtype=torch.float32, device="cuda"))
             assert ei.value.status == 6
-    with bd.BlockedMatrix(A, value_dtype="bf16", record_layout=2) as M:   # lane streams
+    with bd.BlockedMatrix(A, value_dtype="bf16") as M:   # lane streams (the default)
         with pytest.raises(bd.CbspmvError) as ei:
             M.spmm(X, Y)
         assert ei.value.status == 6

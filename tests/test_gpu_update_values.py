@@ -34,15 +34,16 @@ def new_values(A, seed):
 
 @pytest.mark.parametrize("fmt", ["f64", "f32", "bf16", "f16"])
 @pytest.mark.parametrize("name", list(CASES))
-def test_update_equals_fresh_analysis(env, fmt, name):
+@pytest.mark.parametrize("layout", [0, 1])
+def test_update_equals_fresh_analysis(env, fmt, name, layout):
     bd, torch = env
     A = CASES[name]()
     v2 = new_values(A, 77)
     A2 = I.CSR(A.m, A.n, A.row_ptr, A.col, v2)
     vec = torch.float64 if fmt == "f64" else torch.float32
     x = I.vector_x(A.n, 5)
-    with bd.BlockedMatrix(A, value_dtype=fmt, keep_value_map=True) as M, \
-            bd.BlockedMatrix(A2, value_dtype=fmt) as F:
+    with bd.BlockedMatrix(A, value_dtype=fmt, keep_value_map=True, record_layout=layout) as M, \
+            bd.BlockedMatrix(A2, value_dtype=fmt, record_layout=layout) as F:
         M.update_values(v2)
         torch.cuda.synchronize()
         rp, col, val = M.export_csr()

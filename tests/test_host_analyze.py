@@ -290,7 +290,7 @@ def test_direct_descriptors_where_columns_are_known_per_chunk(bd):
         st = M.stats()
         assert_roundtrip(M, A)
     assert st["n_direct_units"] == st["n_xseq_units"] + st["n_entry_mode_units"] > 0
-    with host(bd, A, value_dtype="bf16") as M:
+    with host(bd, A, value_dtype="bf16", record_layout=1) as M:
         st = M.stats()
         rp, col, val = M.export_csr()
     assert st["n_direct_units"] == st["n_xseq_units"] + st["n_entry_mode_units"] > 0
