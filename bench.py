@@ -57,6 +57,7 @@ KERNEL_TRAFFIC = {
     "run kernel rev 15": {("fem3x3_band_1m", "f64"): 1.0187e9},
     "run kernel rev 16": {("fem3x3_band_1m", "f64"): 1.0192e9},
     "run kernel rev 17": {("fem3x3_band_1m", "f64"): 0.9617e9, ("fem3x3_band_1m", "bf16", "lanes"): 0.4427e9},
+    "run kernel rev 20": {("fem3x3_band_1m", "f64"): 0.9603e9, ("fem3x3_band_1m", "bf16", "lanes"): 0.4415e9},
 }
 
 
@@ -523,8 +524,12 @@ SERVE_POOLS = {
     # SPD 3D 7-point Laplacians (CG and y = Ax) and R-MAT matrices (y = Ax only)
     "small": {"lap": [32, 38, 44, 50, 56, 62], "rmat": [(14, 3), (15, 4), (16, 5)], "requests": 2000,
               "baseline_requests": 300},
+    # the 32-matrix pool of the serving workload; "config5" serves 3,000 requests per served
+    # run (the default, minutes on the box), "full" the workload's 10,000
+    "config5": {"lap": list(range(32, 129, 6)), "rmat": [(s, 3 + k) for s in range(16, 21) for k in range(3)],
+                "requests": 3000, "baseline_requests": 1500},
     "full": {"lap": list(range(32, 129, 6)), "rmat": [(s, 3 + k) for s in range(16, 21) for k in range(3)],
-             "requests": 10000, "baseline_requests": 600},
+             "requests": 10000, "baseline_requests": 1500},
 }
 
 
@@ -589,13 +594,13 @@ def serve_run(S, ids, mats, n_req, rate, seed):
             "launches": st["launches"] - st0["launches"]}
 
 
-def serve_bench(pool_name, seed=5, inner_steps=8, max_cg=0):
+def serve_bench(pool_name, seed=5, inner_steps=16, max_cg=0, inner_tol=1e-5):
     """Both modes' burst capacity; then Poisson arrivals at one common rate (70% of the
     one-at-a-time capacity, a load both modes sustain) for both, and the served mode also at
     70% of its own capacity."""
     from paper_2605_18515_gb300 import binding as bd
     mats, spec = serve_pool(pool_name)
-    served_opts = dict(max_inflight=64, cg_inner_dtype="bf16", inner_tol=1e-4, memory_budget=8 << 30,
+    served_opts = dict(max_inflight=64, cg_inner_dtype="bf16", inner_tol=inner_tol, memory_budget=8 << 30,
                        inner_steps=inner_steps, max_inflight_cg=max_cg)
     base_opts = dict(max_inflight=1, cg_inner_dtype="f64", inner_tol=1e-9, memory_budget=8 << 30)
     with bd.Server(**base_opts) as S:
@@ -612,7 +617,7 @@ def serve_bench(pool_name, seed=5, inner_steps=8, max_cg=0):
                    f"{len(spec['rmat'])} R-MAT (scales {spec['rmat'][0][0]}-{spec['rmat'][-1][0]})",
            "mix": "70% y=Ax (FP64), 30% CG to 1e-8 relative residual",
            "served": {"mode": "continuous batching, 64 in flight, BF16-value CG with FP64 refinement, "
-                              f"{inner_steps} inner CG iterations per tick, "
+                              f"{inner_steps} inner CG iterations per tick, inner tolerance {inner_tol:g}, "
                               f"{max_cg or 64} CG solves in flight at most",
                       "capacity": cap, "poisson_same_load": same, "poisson_at_70pct": load},
            "one_at_a_time_fp64": {"mode": "one request at a time, FP64 products and FP64 CG",
@@ -620,9 +625,12 @@ def serve_bench(pool_name, seed=5, inner_steps=8, max_cg=0):
            "same_load_req_per_s": round(common, 1),
            "capacity_ratio": round(cap["req_per_s"] / max(bcap["req_per_s"], 1e-9), 2),
            "p99_ratio_same_load": round(same["p99_ms"] / max(bload["p99_ms"], 1e-9), 3)}
-    if pool_name != "full":
-        out["note"] = ("default run: 9-matrix pool; the full pool of 32 matrices and 10,000 requests "
-                       "(about 80 s to generate, minutes to serve) runs with --serve-full")
+    out["requests_per_served_run"] = spec["requests"]
+    if pool_name == "config5":
+        out["note"] = ("default run: the 32-matrix pool with 3,000 requests per served run and 1,500 per "
+                       "one-at-a-time run, to keep the bench within minutes; --serve-full serves 10,000")
+    elif pool_name == "small":
+        out["note"] = "9-matrix pool (--serve-pool small)"
     return out
 
 
@@ -676,15 +684,20 @@ def main():
     ap.add_argument("--no-spmm", action="store_true", help="skip the tensor-core multi-vector measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-matrix batched measurement")
     ap.add_argument("--no-value-types", action="store_true", help="skip the reduced value types measurement")
+    ap.add_argument("--no-device-analysis", action="store_true",
+                    help="skip the device-side analysis measurement (analysis block)")
     ap.add_argument("--layout", choices=["default", "records", "lanes"], default="default",
                     help="layout of the timed handle: default (lane streams for every value type), "
                          "records, or lane streams")
     ap.add_argument("--batched-full", action="store_true", help="batched matrices up to 1e6 rows (default 2e5)")
     ap.add_argument("--serve-full", action="store_true",
-                    help="serving measurement on the full pool (17 Laplacians, 15 R-MAT, 10,000 requests)")
+                    help="serving measurement with 10,000 requests per served run (the 32-matrix pool)")
+    ap.add_argument("--serve-pool", choices=["small", "config5", "full"], default="config5",
+                    help="serving pool: 9 small matrices, or the 32-matrix pool with 3,000 (config5) or "
+                         "10,000 (full) requests per served run")
     ap.add_argument("--serve-max-cg", type=int, default=0,
                     help="CG solves in flight at most in the served mode (0: no separate limit)")
-    ap.add_argument("--serve-inner-steps", type=int, default=8,
+    ap.add_argument("--serve-inner-steps", type=int, default=16,
                     help="inner CG iterations per tick of the served mode (1..64)")
     ap.add_argument("--traffic-bytes", type=float, default=None,
                     help="ncu DRAM bytes per launch of the timed kernel, if captured for this build")
@@ -892,12 +905,12 @@ def main():
             line["batched"] = batched
         if abl:
             line["ablation"] = abl
-        if not lp and ws == 1:
+        if not lp and ws == 1 and not args.no_device_analysis:
             line["analysis"] = device_analysis_bench(bd, torch, A, st, host_call_ms, ms_max, local, stream)
         if not lp and ws == 1 and not args.no_value_types:
             line["value_types"] = value_types_bench(bd, A, x, stream)
         if not args.no_serve and ws == 1:
-            line["serving"] = serve_bench("full" if args.serve_full else "small", inner_steps=args.serve_inner_steps,
+            line["serving"] = serve_bench("full" if args.serve_full else args.serve_pool, inner_steps=args.serve_inner_steps,
                                           max_cg=args.serve_max_cg)
         if err:
             line["error_vs_fp64_oracle"] = err

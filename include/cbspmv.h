@@ -193,8 +193,11 @@ cbspmv_status_t cbspmv_run_host(cbspmv_handle_t h, const void* x_host, void* y_h
  * column-major m x k with ldy >= m. Element type, alignment and the no-overlap rule
  * (between the whole spans of X and Y) are those of cbspmv_run; k = 0 does nothing.
  * Reduced value types: the columns are computed in passes of 4 (then 2, then 1) vectors
- * in the record layout, of 4 (then 1) in the lane-stream layout: each pass reads every unit
- * of the matrix once and multiplies it into all its vectors, so the matrix is read
+ * in the record layout, of 4 (then 1) in the lane-stream layout, except for matrices of 2^22
+ * or more stored entries whose gathered x slots serve fewer than two entries each
+ * (16 x sub-blocks > nnz / 2: one column per pass, since a pass gathers every slot once
+ * per vector): each pass reads every
+ * unit of the matrix once and multiplies it into all its vectors, so the matrix is read
  * ceil(k/4)-ish times instead of k times. FP64 values in the lane-stream
  * layout: one column per pass, since the FP64 FMA pipe, not the matrix bytes, bounds the
  * product (a pass over several vectors measured slower per vector). Each column is computed exactly as

@@ -535,7 +535,7 @@ static cbspmv_status_t build_lane_programs(const cbspmv_csr_t& A, Plan& p, const
 // Step 4a of the analysis: units of work over the tiles of p (p.tiles in block-row order,
 // tile_off: nbr + 1 tile offsets of the block rows). Fills p.units (matrix order),
 // p.split_rows, p.n_split_rows, p.n_split_wide and p.n_slots.
-void cut_units(Plan& p, const std::vector<int64_t>& tile_off, const cbspmv_opts_t& opts) {
+void cut_units(Plan& p, const std::vector<int64_t>& tile_off, const cbspmv_opts_t& opts, int n_workers) {
   const int64_t nbr = p.nbr;
   // Record layout: every unit must fit one warp's shared-memory
   // buffer (stream bytes, tiles, multiply-adds incl. Dense zero fill). Lane-stream layout:
@@ -543,8 +543,22 @@ void cut_units(Plan& p, const std::vector<int64_t>& tile_off, const cbspmv_opts_
   // unit, and its work is its stored entries.
   const bool lanes = p.lanes;
   const uint32_t BMAX = lanes ? UINT32_MAX : CB_B_MAX_FOR(p.vsize);   // stream bytes per unit
+  // Lane-stream default: CB_LANE_WORK_DEFAULT entries per unit, smaller when that would
+  // leave CTAs without a unit (a small matrix is then spread over all SMs), but never below
+  // 256 entries or below the largest block row (so no block row is cut into more parts)
+  uint32_t lane_default = CB_LANE_WORK_DEFAULT;
+  if (lanes && opts.unit_work <= 0 && n_workers > 0 && p.nnz / CB_LANE_WORK_DEFAULT < n_workers) {
+    int64_t wmax = 0;   // entries of the largest block row
+    for (int64_t b = 0; b < nbr; ++b) {
+      int64_t w = 0;
+      for (int64_t t = tile_off[b]; t < tile_off[b + 1]; ++t) w += p.tiles[t].nnz;
+      wmax = std::max(wmax, w);
+    }
+    lane_default = (uint32_t)std::min<int64_t>(CB_LANE_WORK_DEFAULT,
+                                               std::max<int64_t>({int64_t{256}, wmax, p.nnz / n_workers}));
+  }
   const uint32_t U = lanes ? (opts.unit_work > 0 ? std::min<uint32_t>((uint32_t)opts.unit_work, CB_LANE_WORK_MAX)
-                                                 : CB_LANE_WORK_DEFAULT)
+                                                 : lane_default)
                            : (opts.unit_work > 0 ? std::min<uint32_t>((uint32_t)opts.unit_work, CB_UNIT_WORK_MAX)
                                                  : CB_UNIT_WORK_DEFAULT);
   const int64_t TMAX = lanes ? CB_LANE_T_MAX : CB_T_MAX;
@@ -934,7 +948,7 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
     }
   });
 
-  cut_units(p, tile_off, opts);
+  cut_units(p, tile_off, opts, n_workers);
   const bool lanes = p.lanes;
   const uint32_t BMAX = lanes ? UINT32_MAX : CB_B_MAX_FOR(p.vsize);
 

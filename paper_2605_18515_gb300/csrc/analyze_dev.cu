@@ -762,7 +762,7 @@ cbspmv_status_t analyze_device(const cbspmv_csr_t& A, const cbspmv_opts_t& opts,
   });
 
   // --- 4. units, load balance and lane offsets on the host; lane programs on the GPU
-  cut_units(p, tile_off, opts);
+  cut_units(p, tile_off, opts, n_workers);
   st = check_units(p, msg);
   if (st != CBSPMV_OK) return st;
   std::vector<double> load;

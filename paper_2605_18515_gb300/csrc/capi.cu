@@ -486,6 +486,20 @@ static cbspmv_status_t ensure_partial_multi(cbspmv_handle_t h) {
   return ok();
 }
 
+// Whether cbspmv_run_multi computes several vectors per pass. FP64 lane streams: no, the
+// FP64 FMA pipe bounds the product (passes of 1, 2 and 4 vectors measured 0.198, 0.236 and
+// 0.295 ms per vector on the FEM band). Lane streams of the reduced types: yes, except for
+// large matrices whose gathered x slots serve fewer than two stored entries each: a pass
+// over four vectors gathers four values per slot, which on R-MAT scale 21 (about one entry
+// per slot) measured slower per vector than single passes (0.189 against 0.148 ms, FP32),
+// on the FEM band faster (0.093 against 0.116 ms, BF16); on small matrices the launches
+// saved outweigh the gathers. The record layout: yes.
+static bool multi_vector_passes(const cb::Plan& p) {
+  if (!p.lanes) return true;
+  if (p.vsize == 8) return false;
+  return p.nnz < (int64_t{1} << 22) || 32 * (uint64_t)p.tiles.size() <= (uint64_t)p.nnz;
+}
+
 cbspmv_status_t cbspmv_run_multi(cbspmv_handle_t h, int k, const void* X, int64_t ldx, void* Y, int64_t ldy,
                                  double alpha, double beta, void* stream) {
   cbspmv_status_t st = check_run_args(h, k, X, ldx, Y, ldy);
@@ -499,14 +513,11 @@ cbspmv_status_t cbspmv_run_multi(cbspmv_handle_t h, int k, const void* X, int64_
     const cbspmv_status_t st = ensure_partial_multi(h);
     if (st != CBSPMV_OK) return st;
   }
-  // passes of 4, then 2, then 1 vectors; each pass reads the matrix once. FP64 lane-stream
-  // handles take one vector per pass: their product is bound by the FP64 FMA pipe, so a pass
-  // over several vectors saves no time (measured 0.198, 0.236 and 0.295 ms per vector for
-  // passes of 1, 2 and 4 vectors on the FEM band). Lane-stream handles of the reduced types
-  // take passes of 4, then single vectors.
-  const bool lanes64 = p.lanes && p.vsize == 8;
+  // passes of 4, then 2, then 1 vectors (records), of 4 then 1 (lane streams), or single
+  // vectors (see multi_vector_passes); each pass reads the matrix once
+  const bool multi = multi_vector_passes(p);
   for (int j = 0; j < k;) {
-    const int nv = lanes64 ? 1 : k - j >= 4 ? 4 : p.lanes ? 1 : k - j >= 2 ? 2 : 1;
+    const int nv = !multi ? 1 : k - j >= 4 ? 4 : p.lanes ? 1 : k - j >= 2 ? 2 : 1;
     cb::RunArgs a = run_args(h, (const char*)X + es * j * ldx, (char*)Y + es * j * ldy, alpha, beta);
     a.nvec = nv;
     a.ldx = ldx;
@@ -662,8 +673,9 @@ cbspmv_status_t cbspmv_run_batched(int count, const cbspmv_handle_t* hs, const i
     if (hs[i]->device != hs[0]->device) return fail(CBSPMV_ERR_INVALID, "problems on different devices");
   // Handles other than FP64 lane streams take their columns in passes of four where they
   // can (round r4 of quads holds the r4-th group of four columns of every such handle), the
-  // rest one at a time; the quads use each handle's 4-vector partial-sum buffer, allocated
-  // here first.
+  // rest one at a time (a batch of many matrices gains more from fewer launches than a
+  // large R-MAT loses to the gathers of four vectors); the quads use each handle's 4-vector
+  // partial-sum buffer, allocated here first.
   std::vector<std::vector<cb::RunArgs>> rounds;   // per round, all value types mixed
   std::vector<std::vector<cb::RunArgs>> quads;
   std::vector<std::pair<cbspmv_handle_t, int>> seen, seen4;
@@ -1089,7 +1101,7 @@ const char* cbspmv_last_error(void) { return g_err.c_str(); }
 
 // The run-kernel revision changes whenever the kernel's code changes (measurements taken
 // with a profiler are tied to it).
-const char* cbspmv_version(void) { return "cbspmv 0.6 (sm_103a; run kernel rev 18)"; }
+const char* cbspmv_version(void) { return "cbspmv 0.6 (sm_103a; run kernel rev 20)"; }
 
 }  // extern "C"
 

@@ -93,7 +93,7 @@ cbspmv_status_t analyze_host(const cbspmv_csr_t& A, const cbspmv_opts_t& opts, i
 // Steps of the analysis shared by the host analysis and the device analysis of
 // analyze_dev.cu (which builds p.tiles, the block-row tile offsets and the aggregation on
 // the GPU, and the lane programs there too).
-void cut_units(Plan& p, const std::vector<int64_t>& tile_off, const cbspmv_opts_t& opts);
+void cut_units(Plan& p, const std::vector<int64_t>& tile_off, const cbspmv_opts_t& opts, int n_workers);
 cbspmv_status_t check_units(const Plan& p, std::string* msg);
 void balance_units(Plan& p, const cbspmv_opts_t& opts, int n_workers, std::vector<double>* load);
 cbspmv_status_t lane_offsets(Plan& p, std::vector<uint64_t>* voff, std::vector<uint64_t>* woff,

@@ -767,8 +767,8 @@ __global__ void __launch_bounds__(32 * Geom<V, kK>::kWarps, 1) spmv_kernel(const
 
 // Adds the parts of every block row cut into several units, in part order, and writes y.
 template <class Acc, int kMaxP, int kK>
-__global__ void __launch_bounds__(256) combine_kernel(const __grid_constant__ BatchArgs<kMaxP> b) {
-  const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void combine_narrow(const BatchArgs<kMaxP>& b, uint32_t blk) {
+  const uint32_t g = blk * 256u + threadIdx.x;
   const uint32_t srg = g >> 4, r = g & 15u;
   if (srg >= b.split_base[b.count]) return;
   int q = 0;
@@ -821,8 +821,8 @@ __global__ void __launch_bounds__(256) combine_kernel(const __grid_constant__ Ba
 // power-law matrices can have hundreds of parts: with one thread per row, every iteration
 // would wait a full memory latency.
 template <class Acc, int kMaxP, int kK>
-__global__ void __launch_bounds__(256) combine_wide_kernel(const __grid_constant__ BatchArgs<kMaxP> b) {
-  const uint32_t srg = blockIdx.x;
+__device__ __forceinline__ void combine_wide(const BatchArgs<kMaxP>& b, uint32_t blk) {
+  const uint32_t srg = blk;
   const uint32_t r = threadIdx.x >> 4, lane = threadIdx.x & 15u;
   int q = 0;
   if (kMaxP > 1) {
@@ -860,6 +860,17 @@ __global__ void __launch_bounds__(256) combine_wide_kernel(const __grid_constant
       y[gr] = v;
     }
   }
+}
+
+// Adds the parts of split block rows: blocks [0, nb_narrow) take rows with few parts (16
+// threads per row), the remaining blocks one row with many parts each. One launch, a
+// programmatic dependent of the run kernel: it waits until that grid has completed and
+// its partial sums are visible (a no-op after an ordinary launch).
+template <class Acc, int kMaxP, int kK>
+__global__ void __launch_bounds__(256) combine_kernel(const __grid_constant__ BatchArgs<kMaxP> b, uint32_t nb_narrow) {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (blockIdx.x < nb_narrow) combine_narrow<Acc, kMaxP, kK>(b, blockIdx.x);
+  else combine_wide<Acc, kMaxP, kK>(b, blockIdx.x - nb_narrow);
 }
 
 // ---- lane-stream run kernel (FP64 values, layout in cb_layout.h) -------------------------
@@ -987,6 +998,10 @@ __global__ void __launch_bounds__(32 * LaneGeom<typename ValT<V>::Acc, kK>::kWar
   Acc* srow = reinterpret_cast<Acc*>(W + G::kOffRow);
   Acc* cval = reinterpret_cast<Acc*>(W + G::kOffCv);
   int32_t* crow = reinterpret_cast<int32_t*>(W + G::kOffCr);
+  // every CTA of this persistent grid is resident from the start, so the dependent combine
+  // launch (if any) may be scheduled now: its CTAs take SMs as this grid's CTAs finish and
+  // wait for the whole grid before reading the partial sums
+  asm volatile("griddepcontrol.launch_dependents;");
   const int P = b.count;
   if ((int)threadIdx.x < P) {
     const RunArgs& a = b.p[threadIdx.x];
@@ -1503,17 +1518,20 @@ template <class Acc, int kMaxP, int kK>
 cudaError_t launch_combine(const BatchArgs<kMaxP>& b, cudaStream_t stream) {
   cudaError_t e = cudaSuccess;
   const uint32_t nsplit = b.split_base[b.count], nwide = b.wide_base[b.count];
-  if (nsplit) {
-    const uint32_t threads = 16u * nsplit;
-    combine_kernel<Acc, kMaxP, kK><<<(threads + 255) / 256, 256, 0, stream>>>(b);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  if (nwide) {
-    combine_wide_kernel<Acc, kMaxP, kK><<<nwide, 256, 0, stream>>>(b);
-    e = cudaGetLastError();
-  }
-  return e;
+  if (!nsplit && !nwide) return e;
+  // one launch for both kinds of split rows, a programmatic dependent of the run kernel
+  // (its launch overlaps the run kernel's tail)
+  cudaLaunchAttribute pdl[1];
+  pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  pdl[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg{};
+  const uint32_t nb_narrow = (16u * nsplit + 255u) / 256u;
+  cfg.gridDim = dim3(nb_narrow + nwide);
+  cfg.blockDim = dim3(256);
+  cfg.stream = stream;
+  cfg.attrs = pdl;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, combine_kernel<Acc, kMaxP, kK>, b, nb_narrow);
 }
 
 template <class V, int kMaxP, int kK>
@@ -1544,18 +1562,8 @@ cudaError_t launch_typed(const BatchArgs<kMaxP>& b, int grid, cudaStream_t strea
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[1], stream)) != cudaSuccess) return e;
-  const uint32_t nsplit = b.split_base[b.count], nwide = b.wide_base[b.count];
-  if (nsplit) {
-    const uint32_t threads = 16u * nsplit;
-    combine_kernel<Acc, kMaxP, kK><<<(threads + 255) / 256, 256, 0, stream>>>(b);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  if (nwide) {
-    combine_wide_kernel<Acc, kMaxP, kK><<<nwide, 256, 0, stream>>>(b);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
+  e = launch_combine<Acc, kMaxP, kK>(b, stream);
+  if (e != cudaSuccess) return e;
   if (ev) e = cudaEventRecord(ev[2], stream);
   return e;
 }
@@ -1689,6 +1697,9 @@ cudaError_t launch_spmv_batch(const RunArgs* a, int count, int grid, cudaStream_
   for (int i = 0; i < count; ++i)
     if (a[i].value_dtype != a[0].value_dtype || a[i].nvec != a[0].nvec || (a[i].nvec != 1 && a[i].nvec != 4))
       return cudaErrorInvalidValue;
+  // a single problem takes the single-product instantiation: the same arithmetic (so the
+  // same result), without the 64-problem argument block or the problem lookup
+  if (count == 1) return launch_spmv(a[0], grid, stream);
   // one layout per launch: problems of the other layout go to launches of their own
   for (int i = 1; i < count; ++i)
     if (a[i].lanes != a[0].lanes) {

@@ -61,7 +61,7 @@ cbspmv_status_t sfail(cbspmv_status_t s, const char* fmt, ...) {
 // ---- device side: batched vector steps of CG ----------------------------------------------
 constexpr int kMaxSlots = 64;       // requests in flight (one batched launch each step)
 constexpr int kMaxMatrices = 1024;  // registered matrices per server
-constexpr int kVecBlock = 4096;     // vector elements per block of a batched vector kernel
+constexpr int kVecBlock = 1024;     // vector elements per block of a batched vector kernel
 constexpr int kVecThreads = 256;
 
 // Per-request scalars on the device (one array for all slots, copied back every tick).
@@ -70,7 +70,8 @@ struct Scalars {
   int done;          // refinement: ||r|| <= tol ||b||
   int inner_done;    // correction solve finished
   int inner_it, inner_cap;
-  int pad[4];
+  unsigned arrive;   // blocks of the current vector step that have stored their partial sum
+  int pad[3];
 };
 
 enum Op : int {
@@ -95,6 +96,7 @@ struct VecDesc {
   void* p;
   const void* q;
   double* part;          // nblk partial sums
+  int first_outer;       // kOpRefineDot: the first refinement (x = 0, so r = b gives ||b||)
 };
 struct VecBatch {
   int count;
@@ -174,51 +176,56 @@ __global__ void __launch_bounds__(kVecThreads) vec_kernel(const __grid_constant_
   }
   // deterministic block sum: fixed shuffle tree, then the block's warps in order
   __shared__ double ws[kVecThreads / 32];
+  __shared__ int last;
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
   __syncthreads();
-  if (threadIdx.x == 0 && v.part) {
+  if (v.op == kOpRefinePre || v.op == kOpDirection || !v.part) return;   // steps without a sum
+  if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w = 0; w < kVecThreads / 32; ++w) t += ws[w];
     v.part[blk] = t;
+    __threadfence();   // the partial before the arrival count
+    last = atomicAdd(&sc[v.slot].arrive, 1u) == (unsigned)v.nblk - 1u;
   }
-}
-
-// One warp per request: adds the request's block partials in a fixed order and updates its
-// scalars for the step that produced them.
-__global__ void finalize_kernel(const __grid_constant__ VecBatch b, Scalars* sc, uint32_t first_outer_mask_lo,
-                                uint32_t first_outer_mask_hi) {
-  const int q = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (q >= b.count) return;
-  const VecDesc& v = b.v[q];
+  __syncthreads();
+  // the request's last block to arrive adds the block partials in a fixed order (so the
+  // result does not depend on which block is last: thread-strided sums, the shuffle tree,
+  // the warps in order) and updates the request's scalars for the step; no block waits
+  // for another
+  if (!last) return;
+  __threadfence();
   double t = 0.0;
-  for (int i = lane; i < v.nblk; i += 32) t += v.part[i];
+  for (int i = threadIdx.x; i < v.nblk; i += kVecThreads) t += __ldcg(v.part + i);
   for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-  if (lane != 0) return;
-  Scalars& s = sc[v.slot];
-  if ((v.op == kOpPQ || v.op == kOpUpdate) && s.inner_done) return;   // (see vec_kernel)
-  const bool first_outer = q < 32 ? ((first_outer_mask_lo >> q) & 1u) : ((first_outer_mask_hi >> (q - 32)) & 1u);
+  __syncthreads();   // (every thread is done with ws)
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  t = 0.0;
+  for (int w = 0; w < kVecThreads / 32; ++w) t += ws[w];
+  Scalars& w = sc[v.slot];
+  w.arrive = 0u;
   switch (v.op) {
     case kOpRefineDot:
-      s.rn2 = t;
-      if (first_outer) s.bn2 = t;        // x starts at 0, so the first residual is b
-      s.done = (t <= s.tol2 * s.bn2) ? 1 : 0;
+      w.rn2 = t;
+      if (v.first_outer) w.bn2 = t;        // x starts at 0, so the first residual is b
+      w.done = (t <= w.tol2 * w.bn2) ? 1 : 0;
       break;
     case kOpRefineStart:
-      s.rr = s.rr0 = t;
-      s.inner_it = 0;
-      s.inner_done = t == 0.0 ? 1 : 0;
+      w.rr = w.rr0 = t;
+      w.inner_it = 0;
+      w.inner_done = t == 0.0 ? 1 : 0;
       break;
     case kOpPQ:
-      s.pq = t;
-      s.alpha = t != 0.0 ? s.rr / t : 0.0;
+      w.pq = t;
+      w.alpha = t != 0.0 ? w.rr / t : 0.0;
       break;
     case kOpUpdate:
-      s.beta = s.rr != 0.0 ? t / s.rr : 0.0;
-      s.rr = t;
-      s.inner_it += 1;
-      s.inner_done = (t <= s.tol_in2 * s.rr0 || s.inner_it >= s.inner_cap || !(t == t)) ? 1 : 0;
+      w.beta = w.rr != 0.0 ? t / w.rr : 0.0;
+      w.rr = t;
+      w.inner_it += 1;
+      w.inner_done = (t <= w.tol_in2 * w.rr0 || w.inner_it >= w.inner_cap || !(t == t)) ? 1 : 0;
       break;
     default:
       break;
@@ -494,24 +501,18 @@ cbspmv_status_t cbspmv_server_s::tick(std::vector<std::shared_ptr<Req>>& act, st
   if (!lo.empty()) cu(cb::launch_spmv_batch(lo.data(), (int)lo.size(), grid, s), "batched product (inner)");
   stats.launches += (hi.empty() ? 0 : 1) + (lo.empty() ? 0 : 1);
   // 4. dot products and updates
+  // (each vector step's last block per request finishes the step's dot product and the
+  // request's scalars: no separate launch)
   VecBatch v1{};
-  uint32_t first_lo = 0, first_hi = 0;
   for (auto& r : act) {
     if (r->ph == kPhRefine) {
-      if (r->outer == 0) {
-        const int q = v1.count;
-        if (q < 32) first_lo |= 1u << q; else first_hi |= 1u << (q - 32);
-      }
       add(v1, r, kOpRefineDot);
+      v1.v[v1.count - 1].first_outer = r->outer == 0;
     } else if (r->ph == kPhInner) {
       add(v1, r, kOpPQ);
     }
   }
   cu(vec(v1), "dot step 1");
-  if (v1.count) {
-    finalize_kernel<<<(v1.count + 3) / 4, 128, 0, s>>>(v1, d_sc, first_lo, first_hi);
-    cu(cudaGetLastError(), "finalize 1");
-  }
   // the refinement's convergence is known on the device; requests that continue start or
   // continue their inner solve
   VecBatch v2{};
@@ -520,10 +521,6 @@ cbspmv_status_t cbspmv_server_s::tick(std::vector<std::shared_ptr<Req>>& act, st
     else if (r->ph == kPhInner) add(v2, r, kOpUpdate);
   }
   cu(vec(v2), "dot step 2");
-  if (v2.count) {
-    finalize_kernel<<<(v2.count + 3) / 4, 128, 0, s>>>(v2, d_sc, 0u, 0u);
-    cu(cudaGetLastError(), "finalize 2");
-  }
   VecBatch v3{};
   for (auto& r : act)
     if (r->ph == kPhInner) add(v3, r, kOpDirection);
@@ -549,11 +546,7 @@ cbspmv_status_t cbspmv_server_s::tick(std::vector<std::shared_ptr<Req>>& act, st
       if (!lo2.empty()) cu(cb::launch_spmv_batch(lo2.data(), (int)lo2.size(), grid, s), "batched product (inner)");
       stats.launches += lo2.empty() ? 0 : 1;
       cu(vec(vpq), "inner p.q");
-      finalize_kernel<<<(vpq.count + 3) / 4, 128, 0, s>>>(vpq, d_sc, 0u, 0u);
-      cu(cudaGetLastError(), "inner finalize 1");
       cu(vec(vup), "inner update");
-      finalize_kernel<<<(vup.count + 3) / 4, 128, 0, s>>>(vup, d_sc, 0u, 0u);
-      cu(cudaGetLastError(), "inner finalize 2");
       cu(vec(vdir), "inner direction");
     }
   }
