@@ -367,8 +367,10 @@ cbspmv_status_t cbspmv_measure_fp64_fma(int device, void* stream, double* gflops
  * tick: the products of all in-flight requests run as one batched launch of the run kernel
  * per value type (see cbspmv_run_batched), the CG vector steps as batched kernels; a solve
  * in its inner CG phase runs up to inner_steps inner iterations per tick (its scalars stay
- * on the device, and the steps after its inner convergence do nothing). Each result is the
- * same whether the request runs alone or among others.
+ * on the device, and the steps after its inner convergence do nothing; with
+ * cg_oldest_first the older solves run more of them, which brings the serving of long
+ * solves closer to arrival order). Each result is the same whether the request runs alone
+ * or among others, and with either option.
  * CG (mixed precision with FP64 refinement): r = b - A x and x += d in FP64 with the
  * FP64-value product; each correction A d = r is solved by CG on cg_inner_dtype values
  * (FP32 vectors and accumulation for the reduced types; FP64 for CBSPMV_F64) to
@@ -386,7 +388,10 @@ typedef struct {
   int inner_steps;          /* inner CG iterations per engine tick, 1..64 (default 8; 0 = 8) */
   int max_inflight_cg;      /* CG solves in flight at most (0 = max_inflight); products keep
                                being admitted past CG requests that wait for this limit */
-  int reserved[6];
+  int cg_oldest_first;      /* 1: per tick the oldest solve in its inner phase runs all
+                               inner_steps iterations, the next inner_steps / 2, the others
+                               inner_steps / 4 (at least 1); 0 (default): all inner_steps */
+  int reserved[5];
 } cbspmv_server_opts_t;
 
 enum { CBSPMV_REQ_SPMV = 0, CBSPMV_REQ_CG = 1 };

@@ -67,7 +67,8 @@ class ServerOpts(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("memory_budget", ctypes.c_int64), ("max_inflight", ctypes.c_int),
                 ("cg_inner_dtype", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("inner_max_iter", ctypes.c_int), ("max_outer", ctypes.c_int),
-                ("inner_steps", ctypes.c_int), ("max_inflight_cg", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+                ("inner_steps", ctypes.c_int), ("max_inflight_cg", ctypes.c_int), ("cg_oldest_first", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
 
 
 class Request(ctypes.Structure):
@@ -439,7 +440,8 @@ class Server:
     continuous batching of in-flight requests on the device."""
 
     def __init__(self, device=0, memory_budget=4 << 30, max_inflight=64, cg_inner_dtype="bf16",
-                 inner_tol=1e-4, inner_max_iter=2000, max_outer=30, inner_steps=8, max_inflight_cg=0):
+                 inner_tol=1e-4, inner_max_iter=2000, max_outer=30, inner_steps=8, max_inflight_cg=0,
+                 cg_oldest_first=False):
         o = ServerOpts()
         _check(lib().cbspmv_server_default_opts(ctypes.byref(o)))
         o.device, o.memory_budget, o.max_inflight = device, int(memory_budget), max_inflight
@@ -447,6 +449,7 @@ class Server:
         o.inner_tol, o.inner_max_iter, o.max_outer = inner_tol, inner_max_iter, max_outer
         o.inner_steps = inner_steps
         o.max_inflight_cg = max_inflight_cg
+        o.cg_oldest_first = 1 if cg_oldest_first else 0
         self._s = ctypes.c_void_p(None)
         _check(lib().cbspmv_server_create(ctypes.byref(o), ctypes.byref(self._s)))
         self._keep: dict[int, tuple] = {}

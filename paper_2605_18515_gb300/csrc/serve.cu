@@ -526,23 +526,45 @@ cbspmv_status_t cbspmv_server_s::tick(std::vector<std::shared_ptr<Req>>& act, st
     if (r->ph == kPhInner) add(v3, r, kOpDirection);
   cu(vec(v3), "direction step");
   // 4b. further inner iterations of the solves in their inner phase: q = A p, alpha,
-  //     updates, direction; a solve whose inner CG converged meanwhile skips them (device)
+  //     updates, direction; a solve whose inner CG converged meanwhile skips them (device).
+  //     Each solve runs `quota` iterations this tick: all inner_steps, or with
+  //     cg_oldest_first inner_steps for the oldest, half for the next, a quarter for the rest
   {
+    std::vector<std::pair<int, std::shared_ptr<Req>>> inner;   // (quota, request), oldest first
+    for (auto& r : act)
+      if (r->ph == kPhInner) {
+        const int rank = (int)inner.size();
+        const int q = !o.cg_oldest_first || rank == 0 ? o.inner_steps
+                      : std::max(1, rank == 1 ? o.inner_steps / 2 : o.inner_steps / 4);
+        inner.push_back({q, r});
+      }
     std::vector<cb::RunArgs> lo2;
     VecBatch vpq{}, vup{}, vdir{};
-    for (auto& r : act) {
-      if (r->ph != kPhInner) continue;
-      const Matrix& M = mats[r->q.matrix];
-      cb::RunArgs a{};
-      int g = 0, ns = 0, dt = 0;
-      cb::server_run_args(M.lo, r->p, r->qv, 1.0, 0.0, r->part_lo, &a, &g, &ns, &dt);
-      if (M.m) lo2.push_back(a);
-      grid = g;
-      add(vpq, r, kOpPQ);
-      add(vup, r, kOpUpdate);
-      add(vdir, r, kOpDirection);
-    }
-    for (int it = 1; it < o.inner_steps && vpq.count; ++it) {
+    int members = -1;
+    for (int it = 1; it < o.inner_steps; ++it) {
+      int n = 0;
+      for (auto& e : inner) n += e.first > it;
+      if (n == 0) break;
+      if (n != members) {   // the batches of the solves with iterations left
+        members = n;
+        lo2.clear();
+        vpq = VecBatch{};
+        vup = VecBatch{};
+        vdir = VecBatch{};
+        for (auto& e : inner) {
+          if (e.first <= it) continue;
+          const auto& r = e.second;
+          const Matrix& M = mats[r->q.matrix];
+          cb::RunArgs a{};
+          int g = 0, ns = 0, dt = 0;
+          cb::server_run_args(M.lo, r->p, r->qv, 1.0, 0.0, r->part_lo, &a, &g, &ns, &dt);
+          if (M.m) lo2.push_back(a);
+          grid = g;
+          add(vpq, r, kOpPQ);
+          add(vup, r, kOpUpdate);
+          add(vdir, r, kOpDirection);
+        }
+      }
       if (!lo2.empty()) cu(cb::launch_spmv_batch(lo2.data(), (int)lo2.size(), grid, s), "batched product (inner)");
       stats.launches += lo2.empty() ? 0 : 1;
       cu(vec(vpq), "inner p.q");
@@ -695,6 +717,7 @@ cbspmv_status_t cbspmv_server_create(const cbspmv_server_opts_t* opts, cbspmv_se
   if (o.inner_steps < 0 || o.inner_steps > 64) return sfail(CBSPMV_ERR_INVALID, "inner_steps must be in [0, 64]");
   if (o.max_inflight_cg < 0 || o.max_inflight_cg > kMaxSlots)
     return sfail(CBSPMV_ERR_INVALID, "max_inflight_cg must be in [0, %d]", kMaxSlots);
+  if (o.cg_oldest_first != 0 && o.cg_oldest_first != 1) return sfail(CBSPMV_ERR_INVALID, "cg_oldest_first must be 0 or 1");
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
   if (e != cudaSuccess) return sfail(CBSPMV_ERR_CUDA, "cudaGetDeviceCount: %s", cudaGetErrorString(e));

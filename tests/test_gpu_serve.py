@@ -186,3 +186,30 @@ def test_cg_limit_lets_products_pass(env):
         assert np.array_equal(a, b)
     for x, b in zip(res[1][1], bs):
         assert true_rel_residual(L, x, b) <= TOL * 1.0001
+
+
+@pytest.mark.parametrize("inner_steps", [4, 16])
+def test_oldest_first_quotas_keep_results(env, inner_steps):
+    """cg_oldest_first: the oldest solve in its inner phase runs all inner_steps iterations
+    per tick, the next half, the rest a quarter; every solve's result equals the same
+    server's without the option bit for bit (iterations do not depend on how a tick groups
+    them) and reaches the tolerance; products in the mix are unchanged."""
+    bd, torch = env
+    L1, L2 = I.laplacian3d(12), I.laplacian3d(16)
+    bs = [I.uniform_pm1(110 + i, I.TAG_RHS, (L1 if i % 2 else L2).n) for i in range(5)]
+    xs = [I.uniform_pm1(120 + i, I.TAG_X, L2.n) for i in range(3)]
+    res = {}
+    for oldest in (True, False):
+        with bd.Server(inner_steps=inner_steps, cg_oldest_first=oldest) as S:
+            m1, m2 = S.register(L1), S.register(L2)
+            cg = [S.submit_cg(m1 if i % 2 else m2, b, TOL) for i, b in enumerate(bs)]
+            pr = [S.submit_spmv(m2, x) for x in xs]
+            rc = [S.wait(t) for t, _ in cg]
+            rp = [S.wait(t) for t, _ in pr]
+            assert all(r["status"] == 0 for r in rc + rp)
+            res[oldest] = ([x for _, x in cg], [y for _, y in pr], [r["iterations"] for r in rc])
+    for a, b in zip(res[True][0] + res[True][1], res[False][0] + res[False][1]):
+        assert np.array_equal(a, b)
+    assert res[True][2] == res[False][2]
+    for i, (x, b) in enumerate(zip(res[True][0], bs)):
+        assert true_rel_residual(L1 if i % 2 else L2, x, b) <= TOL * 1.0001
