@@ -217,6 +217,23 @@ def test_unit_sizes(env, unit_work):
     check(A, x, y)
 
 
+def test_small_matrix_units_spread_over_the_sms(env):
+    """With fewer default lane units (2,048 entries) than CTAs the analysis shrinks the unit
+    to max(256, largest block row, nnz / CTAs) entries: the 64x64 Laplacian (20,224
+    entries, block rows of 80) gets one unit of ~256 entries per CTA instead of 10 units,
+    and the product still matches the oracle; an explicit unit_work is kept as given."""
+    bd, torch = env
+    A = I.laplacian2d(64)
+    x = I.vector_x(A.n, 19)
+    y, st = gpu_spmv(env, A, x)
+    assert st["lane_layout"] == 1 and st["n_workers"] >= 100
+    assert st["n_units"] >= 64 and st["n_split_units"] == 0
+    check(A, x, y)
+    y2, st2 = gpu_spmv(env, A, x, unit_work=2048)
+    assert st2["n_units"] <= 12
+    check(A, x, y2)
+
+
 def test_load_balance_toggle_same_result(env):
     A = I.rmat(13, 16, seed=5)
     x = I.vector_x(A.n, 15)
