@@ -1101,7 +1101,7 @@ const char* cbspmv_last_error(void) { return g_err.c_str(); }
 
 // The run-kernel revision changes whenever the kernel's code changes (measurements taken
 // with a profiler are tied to it).
-const char* cbspmv_version(void) { return "cbspmv 0.6 (sm_103a; run kernel rev 20)"; }
+const char* cbspmv_version(void) { return "cbspmv 0.6 (sm_103a; run kernel rev 21)"; }
 
 }  // extern "C"
 

@@ -892,10 +892,14 @@ __global__ void __launch_bounds__(256) combine_kernel(const __grid_constant__ Ba
 #define CB_LANE_WARPS 20       // worker warps per SM (measured on the FEM band: 16 -> 20 -> 24)
 #endif
 #ifndef CB_LANE_WARPS_LP
-#define CB_LANE_WARPS_LP 32    // the same for the 4- and 2-byte value types (20 -> 24 -> 28 -> 32)
+#define CB_LANE_WARPS_LP 32    // the same for the 2-byte value types (20 -> 24 -> 28 -> 32)
 #endif
-template <class Acc, int kK>
+#ifndef CB_LANE_WARPS_F32
+#define CB_LANE_WARPS_F32 28   // FP32 values (32 -> 28: FEM -1%, R-MAT -3.5%; registers 64 -> 73)
+#endif
+template <class V, int kK>
 struct LaneGeom {
+  using Acc = typename ValT<V>::Acc;
   static constexpr uint32_t kSlot = (uint32_t)sizeof(Acc) * kK;       // bytes of one x slot
   static constexpr uint32_t kXBuf = CB_LANE_SLOTS * kSlot;            // one x buffer
   static constexpr uint32_t kOffRow = 2 * kXBuf;                      // row sums, CB_R_MAX x kK
@@ -905,7 +909,7 @@ struct LaneGeom {
   static constexpr uint32_t kFit = (kSmemMax - kHeaderBytes) / kWarpBytes;
   // the FP64 walk is bound by the FP64 FMA pipe (20 warps measured best); the reduced types'
   // walk by latency, where more warps per SM help (registers shrink to fit)
-  static constexpr int kWant = sizeof(Acc) == 8 ? CB_LANE_WARPS : CB_LANE_WARPS_LP;
+  static constexpr int kWant = sizeof(V) == 8 ? CB_LANE_WARPS : sizeof(V) == 4 ? CB_LANE_WARPS_F32 : CB_LANE_WARPS_LP;
   static_assert(kWant <= 32, "at most 1024 threads per CTA");
   static constexpr int kWarps = kFit < (uint32_t)kWant ? (int)kFit : kWant;
   static constexpr uint32_t kSmem = kHeaderBytes + kWarps * kWarpBytes;
@@ -982,10 +986,10 @@ template <> struct LaneVals<__half> {
 // shared memory, rows that cross lane runs are joined through the neighbouring lanes, and
 // the unit's rows are written to y (or to the partial-sum slot of a block-row part).
 template <class V, int kMaxP, int kK>
-__global__ void __launch_bounds__(32 * LaneGeom<typename ValT<V>::Acc, kK>::kWarps, 1)
+__global__ void __launch_bounds__(32 * LaneGeom<V, kK>::kWarps, 1)
     spmv_lanes_kernel(const __grid_constant__ BatchArgs<kMaxP> b) {
   using Acc = typename ValT<V>::Acc;
-  using G = LaneGeom<Acc, kK>;
+  using G = LaneGeom<V, kK>;
   constexpr bool kGrouped = sizeof(V) != 8;
   constexpr int kB = kGrouped ? CB_LANE_BATCH : 1;
   constexpr uint32_t kFull = 0xffffffffu;
@@ -1506,7 +1510,7 @@ cudaError_t configure_lanes() {
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64 || !configured[dev].load(std::memory_order_acquire)) {
     e = cudaFuncSetAttribute(spmv_lanes_kernel<V, kMaxP, kK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)LaneGeom<typename ValT<V>::Acc, kK>::kSmem);
+                             (int)LaneGeom<V, kK>::kSmem);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) configured[dev].store(true, std::memory_order_release);
   }
@@ -1537,7 +1541,7 @@ cudaError_t launch_combine(const BatchArgs<kMaxP>& b, cudaStream_t stream) {
 template <class V, int kMaxP, int kK>
 cudaError_t launch_lanes(const BatchArgs<kMaxP>& b, int grid, cudaStream_t stream, cudaEvent_t* ev) {
   using Acc = typename ValT<V>::Acc;
-  using G = LaneGeom<Acc, kK>;
+  using G = LaneGeom<V, kK>;
   cudaError_t e = configure_lanes<V, kMaxP, kK>();
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[0], stream)) != cudaSuccess) return e;
@@ -1643,7 +1647,7 @@ cudaError_t launch_repack(uint8_t* stream, const uint32_t* slot, const double* v
 size_t spmv_smem_bytes() {
   const uint32_t v[] = {Geom<double>::kSmem, Geom<float>::kSmem, Geom<__half>::kSmem, Geom<double, 4>::kSmem,
                         Geom<float, 4>::kSmem, Geom<__half, 4>::kSmem, LaneGeom<double, 1>::kSmem,
-                        LaneGeom<float, 1>::kSmem};
+                        LaneGeom<float, 1>::kSmem, LaneGeom<__nv_bfloat16, 1>::kSmem, LaneGeom<float, 4>::kSmem};
   uint32_t m = 0;
   for (uint32_t x : v) m = x > m ? x : m;
   return m;
