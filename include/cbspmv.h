@@ -83,7 +83,10 @@ typedef struct {
  *   col_agg: -1 decide by th0, 0 never aggregate, 1 always aggregate.
  *   value_dtype: storage type of the values (CBSPMV_F64 for the FP64 path; see
  *        cbspmv_dtype_t for the reduced types).
- *   unit_work: target number of multiply-adds per scheduling unit (0 = default).
+ *   unit_work: target number of multiply-adds per scheduling unit (0 = default: 2,048
+ *        stored entries in the lane-stream layout, or fewer, down to max(256, the largest
+ *        block row), when the matrix has fewer such units than the handle has CTAs; 1,024
+ *        multiply-adds in the record layout).
  *   load_balance: 1 (default) spread units over workers by the longest-first
  *        priority-queue rule; 0 deal them out round-robin in matrix order (ablation).
  *   device: CUDA device ordinal for the handle's memory; -1 builds a host-only handle
