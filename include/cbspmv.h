@@ -221,10 +221,12 @@ cbspmv_status_t cbspmv_run_multi(cbspmv_handle_t h, int k, const void* X, int64_
  * zero-filled 16x16 BF16 tile and multiplied with mma.sync.m16n8k16 (BF16 inputs, FP32
  * accumulation); every x is split exactly into three BF16 parts (|x - sum| <= 2^-25 |x|) so
  * the products keep FP32 accuracy; a row's result has error at most gamma_{6r + 16} with
- * u = 2^-23 times sum_j |a_ij x_j| (r = stored entries of the row), see the design notes.
- * Up to 32 columns per launch (the matrix is read once per 32 columns), plus one small
- * launch that adds the segments of block rows with more than 64 sub-blocks. The first call
- * builds the segment list and allocates a partial-sum buffer (owned by the handle). Like
+ * u = 2^-23 times sum_j |a_ij x_j| (r = stored entries of the row). Per 32 columns one
+ * pass splits X into a workspace (8 bytes per x) and one launch multiplies (the matrix is
+ * read once per 32 columns), plus one small launch that adds the segments of block rows
+ * with more than 64 sub-blocks. The first call builds the segment list and allocates a
+ * partial-sum buffer, and the split-X workspace grows to n x 32 x 8 bytes at most (both
+ * owned by the handle). Like
  * Dense zero fill, a non-finite x reaches every row of a sub-block holding its column.
  * Asynchronous on `stream`. Errors: CBSPMV_ERR_INVALID (arguments), CBSPMV_ERR_UNSUPPORTED,
  * CBSPMV_ERR_OOM, CBSPMV_ERR_CUDA. */

@@ -117,6 +117,8 @@ struct cbspmv_handle_s {
   cb::SpmmSplit* d_spmm_splits = nullptr;
   float* d_spmm_partial = nullptr;
   uint32_t* d_spmm_counter = nullptr;
+  uint2* d_spmm_xs = nullptr;          // split X workspace (n x kpad), grown on demand
+  size_t spmm_xs_cap = 0;
   uint32_t spmm_nseg = 0, spmm_nsplit = 0;
   bool spmm_ready = false;
   long long wait_budget = 4000000000LL;   // device wait budget of the record kernel (clock64 cycles)
@@ -131,7 +133,7 @@ struct cbspmv_handle_s {
     void* ptrs[] = {d_stream, d_tiles, d_rcols, d_units, d_blob, d_wunits, d_woff, d_partial, d_split_rows,
                     d_err, d_xstage, d_ystage, d_partial_multi, d_vslot, d_valstage,
                     d_lunits, d_lvals, d_lwords, d_lgcols,
-                    d_spmm_segs, d_spmm_splits, d_spmm_partial, d_spmm_counter};
+                    d_spmm_segs, d_spmm_splits, d_spmm_partial, d_spmm_counter, d_spmm_xs};
     for (void* p : ptrs)
       if (p) cudaFree(p);
     d_stream = nullptr;
@@ -157,6 +159,8 @@ struct cbspmv_handle_s {
     d_spmm_splits = nullptr;
     d_spmm_partial = nullptr;
     d_spmm_counter = nullptr;
+    d_spmm_xs = nullptr;
+    spmm_xs_cap = 0;
     spmm_ready = false;
   }
 };
@@ -605,6 +609,24 @@ cbspmv_status_t cbspmv_spmm(cbspmv_handle_t h, int k, const void* X, int64_t ldx
     const cbspmv_status_t st = spmm_prepare(h, s);
     if (st != CBSPMV_OK) return st;
   }
+  // the workspace of the split X: n x kpad (k rounded up to 8, at most 32) elements of 8 bytes
+  {
+    const int kmax = k < 32 ? k : 32;
+    const size_t need = (size_t)(p.n > 0 ? p.n : 1) * (size_t)((kmax + 7) / 8 * 8);
+    if (need > h->spmm_xs_cap) {
+      if (h->d_spmm_xs) {
+        CB_CUDA(cudaStreamSynchronize(s));   // (earlier launches may still read it)
+        cudaFree(h->d_spmm_xs);
+        h->d_spmm_xs = nullptr;
+        h->spmm_xs_cap = 0;
+      }
+      const cudaError_t e = dev_malloc((void**)&h->d_spmm_xs, need * sizeof(uint2));
+      if (e != cudaSuccess)
+        return fail(e == cudaErrorMemoryAllocation ? CBSPMV_ERR_OOM : CBSPMV_ERR_CUDA, "cbspmv_spmm workspace: %s",
+                    cudaGetErrorString(e));
+      h->spmm_xs_cap = need;
+    }
+  }
   // 32 columns per launch (the 16 x 32 accumulators of a segment stay in registers)
   for (int j0 = 0; j0 < k; j0 += 32) {
     cb::SpmmArgs a{};
@@ -624,6 +646,8 @@ cbspmv_status_t cbspmv_spmm(cbspmv_handle_t h, int k, const void* X, int64_t ldx
     a.ldx = ldx;
     a.ldy = ldy;
     a.k = k - j0 < 32 ? k - j0 : 32;
+    a.xs = h->d_spmm_xs;
+    a.kpad = (a.k + 7) / 8 * 8;
     a.alpha = (float)alpha;
     a.beta = (float)beta;
     a.alpha_one = alpha == 1.0;

@@ -30,6 +30,8 @@ struct SpmmArgs {
   float* partial;             // 16 x k per slot
   uint32_t* counter;          // segment ticket (zeroed before each launch)
   const void* x;              // n x k FP32, row-major, leading dimension ldx
+  uint2* xs;                  // workspace, n x kpad: each x split into BF16 parts h | m << 16, l
+  int kpad;                   // k rounded up to 8
   void* y;                    // m x k FP32, row-major, leading dimension ldy
   int64_t m, n, ldx, ldy;
   int k;                      // 1..32

@@ -13,7 +13,8 @@
 //     operands, X is FP32: each x is split exactly into three BF16 parts, h + m + l, with
 //     |x - (h + m + l)| <= 2^-25 |x|, and the three partial products are accumulated in
 //     FP32 (products of two BF16 numbers are exact in FP32), so the result keeps FP32-level
-//     accuracy while the stored values stay BF16;
+//     accuracy while the stored values stay BF16. The split is done once per x by a first
+//     pass into a workspace of 8 bytes per x (h, m; l), not once per sub-block using it;
 //   * the 16 x k accumulators stay in registers across the block row's sub-blocks; whole
 //     block rows write Y once, block rows cut into segments store 16 x k partial sums that a
 //     second kernel adds in segment order.
@@ -54,6 +55,24 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// Splits X (n x k, FP32, row-major with leading dimension ldx) into the workspace: element
+// (i, j) of the n x kpad result holds h | m << 16 and l of split3(x_ij), zero past k.
+__global__ void __launch_bounds__(256) split_x_kernel(const SpmmArgs a) {
+  const uint64_t total = (uint64_t)a.n * (uint64_t)a.kpad;
+  const float* X = static_cast<const float*>(a.x);
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t i = e / (uint64_t)a.kpad;
+    const int j = (int)(e % (uint64_t)a.kpad);
+    uint2 q = make_uint2(0u, 0u);
+    if (j < a.k) {
+      __nv_bfloat16 h, m, l;
+      split3(X[(int64_t)i * a.ldx + j], h, m, l);
+      q = make_uint2(pack2(h, m), pack2(l, __float2bfloat16_rn(0.f)));
+    }
+    a.xs[e] = q;
+  }
+}
+
 // Sub-blocks are taken in rounds of kB: the records, column indices and X values of a
 // round's sub-blocks are loaded stage by stage for all of them before any is multiplied, so
 // the three dependent memory latencies of a sub-block (record, restore_cols, X) are paid
@@ -65,7 +84,6 @@ __global__ void __launch_bounds__(32 * kWarps) spmm_bf16_kernel(const SpmmArgs a
   uint8_t* T = tiles_smem + warp * kTileBytes;
   const uint32_t g = lane >> 2, tig = lane & 3;     // MMA group and thread in group
   const int k = a.k;
-  const float* X = static_cast<const float*>(a.x);
   float* Y = static_cast<float*>(a.y);
   constexpr uint32_t kNoEntry = 0xffffffffu;
   for (;;) {
@@ -123,8 +141,8 @@ __global__ void __launch_bounds__(32 * kWarps) spmm_bf16_kernel(const SpmmArgs a
           col[b][i] = cc < a.n ? (int32_t)cc : -1;
         }
       }
-      // 3. the X values of this lane's B fragments
-      float xv[kB][kNB][4];
+      // 3. the split X values of this lane's B fragments (zero past k and past n)
+      uint2 xv[kB][kNB][4];
 #pragma unroll
       for (int b = 0; b < kB; ++b)
 #pragma unroll
@@ -132,7 +150,7 @@ __global__ void __launch_bounds__(32 * kWarps) spmm_bf16_kernel(const SpmmArgs a
           const int j = nb * 8 + (int)g;
 #pragma unroll
           for (int i = 0; i < 4; ++i)
-            xv[b][nb][i] = (col[b][i] >= 0 && j < k) ? __ldg(X + (int64_t)col[b][i] * a.ldx + j) : 0.f;
+            xv[b][nb][i] = col[b][i] >= 0 ? __ldg(a.xs + (int64_t)col[b][i] * a.kpad + j) : make_uint2(0u, 0u);
         }
       // 4. each sub-block: A as a zero-filled 16x16 BF16 tile, row-major, then the MMAs
 #pragma unroll
@@ -170,13 +188,11 @@ __global__ void __launch_bounds__(32 * kWarps) spmm_bf16_kernel(const SpmmArgs a
         }
 #pragma unroll
         for (int nb = 0; nb < kNB; ++nb) {
-          __nv_bfloat16 h[4], m[4], l[4];
-#pragma unroll
-          for (int i = 0; i < 4; ++i) split3(xv[b][nb][i], h[i], m[i], l[i]);
-          // smallest parts first
-          mma_bf16(c[nb], af, pack2(l[0], l[1]), pack2(l[2], l[3]));
-          mma_bf16(c[nb], af, pack2(m[0], m[1]), pack2(m[2], m[3]));
-          mma_bf16(c[nb], af, pack2(h[0], h[1]), pack2(h[2], h[3]));
+          const uint2* q = xv[b][nb];
+          // smallest parts first; rows 2 tig, 2 tig + 1 (and + 8) pair up in the B fragment
+          mma_bf16(c[nb], af, __byte_perm(q[0].y, q[1].y, 0x5410), __byte_perm(q[2].y, q[3].y, 0x5410));
+          mma_bf16(c[nb], af, __byte_perm(q[0].x, q[1].x, 0x7632), __byte_perm(q[2].x, q[3].x, 0x7632));
+          mma_bf16(c[nb], af, __byte_perm(q[0].x, q[1].x, 0x5410), __byte_perm(q[2].x, q[3].x, 0x5410));
         }
         __syncwarp();   // the tile buffer is rewritten by the next sub-block
       }
@@ -230,6 +246,13 @@ __global__ void __launch_bounds__(256) spmm_combine_kernel(const SpmmArgs a) {
 cudaError_t launch_spmm_bf16(const SpmmArgs& a, int grid, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
+  if (a.n > 0) {
+    const uint64_t total = (uint64_t)a.n * (uint64_t)a.kpad;
+    const unsigned blocks = (unsigned)((total + 255) / 256 < 152ull * 32 ? (total + 255) / 256 : 152ull * 32);
+    split_x_kernel<<<blocks, 256, 0, s>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   const int nb = (a.k + 7) / 8;
   switch (nb) {   // rounds of 4 sub-blocks, 2 at the widest (registers)
     case 1: spmm_bf16_kernel<1, 4><<<grid, 32 * kWarps, 0, s>>>(a); break;
