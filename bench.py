@@ -597,7 +597,7 @@ def serve_run(S, ids, mats, n_req, rate, seed):
             "launches": st["launches"] - st0["launches"]}
 
 
-def serve_bench(pool_name, seed=5, inner_steps=16, max_cg=0, inner_tol=1e-5):
+def serve_bench(pool_name, seed=5, inner_steps=16, max_cg=0, inner_tol=1e-6):
     """Both modes' burst capacity; then Poisson arrivals at one common rate (70% of the
     one-at-a-time capacity, a load both modes sustain) for both, and the served mode also at
     70% of its own capacity."""
@@ -620,7 +620,8 @@ def serve_bench(pool_name, seed=5, inner_steps=16, max_cg=0, inner_tol=1e-5):
                    f"{len(spec['rmat'])} R-MAT (scales {spec['rmat'][0][0]}-{spec['rmat'][-1][0]})",
            "mix": "70% y=Ax (FP64), 30% CG to 1e-8 relative residual",
            "served": {"mode": "continuous batching, 64 in flight, BF16-value CG with FP64 refinement, "
-                              f"{inner_steps} inner CG iterations per tick, inner tolerance {inner_tol:g}, "
+                              f"{inner_steps} inner CG iterations per tick, inner tolerance {inner_tol:g} "
+                              "(later corrections stop at the gap to the outer tolerance), "
                               f"{max_cg or 64} CG solves in flight at most",
                       "capacity": cap, "poisson_same_load": same, "poisson_at_70pct": load},
            "one_at_a_time_fp64": {"mode": "one request at a time, FP64 products and FP64 CG",

@@ -378,8 +378,11 @@ cbspmv_status_t cbspmv_measure_fp64_fma(int device, void* stream, double* gflops
  * or among others, and with either option.
  * CG (mixed precision with FP64 refinement): r = b - A x and x += d in FP64 with the
  * FP64-value product; each correction A d = r is solved by CG on cg_inner_dtype values
- * (FP32 vectors and accumulation for the reduced types; FP64 for CBSPMV_F64) to
- * inner_tol relative to its start; the solve ends when ||b - A x|| <= tol ||b|| (FP64). */
+ * (FP32 vectors and accumulation for the reduced types; FP64 for CBSPMV_F64) until its
+ * residual is max(inner_tol, 0.3 tol ||b|| / ||r||) times its start, r being the FP64
+ * residual the correction starts from (the first correction, r = b, stops at
+ * max(inner_tol, 0.3 tol), a later one as soon as it closes the gap to tol); the solve ends when
+ * ||b - A x|| <= tol ||b|| (FP64). */
 typedef struct cbspmv_server_s* cbspmv_server_t;
 
 typedef struct {
@@ -387,7 +390,8 @@ typedef struct {
   int64_t memory_budget;    /* bytes of request workspace (allocated at creation) */
   int max_inflight;         /* requests in flight, 1..64 (1 = one request at a time) */
   cbspmv_dtype_t cg_inner_dtype;  /* values of the inner CG product (default BF16) */
-  double inner_tol;         /* inner CG: stop at ||r|| <= inner_tol ||r0|| (default 1e-4) */
+  double inner_tol;         /* inner CG: stop at ||r|| <= inner_tol ||r0|| at the tightest
+                               (default 1e-4; see above for later corrections) */
   int inner_max_iter;       /* inner CG iterations per correction (default 2000) */
   int max_outer;            /* refinement steps before a solve fails (default 30) */
   int inner_steps;          /* inner CG iterations per engine tick, 1..64 (default 8; 0 = 8) */

@@ -11,7 +11,9 @@
 //     residual r = b - A x and the solution update stay in FP64 (FP64-value product);
 //     each correction A d = r is solved by conjugate gradients with the product on
 //     reduced-precision values (BF16 storage, FP32 x, y and accumulation) and FP32
-//     vectors; a solve ends when ||b - A x|| <= tol * ||b|| in FP64.
+//     vectors, until its residual falls by max(inner_tol, 0.3 tol ||b|| / ||r||) (a later
+//     correction only needs to close the gap to tol); a solve ends when
+//     ||b - A x|| <= tol * ||b|| in FP64.
 // Per tick, the products of all in-flight requests run as one batched launch of the run
 // kernel per value type; the CG vector updates and dot products run as batched kernels
 // over all requests; one small device-to-host copy of the requests' scalars decides the
@@ -63,10 +65,14 @@ constexpr int kMaxSlots = 64;       // requests in flight (one batched launch ea
 constexpr int kMaxMatrices = 1024;  // registered matrices per server
 constexpr int kVecBlock = 1024;     // vector elements per block of a batched vector kernel
 constexpr int kVecThreads = 256;
+// A correction A d = r only has to bring the FP64 residual below tol ||b||: it stops at
+// max(inner_tol, kCorSafety * tol ||b|| / ||r||) relative to its start (squared here).
+constexpr double kCorSafety2 = 0.3 * 0.3;
 
 // Per-request scalars on the device (one array for all slots, copied back every tick).
 struct Scalars {
   double rr, rr0, pq, alpha, beta, rn2, bn2, tol2, tol_in2;
+  double tol_cor2;   // squared relative tolerance of the current correction solve
   int done;          // refinement: ||r|| <= tol ||b||
   int inner_done;    // correction solve finished
   int inner_it, inner_cap;
@@ -216,6 +222,7 @@ __global__ void __launch_bounds__(kVecThreads) vec_kernel(const __grid_constant_
       w.rr = w.rr0 = t;
       w.inner_it = 0;
       w.inner_done = t == 0.0 ? 1 : 0;
+      w.tol_cor2 = w.rn2 > 0.0 ? fmax(w.tol_in2, kCorSafety2 * w.tol2 * w.bn2 / w.rn2) : w.tol_in2;
       break;
     case kOpPQ:
       w.pq = t;
@@ -225,7 +232,7 @@ __global__ void __launch_bounds__(kVecThreads) vec_kernel(const __grid_constant_
       w.beta = w.rr != 0.0 ? t / w.rr : 0.0;
       w.rr = t;
       w.inner_it += 1;
-      w.inner_done = (t <= w.tol_in2 * w.rr0 || w.inner_it >= w.inner_cap || !(t == t)) ? 1 : 0;
+      w.inner_done = (t <= w.tol_cor2 * w.rr0 || w.inner_it >= w.inner_cap || !(t == t)) ? 1 : 0;
       break;
     default:
       break;

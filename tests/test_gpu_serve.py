@@ -101,6 +101,43 @@ def test_mixed_precision_cg_needs_few_refinements(env):
     assert true_rel_residual(L, x, b) <= TOL * 1.0001
 
 
+def cg_iterations_fp64(A, b, rel):
+    """Iterations of textbook CG in FP64 from x = 0 until its residual is rel ||b||."""
+    import scipy.sparse as sp
+    M = sp.csr_matrix((A.val, A.col, A.row_ptr), shape=(A.m, A.n))
+    r = b.copy()
+    p = r.copy()
+    rr = rr0 = float(r @ r)
+    k = 0
+    while rr > rel * rel * rr0:
+        q = M @ p
+        al = rr / float(p @ q)
+        r -= al * q
+        t = float(r @ r)
+        p = r + (t / rr) * p
+        rr = t
+        k += 1
+    return k
+
+
+def test_later_corrections_stop_at_the_gap_to_tol(env):
+    """A correction after the first only has to close the gap between its starting residual
+    and tol ||b|| (with 0.3 to spare): with inner_tol 1e-6 and tol 1e-8 the first correction
+    takes the iterations of a 1e-6 solve (N) and the second those of a ~3e-3 one, so the
+    solve takes two refinements and well under the 2N iterations of two full-depth
+    corrections (FP32 simulation of this 20^3 case: 84 against 128, N = 63)."""
+    bd, _ = env
+    L = I.laplacian3d(20)
+    b = I.uniform_pm1(9, I.TAG_RHS, L.n)
+    with bd.Server(cg_inner_dtype="bf16", inner_tol=1e-6) as S:
+        t, x = S.submit_cg(S.register(L), b, TOL)
+        r = S.wait(t)
+    n1 = cg_iterations_fp64(L, b, 1e-6)
+    assert r["status"] == 0 and r["refinements"] == 2, r
+    assert r["iterations"] <= 1.5 * n1, (r["iterations"], n1)
+    assert true_rel_residual(L, x, b) <= TOL * 1.0001
+
+
 def test_fp64_one_at_a_time_mode(env):
     bd, _ = env
     L = I.laplacian3d(12)
