@@ -226,7 +226,8 @@ cbspmv_status_t cbspmv_run_multi(cbspmv_handle_t h, int k, const void* X, int64_
  * read once per 32 columns), plus one small launch that adds the segments of block rows
  * with more than 64 sub-blocks. The first call builds the segment list and allocates a
  * partial-sum buffer, and the split-X workspace grows to n x 32 x 8 bytes at most (both
- * owned by the handle). Like
+ * owned by the handle and shared by its calls: calls on one handle whose work may overlap on
+ * the GPU, on other streams, race, so serialise them). Like
  * Dense zero fill, a non-finite x reaches every row of a sub-block holding its column.
  * Asynchronous on `stream`. Errors: CBSPMV_ERR_INVALID (arguments), CBSPMV_ERR_UNSUPPORTED,
  * CBSPMV_ERR_OOM, CBSPMV_ERR_CUDA. */
