@@ -13,7 +13,13 @@
 //     reduced-precision values (BF16 storage, FP32 x, y and accumulation) and FP32
 //     vectors, until its residual falls by max(inner_tol, 0.3 tol ||b|| / ||r||) (a later
 //     correction only needs to close the gap to tol); a solve ends when
-//     ||b - A x|| <= tol * ||b|| in FP64.
+//     ||b - A x|| <= tol * ||b|| in FP64. The inner CG is the Chronopoulos-Gear form
+//     (1989): the product is w = A r of the current residual, and the step lengths come
+//     from r.r and w.r alone (alpha = rr / (wr - beta rr / alpha_prev), beta = rr /
+//     rr_prev), with s = A p carried by the recurrence s = w + beta s. An iteration is one
+//     product, one dot-product step (w.r) and one fused update (p, s, d, r and the next r.r),
+//     one launch fewer than the textbook order (alpha needs p.Ap after the product, beta
+//     r.r after the update); in exact arithmetic the iterates are those of textbook CG.
 // Per tick, the products of all in-flight requests run as one batched launch of the run
 // kernel per value type; the CG vector updates and dot products run as batched kernels
 // over all requests; one small device-to-host copy of the requests' scalars decides the
@@ -71,7 +77,7 @@ constexpr double kCorSafety2 = 0.3 * 0.3;
 
 // Per-request scalars on the device (one array for all slots, copied back every tick).
 struct Scalars {
-  double rr, rr0, pq, alpha, beta, rn2, bn2, tol2, tol_in2;
+  double rr, rr_prev, rr0, wr, alpha, beta, rn2, bn2, tol2, tol_in2;
   double tol_cor2;   // squared relative tolerance of the current correction solve
   int done;          // refinement: ||r|| <= tol ||b||
   int inner_done;    // correction solve finished
@@ -84,10 +90,10 @@ enum Op : int {
   kOpNone = 0,
   kOpRefinePre,    // x64 += d; r64 = b (before r64 = -A x64 + r64)
   kOpRefineDot,    // partial r64 . r64
-  kOpRefineStart,  // r_in = r64; d = 0; p = r_in; partial r_in . r_in
-  kOpPQ,           // partial p . q
-  kOpUpdate,       // d += alpha p; r_in -= alpha q; partial r_in . r_in
-  kOpDirection,    // p = r_in + beta p
+  kOpRefineStart,  // r_in = r64; d = p = s = 0; partial r_in . r_in
+  kOpWR,           // partial w . r_in (w = A r_in)
+  kOpUpdate,       // p = r_in + beta p; s = w + beta s; d += alpha p; r_in -= alpha s;
+                   // partial r_in . r_in
 };
 
 struct VecDesc {
@@ -100,7 +106,8 @@ struct VecDesc {
   void* d;               // inner vectors: float (mixed precision) or double (FP64 CG)
   void* r;
   void* p;
-  const void* q;
+  void* s;               // A p
+  const void* w;         // A r
   double* part;          // nblk partial sums
   int first_outer;       // kOpRefineDot: the first refinement (x = 0, so r = b gives ||b||)
 };
@@ -112,6 +119,11 @@ struct VecBatch {
 
 template <class T>
 __global__ void __launch_bounds__(kVecThreads) vec_kernel(const __grid_constant__ VecBatch b, Scalars* sc) {
+  // A dot-product or update step may be launched as a programmatic dependent of the kernel
+  // before it: it waits for that kernel's completion and memory before touching anything,
+  // and lets the next step's launch start at once (that step waits in turn).
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;");
   // request of this block: the last q with blk_base[q] <= blockIdx.x
   int lo = 0, hi = b.count - 1;
   while (lo < hi) {
@@ -125,11 +137,12 @@ __global__ void __launch_bounds__(kVecThreads) vec_kernel(const __grid_constant_
   const Scalars& s = sc[v.slot];
   // the inner steps of a solve whose inner CG has converged do nothing (a tick may run
   // several inner iterations; the device knows when a solve converged, the host later)
-  if ((v.op == kOpPQ || v.op == kOpUpdate || v.op == kOpDirection) && s.inner_done) return;
+  if ((v.op == kOpWR || v.op == kOpUpdate) && s.inner_done) return;
   T* d = static_cast<T*>(v.d);
   T* r = static_cast<T*>(v.r);
   T* p = static_cast<T*>(v.p);
-  const T* q = static_cast<const T*>(v.q);
+  T* sv = static_cast<T*>(v.s);
+  const T* wv = static_cast<const T*>(v.w);
   double acc = 0.0;
   switch (v.op) {
     case kOpRefinePre:
@@ -145,7 +158,8 @@ __global__ void __launch_bounds__(kVecThreads) vec_kernel(const __grid_constant_
       for (int64_t i = i0 + threadIdx.x; i < i1; i += kVecThreads) {
         const T ri = (T)v.r64[i];
         r[i] = ri;
-        p[i] = ri;
+        p[i] = T(0);
+        sv[i] = T(0);
         d[i] = T(0);
         acc = fma((double)ri, (double)ri, acc);
       }
@@ -154,27 +168,27 @@ __global__ void __launch_bounds__(kVecThreads) vec_kernel(const __grid_constant_
     // mixed-precision solve (an FP64 FMA, or a conversion to FP64, per element would hold
     // GB300's slow FP64 pipe longer than the whole FP32 step; the inner solve only needs a
     // residual reduction of inner_tol), FP64 for the FP64 solve. Each block's sum is FP64.
-    case kOpPQ: {
+    case kOpWR: {
       T a = T(0);
-      for (int64_t i = i0 + threadIdx.x; i < i1; i += kVecThreads) a = fma(p[i], q[i], a);
+      for (int64_t i = i0 + threadIdx.x; i < i1; i += kVecThreads) a = fma(wv[i], r[i], a);
       acc = (double)a;
       break;
     }
     case kOpUpdate: {
-      const T al = (T)s.alpha;
+      const T al = (T)s.alpha, be = (T)s.beta;
       T a = T(0);
       for (int64_t i = i0 + threadIdx.x; i < i1; i += kVecThreads) {
-        d[i] = fma(al, p[i], d[i]);
-        const T ri = fma(-al, q[i], r[i]);
-        r[i] = ri;
-        a = fma(ri, ri, a);
+        const T ri = r[i];
+        const T pi = fma(be, p[i], ri);
+        const T si = fma(be, sv[i], wv[i]);
+        p[i] = pi;
+        sv[i] = si;
+        d[i] = fma(al, pi, d[i]);
+        const T rn = fma(-al, si, ri);
+        r[i] = rn;
+        a = fma(rn, rn, a);
       }
       acc = (double)a;
-      break;
-    }
-    case kOpDirection: {
-      const T be = (T)s.beta;
-      for (int64_t i = i0 + threadIdx.x; i < i1; i += kVecThreads) p[i] = fma(be, p[i], r[i]);
       break;
     }
     default:
@@ -186,7 +200,7 @@ __global__ void __launch_bounds__(kVecThreads) vec_kernel(const __grid_constant_
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
   __syncthreads();
-  if (v.op == kOpRefinePre || v.op == kOpDirection || !v.part) return;   // steps without a sum
+  if (v.op == kOpRefinePre || !v.part) return;   // a step without a sum
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w = 0; w < kVecThreads / 32; ++w) t += ws[w];
@@ -224,12 +238,20 @@ __global__ void __launch_bounds__(kVecThreads) vec_kernel(const __grid_constant_
       w.inner_done = t == 0.0 ? 1 : 0;
       w.tol_cor2 = w.rn2 > 0.0 ? fmax(w.tol_in2, kCorSafety2 * w.tol2 * w.bn2 / w.rn2) : w.tol_in2;
       break;
-    case kOpPQ:
-      w.pq = t;
-      w.alpha = t != 0.0 ? w.rr / t : 0.0;
+    case kOpWR: {   // the step lengths from rr = r.r and wr = (A r).r alone
+      w.wr = t;
+      if (w.inner_it == 0) {
+        w.beta = 0.0;
+        w.alpha = t != 0.0 ? w.rr / t : 0.0;
+      } else {
+        w.beta = w.rr_prev != 0.0 ? w.rr / w.rr_prev : 0.0;
+        const double den = w.alpha != 0.0 ? t - w.beta * w.rr / w.alpha : 0.0;
+        w.alpha = den != 0.0 ? w.rr / den : 0.0;
+      }
       break;
+    }
     case kOpUpdate:
-      w.beta = w.rr != 0.0 ? t / w.rr : 0.0;
+      w.rr_prev = w.rr;
       w.rr = t;
       w.inner_it += 1;
       w.inner_done = (t <= w.tol_cor2 * w.rr0 || w.inner_it >= w.inner_cap || !(t == t)) ? 1 : 0;
@@ -301,7 +323,7 @@ struct Req {
   size_t off = 0, bytes = 0;
   // device workspace (inside the arena)
   double *x64 = nullptr, *r64 = nullptr, *b64 = nullptr, *y64 = nullptr;
-  void *d = nullptr, *r = nullptr, *p = nullptr, *qv = nullptr;
+  void *d = nullptr, *r = nullptr, *p = nullptr, *sv = nullptr, *wv = nullptr;   // inner CG vectors
   void* part_hi = nullptr;   // partial sums of split block rows, FP64-value product
   void* part_lo = nullptr;   // same, inner product
   double* dots = nullptr;
@@ -375,7 +397,7 @@ static size_t workspace_bytes(const Matrix& M, int kind, size_t es_in, int* nblk
   } else {
     part_lo = (size_t)std::max(handle_slots(M.lo), 1) * 16 * es_in;
     *nblk = (int)((n + kVecBlock - 1) / kVecBlock);
-    need = 3 * align256(n * 8) + 4 * align256(n * es_in) + align256(part_hi) + align256(part_lo) +
+    need = 3 * align256(n * 8) + 5 * align256(n * es_in) + align256(part_hi) + align256(part_lo) +
            align256((size_t)std::max(*nblk, 1) * 8);
   }
   if (part_hi_out) *part_hi_out = part_hi;
@@ -413,7 +435,8 @@ bool cbspmv_server_s::admit_one(const std::shared_ptr<Req>& r) {
     r->d = take(n * es_in);
     r->r = take(n * es_in);
     r->p = take(n * es_in);
-    r->qv = take(n * es_in);
+    r->sv = take(n * es_in);
+    r->wv = take(n * es_in);
     r->part_hi = take(part_hi);
     r->part_lo = take(part_lo);
     r->dots = (double*)take((size_t)std::max(r->nblk, 1) * 8);
@@ -431,11 +454,22 @@ void cbspmv_server_s::release(const std::shared_ptr<Req>& r) {
   r->slot = -1;
 }
 
+// after_kernel: the step directly follows a kernel on the stream (a product or another
+// step), so its launch may overlap that kernel's tail (programmatic dependent launch)
 template <class T>
-static cudaError_t launch_vec(const VecBatch& b, Scalars* sc, cudaStream_t s) {
+static cudaError_t launch_vec(const VecBatch& b, Scalars* sc, cudaStream_t s, bool after_kernel) {
   if (b.count == 0 || b.blk_base[b.count] == 0) return cudaSuccess;
-  vec_kernel<T><<<b.blk_base[b.count], kVecThreads, 0, s>>>(b, sc);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)b.blk_base[b.count]);
+  cfg.blockDim = dim3(kVecThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute pdl[1];
+  pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  pdl[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = pdl;
+  cfg.numAttrs = after_kernel ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, vec_kernel<T>, b, sc);
 }
 
 cbspmv_status_t cbspmv_server_s::tick(std::vector<std::shared_ptr<Req>>& act, std::string* err) {
@@ -474,17 +508,17 @@ cbspmv_status_t cbspmv_server_s::tick(std::vector<std::shared_ptr<Req>>& act, st
     v.n = mats[r->q.matrix].n;
     v.nblk = r->nblk;
     v.x64 = r->x64; v.r64 = r->r64; v.b64 = r->b64;
-    v.d = r->d; v.r = r->r; v.p = r->p; v.q = r->qv;
+    v.d = r->d; v.r = r->r; v.p = r->p; v.s = r->sv; v.w = r->wv;
     v.part = r->dots;
     b.blk_base[b.count + 1] = b.blk_base[b.count] + r->nblk;
     b.count++;
   };
-  auto vec = [&](const VecBatch& b) {
-    return inner64 ? launch_vec<double>(b, d_sc, s) : launch_vec<float>(b, d_sc, s);
+  auto vec = [&](const VecBatch& b, bool after_kernel) {
+    return inner64 ? launch_vec<double>(b, d_sc, s, after_kernel) : launch_vec<float>(b, d_sc, s, after_kernel);
   };
   for (auto& r : act)
     if (r->ph == kPhRefine) add(vb, r, kOpRefinePre);
-  cu(vec(vb), "refine pre-step");
+  cu(vec(vb, false), "refine pre-step");   // (after the input copies)
   // 3. products: FP64 values (y = Ax requests, true residuals), inner values (CG steps)
   std::vector<cb::RunArgs> hi, lo;
   int grid = 0;
@@ -499,7 +533,7 @@ cbspmv_status_t cbspmv_server_s::tick(std::vector<std::shared_ptr<Req>>& act, st
       cb::server_run_args(M.hi, r->x64, r->r64, -1.0, 1.0, r->part_hi, &a, &g, &ns, &dt);
       if (M.m) hi.push_back(a);
     } else {
-      cb::server_run_args(M.lo, r->p, r->qv, 1.0, 0.0, r->part_lo, &a, &g, &ns, &dt);
+      cb::server_run_args(M.lo, r->r, r->wv, 1.0, 0.0, r->part_lo, &a, &g, &ns, &dt);
       if (M.m) lo.push_back(a);
     }
     grid = g;
@@ -516,10 +550,10 @@ cbspmv_status_t cbspmv_server_s::tick(std::vector<std::shared_ptr<Req>>& act, st
       add(v1, r, kOpRefineDot);
       v1.v[v1.count - 1].first_outer = r->outer == 0;
     } else if (r->ph == kPhInner) {
-      add(v1, r, kOpPQ);
+      add(v1, r, kOpWR);
     }
   }
-  cu(vec(v1), "dot step 1");
+  cu(vec(v1, !hi.empty() || !lo.empty()), "dot step 1");
   // the refinement's convergence is known on the device; requests that continue start or
   // continue their inner solve
   VecBatch v2{};
@@ -527,13 +561,10 @@ cbspmv_status_t cbspmv_server_s::tick(std::vector<std::shared_ptr<Req>>& act, st
     if (r->ph == kPhRefine) add(v2, r, kOpRefineStart);   // harmless for a converged request
     else if (r->ph == kPhInner) add(v2, r, kOpUpdate);
   }
-  cu(vec(v2), "dot step 2");
-  VecBatch v3{};
-  for (auto& r : act)
-    if (r->ph == kPhInner) add(v3, r, kOpDirection);
-  cu(vec(v3), "direction step");
-  // 4b. further inner iterations of the solves in their inner phase: q = A p, alpha,
-  //     updates, direction; a solve whose inner CG converged meanwhile skips them (device).
+  cu(vec(v2, true), "dot step 2");
+  // 4b. further inner iterations of the solves in their inner phase: w = A r, the step
+  //     lengths from w . r, the updates with r . r; a solve whose inner CG converged
+  //     meanwhile skips them (device).
   //     Each solve runs `quota` iterations this tick: all inner_steps, or with
   //     cg_oldest_first inner_steps for the oldest, half for the next, a quarter for the rest
   {
@@ -546,7 +577,7 @@ cbspmv_status_t cbspmv_server_s::tick(std::vector<std::shared_ptr<Req>>& act, st
         inner.push_back({q, r});
       }
     std::vector<cb::RunArgs> lo2;
-    VecBatch vpq{}, vup{}, vdir{};
+    VecBatch vwr{}, vup{};
     int members = -1;
     for (int it = 1; it < o.inner_steps; ++it) {
       int n = 0;
@@ -555,28 +586,25 @@ cbspmv_status_t cbspmv_server_s::tick(std::vector<std::shared_ptr<Req>>& act, st
       if (n != members) {   // the batches of the solves with iterations left
         members = n;
         lo2.clear();
-        vpq = VecBatch{};
+        vwr = VecBatch{};
         vup = VecBatch{};
-        vdir = VecBatch{};
         for (auto& e : inner) {
           if (e.first <= it) continue;
           const auto& r = e.second;
           const Matrix& M = mats[r->q.matrix];
           cb::RunArgs a{};
           int g = 0, ns = 0, dt = 0;
-          cb::server_run_args(M.lo, r->p, r->qv, 1.0, 0.0, r->part_lo, &a, &g, &ns, &dt);
+          cb::server_run_args(M.lo, r->r, r->wv, 1.0, 0.0, r->part_lo, &a, &g, &ns, &dt);
           if (M.m) lo2.push_back(a);
           grid = g;
-          add(vpq, r, kOpPQ);
+          add(vwr, r, kOpWR);
           add(vup, r, kOpUpdate);
-          add(vdir, r, kOpDirection);
         }
       }
       if (!lo2.empty()) cu(cb::launch_spmv_batch(lo2.data(), (int)lo2.size(), grid, s), "batched product (inner)");
       stats.launches += lo2.empty() ? 0 : 1;
-      cu(vec(vpq), "inner p.q");
-      cu(vec(vup), "inner update");
-      cu(vec(vdir), "inner direction");
+      cu(vec(vwr, !lo2.empty()), "inner w.r");
+      cu(vec(vup, true), "inner update");
     }
   }
   // 5. scalars back to the host, then decide every request's next step
