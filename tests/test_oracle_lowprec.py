@@ -108,3 +108,76 @@ def test_fp32_bound_catches_a_dropped_term():
     bad[r] -= A.val[k] * x[A.col[k]]
     assert L.within_bound(y, y, s, L.fp32_bound(A))[0]
     assert not L.within_bound(bad, y, s, L.fp32_bound(A))[0]
+
+
+def _fp32_orders(p):
+    """Sums of the FP32 products p (float32 array) in five FP32 evaluation orders: left to
+    right, right to left, a pairwise tree, 32 strided partial sums added by a halving tree
+    (a warp's order), and one random permutation."""
+    f = np.float32
+    out = []
+    for seq in (p, p[::-1], np.random.default_rng(p.size).permutation(p)):
+        acc = f(0)
+        for v in seq:
+            acc = f(acc + v)
+        out.append(acc)
+    def tree(v):
+        v = list(v) or [f(0)]
+        while len(v) > 1:
+            v = [f(v[i] + v[i + 1]) if i + 1 < len(v) else v[i] for i in range(0, len(v), 2)]
+        return v[0]
+    out.append(tree(p))
+    lanes = [f(0)] * 32
+    for i, v in enumerate(p):
+        lanes[i % 32] = f(lanes[i % 32] + v)
+    out.append(tree(lanes))
+    return out
+
+
+def test_fp32_bound_holds_for_every_evaluation_order():
+    """Soundness of the acceptance bound (Higham, Sec. 3.1): a row of k FP32 products summed in
+    FP32 in any order, then scaled by alpha and updated with beta y0 in FP32, stays within
+    fp32_bound's gamma_{k + 10} times sum |a x| of the exact result (exact products and a
+    correctly rounded sum, math.fsum). Rows of 1..400 entries mixing signs and 12 decades."""
+    import math
+    from paper_2605_18515_gb300.inputs import CSR
+    rng = np.random.default_rng(21)
+    f = np.float32
+    worst = 0.0
+    for trial in range(60):
+        k = int(rng.integers(1, 401))
+        a = (rng.standard_normal(k) * 10.0 ** rng.integers(-6, 6, k)).astype(f)
+        x = rng.uniform(-1, 1, k).astype(f)
+        alpha, beta, y0 = (f(1), f(0), f(0)) if trial % 2 else (f(-0.7), f(1.3), f(rng.standard_normal()))
+        A = CSR(1, k, np.array([0, k], np.int64), np.arange(k, dtype=np.int32), a.astype(np.float64))
+        g = L.fp32_bound(A)[0]
+        exact_terms = [float(ai) * float(xi) for ai, xi in zip(a, x)]   # exact in FP64 (24 + 24 bits)
+        dot = math.fsum(exact_terms)
+        exact = float(alpha) * dot + float(beta) * float(y0)
+        scale = abs(float(alpha)) * math.fsum(abs(t) for t in exact_terms) + abs(float(beta) * float(y0))
+        for sfp in _fp32_orders((a * x).astype(f)):
+            y = f(f(alpha * sfp) + f(beta * y0))
+            err = abs(float(y) - exact)
+            assert err <= g * scale, (trial, k, err / scale, g)
+            worst = max(worst, err / scale / g)
+    assert worst > 0.0
+
+
+def test_fp32_bound_is_nearly_attained():
+    """Tightness: the bound is not loose by more than a small factor. A row holding 1 and
+    then k - 1 entries of 2^-24 (x = 1) summed left to right in FP32 stays at 1 (each
+    1 + 2^-24 is a tie that rounds to even), an error of (k - 1) 2^-24 against a scale of
+    1 + (k - 1) 2^-24: that is (k - 1) / (k + 10) of gamma_{k + 10}, within it and above 0.8
+    of it for k = 128. A unit roundoff of 2^-23 in the bound (twice too loose) fails here."""
+    from paper_2605_18515_gb300.inputs import CSR
+    f = np.float32
+    k = 128
+    a = np.concatenate([[1.0], np.full(k - 1, 2.0 ** -24)])
+    A = CSR(1, k, np.array([0, k], np.int64), np.arange(k, dtype=np.int32), a)
+    acc = f(0)
+    for v in a.astype(f):
+        acc = f(acc + v)
+    assert acc == f(1)
+    exact = 1.0 + (k - 1) * 2.0 ** -24
+    ratio = abs(float(acc) - exact) / exact / L.fp32_bound(A)[0]
+    assert 0.8 < ratio <= 1.0, ratio
