@@ -17,6 +17,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -147,6 +148,13 @@ class ClockSampler:
         reasons = sorted({names[i] for s in use for i in range(4) if len(s) > 4 + i and s[4 + i].lower().startswith("active")})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(use), "in_window": len(inwin)}
+
+
+def timed_repeats(steps, est_ms_per_step, target_s=1.0):
+    """Repeats of the `steps`-product block in the timed region: enough for the region to
+    last about target_s, so that the clock sampler (one sample per 25 ms) sees it; at least 1."""
+    block_s = max(steps, 1) * max(est_ms_per_step, 1e-6) * 1e-3
+    return max(1, int(math.ceil(target_s / block_s)))
 
 
 def max_over_ranks(values, dist=None, device="cpu"):
@@ -744,6 +752,19 @@ def main():
             M.run(xd, yd, 1.0, 0.0, stream=stream)
         stream.synchronize()
         M.check_device(stream)
+        # the timed region repeats the block of `steps` products until it lasts ~1 s, so that
+        # the clock samples fall inside it (ms_per_step is the average over all repeats); the
+        # time per product is estimated after the warm-up from a short untimed batch, the
+        # slowest rank's estimate giving every rank the same count
+        n_cal = max(3, min(args.steps, 50))
+        wa, wb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        wa.record(stream)
+        for _ in range(n_cal):
+            M.run(xd, yd, 1.0, 0.0, stream=stream)
+        wb.record(stream)
+        stream.synchronize()
+        est_ms = wa.elapsed_time(wb) / n_cal
+        repeats = timed_repeats(args.steps, max_over_ranks([est_ms], dist, "cuda")[0])
         # the FP64 FMA roofline, measured on this device now (before the timed region)
         fma = bd.measure_fp64_fma(local, stream) if not lp else None
 
@@ -756,7 +777,7 @@ def main():
         torch.cuda.synchronize()
         w0 = time.time()
         ev0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(args.steps * repeats):
             M.run(xd, yd, 1.0, 0.0, stream=stream)
         ev1.record(stream)
         ev1.synchronize()
@@ -766,7 +787,7 @@ def main():
             dist.barrier()
         time.sleep(0.25)
         sampler.stop()
-        ms = ev0.elapsed_time(ev1) / args.steps
+        ms = ev0.elapsed_time(ev1) / (args.steps * repeats)
         M.check_device(stream)
 
         # end to end through the C ABI from pinned host memory
@@ -889,7 +910,11 @@ def main():
             "e2e": {"value": round(job_gflops(ws, flops, e2e_max), 3), "unit": "GFLOP/s",
                     "ms_per_step": round(e2e_max, 4), "h2d_bytes_per_step": esz * A.n,
                     "d2h_bytes_per_step": esz * A.m, "api": "cbspmv_run_host"},
-            "gpu_launches": args.steps * kt["launches_per_run"],
+            "gpu_launches": args.steps * repeats * kt["launches_per_run"],
+            "timed_region": {"repeats": repeats, "products": args.steps * repeats,
+                             "seconds": round(args.steps * repeats * ms * 1e-3, 3),
+                             "note": "the block of `steps` products repeated until the region lasts "
+                                     "~1 s; ms_per_step is the average over all of them"},
             "clocks": clocks,
             "analyze_ms": round(st["analyze_ms"], 1),
         }

@@ -40,3 +40,16 @@ def test_replica_max_and_throughput(tmp_path):
     import bench
     assert bench.job_gflops(2, 1e9, 2.0) == pytest.approx(1000.0)   # 2 ranks x 1 GFLOP in 2 ms
     assert bench.max_over_ranks([3.0, 4.0]) == [3.0, 4.0]           # one process
+
+
+def test_timed_region_lasts_about_a_second():
+    """A short block of products is repeated until the timed region lasts ~1 s (so the 25 ms
+    clock samples fall inside it); a block that already lasts that long runs once."""
+    import bench
+    assert bench.timed_repeats(20, 0.19) == 264          # 20 x 0.19 ms = 3.8 ms per block
+    assert bench.timed_repeats(5000, 0.3) == 1           # 1.5 s already
+    assert bench.timed_repeats(5000, 0.19) == 2          # 0.95 s: one more block
+    assert bench.timed_repeats(0, 0.0) >= 1
+    for steps, est in ((1, 0.005), (7, 0.12), (300, 1.1)):
+        r = bench.timed_repeats(steps, est)
+        assert r * steps * est * 1e-3 >= 1.0 > (r - 1) * steps * est * 1e-3
