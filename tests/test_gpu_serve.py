@@ -125,7 +125,8 @@ def test_later_corrections_stop_at_the_gap_to_tol(env):
     and tol ||b|| (with 0.3 to spare): with inner_tol 1e-6 and tol 1e-8 the first correction
     takes the iterations of a 1e-6 solve (N) and the second those of a ~3e-3 one, so the
     solve takes two refinements and well under the 2N iterations of two full-depth
-    corrections (FP32 simulation of this 20^3 case: 84 against 128, N = 63)."""
+    corrections (an FP32 simulation of a 20^3 Laplacian with another uniform right-hand side:
+    84 iterations against 128, N = 63)."""
     bd, _ = env
     L = I.laplacian3d(20)
     b = I.uniform_pm1(9, I.TAG_RHS, L.n)
